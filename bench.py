@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the SDM coalescence step on one B300 (per rank).
+
+Workload (default): the gravitational box -- one cell of 2^20 super-droplets,
+lognormal radii (median 15 um, sigma_g 1.4), n0 = 1e8 m^-3, dV = 1e6 m^3,
+dt = 1 s, FP64-exact decisions.  A "step" is one coalescence timestep over all
+super-droplets (Fig. "fig:algo": removal, shuffle, pairing, eq. (p), gamma,
+update).  Metric: super-droplet-steps per second (live SDs x steps / time).
+
+The 16 MB state fits in the 126 MB L2, so L2 is flushed (a 256 MB write)
+between timed steps and each step is timed alone with CUDA events on the
+library's stream; ms_per_step is their mean.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own box (independent problems: weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_06318_b300 import inputs  # noqa: E402
+
+METRIC = "coalescence super-droplet-steps/s on 1 B300, % HBM roofline; batched/surrogate vs FP64"
+UNIT = "SD-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name, rank=0):
+    s = inputs.WORKLOADS[name]() if name != "gravitational_box" else inputs.gravitational_box(seed=42 + rank)
+    return s
+
+
+def cpu_baseline(s, budget_s=12.0):
+    """The oracle as it stands, single-threaded on a host core, on a bounded sample of steps."""
+    import oracle
+    o = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    n_live = int(np.count_nonzero(o.xi))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(s["dt"], 42, steps)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_live * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the {s['name']} workload ({n_live} SDs), single-threaded C, FP64"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    s = workload(args.workload)
+    n = len(s["xi"])
+    # bound the run to a few minutes: a full step of the oracle on this workload
+    probe = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    t0 = time.perf_counter()
+    probe.step(s["dt"], 42, 0)
+    t_step = time.perf_counter() - t0
+    sample = s
+    if (args.steps + args.warmup) * t_step > 150.0 and args.workload == "gravitational_box":
+        n_sub = 1 << int(np.floor(np.log2(max(1024, n * 150.0 / ((args.steps + args.warmup) * t_step)))))
+        sample = inputs.gravitational_box(n_sd=n_sub)
+    o = oracle.System(sample["xi"], sample["v"], sample["cell_start"], sample["dv"], sample["kernel_id"],
+                      sample["golovin_b"])
+    for w in range(args.warmup):
+        o.step(sample["dt"], 42, w)
+    n_live = int(np.count_nonzero(o.xi))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        o.step(sample["dt"], 42, args.warmup + k)
+    el = time.perf_counter() - t0
+    value = n_live * args.steps / el
+    desc = (f"{args.steps} timed steps of {sample['name']} with {len(sample['xi'])} SDs "
+            f"(oracle, single-threaded C, FP64)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n_sd": len(sample["xi"]), "n_cell": 1,
+                                            "kernel": "gravitational", "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2101_06318_b300 import sdm
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    s = workload(args.workload, rank)
+    n = len(s["xi"])
+    prec = args.precision
+    with torch.cuda.stream(stream):
+        st = sdm.from_inputs(s)
+        if args.schedule:
+            st.set_schedule(**json.loads(args.schedule))
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        step = 0
+        for _ in range(args.warmup):
+            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+            step += 1
+        st.sync()
+        live0 = st.remove_zero()
+        stats0 = None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        st.set_profiling(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))                    # evict the state from L2 between steps
+                ev[k][0].record(stream)
+                st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+                ev[k][1].record(stream)
+                step += 1
+            torch.cuda.synchronize()
+        prof = st.profile()
+        st.set_profiling(False)
+        st.sync()
+        if dist:
+            dist.barrier()
+        times = [a.elapsed_time(b) for a, b in ev]
+        live1 = st.remove_zero()
+        ms = float(np.mean(times))
+        sd_steps = 0.5 * (live0 + live1) * args.steps
+        # collisions per step (for the write part of the algorithmic bytes), one extra stats step
+        stats = st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], stats=True)
+        step += 1
+        launches = st.launches_per_step() * args.steps
+
+        # e2e: host (pinned) buffers in, step, host buffers out, through the C ABI
+        xi_h, at_h, _ = st.get_state()
+        xi_p = torch.from_numpy(xi_h.view(np.int64)).pin_memory()
+        at_p = torch.from_numpy(at_h).pin_memory()
+        e2e_steps = min(args.steps, 50)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            st.set_state(xi_p, at_p)
+            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+            st.get_state(xi_p, at_p)
+            step += 1
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        bytes_io = xi_p.numel() * 8 + at_p.numel() * 8
+
+    # max over ranks
+    tot_ms = ms * args.steps
+    if dist:
+        t = torch.tensor([tot_ms, sd_steps, e2e_s], dtype=torch.float64, device=dev)
+        ts = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(ts, t)
+        tot_ms = max(float(x[0]) for x in ts)
+        sd_total = sum(float(x[1]) for x in ts)
+        e2e_s = max(float(x[2]) for x in ts)
+    else:
+        sd_total = sd_steps
+    if rank != 0:
+        return
+    value = sd_total / (tot_ms * 1e-3)
+    peak, peak_src = _peaks()
+    # algorithmic bytes per SD-step: read xi and v (16 B); each collision writes at most
+    # 2 x (xi + v) = 32 B
+    bytes_step = 16.0 * live0 + 32.0 * stats["n_collisions"]
+    kern = {k: {"launches": v[0], "ms_total": v[1], "ms_per_launch": (v[1] / v[0] if v[0] else None)}
+            for k, v in prof.items() if v[0]}
+    tot_k = sum(v["ms_total"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["ms_total"] / tot_k
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    step_kernel_ms = sum(v["ms_per_launch"] for v in kern.values())
+    achieved_step = bytes_step / (step_kernel_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "+".join(kern), "dominant": dom,
+                "achieved": achieved_step, "peak": peak, "unit": "GB/s", "frac": achieved_step / peak,
+                "peak_source": f"{peak_src} hbm_gbs", "traffic": None,
+                "algorithmic_bytes_per_step": bytes_step,
+                "note": "algorithmic bytes of the whole step over the summed device time of its kernels"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_sd": n, "n_cell": len(s["dv"]), "kernel": "gravitational",
+                   "precision": prec, "dt_s": s["dt"], "dV_m3": float(s["dv"][0]), "n0_m3": 1e8,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}",
+                   "schedule": st.schedule},
+        "roofline": roofline,
+        "kernels": kern,
+        "e2e": {"value": (sd_total / args.steps) / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "stats_per_step": stats,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(s)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gravitational_box", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--schedule", default=None, help="JSON of sdm_schedule fields")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

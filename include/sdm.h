@@ -1,0 +1,239 @@
+/*
+ * sdm.h -- C ABI of the B300 (sm_103a) Super-Droplet Method coalescence
+ * library (libsdm.so).
+ *
+ * The library implements the coalescence step of the Super-Droplet Method as
+ * organised in Bartman & Arabas, arXiv:2101.06318: the state of Sec. 3.1
+ * (multiplicities, extensive attributes, cell segmentation; Fig. "lst:vars"),
+ * and the per-timestep workflow of Sec. 3.2, Fig. "fig:algo" -- Step 0
+ * removal of zero-multiplicity super-droplets, Step 1 cell-wise shuffling and
+ * pairing, Step 2 collision probability, eq. (p), Step 3 collision triggering
+ * (gamma, eq. (gamma2)) and attribute update (eqs. (coal_attr_0), (coal)).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an sdm_status and never aborts, traps or exits.
+ *  - Device work is enqueued on the CUDA stream given to sdm_alloc (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream).  Calls
+ *    return once the work is enqueued unless stated otherwise; errors found
+ *    by kernels (capacity overflow and similar) are latched in a device error
+ *    word and returned by sdm_sync and by the next call that synchronises.
+ *  - "ptrs_on_device" arguments say whether a pointer is device memory
+ *    (non-zero) or host memory (0).  Host memory may be pageable or pinned;
+ *    the library copies out of / into it before returning.
+ *  - A state is not thread-safe: one host thread at a time per state.
+ *    Different states are independent.
+ *  - All arrays are structure-of-arrays: xi[n_slots], attr[n_attr][n_slots]
+ *    (row-major, attribute 0 is the particle volume v in m^3).
+ *
+ * Slot model.  Storage is a fixed array of slots grouped by cell: cell c owns
+ * slots [cell_start[c], cell_start[c+1]).  A slot whose multiplicity is 0 is a
+ * removed super-droplet (Sec. 2.2, "the j-th super-droplet is removed"); Step 0
+ * excludes it from the cell's list every step.  The slot's index within its
+ * cell is the super-droplet's identity for the random number contract, so the
+ * results never depend on how or when storage is compacted.
+ *
+ * Random number contract (Philox4x32-10, Salmon et al. SC'11; key = seed):
+ *   shuffle key of local slot l of cell c at step s = philox(l>>2, c, s, 0)[l&3]
+ *   phi of candidate pair m of cell c at step s: x = philox(m>>1, c, s, 1),
+ *       u53 = ((x[2(m&1)] << 32) | x[2(m&1)+1]) >> 11, phi = u53 * 2^-53
+ *   a cell's live SDs are ordered by (key, l) ascending; pair m is made of
+ *   the SDs at positions 2m and 2m+1 of that order (Sec. 2.2 Step 1,
+ *   Fig. "pair_flag").
+ */
+#ifndef SDM_H
+#define SDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDM_OK = 0,
+    SDM_EINVAL = 1,     /* invalid argument or invalid initial state */
+    SDM_ENOMEM = 2,     /* device or host allocation failed / workspace too small */
+    SDM_ECAPACITY = 3,  /* a size limit was exceeded (slots, cells, bucket capacity) */
+    SDM_ERANGE = 4,     /* a multiplicity >= 2^53 (xi must convert to double exactly) */
+    SDM_ECUDA = 5,      /* a CUDA runtime call failed */
+    SDM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    SDM_ENOTSUP = 7     /* option not supported by this build */
+} sdm_status;
+
+/* Coalescence kernel a(v1, v2) selected per cell (Sec. 4). */
+typedef enum {
+    SDM_KERNEL_GOLOVIN = 0,        /* a = b (v1 + v2), b = sdm_step_params.golovin_b */
+    SDM_KERNEL_GRAVITATIONAL = 1   /* pi (r1+r2)^2 |vt(r1) - vt(r2)| E(r1, r2) */
+} sdm_kernel_id;
+
+/* Arithmetic of the collision decision (Steps 2-3). */
+typedef enum {
+    /* Results identical, bit for bit, to an FP64 evaluation of eq. (p) and
+     * gamma: the probability is first bounded in FP32 and only pairs whose
+     * integer outcome the bound cannot settle are re-evaluated in FP64. */
+    SDM_PREC_FP64 = 0,
+    /* The decision is taken from the FP32 value of p and a 24-bit phi;
+     * multiplicities stay exact uint64 and the attribute update stays FP64. */
+    SDM_PREC_FP32 = 1
+} sdm_precision;
+
+typedef struct sdm_state sdm_state;   /* opaque, owned by the library */
+
+typedef struct {
+    double dt;                 /* time step [s] (> 0) */
+    double golovin_b;          /* Golovin constant b [1/s] */
+    uint64_t seed;             /* Philox key */
+    uint32_t step;             /* index s of the first step enqueued by this call */
+    uint32_t precision;        /* sdm_precision */
+    /* Optional device pointer.  When non-NULL the step index is read from
+     * *d_step on the device and incremented there after each step (the host
+     * 'step' field is ignored), so a captured CUDA graph advances the random
+     * stream on every replay. */
+    uint32_t* d_step;
+} sdm_step_params;
+
+typedef struct {
+    uint64_t n_pairs;        /* candidate pairs examined */
+    uint64_t n_collisions;   /* pairs with gamma~ > 0 */
+    uint64_t n_removed;      /* super-droplets whose multiplicity became 0 */
+    uint64_t sum_gamma;      /* sum of gamma~ over pairs */
+    uint64_t n_fp64;         /* pairs whose decision was re-evaluated in FP64 */
+} sdm_step_stats;
+
+/* Tunables of the device schedule.  They change speed only: results do not
+ * depend on them (the random stream is keyed by cell and slot, not by tile). */
+typedef struct {
+    uint32_t tile_slots;      /* max slots of the cells packed into one CTA (power of 2, 256..4096) */
+    uint32_t tile_threads;    /* threads per tile CTA (64..512, multiple of 32) */
+    uint32_t bucket_target;   /* mean SDs per bucket in the large-cell sort (256..4096, power of 2) */
+    uint32_t persistent;      /* 0: one CTA per tile; k > 0: k CTAs per SM pulling tiles */
+} sdm_schedule;
+
+/* Library version string. */
+const char* sdm_version(void);
+
+/* Human readable name of a status code. */
+const char* sdm_status_str(sdm_status s);
+
+/* Bytes of device workspace needed by a state of this size when the caller
+ * provides the memory (an upper bound for any cell layout). */
+size_t sdm_workspace_bytes(uint64_t n_slots_cap, uint32_t n_cell, uint32_t n_attr);
+
+/* Create a state on the current CUDA device.
+ *   n_slots_cap: maximum number of slots (< 2^32);  n_cell >= 1;  n_attr >= 1.
+ *   cuda_stream: cudaStream_t (as void*) all device work is ordered on.
+ *   workspace, ws_bytes: optional caller-owned device buffer (e.g. a torch
+ *     tensor) from which all device memory is carved; NULL = the library
+ *     allocates with cudaMalloc.  The library never frees caller memory; the
+ *     buffer must outlive the state.
+ * Errors: SDM_EINVAL (bad sizes), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_alloc(sdm_state** out, uint64_t n_slots_cap, uint32_t n_cell, uint32_t n_attr,
+                     void* cuda_stream, void* workspace, size_t ws_bytes);
+
+/* Load the initial super-droplet population (Sec. 3.1 state; Sec. 4 set-ups).
+ *   xi[n_sd]          multiplicities (0 = removed slot, kept as storage)
+ *   attr[n_attr][n_sd] extensive attributes, row-major, attr[0] = volume v > 0
+ *   cell_id[n_sd]     cell of each SD (< n_cell); SDs are grouped by cell with a
+ *                     stable counting sort, so slot order within a cell is the
+ *                     input order.
+ *   dv[n_cell]        cell volume Delta V [m^3] (> 0)
+ *   kernel_id[n_cell] sdm_kernel_id per cell; NULL = all Golovin.
+ * Errors: SDM_EINVAL (cell_id >= n_cell, v not finite and > 0 on a live slot,
+ * dv <= 0, unknown kernel id), SDM_ERANGE (xi >= 2^53), SDM_ECAPACITY
+ * (n_sd > n_slots_cap).  Synchronises the stream. */
+sdm_status sdm_init_state(sdm_state* st, const uint64_t* xi, const double* attr,
+                          const uint32_t* cell_id, uint64_t n_sd, const double* dv,
+                          const uint8_t* kernel_id, int ptrs_on_device);
+
+/* Same as sdm_init_state but the layout is given as cell_start[n_cell+1]
+ * (slots already grouped by cell; cell_start[0] = 0, non-decreasing,
+ * cell_start[n_cell] = n_sd).  No sorting is done. */
+sdm_status sdm_init_state_segmented(sdm_state* st, const uint64_t* xi, const double* attr,
+                                    const uint32_t* cell_start, uint64_t n_sd, const double* dv,
+                                    const uint8_t* kernel_id, int ptrs_on_device);
+
+/* Overwrite xi and attr of an initialised state in its own slot layout
+ * (checkpoint restore, or host-resident state streamed in).  Validates like
+ * sdm_init_state.  Asynchronous for device pointers. */
+sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, int ptrs_on_device);
+
+/* Copy the state out in slot layout: xi[n_sd], attr[n_attr][n_sd] (either may
+ * be NULL), cell_start[n_cell+1] (may be NULL), *n_sd (may be NULL).  For
+ * host pointers the call synchronises; removed SDs appear with xi = 0. */
+sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* cell_start,
+                         uint64_t* n_sd, int ptrs_on_device);
+
+/* Enqueue n_steps coalescence timesteps (Fig. "fig:algo", Steps 0-3), step
+ * indices params->step .. params->step + n_steps - 1 (or read from
+ * params->d_step).  stats (nullable) receives the sums over the steps; when
+ * non-NULL the call synchronises to read them.  Without stats the call is
+ * asynchronous and capturable in a CUDA graph (use d_step for replays). */
+sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
+                                sdm_step_stats* stats);
+
+/* Step 0 on its own (remove_if_equal_0): count the live SDs of every cell.
+ * Removal is already applied inside every step, so this call changes no
+ * result; it reports the total live count (nullable) and is idempotent.
+ * Synchronises when n_live is non-NULL. */
+sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live);
+
+/* Mass spectrum (Sec. 4): out[b] = rho * sum(xi v) / (V * ln(r[b+1]/r[b])) over
+ * live SDs with (4 pi/3) r[b]^3 <= v < (4 pi/3) r[b+1]^3, rho = 1000 kg/m^3.
+ * cell = index of one cell, or UINT32_MAX for all cells (V = sum of dV).
+ * r_edges[n_bins+1] (host), increasing, > 0.  out[n_bins] host or device. */
+sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, uint32_t cell,
+                        double* out, int out_on_device);
+
+/* Totals over live SDs: *n_total = sum xi (exact), *mass = sum xi v (FP64,
+ * summation order unspecified), *n_live.  Any pointer may be NULL.
+ * Synchronises. */
+sdm_status sdm_totals(sdm_state* st, uint64_t* n_total, double* mass, uint64_t* n_live);
+
+/* Read or change the device schedule (speed only). */
+sdm_status sdm_get_schedule(sdm_state* st, sdm_schedule* out);
+sdm_status sdm_set_schedule(sdm_state* st, const sdm_schedule* sched);
+
+/* Time candidate schedules on the current state (the state is saved and
+ * restored around the trials) and keep the fastest.  n_steps per trial.
+ * Synchronises.  best (nullable) receives the chosen schedule. */
+sdm_status sdm_autotune(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
+                        sdm_schedule* best);
+
+/* Wait for all work enqueued on the state's stream; returns the first error
+ * latched by a kernel since the last sdm_sync (then clears it), or SDM_ECUDA. */
+sdm_status sdm_sync(sdm_state* st);
+
+/* Release the state and the device memory the library allocated. NULL is a no-op. */
+void sdm_free(sdm_state* st);
+
+/* Kernel profiling.  While enabled, every kernel launch of the coalescence step
+ * is bracketed by CUDA events on the state's stream; sdm_get_profile
+ * synchronises and reports, per kernel kind (0 = small-cell tile kernel,
+ * 1 = large-cell scatter, 2 = large-cell finish), the number of launches and
+ * their summed device time in ms since profiling was enabled.  Arrays have
+ * SDM_N_KERNEL_KINDS entries.  Not for use inside CUDA graph capture. */
+#define SDM_N_KERNEL_KINDS 3
+sdm_status sdm_set_profiling(sdm_state* st, int enable);
+sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms);
+
+/* Number of kernel launches one timestep enqueues with the current schedule
+ * (a d_step step adds one more for the counter). */
+sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n);
+
+/* Evaluate, for n pairs (v1[i], v2[i]) with multiplicities (xi1[i], xi2[i]) in
+ * a cell of n_cell_sd live SDs and volume dv, the collision kernel and eq.
+ * (p) both ways: p64[i] is the FP64 value the library uses when it
+ * re-evaluates a pair (bit-identical to the documented operation order), and
+ * p32[i], err32[i] the FP32 value and its error bound, |p64 - p32| <= err32.
+ * All arrays are device pointers.  Exposes Step 2 alone for testing
+ * (dependency injection, Sec. 5). */
+sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2,
+                          const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd,
+                          double dv, double dt, double golovin_b,
+                          double* p64, float* p32, float* err32);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDM_H */

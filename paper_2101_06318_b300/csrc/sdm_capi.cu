@@ -1,0 +1,906 @@
+// sdm_capi.cu -- host side of the C ABI declared in include/sdm.h.
+//
+// Owns the device state (structure-of-arrays slots grouped by cell), plans the
+// device schedule (which cells are packed into shared-memory tiles and which
+// go through the two-pass large-cell path), validates inputs and launches the
+// kernels of sdm_kernels.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sdm.h"
+#include "sdm_kernels.cuh"
+
+using namespace sdm;
+
+namespace {
+
+constexpr uint64_t XI_LIMIT = 1ull << 53;
+constexpr double RHO_WATER = 1000.0;
+constexpr double FOUR_PI_OVER_THREE = 4.18879020478639053;
+constexpr uint32_t ERR_INVALID = 1u << 8;
+constexpr uint32_t ERR_RANGE = 1u << 9;
+
+struct DevAlloc {
+    void* p;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct sdm_state {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t cap = 0;
+    uint32_t n_cell = 0, n_attr = 0;
+    uint64_t n_sd = 0;
+    bool initialised = false;
+
+    // memory: either owned cudaMalloc blocks or a caller workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0, ws_fixed = 0, ws_used = 0;
+    std::vector<DevAlloc> owned_fixed, owned_layout;
+
+    // state arrays
+    uint64_t* d_xi = nullptr;
+    double* d_attr = nullptr;
+    uint32_t* d_cell_start = nullptr;
+    double* d_dv = nullptr;
+    uint8_t* d_kid = nullptr;
+    uint32_t* d_err = nullptr;
+    unsigned long long* d_stats = nullptr;   // [5]
+    unsigned long long* d_acc = nullptr;     // [4] totals scratch
+    uint32_t* d_work = nullptr;              // [2] persistent tile counter
+
+    // schedule / layout
+    sdm_schedule sched{};
+    TileDesc* d_tiles = nullptr;
+    uint32_t n_tiles = 0, max_cells_per_tile = 0;
+    TileLayout tile_L{};
+    BigCell* d_big = nullptr;
+    uint32_t n_big = 0;
+    BigChunk* d_chunks = nullptr;
+    uint32_t n_chunks = 0;
+    uint32_t* d_bucket_big = nullptr;
+    uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
+    uint32_t* d_cursor = nullptr;            // [2][n_buckets]
+    uint64_t* d_scratch = nullptr;
+    FinishLayout fin_L{};
+    int clean_parity = -1;                   // -1: both cursor buffers zero; 0/1: that one; 2: unknown
+
+    // host copies of the layout
+    std::vector<uint32_t> h_cell_start;
+    std::vector<double> h_dv;
+    std::vector<uint8_t> h_kid;
+    int n_sm = 148;
+
+    // optional per-kernel event timing
+    bool profiling = false;
+    struct Rec { int kind; cudaEvent_t e0, e1; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    uint32_t prof_launches[SDM_N_KERNEL_KINDS] = {0, 0, 0};
+    double prof_ms[SDM_N_KERNEL_KINDS] = {0, 0, 0};
+};
+
+namespace {
+
+sdm_status cuda_status(cudaError_t e)
+{
+    return e == cudaSuccess ? SDM_OK : (e == cudaErrorMemoryAllocation ? SDM_ENOMEM : SDM_ECUDA);
+}
+
+#define SDM_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_status(e_);   \
+    } while (0)
+
+#define SDM_TRY(call)                                    \
+    do {                                                 \
+        sdm_status s_ = (call);                          \
+        if (s_ != SDM_OK) return s_;                     \
+    } while (0)
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// allocate device memory: from the workspace (bump) or with cudaMalloc
+sdm_status dev_alloc(sdm_state* st, void** out, size_t bytes, bool layout)
+{
+    bytes = round256(bytes + 256);   // padding: bulk prefetches may round the end up to 16 bytes
+    if (st->ws) {
+        if (st->ws_used + bytes > st->ws_bytes) return SDM_ENOMEM;
+        *out = st->ws + st->ws_used;
+        st->ws_used += bytes;
+        return SDM_OK;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SDM_ENOMEM;
+    }
+    (layout ? st->owned_layout : st->owned_fixed).push_back({p, bytes});
+    *out = p;
+    return SDM_OK;
+}
+
+void free_layout(sdm_state* st)
+{
+    for (auto& a : st->owned_layout) cudaFree(a.p);
+    st->owned_layout.clear();
+    if (st->ws) st->ws_used = st->ws_fixed;
+    st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
+    st->d_cursor = nullptr; st->d_scratch = nullptr;
+    st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
+}
+
+template <typename T>
+sdm_status upload(sdm_state* st, T** d, const std::vector<T>& h)
+{
+    if (h.empty()) { *d = nullptr; return SDM_OK; }
+    SDM_TRY(dev_alloc(st, (void**)d, h.size() * sizeof(T), true));
+    SDM_CUDA(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st->stream));
+    return SDM_OK;
+}
+
+uint32_t ceil_log2_h(uint64_t w)
+{
+    uint32_t b = 0;
+    while ((1ull << b) < w) ++b;
+    return b;
+}
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+sdm_status check_schedule(const sdm_schedule& s)
+{
+    if (!is_pow2(s.tile_slots) || s.tile_slots < 256 || s.tile_slots > 4096) return SDM_EINVAL;
+    if (s.tile_threads < 64 || s.tile_threads > 512 || s.tile_threads % 32) return SDM_EINVAL;
+    if (!is_pow2(s.bucket_target) || s.bucket_target < 256 || s.bucket_target > 4096) return SDM_EINVAL;
+    if (s.persistent > 32) return SDM_EINVAL;
+    return SDM_OK;
+}
+
+// Plan tiles (runs of consecutive small cells) and the large-cell buckets.
+sdm_status build_layout(sdm_state* st)
+{
+    free_layout(st);
+    const sdm_schedule& S = st->sched;
+    const std::vector<uint32_t>& cs = st->h_cell_start;
+    const uint32_t max_cells = std::min<uint32_t>(256, S.tile_slots);
+    std::vector<TileDesc> tiles;
+    std::vector<BigCell> bigs;
+    std::vector<BigChunk> chunks;
+    std::vector<uint32_t> bucket_big;
+    TileDesc cur{0, 0, 0, 0};
+    uint32_t cur_slots = 0;
+    auto flush = [&]() {
+        if (cur.n_cells && cur_slots) {
+            cur.slot_end = cur.slot_begin + cur_slots;
+            tiles.push_back(cur);
+        }
+        cur.n_cells = 0;
+        cur_slots = 0;
+    };
+    const uint32_t tbits = ceil_log2_h(S.bucket_target);
+    uint32_t bucket_cap = 0, max_nb = 1;
+    for (uint32_t c = 0; c < st->n_cell; ++c) {
+        const uint32_t w = cs[c + 1] - cs[c];
+        if (w > S.tile_slots) {
+            flush();
+            BigCell b{};
+            b.cell = c;
+            b.slot_begin = cs[c];
+            b.width = w;
+            const uint32_t lw = ceil_log2_h(w);
+            uint32_t nbits = lw > tbits ? lw - tbits : 0;
+            nbits = std::min<uint32_t>(nbits, BIG_MAX_BUCKET_BITS);
+            b.nbits = nbits;
+            b.bucket_base = (uint32_t)bucket_big.size();
+            const uint32_t nb = 1u << nbits;
+            for (uint32_t k = 0; k < nb; ++k) bucket_big.push_back((uint32_t)bigs.size());
+            const uint32_t mean = (w + nb - 1) / nb;
+            bucket_cap = std::max(bucket_cap, 2 * mean + 64);
+            max_nb = std::max(max_nb, nb);
+            for (uint32_t l = 0; l < w; l += BIG_CHUNK)
+                chunks.push_back(BigChunk{(uint32_t)bigs.size(), l, std::min(w, l + BIG_CHUNK), 0});
+            bigs.push_back(b);
+            continue;
+        }
+        if (cur.n_cells && (cur_slots + w > S.tile_slots || cur.n_cells == max_cells)) flush();
+        if (cur.n_cells == 0) { cur.slot_begin = cs[c]; cur.cell_begin = c; }
+        cur.n_cells++;
+        cur_slots += w;
+    }
+    flush();
+    bucket_cap = (bucket_cap + 31) & ~31u;
+    if (!bigs.empty()) {
+        const FinishLayout fl = finish_layout(bucket_cap);
+        if (fl.bytes > 200 * 1024) return SDM_ECAPACITY;   // a cell too large for this bucket width
+        st->fin_L = fl;
+    }
+    st->tile_L = tile_layout(S.tile_slots, max_cells);
+    st->max_cells_per_tile = max_cells;
+    if (st->tile_L.bytes > 227 * 1024) return SDM_ECAPACITY;
+    SDM_TRY(upload(st, &st->d_tiles, tiles));
+    SDM_TRY(upload(st, &st->d_big, bigs));
+    SDM_TRY(upload(st, &st->d_chunks, chunks));
+    SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
+    st->n_tiles = (uint32_t)tiles.size();
+    st->n_big = (uint32_t)bigs.size();
+    st->n_chunks = (uint32_t)chunks.size();
+    st->n_buckets = (uint32_t)bucket_big.size();
+    st->bucket_cap = bucket_cap;
+    st->max_nb = max_nb;
+    if (st->n_buckets) {
+        SDM_TRY(dev_alloc(st, (void**)&st->d_cursor, sizeof(uint32_t) * 2 * st->n_buckets, true));
+        SDM_CUDA(cudaMemsetAsync(st->d_cursor, 0, sizeof(uint32_t) * 2 * st->n_buckets, st->stream));
+        SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
+        st->clean_parity = -1;
+        const uint32_t scatter_smem = sizeof(uint32_t) * (2 * max_nb + 2 * BIG_CHUNK);
+        SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
+        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->fin_L.bytes));
+    }
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
+    return SDM_OK;
+}
+
+// host-side validation of an initial state
+sdm_status validate_host(const sdm_state* st, const uint64_t* xi, const double* attr, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        if (xi[i] >= XI_LIMIT) return SDM_ERANGE;
+        for (uint32_t a = 0; a < st->n_attr; ++a) {
+            const double v = attr[(uint64_t)a * n + i];
+            if (!std::isfinite(v)) return SDM_EINVAL;
+            if (a == 0 && xi[i] != 0 && !(v > 0.0)) return SDM_EINVAL;
+        }
+    }
+    return SDM_OK;
+}
+
+sdm_status set_cells(sdm_state* st, const std::vector<uint32_t>& cs, const double* dv, const uint8_t* kid)
+{
+    st->h_cell_start = cs;
+    st->h_dv.assign(dv, dv + st->n_cell);
+    st->h_kid.assign(st->n_cell, 0);
+    if (kid) st->h_kid.assign(kid, kid + st->n_cell);
+    for (uint32_t c = 0; c < st->n_cell; ++c) {
+        if (!(st->h_dv[c] > 0.0) || !std::isfinite(st->h_dv[c])) return SDM_EINVAL;
+        if (st->h_kid[c] > SDM_KERNEL_GRAVITATIONAL) return SDM_EINVAL;
+    }
+    SDM_CUDA(cudaMemcpyAsync(st->d_cell_start, cs.data(), sizeof(uint32_t) * (st->n_cell + 1), cudaMemcpyHostToDevice,
+                             st->stream));
+    SDM_CUDA(cudaMemcpyAsync(st->d_dv, st->h_dv.data(), sizeof(double) * st->n_cell, cudaMemcpyHostToDevice, st->stream));
+    SDM_CUDA(cudaMemcpyAsync(st->d_kid, st->h_kid.data(), st->n_cell, cudaMemcpyHostToDevice, st->stream));
+    return SDM_OK;
+}
+
+// copy the slot arrays (already grouped by cell) to the device
+sdm_status upload_slots(sdm_state* st, const uint64_t* xi, const double* attr, uint64_t n)
+{
+    SDM_CUDA(cudaMemcpyAsync(st->d_xi, xi, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st->stream));
+    for (uint32_t a = 0; a < st->n_attr; ++a)
+        SDM_CUDA(cudaMemcpyAsync(st->d_attr + (uint64_t)a * st->cap, attr + (uint64_t)a * n, sizeof(double) * n,
+                                 cudaMemcpyHostToDevice, st->stream));
+    return SDM_OK;
+}
+
+template <typename T>
+sdm_status to_host(std::vector<T>& h, const T* p, uint64_t n, int on_device, cudaStream_t s)
+{
+    h.resize(n);
+    if (!n) return SDM_OK;
+    if (on_device) {
+        SDM_CUDA(cudaMemcpyAsync(h.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+        SDM_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(h.data(), p, sizeof(T) * n);
+    }
+    return SDM_OK;
+}
+
+sdm_status init_common(sdm_state* st, const uint64_t* xi, const double* attr, const std::vector<uint32_t>& cs,
+                       uint64_t n, const double* dv, const uint8_t* kid)
+{
+    SDM_TRY(validate_host(st, xi, attr, n));
+    SDM_TRY(set_cells(st, cs, dv, kid));
+    SDM_TRY(upload_slots(st, xi, attr, n));
+    st->n_sd = n;
+    SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+    SDM_TRY(build_layout(st));
+    st->initialised = true;
+    return SDM_OK;
+}
+
+__global__ void validate_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ attr, uint64_t n,
+                                uint64_t stride, uint32_t n_attr, uint32_t* err)
+{
+    uint32_t bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = xi[i];
+        if (x >= XI_LIMIT) bad |= ERR_RANGE;
+        for (uint32_t a = 0; a < n_attr; ++a) {
+            const double v = attr[(uint64_t)a * stride + i];
+            if (!isfinite(v) || (a == 0 && x != 0 && !(v > 0.0))) bad |= ERR_INVALID;
+        }
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+sdm_status err_to_status(uint32_t e)
+{
+    if (!e) return SDM_OK;
+    if (e & ERR_RANGE) return SDM_ERANGE;
+    if (e & ERR_INVALID) return SDM_EINVAL;
+    if (e & (ERR_BUCKET_OVERFLOW | ERR_TILE_OVERFLOW)) return SDM_ECAPACITY;
+    if (e & ERR_TIMEOUT) return SDM_ETIMEOUT;
+    return SDM_ECUDA;
+}
+
+cudaEvent_t pooled_event(sdm_state* st)
+{
+    if (!st->ev_pool.empty()) {
+        cudaEvent_t e = st->ev_pool.back();
+        st->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    sdm_state* st;
+    int kind;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(sdm_state* s, int k) : st(s), kind(k)
+    {
+        if (st->profiling) {
+            e0 = pooled_event(st);
+            cudaEventRecord(e0, st->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (e0) {
+            cudaEvent_t e1 = pooled_event(st);
+            cudaEventRecord(e1, st->stream);
+            st->recs.push_back({kind, e0, e1});
+        }
+    }
+};
+
+void collect_profile(sdm_state* st)
+{
+    if (st->recs.empty()) return;
+    cudaStreamSynchronize(st->stream);
+    for (auto& r : st->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        st->prof_ms[r.kind] += ms;
+        st->prof_launches[r.kind] += 1;
+        st->ev_pool.push_back(r.e0);
+        st->ev_pool.push_back(r.e1);
+    }
+    st->recs.clear();
+}
+
+sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_steps, bool with_stats)
+{
+    StepArgs a{};
+    a.xi = st->d_xi;
+    a.attr = st->d_attr;
+    a.stride = st->cap;
+    a.n_attr = st->n_attr;
+    a.precision = p->precision;
+    a.cell_start = st->d_cell_start;
+    a.dv = st->d_dv;
+    a.kid = st->d_kid;
+    a.dt = p->dt;
+    a.golovin_b = p->golovin_b;
+    a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.d_step = p->d_step;
+    a.stats = with_stats ? st->d_stats : nullptr;
+    a.err = st->d_err;
+    const sdm_schedule& S = st->sched;
+    if (st->n_buckets) {
+        if (p->d_step) {
+            st->clean_parity = 2;   // buffer 0 is cleared before every step below
+        } else {
+            const int need = (int)(p->step & 1u);
+            if (st->clean_parity != -1 && st->clean_parity != need) {
+                SDM_CUDA(cudaMemsetAsync(st->d_cursor + (size_t)need * st->n_buckets, 0,
+                                         sizeof(uint32_t) * st->n_buckets, st->stream));
+            }
+        }
+    }
+    const uint32_t scatter_smem = sizeof(uint32_t) * (2 * st->max_nb + 2 * BIG_CHUNK);
+    for (uint32_t s = 0; s < n_steps; ++s) {
+        a.step = p->step + s;
+        if (st->n_tiles) {
+            uint32_t grid = st->n_tiles;
+            uint32_t* work = nullptr;
+            if (S.persistent) {
+                grid = std::min<uint32_t>(st->n_tiles, S.persistent * (uint32_t)st->n_sm);
+                work = st->d_work;
+            }
+            ProfScope ps(st, 0);
+            tile_step_kernel<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
+                                                                                    st->tile_L, work);
+        }
+        if (st->n_buckets) {
+            // cursor buffers alternate with the step parity (the finishing pass clears the other one)
+            const uint32_t par = p->d_step ? 0u : (a.step & 1u);
+            uint32_t* cur = st->d_cursor + (size_t)par * st->n_buckets;
+            uint32_t* nxt = st->d_cursor + (size_t)(par ^ 1u) * st->n_buckets;
+            if (p->d_step) {
+                // with a device step counter the parity is unknown here: always use buffer 0, cleared first
+                SDM_CUDA(cudaMemsetAsync(cur, 0, sizeof(uint32_t) * st->n_buckets, st->stream));
+            }
+            {
+                ProfScope ps(st, 1);
+                big_scatter_kernel<<<st->n_chunks, 512, scatter_smem, st->stream>>>(a, st->d_big, st->d_chunks,
+                                                                                   st->d_scratch, cur, st->bucket_cap);
+            }
+            {
+                ProfScope ps(st, 2);
+                big_finish_kernel<<<st->n_buckets, 256, st->fin_L.bytes, st->stream>>>(
+                    a, st->d_big, st->d_bucket_big, st->d_scratch, cur, nxt, st->fin_L);
+            }
+            if (!p->d_step) st->clean_parity = (int)(par ^ 1u);
+        }
+        if (p->d_step) advance_step_kernel<<<1, 32, 0, st->stream>>>(p->d_step, 1u);
+        SDM_CUDA(cudaGetLastError());
+    }
+    return SDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdm_version(void) { return "sdm-b300 1.0 (sm_103a)"; }
+
+const char* sdm_status_str(sdm_status s)
+{
+    switch (s) {
+    case SDM_OK: return "SDM_OK";
+    case SDM_EINVAL: return "SDM_EINVAL: invalid argument or state";
+    case SDM_ENOMEM: return "SDM_ENOMEM: out of memory";
+    case SDM_ECAPACITY: return "SDM_ECAPACITY: capacity exceeded";
+    case SDM_ERANGE: return "SDM_ERANGE: multiplicity >= 2^53";
+    case SDM_ECUDA: return "SDM_ECUDA: CUDA runtime error";
+    case SDM_ETIMEOUT: return "SDM_ETIMEOUT: bounded wait expired";
+    case SDM_ENOTSUP: return "SDM_ENOTSUP: not supported";
+    }
+    return "unknown sdm_status";
+}
+
+size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
+{
+    size_t b = 0;
+    b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256);
+    b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
+    b += 4 * round256(512);
+    // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
+    b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
+    b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
+    const size_t max_buckets = 3 * cap / 256 + 1;
+    const size_t max_cap = 2 * 4096 + 64 + 32;
+    b += round256(4 * max_buckets + 256) + round256(8 * max_buckets + 256);
+    b += round256(8 * max_buckets * max_cap + 256);
+    return b;
+}
+
+sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_attr, void* cuda_stream,
+                     void* workspace, size_t ws_bytes)
+{
+    if (!out) return SDM_EINVAL;
+    *out = nullptr;
+    if (cap == 0 || cap >= (1ull << 32) || n_cell == 0 || n_attr == 0 || n_attr > 64) return SDM_EINVAL;
+    sdm_state* st = new (std::nothrow) sdm_state();
+    if (!st) return SDM_ENOMEM;
+    st->stream = (cudaStream_t)cuda_stream;
+    st->cap = cap;
+    st->n_cell = n_cell;
+    st->n_attr = n_attr;
+    st->sched = sdm_schedule{1024, 256, 1024, 0};
+    if (cudaGetDevice(&st->device) != cudaSuccess) { delete st; return SDM_ECUDA; }
+    cudaDeviceGetAttribute(&st->n_sm, cudaDevAttrMultiProcessorCount, st->device);
+    if (workspace) {
+        st->ws = (char*)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+        const size_t skew = (size_t)(st->ws - (char*)workspace);
+        if (ws_bytes <= skew) { delete st; return SDM_ENOMEM; }
+        st->ws_bytes = ws_bytes - skew;
+    }
+    sdm_status s = SDM_OK;
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_xi, sizeof(uint64_t) * cap, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_attr, sizeof(double) * cap * n_attr, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_cell_start, sizeof(uint32_t) * ((size_t)n_cell + 1), false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_dv, sizeof(double) * n_cell, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_kid, n_cell, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_err, 64, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_stats, 64, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_acc, 64, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_work, 64, false);
+    if (s == SDM_OK && cudaMemsetAsync(st->d_err, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
+    if (s == SDM_OK && cudaMemsetAsync(st->d_work, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
+    if (s == SDM_OK && cudaMemsetAsync(st->d_xi, 0, sizeof(uint64_t) * cap, st->stream) != cudaSuccess) s = SDM_ECUDA;
+    if (s == SDM_OK && cudaStreamSynchronize(st->stream) != cudaSuccess) s = SDM_ECUDA;
+    if (s != SDM_OK) { sdm_free(st); return s; }
+    st->ws_fixed = st->ws_used;
+    *out = st;
+    return SDM_OK;
+}
+
+void sdm_free(sdm_state* st)
+{
+    if (!st) return;
+    if (st->stream) cudaStreamSynchronize(st->stream);
+    free_layout(st);
+    for (auto& a : st->owned_fixed) cudaFree(a.p);
+    collect_profile(st);
+    for (auto e : st->ev_pool) cudaEventDestroy(e);
+    delete st;
+}
+
+sdm_status sdm_init_state(sdm_state* st, const uint64_t* xi, const double* attr, const uint32_t* cell_id,
+                          uint64_t n_sd, const double* dv, const uint8_t* kernel_id, int on_dev)
+{
+    if (!st || !xi || !attr || !cell_id || !dv) return SDM_EINVAL;
+    if (n_sd > st->cap) return SDM_ECAPACITY;
+    std::vector<uint64_t> hx;
+    std::vector<double> ha, hdv;
+    std::vector<uint32_t> hc;
+    std::vector<uint8_t> hk;
+    SDM_TRY(to_host(hx, xi, n_sd, on_dev, st->stream));
+    SDM_TRY(to_host(ha, attr, n_sd * st->n_attr, on_dev, st->stream));
+    SDM_TRY(to_host(hc, cell_id, n_sd, on_dev, st->stream));
+    SDM_TRY(to_host(hdv, dv, st->n_cell, on_dev, st->stream));
+    if (kernel_id) SDM_TRY(to_host(hk, kernel_id, st->n_cell, on_dev, st->stream));
+    // stable counting sort by cell: slot order inside a cell is the input order
+    std::vector<uint32_t> cs(st->n_cell + 1, 0);
+    for (uint64_t i = 0; i < n_sd; ++i) {
+        if (hc[i] >= st->n_cell) return SDM_EINVAL;
+        cs[hc[i] + 1]++;
+    }
+    for (uint32_t c = 0; c < st->n_cell; ++c) cs[c + 1] += cs[c];
+    std::vector<uint32_t> pos(cs.begin(), cs.end() - 1);
+    std::vector<uint64_t> sx(n_sd);
+    std::vector<double> sa(n_sd * st->n_attr);
+    for (uint64_t i = 0; i < n_sd; ++i) {
+        const uint32_t d = pos[hc[i]]++;
+        sx[d] = hx[i];
+        for (uint32_t a = 0; a < st->n_attr; ++a) sa[(uint64_t)a * n_sd + d] = ha[(uint64_t)a * n_sd + i];
+    }
+    return init_common(st, sx.data(), sa.data(), cs, n_sd, hdv.data(), kernel_id ? hk.data() : nullptr);
+}
+
+sdm_status sdm_init_state_segmented(sdm_state* st, const uint64_t* xi, const double* attr, const uint32_t* cell_start,
+                                    uint64_t n_sd, const double* dv, const uint8_t* kernel_id, int on_dev)
+{
+    if (!st || !xi || !attr || !cell_start || !dv) return SDM_EINVAL;
+    if (n_sd > st->cap) return SDM_ECAPACITY;
+    std::vector<uint64_t> hx;
+    std::vector<double> ha, hdv;
+    std::vector<uint32_t> hcs;
+    std::vector<uint8_t> hk;
+    SDM_TRY(to_host(hcs, cell_start, (uint64_t)st->n_cell + 1, on_dev, st->stream));
+    if (hcs[0] != 0 || hcs[st->n_cell] != n_sd) return SDM_EINVAL;
+    for (uint32_t c = 0; c < st->n_cell; ++c)
+        if (hcs[c + 1] < hcs[c]) return SDM_EINVAL;
+    SDM_TRY(to_host(hx, xi, n_sd, on_dev, st->stream));
+    SDM_TRY(to_host(ha, attr, n_sd * st->n_attr, on_dev, st->stream));
+    SDM_TRY(to_host(hdv, dv, st->n_cell, on_dev, st->stream));
+    if (kernel_id) SDM_TRY(to_host(hk, kernel_id, st->n_cell, on_dev, st->stream));
+    return init_common(st, hx.data(), ha.data(), hcs, n_sd, hdv.data(), kernel_id ? hk.data() : nullptr);
+}
+
+sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, int on_dev)
+{
+    if (!st || !xi || !attr) return SDM_EINVAL;
+    if (!st->initialised) return SDM_EINVAL;
+    const uint64_t n = st->n_sd;
+    const cudaMemcpyKind k = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SDM_CUDA(cudaMemcpyAsync(st->d_xi, xi, sizeof(uint64_t) * n, k, st->stream));
+    for (uint32_t a = 0; a < st->n_attr; ++a)
+        SDM_CUDA(cudaMemcpyAsync(st->d_attr + (uint64_t)a * st->cap, attr + (uint64_t)a * n, sizeof(double) * n, k,
+                                 st->stream));
+    if (n) {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 4 * (uint64_t)st->n_sm);
+        validate_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, n, st->cap, st->n_attr, st->d_err);
+        SDM_CUDA(cudaGetLastError());
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* cell_start, uint64_t* n_sd, int on_dev)
+{
+    if (!st || !st->initialised) return SDM_EINVAL;
+    const uint64_t n = st->n_sd;
+    const cudaMemcpyKind k = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (xi) SDM_CUDA(cudaMemcpyAsync(xi, st->d_xi, sizeof(uint64_t) * n, k, st->stream));
+    if (attr)
+        for (uint32_t a = 0; a < st->n_attr; ++a)
+            SDM_CUDA(cudaMemcpyAsync(attr + (uint64_t)a * n, st->d_attr + (uint64_t)a * st->cap, sizeof(double) * n, k,
+                                     st->stream));
+    if (cell_start) {
+        if (on_dev)
+            SDM_CUDA(cudaMemcpyAsync(cell_start, st->d_cell_start, sizeof(uint32_t) * (st->n_cell + 1),
+                                     cudaMemcpyDeviceToDevice, st->stream));
+        else
+            std::memcpy(cell_start, st->h_cell_start.data(), sizeof(uint32_t) * (st->n_cell + 1));
+    }
+    if (n_sd) *n_sd = n;
+    if (!on_dev) SDM_CUDA(cudaStreamSynchronize(st->stream));
+    return SDM_OK;
+}
+
+sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* p, uint32_t n_steps, sdm_step_stats* stats)
+{
+    if (!st || !p) return SDM_EINVAL;
+    if (!st->initialised) return SDM_EINVAL;
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return SDM_EINVAL;
+    if (p->precision > SDM_PREC_FP32) return SDM_EINVAL;
+    if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
+    if (n_steps == 0) return SDM_OK;
+    if (stats) SDM_CUDA(cudaMemsetAsync(st->d_stats, 0, 5 * sizeof(unsigned long long), st->stream));
+    SDM_TRY(launch_steps(st, p, n_steps, stats != nullptr));
+    if (stats) {
+        unsigned long long h[5];
+        uint32_t e = 0;
+        SDM_CUDA(cudaMemcpyAsync(h, st->d_stats, sizeof h, cudaMemcpyDeviceToHost, st->stream));
+        SDM_CUDA(cudaMemcpyAsync(&e, st->d_err, sizeof e, cudaMemcpyDeviceToHost, st->stream));
+        SDM_CUDA(cudaStreamSynchronize(st->stream));
+        stats->n_pairs = h[0];
+        stats->n_collisions = h[1];
+        stats->n_removed = h[2];
+        stats->sum_gamma = h[3];
+        stats->n_fp64 = h[4];
+        if (e) {
+            SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+            return err_to_status(e);
+        }
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live)
+{
+    if (!st || !st->initialised) return SDM_EINVAL;
+    if (!n_live) return SDM_OK;
+    SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, sizeof(unsigned long long), st->stream));
+    if (st->n_sd) {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
+        count_live_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->n_sd, st->d_acc);
+        SDM_CUDA(cudaGetLastError());
+    }
+    unsigned long long h = 0;
+    SDM_CUDA(cudaMemcpyAsync(&h, st->d_acc, sizeof h, cudaMemcpyDeviceToHost, st->stream));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
+    *n_live = h;
+    return SDM_OK;
+}
+
+sdm_status sdm_totals(sdm_state* st, uint64_t* n_total, double* mass, uint64_t* n_live)
+{
+    if (!st || !st->initialised) return SDM_EINVAL;
+    SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, 4 * sizeof(unsigned long long), st->stream));
+    if (st->n_sd) {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
+        totals_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->n_sd, st->d_acc, (double*)(st->d_acc + 1),
+                                                     st->d_acc + 2);
+        SDM_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[4];
+    SDM_CUDA(cudaMemcpyAsync(h, st->d_acc, sizeof h, cudaMemcpyDeviceToHost, st->stream));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
+    if (n_total) *n_total = h[0];
+    if (mass) std::memcpy(mass, &h[1], sizeof(double));
+    if (n_live) *n_live = h[2];
+    return SDM_OK;
+}
+
+sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, uint32_t cell, double* out,
+                        int out_on_device)
+{
+    if (!st || !st->initialised || !r_edges || !out || n_bins == 0) return SDM_EINVAL;
+    for (uint32_t b = 0; b < n_bins; ++b)
+        if (!(r_edges[b] > 0.0) || !(r_edges[b + 1] > r_edges[b])) return SDM_EINVAL;
+    uint32_t c0 = 0, c1 = st->n_cell;
+    if (cell != UINT32_MAX) {
+        if (cell >= st->n_cell) return SDM_EINVAL;
+        c0 = cell;
+        c1 = cell + 1;
+    }
+    std::vector<double> ve(n_bins + 1), msum(n_bins);
+    for (uint32_t b = 0; b <= n_bins; ++b) {
+        double t = FOUR_PI_OVER_THREE * r_edges[b];
+        t = t * r_edges[b];
+        ve[b] = t * r_edges[b];
+    }
+    double* d_ve = nullptr;
+    double* d_sum = nullptr;
+    SDM_CUDA(cudaMallocAsync((void**)&d_ve, sizeof(double) * (2 * n_bins + 1), st->stream));
+    d_sum = d_ve + n_bins + 1;
+    sdm_status rs = SDM_OK;
+    do {
+        if (cudaMemcpyAsync(d_ve, ve.data(), sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice, st->stream) ||
+            cudaMemsetAsync(d_sum, 0, sizeof(double) * n_bins, st->stream)) { rs = SDM_ECUDA; break; }
+        const uint64_t s0 = st->h_cell_start[c0], s1 = st->h_cell_start[c1];
+        if (s1 > s0) {
+            const uint32_t grid = (uint32_t)std::min<uint64_t>((s1 - s0 + 255) / 256, 2 * (uint64_t)st->n_sm);
+            spectrum_kernel<<<grid, 256, sizeof(double) * n_bins, st->stream>>>(st->d_xi, st->d_attr, s0, s1, d_ve,
+                                                                               n_bins, d_sum);
+            if (cudaGetLastError() != cudaSuccess) { rs = SDM_ECUDA; break; }
+        }
+        if (cudaMemcpyAsync(msum.data(), d_sum, sizeof(double) * n_bins, cudaMemcpyDeviceToHost, st->stream) ||
+            cudaStreamSynchronize(st->stream)) { rs = SDM_ECUDA; break; }
+    } while (0);
+    cudaFreeAsync(d_ve, st->stream);
+    if (rs != SDM_OK) return rs;
+    double V = 0.0;
+    for (uint32_t c = c0; c < c1; ++c) V = V + st->h_dv[c];
+    std::vector<double> res(n_bins);
+    for (uint32_t b = 0; b < n_bins; ++b) {
+        const double dlnr = std::log(r_edges[b + 1]) - std::log(r_edges[b]);
+        res[b] = RHO_WATER * msum[b] / (V * dlnr);
+    }
+    if (out_on_device) {
+        SDM_CUDA(cudaMemcpyAsync(out, res.data(), sizeof(double) * n_bins, cudaMemcpyHostToDevice, st->stream));
+        SDM_CUDA(cudaStreamSynchronize(st->stream));
+    } else {
+        std::memcpy(out, res.data(), sizeof(double) * n_bins);
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_get_schedule(sdm_state* st, sdm_schedule* out)
+{
+    if (!st || !out) return SDM_EINVAL;
+    *out = st->sched;
+    return SDM_OK;
+}
+
+sdm_status sdm_set_schedule(sdm_state* st, const sdm_schedule* s)
+{
+    if (!st || !s) return SDM_EINVAL;
+    SDM_TRY(check_schedule(*s));
+    const sdm_schedule old = st->sched;
+    st->sched = *s;
+    if (st->initialised) {
+        sdm_status r = build_layout(st);
+        if (r != SDM_OK) {
+            st->sched = old;
+            build_layout(st);
+            return r;
+        }
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_autotune(sdm_state* st, const sdm_step_params* p, uint32_t n_steps, sdm_schedule* best)
+{
+    if (!st || !p || !st->initialised || n_steps == 0) return SDM_EINVAL;
+    const uint64_t n = st->n_sd;
+    // save the state so that every trial starts from it
+    uint64_t* sx = nullptr;
+    double* sa = nullptr;
+    SDM_CUDA(cudaMalloc(&sx, sizeof(uint64_t) * (n + 1)));
+    if (cudaMalloc(&sa, sizeof(double) * (n * st->n_attr + 1)) != cudaSuccess) { cudaFree(sx); return SDM_ENOMEM; }
+    sdm_status rs = sdm_get_state(st, sx, sa, nullptr, nullptr, 1);
+    std::vector<sdm_schedule> cands;
+    const sdm_schedule cur = st->sched;
+    for (uint32_t ts : {512u, 1024u, 2048u, 4096u})
+        for (uint32_t th : {128u, 256u, 512u})
+            for (uint32_t pers : {0u, 4u})
+                cands.push_back(sdm_schedule{ts, th, cur.bucket_target, pers});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    sdm_schedule bs = cur;
+    float bt = 1e30f;
+    auto trial = [&](const sdm_schedule& c) -> float {
+        if (sdm_set_schedule(st, &c) != SDM_OK) return 1e30f;
+        sdm_step_params q = *p;
+        q.d_step = nullptr;
+        if (sdm_set_state(st, sx, sa, 1) != SDM_OK) return 1e30f;
+        launch_steps(st, &q, 1, false);   // warm-up
+        sdm_set_state(st, sx, sa, 1);
+        cudaEventRecord(e0, st->stream);
+        launch_steps(st, &q, n_steps, false);
+        cudaEventRecord(e1, st->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    for (const auto& c : cands) {
+        const float t = trial(c);
+        if (t < bt) { bt = t; bs = c; }
+    }
+    // then the bucket width of the large-cell path
+    for (uint32_t bw : {512u, 1024u, 2048u}) {
+        sdm_schedule c = bs;
+        c.bucket_target = bw;
+        const float t = trial(c);
+        if (t < bt) { bt = t; bs = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs == SDM_OK) rs = sdm_set_schedule(st, &bs);
+    if (rs == SDM_OK) rs = sdm_set_state(st, sx, sa, 1);
+    if (rs == SDM_OK) rs = cuda_status(cudaStreamSynchronize(st->stream));
+    cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream);
+    cudaStreamSynchronize(st->stream);
+    cudaFree(sx);
+    cudaFree(sa);
+    if (best) *best = bs;
+    return rs;
+}
+
+sdm_status sdm_sync(sdm_state* st)
+{
+    if (!st) return SDM_EINVAL;
+    uint32_t e = 0;
+    SDM_CUDA(cudaMemcpyAsync(&e, st->d_err, sizeof e, cudaMemcpyDeviceToHost, st->stream));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
+    if (e) {
+        SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+        SDM_CUDA(cudaStreamSynchronize(st->stream));
+        return err_to_status(e);
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_set_profiling(sdm_state* st, int enable)
+{
+    if (!st) return SDM_EINVAL;
+    collect_profile(st);
+    st->profiling = enable != 0;
+    for (int k = 0; k < SDM_N_KERNEL_KINDS; ++k) { st->prof_launches[k] = 0; st->prof_ms[k] = 0.0; }
+    return SDM_OK;
+}
+
+sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms)
+{
+    if (!st) return SDM_EINVAL;
+    collect_profile(st);
+    for (int k = 0; k < SDM_N_KERNEL_KINDS; ++k) {
+        if (launches) launches[k] = st->prof_launches[k];
+        if (ms) ms[k] = st->prof_ms[k];
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n)
+{
+    if (!st || !n) return SDM_EINVAL;
+    *n = (st->n_tiles ? 1u : 0u) + (st->n_buckets ? 2u : 0u);
+    return SDM_OK;
+}
+
+sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2, const uint64_t* xi1,
+                          const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt, double golovin_b,
+                          double* p64, float* p32, float* err32)
+{
+    if (!st || !v1 || !v2 || !xi1 || !xi2 || !p64 || !p32 || !err32) return SDM_EINVAL;
+    if (kernel_id > SDM_KERNEL_GRAVITATIONAL || n_cell_sd < 2 || !(dv > 0) || !(dt > 0)) return SDM_EINVAL;
+    if (n == 0) return SDM_OK;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 8 * (uint64_t)st->n_sm);
+    eval_pairs_kernel<<<grid, 256, 0, st->stream>>>(kernel_id, v1, v2, xi1, xi2, n, n_cell_sd, dv, dt, golovin_b, p64,
+                                                    p32, err32);
+    SDM_CUDA(cudaGetLastError());
+    return SDM_OK;
+}
+
+}  // extern "C"

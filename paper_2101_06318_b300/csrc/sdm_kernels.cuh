@@ -1,0 +1,742 @@
+// sdm_kernels.cuh -- CUDA kernels of one SDM coalescence timestep (sm_103a).
+//
+// A timestep (Fig. "fig:algo") is executed by two kinds of launches, both
+// fusing Steps 0-3 so that the state is read once and only changed
+// super-droplets are written:
+//
+//  tile_step_kernel   one CTA per tile of consecutive small cells (all slots
+//                     of the tile fit in shared memory): load xi and v,
+//                     generate the Philox keys, sort each cell's live SDs by
+//                     (key, slot) with a counting sort on the key's top bits
+//                     plus an exact rank inside each bucket, pair neighbours,
+//                     evaluate eq. (p) and gamma, and write the updated pairs.
+//  big_scatter_kernel / big_finish_kernel
+//                     cells too large for one CTA: the first pass scatters
+//                     (key, slot) records into fixed-capacity buckets given by
+//                     the key's top bits (no global scan needed), the second
+//                     sorts each bucket in shared memory, works out the
+//                     bucket's offset in the cell's sorted list from the bucket
+//                     counts, and processes the pairs (gathering xi and v).
+//
+// Both orders are the same total order of the cell, (key, slot) ascending, so
+// the tile size, bucket width and launch shape never change a result.
+#pragma once
+#include "sdm_math.cuh"
+
+namespace sdm {
+
+enum : uint32_t {
+    ERR_BUCKET_OVERFLOW = 1u,
+    ERR_TILE_OVERFLOW = 2u,
+    ERR_TIMEOUT = 4u,
+};
+
+constexpr uint32_t PREC_FP64 = 0, PREC_FP32 = 1;
+constexpr uint32_t DEAD = 0xffffffffu;
+
+struct StepArgs {
+    uint64_t* xi;
+    double* attr;               // [n_attr][stride], attr 0 = volume
+    uint64_t stride;
+    uint32_t n_attr;
+    uint32_t precision;
+    const uint32_t* cell_start; // [n_cell + 1]
+    const double* dv;           // [n_cell]
+    const uint8_t* kid;         // [n_cell]
+    double dt;
+    double golovin_b;
+    uint32_t seed_lo, seed_hi;
+    uint32_t step;              // used when d_step == nullptr
+    const uint32_t* d_step;
+    unsigned long long* stats;  // [5] or nullptr
+    uint32_t* err;
+};
+
+struct TileDesc { uint32_t slot_begin, slot_end, cell_begin, n_cells; };
+struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, pad; };
+struct BigChunk { uint32_t big, l_begin, l_end, pad; };
+
+__device__ __forceinline__ uint32_t step_index(const StepArgs& a)
+{
+    return a.d_step ? *a.d_step : a.step;
+}
+
+struct LocalStats {
+    unsigned long long pairs, collisions, removed, sum_gamma, fp64;
+};
+
+struct CellCtx {
+    uint32_t gid;      // global cell index
+    uint32_t n;        // live SDs at the start of the step
+    uint32_t kid;      // kernel id
+    float s_dtdv32;    // pair-count ratio * dt / dV in FP32
+    double dv;
+};
+
+__device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, double dt, double dv)
+{
+    // ((n^2 - n)/2) / floor(n/2) is n - 1 (n even) or n (n odd): exact integer
+    const float s = (float)(n - 1u + (n & 1u));
+    return s * (__double2float_rn(dt) / __double2float_rn(dv));
+}
+
+// Step 2 + Step 3 for candidate pair m = (first, second) of a cell.  Writes the
+// updated multiplicities and attributes of the pair to global memory.
+__device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
+                                             uint32_t step, uint32_t m, uint64_t g1, uint64_t g2, uint64_t x1,
+                                             uint64_t x2, double v1, double v2, LocalStats& ls)
+{
+    const uint64_t u53 = phi_u53(a.seed_lo, a.seed_hi, c.gid, step, m);
+    const bool swap = x1 < x2;                 // j = first unless it has the smaller multiplicity
+    const uint64_t xj = swap ? x2 : x1, xk = swap ? x1 : x2;
+    const float scale32 = __ull2float_rn(xj) * c.s_dtdv32;
+    const P32 pe = pair_prob_f(T, c.kid, v1, v2, scale32, (float)a.golovin_b);
+    uint64_t g;
+    if (a.precision == PREC_FP32) {
+        g = gamma_tilde_f(pe.p, u53, xj, xk);
+    } else if (!gamma_tilde_certified(pe, u53, xj, xk, &g)) {
+        const double K = kernel_d(c.kid, v1, v2, a.golovin_b);
+        const double p = pair_prob_d(K, xj, c.n, a.dt, c.dv);
+        g = gamma_tilde_d(p, u53, xj, xk);
+        ls.fp64++;
+    }
+    ls.pairs++;
+    if (g == 0) return;
+    const uint64_t gj = swap ? g2 : g1, gk = swap ? g1 : g2;
+    const double vj = swap ? v2 : v1, vk = swap ? v1 : v2;
+    const double gd = __ull2double_rn(g);
+    const uint64_t new_n = xj - g * xk;
+    if (new_n > 0) {                                          // case 1, eq. (coal_attr_0)
+        a.xi[gj] = new_n;
+        a.attr[gk] = __dadd_rn(__dmul_rn(gd, vj), vk);
+        for (uint32_t i = 1; i < a.n_attr; ++i) {
+            double* A = a.attr + (uint64_t)i * a.stride;
+            A[gk] = __dadd_rn(__dmul_rn(gd, A[gj]), A[gk]);
+        }
+    } else {                                                  // case 2, eq. (coal)
+        const uint64_t h = xk / 2;
+        a.xi[gj] = h;
+        a.xi[gk] = xk - h;
+        const double nv = __dadd_rn(__dmul_rn(gd, vj), vk);
+        a.attr[gj] = nv;
+        a.attr[gk] = nv;
+        for (uint32_t i = 1; i < a.n_attr; ++i) {
+            double* A = a.attr + (uint64_t)i * a.stride;
+            const double t = __dadd_rn(__dmul_rn(gd, A[gj]), A[gk]);
+            A[gj] = t;
+            A[gk] = t;
+        }
+        if (h == 0) ls.removed++;
+    }
+    ls.collisions++;
+    ls.sum_gamma += g;
+}
+
+// ---------------------------------------------------------------------------
+// block helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void flush_stats(const StepArgs& a, LocalStats& ls, unsigned long long* red)
+{
+    if (!a.stats) return;
+    unsigned long long v[5] = {ls.pairs, ls.collisions, ls.removed, ls.sum_gamma, ls.fp64};
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const unsigned long long s = warp_sum(v[k]);
+        if (lane == 0 && s) atomicAdd(&red[k], s);
+    }
+    __syncthreads();
+    if (threadIdx.x < 5 && red[threadIdx.x]) atomicAdd(&a.stats[threadIdx.x], red[threadIdx.x]);
+}
+
+// Exclusive scan of a[0..n) in place (block-wide); a[n] receives the total.
+// 'warp_tot' needs 33 entries of shared memory.
+__device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* warp_tot)
+{
+    const uint32_t nt = blockDim.x, tid = threadIdx.x;
+    const uint32_t per = (n + nt - 1) / nt;
+    const uint32_t b0 = min(n, tid * per), b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += a[i];
+    // inclusive warp scan of the thread sums
+    const int lane = tid & 31, wid = tid >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t nw = (nt + 31) >> 5;
+        uint32_t w = lane < (int)nw ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (int)nw) warp_tot[lane] = wi - w;     // exclusive warp offsets
+        if (lane == 31) warp_tot[32] = wi;               // block total
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[wid] + inc - s;
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t t = a[i];
+        a[i] = run;
+        run += t;
+    }
+    if (tid == 0) a[n] = warp_tot[32];
+    __syncthreads();
+}
+
+// largest c in [0, n) with pre[c] <= x (pre non-decreasing)
+__device__ __forceinline__ uint32_t find_segment(const uint32_t* pre, uint32_t n, uint32_t x)
+{
+    uint32_t lo = 0, hi = n;   // invariant: pre[lo] <= x, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__host__ __device__ __forceinline__ uint32_t ceil_log2(uint32_t w)
+{
+#ifdef __CUDA_ARCH__
+    return w <= 1 ? 0u : 32u - __clz(w - 1u);
+#else
+    return w <= 1 ? 0u : 32u - (uint32_t)__builtin_clz(w - 1u);
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// Tile kernel: whole small cells in shared memory.
+// ---------------------------------------------------------------------------
+struct TileLayout {
+    uint32_t tile_slots, max_cells;
+    // byte offsets
+    uint32_t o_xi, o_v, o_key, o_bo, o_cnt, o_tmp, o_srt, o_cs, o_gb, o_bb, o_pb, o_ss, o_nb, o_ctx, o_red, o_wt, o_tab;
+    uint32_t bytes;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t max_cells)
+{
+    TileLayout L;
+    L.tile_slots = tile_slots;
+    L.max_cells = max_cells;
+    uint32_t o = 0;
+    L.o_xi = o;  o = align_up(o + 8 * tile_slots, 16);
+    L.o_v = o;   o = align_up(o + 8 * tile_slots, 16);
+    L.o_key = o; o = align_up(o + 4 * tile_slots, 16);
+    L.o_bo = o;  o = align_up(o + 4 * tile_slots, 16);
+    L.o_cnt = o; o = align_up(o + 4 * (2 * tile_slots + 1), 16);
+    L.o_tmp = o; o = align_up(o + 2 * tile_slots, 16);
+    L.o_srt = o; o = align_up(o + 2 * tile_slots, 16);
+    L.o_cs = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_gb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_bb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_pb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_ss = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_nb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_ctx = o; o = align_up(o + (uint32_t)sizeof(CellCtx) * max_cells, 16);
+    L.o_red = o; o = align_up(o + 8 * 8, 16);
+    L.o_wt = o;  o = align_up(o + 4 * 40, 16);
+    L.o_tab = o; o = align_up(o + (uint32_t)sizeof(EffTab), 16);
+    L.bytes = o;
+    return L;
+}
+
+// warp 0 computes an exclusive scan over n (<= max_cells) values in place; a[n] = total
+__device__ __forceinline__ void warp0_exclusive_scan(uint32_t* a, uint32_t n)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t v = i < n ? a[i] : 0u;
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (i < n) a[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) a[n] = carry;
+}
+
+__device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLayout& L, unsigned char* smem,
+                             uint32_t step, LocalStats& ls)
+{
+    uint64_t* xi_s = (uint64_t*)(smem + L.o_xi);
+    double* v_s = (double*)(smem + L.o_v);
+    uint32_t* key_s = (uint32_t*)(smem + L.o_key);
+    uint32_t* bo_s = (uint32_t*)(smem + L.o_bo);
+    uint32_t* cnt = (uint32_t*)(smem + L.o_cnt);
+    uint16_t* tmp = (uint16_t*)(smem + L.o_tmp);
+    uint16_t* srt = (uint16_t*)(smem + L.o_srt);
+    uint32_t* cs = (uint32_t*)(smem + L.o_cs);
+    uint32_t* gb = (uint32_t*)(smem + L.o_gb);
+    uint32_t* bb = (uint32_t*)(smem + L.o_bb);
+    uint32_t* pb = (uint32_t*)(smem + L.o_pb);
+    uint32_t* ss = (uint32_t*)(smem + L.o_ss);
+    uint32_t* nbit = (uint32_t*)(smem + L.o_nb);
+    CellCtx* ctx = (CellCtx*)(smem + L.o_ctx);
+    uint32_t* wt = (uint32_t*)(smem + L.o_wt);
+    const EffTab* tab = (const EffTab*)(smem + L.o_tab);
+
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t ns = td.slot_end - td.slot_begin, nc = td.n_cells;
+
+    // per-cell geometry: slot start, groups of 4 slots, 2^nbits buckets
+    for (uint32_t c = tid; c <= nc; c += nt) {
+        const uint32_t s0 = a.cell_start[td.cell_begin + c] - td.slot_begin;
+        cs[c] = s0;
+        if (c < nc) {
+            const uint32_t w = a.cell_start[td.cell_begin + c + 1] - a.cell_start[td.cell_begin + c];
+            gb[c] = (w + 3) >> 2;
+            const uint32_t nb = ceil_log2(w);
+            nbit[c] = nb;
+            bb[c] = w ? 1u << nb : 0u;       // 2^ceil(log2 w) <= 2w buckets, none for an empty cell
+        }
+    }
+    for (uint32_t i = tid; i < ns; i += nt) {
+        xi_s[i] = a.xi[td.slot_begin + i];
+        v_s[i] = a.attr[td.slot_begin + i];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        warp0_exclusive_scan(gb, nc);
+        __syncwarp();
+        warp0_exclusive_scan(bb, nc);
+    }
+    __syncthreads();
+    const uint32_t G = gb[nc], NB = bb[nc];
+    for (uint32_t b = tid; b < NB; b += nt) cnt[b] = 0;
+    __syncthreads();
+
+    // Step 0 + Step 1: live SDs, Philox keys, bucket counts
+    for (uint32_t g = tid; g < G; g += nt) {
+        const uint32_t c = find_segment(gb, nc, g);
+        const uint32_t grp = g - gb[c];
+        const uint32_t w = cs[c + 1] - cs[c];
+        const U4 x = philox(grp, td.cell_begin + c, step, 0u, a.seed_lo, a.seed_hi);
+        const uint32_t nb = nbit[c];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t l = 4 * grp + k;
+            if (l >= w) break;
+            const uint32_t i = cs[c] + l;
+            if (xi_s[i] != 0) {
+                const uint32_t key = u4_word(x, k);
+                const uint32_t b = bb[c] + (nb ? key >> (32u - nb) : 0u);
+                const uint32_t off = atomicAdd(&cnt[b], 1u);
+                key_s[i] = key;
+                bo_s[i] = (b << 16) | off;
+            } else {
+                bo_s[i] = DEAD;
+            }
+        }
+    }
+    __syncthreads();
+    block_exclusive_scan(cnt, NB, wt);
+    for (uint32_t i = tid; i < ns; i += nt) {
+        const uint32_t bo = bo_s[i];
+        if (bo != DEAD) tmp[cnt[bo >> 16] + (bo & 0xffffu)] = (uint16_t)i;
+    }
+    __syncthreads();
+    // exact rank inside the bucket: order by (key, slot)
+    for (uint32_t i = tid; i < ns; i += nt) {
+        const uint32_t bo = bo_s[i];
+        if (bo == DEAD) continue;
+        const uint32_t b = bo >> 16;
+        const uint32_t st = cnt[b], en = cnt[b + 1];
+        const uint32_t key = key_s[i];
+        uint32_t r = 0;
+        for (uint32_t p = st; p < en; ++p) {
+            const uint32_t o = tmp[p];
+            const uint32_t ko = key_s[o];
+            r += (ko < key) || (ko == key && o < i);
+        }
+        srt[st + r] = (uint16_t)i;
+    }
+    // per-cell live counts and pair counts
+    for (uint32_t c = tid; c < nc; c += nt) {
+        const uint32_t s0 = cnt[bb[c]], s1 = cnt[bb[c + 1]];
+        const uint32_t n = s1 - s0;
+        ss[c] = s0;
+        pb[c] = n >> 1;
+        const uint32_t gid = td.cell_begin + c;
+        CellCtx cc;
+        cc.gid = gid;
+        cc.n = n;
+        cc.kid = a.kid[gid];
+        cc.dv = a.dv[gid];
+        cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt, cc.dv) : 0.f;
+        ctx[c] = cc;
+    }
+    __syncthreads();
+    if (tid < 32) warp0_exclusive_scan(pb, nc);
+    __syncthreads();
+    const uint32_t P = pb[nc];
+    // Steps 2-3 for every candidate pair of the tile
+    for (uint32_t t = tid; t < P; t += nt) {
+        const uint32_t c = find_segment(pb, nc, t);
+        const uint32_t m = t - pb[c];
+        const uint32_t i1 = srt[ss[c] + 2 * m], i2 = srt[ss[c] + 2 * m + 1];
+        process_pair(a, tab, ctx[c], step, m, td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
+                     v_s[i1], v_s[i2], ls);
+    }
+}
+
+__global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDesc* __restrict__ tiles,
+                                                         uint32_t n_tiles, TileLayout L, uint32_t* work)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t step = step_index(a);
+    LocalStats ls = {0, 0, 0, 0, 0};
+    unsigned long long* red = (unsigned long long*)(smem + L.o_red);
+    load_eff_tab((EffTab*)(smem + L.o_tab));   // read after the first __syncthreads of tile_process
+    if (work == nullptr) {
+        tile_process(a, tiles[blockIdx.x], L, smem, step, ls);
+    } else {
+        __shared__ uint32_t t_s;
+        for (;;) {
+            if (threadIdx.x == 0) t_s = atomicAdd(&work[0], 1u);
+            __syncthreads();
+            const uint32_t t = t_s;
+            __syncthreads();
+            if (t >= n_tiles) break;
+            tile_process(a, tiles[t], L, smem, step, ls);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint32_t done = atomicAdd(&work[1], 1u);
+            if (done == gridDim.x - 1) { work[0] = 0; work[1] = 0; __threadfence(); }
+        }
+    }
+    if (a.stats) {
+        __syncthreads();
+        if (threadIdx.x < 5) red[threadIdx.x] = 0;
+        __syncthreads();
+        flush_stats(a, ls, red);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Large cells, pass 1: scatter (key, slot) into fixed-capacity buckets.
+// ---------------------------------------------------------------------------
+constexpr uint32_t BIG_CHUNK = 8192;          // slots per scatter CTA (multiple of 4)
+constexpr uint32_t BIG_MAX_BUCKET_BITS = 13;  // <= 8192 buckets per cell
+
+__global__ void __launch_bounds__(512) big_scatter_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                          const BigChunk* __restrict__ chunks,
+                                                          uint64_t* __restrict__ scratch,
+                                                          uint32_t* __restrict__ cursor, uint32_t bucket_cap)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const BigChunk ch = chunks[blockIdx.x];
+    const BigCell C = cells[ch.big];
+    const uint32_t nb = 1u << C.nbits;
+    uint32_t* hist = (uint32_t*)smem;              // nb
+    uint32_t* base = hist + nb;                    // nb
+    uint32_t* key_s = base + nb;                   // BIG_CHUNK
+    uint32_t* bo_s = key_s + BIG_CHUNK;            // BIG_CHUNK
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t step = step_index(a);
+    const uint32_t n = ch.l_end - ch.l_begin;
+
+    if (tid == 0) {
+        // warm L2 with this chunk's volumes: the finishing pass gathers them
+        const uintptr_t p0 = (uintptr_t)(a.attr + C.slot_begin + ch.l_begin) & ~(uintptr_t)15;
+        const uintptr_t p1 = ((uintptr_t)(a.attr + C.slot_begin + ch.l_end) + 15) & ~(uintptr_t)15;
+        const uint32_t bytes = (uint32_t)(p1 - p0);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p0), "r"(bytes) : "memory");
+    }
+    for (uint32_t b = tid; b < nb; b += nt) hist[b] = 0;
+    __syncthreads();
+    const uint32_t ngroups = (n + 3) >> 2;
+    for (uint32_t g = tid; g < ngroups; g += nt) {
+        const uint32_t l0 = ch.l_begin + 4 * g;
+        const U4 x = philox(l0 >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi);
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t l = l0 + k;
+            if (l >= ch.l_end) break;
+            const uint32_t i = l - ch.l_begin;
+            if (a.xi[C.slot_begin + l] != 0) {
+                const uint32_t key = u4_word(x, k);
+                const uint32_t b = C.nbits ? key >> (32u - C.nbits) : 0u;
+                const uint32_t off = atomicAdd(&hist[b], 1u);
+                key_s[i] = key;
+                bo_s[i] = (b << 16) | off;
+            } else {
+                bo_s[i] = DEAD;
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = tid; b < nb; b += nt) {
+        const uint32_t h = hist[b];
+        if (h) base[b] = atomicAdd(&cursor[C.bucket_base + b], h);
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += nt) {
+        const uint32_t bo = bo_s[i];
+        if (bo == DEAD) continue;
+        const uint32_t b = bo >> 16;
+        const uint32_t pos = base[b] + (bo & 0xffffu);
+        if (pos < bucket_cap) {
+            scratch[(uint64_t)(C.bucket_base + b) * bucket_cap + pos] =
+                (((uint64_t)key_s[i]) << 32) | (uint64_t)(ch.l_begin + i);
+        } else {
+            atomicOr(a.err, ERR_BUCKET_OVERFLOW);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Large cells, pass 2: sort one bucket, locate it in the cell's order, pairs.
+// ---------------------------------------------------------------------------
+struct FinishLayout {
+    uint32_t cap;
+    uint32_t o_e, o_srt, o_so, o_cnt, o_tmp, o_red, o_wt, o_tab, bytes;
+};
+
+__host__ __device__ inline FinishLayout finish_layout(uint32_t cap)
+{
+    FinishLayout L;
+    L.cap = cap;
+    const uint32_t nsub_max = 1u << ceil_log2(cap > 2 ? cap : 2);   // >= cap
+    uint32_t o = 0;
+    L.o_e = o;   o = align_up(o + 8 * cap, 16);
+    L.o_srt = o; o = align_up(o + 8 * cap, 16);
+    L.o_so = o;  o = align_up(o + 4 * cap, 16);
+    L.o_cnt = o; o = align_up(o + 4 * (nsub_max + 1), 16);
+    L.o_tmp = o; o = align_up(o + 2 * cap, 16);
+    L.o_red = o; o = align_up(o + 8 * 40, 16);
+    L.o_wt = o;  o = align_up(o + 4 * 40, 16);
+    L.o_tab = o; o = align_up(o + (uint32_t)sizeof(EffTab), 16);
+    L.bytes = o;
+    return L;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t < v ? t : v;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                         const uint32_t* __restrict__ bucket_big,
+                                                         const uint64_t* __restrict__ scratch,
+                                                         const uint32_t* __restrict__ cursor,
+                                                         uint32_t* __restrict__ cursor_next, FinishLayout L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* e_s = (uint64_t*)(smem + L.o_e);
+    uint64_t* srt = (uint64_t*)(smem + L.o_srt);
+    uint32_t* so = (uint32_t*)(smem + L.o_so);
+    uint32_t* cnt = (uint32_t*)(smem + L.o_cnt);
+    uint16_t* tmp = (uint16_t*)(smem + L.o_tmp);
+    unsigned long long* red = (unsigned long long*)(smem + L.o_red);
+    uint32_t* wt = (uint32_t*)(smem + L.o_wt);
+    EffTab* tab = (EffTab*)(smem + L.o_tab);
+    __shared__ unsigned long long s_pre, s_tot, s_next;
+
+    const uint32_t g = blockIdx.x;
+    const BigCell C = cells[bucket_big[g]];
+    const uint32_t b = g - C.bucket_base, nb = 1u << C.nbits;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const uint32_t cap = L.cap;
+    const uint32_t step = step_index(a);
+    LocalStats ls = {0, 0, 0, 0, 0};
+
+    if (tid == 0) { cursor_next[g] = 0; s_pre = 0; s_tot = 0; s_next = ~0ull; }
+    if (tid < 5) red[tid] = 0;
+    load_eff_tab(tab);
+    __syncthreads();
+    // where this bucket starts in the cell's sorted list, and the cell's live count
+    {
+        unsigned long long pre = 0, tot = 0;
+        for (uint32_t b2 = tid; b2 < nb; b2 += nt) {
+            const uint32_t c = min(cursor[C.bucket_base + b2], cap);
+            tot += c;
+            if (b2 < b) pre += c;
+        }
+        pre = warp_sum(pre);
+        tot = warp_sum(tot);
+        if (lane == 0) { atomicAdd(&s_pre, pre); atomicAdd(&s_tot, tot); }
+    }
+    const uint32_t cnt_raw = cursor[g];
+    const uint32_t k = min(cnt_raw, cap);
+    for (uint32_t i = tid; i < k; i += nt) e_s[i] = scratch[(uint64_t)g * cap + i];
+    __syncthreads();
+    const uint32_t S = (uint32_t)s_pre, n = (uint32_t)s_tot;
+
+    // counting sort on the next key bits, then exact rank by the full (key, slot)
+    uint32_t sb = ceil_log2(k > 2 ? k : 2);
+    if (sb > 32u - C.nbits) sb = 32u - C.nbits;
+    const uint32_t nsub = 1u << sb;
+    for (uint32_t s = tid; s < nsub; s += nt) cnt[s] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < k; i += nt) {
+        const uint32_t key = (uint32_t)(e_s[i] >> 32);
+        const uint32_t sub = sb ? (key << C.nbits) >> (32u - sb) : 0u;
+        const uint32_t off = atomicAdd(&cnt[sub], 1u);
+        so[i] = (sub << 16) | off;
+    }
+    __syncthreads();
+    block_exclusive_scan(cnt, nsub, wt);
+    for (uint32_t i = tid; i < k; i += nt) {
+        const uint32_t v = so[i];
+        tmp[cnt[v >> 16] + (v & 0xffffu)] = (uint16_t)i;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < k; i += nt) {
+        const uint32_t sub = so[i] >> 16;
+        const uint32_t st = cnt[sub], en = cnt[sub + 1];
+        const uint64_t e = e_s[i];
+        uint32_t r = 0;
+        for (uint32_t p = st; p < en; ++p) r += e_s[tmp[p]] < e;
+        srt[st + r] = e;
+    }
+    // the partner of this bucket's last SD may be the first SD of the next non-empty bucket
+    const bool need_next = ((S + k) & 1u) && (S + k < n);
+    if (need_next) {
+        __shared__ uint32_t s_nb;
+        if (tid == 0) {
+            uint32_t b2 = b + 1;
+            while (b2 < nb && cursor[C.bucket_base + b2] == 0) ++b2;
+            s_nb = b2;
+        }
+        __syncthreads();
+        const uint32_t b2 = s_nb;
+        if (b2 < nb) {
+            const uint32_t g2 = C.bucket_base + b2;
+            const uint32_t k2 = min(cursor[g2], cap);
+            unsigned long long mn = ~0ull;
+            for (uint32_t i = tid; i < k2; i += nt) {
+                const unsigned long long e = scratch[(uint64_t)g2 * cap + i];
+                mn = e < mn ? e : mn;
+            }
+            mn = warp_min_u64(mn);
+            if (lane == 0) atomicMin(&s_next, mn);
+        }
+    }
+    __syncthreads();
+    const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell],
+                        n >= 2 ? pair_ratio_dtdv_f(n, a.dt, a.dv[C.cell]) : 0.f, a.dv[C.cell]};
+    const uint64_t nxt = s_next;
+    for (uint32_t r = (S & 1u) + 2 * tid; r < k; r += 2 * nt) {
+        const uint32_t q = S + r;
+        if (q + 1 >= n) break;
+        const uint64_t e1 = srt[r];
+        const uint64_t e2 = (r + 1 < k) ? srt[r + 1] : nxt;
+        const uint64_t s1 = C.slot_begin + (uint32_t)e1, s2 = C.slot_begin + (uint32_t)e2;
+        process_pair(a, tab, cc, step, q >> 1, s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls);
+    }
+    if (cnt_raw > cap && tid == 0) atomicOr(a.err, ERR_BUCKET_OVERFLOW);
+    if (a.stats) {
+        __syncthreads();
+        flush_stats(a, ls, red);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small utility kernels
+// ---------------------------------------------------------------------------
+__global__ void advance_step_kernel(uint32_t* d_step, uint32_t by)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d_step += by;
+}
+
+__global__ void totals_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ v, uint64_t n,
+                              unsigned long long* out_n, double* out_mass, unsigned long long* out_live)
+{
+    unsigned long long sn = 0, sl = 0;
+    double sm = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = xi[i];
+        if (x) { sn += x; sl += 1; sm += (double)x * v[i]; }
+    }
+    sn = warp_sum(sn); sl = warp_sum(sl); sm = warp_sum(sm);
+    if ((threadIdx.x & 31) == 0) {
+        if (sn) atomicAdd(out_n, sn);
+        if (sl) atomicAdd(out_live, sl);
+        atomicAdd(out_mass, sm);
+    }
+}
+
+// mass per bin: bin b holds ve[b] <= v < ve[b+1]
+__global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ v, uint64_t s0,
+                                uint64_t s1, const double* __restrict__ ve, uint32_t n_bins, double* out)
+{
+    extern __shared__ double bins[];
+    for (uint32_t b = threadIdx.x; b < n_bins; b += blockDim.x) bins[b] = 0.0;
+    __syncthreads();
+    for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = xi[i];
+        if (!x) continue;
+        const double vi = v[i];
+        if (!(ve[0] <= vi && vi < ve[n_bins])) continue;
+        uint32_t lo = 0, hi = n_bins;          // ve[lo] <= vi < ve[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (ve[mid] <= vi) lo = mid; else hi = mid;
+        }
+        atomicAdd(&bins[lo], __dmul_rn(__ull2double_rn(x), vi));
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < n_bins; b += blockDim.x)
+        if (bins[b] != 0.0) atomicAdd(&out[b], bins[b]);
+}
+
+__global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* v2, const uint64_t* xi1,
+                                  const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt,
+                                  double golovin_b, double* p64, float* p32, float* err32)
+{
+    __shared__ EffTab tab;
+    load_eff_tab(&tab);
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t xmax = xi1[i] > xi2[i] ? xi1[i] : xi2[i];
+        const double K = kernel_d(kid, v1[i], v2[i], golovin_b);
+        p64[i] = pair_prob_d(K, xmax, n_cell_sd, dt, dv);
+        const float scale32 = __ull2float_rn(xmax) * pair_ratio_dtdv_f(n_cell_sd, dt, dv);
+        const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b);
+        p32[i] = pe.p;
+        err32[i] = pe.err;
+    }
+}
+
+__global__ void count_live_kernel(const uint64_t* __restrict__ xi, uint64_t n, unsigned long long* out)
+{
+    unsigned long long c = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        c += xi[i] != 0;
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+}  // namespace sdm

@@ -1,0 +1,350 @@
+// sdm_math.cuh -- device arithmetic of the SDM coalescence step (sm_103a).
+//
+// Three layers:
+//  * Philox4x32-10 (Salmon et al., SC'11) for the shuffle keys and phi.
+//  * The FP64 path: collision kernels and eq. (p) written with explicit
+//    round-to-nearest intrinsics (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn)
+//    so that no operation is contracted or reordered; its results are the
+//    documented operation order evaluated in IEEE double.  B300 executes FP64
+//    at a small fraction of its FP32 rate, so this path only runs for pairs
+//    the FP32 path below cannot settle.
+//  * The FP32 path: the same quantities in single precision together with a
+//    bound err such that |p64 - p32| <= err.  The integer outcome gamma of
+//    Step 3 is taken from [p32 - err, p32 + err] whenever that interval
+//    settles it (the usual case), which gives exactly the FP64 result.
+#pragma once
+#include <cstdint>
+
+namespace sdm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t u4_word(const U4& x, uint32_t i)
+{
+    return i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w;
+}
+
+// 53-bit integer of phi for candidate pair m (phi = u53 * 2^-53).
+__device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, uint32_t cell,
+                                            uint32_t step, uint32_t m)
+{
+    const U4 x = philox(m >> 1, cell, step, 1u, seed_lo, seed_hi);
+    const uint32_t hi = (m & 1u) ? x.z : x.x;
+    const uint32_t lo = (m & 1u) ? x.w : x.y;
+    return ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 11;
+}
+
+// ---------------------------------------------------------------------------
+// Constants of the kernels (each written out here from the definitions).
+// ---------------------------------------------------------------------------
+constexpr double THREE_OVER_FOUR_PI = 0.238732414637843003;
+constexpr double PI_D = 3.14159265358979311600;
+constexpr double VT_K1 = 1.19e8;   // Stokes regime, 1/(m s)
+constexpr double VT_K2 = 8.0e3;    // linear regime, 1/s
+constexpr double VT_K3 = 201.0;    // square-root regime, m^0.5/s
+constexpr int EFF_NR = 12;
+constexpr int EFF_NQ = 11;
+
+// collector radius nodes [m] and efficiency values E[R][q], q = 0, 0.1, ..., 1
+__constant__ double c_eff_R[EFF_NR] = {
+    10e-6, 20e-6, 30e-6, 40e-6, 50e-6, 60e-6, 80e-6, 100e-6, 150e-6, 200e-6, 300e-6, 1000e-6};
+__constant__ double c_eff_E[EFF_NR * EFF_NQ] = {
+    0.000, 0.026, 0.050, 0.070, 0.088, 0.103, 0.116, 0.126, 0.132, 0.137, 0.138,
+    0.000, 0.074, 0.140, 0.199, 0.250, 0.293, 0.328, 0.355, 0.375, 0.386, 0.390,
+    0.000, 0.112, 0.212, 0.301, 0.378, 0.443, 0.496, 0.537, 0.567, 0.584, 0.590,
+    0.000, 0.137, 0.259, 0.367, 0.460, 0.539, 0.604, 0.654, 0.690, 0.712, 0.719,
+    0.000, 0.152, 0.288, 0.408, 0.512, 0.600, 0.672, 0.728, 0.768, 0.792, 0.800,
+    0.000, 0.162, 0.307, 0.435, 0.545, 0.639, 0.716, 0.775, 0.818, 0.844, 0.852,
+    0.000, 0.173, 0.328, 0.465, 0.583, 0.683, 0.765, 0.829, 0.875, 0.902, 0.911,
+    0.000, 0.179, 0.339, 0.480, 0.602, 0.706, 0.791, 0.856, 0.904, 0.932, 0.941,
+    0.000, 0.185, 0.350, 0.496, 0.623, 0.730, 0.817, 0.885, 0.934, 0.963, 0.973,
+    0.000, 0.187, 0.354, 0.502, 0.630, 0.738, 0.827, 0.896, 0.945, 0.975, 0.985,
+    0.000, 0.189, 0.358, 0.506, 0.636, 0.745, 0.834, 0.904, 0.953, 0.983, 0.993,
+    0.000, 0.190, 0.360, 0.510, 0.640, 0.750, 0.839, 0.909, 0.959, 0.989, 0.999,
+};
+
+
+// ---------------------------------------------------------------------------
+// FP64 path (documented operation order, no contraction)
+// ---------------------------------------------------------------------------
+
+// Cube root by +, *, / only: x = m 2^(3q), m in [0.5, 4); y0 = 0.2 m + 0.74;
+// five Newton steps y <- (2y + m/y^2)/3; result y 2^q.  Positive normal x.
+__device__ __forceinline__ double cbrt_d(double x)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7ff) - 1022;
+    double m = __longlong_as_double((long long)((u & 0x800fffffffffffffull) | (1022ull << 52)));
+    const int q = (e >= 0) ? e / 3 : -((-e + 2) / 3);
+    const int rmd = e - 3 * q;
+    if (rmd == 1) m = __dmul_rn(m, 2.0);
+    else if (rmd == 2) m = __dmul_rn(m, 4.0);
+    double y = __dmul_rn(0.2, m);
+    y = __dadd_rn(y, 0.74);
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        const double a = __dmul_rn(y, y);
+        const double b = __ddiv_rn(m, a);
+        const double c = __dadd_rn(y, y);
+        const double d = __dadd_rn(c, b);
+        y = __ddiv_rn(d, 3.0);
+    }
+    return __dmul_rn(y, __longlong_as_double((long long)((uint64_t)(1023 + q) << 52)));
+}
+
+__device__ __forceinline__ double radius_d(double v)
+{
+    return cbrt_d(__dmul_rn(v, THREE_OVER_FOUR_PI));
+}
+
+__device__ __forceinline__ double vt_d(double r)
+{
+    const double r12 = __ddiv_rn(VT_K2, VT_K1);
+    const double t = __ddiv_rn(VT_K3, VT_K2);
+    const double r23 = __dmul_rn(t, t);
+    if (r < r12) return __dmul_rn(__dmul_rn(VT_K1, r), r);
+    if (r < r23) return __dmul_rn(VT_K2, r);
+    return __dmul_rn(VT_K3, __dsqrt_rn(r));
+}
+
+__device__ __forceinline__ double efficiency_d(double R, double q)
+{
+    int i;
+    double t;
+    if (R <= c_eff_R[0]) {
+        i = 0; t = 0.0;
+    } else if (R >= c_eff_R[EFF_NR - 1]) {
+        i = EFF_NR - 2; t = 1.0;
+    } else {
+        i = 0;
+        while (c_eff_R[i + 1] <= R) ++i;
+        t = __ddiv_rn(__dsub_rn(R, c_eff_R[i]), __dsub_rn(c_eff_R[i + 1], c_eff_R[i]));
+    }
+    const double s = __dmul_rn(q, 10.0);
+    int j = (int)floor(s);
+    double w;
+    if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.0; }
+    else w = __dsub_rn(s, (double)j);
+    const double* E = c_eff_E;
+    const double d0 = __dsub_rn(E[i * EFF_NQ + j + 1], E[i * EFF_NQ + j]);
+    const double d1 = __dsub_rn(E[(i + 1) * EFF_NQ + j + 1], E[(i + 1) * EFF_NQ + j]);
+    const double e0 = __dadd_rn(E[i * EFF_NQ + j], __dmul_rn(w, d0));
+    const double e1 = __dadd_rn(E[(i + 1) * EFF_NQ + j], __dmul_rn(w, d1));
+    return __dadd_rn(e0, __dmul_rn(t, __dsub_rn(e1, e0)));
+}
+
+__device__ __noinline__ double kernel_grav_d(double v1, double v2)
+{
+    const double r1 = radius_d(v1), r2 = radius_d(v2);
+    const double vt1 = vt_d(r1), vt2 = vt_d(r2);
+    const double R = r1 > r2 ? r1 : r2;
+    const double rs = r1 > r2 ? r2 : r1;
+    const double E = efficiency_d(R, __ddiv_rn(rs, R));
+    const double s = __dadd_rn(r1, r2);
+    double a = __dmul_rn(s, s);
+    a = __dmul_rn(PI_D, a);
+    const double dv = fabs(__dsub_rn(vt1, vt2));
+    return __dmul_rn(__dmul_rn(a, dv), E);
+}
+
+__device__ __forceinline__ double kernel_golovin_d(double v1, double v2, double b)
+{
+    return __dmul_rn(b, __dadd_rn(v1, v2));
+}
+
+// eq. (p): p = ((a * max(xi)) * scale) * (dt / dV), scale = ((n^2-n)/2) / floor(n/2)
+__device__ __forceinline__ double pair_prob_d(double K, uint64_t xmax, uint32_t n, double dt, double dv)
+{
+    const uint64_t nn = n;
+    const uint64_t all_pairs = nn * (nn - 1) / 2;
+    const uint64_t cand = nn / 2;
+    const double scale = __ddiv_rn(__ull2double_rn(all_pairs), __ull2double_rn(cand));
+    const double dtdv = __ddiv_rn(dt, dv);
+    double p = K;
+    p = __dmul_rn(p, __ull2double_rn(xmax));
+    p = __dmul_rn(p, scale);
+    p = __dmul_rn(p, dtdv);
+    return p;
+}
+
+// gamma~ = min(floor(p) + [phi < p - floor(p)], floor(xi_j / xi_k)), Step 3 and eq. (gamma2)
+__device__ __forceinline__ uint64_t gamma_tilde_d(double p, uint64_t u53, uint64_t xi_j, uint64_t xi_k)
+{
+    const uint64_t cap = xi_j / xi_k;
+    const double fl = floor(p);
+    const double frac = __dsub_rn(p, fl);
+    if (fl >= __ull2double_rn(cap)) return cap;
+    const double phi = __dmul_rn(__ull2double_rn(u53), 0x1p-53);
+    const uint64_t g = (uint64_t)fl + (phi < frac ? 1ull : 0ull);
+    return g < cap ? g : cap;
+}
+
+__device__ __forceinline__ double kernel_d(uint32_t kid, double v1, double v2, double golovin_b)
+{
+    return kid == 0 ? kernel_golovin_d(v1, v2, golovin_b) : kernel_grav_d(v1, v2);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 path with error bound
+// ---------------------------------------------------------------------------
+struct P32 { float p; float err; };
+
+// Relative bound of the Golovin evaluation: about a dozen correctly rounded
+// FP32 steps (conversions of v, xi, dt, dV included) give |p32 - p| <= 13 u p
+// (u = 2^-24); 2^-17 = 128 u leaves a tenfold margin.
+constexpr float GOLOVIN_REL_BOUND = 0x1p-17f;
+// Bound of the gravitational evaluation relative to
+// B = scale * pi (r1+r2)^2 (vt1 + vt2) >= p / E (E <= 1): cube root (<= 1 ulp),
+// regime choice near the continuous joins, the difference vt1 - vt2 (its
+// absolute error is bounded by the sum vt1 + vt2), and the position inside the
+// efficiency table (interpolation weights carry an absolute error of at most
+// ~250 u because the table nodes are >= 5 % apart) add up to < 400 u;
+// 2^-12 = 4096 u leaves a tenfold margin.
+constexpr float GRAV_REL_BOUND = 0x1p-12f;
+constexpr float ABS_SLACK = 0x1p-100f;   // covers gradual underflow of the last products
+
+__device__ __forceinline__ float vt_f(float r)
+{
+    const float k1 = (float)VT_K1, k2 = (float)VT_K2, k3 = (float)VT_K3;
+    const float r12 = (float)(VT_K2 / VT_K1);
+    const float r23 = (float)((VT_K3 / VT_K2) * (VT_K3 / VT_K2));
+    if (r < r12) return k1 * r * r;
+    if (r < r23) return k2 * r;
+    return k3 * sqrtf(r);
+}
+
+// FP32 copy of the efficiency table, staged in shared memory by every CTA that
+// evaluates the gravitational kernel (divergent lookups into __constant__
+// memory would serialise per distinct address).
+struct EffTab {
+    float R[EFF_NR];          // radius nodes
+    float inv_dR[EFF_NR];     // 1 / (R[i+1] - R[i])
+    float E[EFF_NR * EFF_NQ];
+};
+
+__device__ __forceinline__ void load_eff_tab(EffTab* T)
+{
+    for (int k = threadIdx.x; k < EFF_NR * EFF_NQ; k += blockDim.x) T->E[k] = (float)c_eff_E[k];
+    if (threadIdx.x < EFF_NR) {
+        const int i = threadIdx.x;
+        T->R[i] = (float)c_eff_R[i];
+        T->inv_dR[i] = i + 1 < EFF_NR ? (float)(1.0 / (c_eff_R[i + 1] - c_eff_R[i])) : 0.f;
+    }
+}
+
+__device__ __forceinline__ float efficiency_f(const EffTab* __restrict__ T, float R, float q)
+{
+    int i;
+    float t;
+    if (R <= 10e-6f) { i = 0; t = 0.f; }
+    else if (R >= 1000e-6f) { i = EFF_NR - 2; t = 1.f; }
+    else {
+        // interval index by comparisons against the (uniform) node values
+        i = (R >= 20e-6f) + (R >= 30e-6f) + (R >= 40e-6f) + (R >= 50e-6f) + (R >= 60e-6f) + (R >= 80e-6f) +
+            (R >= 100e-6f) + (R >= 150e-6f) + (R >= 200e-6f) + (R >= 300e-6f);
+        t = (R - T->R[i]) * T->inv_dR[i];
+    }
+    const float s = q * 10.f;
+    int j = (int)s;
+    float w;
+    if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.f; }
+    else w = s - (float)j;
+    const float* E = T->E + i * EFF_NQ + j;
+    const float e0 = E[0] + w * (E[1] - E[0]);
+    const float e1 = E[EFF_NQ] + w * (E[EFF_NQ + 1] - E[EFF_NQ]);
+    return e0 + t * (e1 - e0);
+}
+
+// scale32 = (float)max(xi) * S_c * (dt/dV) in FP32
+__device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_t kid, double v1d, double v2d,
+                                           float scale32, float golovin_bf)
+{
+    const float v1 = __double2float_rn(v1d), v2 = __double2float_rn(v2d);
+    P32 o;
+    if (kid == 0) {
+        const float K = golovin_bf * (v1 + v2);
+        o.p = K * scale32;
+        o.err = o.p * GOLOVIN_REL_BOUND + ABS_SLACK;
+        return o;
+    }
+    const float c = (float)THREE_OVER_FOUR_PI;
+    const float r1 = cbrtf(v1 * c), r2 = cbrtf(v2 * c);
+    const float vt1 = vt_f(r1), vt2 = vt_f(r2);
+    const float R = fmaxf(r1, r2), rs = fminf(r1, r2);
+    const float E = efficiency_f(T, R, rs / R);
+    const float s = r1 + r2;
+    const float base = scale32 * ((float)PI_D * (s * s));
+    o.p = (base * fabsf(vt1 - vt2)) * E;
+    o.err = (base * (vt1 + vt2)) * GRAV_REL_BOUND + ABS_SLACK;
+    return o;
+}
+
+// Decide gamma~ from the FP32 interval.  Returns true when settled (result in
+// *g), false when the FP64 path must decide.
+__device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint64_t xi_j, uint64_t xi_k,
+                                                      uint64_t* g)
+{
+    float lo = __fsub_rd(pe.p, pe.err);
+    const float hi = __fadd_ru(pe.p, pe.err);
+    if (!(hi <= 0x1p62f) || !(lo == lo)) {
+        // huge or non-finite: only the cap can settle it
+        if (lo >= 0x1p62f) { *g = xi_j / xi_k; return true; }
+        return false;
+    }
+    lo = fmaxf(lo, 0.f);
+    const float fl_lo = floorf(lo), fl_hi = floorf(hi);
+    if (fl_lo != fl_hi) {
+        if (fl_lo >= 1.f) {
+            const uint64_t cap = xi_j / xi_k;
+            if ((uint64_t)fl_lo >= cap) { *g = cap; return true; }
+        }
+        return false;
+    }
+    // floor(p) = fl_lo is certain; frac(p) lies in [lo - fl, hi - fl] (both exact)
+    const float f_lo = lo - fl_lo, f_hi = hi - fl_hi;
+    const uint32_t top = (uint32_t)(u53 >> 29);               // phi in [top, top+1) * 2^-24
+    const float phi_lo = (float)top * 0x1p-24f;
+    const float phi_hi = (float)(top + 1u) * 0x1p-24f;
+    uint64_t d;
+    if (phi_hi <= f_lo) d = 1;          // phi < phi_hi <= frac
+    else if (phi_lo >= f_hi) d = 0;     // phi >= phi_lo >= frac
+    else return false;
+    const uint64_t gam = (uint64_t)fl_lo + d;
+    if (gam <= 1) { *g = gam; return true; }       // xi_j >= xi_k so the cap is >= 1
+    const uint64_t cap = xi_j / xi_k;
+    *g = gam < cap ? gam : cap;
+    return true;
+}
+
+// FP32 mode: gamma from p32 and the top 24 bits of phi.
+__device__ __forceinline__ uint64_t gamma_tilde_f(float p, uint64_t u53, uint64_t xi_j, uint64_t xi_k)
+{
+    if (!(p < 0x1p62f)) return xi_j / xi_k;
+    const float fl = floorf(p);
+    const float frac = p - fl;
+    const float phi = (float)(uint32_t)(u53 >> 29) * 0x1p-24f;
+    const uint64_t gam = (uint64_t)fl + (phi < frac ? 1ull : 0ull);
+    if (gam <= 1) return gam;
+    const uint64_t cap = xi_j / xi_k;
+    return gam < cap ? gam : cap;
+}
+
+}  // namespace sdm

@@ -1,0 +1,309 @@
+"""Python binding of libsdm (the C ABI of include/sdm.h): argument marshalling only.
+
+Every step of the coalescence path runs in the library's CUDA kernels; this
+module converts numpy arrays (host memory) and torch CUDA tensors (device
+memory) to pointers, passes the current torch stream, and turns status codes
+into exceptions.  There is no CPU fallback: if the library cannot be built or
+loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PREC = {"fp64": 0, "fp32": 1}
+KERNEL_GOLOVIN = 0
+KERNEL_GRAVITATIONAL = 1
+
+STATUS = {0: "SDM_OK", 1: "SDM_EINVAL", 2: "SDM_ENOMEM", 3: "SDM_ECAPACITY", 4: "SDM_ERANGE",
+          5: "SDM_ECUDA", 6: "SDM_ETIMEOUT", 7: "SDM_ENOTSUP"}
+
+# every entry point declared in include/sdm.h
+EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", "sdm_init_state",
+           "sdm_init_state_segmented", "sdm_set_state", "sdm_get_state", "sdm_coalescence_step",
+           "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_get_schedule", "sdm_set_schedule",
+           "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
+           "sdm_launches_per_step"]
+
+
+class SDMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class StepParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("golovin_b", C.c_double), ("seed", C.c_uint64), ("step", C.c_uint32),
+                ("precision", C.c_uint32), ("d_step", C.c_void_p)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("n_pairs", C.c_uint64), ("n_collisions", C.c_uint64), ("n_removed", C.c_uint64),
+                ("sum_gamma", C.c_uint64), ("n_fp64", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class Schedule(C.Structure):
+    _fields_ = [("tile_slots", C.c_uint32), ("tile_threads", C.c_uint32), ("bucket_target", C.c_uint32),
+                ("persistent", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def lib(build_if_needed: bool = True):
+    """Load libsdm.so (building it in-tree first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise OSError(f"libsdm.so not built: {_build.LIB}")
+        L = C.CDLL(_build.LIB)
+        vp, u32, u64, f64, i32, sz = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double, C.c_int, C.c_size_t
+        L.sdm_version.restype = C.c_char_p
+        L.sdm_status_str.argtypes = [i32]
+        L.sdm_status_str.restype = C.c_char_p
+        L.sdm_workspace_bytes.argtypes = [u64, u32, u32]
+        L.sdm_workspace_bytes.restype = sz
+        L.sdm_alloc.argtypes = [C.POINTER(vp), u64, u32, u32, vp, vp, sz]
+        L.sdm_init_state.argtypes = [vp, vp, vp, vp, u64, vp, vp, i32]
+        L.sdm_init_state_segmented.argtypes = [vp, vp, vp, vp, u64, vp, vp, i32]
+        L.sdm_set_state.argtypes = [vp, vp, vp, i32]
+        L.sdm_get_state.argtypes = [vp, vp, vp, vp, vp, i32]
+        L.sdm_coalescence_step.argtypes = [vp, C.POINTER(StepParams), u32, C.POINTER(StepStats)]
+        L.sdm_remove_zero.argtypes = [vp, vp]
+        L.sdm_spectrum.argtypes = [vp, vp, u32, u32, vp, i32]
+        L.sdm_totals.argtypes = [vp, vp, vp, vp]
+        L.sdm_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+        L.sdm_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+        L.sdm_autotune.argtypes = [vp, C.POINTER(StepParams), u32, C.POINTER(Schedule)]
+        L.sdm_sync.argtypes = [vp]
+        L.sdm_free.argtypes = [vp]
+        L.sdm_free.restype = None
+        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp]
+        L.sdm_set_profiling.argtypes = [vp, i32]
+        L.sdm_get_profile.argtypes = [vp, vp, vp]
+        L.sdm_launches_per_step.argtypes = [vp, vp]
+        for name in EXPORTS:
+            if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free"):
+                getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SDMError(rc, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return C.c_void_p(a.ctypes.data), 0, a
+
+
+def current_stream():
+    torch = _torch()
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsdm needs a CUDA device")
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class State:
+    """One SDM system on the current CUDA device (sdm_state)."""
+
+    def __init__(self, n_slots_cap, n_cell, n_attr=1, stream=None, workspace=None):
+        self._L = lib()
+        self._h = C.c_void_p()
+        self.n_cell = int(n_cell)
+        self.n_attr = int(n_attr)
+        self.cap = int(n_slots_cap)
+        self._ws = workspace
+        stream = current_stream() if stream is None else C.c_void_p(stream)
+        wsp, wsb = (None, 0)
+        if workspace is not None:
+            wsp, wsb = C.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+        _check(self._L.sdm_alloc(C.byref(self._h), self.cap, self.n_cell, self.n_attr, stream, wsp, wsb),
+               "sdm_alloc")
+        self.n_sd = 0
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._L.sdm_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state -----------------------------------------------------------------
+    def init(self, xi, attr, dv, kernel_id=None, cell_id=None, cell_start=None):
+        """Load an initial population; give either cell_id (any order) or cell_start (grouped)."""
+        n = int(xi.shape[0])
+        px, dx, kx = _ptr(xi, np.uint64)
+        pa, da, ka = _ptr(attr, np.float64)
+        pd, dd, kd = _ptr(dv, np.float64)
+        pk, dk, kk = _ptr(kernel_id, np.uint8)
+        on_dev = dx
+        if len({d for d in (dx, da, dd, dk if kernel_id is not None else dx)}) != 1:
+            raise ValueError("all arrays must live on the same side (host or device)")
+        if cell_start is not None:
+            pc, dc, kc = _ptr(cell_start, np.uint32)
+            rc = self._L.sdm_init_state_segmented(self._h, px, pa, pc, n, pd, pk, on_dev)
+        else:
+            pc, dc, kc = _ptr(cell_id, np.uint32)
+            rc = self._L.sdm_init_state(self._h, px, pa, pc, n, pd, pk, on_dev)
+        _check(rc, "sdm_init_state")
+        self.n_sd = n
+
+    def set_state(self, xi, attr):
+        px, dx, kx = _ptr(xi, np.uint64)
+        pa, da, ka = _ptr(attr, np.float64)
+        _check(self._L.sdm_set_state(self._h, px, pa, dx), "sdm_set_state")
+        return kx, ka
+
+    def get_state(self, xi=None, attr=None):
+        """Copy out (xi, attr, cell_start).  Fills the given numpy arrays / CUDA tensors, or returns new numpy."""
+        n = self.n_sd
+        if xi is None and attr is None:
+            xi = np.empty(n, np.uint64)
+            attr = np.empty((self.n_attr, n), np.float64)
+        cs = np.empty(self.n_cell + 1, np.uint32)
+        px, dx, _ = _ptr(xi, np.uint64)
+        pa, da, _ = _ptr(attr, np.float64)
+        _check(self._L.sdm_get_state(self._h, px, pa, None, None, dx), "sdm_get_state")
+        _check(self._L.sdm_get_state(self._h, None, None, C.c_void_p(cs.ctypes.data), None, 0), "sdm_get_state")
+        return xi, attr, cs
+
+    # -- the step ----------------------------------------------------------------
+    def step(self, dt=1.0, seed=42, step=0, n_steps=1, precision="fp64", golovin_b=1500.0, d_step=None,
+             stats=False):
+        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision],
+                       None if d_step is None else d_step.data_ptr())
+        st = StepStats()
+        _check(self._L.sdm_coalescence_step(self._h, C.byref(p), int(n_steps), C.byref(st) if stats else None),
+               "sdm_coalescence_step")
+        return st.as_dict() if stats else None
+
+    def remove_zero(self):
+        n = C.c_uint64()
+        _check(self._L.sdm_remove_zero(self._h, C.byref(n)), "sdm_remove_zero")
+        return int(n.value)
+
+    def spectrum(self, r_edges, cell=None):
+        r = np.ascontiguousarray(r_edges, np.float64)
+        out = np.zeros(len(r) - 1, np.float64)
+        _check(self._L.sdm_spectrum(self._h, C.c_void_p(r.ctypes.data), len(r) - 1,
+                                    0xFFFFFFFF if cell is None else int(cell), C.c_void_p(out.ctypes.data), 0),
+               "sdm_spectrum")
+        return out
+
+    def totals(self):
+        n, m, live = C.c_uint64(), C.c_double(), C.c_uint64()
+        _check(self._L.sdm_totals(self._h, C.byref(n), C.byref(m), C.byref(live)), "sdm_totals")
+        return int(n.value), float(m.value), int(live.value)
+
+    def sync(self):
+        _check(self._L.sdm_sync(self._h), "sdm_sync")
+
+    # -- schedule ------------------------------------------------------------------
+    @property
+    def schedule(self):
+        s = Schedule()
+        _check(self._L.sdm_get_schedule(self._h, C.byref(s)), "sdm_get_schedule")
+        return s.as_dict()
+
+    def set_schedule(self, tile_slots=1024, tile_threads=256, bucket_target=1024, persistent=0):
+        s = Schedule(tile_slots, tile_threads, bucket_target, persistent)
+        _check(self._L.sdm_set_schedule(self._h, C.byref(s)), "sdm_set_schedule")
+
+    def autotune(self, dt=1.0, seed=42, step=0, n_steps=3, precision="fp64", golovin_b=1500.0):
+        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision], None)
+        s = Schedule()
+        _check(self._L.sdm_autotune(self._h, C.byref(p), int(n_steps), C.byref(s)), "sdm_autotune")
+        return s.as_dict()
+
+    # -- profiling ----------------------------------------------------------------
+    KERNEL_KINDS = ("tile_step_kernel", "big_scatter_kernel", "big_finish_kernel")
+
+    def set_profiling(self, on=True):
+        _check(self._L.sdm_set_profiling(self._h, int(bool(on))), "sdm_set_profiling")
+
+    def profile(self):
+        """{kernel name: (launches, total ms)} since profiling was enabled."""
+        n = (C.c_uint32 * 3)()
+        ms = (C.c_double * 3)()
+        _check(self._L.sdm_get_profile(self._h, n, ms), "sdm_get_profile")
+        return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    def launches_per_step(self):
+        n = C.c_uint32()
+        _check(self._L.sdm_launches_per_step(self._h, C.byref(n)), "sdm_launches_per_step")
+        return int(n.value)
+
+    # -- Step 2 alone (testing) ---------------------------------------------------
+    def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0):
+        """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors."""
+        torch = _torch()
+        n = v1.numel()
+        p64 = torch.empty(n, dtype=torch.float64, device=v1.device)
+        p32 = torch.empty(n, dtype=torch.float32, device=v1.device)
+        e32 = torch.empty(n, dtype=torch.float32, device=v1.device)
+        _check(self._L.sdm_eval_pairs(self._h, int(kernel_id), C.c_void_p(v1.data_ptr()), C.c_void_p(v2.data_ptr()),
+                                      C.c_void_p(xi1.data_ptr()), C.c_void_p(xi2.data_ptr()), n, int(n_cell_sd),
+                                      float(dv), float(dt), float(golovin_b), C.c_void_p(p64.data_ptr()),
+                                      C.c_void_p(p32.data_ptr()), C.c_void_p(e32.data_ptr())), "sdm_eval_pairs")
+        return p64, p32, e32
+
+
+def from_inputs(s, n_attr=1, extra_attrs=None, stream=None, device_arrays=False):
+    """Create and initialise a State from an inputs.* workload dict."""
+    n = len(s["xi"])
+    st = State(max(n, 1), len(s["dv"]), n_attr, stream=stream)
+    attr = s["v"][None, :] if extra_attrs is None else np.vstack([s["v"][None, :], extra_attrs])
+    if device_arrays:
+        torch = _torch()
+        st.init(torch.from_numpy(s["xi"].view(np.int64)).cuda(), torch.from_numpy(np.ascontiguousarray(attr)).cuda(),
+                torch.from_numpy(s["dv"]).cuda(), torch.from_numpy(s["kernel_id"]).cuda(),
+                cell_start=torch.from_numpy(s["cell_start"].view(np.int32)).cuda())
+    else:
+        st.init(s["xi"], attr, s["dv"], s["kernel_id"], cell_start=s["cell_start"])
+    return st

@@ -1,0 +1,363 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 mode must reproduce the oracle bit for bit: multiplicities exactly and
+volumes exactly (both sides evaluate the same IEEE operations in the same
+order; the CUDA side only settles most decisions from an FP32 bound first).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_06318_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2101_06318_b300 import sdm  # noqa: E402
+
+
+def _oracle_system(s, attr=None):
+    a = s["v"][None, :] if attr is None else attr
+    return oracle.System(s["xi"], a, s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+
+
+def _gpu_state(s, attr=None, schedule=None):
+    n = len(s["xi"])
+    a = s["v"][None, :] if attr is None else attr
+    st = sdm.State(max(n, 1), len(s["dv"]), a.shape[0])
+    if schedule:
+        st.set_schedule(**schedule)
+    st.init(s["xi"], a, s["dv"], s["kernel_id"], cell_start=s["cell_start"])
+    return st
+
+
+def _run_both(s, n_steps, seed=42, step0=0, attr=None, schedule=None, precision="fp64"):
+    o = _oracle_system(s, attr)
+    ost = o.run(s["dt"], seed, step0, n_steps)
+    g = _gpu_state(s, attr, schedule)
+    gst = g.step(s["dt"], seed, step0, n_steps, precision=precision, golovin_b=s["golovin_b"], stats=True)
+    g.sync()
+    xi, at, cs = g.get_state()
+    g.close()
+    return o, ost, xi, at, gst
+
+
+def _assert_bitexact(o, xi, at):
+    assert np.array_equal(o.xi, xi), f"xi differs at {np.flatnonzero(o.xi != xi)[:10]}"
+    assert np.array_equal(o.attr.view(np.uint64), at.view(np.uint64)), \
+        f"attr differs at {np.argwhere(o.attr != at)[:10]}"
+
+
+def test_golovin_box_bitexact_large_cell_path():
+    s = inputs.golovin_box()                   # one cell of 2^13 SDs -> bucketed large-cell path
+    o, ost, xi, at, gst = _run_both(s, 300)
+    _assert_bitexact(o, xi, at)
+    for k in ("n_pairs", "n_collisions", "n_removed", "sum_gamma"):
+        assert ost[k] == gst[k], k
+    assert gst["n_collisions"] > 1000
+
+
+def test_golovin_box_bitexact_tile_path():
+    s = inputs.golovin_box(n_sd=4096)          # the whole cell handled in shared memory
+    o, ost, xi, at, gst = _run_both(s, 300, schedule=dict(tile_slots=4096, tile_threads=512))
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_cells_bitexact(seed):
+    # irregular cells (Poisson sizes incl. empty and 1-SD cells), dead slots, both kernels,
+    # log-uniform xi so that case 2 and removals occur
+    s = inputs.random_cells(n_cell=700, mean_per_cell=23, seed=seed, dead_fraction=0.05, xi_max=50, dv=1e-12)
+    o, ost, xi, at, gst = _run_both(s, 25, seed=seed)
+    _assert_bitexact(o, xi, at)
+    assert ost == {k: gst[k] for k in ost}
+    assert gst["n_removed"] > 0 and gst["n_collisions"] > 100
+
+
+def test_big_cells_many_buckets_bitexact():
+    rng = np.random.default_rng(5)
+    parts = []
+    for n in (1025, 3000, 4096, 9001, 20000, 2, 1, 0, 777):
+        parts.append(n)
+    counts = np.array(parts)
+    n = int(counts.sum())
+    xi = np.maximum(1, np.floor(np.exp(rng.random(n) * math.log(10 ** 6)))).astype(np.uint64)
+    v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
+    s = inputs._state(xi, v, counts, 10.0, (np.arange(len(counts)) % 2).astype(np.uint8), "big_mix")
+    o, ost, xi_g, at, gst = _run_both(s, 12, schedule=dict(tile_slots=1024, bucket_target=256))
+    _assert_bitexact(o, xi_g, at)
+    assert gst["n_collisions"] > 0
+
+
+def test_multiple_attributes_bitexact():
+    s = inputs.random_cells(n_cell=200, mean_per_cell=30, seed=9, xi_max=1000, dv=1e-11)
+    n = len(s["xi"])
+    rng = np.random.default_rng(1)
+    attr = np.vstack([s["v"], rng.random(n), rng.random(n) * 1e-20]).astype(np.float64)
+    o, ost, xi, at, gst = _run_both(s, 10, attr=attr)
+    _assert_bitexact(o, xi, at)
+
+
+def test_schedule_invariance():
+    s = inputs.random_cells(n_cell=400, mean_per_cell=60, seed=4, xi_max=10 ** 4, dv=1e-2)
+    big = inputs.golovin_box(n_sd=5000)
+    # append one larger cell so both paths run in the same step
+    xi = np.concatenate([s["xi"], big["xi"]])
+    v = np.concatenate([s["v"], big["v"]])
+    counts = np.concatenate([np.diff(s["cell_start"].astype(np.int64)), [5000]])
+    mix = inputs._state(xi, v, counts, np.concatenate([s["dv"], [1e6]]),
+                        np.concatenate([s["kernel_id"], [0]]), "mix")
+    ref = None
+    for sched in (dict(tile_slots=256, tile_threads=64), dict(tile_slots=1024, tile_threads=256),
+                  dict(tile_slots=4096, tile_threads=512, persistent=2), dict(tile_slots=4096, bucket_target=256),
+                  dict(tile_slots=512, bucket_target=4096, persistent=1)):
+        g = _gpu_state(mix, schedule=sched)
+        g.step(1.0, 7, 0, 8)
+        g.sync()
+        got = g.get_state()
+        g.close()
+        if ref is None:
+            ref = got
+            o = _oracle_system(mix)
+            o.run(1.0, 7, 0, 8)
+            _assert_bitexact(o, got[0], got[1])
+        else:
+            assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]), sched
+
+
+def test_gravitational_box_full_size_bitexact():
+    """The benchmarked workload (2^20 SDs in one cell) at full size, a few steps."""
+    s = inputs.gravitational_box()
+    o, ost, xi, at, gst = _run_both(s, 3, seed=42)
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"] > 1000
+    # most decisions are settled from the FP32 bound
+    assert gst["n_fp64"] < 1e-3 * gst["n_pairs"]
+
+
+def test_grid_bimodal_sample_bitexact():
+    s = inputs.grid_bimodal(nx=32, ny=32)      # the 2D-grid workload on a 32 x 32 patch
+    o, ost, xi, at, gst = _run_both(s, 10)
+    _assert_bitexact(o, xi, at)
+
+
+def test_ensemble_sample_bitexact():
+    s = inputs.ensemble(n_members=24)
+    o, ost, xi, at, gst = _run_both(s, 4)
+    _assert_bitexact(o, xi, at)
+
+
+def test_edge_cases():
+    # n_sd = 2 (one pair), 3 (odd), all-dead cell, huge p (caps bind), xi near 2^53
+    xi = np.array([5, 5, 7, 1, 9, 0, 0, (1 << 53) - 1, 3], np.uint64)
+    v = np.array([1e-12, 2e-12, 3e-12, 4e-12, 5e-12, 6e-12, 7e-12, 8e-12, 9e-12])
+    counts = [2, 3, 2, 2]
+    s = inputs._state(xi, v, counts, [1e-20, 1.0, 1.0, 1e-20], [0, 1, 0, 0], "edge")
+    o, ost, xi_g, at, gst = _run_both(s, 5)
+    _assert_bitexact(o, xi_g, at)
+    # empty state
+    e = inputs._state(np.zeros(0, np.uint64), np.zeros(0), [0], 1.0, 0, "empty")
+    g = _gpu_state(e)
+    g.step(1.0, 1, 0, 3)
+    g.sync()
+    assert g.totals() == (0, 0.0, 0)
+
+
+def test_fp32_bound_holds_and_fp64_matches_oracle():
+    rng = np.random.default_rng(2)
+    n = 200000
+    r1 = np.exp(rng.uniform(np.log(0.02e-6), np.log(2e-3), n))
+    r2 = np.where(rng.random(n) < 0.2, r1 * (1 + rng.normal(0, 1e-6, n)),
+                  np.exp(rng.uniform(np.log(0.02e-6), np.log(2e-3), n)))
+    # radii near regime joins and table nodes
+    joins = np.array([8e3 / 1.19e8, (201 / 8e3) ** 2, 10e-6, 20e-6, 40e-6, 100e-6, 300e-6, 1000e-6])
+    r1[:8000] = np.repeat(joins, 1000) * (1 + rng.normal(0, 1e-7, 8000))
+    v1 = 4 / 3 * np.pi * r1 ** 3
+    v2 = 4 / 3 * np.pi * r2 ** 3
+    xi1 = rng.integers(1, 10 ** 9, n).astype(np.uint64)
+    xi2 = rng.integers(1, 10 ** 9, n).astype(np.uint64)
+    g = sdm.State(16, 1)
+    dev = lambda a: torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
+    worst = 0.0
+    for kid, ncell, dv in ((1, 1 << 20, 1e6), (0, 8192, 1e6), (1, 127, 1e3)):
+        p64, p32, e32 = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv)
+        p64, p32, e32 = p64.cpu().numpy(), p32.cpu().numpy().astype(np.float64), e32.cpu().numpy().astype(np.float64)
+        # FP64 value equals the oracle's bit for bit (sampled)
+        for i in rng.choice(n, 2000, replace=False):
+            K = oracle.kernel(kid, v1[i], v2[i], 1500.0)
+            po = oracle.pair_prob(K, xi1[i], xi2[i], oracle.pair_scale(ncell), 1.0, dv)
+            assert p64[i] == po, (kid, i)
+        ratio = np.abs(p64 - p32) / e32
+        worst = max(worst, float(ratio.max()))
+        assert np.all(np.abs(p64 - p32) <= e32), (kid, ratio.max())
+    # the bound is not vacuous either: it is used at well under its full width
+    assert worst < 0.5, worst
+
+
+def test_fp32_mode_close_to_fp64():
+    s = inputs.gravitational_box(n_sd=1 << 16)
+    g64 = _gpu_state(s)
+    g32 = _gpu_state(s)
+    st64 = g64.step(1.0, 42, 0, 1, stats=True)
+    st32 = g32.step(1.0, 42, 0, 1, precision="fp32", stats=True)
+    x64, a64, _ = g64.get_state()
+    x32, a32, _ = g32.get_state()
+    diff = np.count_nonzero(x64 != x32)
+    assert diff <= 4, diff                       # decisions differ only at near ties
+    n64, m64, _ = g64.totals()
+    n32, m32, _ = g32.totals()
+    assert m32 == pytest.approx(m64, rel=1e-12)
+    assert abs(st64["n_collisions"] - st32["n_collisions"]) <= 2
+
+
+def test_spectrum_and_totals_match_oracle():
+    s = inputs.golovin_box()
+    o = _oracle_system(s)
+    o.run(1.0, 42, 0, 500)
+    g = _gpu_state(s)
+    g.step(1.0, 42, 0, 500)
+    r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 101))
+    so = o.spectrum(r_edges)
+    sg = g.spectrum(r_edges)
+    np.testing.assert_allclose(sg, so, rtol=1e-12, atol=0)
+    nt, nl, mo = o.totals()
+    gn, gm, gl = g.totals()
+    assert gn == nt and gl == nl
+    assert gm == pytest.approx(mo, rel=1e-12)
+    # multi-cell spectrum of a single cell and of all
+    s2 = inputs.random_cells(n_cell=50, mean_per_cell=100, seed=3)
+    o2, g2 = _oracle_system(s2), _gpu_state(s2)
+    np.testing.assert_allclose(g2.spectrum(r_edges, cell=7), o2.spectrum(r_edges, cell_lo=7, cell_hi=8), rtol=1e-12)
+    np.testing.assert_allclose(g2.spectrum(r_edges), o2.spectrum(r_edges), rtol=1e-12)
+
+
+def test_mass_conservation_and_remove_zero():
+    s = inputs.random_cells(n_cell=300, mean_per_cell=40, seed=8, xi_max=20, dv=1e-12)
+    g = _gpu_state(s)
+    n0, m0, l0 = g.totals()
+    st = g.step(1.0, 3, 0, 30, stats=True)
+    n1, m1, l1 = g.totals()
+    assert m1 == pytest.approx(m0, rel=1e-12)
+    assert n0 - n1 >= st["sum_gamma"] > 0
+    assert l1 == l0 - st["n_removed"] == g.remove_zero() == g.remove_zero()
+
+
+def test_checkpoint_resume_bitexact():
+    s = inputs.random_cells(n_cell=100, mean_per_cell=50, seed=6, xi_max=1000, dv=1e-3)
+    a = _gpu_state(s)
+    a.step(1.0, 11, 0, 10)
+    xa, aa, _ = a.get_state()
+    b = _gpu_state(s)
+    b.step(1.0, 11, 0, 5)
+    xb, ab, _ = b.get_state()
+    c = _gpu_state(s)
+    c.set_state(xb, ab)
+    c.step(1.0, 11, 5, 5)
+    c.sync()
+    xc, ac, _ = c.get_state()
+    assert np.array_equal(xa, xc) and np.array_equal(aa, ac)
+
+
+def test_cuda_graph_replay_with_device_step_counter():
+    s = inputs.random_cells(n_cell=300, mean_per_cell=40, seed=12, xi_max=10 ** 5, dv=1e-3)
+    big = inputs.golovin_box(n_sd=3000)
+    xi = np.concatenate([s["xi"], big["xi"]])
+    v = np.concatenate([s["v"], big["v"]])
+    counts = np.concatenate([np.diff(s["cell_start"].astype(np.int64)), [3000]])
+    mix = inputs._state(xi, v, counts, np.concatenate([s["dv"], [1e6]]), np.concatenate([s["kernel_id"], [0]]),
+                        "mix")
+    ref = _gpu_state(mix)
+    ref.step(1.0, 5, 0, 12)
+    xr, ar, _ = ref.get_state()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = _gpu_state(mix)
+        d_step = torch.zeros(1, dtype=torch.int32, device="cuda")
+        g.step(1.0, 5, 0, 1, d_step=d_step)          # warm-up outside capture: steps 0
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            g.step(1.0, 5, 0, 4, d_step=d_step)       # captured: 4 steps
+        torch.cuda.synchronize()
+        # the capture itself did not run; 11 more steps = replay 4 + 4 then 3 host steps
+        graph.replay()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(d_step.item()) == 9
+        g.step(1.0, 5, 9, 3)
+        g.sync()
+        xg, ag, _ = g.get_state()
+    assert np.array_equal(xr, xg) and np.array_equal(ar, ag)
+
+
+def test_invalid_inputs_raise():
+    s = inputs.random_cells(n_cell=4, mean_per_cell=5, seed=1, min_per_cell=1)
+    n = len(s["xi"])
+    bad = dict(s)
+    bad["v"] = s["v"].copy()
+    bad["v"][0] = -1.0
+    with pytest.raises(sdm.SDMError) as e:
+        _gpu_state(bad)
+    assert e.value.code == 1
+    bad = dict(s)
+    bad["xi"] = s["xi"].copy()
+    bad["xi"][0] = 1 << 53
+    with pytest.raises(sdm.SDMError) as e:
+        _gpu_state(bad)
+    assert e.value.code == 4
+    st = sdm.State(n - 1, 4)
+    with pytest.raises(sdm.SDMError) as e:
+        st.init(s["xi"], s["v"][None], s["dv"], s["kernel_id"], cell_start=s["cell_start"])
+    assert e.value.code == 3
+    g = _gpu_state(s)
+    with pytest.raises(sdm.SDMError):
+        g.step(dt=-1.0)
+    # invalid data streamed in later is reported at the next sync
+    xi = s["xi"].copy()
+    xi[1] = 1 << 60
+    g.set_state(xi, s["v"][None].copy())
+    with pytest.raises(sdm.SDMError) as e:
+        g.sync()
+    assert e.value.code == 4
+    g.sync()   # the error word was cleared
+
+
+def test_device_pointer_init_and_workspace():
+    s = inputs.random_cells(n_cell=64, mean_per_cell=30, seed=2)
+    n = len(s["xi"])
+    ws_bytes = sdm.lib().sdm_workspace_bytes(n, 64, 1)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    g = sdm.State(n, 64, 1, workspace=ws)
+    g.init(torch.from_numpy(s["xi"].view(np.int64)).cuda(), torch.from_numpy(s["v"][None].copy()).cuda(),
+           torch.from_numpy(s["dv"]).cuda(), torch.from_numpy(s["kernel_id"]).cuda(),
+           cell_start=torch.from_numpy(s["cell_start"].view(np.int32)).cuda())
+    g.step(1.0, 1, 0, 5)
+    o = _oracle_system(s)
+    o.run(1.0, 1, 0, 5)
+    xi_d = torch.empty(n, dtype=torch.int64, device="cuda")
+    at_d = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    g.get_state(xi_d, at_d)
+    torch.cuda.synchronize()
+    _assert_bitexact(o, xi_d.cpu().numpy().view(np.uint64), at_d.cpu().numpy())
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sdm.SDMError) as e:
+        sdm.State(n, 64, 1, workspace=small)
+    assert e.value.code == 2
+
+
+def test_autotune_keeps_results():
+    s = inputs.random_cells(n_cell=500, mean_per_cell=100, seed=3, xi_max=10 ** 4, dv=1e-2)
+    a = _gpu_state(s)
+    best = a.autotune(n_steps=2)
+    assert best["tile_slots"] in (512, 1024, 2048, 4096)
+    a.step(1.0, 2, 0, 6)
+    xa, aa, _ = a.get_state()
+    o = _oracle_system(s)
+    o.run(1.0, 2, 0, 6)
+    _assert_bitexact(o, xa, aa)
