@@ -233,6 +233,43 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
                           double dv, double dt, double golovin_b,
                           double* p64, float* p32, float* err32);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free single-box step.  (No counterpart in the paper: this is a
+ * deployment convenience of the library.)
+ *
+ * Some callers cannot allocate device memory at all: code that runs where the
+ * CUDA allocator may not be called (for example from a host callback enqueued
+ * on a stream), processes whose device memory is fully owned by another pool
+ * or framework with a hard cap, and latency-critical loops that must not hit
+ * the implicit synchronisation of cudaMalloc/cudaFree.  sdm_alloc does not
+ * suit them, so this entry point performs one coalescence timestep of a single
+ * box (one cell, cell index 0 of the random-number contract) directly on the
+ * caller's device arrays, with all scratch memory taken from a fixed array
+ * compiled into the library (about 4.2 MB of device memory, held by every GPU
+ * that loads the library until the process exits).  It calls no allocating
+ * routine.
+ *
+ *   xi[n_sd]                    multiplicities (device, updated in place)
+ *   attr[n_attr][attr_stride]   extensive attributes, row 0 = volume (device,
+ *                               updated in place); attr_stride >= n_sd
+ *   n_sd                        SDs in the box, at most SDM_NOALLOC_MAX_SD;
+ *                               larger boxes return SDM_ECAPACITY
+ *   dv, kernel_id               cell volume [m^3] and sdm_kernel_id
+ *   params                      as for sdm_coalescence_step (d_step allowed)
+ *   cuda_stream                 cudaStream_t the work is ordered on
+ * Results are identical to sdm_coalescence_step on a one-cell state holding
+ * the same arrays.  The call enqueues the step, then waits for the stream to
+ * read the step's error word, and returns it (SDM_ECAPACITY on a bucket
+ * overflow).  The first call on each device looks up the device address of
+ * the fixed scratch array (once per device, under a lock); make that first
+ * call before capturing any stream.  All calls share the one scratch array:
+ * calls that overlap on the GPU (different streams, or several host threads)
+ * race with each other and must be serialised by the caller. */
+#define SDM_NOALLOC_MAX_SD (1u << 18)
+sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, uint32_t n_attr, uint64_t attr_stride,
+                                        uint32_t n_sd, double dv, uint32_t kernel_id,
+                                        const sdm_step_params* params, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -904,3 +905,128 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
 }
 
 }  // extern "C"
+// ---------------------------------------------------------------------------
+// Allocation-free single-box step: the large-cell kernels run on the caller's
+// arrays with their scratch in a fixed array compiled into the library.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t NA_TARGET_BITS = 10;                                   // 1024 SDs per bucket on average
+constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 256
+constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 2112 records per bucket
+constexpr uint32_t NA_MAX_CHUNKS = (SDM_NOALLOC_MAX_SD + BIG_CHUNK - 1) / BIG_CHUNK;
+// byte offsets inside the scratch array
+constexpr size_t NA_OFF_CELL = 0;        // BigCell
+constexpr size_t NA_OFF_DV = 64;         // double dv
+constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
+constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
+constexpr size_t NA_OFF_CHUNKS = 256;
+constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
+constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;
+constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 8 * NA_MAX_BUCKETS + 255) / 256 * 256;
+constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
+
+// one per loaded library and device; its contents persist between calls
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
+
+// device address of the scratch array on the current device (looked up once per device)
+sdm_status noalloc_scratch(unsigned char** out)
+{
+    int dev = 0;
+    SDM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return SDM_ENOTSUP;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return SDM_ECUDA;
+        const FinishLayout fl = finish_layout(NA_MAX_CAP);
+        const uint32_t scatter_smem = sizeof(uint32_t) * (2 * NA_MAX_BUCKETS + 2 * BIG_CHUNK);
+        SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
+        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
+        g_na_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_na_ptr[dev];
+    return SDM_OK;
+}
+
+}  // namespace
+
+extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, uint32_t n_attr,
+                                                   uint64_t attr_stride, uint32_t n_sd, double dv,
+                                                   uint32_t kernel_id, const sdm_step_params* p,
+                                                   void* cuda_stream)
+{
+    if (!p || (n_sd && (!xi || !attr)) || n_attr == 0 || attr_stride < n_sd) return SDM_EINVAL;
+    if (n_sd > SDM_NOALLOC_MAX_SD) return SDM_ECAPACITY;
+    if (kernel_id > SDM_KERNEL_GRAVITATIONAL || !(dv > 0.0) || !std::isfinite(dv)) return SDM_EINVAL;
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt) || p->precision > SDM_PREC_FP32) return SDM_EINVAL;
+    if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
+    if (n_sd < 2) return SDM_OK;
+    unsigned char* base = nullptr;
+    SDM_TRY(noalloc_scratch(&base));
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // the same bucket geometry as the large-cell path with a 1024-SD bucket target
+    BigCell C{};
+    C.cell = 0;
+    C.slot_begin = 0;
+    C.width = n_sd;
+    C.nbits = ceil_log2_h(n_sd) > NA_TARGET_BITS ? ceil_log2_h(n_sd) - NA_TARGET_BITS : 0;
+    C.bucket_base = 0;
+    const uint32_t nb = 1u << C.nbits;
+    const uint32_t cap = ((2 * ((n_sd + nb - 1) / nb) + 64) + 31) & ~31u;
+    BigChunk chunks[NA_MAX_CHUNKS];
+    uint32_t n_chunks = 0;
+    for (uint32_t l = 0; l < n_sd; l += BIG_CHUNK) chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), 0};
+    uint32_t bucket_big[NA_MAX_BUCKETS] = {};
+    unsigned char head[256] = {};
+    const uint8_t kid = (uint8_t)kernel_id;
+    std::memcpy(head + NA_OFF_CELL, &C, sizeof C);
+    std::memcpy(head + NA_OFF_DV, &dv, sizeof dv);
+    std::memcpy(head + NA_OFF_KID, &kid, 1);
+
+    // descriptors in; cursors and error word start at zero on every call
+    SDM_CUDA(cudaMemcpyAsync(base, head, sizeof head, cudaMemcpyHostToDevice, stream));
+    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_CHUNKS, chunks, sizeof(BigChunk) * n_chunks, cudaMemcpyHostToDevice, stream));
+    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_big, 4 * nb, cudaMemcpyHostToDevice, stream));
+    SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 8 * NA_MAX_BUCKETS, stream));
+
+    StepArgs a{};
+    a.xi = xi;
+    a.attr = attr;
+    a.stride = attr_stride;
+    a.n_attr = n_attr;
+    a.precision = p->precision;
+    a.cell_start = nullptr;                       // not read by the large-cell kernels
+    a.dv = (const double*)(base + NA_OFF_DV);
+    a.kid = (const uint8_t*)(base + NA_OFF_KID);
+    a.dt = p->dt;
+    a.golovin_b = p->golovin_b;
+    a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.step = p->step;
+    a.d_step = p->d_step;
+    a.stats = nullptr;
+    a.err = (uint32_t*)(base + NA_OFF_ERR);
+    const BigCell* d_cell = (const BigCell*)(base + NA_OFF_CELL);
+    uint32_t* cur = (uint32_t*)(base + NA_OFF_CURSOR);
+    uint32_t* nxt = cur + NA_MAX_BUCKETS;
+    uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
+    const FinishLayout fl = finish_layout(cap);
+    const uint32_t scatter_smem = sizeof(uint32_t) * (2 * nb + 2 * BIG_CHUNK);
+    big_scatter_kernel<<<n_chunks, 512, scatter_smem, stream>>>(a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS),
+                                                                rec, cur, cap);
+    big_finish_kernel<<<nb, 256, fl.bytes, stream>>>(a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, cur, nxt,
+                                                      fl);
+    if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
+    SDM_CUDA(cudaGetLastError());
+    uint32_t e = 0;
+    SDM_CUDA(cudaMemcpyAsync(&e, base + NA_OFF_ERR, sizeof e, cudaMemcpyDeviceToHost, stream));
+    SDM_CUDA(cudaStreamSynchronize(stream));
+    return err_to_status(e);
+}

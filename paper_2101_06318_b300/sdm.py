@@ -32,7 +32,7 @@ EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", 
            "sdm_init_state_segmented", "sdm_set_state", "sdm_get_state", "sdm_coalescence_step",
            "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_get_schedule", "sdm_set_schedule",
            "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
-           "sdm_launches_per_step"]
+           "sdm_launches_per_step", "sdm_coalescence_step_noalloc"]
 
 
 class SDMError(RuntimeError):
@@ -98,6 +98,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_set_profiling.argtypes = [vp, i32]
         L.sdm_get_profile.argtypes = [vp, vp, vp]
         L.sdm_launches_per_step.argtypes = [vp, vp]
+        L.sdm_coalescence_step_noalloc.argtypes = [vp, vp, u32, u64, u32, f64, u32, C.POINTER(StepParams), vp]
         for name in EXPORTS:
             if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free"):
                 getattr(L, name).restype = i32
