@@ -73,7 +73,7 @@ typedef enum {
      * gamma: the probability is first bounded in FP32 and only pairs whose
      * integer outcome the bound cannot settle are re-evaluated in FP64. */
     SDM_PREC_FP64 = 0,
-    /* The decision is taken from the FP32 value of p and a 24-bit phi;
+    /* The decision is taken from the FP32 value of p and the leading 23 bits of phi;
      * multiplicities stay exact uint64 and the attribute update stays FP64. */
     SDM_PREC_FP32 = 1
 } sdm_precision;
@@ -245,7 +245,7 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
  * suit them, so this entry point performs one coalescence timestep of a single
  * box (one cell, cell index 0 of the random-number contract) directly on the
  * caller's device arrays, with all scratch memory taken from a fixed array
- * compiled into the library (about 4.2 MB of device memory, held by every GPU
+ * compiled into the library (about 13 MB of device memory, held by every GPU
  * that loads the library until the process exits).  It calls no allocating
  * routine.
  *

@@ -26,6 +26,7 @@ constexpr double RHO_WATER = 1000.0;
 constexpr double FOUR_PI_OVER_THREE = 4.18879020478639053;
 constexpr uint32_t ERR_INVALID = 1u << 8;
 constexpr uint32_t ERR_RANGE = 1u << 9;
+constexpr uint32_t FINISH_SMEM = 200 * 1024;   // dynamic shared memory budget of the finishing pass
 
 struct DevAlloc {
     void* p;
@@ -69,10 +70,12 @@ struct sdm_state {
     uint32_t n_chunks = 0;
     uint32_t* d_bucket_big = nullptr;
     uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
-    uint32_t* d_cursor = nullptr;            // [2][n_buckets]
+    uint32_t* d_cursor = nullptr;            // [n_buckets] appends per bucket (zero between steps)
+    uint32_t* d_bstart = nullptr;            // [n_buckets + 1] bucket offsets of the current step
+    uint32_t* d_ticket = nullptr;            // [1] CTAs of the scatter pass that finished
     uint64_t* d_scratch = nullptr;
     FinishLayout fin_L{};
-    int clean_parity = -1;                   // -1: both cursor buffers zero; 0/1: that one; 2: unknown
+    uint32_t fin_grid = 0, n_buckets_planned = 0;
 
     // host copies of the layout
     std::vector<uint32_t> h_cell_start;
@@ -137,7 +140,7 @@ void free_layout(sdm_state* st)
     st->owned_layout.clear();
     if (st->ws) st->ws_used = st->ws_fixed;
     st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
-    st->d_cursor = nullptr; st->d_scratch = nullptr;
+    st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
 }
 
@@ -163,7 +166,7 @@ sdm_status check_schedule(const sdm_schedule& s)
 {
     if (!is_pow2(s.tile_slots) || s.tile_slots < 256 || s.tile_slots > 4096) return SDM_EINVAL;
     if (s.tile_threads < 64 || s.tile_threads > 512 || s.tile_threads % 32) return SDM_EINVAL;
-    if (!is_pow2(s.bucket_target) || s.bucket_target < 256 || s.bucket_target > 4096) return SDM_EINVAL;
+    if (!is_pow2(s.bucket_target) || s.bucket_target < 64 || s.bucket_target > 2048) return SDM_EINVAL;
     if (s.persistent > 32) return SDM_EINVAL;
     return SDM_OK;
 }
@@ -221,10 +224,16 @@ sdm_status build_layout(sdm_state* st)
     }
     flush();
     bucket_cap = (bucket_cap + 31) & ~31u;
+    st->n_buckets_planned = (uint32_t)bucket_big.size();
     if (!bigs.empty()) {
-        const FinishLayout fl = finish_layout(bucket_cap);
-        if (fl.bytes > 200 * 1024) return SDM_ECAPACITY;   // a cell too large for this bucket width
+        const FinishLayout fl = finish_layout(bucket_cap, FINISH_SMEM);
+        if (fl.bytes > FINISH_SMEM) return SDM_ECAPACITY;   // a cell too large for this bucket width
         st->fin_L = fl;
+        int per_sm = 0;
+        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_finish_kernel, 32 * fl.warps, fl.bytes));
+        const uint32_t need = (st->n_buckets_planned + fl.warps - 1) / fl.warps;
+        st->fin_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
     }
     st->tile_L = tile_layout(S.tile_slots, max_cells);
     st->max_cells_per_tile = max_cells;
@@ -240,13 +249,16 @@ sdm_status build_layout(sdm_state* st)
     st->bucket_cap = bucket_cap;
     st->max_nb = max_nb;
     if (st->n_buckets) {
-        SDM_TRY(dev_alloc(st, (void**)&st->d_cursor, sizeof(uint32_t) * 2 * st->n_buckets, true));
-        SDM_CUDA(cudaMemsetAsync(st->d_cursor, 0, sizeof(uint32_t) * 2 * st->n_buckets, st->stream));
-        SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
-        st->clean_parity = -1;
-        const uint32_t scatter_smem = sizeof(uint32_t) * (2 * max_nb + 2 * BIG_CHUNK);
+        // cursors (n_buckets), the ticket, then the offsets (n_buckets + 1), all zeroed once here;
+        // afterwards the scatter pass leaves cursors and ticket at zero at the end of every step
+        const size_t words = 2 * (size_t)st->n_buckets + 2;
+        SDM_TRY(dev_alloc(st, (void**)&st->d_cursor, sizeof(uint32_t) * words, true));
+        SDM_CUDA(cudaMemsetAsync(st->d_cursor, 0, sizeof(uint32_t) * words, st->stream));
+        st->d_ticket = st->d_cursor + st->n_buckets;
+        st->d_bstart = st->d_ticket + 1;
+        SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, 3 * sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
+        const uint32_t scatter_smem = sizeof(uint32_t) * 2 * max_nb;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
-        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->fin_L.bytes));
     }
     SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
     SDM_CUDA(cudaStreamSynchronize(st->stream));
@@ -407,24 +419,15 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.kid = st->d_kid;
     a.dt = p->dt;
     a.golovin_b = p->golovin_b;
+    a.dt_f = (float)p->dt;
+    a.golovin_bf = (float)p->golovin_b;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.d_step = p->d_step;
     a.stats = with_stats ? st->d_stats : nullptr;
     a.err = st->d_err;
     const sdm_schedule& S = st->sched;
-    if (st->n_buckets) {
-        if (p->d_step) {
-            st->clean_parity = 2;   // buffer 0 is cleared before every step below
-        } else {
-            const int need = (int)(p->step & 1u);
-            if (st->clean_parity != -1 && st->clean_parity != need) {
-                SDM_CUDA(cudaMemsetAsync(st->d_cursor + (size_t)need * st->n_buckets, 0,
-                                         sizeof(uint32_t) * st->n_buckets, st->stream));
-            }
-        }
-    }
-    const uint32_t scatter_smem = sizeof(uint32_t) * (2 * st->max_nb + 2 * BIG_CHUNK);
+    const uint32_t scatter_smem = sizeof(uint32_t) * 2 * st->max_nb;
     for (uint32_t s = 0; s < n_steps; ++s) {
         a.step = p->step + s;
         if (st->n_tiles) {
@@ -439,25 +442,17 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                                                                                     st->tile_L, work);
         }
         if (st->n_buckets) {
-            // cursor buffers alternate with the step parity (the finishing pass clears the other one)
-            const uint32_t par = p->d_step ? 0u : (a.step & 1u);
-            uint32_t* cur = st->d_cursor + (size_t)par * st->n_buckets;
-            uint32_t* nxt = st->d_cursor + (size_t)(par ^ 1u) * st->n_buckets;
-            if (p->d_step) {
-                // with a device step counter the parity is unknown here: always use buffer 0, cleared first
-                SDM_CUDA(cudaMemsetAsync(cur, 0, sizeof(uint32_t) * st->n_buckets, st->stream));
-            }
+            const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
                 ProfScope ps(st, 1);
-                big_scatter_kernel<<<st->n_chunks, 512, scatter_smem, st->stream>>>(a, st->d_big, st->d_chunks,
-                                                                                   st->d_scratch, cur, st->bucket_cap);
+                big_scatter_kernel<<<st->n_chunks, BIG_SCATTER_THREADS, scatter_smem, st->stream>>>(
+                    a, st->d_big, st->d_chunks, st->d_scratch, bk);
             }
             {
                 ProfScope ps(st, 2);
-                big_finish_kernel<<<st->n_buckets, 256, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_big, st->d_scratch, cur, nxt, st->fin_L);
+                big_finish_kernel<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
+                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->fin_L);
             }
-            if (!p->d_step) st->clean_parity = (int)(par ^ 1u);
         }
         if (p->d_step) advance_step_kernel<<<1, 32, 0, st->stream>>>(p->d_step, 1u);
         SDM_CUDA(cudaGetLastError());
@@ -495,10 +490,10 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
-    const size_t max_buckets = 3 * cap / 256 + 1;
-    const size_t max_cap = 2 * 4096 + 64 + 32;
+    const size_t max_buckets = 3 * cap / 64 + 1;
+    const size_t max_cap = 2 * 2048 + 64 + 32;
     b += round256(4 * max_buckets + 256) + round256(8 * max_buckets + 256);
-    b += round256(8 * max_buckets * max_cap + 256);
+    b += round256(3 * 8 * max_buckets * max_cap + 256);
     return b;
 }
 
@@ -514,7 +509,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
     st->cap = cap;
     st->n_cell = n_cell;
     st->n_attr = n_attr;
-    st->sched = sdm_schedule{1024, 256, 1024, 0};
+    st->sched = sdm_schedule{1024, 256, 256, 0};
     if (cudaGetDevice(&st->device) != cudaSuccess) { delete st; return SDM_ECUDA; }
     cudaDeviceGetAttribute(&st->n_sm, cudaDevAttrMultiProcessorCount, st->device);
     if (workspace) {
@@ -830,7 +825,7 @@ sdm_status sdm_autotune(sdm_state* st, const sdm_step_params* p, uint32_t n_step
         if (t < bt) { bt = t; bs = c; }
     }
     // then the bucket width of the large-cell path
-    for (uint32_t bw : {512u, 1024u, 2048u}) {
+    for (uint32_t bw : {128u, 256u, 512u, 1024u}) {
         sdm_schedule c = bs;
         c.bucket_target = bw;
         const float t = trial(c);
@@ -911,9 +906,9 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr uint32_t NA_TARGET_BITS = 10;                                   // 1024 SDs per bucket on average
-constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 256
-constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 2112 records per bucket
+constexpr uint32_t NA_TARGET_BITS = 8;                                    // 256 SDs per bucket on average
+constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 1024
+constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 576 records per bucket
 constexpr uint32_t NA_MAX_CHUNKS = (SDM_NOALLOC_MAX_SD + BIG_CHUNK - 1) / BIG_CHUNK;
 // byte offsets inside the scratch array
 constexpr size_t NA_OFF_CELL = 0;        // BigCell
@@ -922,9 +917,10 @@ constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
 constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
 constexpr size_t NA_OFF_CHUNKS = 256;
 constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
-constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;
-constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 8 * NA_MAX_BUCKETS + 255) / 256 * 256;
-constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
+constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
+constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
+constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
+constexpr size_t NA_BYTES = NA_OFF_RECORDS + 3 * sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
 
 // one per loaded library and device; its contents persist between calls
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -944,8 +940,8 @@ sdm_status noalloc_scratch(unsigned char** out)
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) return SDM_ECUDA;
-        const FinishLayout fl = finish_layout(NA_MAX_CAP);
-        const uint32_t scatter_smem = sizeof(uint32_t) * (2 * NA_MAX_BUCKETS + 2 * BIG_CHUNK);
+        const FinishLayout fl = finish_layout(NA_MAX_CAP, FINISH_SMEM);
+        const uint32_t scatter_smem = sizeof(uint32_t) * 2 * NA_MAX_BUCKETS;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
         SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
         g_na_ptr[dev] = (unsigned char*)p;
@@ -994,7 +990,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     SDM_CUDA(cudaMemcpyAsync(base, head, sizeof head, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_CHUNKS, chunks, sizeof(BigChunk) * n_chunks, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_big, 4 * nb, cudaMemcpyHostToDevice, stream));
-    SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 8 * NA_MAX_BUCKETS, stream));
+    SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
 
     StepArgs a{};
     a.xi = xi;
@@ -1007,6 +1003,8 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.kid = (const uint8_t*)(base + NA_OFF_KID);
     a.dt = p->dt;
     a.golovin_b = p->golovin_b;
+    a.dt_f = (float)p->dt;
+    a.golovin_bf = (float)p->golovin_b;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.step = p->step;
@@ -1014,15 +1012,16 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.stats = nullptr;
     a.err = (uint32_t*)(base + NA_OFF_ERR);
     const BigCell* d_cell = (const BigCell*)(base + NA_OFF_CELL);
-    uint32_t* cur = (uint32_t*)(base + NA_OFF_CURSOR);
-    uint32_t* nxt = cur + NA_MAX_BUCKETS;
+    uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
+    // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
+    const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
     uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
-    const FinishLayout fl = finish_layout(cap);
-    const uint32_t scatter_smem = sizeof(uint32_t) * (2 * nb + 2 * BIG_CHUNK);
-    big_scatter_kernel<<<n_chunks, 512, scatter_smem, stream>>>(a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS),
-                                                                rec, cur, cap);
-    big_finish_kernel<<<nb, 256, fl.bytes, stream>>>(a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, cur, nxt,
-                                                      fl);
+    const FinishLayout fl = finish_layout(cap, FINISH_SMEM);
+    const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
+    big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
+        a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
+    big_finish_kernel<<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
+        a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, fl);
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());
     uint32_t e = 0;

@@ -45,6 +45,8 @@ struct StepArgs {
     const uint8_t* kid;         // [n_cell]
     double dt;
     double golovin_b;
+    float dt_f;                 // dt and golovin_b rounded to float on the host
+    float golovin_bf;
     uint32_t seed_lo, seed_hi;
     uint32_t step;              // used when d_step == nullptr
     const uint32_t* d_step;
@@ -73,31 +75,38 @@ struct CellCtx {
     double dv;
 };
 
-__device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, double dt, double dv)
+__device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, float dt_f, double dv)
 {
     // ((n^2 - n)/2) / floor(n/2) is n - 1 (n even) or n (n odd): exact integer
     const float s = (float)(n - 1u + (n & 1u));
-    return s * (__double2float_rn(dt) / __double2float_rn(dv));
+    return s * (dt_f / d2f_trunc(dv));
 }
 
-// Step 2 + Step 3 for candidate pair m = (first, second) of a cell.  Writes the
-// updated multiplicities and attributes of the pair to global memory.
-__device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
-                                             uint32_t step, uint32_t m, uint64_t g1, uint64_t g2, uint64_t x1,
-                                             uint64_t x2, double v1, double v2, LocalStats& ls)
+// phi integers of candidate pairs 2M and 2M+1 of a cell (one Philox call)
+__device__ __forceinline__ void phi_pair_u53(const StepArgs& a, uint32_t cell, uint32_t step, uint32_t M,
+                                             uint64_t& u0, uint64_t& u1)
 {
-    const uint64_t u53 = phi_u53(a.seed_lo, a.seed_hi, c.gid, step, m);
+    const U4 x = philox(M, cell, step, 1u, a.seed_lo, a.seed_hi);
+    u0 = ((((uint64_t)x.x) << 32) | (uint64_t)x.y) >> 11;
+    u1 = ((((uint64_t)x.z) << 32) | (uint64_t)x.w) >> 11;
+}
+
+// Step 2 + Step 3 for one candidate pair (first, second) of a cell with phi
+// integer u53.  Writes the updated multiplicities and attributes of the pair to
+// global memory.
+__device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
+                                             uint64_t u53, uint64_t g1, uint64_t g2, uint64_t x1, uint64_t x2,
+                                             double v1, double v2, LocalStats& ls)
+{
     const bool swap = x1 < x2;                 // j = first unless it has the smaller multiplicity
     const uint64_t xj = swap ? x2 : x1, xk = swap ? x1 : x2;
-    const float scale32 = __ull2float_rn(xj) * c.s_dtdv32;
-    const P32 pe = pair_prob_f(T, c.kid, v1, v2, scale32, (float)a.golovin_b);
+    const float scale32 = u64_to_f_trunc(xj) * c.s_dtdv32;
+    const P32 pe = pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf);
     uint64_t g;
     if (a.precision == PREC_FP32) {
         g = gamma_tilde_f(pe.p, u53, xj, xk);
     } else if (!gamma_tilde_certified(pe, u53, xj, xk, &g)) {
-        const double K = kernel_d(c.kid, v1, v2, a.golovin_b);
-        const double p = pair_prob_d(K, xj, c.n, a.dt, c.dv);
-        g = gamma_tilde_d(p, u53, xj, xk);
+        g = gamma_tilde_fp64_path(c.kid, v1, v2, a.golovin_b, c.n, a.dt, c.dv, u53, xj, xk);
         ls.fp64++;
     }
     ls.pairs++;
@@ -379,27 +388,35 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         const uint32_t s0 = cnt[bb[c]], s1 = cnt[bb[c + 1]];
         const uint32_t n = s1 - s0;
         ss[c] = s0;
-        pb[c] = n >> 1;
         const uint32_t gid = td.cell_begin + c;
         CellCtx cc;
         cc.gid = gid;
         cc.n = n;
         cc.kid = a.kid[gid];
         cc.dv = a.dv[gid];
-        cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt, cc.dv) : 0.f;
+        cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, cc.dv) : 0.f;
         ctx[c] = cc;
+        pb[c] = (n >> 1) + 1u >> 1;              // groups of two pairs (one Philox call each)
     }
     __syncthreads();
     if (tid < 32) warp0_exclusive_scan(pb, nc);
     __syncthreads();
     const uint32_t P = pb[nc];
-    // Steps 2-3 for every candidate pair of the tile
+    // Steps 2-3 for every candidate pair of the tile, two consecutive pairs per thread
     for (uint32_t t = tid; t < P; t += nt) {
         const uint32_t c = find_segment(pb, nc, t);
-        const uint32_t m = t - pb[c];
-        const uint32_t i1 = srt[ss[c] + 2 * m], i2 = srt[ss[c] + 2 * m + 1];
-        process_pair(a, tab, ctx[c], step, m, td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
-                     v_s[i1], v_s[i2], ls);
+        const uint32_t M = t - pb[c];
+        const CellCtx& cc = ctx[c];
+        uint64_t u[2];
+        phi_pair_u53(a, cc.gid, step, M, u[0], u[1]);
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t m = 2 * M + h;
+            if (m >= (cc.n >> 1)) break;
+            const uint32_t i1 = srt[ss[c] + 2 * m], i2 = srt[ss[c] + 2 * m + 1];
+            process_pair(a, tab, cc, u[h], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2], v_s[i1],
+                         v_s[i2], ls);
+        }
     }
 }
 
@@ -441,98 +458,154 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
 // ---------------------------------------------------------------------------
 // Large cells, pass 1: scatter (key, slot) into fixed-capacity buckets.
 // ---------------------------------------------------------------------------
-constexpr uint32_t BIG_CHUNK = 8192;          // slots per scatter CTA (multiple of 4)
+constexpr uint32_t BIG_CHUNK = 2048;          // slots per scatter CTA (multiple of 4)
+constexpr uint32_t BIG_SCATTER_THREADS = 256;
+constexpr uint32_t BIG_GROUPS_PER_THREAD = BIG_CHUNK / 4 / BIG_SCATTER_THREADS;
 constexpr uint32_t BIG_MAX_BUCKET_BITS = 13;  // <= 8192 buckets per cell
 
-__global__ void __launch_bounds__(512) big_scatter_kernel(StepArgs a, const BigCell* __restrict__ cells,
-                                                          const BigChunk* __restrict__ chunks,
-                                                          uint64_t* __restrict__ scratch,
-                                                          uint32_t* __restrict__ cursor, uint32_t bucket_cap)
+// Bucket bookkeeping shared by the two passes.
+//   cursor[b]  records appended to bucket b in this step (zero between steps)
+//   bstart[b]  exclusive prefix of the (capacity-clamped) counts over all
+//              buckets, bstart[n_buckets] = total; written by the last CTA of
+//              pass 1, which also clears cursor[] and the ticket.
+struct BucketBook {
+    uint32_t* cursor;
+    uint32_t* bstart;
+    uint32_t* ticket;
+    uint32_t n_buckets;
+    uint32_t cap;
+};
+
+// Records of bucket b (capacity cap) live at rec + b * 3 * cap:
+//   [0, cap)      (key << 32) | local slot
+//   [cap, 2cap)   multiplicity xi
+//   [2cap, 3cap)  volume v (bits)
+// so that the finishing pass reads its bucket contiguously and never gathers.
+__global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                                         const BigChunk* __restrict__ chunks,
+                                                                         uint64_t* __restrict__ rec, BucketBook bk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_last;
+    __shared__ uint32_t wt[40];
     const BigChunk ch = chunks[blockIdx.x];
     const BigCell C = cells[ch.big];
     const uint32_t nb = 1u << C.nbits;
     uint32_t* hist = (uint32_t*)smem;              // nb
     uint32_t* base = hist + nb;                    // nb
-    uint32_t* key_s = base + nb;                   // BIG_CHUNK
-    uint32_t* bo_s = key_s + BIG_CHUNK;            // BIG_CHUNK
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t step = step_index(a);
-    const uint32_t n = ch.l_end - ch.l_begin;
 
-    if (tid == 0) {
-        // warm L2 with this chunk's volumes: the finishing pass gathers them
-        const uintptr_t p0 = (uintptr_t)(a.attr + C.slot_begin + ch.l_begin) & ~(uintptr_t)15;
-        const uintptr_t p1 = ((uintptr_t)(a.attr + C.slot_begin + ch.l_end) + 15) & ~(uintptr_t)15;
-        const uint32_t bytes = (uint32_t)(p1 - p0);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p0), "r"(bytes) : "memory");
+    // multiplicities and volumes of this thread's groups first (one memory round trip)
+    uint64_t xv[BIG_GROUPS_PER_THREAD][4];
+    double vv[BIG_GROUPS_PER_THREAD][4];
+#pragma unroll
+    for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
+        const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const bool in = l0 + k < ch.l_end;
+            xv[q][k] = in ? a.xi[C.slot_begin + l0 + k] : 0ull;
+            vv[q][k] = in ? a.attr[C.slot_begin + l0 + k] : 0.0;
+        }
     }
     for (uint32_t b = tid; b < nb; b += nt) hist[b] = 0;
     __syncthreads();
-    const uint32_t ngroups = (n + 3) >> 2;
-    for (uint32_t g = tid; g < ngroups; g += nt) {
-        const uint32_t l0 = ch.l_begin + 4 * g;
+    uint32_t kb[BIG_GROUPS_PER_THREAD][4];        // key, then bucket << 16 | offset
+    uint32_t keys[BIG_GROUPS_PER_THREAD][4];
+#pragma unroll
+    for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
+        const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
         const U4 x = philox(l0 >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi);
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t l = l0 + k;
-            if (l >= ch.l_end) break;
-            const uint32_t i = l - ch.l_begin;
-            if (a.xi[C.slot_begin + l] != 0) {
-                const uint32_t key = u4_word(x, k);
-                const uint32_t b = C.nbits ? key >> (32u - C.nbits) : 0u;
-                const uint32_t off = atomicAdd(&hist[b], 1u);
-                key_s[i] = key;
-                bo_s[i] = (b << 16) | off;
-            } else {
-                bo_s[i] = DEAD;
+            keys[q][k] = u4_word(x, k);
+            kb[q][k] = DEAD;
+            if (l0 + k < ch.l_end && xv[q][k] != 0) {
+                const uint32_t b = C.nbits ? keys[q][k] >> (32u - C.nbits) : 0u;
+                kb[q][k] = (b << 16) | atomicAdd(&hist[b], 1u);
             }
         }
     }
     __syncthreads();
     for (uint32_t b = tid; b < nb; b += nt) {
         const uint32_t h = hist[b];
-        if (h) base[b] = atomicAdd(&cursor[C.bucket_base + b], h);
+        if (h) base[b] = atomicAdd(&bk.cursor[C.bucket_base + b], h);
     }
     __syncthreads();
-    for (uint32_t i = tid; i < n; i += nt) {
-        const uint32_t bo = bo_s[i];
-        if (bo == DEAD) continue;
-        const uint32_t b = bo >> 16;
-        const uint32_t pos = base[b] + (bo & 0xffffu);
-        if (pos < bucket_cap) {
-            scratch[(uint64_t)(C.bucket_base + b) * bucket_cap + pos] =
-                (((uint64_t)key_s[i]) << 32) | (uint64_t)(ch.l_begin + i);
-        } else {
-            atomicOr(a.err, ERR_BUCKET_OVERFLOW);
+#pragma unroll
+    for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
+        const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t bo = kb[q][k];
+            if (bo == DEAD) continue;
+            const uint32_t b = bo >> 16;
+            const uint32_t pos = base[b] + (bo & 0xffffu);
+            if (pos < bk.cap) {
+                uint64_t* r = rec + (uint64_t)(C.bucket_base + b) * 3 * bk.cap + pos;
+                r[0] = (((uint64_t)keys[q][k]) << 32) | (uint64_t)(l0 + k);
+                r[bk.cap] = xv[q][k];
+                r[2 * bk.cap] = (uint64_t)__double_as_longlong(vv[q][k]);
+            }
         }
     }
+    // the last CTA to finish turns the bucket counts into offsets and clears them (the
+    // cursor atomics above returned, so they are complete before the ticket is taken)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = (atomicAdd(bk.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    uint32_t over = 0;
+    for (uint32_t b = tid; b < bk.n_buckets; b += nt) {
+        const uint32_t c = *(volatile uint32_t*)&bk.cursor[b];
+        over |= c > bk.cap;
+        bk.bstart[b] = min(c, bk.cap);
+        bk.cursor[b] = 0;
+    }
+    if (over) atomicOr(a.err, ERR_BUCKET_OVERFLOW);
+    __syncthreads();
+    block_exclusive_scan(bk.bstart, bk.n_buckets, wt);
+    if (tid == 0) *bk.ticket = 0;
 }
 
 // ---------------------------------------------------------------------------
-// Large cells, pass 2: sort one bucket, locate it in the cell's order, pairs.
+// Large cells, pass 2: one warp per bucket -- sort it, locate it in the cell's
+// order, process its pairs.  Warps never wait for each other (no block barrier
+// after the table is staged), so the loads of one warp overlap the arithmetic
+// of the others.
 // ---------------------------------------------------------------------------
 struct FinishLayout {
-    uint32_t cap;
-    uint32_t o_e, o_srt, o_so, o_cnt, o_tmp, o_red, o_wt, o_tab, bytes;
+    uint32_t cap;          // records per bucket
+    uint32_t nsub_max;     // sub-bucket counters per warp
+    uint32_t warps;        // warps (buckets in flight) per CTA
+    uint32_t o_key, o_slot, o_off, o_cnt, o_tmp, o_srt, warp_bytes;   // per-warp region layout
+    uint32_t o_tab, bytes;
 };
 
-__host__ __device__ inline FinishLayout finish_layout(uint32_t cap)
+__host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max_smem)
 {
     FinishLayout L;
     L.cap = cap;
-    const uint32_t nsub_max = 1u << ceil_log2(cap > 2 ? cap : 2);   // >= cap
+    L.nsub_max = 1u << (ceil_log2(cap > 2 ? cap : 2) - 1);          // about two records per counter
     uint32_t o = 0;
-    L.o_e = o;   o = align_up(o + 8 * cap, 16);
-    L.o_srt = o; o = align_up(o + 8 * cap, 16);
-    L.o_so = o;  o = align_up(o + 4 * cap, 16);
-    L.o_cnt = o; o = align_up(o + 4 * (nsub_max + 1), 16);
+    L.o_key = o; o = align_up(o + 4 * cap, 16);
+    L.o_slot = o; o = align_up(o + 4 * cap, 16);
+    L.o_off = o; o = align_up(o + 2 * cap, 16);
+    L.o_cnt = o; o = align_up(o + 4 * (L.nsub_max + 1), 16);
     L.o_tmp = o; o = align_up(o + 2 * cap, 16);
-    L.o_red = o; o = align_up(o + 8 * 40, 16);
-    L.o_wt = o;  o = align_up(o + 4 * 40, 16);
-    L.o_tab = o; o = align_up(o + (uint32_t)sizeof(EffTab), 16);
-    L.bytes = o;
+    L.o_srt = o; o = align_up(o + 2 * cap, 16);
+    L.warp_bytes = o;
+    L.o_tab = 0;
+    const uint32_t tab = align_up((uint32_t)sizeof(EffTab), 16);
+    uint32_t w = (max_smem - tab) / L.warp_bytes;
+    w = w > 8 ? 8 : (w < 1 ? 1 : w);
+    L.warps = w;
+    L.bytes = tab + w * L.warp_bytes;
     return L;
 }
 
@@ -546,116 +619,164 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
-                                                         const uint32_t* __restrict__ bucket_big,
-                                                         const uint64_t* __restrict__ scratch,
-                                                         const uint32_t* __restrict__ cursor,
-                                                         uint32_t* __restrict__ cursor_next, FinishLayout L)
+// exclusive scan of a[0..n) by one warp; a[n] = total
+__device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uint32_t lane)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* e_s = (uint64_t*)(smem + L.o_e);
-    uint64_t* srt = (uint64_t*)(smem + L.o_srt);
-    uint32_t* so = (uint32_t*)(smem + L.o_so);
-    uint32_t* cnt = (uint32_t*)(smem + L.o_cnt);
-    uint16_t* tmp = (uint16_t*)(smem + L.o_tmp);
-    unsigned long long* red = (unsigned long long*)(smem + L.o_red);
-    uint32_t* wt = (uint32_t*)(smem + L.o_wt);
-    EffTab* tab = (EffTab*)(smem + L.o_tab);
-    __shared__ unsigned long long s_pre, s_tot, s_next;
-
-    const uint32_t g = blockIdx.x;
-    const BigCell C = cells[bucket_big[g]];
-    const uint32_t b = g - C.bucket_base, nb = 1u << C.nbits;
-    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-    const uint32_t cap = L.cap;
-    const uint32_t step = step_index(a);
-    LocalStats ls = {0, 0, 0, 0, 0};
-
-    if (tid == 0) { cursor_next[g] = 0; s_pre = 0; s_tot = 0; s_next = ~0ull; }
-    if (tid < 5) red[tid] = 0;
-    load_eff_tab(tab);
-    __syncthreads();
-    // where this bucket starts in the cell's sorted list, and the cell's live count
-    {
-        unsigned long long pre = 0, tot = 0;
-        for (uint32_t b2 = tid; b2 < nb; b2 += nt) {
-            const uint32_t c = min(cursor[C.bucket_base + b2], cap);
-            tot += c;
-            if (b2 < b) pre += c;
-        }
-        pre = warp_sum(pre);
-        tot = warp_sum(tot);
-        if (lane == 0) { atomicAdd(&s_pre, pre); atomicAdd(&s_tot, tot); }
+    const uint32_t per = (n + 31) >> 5;
+    const uint32_t b0 = min(n, lane * per), b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += a[i];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
     }
-    const uint32_t cnt_raw = cursor[g];
-    const uint32_t k = min(cnt_raw, cap);
-    for (uint32_t i = tid; i < k; i += nt) e_s[i] = scratch[(uint64_t)g * cap + i];
-    __syncthreads();
-    const uint32_t S = (uint32_t)s_pre, n = (uint32_t)s_tot;
+    uint32_t run = inc - s;
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t t = a[i];
+        a[i] = run;
+        run += t;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) a[n] = tot;
+    __syncwarp();
+}
 
-    // counting sort on the next key bits, then exact rank by the full (key, slot)
-    uint32_t sb = ceil_log2(k > 2 ? k : 2);
+__device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
+                                              const BigCell* __restrict__ cells,
+                                              const uint32_t* __restrict__ bucket_big,
+                                              const uint64_t* __restrict__ rec, const uint32_t* __restrict__ bstart,
+                                              const FinishLayout& L, unsigned char* ws, uint32_t g, uint32_t lane,
+                                              uint32_t step, LocalStats& ls)
+{
+    uint32_t* key = (uint32_t*)(ws + L.o_key);
+    uint32_t* slot = (uint32_t*)(ws + L.o_slot);
+    uint16_t* off = (uint16_t*)(ws + L.o_off);
+    uint32_t* cnt = (uint32_t*)(ws + L.o_cnt);
+    uint16_t* tmp = (uint16_t*)(ws + L.o_tmp);
+    uint16_t* srt = (uint16_t*)(ws + L.o_srt);
+    const uint32_t cap = L.cap;
+    const BigCell C = cells[bucket_big[g]];
+    const uint32_t nb = 1u << C.nbits;
+    // where this bucket starts in the cell's sorted list, its size, the cell's live count
+    const uint32_t b0 = bstart[C.bucket_base];
+    const uint32_t S = bstart[g] - b0;
+    const uint32_t k = bstart[g + 1] - bstart[g];
+    const uint32_t n = bstart[C.bucket_base + nb] - b0;
+    const uint64_t* R = rec + (uint64_t)g * 3 * cap;
+    for (uint32_t i = lane; i < k; i += 32) {
+        const uint64_t e = R[i];
+        key[i] = (uint32_t)(e >> 32);
+        slot[i] = (uint32_t)e;
+    }
+    // counting sort on the key bits below the bucket's, then exact rank by (key, slot)
+    uint32_t sb = ceil_log2(k > 2 ? k : 2) - 1;
     if (sb > 32u - C.nbits) sb = 32u - C.nbits;
     const uint32_t nsub = 1u << sb;
-    for (uint32_t s = tid; s < nsub; s += nt) cnt[s] = 0;
-    __syncthreads();
-    for (uint32_t i = tid; i < k; i += nt) {
-        const uint32_t key = (uint32_t)(e_s[i] >> 32);
-        const uint32_t sub = sb ? (key << C.nbits) >> (32u - sb) : 0u;
-        const uint32_t off = atomicAdd(&cnt[sub], 1u);
-        so[i] = (sub << 16) | off;
+    for (uint32_t t = lane; t <= nsub; t += 32) cnt[t] = 0;
+    __syncwarp();
+    const uint32_t sh = 32u - sb;
+    for (uint32_t i = lane; i < k; i += 32) {
+        const uint32_t sub = sb ? (key[i] << C.nbits) >> sh : 0u;
+        off[i] = (uint16_t)atomicAdd(&cnt[sub], 1u);
     }
-    __syncthreads();
-    block_exclusive_scan(cnt, nsub, wt);
-    for (uint32_t i = tid; i < k; i += nt) {
-        const uint32_t v = so[i];
-        tmp[cnt[v >> 16] + (v & 0xffffu)] = (uint16_t)i;
+    __syncwarp();
+    warp_exclusive_scan(cnt, nsub, lane);
+    for (uint32_t i = lane; i < k; i += 32) {
+        const uint32_t sub = sb ? (key[i] << C.nbits) >> sh : 0u;
+        tmp[cnt[sub] + off[i]] = (uint16_t)i;
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < k; i += nt) {
-        const uint32_t sub = so[i] >> 16;
+    __syncwarp();
+    for (uint32_t i = lane; i < k; i += 32) {
+        const uint32_t ki = key[i];
+        const uint32_t sub = sb ? (ki << C.nbits) >> sh : 0u;
         const uint32_t st = cnt[sub], en = cnt[sub + 1];
-        const uint64_t e = e_s[i];
         uint32_t r = 0;
-        for (uint32_t p = st; p < en; ++p) r += e_s[tmp[p]] < e;
-        srt[st + r] = e;
+        const uint32_t si = slot[i];
+        for (uint32_t p = st; p < en; ++p) {
+            const uint32_t o = tmp[p];
+            const uint32_t ko = key[o];
+            r += (ko < ki) || (ko == ki && slot[o] < si);     // equal keys: lower slot first
+        }
+        srt[st + r] = (uint16_t)i;
     }
     // the partner of this bucket's last SD may be the first SD of the next non-empty bucket
-    const bool need_next = ((S + k) & 1u) && (S + k < n);
-    if (need_next) {
-        __shared__ uint32_t s_nb;
-        if (tid == 0) {
-            uint32_t b2 = b + 1;
-            while (b2 < nb && cursor[C.bucket_base + b2] == 0) ++b2;
-            s_nb = b2;
-        }
-        __syncthreads();
-        const uint32_t b2 = s_nb;
+    unsigned long long nxt = ~0ull;
+    if (((S + k) & 1u) && (S + k < n)) {
+        uint32_t b2 = g - C.bucket_base + 1;
+        while (b2 < nb && bstart[C.bucket_base + b2 + 1] == bstart[C.bucket_base + b2]) ++b2;
         if (b2 < nb) {
             const uint32_t g2 = C.bucket_base + b2;
-            const uint32_t k2 = min(cursor[g2], cap);
-            unsigned long long mn = ~0ull;
-            for (uint32_t i = tid; i < k2; i += nt) {
-                const unsigned long long e = scratch[(uint64_t)g2 * cap + i];
-                mn = e < mn ? e : mn;
+            const uint32_t k2 = bstart[g2 + 1] - bstart[g2];
+            const uint64_t* R2 = rec + (uint64_t)g2 * 3 * cap;
+            for (uint32_t i = lane; i < k2; i += 32) {
+                const unsigned long long e = R2[i];
+                nxt = e < nxt ? e : nxt;
             }
-            mn = warp_min_u64(mn);
-            if (lane == 0) atomicMin(&s_next, mn);
+            nxt = warp_min_u64(nxt);
         }
     }
-    __syncthreads();
-    const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell],
-                        n >= 2 ? pair_ratio_dtdv_f(n, a.dt, a.dv[C.cell]) : 0.f, a.dv[C.cell]};
-    const uint64_t nxt = s_next;
-    for (uint32_t r = (S & 1u) + 2 * tid; r < k; r += 2 * nt) {
-        const uint32_t q = S + r;
-        if (q + 1 >= n) break;
-        const uint64_t e1 = srt[r];
-        const uint64_t e2 = (r + 1 < k) ? srt[r + 1] : nxt;
-        const uint64_t s1 = C.slot_begin + (uint32_t)e1, s2 = C.slot_begin + (uint32_t)e2;
-        process_pair(a, tab, cc, step, q >> 1, s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls);
+    __syncwarp();
+    if (k == 0 || n < 2) return;
+    const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell], pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]),
+                        a.dv[C.cell]};
+    // pairs m whose first SD (cell position 2m) lies in this bucket: 2m in [S, S+k), 2m+1 < n;
+    // each lane takes two consecutive pairs (one Philox call)
+    const uint32_t m_lo = (S + 1) >> 1;
+    const uint32_t m_hi = min((S + k - 1) >> 1, (n >> 1) - 1);      // inclusive
+    if (m_lo > m_hi) return;
+    for (uint32_t M = (m_lo >> 1) + lane; M <= (m_hi >> 1); M += 32) {
+        // gather both pairs' records first (one round trip), then the arithmetic
+        uint64_t sl[2][2], xg[2][2];
+        double vg[2][2];
+        bool ok[2];
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t m = 2 * M + h;
+            ok[h] = m >= m_lo && m <= m_hi;
+            const uint32_t r = ok[h] ? 2 * m - S : 0u;
+            const uint32_t i1 = srt[r];
+            const bool last = r + 1 >= k;              // partner is the first SD of the next bucket
+            const uint32_t i2 = last ? i1 : srt[r + 1];
+            sl[h][0] = C.slot_begin + slot[i1];
+            sl[h][1] = C.slot_begin + (last ? (uint32_t)nxt : slot[i2]);
+            xg[h][0] = R[cap + i1];
+            vg[h][0] = __longlong_as_double((long long)R[2 * cap + i1]);
+            if (ok[h] && last) {
+                xg[h][1] = a.xi[sl[h][1]];
+                vg[h][1] = a.attr[sl[h][1]];
+            } else {
+                xg[h][1] = R[cap + i2];
+                vg[h][1] = __longlong_as_double((long long)R[2 * cap + i2]);
+            }
+        }
+        uint64_t u[2];
+        phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h)
+            if (ok[h]) process_pair(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls);
     }
-    if (cnt_raw > cap && tid == 0) atomicOr(a.err, ERR_BUCKET_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                         const uint32_t* __restrict__ bucket_big,
+                                                         const uint64_t* __restrict__ rec,
+                                                         const uint32_t* __restrict__ bstart, uint32_t n_buckets,
+                                                         FinishLayout L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long red[8];
+    EffTab* tab = (EffTab*)(smem + L.o_tab);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
+    const uint32_t step = step_index(a);
+    LocalStats ls = {0, 0, 0, 0, 0};
+    load_eff_tab(tab);
+    if (tid < 5) red[tid] = 0;
+    __syncthreads();
+    for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
+        finish_bucket(a, tab, cells, bucket_big, rec, bstart, L, ws, g, lane, step, ls);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
@@ -723,7 +844,7 @@ __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* 
         const uint64_t xmax = xi1[i] > xi2[i] ? xi1[i] : xi2[i];
         const double K = kernel_d(kid, v1[i], v2[i], golovin_b);
         p64[i] = pair_prob_d(K, xmax, n_cell_sd, dt, dv);
-        const float scale32 = __ull2float_rn(xmax) * pair_ratio_dtdv_f(n_cell_sd, dt, dv);
+        const float scale32 = u64_to_f_trunc(xmax) * pair_ratio_dtdv_f(n_cell_sd, (float)dt, dv);
         const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b);
         p32[i] = pe.p;
         err32[i] = pe.err;

@@ -64,22 +64,34 @@ constexpr int EFF_NR = 12;
 constexpr int EFF_NQ = 11;
 
 // collector radius nodes [m] and efficiency values E[R][q], q = 0, 0.1, ..., 1
-__constant__ double c_eff_R[EFF_NR] = {
-    10e-6, 20e-6, 30e-6, 40e-6, 50e-6, 60e-6, 80e-6, 100e-6, 150e-6, 200e-6, 300e-6, 1000e-6};
-__constant__ double c_eff_E[EFF_NR * EFF_NQ] = {
-    0.000, 0.026, 0.050, 0.070, 0.088, 0.103, 0.116, 0.126, 0.132, 0.137, 0.138,
-    0.000, 0.074, 0.140, 0.199, 0.250, 0.293, 0.328, 0.355, 0.375, 0.386, 0.390,
-    0.000, 0.112, 0.212, 0.301, 0.378, 0.443, 0.496, 0.537, 0.567, 0.584, 0.590,
-    0.000, 0.137, 0.259, 0.367, 0.460, 0.539, 0.604, 0.654, 0.690, 0.712, 0.719,
-    0.000, 0.152, 0.288, 0.408, 0.512, 0.600, 0.672, 0.728, 0.768, 0.792, 0.800,
-    0.000, 0.162, 0.307, 0.435, 0.545, 0.639, 0.716, 0.775, 0.818, 0.844, 0.852,
-    0.000, 0.173, 0.328, 0.465, 0.583, 0.683, 0.765, 0.829, 0.875, 0.902, 0.911,
-    0.000, 0.179, 0.339, 0.480, 0.602, 0.706, 0.791, 0.856, 0.904, 0.932, 0.941,
-    0.000, 0.185, 0.350, 0.496, 0.623, 0.730, 0.817, 0.885, 0.934, 0.963, 0.973,
-    0.000, 0.187, 0.354, 0.502, 0.630, 0.738, 0.827, 0.896, 0.945, 0.975, 0.985,
-    0.000, 0.189, 0.358, 0.506, 0.636, 0.745, 0.834, 0.904, 0.953, 0.983, 0.993,
-    0.000, 0.190, 0.360, 0.510, 0.640, 0.750, 0.839, 0.909, 0.959, 0.989, 0.999,
-};
+#define SDM_EFF_RADII(X) X(10e-6) X(20e-6) X(30e-6) X(40e-6) X(50e-6) X(60e-6) X(80e-6) X(100e-6) X(150e-6) \
+    X(200e-6) X(300e-6) X(1000e-6)
+#define SDM_EFF_VALUES(X) \
+    X(0.000) X(0.026) X(0.050) X(0.070) X(0.088) X(0.103) X(0.116) X(0.126) X(0.132) X(0.137) X(0.138) \
+    X(0.000) X(0.074) X(0.140) X(0.199) X(0.250) X(0.293) X(0.328) X(0.355) X(0.375) X(0.386) X(0.390) \
+    X(0.000) X(0.112) X(0.212) X(0.301) X(0.378) X(0.443) X(0.496) X(0.537) X(0.567) X(0.584) X(0.590) \
+    X(0.000) X(0.137) X(0.259) X(0.367) X(0.460) X(0.539) X(0.604) X(0.654) X(0.690) X(0.712) X(0.719) \
+    X(0.000) X(0.152) X(0.288) X(0.408) X(0.512) X(0.600) X(0.672) X(0.728) X(0.768) X(0.792) X(0.800) \
+    X(0.000) X(0.162) X(0.307) X(0.435) X(0.545) X(0.639) X(0.716) X(0.775) X(0.818) X(0.844) X(0.852) \
+    X(0.000) X(0.173) X(0.328) X(0.465) X(0.583) X(0.683) X(0.765) X(0.829) X(0.875) X(0.902) X(0.911) \
+    X(0.000) X(0.179) X(0.339) X(0.480) X(0.602) X(0.706) X(0.791) X(0.856) X(0.904) X(0.932) X(0.941) \
+    X(0.000) X(0.185) X(0.350) X(0.496) X(0.623) X(0.730) X(0.817) X(0.885) X(0.934) X(0.963) X(0.973) \
+    X(0.000) X(0.187) X(0.354) X(0.502) X(0.630) X(0.738) X(0.827) X(0.896) X(0.945) X(0.975) X(0.985) \
+    X(0.000) X(0.189) X(0.358) X(0.506) X(0.636) X(0.745) X(0.834) X(0.904) X(0.953) X(0.983) X(0.993) \
+    X(0.000) X(0.190) X(0.360) X(0.510) X(0.640) X(0.750) X(0.839) X(0.909) X(0.959) X(0.989) X(0.999)
+#define SDM_AS_DOUBLE(v) v,
+#define SDM_AS_FLOAT(v) (float)(v),
+__constant__ double c_eff_R[EFF_NR] = {SDM_EFF_RADII(SDM_AS_DOUBLE)};
+__constant__ double c_eff_E[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
+// the same table rounded to float (the FP32 path stages it in shared memory)
+__constant__ float c_eff_Rf[EFF_NR] = {SDM_EFF_RADII(SDM_AS_FLOAT)};
+__constant__ float c_eff_Ef[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_FLOAT)};
+// 1 / (R[i+1] - R[i]) rounded to float (last entry unused)
+#define SDM_INV_DR(i) (float)(1.0 / (c_eff_R_h[(i) + 1] - c_eff_R_h[i]))
+constexpr double c_eff_R_h[EFF_NR] = {SDM_EFF_RADII(SDM_AS_DOUBLE)};
+__constant__ float c_eff_invdRf[EFF_NR] = {SDM_INV_DR(0), SDM_INV_DR(1), SDM_INV_DR(2), SDM_INV_DR(3), SDM_INV_DR(4),
+                                           SDM_INV_DR(5), SDM_INV_DR(6), SDM_INV_DR(7), SDM_INV_DR(8), SDM_INV_DR(9),
+                                           SDM_INV_DR(10), 0.f};
 
 
 // ---------------------------------------------------------------------------
@@ -202,24 +214,82 @@ __device__ __forceinline__ double kernel_d(uint32_t kid, double v1, double v2, d
     return kid == 0 ? kernel_golovin_d(v1, v2, golovin_b) : kernel_grav_d(v1, v2);
 }
 
+// The whole FP64 decision of one pair: kernel, eq. (p), gamma~.  Kept out of line so
+// that none of its (slow on B300) FP64 work is hoisted into the common path.
+__device__ __noinline__ uint64_t gamma_tilde_fp64_path(uint32_t kid, double v1, double v2, double golovin_b,
+                                                       uint32_t n, double dt, double dv, uint64_t u53,
+                                                       uint64_t xi_j, uint64_t xi_k)
+{
+    const double K = kernel_d(kid, v1, v2, golovin_b);
+    const double p = pair_prob_d(K, xi_j, n, dt, dv);
+    return gamma_tilde_d(p, u53, xi_j, xi_k);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 path with error bound
 // ---------------------------------------------------------------------------
+// Conversions to float are done with integer operations: on B300 the
+// double->float and 64-bit integer->float conversion instructions issue on the
+// (narrow) FP64 pipe.  Both helpers truncate the mantissa, so the result is
+// within 2^-23 relative of the input (exact when the input fits 24 bits).
+
+// |x| in [2^-126, 2^128): truncated float; smaller magnitudes give 0, larger +-inf.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - (1023 - 127);
+    const uint32_t sign = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+__device__ __forceinline__ float u64_to_f_trunc(uint64_t x)
+{
+    if (x == 0) return 0.f;
+    const int lz = __clzll((long long)x);
+    const uint64_t n = x << lz;                       // leading one at bit 63
+    return __uint_as_float(((uint32_t)(127 + 63 - lz) << 23) | ((uint32_t)(n >> 40) & 0x7fffffu));
+}
+
+// floor of a float >= 2^23 (such floats are integers), from its bits; saturates at
+// 2^64 - 1 (infinity and NaN included).
+__device__ __forceinline__ uint64_t f2u64_int(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    if (e >= 64 || (b >> 31)) return ~0ull;
+    const uint64_t m = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+    return e >= 23 ? m << (e - 23) : m >> (23 - e);
+}
+
+// phi = u53 * 2^-53 lies in [t, t + 2^-23) with t = (u53 >> 30) * 2^-23; t is built
+// exactly from bits as (1 + t) - 1.
+__device__ __forceinline__ void phi_bounds23(uint64_t u53, float& lo, float& hi)
+{
+    const uint32_t t23 = (uint32_t)(u53 >> 30);
+    lo = __uint_as_float(0x3F800000u | t23) - 1.0f;
+    hi = lo + 0x1p-23f;
+}
+
 struct P32 { float p; float err; };
 
-// Relative bound of the Golovin evaluation: about a dozen correctly rounded
-// FP32 steps (conversions of v, xi, dt, dV included) give |p32 - p| <= 13 u p
-// (u = 2^-24); 2^-17 = 128 u leaves a tenfold margin.
+// Relative bound of the Golovin evaluation: five truncating conversions
+// (v1, v2, xi, and the per-cell dt, dV: <= 2u each, u = 2^-24) and seven
+// rounded FP32 operations give |p32 - p| <= 18 u p; 2^-17 = 128 u leaves a
+// sevenfold margin.
 constexpr float GOLOVIN_REL_BOUND = 0x1p-17f;
 // Bound of the gravitational evaluation relative to
-// B = scale * pi (r1+r2)^2 (vt1 + vt2) >= p / E (E <= 1): cube root (<= 1 ulp),
-// regime choice near the continuous joins, the difference vt1 - vt2 (its
-// absolute error is bounded by the sum vt1 + vt2), and the position inside the
-// efficiency table (interpolation weights carry an absolute error of at most
-// ~250 u because the table nodes are >= 5 % apart) add up to < 400 u;
-// 2^-12 = 4096 u leaves a tenfold margin.
+// B = scale * pi (r1+r2)^2 (vt1 + vt2) >= p / E (E <= 1): volume conversion
+// and cube root (<= 4u on r), regime choice near the continuous joins, the
+// difference vt1 - vt2 (its absolute error is bounded by the sum vt1 + vt2),
+// and the position inside the efficiency table (interpolation weights carry an
+// absolute error of at most ~250 u because neighbouring radius nodes are
+// >= 1/7 apart relative to the radius) add up to < 400 u; 2^-12 = 4096 u
+// leaves a tenfold margin.
 constexpr float GRAV_REL_BOUND = 0x1p-12f;
 constexpr float ABS_SLACK = 0x1p-100f;   // covers gradual underflow of the last products
+constexpr float MIN_NORMAL_V = 0x1p-120f; // smaller float volumes are sent to the FP64 path
 
 __device__ __forceinline__ float vt_f(float r)
 {
@@ -242,11 +312,10 @@ struct EffTab {
 
 __device__ __forceinline__ void load_eff_tab(EffTab* T)
 {
-    for (int k = threadIdx.x; k < EFF_NR * EFF_NQ; k += blockDim.x) T->E[k] = (float)c_eff_E[k];
+    for (int k = threadIdx.x; k < EFF_NR * EFF_NQ; k += blockDim.x) T->E[k] = c_eff_Ef[k];
     if (threadIdx.x < EFF_NR) {
-        const int i = threadIdx.x;
-        T->R[i] = (float)c_eff_R[i];
-        T->inv_dR[i] = i + 1 < EFF_NR ? (float)(1.0 / (c_eff_R[i + 1] - c_eff_R[i])) : 0.f;
+        T->R[threadIdx.x] = c_eff_Rf[threadIdx.x];
+        T->inv_dR[threadIdx.x] = c_eff_invdRf[threadIdx.x];
     }
 }
 
@@ -263,22 +332,25 @@ __device__ __forceinline__ float efficiency_f(const EffTab* __restrict__ T, floa
         t = (R - T->R[i]) * T->inv_dR[i];
     }
     const float s = q * 10.f;
-    int j = (int)s;
+    const float sf = __fadd_rd(s, 0x1p23f);               // 2^23 + floor(s), exact for 0 <= s < 2^23
+    int j = (int)(__float_as_uint(sf) - 0x4B000000u);
     float w;
     if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.f; }
-    else w = s - (float)j;
+    else w = s - (sf - 0x1p23f);
     const float* E = T->E + i * EFF_NQ + j;
     const float e0 = E[0] + w * (E[1] - E[0]);
     const float e1 = E[EFF_NQ] + w * (E[EFF_NQ + 1] - E[EFF_NQ]);
     return e0 + t * (e1 - e0);
 }
 
-// scale32 = (float)max(xi) * S_c * (dt/dV) in FP32
+// p in FP32 with its bound.  scale32 = max(xi) * S_c * dt / dV in FP32.
+// A non-finite or NaN err marks the pair for the FP64 path.
 __device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_t kid, double v1d, double v2d,
                                            float scale32, float golovin_bf)
 {
-    const float v1 = __double2float_rn(v1d), v2 = __double2float_rn(v2d);
+    const float v1 = d2f_trunc(v1d), v2 = d2f_trunc(v2d);
     P32 o;
+    if (!(fminf(v1, v2) >= MIN_NORMAL_V)) { o.p = 0.f; o.err = __int_as_float(0x7fc00000); return o; }
     if (kid == 0) {
         const float K = golovin_bf * (v1 + v2);
         o.p = K * scale32;
@@ -304,47 +376,59 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
 {
     float lo = __fsub_rd(pe.p, pe.err);
     const float hi = __fadd_ru(pe.p, pe.err);
-    if (!(hi <= 0x1p62f) || !(lo == lo)) {
-        // huge or non-finite: only the cap can settle it
-        if (lo >= 0x1p62f) { *g = xi_j / xi_k; return true; }
-        return false;
-    }
-    lo = fmaxf(lo, 0.f);
-    const float fl_lo = floorf(lo), fl_hi = floorf(hi);
-    if (fl_lo != fl_hi) {
-        if (fl_lo >= 1.f) {
+    if (!(hi < 0x1p23f) || !(lo == lo)) {
+        // large, non-finite or NaN: only a binding cap can settle it here
+        if (lo >= 0x1p23f && lo == lo) {
             const uint64_t cap = xi_j / xi_k;
-            if ((uint64_t)fl_lo >= cap) { *g = cap; return true; }
+            if (f2u64_int(lo) >= cap) { *g = cap; return true; }   // floor(p) >= lo >= cap
         }
         return false;
     }
-    // floor(p) = fl_lo is certain; frac(p) lies in [lo - fl, hi - fl] (both exact)
-    const float f_lo = lo - fl_lo, f_hi = hi - fl_hi;
-    const uint32_t top = (uint32_t)(u53 >> 29);               // phi in [top, top+1) * 2^-24
-    const float phi_lo = (float)top * 0x1p-24f;
-    const float phi_hi = (float)(top + 1u) * 0x1p-24f;
-    uint64_t d;
+    lo = fmaxf(lo, 0.f);
+    // floors of lo and hi (both in [0, 2^23)) from the bits of x + 2^23 rounded down;
+    // no float<->int conversion instruction is used (on B300 they issue on the FP64 pipe)
+    const float tl = __fadd_rd(lo, 0x1p23f), th = __fadd_rd(hi, 0x1p23f);
+    const uint32_t m = __float_as_uint(tl) - 0x4B000000u;      // floor(lo)
+    if (tl != th) {
+        if (m >= 1u) {
+            const uint64_t cap = xi_j / xi_k;
+            if ((uint64_t)m >= cap) { *g = cap; return true; }
+        }
+        return false;
+    }
+    // floor(p) = m is certain; frac(p) lies in [lo - m, hi - m] (both exact)
+    const float fl = tl - 0x1p23f;
+    const float f_lo = lo - fl, f_hi = hi - fl;
+    float phi_lo, phi_hi;
+    phi_bounds23(u53, phi_lo, phi_hi);
+    uint32_t d;
     if (phi_hi <= f_lo) d = 1;          // phi < phi_hi <= frac
     else if (phi_lo >= f_hi) d = 0;     // phi >= phi_lo >= frac
     else return false;
-    const uint64_t gam = (uint64_t)fl_lo + d;
-    if (gam <= 1) { *g = gam; return true; }       // xi_j >= xi_k so the cap is >= 1
+    const uint32_t gam = m + d;
+    if (gam <= 1u) { *g = gam; return true; }      // xi_j >= xi_k so the cap is >= 1
     const uint64_t cap = xi_j / xi_k;
-    *g = gam < cap ? gam : cap;
+    *g = (uint64_t)gam < cap ? (uint64_t)gam : cap;
     return true;
 }
 
-// FP32 mode: gamma from p32 and the top 24 bits of phi.
+// FP32 mode: gamma from p32 and the leading 23 bits of phi.
 __device__ __forceinline__ uint64_t gamma_tilde_f(float p, uint64_t u53, uint64_t xi_j, uint64_t xi_k)
 {
-    if (!(p < 0x1p62f)) return xi_j / xi_k;
-    const float fl = floorf(p);
-    const float frac = p - fl;
-    const float phi = (float)(uint32_t)(u53 >> 29) * 0x1p-24f;
-    const uint64_t gam = (uint64_t)fl + (phi < frac ? 1ull : 0ull);
-    if (gam <= 1) return gam;
+    if (!(p < 0x1p23f)) {
+        const uint64_t cap = xi_j / xi_k;
+        const uint64_t gam = f2u64_int(p);          // floats >= 2^23 are integers
+        return gam < cap ? gam : cap;
+    }
+    const float t = __fadd_rd(p, 0x1p23f);
+    const uint32_t fl = __float_as_uint(t) - 0x4B000000u;
+    const float frac = p - (t - 0x1p23f);
+    float phi_lo, phi_hi;
+    phi_bounds23(u53, phi_lo, phi_hi);
+    const uint32_t gam = fl + (phi_lo < frac ? 1u : 0u);
+    if (gam <= 1u) return gam;
     const uint64_t cap = xi_j / xi_k;
-    return gam < cap ? gam : cap;
+    return (uint64_t)gam < cap ? (uint64_t)gam : cap;
 }
 
 }  // namespace sdm

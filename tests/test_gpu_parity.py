@@ -116,7 +116,7 @@ def test_schedule_invariance():
     ref = None
     for sched in (dict(tile_slots=256, tile_threads=64), dict(tile_slots=1024, tile_threads=256),
                   dict(tile_slots=4096, tile_threads=512, persistent=2), dict(tile_slots=4096, bucket_target=256),
-                  dict(tile_slots=512, bucket_target=4096, persistent=1)):
+                  dict(tile_slots=512, bucket_target=2048, persistent=1)):
         g = _gpu_state(mix, schedule=sched)
         g.step(1.0, 7, 0, 8)
         g.sync()
