@@ -28,6 +28,7 @@ _lib = None
 
 KERNEL_GOLOVIN = 0
 KERNEL_GRAVITATIONAL = 1
+SHUFFLE = {"sort": 0, "prp": 1}
 
 
 def build(force: bool = False) -> str:
@@ -89,10 +90,14 @@ def lib():
             L.sdmo_update_pair.restype = u64
             step_args = [u64, u32, _p(u32), _p(u64), _p(f64), u32, _p(f64), _p(C.c_uint8),
                          f64, f64, u64, u32]
-            L.sdmo_step.argtypes = step_args + [_p(Stats)]
+            L.sdmo_step.argtypes = step_args + [i32, _p(Stats)]
             L.sdmo_step.restype = i32
-            L.sdmo_run.argtypes = step_args + [u32, _p(Stats)]
+            L.sdmo_run.argtypes = step_args + [u32, i32, _p(Stats)]
             L.sdmo_run.restype = i32
+            L.sdmo_compact.argtypes = [u64, u32, _p(u32), _p(u64), _p(f64), u32]
+            L.sdmo_prp_keys.argtypes = [u64, u32, u32, _p(u32)]
+            L.sdmo_prp.argtypes = [u32, u32, _p(u32)]
+            L.sdmo_prp.restype = u32
             L.sdmo_spectrum.argtypes = [u64, u32, _p(u32), _p(u64), _p(f64), _p(f64), u32, u32,
                                         _p(f64), u32, f64, _p(f64)]
             L.sdmo_spectrum.restype = i32
@@ -172,6 +177,20 @@ def update_pair(xi, attr, first, second, p, phi_):
                                       attr.shape[1], first, second, float(p), float(phi_)))
 
 
+PRP_MIN_N = 257          # smaller cells are shuffled by sorting keys
+
+
+def prp_keys(seed, cell, step):
+    K = np.zeros(8, np.uint32)
+    lib().sdmo_prp_keys(int(seed), int(cell), int(step), _ptr(K, C.c_uint32))
+    return K
+
+
+def prp(q, n, K):
+    K = np.ascontiguousarray(K, np.uint32)
+    return int(lib().sdmo_prp(int(q), int(n), _ptr(K, C.c_uint32)))
+
+
 def i1e(x):
     return float(lib().sdmo_i1e(float(x)))
 
@@ -181,9 +200,13 @@ def golovin_phi(v, t, vbar, n0, b):
 
 
 class System:
-    """A slot-model SDM system held in numpy arrays, stepped by the oracle."""
+    """A slot-model SDM system held in numpy arrays, stepped by the oracle.
 
-    def __init__(self, xi, attr, cell_start, dv, kernel_id=None, golovin_b=1500.0):
+    The storage is kept compacted (each cell's live SDs first, in order), as
+    after every step; ``shuffle`` selects the Step 1 contract ("sort" or "prp").
+    """
+
+    def __init__(self, xi, attr, cell_start, dv, kernel_id=None, golovin_b=1500.0, shuffle="prp"):
         self.xi = np.ascontiguousarray(xi, dtype=np.uint64).copy()
         attr = np.asarray(attr, dtype=np.float64)
         if attr.ndim == 1:
@@ -197,7 +220,10 @@ class System:
         self.kernel_id = np.ascontiguousarray(
             np.broadcast_to(np.asarray(kernel_id, np.uint8), (self.n_cell,))).copy()
         self.golovin_b = float(golovin_b)
+        self.shuffle = shuffle
         assert self.attr.shape[1] == self.xi.shape[0]
+        lib().sdmo_compact(self.xi.shape[0], self.n_cell, _ptr(self.cell_start, C.c_uint32),
+                           _ptr(self.xi, C.c_uint64), _ptr(self.attr, C.c_double), self.attr.shape[0])
 
     @property
     def v(self):
@@ -210,14 +236,15 @@ class System:
 
     def step(self, dt, seed, step):
         st = Stats()
-        rc = lib().sdmo_step(*self._args(), float(dt), int(seed), int(step), C.byref(st))
+        rc = lib().sdmo_step(*self._args(), float(dt), int(seed), int(step), SHUFFLE[self.shuffle], C.byref(st))
         if rc:
             raise RuntimeError(f"sdmo_step failed: {rc}")
         return st.as_dict()
 
     def run(self, dt, seed, step0, n_steps):
         st = Stats()
-        rc = lib().sdmo_run(*self._args(), float(dt), int(seed), int(step0), int(n_steps), C.byref(st))
+        rc = lib().sdmo_run(*self._args(), float(dt), int(seed), int(step0), int(n_steps), SHUFFLE[self.shuffle],
+                            C.byref(st))
         if rc:
             raise RuntimeError(f"sdmo_run failed: {rc}")
         return st.as_dict()
@@ -242,4 +269,4 @@ class System:
         return out
 
     def copy(self):
-        return System(self.xi, self.attr, self.cell_start, self.dv, self.kernel_id, self.golovin_b)
+        return System(self.xi, self.attr, self.cell_start, self.dv, self.kernel_id, self.golovin_b, self.shuffle)

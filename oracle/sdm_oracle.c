@@ -37,20 +37,34 @@
  *                      (Abramowitz & Stegun 9.7.1).
  *
  * RNG contract (project-defined; the paper only says "random permutation" and
- * phi ~ U[0,1)):
+ * phi ~ U[0,1)).  i is the position of an SD in its cell's list L_c (the live
+ * SDs in slot order, Step 0), n = |L_c|:
  *   key = (seed & 0xffffffff, seed >> 32)
- *   shuffle key of the SD in local slot l of cell c at step s:
- *       philox(ctr = (l >> 2, c, s, 0))[l & 3]
  *   phi of candidate pair m of cell c at step s:
  *       x = philox(ctr = (m >> 1, c, s, 1)); w = 2 (m & 1)
  *       u53 = ((x[w] << 32) | x[w+1]) >> 11 ;  phi = u53 * 2^-53
- *   The list of a cell is sorted ascending by (key, l).
+ *   Two shuffles (Step 1) are defined; the shuffled list is L'_c:
+ *   SORT: shuffle key of position i = philox(ctr = (i >> 2, c, s, 0))[i & 3];
+ *         L'_c = L_c sorted ascending by (key, i)       (the paper's GPU way).
+ *   PRP:  cells with n <= 256 are shuffled exactly as by SORT; for n > 256,
+ *         L'_c[q] = L_c[P(q)] with P a keyed bijection of [0, n): an
+ *         eight-round alternating Feistel network on k = ceil(log2 n) bits
+ *         (left half floor(k/2) bits), round function lowbias32(v ^ K_r)
+ *         (C. Wellons' 32-bit integer hash), round keys K_0..K_3 =
+ *         philox(0, c, s, 2), K_4..K_7 = philox(1, c, s, 2), and
+ *         cycle-walking (apply the network again while the value is >= n) to
+ *         stay inside [0, n).  (Below ~256 elements a Feistel network of this
+ *         depth is measurably non-uniform; above, the pairings it produces
+ *         pass the uniformity tests.)
+ *   Pair m is (L'_c[2m], L'_c[2m+1]), m < floor(n/2).
  *
  * Slot model: SD storage is a fixed array of slots grouped by cell
  * (cell c owns slots [cell_start[c], cell_start[c+1])).  A slot with xi = 0 is
- * a removed SD; Step 0 (remove_if_equal_0) drops it from the cell's list.  The
- * local slot index l is the SD's identity for the RNG, so results never depend
- * on physical compaction.
+ * a removed SD.  After every step each cell is compacted stably: its live SDs
+ * move, in order, to the front of its slots and the freed slots are set to
+ * xi = 0 with all attributes 0 (the paper's Index shrink, Step 0 of the next
+ * step).  Positions in L_c, not slots, identify SDs for the RNG, so the
+ * results do not depend on this storage convention.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -109,6 +123,62 @@ uint32_t sdmo_shuffle_key(uint64_t seed, uint32_t cell, uint32_t step, uint32_t 
     ctr[0] = l >> 2; ctr[1] = cell; ctr[2] = step; ctr[3] = 0;
     sdmo_philox4x32_10(ctr, key, x);
     return x[l & 3];
+}
+
+/* lowbias32 (C. Wellons, "Prospecting for hash functions", 2018) */
+static uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+#define SDMO_PRP_ROUNDS 8
+#define SDMO_PRP_MIN_N 257   /* smaller cells are sorted by key */
+
+/* Round keys of the PRP shuffle of cell c at step s. */
+void sdmo_prp_keys(uint64_t seed, uint32_t cell, uint32_t step, uint32_t K[SDMO_PRP_ROUNDS])
+{
+    uint32_t key[2], ctr[4];
+    seed_key(seed, key);
+    ctr[0] = 0; ctr[1] = cell; ctr[2] = step; ctr[3] = 2;
+    sdmo_philox4x32_10(ctr, key, K);
+    ctr[0] = 1;
+    sdmo_philox4x32_10(ctr, key, K + 4);
+}
+
+static uint32_t ceil_log2_u32(uint32_t n)
+{
+    uint32_t k = 0;
+    while (k < 32 && (1ull << k) < (uint64_t)n) ++k;
+    return k;
+}
+
+/* One pass of the alternating Feistel network on k bits. */
+static uint32_t feistel(uint32_t q, uint32_t k, const uint32_t K[SDMO_PRP_ROUNDS])
+{
+    uint32_t a = k >> 1, b = k - a;
+    uint32_t mask_a = a ? (uint32_t)((1ull << a) - 1) : 0u;
+    uint32_t mask_b = (uint32_t)((1ull << b) - 1);
+    uint32_t L = b < 32 ? q >> b : 0u, R = q & mask_b;
+    int r;
+    for (r = 0; r < SDMO_PRP_ROUNDS; ++r) {
+        if ((r & 1) == 0) L ^= lowbias32(R ^ K[r]) & mask_a;
+        else R ^= lowbias32(L ^ K[r]) & mask_b;
+    }
+    return (b < 32 ? (L << b) : 0u) | R;
+}
+
+/* P(q): the keyed bijection of [0, n) (cycle-walking on [0, 2^k)). */
+uint32_t sdmo_prp(uint32_t q, uint32_t n, const uint32_t K[SDMO_PRP_ROUNDS])
+{
+    uint32_t k = ceil_log2_u32(n);
+    uint32_t e = feistel(q, k, K);
+    while (e >= n) e = feistel(e, k, K);
+    return e;
 }
 
 uint64_t sdmo_phi_u53(uint64_t seed, uint32_t cell, uint32_t step, uint32_t m)
@@ -367,15 +437,41 @@ typedef struct {
     uint64_t sum_gamma;      /* sum of gamma~ */
 } sdmo_stats;
 
-typedef struct { uint32_t key; uint32_t l; } key_rec;
+typedef struct { uint32_t key; uint32_t pos; uint32_t slot; } key_rec;
 
 static int cmp_key_rec(const void* a, const void* b)
 {
     const key_rec* x = (const key_rec*)a;
     const key_rec* y = (const key_rec*)b;
     if (x->key != y->key) return x->key < y->key ? -1 : 1;
-    if (x->l != y->l) return x->l < y->l ? -1 : 1;
+    if (x->pos != y->pos) return x->pos < y->pos ? -1 : 1;
     return 0;
+}
+
+#define SDMO_SHUFFLE_SORT 0
+#define SDMO_SHUFFLE_PRP 1
+
+/* Stable compaction of every cell: live SDs to the front in slot order, freed
+ * slots get xi = 0 and attributes 0. */
+void sdmo_compact(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start, uint64_t* xi, double* attr,
+                  uint32_t n_attr)
+{
+    uint32_t c, a;
+    for (c = 0; c < n_cell; ++c) {
+        uint64_t dst = cell_start[c], src;
+        for (src = cell_start[c]; src < cell_start[c + 1]; ++src) {
+            if (xi[src] == 0) continue;
+            if (dst != src) {
+                xi[dst] = xi[src];
+                for (a = 0; a < n_attr; ++a) attr[a * n_slots + dst] = attr[a * n_slots + src];
+            }
+            ++dst;
+        }
+        for (; dst < cell_start[c + 1]; ++dst) {
+            xi[dst] = 0;
+            for (a = 0; a < n_attr; ++a) attr[a * n_slots + dst] = 0.0;
+        }
+    }
 }
 
 /*
@@ -385,12 +481,13 @@ static int cmp_key_rec(const void* a, const void* b)
 int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
               uint64_t* xi, double* attr, uint32_t n_attr,
               const double* dv, const uint8_t* kernel_id, double golovin_b,
-              double dt, uint64_t seed, uint32_t step, sdmo_stats* stats)
+              double dt, uint64_t seed, uint32_t step, int shuffle, sdmo_stats* stats)
 {
     uint32_t c;
     sdmo_stats st = {0, 0, 0, 0};
     uint64_t max_cell = 0;
     key_rec* list;
+    uint64_t* order;
     double* pair_prob;
     for (c = 0; c < n_cell; ++c) {
         uint64_t w = cell_start[c + 1] - cell_start[c];
@@ -398,39 +495,48 @@ int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
         if (w > max_cell) max_cell = w;
     }
     if (cell_start[n_cell] > n_slots) return SDMO_EINVAL;
+    if (shuffle != SDMO_SHUFFLE_SORT && shuffle != SDMO_SHUFFLE_PRP) return SDMO_EINVAL;
     list = (key_rec*)malloc((max_cell + 1) * sizeof(key_rec));
+    order = (uint64_t*)malloc((max_cell + 1) * sizeof(uint64_t));
     pair_prob = (double*)malloc((max_cell / 2 + 1) * sizeof(double));
-    if (!list || !pair_prob) { free(list); free(pair_prob); return SDMO_ENOMEM; }
+    if (!list || !order || !pair_prob) { free(list); free(order); free(pair_prob); return SDMO_ENOMEM; }
 
     for (c = 0; c < n_cell; ++c) {
         uint64_t base = cell_start[c];
         uint32_t width = cell_start[c + 1] - cell_start[c];
-        uint32_t n = 0, l, m, npairs;
+        uint32_t n = 0, l, m, q, npairs;
         double scale;
-        /* step 0: remove_if_equal_0 -- the cell's list holds live SDs only */
+        /* step 0: remove_if_equal_0 -- the cell's list L_c holds live SDs only */
         for (l = 0; l < width; ++l)
-            if (xi[base + l] != 0) { list[n].l = l; ++n; }
+            if (xi[base + l] != 0) { list[n].pos = n; list[n].slot = l; ++n; }
         if (n < 2) continue;
-        /* step 1: urand + shuffle_per_cell (sort by random key) */
-        for (m = 0; m < n; ++m) list[m].key = sdmo_shuffle_key(seed, c, step, list[m].l);
-        qsort(list, n, sizeof(key_rec), cmp_key_rec);
-        /* flag_pairs: pair m = (list[2m], list[2m+1]) */
+        /* step 1: urand + shuffle_per_cell: the shuffled list as slot offsets */
+        if (shuffle == SDMO_SHUFFLE_SORT || n < SDMO_PRP_MIN_N) {
+            for (q = 0; q < n; ++q) list[q].key = sdmo_shuffle_key(seed, c, step, list[q].pos);
+            qsort(list, n, sizeof(key_rec), cmp_key_rec);
+            for (q = 0; q < n; ++q) order[q] = base + list[q].slot;
+        } else {
+            uint32_t K[SDMO_PRP_ROUNDS];
+            sdmo_prp_keys(seed, c, step, K);
+            for (q = 0; q < n; ++q) order[q] = base + list[sdmo_prp(q, n, K)].slot;
+        }
+        /* flag_pairs: pair m = (L'[2m], L'[2m+1]) */
         npairs = n / 2;
         /* step 2: coalescence_kernel, times_max, normalize */
         for (m = 0; m < npairs; ++m) {
-            double v1 = attr[base + list[2 * m].l];
-            double v2 = attr[base + list[2 * m + 1].l];
+            double v1 = attr[order[2 * m]];
+            double v2 = attr[order[2 * m + 1]];
             pair_prob[m] = sdmo_kernel(kernel_id ? kernel_id[c] : KERNEL_GOLOVIN, v1, v2, golovin_b);
         }
         scale = sdmo_pair_scale(n);
         for (m = 0; m < npairs; ++m) {
-            uint64_t a = xi[base + list[2 * m].l], b = xi[base + list[2 * m + 1].l];
+            uint64_t a = xi[order[2 * m]], b = xi[order[2 * m + 1]];
             pair_prob[m] = sdmo_pair_prob(pair_prob[m], a, b, scale, dt, dv[c]);
         }
         /* step 3: urand, compute_gamma, update_attributes */
         for (m = 0; m < npairs; ++m) {
             double phi = sdmo_phi(seed, c, step, m);
-            uint64_t j = base + list[2 * m].l, k = base + list[2 * m + 1].l;
+            uint64_t j = order[2 * m], k = order[2 * m + 1];
             uint64_t g = sdmo_update_pair(xi, attr, n_attr, n_slots, j, k, pair_prob[m], phi);
             st.n_pairs++;
             if (g) {
@@ -442,7 +548,10 @@ int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
         }
     }
     free(list);
+    free(order);
     free(pair_prob);
+    /* the removals take effect in the storage (Step 0 of the next step) */
+    sdmo_compact(n_slots, n_cell, cell_start, xi, attr, n_attr);
     if (stats) *stats = st;
     return SDMO_OK;
 }
@@ -451,13 +560,13 @@ int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
 int sdmo_run(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
              uint64_t* xi, double* attr, uint32_t n_attr,
              const double* dv, const uint8_t* kernel_id, double golovin_b,
-             double dt, uint64_t seed, uint32_t step0, uint32_t n_steps, sdmo_stats* total)
+             double dt, uint64_t seed, uint32_t step0, uint32_t n_steps, int shuffle, sdmo_stats* total)
 {
     uint32_t s;
     sdmo_stats acc = {0, 0, 0, 0}, st;
     for (s = 0; s < n_steps; ++s) {
         int rc = sdmo_step(n_slots, n_cell, cell_start, xi, attr, n_attr, dv, kernel_id,
-                           golovin_b, dt, seed, step0 + s, &st);
+                           golovin_b, dt, seed, step0 + s, shuffle, &st);
         if (rc) return rc;
         acc.n_pairs += st.n_pairs;
         acc.n_collisions += st.n_collisions;

@@ -23,16 +23,19 @@ import oracle
 from paper_2101_06318_b300 import inputs
 
 
-def _one_cell(xi, v, dv, kernel_id=0, b=1500.0):
+SHUFFLES = ["sort", "prp"]
+
+
+def _one_cell(xi, v, dv, kernel_id=0, b=1500.0, shuffle="prp"):
     n = len(xi)
-    return oracle.System(np.array(xi, np.uint64), np.array(v, np.float64), [0, n], dv, kernel_id, b)
+    return oracle.System(np.array(xi, np.uint64), np.array(v, np.float64), [0, n], dv, kernel_id, b, shuffle)
 
 
-def _pairing_after_one_step(n, seed, step):
+def _pairing_after_one_step(n, seed, step, shuffle):
     # equal xi = 2: every selected pair collides (p huge) with gamma~ = 1 and case 2,
     # so both partners end with v_i + v_partner; unpaired SDs are unchanged.
     v = np.array([(i + 1) * 1e-12 for i in range(n)])
-    s = _one_cell([2] * n, v, dv=1e-30)
+    s = _one_cell([2] * n, v, dv=1e-30, shuffle=shuffle)
     s.step(1.0, seed, step)
     pairs = set()
     for i in range(n):
@@ -43,10 +46,11 @@ def _pairing_after_one_step(n, seed, step):
     return tuple(sorted(pairs))
 
 
-@pytest.mark.parametrize("n,n_pairings", [(4, 3), (5, 15)])
-def test_pairing_is_uniform(n, n_pairings):
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+@pytest.mark.parametrize("n,n_pairings", [(4, 3), (5, 15), (6, 15)])   # small cells: both shuffles sort
+def test_pairing_is_uniform(n, n_pairings, shuffle):
     trials = 300 * n_pairings
-    cnt = Counter(_pairing_after_one_step(n, 1234, s) for s in range(trials))
+    cnt = Counter(_pairing_after_one_step(n, 1234, s, shuffle) for s in range(trials))
     assert len(cnt) == n_pairings
     for pairing in cnt:
         flat = [i for p in pairing for i in p]
@@ -55,7 +59,8 @@ def test_pairing_is_uniform(n, n_pairings):
     assert pval > 1e-4, (chi2, pval, cnt)
 
 
-def test_expected_coalescences_match_all_pairs_sum():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_expected_coalescences_match_all_pairs_sum(shuffle):
     rng = np.random.default_rng(11)
     n = 6
     xi = rng.integers(1000, 10 ** 6, n).astype(np.uint64)
@@ -67,7 +72,7 @@ def test_expected_coalescences_match_all_pairs_sum():
     dv = pmax / 0.5
     want = sum(b * (v[i] + v[j]) * float(xi[i]) * float(xi[j]) * dt / dv
                for i in range(n) for j in range(i + 1, n))
-    base = _one_cell(xi, v, dv, 0, b)
+    base = _one_cell(xi, v, dv, 0, b, shuffle)
     tot0 = int(base.xi.sum())
     trials = 40000
     d = np.empty(trials)
@@ -79,7 +84,8 @@ def test_expected_coalescences_match_all_pairs_sum():
     assert abs(mean - want) < 5 * sem, (mean, want, sem)
 
 
-def test_three_sd_cell_exact_distribution():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_three_sd_cell_exact_distribution(shuffle):
     xi = [9, 4, 6]
     v = [3e-14, 5e-14, 1e-14]
     b, dt, dv = 1500.0, 1.0, 1.3e-9
@@ -105,7 +111,7 @@ def test_three_sd_cell_exact_distribution():
     trials = 30000
     mc = Counter()
     for s in range(trials):
-        sys_ = _one_cell(xi, v, dv, 0, b)
+        sys_ = _one_cell(xi, v, dv, 0, b, shuffle)
         sys_.step(dt, 99, s)
         mc[(tuple(int(t) for t in sys_.xi), tuple(sys_.v))] += 1
     assert set(mc) <= set(exact)
@@ -142,9 +148,9 @@ def test_golovin_pdf_initial_condition_and_moments():
         assert mass == pytest.approx(vbar, rel=2e-3)
 
 
-def _golovin_run(seed, t_end):
+def _golovin_run(seed, t_end, shuffle):
     s = inputs.golovin_box()
-    sys_ = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    sys_ = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle)
     sys_.run(1.0, seed, 0, t_end)
     return sys_
 
@@ -167,8 +173,8 @@ def test_golovin_sdm_matches_analytic_spectrum_and_number():
     rc = np.sqrt(r_edges[1:] * r_edges[:-1])
     t = 3600
     specs, numbers = [], []
-    for seed in (42, 43):
-        sys_ = _golovin_run(seed, t)
+    for seed, shuffle in ((42, "prp"), (43, "sort")):
+        sys_ = _golovin_run(seed, t, shuffle)
         specs.append(sys_.spectrum(r_edges))
         numbers.append(sys_.totals()[0])
         assert sys_.totals()[2] == pytest.approx(
@@ -179,8 +185,57 @@ def test_golovin_sdm_matches_analytic_spectrum_and_number():
     sdm = _smooth_twice(np.mean(specs, axis=0))
     vc = 4 / 3 * math.pi * rc ** 3
     ana = np.array([3 * 1000.0 * x * x * n0 * oracle.golovin_phi(x, t, vbar, n0, b) for x in vc])
+    # tolerances from an ensemble of oracle runs (4 pairs of seeds): the median relative
+    # deviation over bins above 5 % of the peak was 0.045-0.10, the maximum over bins
+    # above 20 % of the peak 0.16-0.25 (the far tails are shot-noise dominated)
     sel = ana > 0.05 * ana.max()
     rel = np.abs(sdm[sel] - ana[sel]) / ana[sel]
-    assert np.median(rel) < 0.15 and rel.max() < 0.6, (np.median(rel), rel.max())
+    core = ana[sel] > 0.2 * ana.max()
+    assert np.median(rel) < 0.15 and rel[core].max() < 0.4, (np.median(rel), rel[core].max())
     # the peak sits in the same place
     assert abs(int(np.argmax(sdm)) - int(np.argmax(ana))) <= 4
+
+
+# --------------------------------------------------------------------------
+# the keyed bijection of the PRP shuffle
+# --------------------------------------------------------------------------
+
+def test_prp_is_a_bijection():
+    rng = np.random.default_rng(4)
+    for n in list(range(2, 70)) + [127, 128, 129, 1000, 4097]:
+        K = oracle.prp_keys(int(rng.integers(0, 2 ** 63)), int(rng.integers(0, 1000)), int(rng.integers(0, 1000)))
+        img = [oracle.prp(q, n, K) for q in range(n)]
+        assert sorted(img) == list(range(n)), n
+    # a large n, sampled: distinct and inside [0, n)
+    n = (1 << 20) + 12345
+    K = oracle.prp_keys(42, 0, 7)
+    qs = rng.choice(n, 20000, replace=False)
+    img = [oracle.prp(int(q), n, K) for q in qs]
+    assert len(set(img)) == len(img) and max(img) < n
+
+
+@pytest.mark.parametrize("n", [257, 300, 1024, 4097])
+def test_prp_pairs_look_like_a_uniform_random_matching(n):
+    """For a uniform random matching of n items the distance |i - j| of a pair follows
+    P(d) = 2 (n - d) / (n (n - 1)) and the partner of a fixed item is uniform over the
+    others; chi-square on integer-aligned bins of both."""
+    steps = max(200, 400000 // n)
+    dist = np.zeros(n, np.int64)
+    partner_of_0 = []
+    for step in range(steps):
+        K = oracle.prp_keys(7, 3, step)
+        img = [oracle.prp(q, n, K) for q in range(n)]
+        for m in range(n // 2):
+            dist[abs(img[2 * m] - img[2 * m + 1])] += 1
+        pos0 = img.index(0)
+        if pos0 ^ 1 < n:
+            partner_of_0.append(img[pos0 ^ 1])
+    d = np.arange(1, n)
+    pd = 2.0 * (n - d) / (n * (n - 1))
+    cut = np.r_[0, np.unique(np.searchsorted(np.cumsum(pd), np.linspace(0, 1, 31)[1:-1]))]
+    obs = np.add.reduceat(dist[1:], cut)
+    exp = np.add.reduceat(pd, cut)
+    exp = exp * obs.sum() / exp.sum()
+    assert stats.chisquare(obs, exp).pvalue > 1e-4
+    p0 = np.bincount(np.array(partner_of_0) * 16 // n, minlength=16)
+    assert stats.chisquare(p0).pvalue > 1e-4
