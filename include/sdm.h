@@ -26,19 +26,28 @@
  *    (row-major, attribute 0 is the particle volume v in m^3).
  *
  * Slot model.  Storage is a fixed array of slots grouped by cell: cell c owns
- * slots [cell_start[c], cell_start[c+1]).  A slot whose multiplicity is 0 is a
- * removed super-droplet (Sec. 2.2, "the j-th super-droplet is removed"); Step 0
- * excludes it from the cell's list every step.  The slot's index within its
- * cell is the super-droplet's identity for the random number contract, so the
- * results never depend on how or when storage is compacted.
+ * slots [cell_start[c], cell_start[c+1]).  The live super-droplets of a cell
+ * always occupy the first n_c of its slots, in list order; the other slots
+ * hold xi = 0 and attributes 0.  When a super-droplet is removed (Sec. 2.2,
+ * "the j-th super-droplet is removed") the cell is compacted stably at the end
+ * of the step, which is the paper's Step 0 (remove_if_equal_0) of the next
+ * step.  An SD's position in its cell's list is its identity for the random
+ * number contract.
  *
- * Random number contract (Philox4x32-10, Salmon et al. SC'11; key = seed):
- *   shuffle key of local slot l of cell c at step s = philox(l>>2, c, s, 0)[l&3]
- *   phi of candidate pair m of cell c at step s: x = philox(m>>1, c, s, 1),
+ * Random number contract (Philox4x32-10, Salmon et al. SC'11; key = seed).
+ * Position i in the list of cell c (n live SDs) at step s:
+ *   phi of candidate pair m: x = philox(m>>1, c, s, 1),
  *       u53 = ((x[2(m&1)] << 32) | x[2(m&1)+1]) >> 11, phi = u53 * 2^-53
- *   a cell's live SDs are ordered by (key, l) ascending; pair m is made of
- *   the SDs at positions 2m and 2m+1 of that order (Sec. 2.2 Step 1,
- *   Fig. "pair_flag").
+ *   Step 1 shuffle (sdm_shuffle), giving the shuffled list L':
+ *   SDM_SHUFFLE_SORT: key(i) = philox(i>>2, c, s, 0)[i&3]; L' = L ordered by
+ *       (key, i) ascending (the paper's GPU approach, Sec. 3.2).
+ *   SDM_SHUFFLE_PRP: cells with n <= 256 as SORT; larger cells L'[q] = L[P(q)]
+ *       with P the keyed bijection of [0, n) given by an eight-round
+ *       alternating Feistel network on ceil(log2 n) bits (left half the
+ *       smaller), round function lowbias32(v ^ K_r), round keys
+ *       K_0..3 = philox(0, c, s, 2), K_4..7 = philox(1, c, s, 2), and
+ *       cycle-walking into [0, n).  No sort and no data exchange is needed.
+ *   Pair m is (L'[2m], L'[2m+1]) (Sec. 2.2 Step 1, Fig. "pair_flag").
  */
 #ifndef SDM_H
 #define SDM_H
@@ -78,6 +87,12 @@ typedef enum {
     SDM_PREC_FP32 = 1
 } sdm_precision;
 
+/* Step 1 shuffle contract (see the random number contract above). */
+typedef enum {
+    SDM_SHUFFLE_PRP = 0,    /* keyed bijection for cells of more than 256 SDs (default) */
+    SDM_SHUFFLE_SORT = 1    /* sort by Philox key in every cell */
+} sdm_shuffle;
+
 typedef struct sdm_state sdm_state;   /* opaque, owned by the library */
 
 typedef struct {
@@ -86,6 +101,8 @@ typedef struct {
     uint64_t seed;             /* Philox key */
     uint32_t step;             /* index s of the first step enqueued by this call */
     uint32_t precision;        /* sdm_precision */
+    uint32_t shuffle;          /* sdm_shuffle */
+    uint32_t reserved;         /* must be 0 */
     /* Optional device pointer.  When non-NULL the step index is read from
      * *d_step on the device and incremented there after each step (the host
      * 'step' field is ignored), so a captured CUDA graph advances the random
@@ -132,7 +149,8 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t n_slots_cap, uint32_t n_cell, uin
                      void* cuda_stream, void* workspace, size_t ws_bytes);
 
 /* Load the initial super-droplet population (Sec. 3.1 state; Sec. 4 set-ups).
- *   xi[n_sd]          multiplicities (0 = removed slot, kept as storage)
+ *   xi[n_sd]          multiplicities (0 = removed slot; removed slots are moved
+ *                     behind the live ones of their cell)
  *   attr[n_attr][n_sd] extensive attributes, row-major, attr[0] = volume v > 0
  *   cell_id[n_sd]     cell of each SD (< n_cell); SDs are grouped by cell with a
  *                     stable counting sort, so slot order within a cell is the
@@ -154,8 +172,11 @@ sdm_status sdm_init_state_segmented(sdm_state* st, const uint64_t* xi, const dou
                                     const uint8_t* kernel_id, int ptrs_on_device);
 
 /* Overwrite xi and attr of an initialised state in its own slot layout
- * (checkpoint restore, or host-resident state streamed in).  Validates like
- * sdm_init_state.  Asynchronous for device pointers. */
+ * (checkpoint restore, or host-resident state streamed in, e.g. the arrays
+ * sdm_get_state returned).  The live SDs of every cell must come first (as
+ * sdm_get_state returns them).  Validated on the device like sdm_init_state
+ * plus that layout rule; a violation is reported by the next sdm_sync
+ * (SDM_EINVAL or SDM_ERANGE).  Asynchronous. */
 sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, int ptrs_on_device);
 
 /* Copy the state out in slot layout: xi[n_sd], attr[n_attr][n_sd] (either may
@@ -212,8 +233,9 @@ void sdm_free(sdm_state* st);
  * synchronises and reports, per kernel kind (0 = small-cell tile kernel,
  * 1 = large-cell scatter, 2 = large-cell finish), the number of launches and
  * their summed device time in ms since profiling was enabled.  Arrays have
- * SDM_N_KERNEL_KINDS entries.  Not for use inside CUDA graph capture. */
-#define SDM_N_KERNEL_KINDS 3
+ * SDM_N_KERNEL_KINDS entries (kind 3 = large-cell kernel of the PRP contract).
+ * Not for use inside CUDA graph capture. */
+#define SDM_N_KERNEL_KINDS 4
 sdm_status sdm_set_profiling(sdm_state* st, int enable);
 sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms);
 
@@ -257,8 +279,10 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
  *   dv, kernel_id               cell volume [m^3] and sdm_kernel_id
  *   params                      as for sdm_coalescence_step (d_step allowed)
  *   cuda_stream                 cudaStream_t the work is ordered on
- * Results are identical to sdm_coalescence_step on a one-cell state holding
- * the same arrays.  The call enqueues the step, then waits for the stream to
+ * The live SDs must come first in the arrays (as sdm_get_state returns them);
+ * removals compact them at the end of the step.  Results are identical to
+ * sdm_coalescence_step on a one-cell state holding the same arrays, for both
+ * shuffle contracts.  The call enqueues the step, then waits for the stream to
  * read the step's error word, and returns it (SDM_ECAPACITY on a bucket
  * overflow).  The first call on each device looks up the device address of
  * the fixed scratch array (once per device, under a lock); make that first

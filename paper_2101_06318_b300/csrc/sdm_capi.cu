@@ -58,6 +58,7 @@ struct sdm_state {
     unsigned long long* d_stats = nullptr;   // [5]
     unsigned long long* d_acc = nullptr;     // [4] totals scratch
     uint32_t* d_work = nullptr;              // [2] persistent tile counter
+    uint32_t* d_n_live = nullptr;            // [n_cell] live SDs per cell (a prefix of its slots)
 
     // schedule / layout
     sdm_schedule sched{};
@@ -74,6 +75,9 @@ struct sdm_state {
     uint32_t* d_bstart = nullptr;            // [n_buckets + 1] bucket offsets of the current step
     uint32_t* d_ticket = nullptr;            // [1] CTAs of the scatter pass that finished
     uint64_t* d_scratch = nullptr;
+    uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then [1] end-of-step ticket
+    BigWork* d_big_work = nullptr;           // PRP contract: candidate-pair ranges (work items)
+    uint32_t n_big_work = 0, prp_grid = 0;
     FinishLayout fin_L{};
     uint32_t fin_grid = 0, n_buckets_planned = 0;
 
@@ -88,8 +92,8 @@ struct sdm_state {
     struct Rec { int kind; cudaEvent_t e0, e1; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> ev_pool;
-    uint32_t prof_launches[SDM_N_KERNEL_KINDS] = {0, 0, 0};
-    double prof_ms[SDM_N_KERNEL_KINDS] = {0, 0, 0};
+    uint32_t prof_launches[SDM_N_KERNEL_KINDS] = {0, 0, 0, 0};
+    double prof_ms[SDM_N_KERNEL_KINDS] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -141,6 +145,7 @@ void free_layout(sdm_state* st)
     if (st->ws) st->ws_used = st->ws_fixed;
     st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
+    st->d_big_removed = nullptr; st->d_big_work = nullptr; st->n_big_work = 0;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
 }
 
@@ -182,6 +187,7 @@ sdm_status build_layout(sdm_state* st)
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
     std::vector<uint32_t> bucket_big;
+    std::vector<BigWork> work;
     TileDesc cur{0, 0, 0, 0};
     uint32_t cur_slots = 0;
     auto flush = [&]() {
@@ -214,6 +220,9 @@ sdm_status build_layout(sdm_state* st)
             max_nb = std::max(max_nb, nb);
             for (uint32_t l = 0; l < w; l += BIG_CHUNK)
                 chunks.push_back(BigChunk{(uint32_t)bigs.size(), l, std::min(w, l + BIG_CHUNK), 0});
+            const uint32_t pairs = std::max<uint32_t>(1, w / 2);   // candidate pairs at full occupancy
+            for (uint32_t m = 0; m < pairs; m += PRP_THREADS)
+                work.push_back(BigWork{(uint32_t)bigs.size(), m, std::min(pairs, m + PRP_THREADS), 0});
             bigs.push_back(b);
             continue;
         }
@@ -242,6 +251,17 @@ sdm_status build_layout(sdm_state* st)
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
     SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
+    SDM_TRY(upload(st, &st->d_big_work, work));
+    st->n_big_work = (uint32_t)work.size();
+    if (!work.empty()) {
+        int per_sm = 0;
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0));
+        st->prp_grid = std::max<uint32_t>(1, std::min<uint32_t>(st->n_big_work, (uint32_t)std::max(per_sm, 1) * st->n_sm));
+    }
+    if (!bigs.empty()) {
+        SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * (bigs.size() + 1), true));
+        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (bigs.size() + 1), st->stream));
+    }
     st->n_tiles = (uint32_t)tiles.size();
     st->n_big = (uint32_t)bigs.size();
     st->n_chunks = (uint32_t)chunks.size();
@@ -320,12 +340,29 @@ sdm_status to_host(std::vector<T>& h, const T* p, uint64_t n, int on_device, cud
     return SDM_OK;
 }
 
-sdm_status init_common(sdm_state* st, const uint64_t* xi, const double* attr, const std::vector<uint32_t>& cs,
+sdm_status init_common(sdm_state* st, const uint64_t* xi_in, const double* attr_in, const std::vector<uint32_t>& cs,
                        uint64_t n, const double* dv, const uint8_t* kid)
 {
-    SDM_TRY(validate_host(st, xi, attr, n));
+    SDM_TRY(validate_host(st, xi_in, attr_in, n));
+    // stable compaction of every cell: live SDs first, in input order; removed slots zeroed
+    std::vector<uint64_t> xi(n, 0);
+    std::vector<double> attr((size_t)n * st->n_attr, 0.0);
+    std::vector<uint32_t> n_live(st->n_cell, 0);
+    for (uint32_t c = 0; c < st->n_cell; ++c) {
+        uint64_t dst = cs[c];
+        for (uint64_t i = cs[c]; i < cs[c + 1]; ++i) {
+            if (xi_in[i] == 0) continue;
+            xi[dst] = xi_in[i];
+            for (uint32_t a = 0; a < st->n_attr; ++a) attr[(uint64_t)a * n + dst] = attr_in[(uint64_t)a * n + i];
+            ++dst;
+        }
+        n_live[c] = (uint32_t)(dst - cs[c]);
+    }
     SDM_TRY(set_cells(st, cs, dv, kid));
-    SDM_TRY(upload_slots(st, xi, attr, n));
+    SDM_TRY(upload_slots(st, xi.data(), attr.data(), n));
+    SDM_CUDA(cudaMemcpyAsync(st->d_n_live, n_live.data(), sizeof(uint32_t) * st->n_cell, cudaMemcpyHostToDevice,
+                             st->stream));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
     st->n_sd = n;
     SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
     SDM_TRY(build_layout(st));
@@ -333,19 +370,47 @@ sdm_status init_common(sdm_state* st, const uint64_t* xi, const double* attr, co
     return SDM_OK;
 }
 
+// largest c with cs[c] <= i
+__device__ uint32_t cell_of(const uint32_t* cs, uint32_t n_cell, uint64_t i)
+{
+    uint32_t lo = 0, hi = n_cell;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cs[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void validate_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ attr, uint64_t n,
-                                uint64_t stride, uint32_t n_attr, uint32_t* err)
+                                uint64_t stride, uint32_t n_attr, const uint32_t* __restrict__ cs, uint32_t n_cell,
+                                uint32_t* err)
 {
     uint32_t bad = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = xi[i];
         if (x >= XI_LIMIT) bad |= ERR_RANGE;
+        // live SDs must precede the removed slots of their cell
+        if (x != 0 && i > 0 && xi[i - 1] == 0 && cs[cell_of(cs, n_cell, i)] != i) bad |= ERR_INVALID;
         for (uint32_t a = 0; a < n_attr; ++a) {
             const double v = attr[(uint64_t)a * stride + i];
             if (!isfinite(v) || (a == 0 && x != 0 && !(v > 0.0))) bad |= ERR_INVALID;
         }
     }
     if (bad) atomicOr(err, bad);
+}
+
+// live count of every cell: the length of the live prefix of its slots
+__global__ void live_count_kernel(const uint64_t* __restrict__ xi, const uint32_t* __restrict__ cs, uint32_t n_cell,
+                                  uint32_t* n_live)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cell; c += gridDim.x * blockDim.x) {
+        uint64_t lo = cs[c], hi = cs[c + 1];          // first removed slot in [lo, hi]
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (xi[mid] != 0) lo = mid + 1; else hi = mid;
+        }
+        n_live[c] = (uint32_t)(lo - cs[c]);
+    }
 }
 
 sdm_status err_to_status(uint32_t e)
@@ -424,6 +489,8 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.d_step = p->d_step;
+    a.shuffle = p->shuffle;
+    a.n_live = st->d_n_live;
     a.stats = with_stats ? st->d_stats : nullptr;
     a.err = st->d_err;
     const sdm_schedule& S = st->sched;
@@ -441,7 +508,12 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             tile_step_kernel<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
                                                                                     st->tile_L, work);
         }
-        if (st->n_buckets) {
+        const BigBook bb{st->d_big_removed + st->n_big, st->d_big_removed, st->n_big};
+        if (st->n_big && p->shuffle == SDM_SHUFFLE_PRP) {
+            ProfScope ps(st, 3);
+            big_prp_kernel<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->d_big, st->d_big_work, st->n_big_work,
+                                                                         bb);
+        } else if (st->n_big) {
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
                 ProfScope ps(st, 1);
@@ -451,7 +523,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             {
                 ProfScope ps(st, 2);
                 big_finish_kernel<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->fin_L);
+                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->fin_L, bb);
             }
         }
         if (p->d_step) advance_step_kernel<<<1, 32, 0, st->stream>>>(p->d_step, 1u);
@@ -486,7 +558,8 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     size_t b = 0;
     b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256);
     b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
-    b += 4 * round256(512);
+    b += 4 * round256(512) + round256(4 * (size_t)n_cell + 256);
+    b += round256(sizeof(BigWork) * (cap / 2 / PRP_THREADS + n_cell + 1) + 256) + round256(4 * (size_t)n_cell + 260);
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
@@ -528,6 +601,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_stats, 64, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_acc, 64, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_work, 64, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_n_live, sizeof(uint32_t) * n_cell, false);
     if (s == SDM_OK && cudaMemsetAsync(st->d_err, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
     if (s == SDM_OK && cudaMemsetAsync(st->d_work, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
     if (s == SDM_OK && cudaMemsetAsync(st->d_xi, 0, sizeof(uint64_t) * cap, st->stream) != cudaSuccess) s = SDM_ECUDA;
@@ -613,9 +687,13 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
                                  st->stream));
     if (n) {
         const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 4 * (uint64_t)st->n_sm);
-        validate_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, n, st->cap, st->n_attr, st->d_err);
+        validate_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, n, st->cap, st->n_attr, st->d_cell_start,
+                                                      st->n_cell, st->d_err);
         SDM_CUDA(cudaGetLastError());
     }
+    const uint32_t cgrid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm));
+    live_count_kernel<<<cgrid, 256, 0, st->stream>>>(st->d_xi, st->d_cell_start, st->n_cell, st->d_n_live);
+    SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }
 
@@ -647,6 +725,7 @@ sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* p, uint32_
     if (!st->initialised) return SDM_EINVAL;
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return SDM_EINVAL;
     if (p->precision > SDM_PREC_FP32) return SDM_EINVAL;
+    if (p->shuffle > SDM_SHUFFLE_SORT || p->reserved != 0) return SDM_EINVAL;
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
     if (n_steps == 0) return SDM_OK;
     if (stats) SDM_CUDA(cudaMemsetAsync(st->d_stats, 0, 5 * sizeof(unsigned long long), st->stream));
@@ -881,7 +960,7 @@ sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms)
 sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n)
 {
     if (!st || !n) return SDM_EINVAL;
-    *n = (st->n_tiles ? 1u : 0u) + (st->n_buckets ? 2u : 0u);
+    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? 2u : 0u);   // PRP contract: 1 large-cell kernel
     return SDM_OK;
 }
 
@@ -910,13 +989,16 @@ constexpr uint32_t NA_TARGET_BITS = 8;                                    // 256
 constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 1024
 constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 576 records per bucket
 constexpr uint32_t NA_MAX_CHUNKS = (SDM_NOALLOC_MAX_SD + BIG_CHUNK - 1) / BIG_CHUNK;
+constexpr uint32_t NA_MAX_WORK = (SDM_NOALLOC_MAX_SD / 2 + PRP_THREADS - 1) / PRP_THREADS;
 // byte offsets inside the scratch array
 constexpr size_t NA_OFF_CELL = 0;        // BigCell
 constexpr size_t NA_OFF_DV = 64;         // double dv
 constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
 constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
+constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, removal flag, end-of-step ticket
 constexpr size_t NA_OFF_CHUNKS = 256;
-constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
+constexpr size_t NA_OFF_WORK = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
+constexpr size_t NA_OFF_BBIG = NA_OFF_WORK + sizeof(BigWork) * NA_MAX_WORK;
 constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
 constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
 constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
@@ -928,9 +1010,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
+uint32_t g_na_prp_grid[NA_MAX_DEVICES] = {};
 
 // device address of the scratch array on the current device (looked up once per device)
-sdm_status noalloc_scratch(unsigned char** out)
+sdm_status noalloc_scratch(unsigned char** out, uint32_t* prp_grid)
 {
     int dev = 0;
     SDM_CUDA(cudaGetDevice(&dev));
@@ -944,9 +1027,14 @@ sdm_status noalloc_scratch(unsigned char** out)
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * NA_MAX_BUCKETS;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
         SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
+        int n_sm = 0, per_sm = 0;
+        SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0));
+        g_na_prp_grid[dev] = (uint32_t)std::max(1, n_sm * std::max(per_sm, 1));
         g_na_ptr[dev] = (unsigned char*)p;
     }
     *out = g_na_ptr[dev];
+    *prp_grid = g_na_prp_grid[dev];
     return SDM_OK;
 }
 
@@ -961,13 +1049,15 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     if (n_sd > SDM_NOALLOC_MAX_SD) return SDM_ECAPACITY;
     if (kernel_id > SDM_KERNEL_GRAVITATIONAL || !(dv > 0.0) || !std::isfinite(dv)) return SDM_EINVAL;
     if (!(p->dt > 0.0) || !std::isfinite(p->dt) || p->precision > SDM_PREC_FP32) return SDM_EINVAL;
+    if (p->shuffle > SDM_SHUFFLE_SORT || p->reserved != 0) return SDM_EINVAL;
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
     if (n_sd < 2) return SDM_OK;
     unsigned char* base = nullptr;
-    SDM_TRY(noalloc_scratch(&base));
+    uint32_t prp_grid = 1;
+    SDM_TRY(noalloc_scratch(&base, &prp_grid));
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    // the same bucket geometry as the large-cell path with a 1024-SD bucket target
+    // the same geometry as the large-cell path with a 256-SD bucket target
     BigCell C{};
     C.cell = 0;
     C.slot_begin = 0;
@@ -979,18 +1069,27 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     BigChunk chunks[NA_MAX_CHUNKS];
     uint32_t n_chunks = 0;
     for (uint32_t l = 0; l < n_sd; l += BIG_CHUNK) chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), 0};
+    BigWork work[NA_MAX_WORK];
+    uint32_t n_work = 0;
+    const uint32_t pairs = n_sd / 2;
+    for (uint32_t m = 0; m < pairs; m += PRP_THREADS) work[n_work++] = BigWork{0, m, std::min(pairs, m + PRP_THREADS), 0};
     uint32_t bucket_big[NA_MAX_BUCKETS] = {};
     unsigned char head[256] = {};
     const uint8_t kid = (uint8_t)kernel_id;
+    const uint32_t cell_start[2] = {0, n_sd};
     std::memcpy(head + NA_OFF_CELL, &C, sizeof C);
     std::memcpy(head + NA_OFF_DV, &dv, sizeof dv);
     std::memcpy(head + NA_OFF_KID, &kid, 1);
+    std::memcpy(head + NA_OFF_LIVE, cell_start, sizeof cell_start);   // n_live, flag and ticket stay 0
 
-    // descriptors in; cursors and error word start at zero on every call
+    // descriptors in; cursors, tickets, flags and the error word start at zero on every call
     SDM_CUDA(cudaMemcpyAsync(base, head, sizeof head, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_CHUNKS, chunks, sizeof(BigChunk) * n_chunks, cudaMemcpyHostToDevice, stream));
+    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_WORK, work, sizeof(BigWork) * n_work, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_big, 4 * nb, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
+    uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4] ticket
+    live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
 
     StepArgs a{};
     a.xi = xi;
@@ -998,7 +1097,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.stride = attr_stride;
     a.n_attr = n_attr;
     a.precision = p->precision;
-    a.cell_start = nullptr;                       // not read by the large-cell kernels
+    a.cell_start = live;
     a.dv = (const double*)(base + NA_OFF_DV);
     a.kid = (const uint8_t*)(base + NA_OFF_KID);
     a.dt = p->dt;
@@ -1008,20 +1107,28 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.step = p->step;
+    a.shuffle = p->shuffle;
     a.d_step = p->d_step;
+    a.n_live = live + 2;
     a.stats = nullptr;
     a.err = (uint32_t*)(base + NA_OFF_ERR);
     const BigCell* d_cell = (const BigCell*)(base + NA_OFF_CELL);
-    uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
-    // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
-    const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
-    uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
-    const FinishLayout fl = finish_layout(cap, FINISH_SMEM);
-    const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
-    big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
-        a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
-    big_finish_kernel<<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
-        a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, fl);
+    const BigBook bb{live + 4, live + 3, 1};
+    if (p->shuffle == SDM_SHUFFLE_PRP) {
+        big_prp_kernel<<<std::min<uint32_t>(n_work, prp_grid), PRP_THREADS, 0, stream>>>(
+            a, d_cell, (const BigWork*)(base + NA_OFF_WORK), n_work, bb);
+    } else {
+        uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
+        // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
+        const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
+        uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
+        const FinishLayout fl = finish_layout(cap, FINISH_SMEM);
+        const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
+        big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
+            a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
+        big_finish_kernel<<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
+            a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, fl, bb);
+    }
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());
     uint32_t e = 0;

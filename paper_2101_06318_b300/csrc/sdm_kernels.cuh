@@ -32,6 +32,7 @@ enum : uint32_t {
 };
 
 constexpr uint32_t PREC_FP64 = 0, PREC_FP32 = 1;
+constexpr uint32_t SHUFFLE_PRP = 0, SHUFFLE_SORT = 1;
 constexpr uint32_t DEAD = 0xffffffffu;
 
 struct StepArgs {
@@ -49,10 +50,18 @@ struct StepArgs {
     float golovin_bf;
     uint32_t seed_lo, seed_hi;
     uint32_t step;              // used when d_step == nullptr
+    uint32_t shuffle;           // SHUFFLE_PRP or SHUFFLE_SORT
     const uint32_t* d_step;
+    uint32_t* n_live;           // [n_cell] live SDs per cell (a prefix of its slots)
     unsigned long long* stats;  // [5] or nullptr
     uint32_t* err;
 };
+
+// a cell is shuffled by sorting keys when it is small or the SORT contract is selected
+__device__ __forceinline__ bool sorts(const StepArgs& a, uint32_t n)
+{
+    return a.shuffle == SHUFFLE_SORT || n < PRP_MIN_N;
+}
 
 struct TileDesc { uint32_t slot_begin, slot_end, cell_begin, n_cells; };
 struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, pad; };
@@ -96,7 +105,7 @@ __device__ __forceinline__ void phi_pair_u53(const StepArgs& a, uint32_t cell, u
 // global memory.
 __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
                                              uint64_t u53, uint64_t g1, uint64_t g2, uint64_t x1, uint64_t x2,
-                                             double v1, double v2, LocalStats& ls)
+                                             double v1, double v2, LocalStats& ls, uint32_t* removed_flag)
 {
     const bool swap = x1 < x2;                 // j = first unless it has the smaller multiplicity
     const uint64_t xj = swap ? x2 : x1, xk = swap ? x1 : x2;
@@ -135,7 +144,10 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
             A[gj] = t;
             A[gk] = t;
         }
-        if (h == 0) ls.removed++;
+        if (h == 0) {
+            ls.removed++;
+            *removed_flag = 1u;     // the cell needs compaction after the step
+        }
     }
     ls.collisions++;
     ls.sum_gamma += g;
@@ -234,7 +246,8 @@ __host__ __device__ __forceinline__ uint32_t ceil_log2(uint32_t w)
 struct TileLayout {
     uint32_t tile_slots, max_cells;
     // byte offsets
-    uint32_t o_xi, o_v, o_key, o_bo, o_cnt, o_tmp, o_srt, o_cs, o_gb, o_bb, o_pb, o_ss, o_nb, o_ctx, o_red, o_wt, o_tab;
+    uint32_t o_xi, o_v, o_key, o_bo, o_cnt, o_tmp, o_srt, o_cs, o_gb, o_bb, o_pb, o_ss, o_nb, o_n, o_rem, o_pp, o_ctx, o_red,
+        o_wt, o_tab;
     uint32_t bytes;
 };
 
@@ -259,6 +272,9 @@ __host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t 
     L.o_pb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
     L.o_ss = o;  o = align_up(o + 4 * (max_cells + 1), 16);
     L.o_nb = o;  o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_n = o;   o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_rem = o; o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_pp = o;  o = align_up(o + 4 * (max_cells + 1), 16);
     L.o_ctx = o; o = align_up(o + (uint32_t)sizeof(CellCtx) * max_cells, 16);
     L.o_red = o; o = align_up(o + 8 * 8, 16);
     L.o_wt = o;  o = align_up(o + 4 * 40, 16);
@@ -288,6 +304,45 @@ __device__ __forceinline__ void warp0_exclusive_scan(uint32_t* a, uint32_t n)
     if (lane == 0) a[n] = carry;
 }
 
+// Stable compaction of one cell by one warp: the live SDs of slots
+// [base, base + n_old) move, in order, to the front; the freed slots get xi = 0
+// and attributes 0.  Attribute rows move first (liveness is read from xi, which
+// moves last); within a chunk of 32 every lane reads before any lane writes, and
+// a destination never lies after its source.  Returns the new live count.
+__device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t n_old, uint32_t lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t dst = 0;
+    for (uint32_t r = 0; r <= a.n_attr; ++r) {
+        dst = 0;
+        for (uint32_t off = 0; off < n_old; off += 32) {
+            const uint32_t i = off + lane;
+            const bool in = i < n_old;
+            const uint64_t x = in ? a.xi[base + i] : 0ull;
+            const bool live = x != 0;
+            const unsigned mask = __ballot_sync(0xffffffffu, live);
+            const uint32_t pos = dst + __popc(mask & lt);
+            if (r < a.n_attr) {
+                double* A = a.attr + (uint64_t)r * a.stride + base;
+                const double v = in ? A[i] : 0.0;
+                __syncwarp();
+                if (live) A[pos] = v;
+            } else {
+                __syncwarp();
+                if (live) a.xi[base + pos] = x;
+            }
+            dst += __popc(mask);
+            __syncwarp();
+        }
+    }
+    for (uint32_t i = dst + lane; i < n_old; i += 32) {
+        a.xi[base + i] = 0ull;
+        for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
+    }
+    __syncwarp();
+    return dst;
+}
+
 __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLayout& L, unsigned char* smem,
                              uint32_t step, LocalStats& ls)
 {
@@ -304,6 +359,9 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     uint32_t* pb = (uint32_t*)(smem + L.o_pb);
     uint32_t* ss = (uint32_t*)(smem + L.o_ss);
     uint32_t* nbit = (uint32_t*)(smem + L.o_nb);
+    uint32_t* ncl = (uint32_t*)(smem + L.o_n);
+    uint32_t* rem = (uint32_t*)(smem + L.o_rem);
+    uint32_t* pp = (uint32_t*)(smem + L.o_pp);
     CellCtx* ctx = (CellCtx*)(smem + L.o_ctx);
     uint32_t* wt = (uint32_t*)(smem + L.o_wt);
     const EffTab* tab = (const EffTab*)(smem + L.o_tab);
@@ -311,16 +369,22 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t ns = td.slot_end - td.slot_begin, nc = td.n_cells;
 
-    // per-cell geometry: slot start, groups of 4 slots, 2^nbits buckets
+    // per cell: slot offset, live count (the live SDs are the first n slots), and
+    // what Step 1 needs: key groups and buckets for sorted cells, the list length
+    // for PRP-shuffled cells
     for (uint32_t c = tid; c <= nc; c += nt) {
-        const uint32_t s0 = a.cell_start[td.cell_begin + c] - td.slot_begin;
-        cs[c] = s0;
+        cs[c] = a.cell_start[td.cell_begin + c] - td.slot_begin;
         if (c < nc) {
             const uint32_t w = a.cell_start[td.cell_begin + c + 1] - a.cell_start[td.cell_begin + c];
-            gb[c] = (w + 3) >> 2;
-            const uint32_t nb = ceil_log2(w);
+            const uint32_t n = min(a.n_live[td.cell_begin + c], w);
+            const bool srt_c = sorts(a, n);
+            ncl[c] = n;
+            rem[c] = 0;
+            const uint32_t nb = ceil_log2(n);
             nbit[c] = nb;
-            bb[c] = w ? 1u << nb : 0u;       // 2^ceil(log2 w) <= 2w buckets, none for an empty cell
+            gb[c] = srt_c ? (n + 3) >> 2 : 0u;
+            bb[c] = (srt_c && n) ? 1u << nb : 0u;      // 2^ceil(log2 n) <= 2n buckets
+            pp[c] = srt_c ? 0u : n;
         }
     }
     for (uint32_t i = tid; i < ns; i += nt) {
@@ -332,33 +396,32 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         warp0_exclusive_scan(gb, nc);
         __syncwarp();
         warp0_exclusive_scan(bb, nc);
+        __syncwarp();
+        warp0_exclusive_scan(pp, nc);
     }
     __syncthreads();
     const uint32_t G = gb[nc], NB = bb[nc];
     for (uint32_t b = tid; b < NB; b += nt) cnt[b] = 0;
+    for (uint32_t i = tid; i < ns; i += nt) bo_s[i] = DEAD;
     __syncthreads();
 
-    // Step 0 + Step 1: live SDs, Philox keys, bucket counts
+    // Step 1 for sorted cells: Philox keys of the list positions, bucket counts
     for (uint32_t g = tid; g < G; g += nt) {
         const uint32_t c = find_segment(gb, nc, g);
         const uint32_t grp = g - gb[c];
-        const uint32_t w = cs[c + 1] - cs[c];
+        const uint32_t n = ncl[c];
         const U4 x = philox(grp, td.cell_begin + c, step, 0u, a.seed_lo, a.seed_hi);
         const uint32_t nb = nbit[c];
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             const uint32_t l = 4 * grp + k;
-            if (l >= w) break;
+            if (l >= n) break;
             const uint32_t i = cs[c] + l;
-            if (xi_s[i] != 0) {
-                const uint32_t key = u4_word(x, k);
-                const uint32_t b = bb[c] + (nb ? key >> (32u - nb) : 0u);
-                const uint32_t off = atomicAdd(&cnt[b], 1u);
-                key_s[i] = key;
-                bo_s[i] = (b << 16) | off;
-            } else {
-                bo_s[i] = DEAD;
-            }
+            const uint32_t key = u4_word(x, k);
+            const uint32_t b = bb[c] + (nb ? key >> (32u - nb) : 0u);
+            const uint32_t off = atomicAdd(&cnt[b], 1u);
+            key_s[i] = key;
+            bo_s[i] = (b << 16) | off;
         }
     }
     __syncthreads();
@@ -368,7 +431,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         if (bo != DEAD) tmp[cnt[bo >> 16] + (bo & 0xffffu)] = (uint16_t)i;
     }
     __syncthreads();
-    // exact rank inside the bucket: order by (key, slot)
+    // exact rank inside the bucket: order by (key, list position)
     for (uint32_t i = tid; i < ns; i += nt) {
         const uint32_t bo = bo_s[i];
         if (bo == DEAD) continue;
@@ -383,11 +446,10 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         }
         srt[st + r] = (uint16_t)i;
     }
-    // per-cell live counts and pair counts
+    // where each cell's shuffled list starts in srt; per-cell constants of eq. (p)
     for (uint32_t c = tid; c < nc; c += nt) {
-        const uint32_t s0 = cnt[bb[c]], s1 = cnt[bb[c + 1]];
-        const uint32_t n = s1 - s0;
-        ss[c] = s0;
+        const uint32_t n = ncl[c];
+        ss[c] = sorts(a, n) ? cnt[bb[c]] : NB ? cnt[NB] + pp[c] : pp[c];
         const uint32_t gid = td.cell_begin + c;
         CellCtx cc;
         cc.gid = gid;
@@ -399,11 +461,19 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         pb[c] = (n >> 1) + 1u >> 1;              // groups of two pairs (one Philox call each)
     }
     __syncthreads();
+    // Step 1 for the larger cells under the PRP contract: L'[q] = L[P(q)]
+    for (uint32_t c = 0; c < nc; ++c) {
+        const uint32_t n = ncl[c];
+        if (sorts(a, n)) continue;
+        Prp P;
+        prp_init(P, a.seed_lo, a.seed_hi, td.cell_begin + c, step, n);
+        for (uint32_t q = tid; q < n; q += nt) srt[ss[c] + q] = (uint16_t)(cs[c] + prp_map(P, q));
+    }
     if (tid < 32) warp0_exclusive_scan(pb, nc);
     __syncthreads();
-    const uint32_t P = pb[nc];
+    const uint32_t P2 = pb[nc];
     // Steps 2-3 for every candidate pair of the tile, two consecutive pairs per thread
-    for (uint32_t t = tid; t < P; t += nt) {
+    for (uint32_t t = tid; t < P2; t += nt) {
         const uint32_t c = find_segment(pb, nc, t);
         const uint32_t M = t - pb[c];
         const CellCtx& cc = ctx[c];
@@ -415,8 +485,16 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             if (m >= (cc.n >> 1)) break;
             const uint32_t i1 = srt[ss[c] + 2 * m], i2 = srt[ss[c] + 2 * m + 1];
             process_pair(a, tab, cc, u[h], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2], v_s[i1],
-                         v_s[i2], ls);
+                         v_s[i2], ls, &rem[c]);
         }
+    }
+    __syncthreads();
+    // removals take effect in storage: compact the cells that lost SDs (rare)
+    const uint32_t warp = tid >> 5, nw = nt >> 5, lane = tid & 31;
+    for (uint32_t c = warp; c < nc; c += nw) {
+        if (!rem[c]) continue;
+        const uint32_t n_new = warp_compact_cell(a, td.slot_begin + cs[c], ncl[c], lane);
+        if (lane == 0) a.n_live[td.cell_begin + c] = n_new;
     }
 }
 
@@ -453,6 +531,175 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
         __syncthreads();
         flush_stats(a, ls, red);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Large cells: bookkeeping shared by their kernels and the end-of-step
+// compaction done by the last CTA of the step's final large-cell kernel.
+// ---------------------------------------------------------------------------
+struct BigBook {
+    uint32_t* ticket;      // CTAs of the current kernel that finished (reset by the last one)
+    uint32_t* removed;     // [n_big] an SD of this cell was removed during the step
+    uint32_t n_big;
+};
+
+// Stable compaction of one cell by the whole block (chunks of blockDim slots;
+// see warp_compact_cell).  wt needs 33 words of shared memory.
+__device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_t n_old, uint32_t* wt)
+{
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t dst = 0;
+    for (uint32_t r = 0; r <= a.n_attr; ++r) {
+        dst = 0;
+        for (uint32_t off = 0; off < n_old; off += nt) {
+            const uint32_t i = off + tid;
+            const bool in = i < n_old;
+            const uint64_t x = in ? a.xi[base + i] : 0ull;
+            const bool live = x != 0;
+            const unsigned mask = __ballot_sync(0xffffffffu, live);
+            if (lane == 0) wt[warp] = __popc(mask);
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t w = lane < nw ? wt[lane] : 0u;
+                uint32_t inc = w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= (uint32_t)o) inc += t;
+                }
+                if (lane < nw) wt[lane] = inc - w;
+                if (lane == 31) wt[32] = inc;
+            }
+            __syncthreads();
+            const uint32_t pos = dst + wt[warp] + __popc(mask & lt);
+            if (r < a.n_attr) {
+                double* A = a.attr + (uint64_t)r * a.stride + base;
+                const double v = in ? A[i] : 0.0;
+                __syncthreads();
+                if (live) A[pos] = v;
+            } else {
+                __syncthreads();
+                if (live) a.xi[base + pos] = x;
+            }
+            dst += wt[32];
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = dst + tid; i < n_old; i += nt) {
+        a.xi[base + i] = 0ull;
+        for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
+    }
+    __syncthreads();
+    return dst;
+}
+
+// Called by every CTA at its end: the last one compacts the large cells that
+// lost SDs in this step and resets the bookkeeping.
+__device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ cells, const BigBook& bk, uint32_t* wt)
+{
+    __shared__ uint32_t s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(bk.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (uint32_t b = 0; b < bk.n_big; ++b) {
+        if (!*(volatile uint32_t*)&bk.removed[b]) continue;
+        const BigCell C = cells[b];
+        const uint32_t n_old = min(*(volatile uint32_t*)&a.n_live[C.cell], C.width);
+        const uint32_t n_new = block_compact_cell(a, C.slot_begin, n_old, wt);
+        if (threadIdx.x == 0) {
+            a.n_live[C.cell] = n_new;
+            bk.removed[b] = 0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *bk.ticket = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Large cells under the PRP contract: a persistent grid walks work items of
+// PRP_THREADS candidate pairs; a thread maps its pair's two list positions
+// through the keyed bijection and gathers the two SDs directly (no sort, no
+// exchange, no atomics).  Per-CTA set-up (table, round keys) and the
+// end-of-step ticket are paid once per CTA, not once per item.
+// ---------------------------------------------------------------------------
+constexpr uint32_t PRP_THREADS = 256;
+struct BigWork { uint32_t big, m_begin, m_end, pad; };   // candidate pairs [m_begin, m_end) of one large cell
+
+__global__ void __launch_bounds__(PRP_THREADS, 3) big_prp_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                                const BigWork* __restrict__ work, uint32_t n_work,
+                                                                BigBook bk)
+{
+    __shared__ EffTab tab;
+    __shared__ Prp P;
+    __shared__ CellCtx s_cc;
+    __shared__ uint32_t wt[40];
+    __shared__ uint32_t key_s[PRP_MIN_N];
+    __shared__ uint16_t srt_s[PRP_MIN_N];
+    __shared__ unsigned long long red[8];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t step = step_index(a);
+    LocalStats ls = {0, 0, 0, 0, 0};
+    load_eff_tab(&tab);
+    if (tid < 5) red[tid] = 0;
+    uint32_t cur = 0xffffffffu;                 // large cell whose round keys are staged
+    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
+        const BigWork W = work[w];
+        const BigCell C = cells[W.big];
+        if (W.big != cur) {                     // uniform in the CTA
+            __syncthreads();
+            if (tid == 0) {
+                const uint32_t n = min(a.n_live[C.cell], C.width);
+                prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, n);
+                s_cc = CellCtx{C.cell, n, (uint32_t)a.kid[C.cell],
+                               n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]) : 0.f, a.dv[C.cell]};
+            }
+            __syncthreads();
+            cur = W.big;
+        }
+        const uint32_t n = s_cc.n;
+        const uint32_t npairs = n >> 1;
+        uint32_t* rflag = &bk.removed[W.big];
+        if (n >= PRP_MIN_N) {
+            const uint32_t m = W.m_begin + tid;
+            if (m < W.m_end && m < npairs) {
+                const uint64_t s1 = C.slot_begin + prp_map(P, 2 * m);
+                const uint64_t s2 = C.slot_begin + prp_map(P, 2 * m + 1);
+                const uint64_t x1 = a.xi[s1], x2 = a.xi[s2];
+                const double v1 = a.attr[s1], v2 = a.attr[s2];
+                const uint64_t u = phi_u53(a.seed_lo, a.seed_hi, C.cell, step, m);
+                process_pair(a, &tab, s_cc, u, s1, s2, x1, x2, v1, v2, ls, rflag);
+            }
+        } else if (n >= 2 && W.m_begin == 0) {
+            // few live SDs left in a large cell: sorted by key, all in the item holding pair 0
+            for (uint32_t t = tid; t < n; t += nt)
+                key_s[t] = u4_word(philox(t >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi), t & 3u);
+            __syncthreads();
+            for (uint32_t t = tid; t < n; t += nt) {
+                const uint32_t kt = key_s[t];
+                uint32_t r = 0;
+                for (uint32_t j = 0; j < n; ++j) r += (key_s[j] < kt) || (key_s[j] == kt && j < t);
+                srt_s[r] = (uint16_t)t;
+            }
+            __syncthreads();
+            for (uint32_t mm = tid; mm < npairs; mm += nt) {
+                const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
+                process_pair(a, &tab, s_cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
+                             a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
+            }
+            __syncthreads();
+        }
+    }
+    if (a.stats) {
+        __syncthreads();
+        flush_stats(a, ls, red);
+    }
+    big_end_of_step(a, cells, bk, wt);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,7 +895,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
                                               const uint32_t* __restrict__ bucket_big,
                                               const uint64_t* __restrict__ rec, const uint32_t* __restrict__ bstart,
                                               const FinishLayout& L, unsigned char* ws, uint32_t g, uint32_t lane,
-                                              uint32_t step, LocalStats& ls)
+                                              uint32_t step, LocalStats& ls, uint32_t* removed)
 {
     uint32_t* key = (uint32_t*)(ws + L.o_key);
     uint32_t* slot = (uint32_t*)(ws + L.o_slot);
@@ -657,7 +904,8 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     uint16_t* tmp = (uint16_t*)(ws + L.o_tmp);
     uint16_t* srt = (uint16_t*)(ws + L.o_srt);
     const uint32_t cap = L.cap;
-    const BigCell C = cells[bucket_big[g]];
+    const uint32_t big = bucket_big[g];
+    const BigCell C = cells[big];
     const uint32_t nb = 1u << C.nbits;
     // where this bucket starts in the cell's sorted list, its size, the cell's live count
     const uint32_t b0 = bstart[C.bucket_base];
@@ -755,7 +1003,9 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
         phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h)
-            if (ok[h]) process_pair(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls);
+            if (ok[h])
+                process_pair(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls,
+                             &removed[big]);
     }
 }
 
@@ -763,10 +1013,11 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
                                                          const uint32_t* __restrict__ bucket_big,
                                                          const uint64_t* __restrict__ rec,
                                                          const uint32_t* __restrict__ bstart, uint32_t n_buckets,
-                                                         FinishLayout L)
+                                                         FinishLayout L, BigBook bb)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long red[8];
+    __shared__ uint32_t wt[40];
     EffTab* tab = (EffTab*)(smem + L.o_tab);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
@@ -776,11 +1027,12 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
     if (tid < 5) red[tid] = 0;
     __syncthreads();
     for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
-        finish_bucket(a, tab, cells, bucket_big, rec, bstart, L, ws, g, lane, step, ls);
+        finish_bucket(a, tab, cells, bucket_big, rec, bstart, L, ws, g, lane, step, ls, bb.removed);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
     }
+    big_end_of_step(a, cells, bb, wt);
 }
 
 // ---------------------------------------------------------------------------

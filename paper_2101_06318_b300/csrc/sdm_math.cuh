@@ -53,6 +53,67 @@ __device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, 
 }
 
 // ---------------------------------------------------------------------------
+// PRP shuffle: a keyed bijection P of [0, n) for cells of more than 256 live
+// SDs -- an eight-round alternating Feistel network on k = ceil(log2 n) bits
+// (left half floor(k/2) bits) with round function lowbias32(v ^ K_r)
+// (C. Wellons' 32-bit integer hash), Philox round keys, and cycle-walking.
+// The shuffled list is L'[q] = L[P(q)]: the SDs of pair m are found directly,
+// with no sort and no data movement.
+// ---------------------------------------------------------------------------
+constexpr uint32_t PRP_ROUNDS = 8;
+constexpr uint32_t PRP_MIN_N = 257;      // smaller cells are shuffled by sorting keys
+
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+struct Prp {
+    uint32_t K[PRP_ROUNDS];
+    uint32_t n, b, mask_a, mask_b;
+};
+
+__device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
+                                         uint32_t n)
+{
+    const U4 x = philox(0u, cell, step, 2u, seed_lo, seed_hi);
+    const U4 y = philox(1u, cell, step, 2u, seed_lo, seed_hi);
+    P.K[0] = x.x; P.K[1] = x.y; P.K[2] = x.z; P.K[3] = x.w;
+    P.K[4] = y.x; P.K[5] = y.y; P.K[6] = y.z; P.K[7] = y.w;
+    uint32_t k = 0;
+    while (k < 32 && (1ull << k) < (uint64_t)n) ++k;
+    const uint32_t a = k >> 1;
+    P.n = n;
+    P.b = k - a;
+    P.mask_a = a ? (uint32_t)((1ull << a) - 1) : 0u;
+    P.mask_b = (uint32_t)((1ull << P.b) - 1);
+}
+
+__device__ __forceinline__ uint32_t feistel(const Prp& P, uint32_t q)
+{
+    uint32_t L = q >> P.b, R = q & P.mask_b;
+#pragma unroll
+    for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
+        L ^= lowbias32(R ^ P.K[r]) & P.mask_a;
+        R ^= lowbias32(L ^ P.K[r + 1]) & P.mask_b;
+    }
+    return (L << P.b) | R;
+}
+
+// P(q) for q < n (cycle-walking terminates: q's cycle contains q itself)
+__device__ __forceinline__ uint32_t prp_map(const Prp& P, uint32_t q)
+{
+    uint32_t e = feistel(P, q);
+    while (e >= P.n) e = feistel(P, e);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
 // Constants of the kernels (each written out here from the definitions).
 // ---------------------------------------------------------------------------
 constexpr double THREE_OVER_FOUR_PI = 0.238732414637843003;

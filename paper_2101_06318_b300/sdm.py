@@ -41,9 +41,13 @@ class SDMError(RuntimeError):
         super().__init__(f"{where}: {STATUS.get(code, code)}")
 
 
+SHUFFLE = {"prp": 0, "sort": 1}
+
+
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("golovin_b", C.c_double), ("seed", C.c_uint64), ("step", C.c_uint32),
-                ("precision", C.c_uint32), ("d_step", C.c_void_p)]
+                ("precision", C.c_uint32), ("shuffle", C.c_uint32), ("reserved", C.c_uint32),
+                ("d_step", C.c_void_p)]
 
 
 class StepStats(C.Structure):
@@ -216,8 +220,8 @@ class State:
 
     # -- the step ----------------------------------------------------------------
     def step(self, dt=1.0, seed=42, step=0, n_steps=1, precision="fp64", golovin_b=1500.0, d_step=None,
-             stats=False):
-        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision],
+             stats=False, shuffle="prp"):
+        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision], SHUFFLE[shuffle], 0,
                        None if d_step is None else d_step.data_ptr())
         st = StepStats()
         _check(self._L.sdm_coalescence_step(self._h, C.byref(p), int(n_steps), C.byref(st) if stats else None),
@@ -256,22 +260,22 @@ class State:
         s = Schedule(tile_slots, tile_threads, bucket_target, persistent)
         _check(self._L.sdm_set_schedule(self._h, C.byref(s)), "sdm_set_schedule")
 
-    def autotune(self, dt=1.0, seed=42, step=0, n_steps=3, precision="fp64", golovin_b=1500.0):
-        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision], None)
+    def autotune(self, dt=1.0, seed=42, step=0, n_steps=3, precision="fp64", golovin_b=1500.0, shuffle="prp"):
+        p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision], SHUFFLE[shuffle], 0, None)
         s = Schedule()
         _check(self._L.sdm_autotune(self._h, C.byref(p), int(n_steps), C.byref(s)), "sdm_autotune")
         return s.as_dict()
 
     # -- profiling ----------------------------------------------------------------
-    KERNEL_KINDS = ("tile_step_kernel", "big_scatter_kernel", "big_finish_kernel")
+    KERNEL_KINDS = ("tile_step_kernel", "big_scatter_kernel", "big_finish_kernel", "big_prp_kernel")
 
     def set_profiling(self, on=True):
         _check(self._L.sdm_set_profiling(self._h, int(bool(on))), "sdm_set_profiling")
 
     def profile(self):
         """{kernel name: (launches, total ms)} since profiling was enabled."""
-        n = (C.c_uint32 * 3)()
-        ms = (C.c_double * 3)()
+        n = (C.c_uint32 * 4)()
+        ms = (C.c_double * 4)()
         _check(self._L.sdm_get_profile(self._h, n, ms), "sdm_get_profile")
         return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 

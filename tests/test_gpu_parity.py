@@ -21,9 +21,12 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2101_06318_b300 import sdm  # noqa: E402
 
 
-def _oracle_system(s, attr=None):
+SHUFFLES = ["prp", "sort"]
+
+
+def _oracle_system(s, attr=None, shuffle="prp"):
     a = s["v"][None, :] if attr is None else attr
-    return oracle.System(s["xi"], a, s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    return oracle.System(s["xi"], a, s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle)
 
 
 def _gpu_state(s, attr=None, schedule=None):
@@ -36,11 +39,12 @@ def _gpu_state(s, attr=None, schedule=None):
     return st
 
 
-def _run_both(s, n_steps, seed=42, step0=0, attr=None, schedule=None, precision="fp64"):
-    o = _oracle_system(s, attr)
+def _run_both(s, n_steps, seed=42, step0=0, attr=None, schedule=None, precision="fp64", shuffle="prp"):
+    o = _oracle_system(s, attr, shuffle)
     ost = o.run(s["dt"], seed, step0, n_steps)
     g = _gpu_state(s, attr, schedule)
-    gst = g.step(s["dt"], seed, step0, n_steps, precision=precision, golovin_b=s["golovin_b"], stats=True)
+    gst = g.step(s["dt"], seed, step0, n_steps, precision=precision, golovin_b=s["golovin_b"], stats=True,
+                 shuffle=shuffle)
     g.sync()
     xi, at, cs = g.get_state()
     g.close()
@@ -53,34 +57,38 @@ def _assert_bitexact(o, xi, at):
         f"attr differs at {np.argwhere(o.attr != at)[:10]}"
 
 
-def test_golovin_box_bitexact_large_cell_path():
-    s = inputs.golovin_box()                   # one cell of 2^13 SDs -> bucketed large-cell path
-    o, ost, xi, at, gst = _run_both(s, 300)
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_golovin_box_bitexact_large_cell_path(shuffle):
+    s = inputs.golovin_box()                   # one cell of 2^13 SDs -> large-cell path
+    o, ost, xi, at, gst = _run_both(s, 300, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
     for k in ("n_pairs", "n_collisions", "n_removed", "sum_gamma"):
         assert ost[k] == gst[k], k
     assert gst["n_collisions"] > 1000
 
 
-def test_golovin_box_bitexact_tile_path():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_golovin_box_bitexact_tile_path(shuffle):
     s = inputs.golovin_box(n_sd=4096)          # the whole cell handled in shared memory
-    o, ost, xi, at, gst = _run_both(s, 300, schedule=dict(tile_slots=4096, tile_threads=512))
+    o, ost, xi, at, gst = _run_both(s, 300, schedule=dict(tile_slots=4096, tile_threads=512), shuffle=shuffle)
     _assert_bitexact(o, xi, at)
     assert ost["n_collisions"] == gst["n_collisions"]
 
 
+@pytest.mark.parametrize("shuffle", SHUFFLES)
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_random_cells_bitexact(seed):
+def test_random_cells_bitexact(seed, shuffle):
     # irregular cells (Poisson sizes incl. empty and 1-SD cells), dead slots, both kernels,
-    # log-uniform xi so that case 2 and removals occur
+    # log-uniform xi so that case 2 and removals (and so compaction) occur
     s = inputs.random_cells(n_cell=700, mean_per_cell=23, seed=seed, dead_fraction=0.05, xi_max=50, dv=1e-12)
-    o, ost, xi, at, gst = _run_both(s, 25, seed=seed)
+    o, ost, xi, at, gst = _run_both(s, 25, seed=seed, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
     assert ost == {k: gst[k] for k in ost}
     assert gst["n_removed"] > 0 and gst["n_collisions"] > 100
 
 
-def test_big_cells_many_buckets_bitexact():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_big_cells_many_buckets_bitexact(shuffle):
     rng = np.random.default_rng(5)
     parts = []
     for n in (1025, 3000, 4096, 9001, 20000, 2, 1, 0, 777):
@@ -90,21 +98,40 @@ def test_big_cells_many_buckets_bitexact():
     xi = np.maximum(1, np.floor(np.exp(rng.random(n) * math.log(10 ** 6)))).astype(np.uint64)
     v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
     s = inputs._state(xi, v, counts, 10.0, (np.arange(len(counts)) % 2).astype(np.uint8), "big_mix")
-    o, ost, xi_g, at, gst = _run_both(s, 12, schedule=dict(tile_slots=1024, bucket_target=256))
+    o, ost, xi_g, at, gst = _run_both(s, 12, schedule=dict(tile_slots=1024, bucket_target=256), shuffle=shuffle)
     _assert_bitexact(o, xi_g, at)
     assert gst["n_collisions"] > 0
 
 
-def test_multiple_attributes_bitexact():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_large_cells_with_removals_bitexact(shuffle):
+    # small multiplicities and tiny dV: removals every step inside large cells, so the
+    # end-of-step compaction of large cells runs, down to fewer than 257 live SDs
+    rng = np.random.default_rng(8)
+    counts = np.array([3000, 1500, 700])
+    n = int(counts.sum())
+    xi = rng.integers(1, 4, n).astype(np.uint64)
+    v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
+    s = inputs._state(xi, v, counts, 1e-14, [0, 1, 0], "removals")
+    o, ost, xi_g, at, gst = _run_both(s, 40, schedule=dict(tile_slots=512), shuffle=shuffle)
+    _assert_bitexact(o, xi_g, at)
+    assert gst["n_removed"] > 500
+    live = [int(np.count_nonzero(xi_g[a:b])) for a, b in zip(s["cell_start"][:-1], s["cell_start"][1:])]
+    assert min(live) < 257
+
+
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_multiple_attributes_bitexact(shuffle):
     s = inputs.random_cells(n_cell=200, mean_per_cell=30, seed=9, xi_max=1000, dv=1e-11)
     n = len(s["xi"])
     rng = np.random.default_rng(1)
     attr = np.vstack([s["v"], rng.random(n), rng.random(n) * 1e-20]).astype(np.float64)
-    o, ost, xi, at, gst = _run_both(s, 10, attr=attr)
+    o, ost, xi, at, gst = _run_both(s, 10, attr=attr, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
 
 
-def test_schedule_invariance():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_schedule_invariance(shuffle):
     s = inputs.random_cells(n_cell=400, mean_per_cell=60, seed=4, xi_max=10 ** 4, dv=1e-2)
     big = inputs.golovin_box(n_sd=5000)
     # append one larger cell so both paths run in the same step
@@ -118,38 +145,41 @@ def test_schedule_invariance():
                   dict(tile_slots=4096, tile_threads=512, persistent=2), dict(tile_slots=4096, bucket_target=256),
                   dict(tile_slots=512, bucket_target=2048, persistent=1)):
         g = _gpu_state(mix, schedule=sched)
-        g.step(1.0, 7, 0, 8)
+        g.step(1.0, 7, 0, 8, shuffle=shuffle)
         g.sync()
         got = g.get_state()
         g.close()
         if ref is None:
             ref = got
-            o = _oracle_system(mix)
+            o = _oracle_system(mix, shuffle=shuffle)
             o.run(1.0, 7, 0, 8)
             _assert_bitexact(o, got[0], got[1])
         else:
             assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]), sched
 
 
-def test_gravitational_box_full_size_bitexact():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_gravitational_box_full_size_bitexact(shuffle):
     """The benchmarked workload (2^20 SDs in one cell) at full size, a few steps."""
     s = inputs.gravitational_box()
-    o, ost, xi, at, gst = _run_both(s, 3, seed=42)
+    o, ost, xi, at, gst = _run_both(s, 3, seed=42, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
     assert ost["n_collisions"] == gst["n_collisions"] > 1000
     # most decisions are settled from the FP32 bound
     assert gst["n_fp64"] < 1e-3 * gst["n_pairs"]
 
 
-def test_grid_bimodal_sample_bitexact():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_grid_bimodal_sample_bitexact(shuffle):
     s = inputs.grid_bimodal(nx=32, ny=32)      # the 2D-grid workload on a 32 x 32 patch
-    o, ost, xi, at, gst = _run_both(s, 10)
+    o, ost, xi, at, gst = _run_both(s, 10, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
 
 
-def test_ensemble_sample_bitexact():
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_ensemble_sample_bitexact(shuffle):
     s = inputs.ensemble(n_members=24)
-    o, ost, xi, at, gst = _run_both(s, 4)
+    o, ost, xi, at, gst = _run_both(s, 4, shuffle=shuffle)
     _assert_bitexact(o, xi, at)
 
 
@@ -326,6 +356,15 @@ def test_invalid_inputs_raise():
         g.sync()
     assert e.value.code == 4
     g.sync()   # the error word was cleared
+    # a live SD behind a removed slot of the same cell breaks the layout rule of set_state
+    cs = s["cell_start"]
+    c = int(np.flatnonzero(np.diff(cs.astype(np.int64)) >= 2)[0])
+    xg = s["xi"].copy()
+    xg[cs[c]] = 0
+    g.set_state(xg, s["v"][None].copy())
+    with pytest.raises(sdm.SDMError) as e:
+        g.sync()
+    assert e.value.code == 1
 
 
 def test_device_pointer_init_and_workspace():

@@ -30,9 +30,10 @@ def _box(n, kernel, seed):
     return inputs.gravitational_box(n_sd=n, seed=seed, dv=1e6)
 
 
-@pytest.mark.parametrize("n,kernel,precision", [(200000, 1, "fp64"), (5000, 0, "fp64"), (3, 0, "fp64"),
-                                                (70000, 1, "fp32")])
-def test_noalloc_matches_allocating_path_two_calls(n, kernel, precision):
+@pytest.mark.parametrize("n,kernel,precision,shuffle", [(200000, 1, "fp64", "prp"), (200000, 1, "fp64", "sort"),
+                                                        (5000, 0, "fp64", "prp"), (3, 0, "fp64", "sort"),
+                                                        (70000, 1, "fp32", "prp")])
+def test_noalloc_matches_allocating_path_two_calls(n, kernel, precision, shuffle):
     L = sdm.lib()
     s = _box(n, kernel, seed=n)
     dv = float(s["dv"][0])
@@ -45,8 +46,8 @@ def test_noalloc_matches_allocating_path_two_calls(n, kernel, precision):
     at_d[0, :n] = torch.from_numpy(s["v"]).cuda()
     stream = torch.cuda.current_stream().cuda_stream
     for step in (0, 1):
-        ref.step(s["dt"], 42, step, 1, precision=precision, golovin_b=s["golovin_b"])
-        p = sdm.StepParams(s["dt"], s["golovin_b"], 42, step, sdm.PREC[precision], None)
+        ref.step(s["dt"], 42, step, 1, precision=precision, golovin_b=s["golovin_b"], shuffle=shuffle)
+        p = sdm.StepParams(s["dt"], s["golovin_b"], 42, step, sdm.PREC[precision], sdm.SHUFFLE[shuffle], 0, None)
         rc = L.sdm_coalescence_step_noalloc(C.c_void_p(xi_d.data_ptr()), C.c_void_p(at_d.data_ptr()), 1, stride, n,
                                             dv, kernel, C.byref(p), C.c_void_p(stream))
         assert rc == 0, sdm.STATUS.get(rc, rc)
@@ -64,7 +65,7 @@ def test_noalloc_rejects_oversized_box():
     n = (1 << 18) + 1
     xi_d = torch.ones(n, dtype=torch.int64, device="cuda")
     at_d = torch.full((1, n), 1e-15, dtype=torch.float64, device="cuda")
-    p = sdm.StepParams(1.0, 1500.0, 1, 0, 0, None)
+    p = sdm.StepParams(1.0, 1500.0, 1, 0, 0, 0, 0, None)
     rc = L.sdm_coalescence_step_noalloc(C.c_void_p(xi_d.data_ptr()), C.c_void_p(at_d.data_ptr()), 1, n, n, 1.0, 0,
                                         C.byref(p), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 3   # SDM_ECAPACITY
