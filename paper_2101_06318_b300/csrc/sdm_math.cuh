@@ -159,28 +159,44 @@ __constant__ float c_eff_invdRf[EFF_NR] = {SDM_INV_DR(0), SDM_INV_DR(1), SDM_INV
 // FP64 path (documented operation order, no contraction)
 // ---------------------------------------------------------------------------
 
-// Cube root by +, *, / only: x = m 2^(3q), m in [0.5, 4); y0 = 0.2 m + 0.74;
-// five Newton steps y <- (2y + m/y^2)/3; result y 2^q.  Positive normal x.
+// Cube root from + and * only: x = m 2^e, m in [0.5, 1), e = 3q + rmd; seed
+// y = ((0.456419 m - 1.19161) m + 1.73758) 2^(-rmd/3) ~ m^(-1/3); M = m 2^rmd;
+// three Newton steps y <- y + y (1 - M y^3)/3; c = (M y) y; one residual
+// correction c <- c - (c^3 - M) y^2/3; result c 2^q.  Positive normal x.
 __device__ __forceinline__ double cbrt_d(double x)
 {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
     const int e = (int)((u >> 52) & 0x7ff) - 1022;
-    double m = __longlong_as_double((long long)((u & 0x800fffffffffffffull) | (1022ull << 52)));
+    const double m = __longlong_as_double((long long)((u & 0x800fffffffffffffull) | (1022ull << 52)));
     const int q = (e >= 0) ? e / 3 : -((-e + 2) / 3);
     const int rmd = e - 3 * q;
-    if (rmd == 1) m = __dmul_rn(m, 2.0);
-    else if (rmd == 2) m = __dmul_rn(m, 4.0);
-    double y = __dmul_rn(0.2, m);
-    y = __dadd_rn(y, 0.74);
-#pragma unroll 1
-    for (int i = 0; i < 5; ++i) {
-        const double a = __dmul_rn(y, y);
-        const double b = __ddiv_rn(m, a);
-        const double c = __dadd_rn(y, y);
-        const double d = __dadd_rn(c, b);
-        y = __ddiv_rn(d, 3.0);
+    const double third = 0.3333333333333333;
+    double y = __dmul_rn(0.456419, m);
+    y = __dsub_rn(y, 1.19161);
+    y = __dmul_rn(y, m);
+    y = __dadd_rn(y, 1.73758);
+    y = __dmul_rn(y, rmd == 0 ? 1.0 : (rmd == 1 ? 0.7937005259840998 : 0.6299605249474366));
+    const double M = rmd == 1 ? __dmul_rn(m, 2.0) : (rmd == 2 ? __dmul_rn(m, 4.0) : m);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double t = __dmul_rn(y, y);
+        t = __dmul_rn(t, y);
+        t = __dmul_rn(M, t);
+        t = __dsub_rn(1.0, t);
+        t = __dmul_rn(t, y);
+        t = __dmul_rn(t, third);
+        y = __dadd_rn(y, t);
     }
-    return __dmul_rn(y, __longlong_as_double((long long)((uint64_t)(1023 + q) << 52)));
+    double c = __dmul_rn(M, y);
+    c = __dmul_rn(c, y);
+    double r = __dmul_rn(c, c);
+    r = __dmul_rn(r, c);
+    r = __dsub_rn(r, M);
+    double t = __dmul_rn(y, y);
+    t = __dmul_rn(t, third);
+    t = __dmul_rn(r, t);
+    c = __dsub_rn(c, t);
+    return __dmul_rn(c, __longlong_as_double((long long)((uint64_t)(1023 + q) << 52)));
 }
 
 __device__ __forceinline__ double radius_d(double v)
@@ -188,11 +204,14 @@ __device__ __forceinline__ double radius_d(double v)
     return cbrt_d(__dmul_rn(v, THREE_OVER_FOUR_PI));
 }
 
+// regime borders k2/k1 and (k3/k2)^2 as rounded in double, written out
+constexpr double VT_R12 = 6.722689075630252e-05;
+constexpr double VT_R23 = 0.0006312656250000001;
+
 __device__ __forceinline__ double vt_d(double r)
 {
-    const double r12 = __ddiv_rn(VT_K2, VT_K1);
-    const double t = __ddiv_rn(VT_K3, VT_K2);
-    const double r23 = __dmul_rn(t, t);
+    const double r12 = VT_R12;
+    const double r23 = VT_R23;
     if (r < r12) return __dmul_rn(__dmul_rn(VT_K1, r), r);
     if (r < r23) return __dmul_rn(VT_K2, r);
     return __dmul_rn(VT_K3, __dsqrt_rn(r));
@@ -341,14 +360,18 @@ struct P32 { float p; float err; };
 // sevenfold margin.
 constexpr float GOLOVIN_REL_BOUND = 0x1p-17f;
 // Bound of the gravitational evaluation relative to
-// B = scale * pi (r1+r2)^2 (vt1 + vt2) >= p / E (E <= 1): volume conversion
-// and cube root (<= 4u on r), regime choice near the continuous joins, the
-// difference vt1 - vt2 (its absolute error is bounded by the sum vt1 + vt2),
-// and the position inside the efficiency table (interpolation weights carry an
-// absolute error of at most ~250 u because neighbouring radius nodes are
-// >= 1/7 apart relative to the radius) add up to < 400 u; 2^-12 = 4096 u
-// leaves a tenfold margin.
-constexpr float GRAV_REL_BOUND = 0x1p-12f;
+// B = scale * pi (r1+r2)^2 (vt1 + vt2) >= p / E (E <= 1), u = 2^-24:
+//  r: truncated v (2u), 3/(4pi) (u), product (u), cbrtf (1 ulp = 2u) -> 3.4u;
+//  vt: k r^2 law 9.8u, plus up to 4.4u where FP32 and FP64 pick different
+//      regimes next to a (continuous) border -> 14.2u; so the difference
+//      vt1 - vt2 is off by at most 15.2u (vt1 + vt2) in absolute terms;
+//  pi (r1 + r2)^2: 11.8u;  scale (xi, S, dt/dV): 9u;
+//  E: the interpolation weight along R is off by <= 28.4u (the radius nodes
+//     satisfy R[i+1] / (R[i+1] - R[i]) <= 6), along q by <= 86u, times table
+//     steps <= 1 and <= 0.2, plus roundings -> |dE| <= 52u absolute;
+// in all |p32 - p64| <= (15.2 + 52 + 23.8) u B = 91u B (the FP64 value's own
+// rounding is ~1e-14 relative).  2^-15 = 512u leaves a 5.6-fold margin.
+constexpr float GRAV_REL_BOUND = 0x1p-15f;
 constexpr float ABS_SLACK = 0x1p-100f;   // covers gradual underflow of the last products
 constexpr float MIN_NORMAL_V = 0x1p-120f; // smaller float volumes are sent to the FP64 path
 
