@@ -19,6 +19,7 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import statistics
@@ -104,6 +105,38 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _source_hash():
+    """sha256 over the per-file sha256 lines of the CUDA sources and the C header."""
+    import hashlib
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2101_06318_b300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "sdm.h"))
+    lines = []
+    for f in files:
+        with open(f, "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+        lines.append(f"{digest}  {os.path.relpath(f, ROOT)}\n")
+    return hashlib.sha256("".join(lines).encode()).hexdigest()
+
+
+def _profiled_traffic(kernel, workload_name, n_sd):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and workload, when the
+    summary was taken on the current sources (else None: the counters are stale)."""
+    short = kernel.split("::")[-1]
+    path = os.path.join(ROOT, "profiles", f"{short}_{workload_name}_{n_sd >> 20}M.md")
+    try:
+        with open(path) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in txt.splitlines() if ln.startswith(("csrc_sha256:", "dram_bytes")))
+    if fields.get("csrc_sha256", "").strip() != _source_hash():
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def workload(name, rank=0):
@@ -247,22 +280,25 @@ def run_ours(args, rank, world, local_rank):
         return
     value = sd_total / (tot_ms * 1e-3)
     peak, peak_src = _peaks()
-    # algorithmic bytes per SD-step: read xi and v (16 B); each collision writes at most
-    # 2 x (xi + v) = 32 B
-    bytes_step = 16.0 * live0 + 32.0 * stats["n_collisions"]
+    # algorithmic bytes per SD-step of the in-place update model: read xi and v, write xi and v
+    # (32 B); the bytes a step must touch at least are the reads (16 B per SD) plus 32 B per collision
+    bytes_step = 32.0 * live0
+    bytes_touched = 16.0 * live0 + 32.0 * stats["n_collisions"]
     kern = {k: {"launches": v[0], "ms_total": v[1], "ms_per_launch": (v[1] / v[0] if v[0] else None)}
             for k, v in prof.items() if v[0]}
     tot_k = sum(v["ms_total"] for v in kern.values()) or 1.0
     for v in kern.values():
         v["share"] = v["ms_total"] / tot_k
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    step_kernel_ms = sum(v["ms_per_launch"] for v in kern.values())
-    achieved_step = bytes_step / (step_kernel_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "+".join(kern), "dominant": dom,
-                "achieved": achieved_step, "peak": peak, "unit": "GB/s", "frac": achieved_step / peak,
-                "peak_source": f"{peak_src} hbm_gbs", "traffic": None,
-                "algorithmic_bytes_per_step": bytes_step,
-                "note": "algorithmic bytes of the whole step over the summed device time of its kernels"}
+    # one launch of the dominant kernel processes every SD of the step (the large-cell kernel holds
+    # the whole box; with tiles only, the tile kernel does), so its algorithmic bytes are the step's
+    achieved = bytes_step / (kern[dom]["ms_per_launch"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                "traffic": _profiled_traffic(dom, args.workload, n),
+                "algorithmic_bytes_per_launch": bytes_step, "bytes_per_unit": 32,
+                "min_bytes_touched_per_launch": bytes_touched,
+                "ms_per_launch": kern[dom]["ms_per_launch"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
