@@ -75,9 +75,11 @@ struct sdm_state {
     uint32_t* d_bstart = nullptr;            // [n_buckets + 1] bucket offsets of the current step
     uint32_t* d_ticket = nullptr;            // [1] CTAs of the scatter pass that finished
     uint64_t* d_scratch = nullptr;
-    uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then [1] end-of-step ticket
-    BigWork* d_big_work = nullptr;           // PRP contract: candidate-pair ranges (work items)
-    uint32_t n_big_work = 0, prp_grid = 0;
+    uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
+    uint32_t n_quads = 0, prp_grid = 0;      // PRP contract: quads of all large cells, grid size
+    uint32_t* d_cta_first = nullptr;         // [prp_grid] first large cell of each CTA (many large cells)
+    float* d_big_xpow = nullptr;             // [n_big] power of two above every multiplicity of the cell
+    BigLaunch prp_launch{};
     FinishLayout fin_L{};
     uint32_t fin_grid = 0, n_buckets_planned = 0;
 
@@ -145,7 +147,7 @@ void free_layout(sdm_state* st)
     if (st->ws) st->ws_used = st->ws_fixed;
     st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
-    st->d_big_removed = nullptr; st->d_big_work = nullptr; st->n_big_work = 0;
+    st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xpow = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
 }
 
@@ -177,6 +179,85 @@ sdm_status check_schedule(const sdm_schedule& s)
 }
 
 // Plan tiles (runs of consecutive small cells) and the large-cell buckets.
+// Early-exit bound table (see pb_bin in sdm_math.cuh), computed on the host in
+// double: [0][b] the bin's upper volume edge, [1][b] pi (2 r)^2 vt(r) Emax (1 + 2^-10)
+// at the bin's upper radius r, Emax the largest efficiency of the table rows that
+// radii in the bin interpolate between; both rounded up to float.
+void fill_pbound_host(float (*t)[PB_NB + 1])
+{
+    constexpr double E_h[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
+    double rowmax[EFF_NR];
+    for (int i = 0; i < EFF_NR; ++i) {
+        rowmax[i] = 0.0;
+        for (int j = 0; j < EFF_NQ; ++j) rowmax[i] = std::max(rowmax[i], E_h[i * EFF_NQ + j]);
+    }
+    auto row_of = [](double r) {   // interpolation interval index of radius r, as in the kernels
+        int i = 0;
+        while (i < EFF_NR - 2 && c_eff_R_h[i + 1] <= r) ++i;
+        return i;
+    };
+    auto up = [](double x) {
+        float f = (float)x;
+        if ((double)f < x) f = std::nextafter(f, INFINITY);
+        return f;
+    };
+    for (uint32_t b = 0; b < PB_NB; ++b) {
+        const int e = PB_EMIN + (int)(b / 4);
+        const double m = (double)(b % 4);
+        const double v_lo = std::ldexp(1.0 + m / 4.0, e), v_hi = std::ldexp(1.0 + (m + 1.0) / 4.0, e);
+        t[0][b] = up(v_hi);
+        const double r_lo = std::cbrt(v_lo * THREE_OVER_FOUR_PI) * (1.0 - 1e-12);
+        const double r_hi = std::cbrt(v_hi * THREE_OVER_FOUR_PI) * (1.0 + 1e-12);
+        const int i0 = row_of(r_lo), i1 = std::min(EFF_NR - 1, row_of(r_hi) + 1);
+        double emax = 0.0;
+        for (int i = i0; i <= i1; ++i) emax = std::max(emax, rowmax[i]);
+        const double vt = r_hi < VT_R12 ? VT_K1 * r_hi * r_hi : (r_hi < VT_R23 ? VT_K2 * r_hi : VT_K3 * std::sqrt(r_hi));
+        t[1][b] = up(PI_D * (4.0 * r_hi * r_hi) * vt * emax * (1.0 + 0x1p-10));
+    }
+    t[0][PB_NB] = t[1][PB_NB] = INFINITY;   // beyond the table: no bound
+}
+
+// Upload the device tables once per device (first use).
+sdm_status ensure_device_tables()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    SDM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SDM_ENOTSUP;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return SDM_OK;
+    static float t[2][PB_NB + 1];
+    fill_pbound_host(t);
+    SDM_CUDA(cudaMemcpyToSymbol(g_pbound, t, sizeof t));
+    done[dev] = true;
+    return SDM_OK;
+}
+
+// Grid of the PRP kernel: one wave of resident CTAs, at most one CTA per warp's worth of quads.
+uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const uint32_t wave = (uint32_t)std::max(per_sm, 1) * (uint32_t)std::max(n_sm, 1);
+    return std::max<uint32_t>(1, std::min<uint32_t>(wave, (n_quads + 31) / 32));
+}
+
+// per large cell: the multiplicity bound of the early exit, from the current state
+sdm_status refresh_big_bounds(sdm_state* st)
+{
+    if (!st->n_big) return SDM_OK;
+    big_xpow_kernel<<<st->n_big, 256, 0, st->stream>>>(st->d_xi, st->d_big, st->d_big_xpow);
+    SDM_CUDA(cudaGetLastError());
+    return SDM_OK;
+}
+
+// the 64-bit ticket follows the removal flags at an 8-byte aligned word
+size_t big_ticket_word(size_t n_big) { return (n_big + 1) & ~(size_t)1; }
+
 sdm_status build_layout(sdm_state* st)
 {
     free_layout(st);
@@ -187,7 +268,7 @@ sdm_status build_layout(sdm_state* st)
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
     std::vector<uint32_t> bucket_big;
-    std::vector<BigWork> work;
+    uint32_t n_quads = 0;
     TileDesc cur{0, 0, 0, 0};
     uint32_t cur_slots = 0;
     auto flush = [&]() {
@@ -220,9 +301,8 @@ sdm_status build_layout(sdm_state* st)
             max_nb = std::max(max_nb, nb);
             for (uint32_t l = 0; l < w; l += BIG_CHUNK)
                 chunks.push_back(BigChunk{(uint32_t)bigs.size(), l, std::min(w, l + BIG_CHUNK), 0});
-            const uint32_t pairs = std::max<uint32_t>(1, w / 2);   // candidate pairs at full occupancy
-            for (uint32_t m = 0; m < pairs; m += PRP_THREADS)
-                work.push_back(BigWork{(uint32_t)bigs.size(), m, std::min(pairs, m + PRP_THREADS), 0});
+            b.quad_begin = n_quads;
+            n_quads += (w / 2 + 1) / 2;                       // quads at full occupancy
             bigs.push_back(b);
             continue;
         }
@@ -251,19 +331,27 @@ sdm_status build_layout(sdm_state* st)
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
     SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
-    SDM_TRY(upload(st, &st->d_big_work, work));
-    st->n_big_work = (uint32_t)work.size();
-    if (!work.empty()) {
-        int per_sm = 0;
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0));
-        st->prp_grid = std::max<uint32_t>(1, std::min<uint32_t>(st->n_big_work, (uint32_t)std::max(per_sm, 1) * st->n_sm));
+    st->n_quads = n_quads;
+    if (n_quads) {
+        st->prp_grid = prp_grid_size(n_quads, st->n_sm);
+        std::vector<uint32_t> first(st->prp_grid);
+        for (uint32_t b = 0, c = 0; b < st->prp_grid; ++b) {
+            const uint32_t qa = (uint32_t)(((uint64_t)b * n_quads) / st->prp_grid);
+            while (c + 1 < bigs.size() && bigs[c + 1].quad_begin <= qa) ++c;
+            first[b] = c;
+        }
+        SDM_TRY(upload(st, &st->d_cta_first, first));
     }
     if (!bigs.empty()) {
-        SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * (bigs.size() + 1), true));
-        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (bigs.size() + 1), st->stream));
+        const size_t words = big_ticket_word(bigs.size()) + 2;
+        SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * words, true));
+        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * words, st->stream));
     }
     st->n_tiles = (uint32_t)tiles.size();
     st->n_big = (uint32_t)bigs.size();
+    if (!bigs.empty()) SDM_TRY(dev_alloc(st, (void**)&st->d_big_xpow, sizeof(float) * bigs.size(), true));
+    st->prp_launch = BigLaunch{st->n_big, n_quads, st->d_big, st->d_big_xpow, st->d_cta_first, {}};
+    for (uint32_t b = 0; b < st->n_big && b < BIG_PARAM_CELLS; ++b) st->prp_launch.pc[b] = bigs[b];
     st->n_chunks = (uint32_t)chunks.size();
     st->n_buckets = (uint32_t)bucket_big.size();
     st->bucket_cap = bucket_cap;
@@ -366,6 +454,7 @@ sdm_status init_common(sdm_state* st, const uint64_t* xi_in, const double* attr_
     st->n_sd = n;
     SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
     SDM_TRY(build_layout(st));
+    SDM_TRY(refresh_big_bounds(st));
     st->initialised = true;
     return SDM_OK;
 }
@@ -508,11 +597,11 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             tile_step_kernel<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
                                                                                     st->tile_L, work);
         }
-        const BigBook bb{st->d_big_removed + st->n_big, st->d_big_removed, st->n_big};
+        const BigBook bb{(unsigned long long*)(st->d_big_removed + big_ticket_word(st->n_big)), st->d_big_removed,
+                         st->n_big};
         if (st->n_big && p->shuffle == SDM_SHUFFLE_PRP) {
             ProfScope ps(st, 3);
-            big_prp_kernel<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->d_big, st->d_big_work, st->n_big_work,
-                                                                         bb);
+            big_prp_kernel<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->prp_launch, bb);
         } else if (st->n_big) {
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
@@ -559,7 +648,7 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256);
     b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
     b += 4 * round256(512) + round256(4 * (size_t)n_cell + 256);
-    b += round256(sizeof(BigWork) * (cap / 2 / PRP_THREADS + n_cell + 1) + 256) + round256(4 * (size_t)n_cell + 260);
+    b += round256(4 * (size_t)n_cell + 260);
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
@@ -592,6 +681,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
         st->ws_bytes = ws_bytes - skew;
     }
     sdm_status s = SDM_OK;
+    if (s == SDM_OK) s = ensure_device_tables();
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_xi, sizeof(uint64_t) * cap, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_attr, sizeof(double) * cap * n_attr, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_cell_start, sizeof(uint32_t) * ((size_t)n_cell + 1), false);
@@ -694,7 +784,7 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
     const uint32_t cgrid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm));
     live_count_kernel<<<cgrid, 256, 0, st->stream>>>(st->d_xi, st->d_cell_start, st->n_cell, st->d_n_live);
     SDM_CUDA(cudaGetLastError());
-    return SDM_OK;
+    return refresh_big_bounds(st);
 }
 
 sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* cell_start, uint64_t* n_sd, int on_dev)
@@ -857,8 +947,10 @@ sdm_status sdm_set_schedule(sdm_state* st, const sdm_schedule* s)
         if (r != SDM_OK) {
             st->sched = old;
             build_layout(st);
+            refresh_big_bounds(st);
             return r;
         }
+        SDM_TRY(refresh_big_bounds(st));
     }
     return SDM_OK;
 }
@@ -989,16 +1081,15 @@ constexpr uint32_t NA_TARGET_BITS = 8;                                    // 256
 constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 1024
 constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 576 records per bucket
 constexpr uint32_t NA_MAX_CHUNKS = (SDM_NOALLOC_MAX_SD + BIG_CHUNK - 1) / BIG_CHUNK;
-constexpr uint32_t NA_MAX_WORK = (SDM_NOALLOC_MAX_SD / 2 + PRP_THREADS - 1) / PRP_THREADS;
 // byte offsets inside the scratch array
 constexpr size_t NA_OFF_CELL = 0;        // BigCell
 constexpr size_t NA_OFF_DV = 64;         // double dv
 constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
 constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
 constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, removal flag, end-of-step ticket
+constexpr size_t NA_OFF_XPOW = 192;      // float multiplicity bound of the box
 constexpr size_t NA_OFF_CHUNKS = 256;
-constexpr size_t NA_OFF_WORK = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
-constexpr size_t NA_OFF_BBIG = NA_OFF_WORK + sizeof(BigWork) * NA_MAX_WORK;
+constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
 constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
 constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
 constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
@@ -1010,10 +1101,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
-uint32_t g_na_prp_grid[NA_MAX_DEVICES] = {};
 
 // device address of the scratch array on the current device (looked up once per device)
-sdm_status noalloc_scratch(unsigned char** out, uint32_t* prp_grid)
+sdm_status noalloc_scratch(unsigned char** out)
 {
     int dev = 0;
     SDM_CUDA(cudaGetDevice(&dev));
@@ -1027,14 +1117,10 @@ sdm_status noalloc_scratch(unsigned char** out, uint32_t* prp_grid)
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * NA_MAX_BUCKETS;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
         SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
-        int n_sm = 0, per_sm = 0;
-        SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0));
-        g_na_prp_grid[dev] = (uint32_t)std::max(1, n_sm * std::max(per_sm, 1));
+        SDM_TRY(ensure_device_tables());
         g_na_ptr[dev] = (unsigned char*)p;
     }
     *out = g_na_ptr[dev];
-    *prp_grid = g_na_prp_grid[dev];
     return SDM_OK;
 }
 
@@ -1053,8 +1139,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
     if (n_sd < 2) return SDM_OK;
     unsigned char* base = nullptr;
-    uint32_t prp_grid = 1;
-    SDM_TRY(noalloc_scratch(&base, &prp_grid));
+    SDM_TRY(noalloc_scratch(&base));
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
     // the same geometry as the large-cell path with a 256-SD bucket target
@@ -1069,10 +1154,8 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     BigChunk chunks[NA_MAX_CHUNKS];
     uint32_t n_chunks = 0;
     for (uint32_t l = 0; l < n_sd; l += BIG_CHUNK) chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), 0};
-    BigWork work[NA_MAX_WORK];
-    uint32_t n_work = 0;
-    const uint32_t pairs = n_sd / 2;
-    for (uint32_t m = 0; m < pairs; m += PRP_THREADS) work[n_work++] = BigWork{0, m, std::min(pairs, m + PRP_THREADS), 0};
+    C.quad_begin = 0;
+    const uint32_t n_quads = (n_sd / 2 + 1) / 2;
     uint32_t bucket_big[NA_MAX_BUCKETS] = {};
     unsigned char head[256] = {};
     const uint8_t kid = (uint8_t)kernel_id;
@@ -1085,11 +1168,13 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     // descriptors in; cursors, tickets, flags and the error word start at zero on every call
     SDM_CUDA(cudaMemcpyAsync(base, head, sizeof head, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_CHUNKS, chunks, sizeof(BigChunk) * n_chunks, cudaMemcpyHostToDevice, stream));
-    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_WORK, work, sizeof(BigWork) * n_work, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_big, 4 * nb, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
-    uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4] ticket
+    uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
+    float* d_xpow = (float*)(base + NA_OFF_XPOW);
+    if (p->shuffle == SDM_SHUFFLE_PRP)
+        big_xpow_kernel<<<1, 256, 0, stream>>>(xi, (const BigCell*)(base + NA_OFF_CELL), d_xpow);
 
     StepArgs a{};
     a.xi = xi;
@@ -1113,10 +1198,14 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.stats = nullptr;
     a.err = (uint32_t*)(base + NA_OFF_ERR);
     const BigCell* d_cell = (const BigCell*)(base + NA_OFF_CELL);
-    const BigBook bb{live + 4, live + 3, 1};
+    const BigBook bb{(unsigned long long*)(live + 4), live + 3, 1};
     if (p->shuffle == SDM_SHUFFLE_PRP) {
-        big_prp_kernel<<<std::min<uint32_t>(n_work, prp_grid), PRP_THREADS, 0, stream>>>(
-            a, d_cell, (const BigWork*)(base + NA_OFF_WORK), n_work, bb);
+        int dev = 0, n_sm = 148;
+        SDM_CUDA(cudaGetDevice(&dev));
+        SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        BigLaunch L{1, n_quads, d_cell, d_xpow, nullptr, {}};
+        L.pc[0] = C;
+        big_prp_kernel<<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]

@@ -64,7 +64,7 @@ __device__ __forceinline__ bool sorts(const StepArgs& a, uint32_t n)
 }
 
 struct TileDesc { uint32_t slot_begin, slot_end, cell_begin, n_cells; };
-struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, pad; };
+struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, quad_begin; };   // quad_begin: PRP contract
 struct BigChunk { uint32_t big, l_begin, l_end, pad; };
 
 __device__ __forceinline__ uint32_t step_index(const StepArgs& a)
@@ -72,8 +72,9 @@ __device__ __forceinline__ uint32_t step_index(const StepArgs& a)
     return a.d_step ? *a.d_step : a.step;
 }
 
-struct LocalStats {
-    unsigned long long pairs, collisions, removed, sum_gamma, fp64;
+struct LocalStats {         // per thread; only the sum of gamma needs 64 bits
+    uint32_t pairs, collisions, removed, fp64;
+    unsigned long long sum_gamma;
 };
 
 struct CellCtx {
@@ -503,7 +504,7 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t step = step_index(a);
-    LocalStats ls = {0, 0, 0, 0, 0};
+    LocalStats ls = {0, 0, 0, 0, 0ull};
     unsigned long long* red = (unsigned long long*)(smem + L.o_red);
     load_eff_tab((EffTab*)(smem + L.o_tab));   // read after the first __syncthreads of tile_process
     if (work == nullptr) {
@@ -538,8 +539,9 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
 // compaction done by the last CTA of the step's final large-cell kernel.
 // ---------------------------------------------------------------------------
 struct BigBook {
-    uint32_t* ticket;      // CTAs of the current kernel that finished (reset by the last one)
-    uint32_t* removed;     // [n_big] an SD of this cell was removed during the step
+    unsigned long long* ticket;   // low word: CTAs of the current kernel that finished; high word:
+                                  // how many of them removed an SD (reset by the last CTA)
+    uint32_t* removed;            // [n_big] an SD of this cell was removed during the step
     uint32_t n_big;
 };
 
@@ -594,18 +596,24 @@ __device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_
     return dst;
 }
 
-// Called by every CTA at its end: the last one compacts the large cells that
-// lost SDs in this step and resets the bookkeeping.
-__device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ cells, const BigBook& bk, uint32_t* wt)
+// Called by every CTA at its end (had_removal: some thread of the CTA removed an
+// SD): the last CTA compacts the large cells that lost SDs in this step and
+// resets the bookkeeping.  One atomic per CTA; the removal count travels in the
+// same word, so without removals the last CTA reads nothing else.
+__device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ cells, const BigBook& bk, uint32_t* wt,
+                                bool had_removal)
 {
-    __shared__ uint32_t s_last;
-    __syncthreads();
+    __shared__ unsigned long long s_old;
+    const bool any = __syncthreads_or(had_removal);
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = (atomicAdd(bk.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+        s_old = atomicAdd(bk.ticket, 1ull + (any ? (1ull << 32) : 0ull));
     }
     __syncthreads();
-    if (!s_last) return;
+    const unsigned long long old = s_old;
+    if ((uint32_t)old != gridDim.x - 1) return;
+    if (threadIdx.x == 0) *bk.ticket = 0ull;
+    if ((old >> 32) == 0 && !any) return;
     __threadfence();
     for (uint32_t b = 0; b < bk.n_big; ++b) {
         if (!*(volatile uint32_t*)&bk.removed[b]) continue;
@@ -618,65 +626,224 @@ __device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ c
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *bk.ticket = 0;
 }
 
 // ---------------------------------------------------------------------------
-// Large cells under the PRP contract: a persistent grid walks work items of
-// PRP_THREADS candidate pairs; a thread maps its pair's two list positions
-// through the keyed bijection and gathers the two SDs directly (no sort, no
-// exchange, no atomics).  Per-CTA set-up (table, round keys) and the
-// end-of-step ticket are paid once per CTA, not once per item.
+// Large cells under the PRP contract.  The candidate pairs of all large cells
+// are taken two at a time -- a "quad": list positions 4q .. 4q+3, pairs 2q and
+// 2q+1, whose phi come from one Philox call -- and the quads, numbered across
+// the cells (BigCell::quad_begin), are split into equal contiguous ranges, one
+// per CTA of a single-wave grid.  Every thread derives the cell's round keys
+// itself (no shared context, no barrier before work starts) and takes two
+// quads at a time: it maps their eight positions through the keyed bijection,
+// issues all eight gathers, computes phi while they are in flight, and settles
+// most pairs by the early exit (phi above an upper bound of p).  The remaining
+// pairs go to a per-warp queue in shared memory and are evaluated 32 at a
+// time, so the long evaluation runs on full warps instead of diverging the
+// common path.
 // ---------------------------------------------------------------------------
 constexpr uint32_t PRP_THREADS = 256;
-struct BigWork { uint32_t big, m_begin, m_end, pad; };   // candidate pairs [m_begin, m_end) of one large cell
+constexpr uint32_t PRP_WARPS = PRP_THREADS / 32;
+#ifndef SDM_PRP_MIN_BLOCKS
+#define SDM_PRP_MIN_BLOCKS 2
+#endif
+constexpr uint32_t BIG_PARAM_CELLS = 8;        // large cells passed by value in the launch
+constexpr uint32_t PQ_CAP = 160;               // queued pairs per warp (< 32 left + 4 x 32 new)
 
-__global__ void __launch_bounds__(PRP_THREADS, 3) big_prp_kernel(StepArgs a, const BigCell* __restrict__ cells,
-                                                                const BigWork* __restrict__ work, uint32_t n_work,
-                                                                BigBook bk)
+struct BigLaunch {
+    uint32_t n_big, n_quads;
+    const BigCell* cells;                      // [n_big] (device)
+    const float* xpow;                         // [n_big] power of two above every multiplicity of the cell
+    const uint32_t* cta_first;                 // [grid] first large cell of each CTA (n_big > BIG_PARAM_CELLS)
+    BigCell pc[BIG_PARAM_CELLS];               // the large cells when n_big <= BIG_PARAM_CELLS
+};
+
+struct PairQueue {
+    uint32_t s1[PQ_CAP], s2[PQ_CAP];
+    unsigned long long u[PQ_CAP];
+};
+
+// eight Feistel evaluations with shared round keys (two quads)
+__device__ __forceinline__ void feistel8(const Prp& P, uint32_t (&x)[8])
 {
-    __shared__ EffTab tab;
-    __shared__ Prp P;
-    __shared__ CellCtx s_cc;
+    uint32_t L[8], R[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { L[i] = x[i] >> P.b; R[i] = x[i] & P.mask_b; }
+#pragma unroll
+    for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) L[i] ^= lowbias32_tail(R[i] ^ P.K[r]) & P.mask_a;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) R[i] ^= lowbias32_tail(L[i] ^ P.K[r + 1]) & P.mask_b;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (L[i] << P.b) | R[i];
+}
+
+// cycle-walking (only when n is not a power of two) of the images whose bit in
+// 'use' is set; the others (positions >= n) never walk
+__device__ __forceinline__ void prp_walk8(const Prp& P, uint32_t use, uint32_t (&e)[8])
+{
+    for (;;) {
+        uint32_t walk = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) walk |= (((use >> i) & 1u) && e[i] >= P.n) ? (1u << i) : 0u;
+        if (!walk) break;
+        uint32_t f[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) f[i] = e[i];
+        feistel8(P, f);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if ((walk >> i) & 1u) e[i] = f[i];
+    }
+}
+
+// Evaluate the top 'take' queued pairs of this warp (lanes < take) and pop them.
+__device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& cc,
+                                            PairQueue& Q, uint32_t& qcnt, uint32_t take, LocalStats& ls,
+                                            uint32_t* removed_flag, uint32_t lane)
+{
+    __syncwarp();
+    if (lane < take) {
+        const uint32_t k = qcnt - take + lane;
+        const uint32_t s1 = Q.s1[k], s2 = Q.s2[k];
+        process_pair(a, T, cc, Q.u[k], s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls, removed_flag);
+    }
+    __syncwarp();
+    qcnt -= take;
+}
+
+// Settle pair (s1, s2) by the early exit or queue it (warp-collective).  c_upx is
+// the cell's early-exit scale times its multiplicity bound.
+__device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, uint32_t& qcnt, bool has, uint32_t s1,
+                                              uint32_t s2, uint32_t vh1, uint32_t vh2, uint32_t w_hi, uint32_t w_lo,
+                                              const float* __restrict__ tb, float c_upx, LocalStats& ls,
+                                              uint32_t lane)
+{
+    bool need = false;
+    if (has) {
+        need = !(__fmul_ru(__ldg(tb + pb_bin(vh1, vh2)), c_upx) <= phi_lo23(w_hi));
+        ls.pairs += need ? 0u : 1u;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (need) {
+        const uint32_t k = qcnt + __popc(m & ((1u << lane) - 1u));
+        Q.s1[k] = s1;
+        Q.s2[k] = s2;
+        Q.u[k] = ((((uint64_t)w_hi) << 32) | (uint64_t)w_lo) >> 11;
+        // the multiplicities are read when the queue is drained: start bringing them to L2
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + s1));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + s2));
+    }
+    qcnt += __popc(m);
+}
+
+__global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kernel(StepArgs a, BigLaunch L,
+                                                                                 BigBook bk)
+{
+    const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
+    __shared__ PairQueue pq[PRP_WARPS];
     __shared__ uint32_t wt[40];
     __shared__ uint32_t key_s[PRP_MIN_N];
     __shared__ uint16_t srt_s[PRP_MIN_N];
     __shared__ unsigned long long red[8];
-    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t step = step_index(a);
-    LocalStats ls = {0, 0, 0, 0, 0};
-    load_eff_tab(&tab);
+    const uint32_t qa = (uint32_t)(((uint64_t)blockIdx.x * L.n_quads) / gridDim.x);
+    const uint32_t qb = (uint32_t)(((uint64_t)(blockIdx.x + 1) * L.n_quads) / gridDim.x);
+    const bool by_value = L.n_big <= BIG_PARAM_CELLS;
+    uint32_t c = 0;                                 // first large cell of this CTA's range
+    if (by_value) {
+        for (uint32_t k = 1; k < L.n_big; ++k)
+            if (L.pc[k].quad_begin <= qa) c = k;
+    } else {
+        c = L.cta_first[blockIdx.x];
+    }
+    LocalStats ls = {0, 0, 0, 0, 0ull};
     if (tid < 5) red[tid] = 0;
-    uint32_t cur = 0xffffffffu;                 // large cell whose round keys are staged
-    for (uint32_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-        const BigWork W = work[w];
-        const BigCell C = cells[W.big];
-        if (W.big != cur) {                     // uniform in the CTA
-            __syncthreads();
-            if (tid == 0) {
-                const uint32_t n = min(a.n_live[C.cell], C.width);
-                prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, n);
-                s_cc = CellCtx{C.cell, n, (uint32_t)a.kid[C.cell],
-                               n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]) : 0.f, a.dv[C.cell]};
-            }
-            __syncthreads();
-            cur = W.big;
-        }
-        const uint32_t n = s_cc.n;
+    PairQueue& Q = pq[warp];
+    uint32_t qcnt = 0;                              // queued pairs of this warp (warp-uniform)
+    for (; qa < qb && c < L.n_big; ++c) {
+        const BigCell C = by_value ? L.pc[c] : L.cells[c];
+        if (C.quad_begin >= qb) break;
+        const uint32_t q_end = c + 1 < L.n_big ? (by_value ? L.pc[c + 1].quad_begin : L.cells[c + 1].quad_begin)
+                                               : L.n_quads;
+        const uint32_t sa = max(qa, C.quad_begin), sb = min(qb, q_end);
+        // the cell's context, in every thread.  The live count n is loading while the round
+        // keys are derived and the first bijection images are computed on the domain of the
+        // cell's width (the same halves whenever ceil(log2 n) = ceil(log2 width))
+        const uint32_t n = min(a.n_live[C.cell], C.width);
+        const uint32_t kid = (uint32_t)a.kid[C.cell];
+        const double dv = a.dv[C.cell];
+        const float xpow = L.xpow[c];
+        Prp P;
+        prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, C.width);
+        const bool same_bits = prp_bits(n) == prp_bits(C.width);
+        const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
+        uint32_t* const rflag = &bk.removed[c];
         const uint32_t npairs = n >> 1;
-        uint32_t* rflag = &bk.removed[W.big];
         if (n >= PRP_MIN_N) {
-            const uint32_t m = W.m_begin + tid;
-            if (m < W.m_end && m < npairs) {
-                const uint64_t s1 = C.slot_begin + prp_map(P, 2 * m);
-                const uint64_t s2 = C.slot_begin + prp_map(P, 2 * m + 1);
-                const uint64_t x1 = a.xi[s1], x2 = a.xi[s2];
-                const double v1 = a.attr[s1], v2 = a.attr[s2];
-                const uint64_t u = phi_u53(a.seed_lo, a.seed_hi, C.cell, step, m);
-                process_pair(a, &tab, s_cc, u, s1, s2, x1, x2, v1, v2, ls, rflag);
+            const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
+            const CellCtx cc{C.cell, n, kid, s32, dv};
+            const float c_upx =
+                __fmul_ru(__fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, a.golovin_bf) : 1.0f), 1.0f + 0x1p-8f),
+                          xpow);
+            // two quads per thread and iteration: g and g + 32 (warp-uniform trip count)
+            for (uint32_t base = sa + warp * 64; base < sb; base += 2 * nt) {
+                uint32_t e[8], qj[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    qj[j] = base + 32 * j + lane - C.quad_begin;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
+                }
+                feistel8(P, e);
+                if (!same_bits) {            // uniform: the live count left the width's power of two
+                    prp_set_domain(P, n);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
+                    feistel8(P, e);
+                } else {
+                    P.n = n;
+                }
+                bool h0[2], h1[2];
+                uint32_t use = 0;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    h0[j] = base + 32 * j + lane < sb && 2 * qj[j] < npairs;
+                    h1[j] = h0[j] && 2 * qj[j] + 1 < npairs;
+                    use |= (h0[j] ? 3u : 0u) << (4 * j);
+                    use |= (h1[j] ? 12u : 0u) << (4 * j);
+                }
+                prp_walk8(P, use, e);
+                // gather the volumes' high words (all the early exit needs with the cell's
+                // multiplicity bound), then phi while they are in flight
+                uint32_t vh[8];
+                const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    e[i] += C.slot_begin;              // slots from here on
+                    vh[i] = ((use >> i) & 1u) ? attr_hi[2 * (size_t)e[i]] : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    U4 w = {0, 0, 0, 0};
+                    if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.seed_lo, a.seed_hi);
+                    exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
+                                  c_upx, ls, lane);
+                    exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
+                                  w.w, tb, c_upx, ls, lane);
+                }
+                while (qcnt >= 32) drain_queue(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
             }
-        } else if (n >= 2 && W.m_begin == 0) {
-            // few live SDs left in a large cell: sorted by key, all in the item holding pair 0
+            if (qcnt > 0) drain_queue(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
+        } else if (n >= 2 && C.quad_begin >= qa) {
+            // few live SDs left in a large cell: sorted by key by the CTA holding the cell's
+            // first quad (n, qa and the cell are the same in all threads: a uniform branch)
+            __syncthreads();
             for (uint32_t t = tid; t < n; t += nt)
                 key_s[t] = u4_word(philox(t >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi), t & 3u);
             __syncthreads();
@@ -687,19 +854,19 @@ __global__ void __launch_bounds__(PRP_THREADS, 3) big_prp_kernel(StepArgs a, con
                 srt_s[r] = (uint16_t)t;
             }
             __syncthreads();
+            const CellCtx cc{C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
             for (uint32_t mm = tid; mm < npairs; mm += nt) {
                 const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
-                process_pair(a, &tab, s_cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
+                process_pair(a, tab, cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
                              a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
             }
-            __syncthreads();
         }
     }
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    big_end_of_step(a, cells, bk, wt);
+    big_end_of_step(a, L.cells, bk, wt, ls.removed != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1022,7 +1189,7 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
     const uint32_t step = step_index(a);
-    LocalStats ls = {0, 0, 0, 0, 0};
+    LocalStats ls = {0, 0, 0, 0, 0ull};
     load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;
     __syncthreads();
@@ -1032,12 +1199,32 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    big_end_of_step(a, cells, bb, wt);
+    big_end_of_step(a, cells, bb, wt, ls.removed != 0);
 }
 
 // ---------------------------------------------------------------------------
 // small utility kernels
 // ---------------------------------------------------------------------------
+// Per large cell: a power of two above the OR (so above the maximum) of the
+// multiplicities in its slots.  Coalescence never raises a multiplicity, so the
+// value bounds every later step until the state is replaced.
+__global__ void big_xpow_kernel(const uint64_t* __restrict__ xi, const BigCell* __restrict__ cells, float* xpow)
+{
+    __shared__ unsigned long long s_or[32];
+    const BigCell C = cells[blockIdx.x];
+    unsigned long long m = 0;
+    for (uint32_t i = threadIdx.x; i < C.width; i += blockDim.x) m |= xi[C.slot_begin + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0) s_or[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 1; w < (blockDim.x + 31) / 32; ++w) m |= s_or[w];
+        m |= s_or[0];
+        xpow[blockIdx.x] = m ? __uint_as_float((127u + 64u - (uint32_t)__clzll((long long)m)) << 23) : 1.0f;
+    }
+}
+
 __global__ void advance_step_kernel(uint32_t* d_step, uint32_t by)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *d_step += by;

@@ -73,20 +73,32 @@ __device__ __forceinline__ uint32_t lowbias32(uint32_t x)
     return x;
 }
 
+// lowbias32 after its first step (x ^= x >> 16).  The Feistel halves have at most
+// 16 bits, so (v ^ K) >> 16 = K >> 16 and lowbias32(v ^ K) = lowbias32_tail(v ^ Kx)
+// with Kx = K ^ (K >> 16): the first step is folded into the round key.
+__device__ __forceinline__ uint32_t lowbias32_tail(uint32_t x)
+{
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 struct Prp {
-    uint32_t K[PRP_ROUNDS];
+    uint32_t K[PRP_ROUNDS];       // folded round keys Kx = K ^ (K >> 16)
     uint32_t n, b, mask_a, mask_b;
 };
 
-__device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
-                                         uint32_t n)
+__device__ __forceinline__ uint32_t prp_bits(uint32_t n)
 {
-    const U4 x = philox(0u, cell, step, 2u, seed_lo, seed_hi);
-    const U4 y = philox(1u, cell, step, 2u, seed_lo, seed_hi);
-    P.K[0] = x.x; P.K[1] = x.y; P.K[2] = x.z; P.K[3] = x.w;
-    P.K[4] = y.x; P.K[5] = y.y; P.K[6] = y.z; P.K[7] = y.w;
-    uint32_t k = 0;
-    while (k < 32 && (1ull << k) < (uint64_t)n) ++k;
+    return n <= 1 ? 0u : 32u - (uint32_t)__clz(n - 1u);   // ceil(log2 n)
+}
+
+// domain [0, n): halves of floor(k/2) and k - floor(k/2) bits, k = ceil(log2 n)
+__device__ __forceinline__ void prp_set_domain(Prp& P, uint32_t n)
+{
+    const uint32_t k = prp_bits(n);
     const uint32_t a = k >> 1;
     P.n = n;
     P.b = k - a;
@@ -94,13 +106,24 @@ __device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed
     P.mask_b = (uint32_t)((1ull << P.b) - 1);
 }
 
+__device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
+                                         uint32_t n)
+{
+    const U4 x = philox(0u, cell, step, 2u, seed_lo, seed_hi);
+    const U4 y = philox(1u, cell, step, 2u, seed_lo, seed_hi);
+    const uint32_t K[PRP_ROUNDS] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int r = 0; r < (int)PRP_ROUNDS; ++r) P.K[r] = K[r] ^ (K[r] >> 16);
+    prp_set_domain(P, n);
+}
+
 __device__ __forceinline__ uint32_t feistel(const Prp& P, uint32_t q)
 {
     uint32_t L = q >> P.b, R = q & P.mask_b;
 #pragma unroll
     for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
-        L ^= lowbias32(R ^ P.K[r]) & P.mask_a;
-        R ^= lowbias32(L ^ P.K[r + 1]) & P.mask_b;
+        L ^= lowbias32_tail(R ^ P.K[r]) & P.mask_a;
+        R ^= lowbias32_tail(L ^ P.K[r + 1]) & P.mask_b;
     }
     return (L << P.b) | R;
 }
@@ -394,6 +417,13 @@ struct EffTab {
     float E[EFF_NR * EFF_NQ];
 };
 
+// the same table in global memory, for kernels that read it through L1 instead of staging it
+__device__ const EffTab g_eff_tab = {
+    {SDM_EFF_RADII(SDM_AS_FLOAT)},
+    {SDM_INV_DR(0), SDM_INV_DR(1), SDM_INV_DR(2), SDM_INV_DR(3), SDM_INV_DR(4), SDM_INV_DR(5), SDM_INV_DR(6),
+     SDM_INV_DR(7), SDM_INV_DR(8), SDM_INV_DR(9), SDM_INV_DR(10), 0.f},
+    {SDM_EFF_VALUES(SDM_AS_FLOAT)}};
+
 __device__ __forceinline__ void load_eff_tab(EffTab* T)
 {
     for (int k = threadIdx.x; k < EFF_NR * EFF_NQ; k += blockDim.x) T->E[k] = c_eff_Ef[k];
@@ -494,6 +524,51 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
     const uint64_t cap = xi_j / xi_k;
     *g = (uint64_t)gam < cap ? (uint64_t)gam : cap;
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Early exit of Step 3: an upper bound of p from the larger volume and the
+// larger multiplicity of a pair.  When phi >= bound >= p (and so p < 1),
+// gamma = floor(p) + [phi < p] = 0 and the pair needs no kernel evaluation.
+// The bound holds for the FP64 value and for the FP32 value alike.
+//   bins of the larger volume v: its double exponent e and two leading
+//   mantissa bits m, bin = 4 (e - PB_EMIN) + m covering
+//   [2^e (1 + m/4), 2^e (1 + (m+1)/4)); volumes below the first bin share
+//   its bound (both kernels grow with v), volumes above the last have none.
+//   table[kind][bin]:  Golovin: the bin's upper edge (K = b (v1 + v2) <= 2 b v);
+//   gravitational: pi (2 r)^2 vt(r) max E over the table rows the bin's radii
+//   touch, r the bin's upper radius (r1 + r2 <= 2 r, |vt1 - vt2| <= vt(r)),
+//   times 1 + 2^-10, rounded up to float.  Filled by the host once per device.
+//   p <= table * c_up * X with c_up = S dt/dV (* 2b for Golovin) * (1 + 2^-8)
+//   rounded up and X a power of two above max(xi1, xi2) -- per pair
+//   2^(64 - clz(xi1 | xi2)), or per cell 2^(64 - clz(OR of its multiplicities)),
+//   which stays valid for every later step because coalescence never raises a
+//   multiplicity; the margins cover the FP32 scale's roundings and the FP32
+//   path's own error.
+// ---------------------------------------------------------------------------
+constexpr int PB_EMIN = -80;
+constexpr uint32_t PB_NB = 4 * 72;                               // exponents -80 .. -9
+constexpr uint32_t PB_HI0 = (uint32_t)(1023 + PB_EMIN) << 2;      // (high word >> 18) of bin 0
+__device__ float g_pbound[2][PB_NB + 1];                          // [kind][PB_NB] = +inf
+
+// bin of the larger of two non-negative volumes from their high words (PB_NB: no bound)
+__device__ __forceinline__ uint32_t pb_bin(uint32_t hi1, uint32_t hi2)
+{
+    const uint32_t h = max(hi1, hi2) >> 18;      // non-negative doubles order as their high words
+    return h < PB_HI0 ? 0u : min(h - PB_HI0, PB_NB);
+}
+
+// 2^(64 - clz(x1 | x2)) > max(x1, x2) as a float (x1 | x2 != 0, both < 2^53)
+__device__ __forceinline__ float xi_pow2_above(uint64_t x1, uint64_t x2)
+{
+    const uint32_t lz = (uint32_t)__clzll((long long)(x1 | x2));
+    return __uint_as_float((127u + 64u - lz) << 23);
+}
+
+// phi's leading 23 bits as a float phi_lo <= phi; w_hi = the high Philox word of the pair's phi
+__device__ __forceinline__ float phi_lo23(uint32_t w_hi)
+{
+    return __uint_as_float(0x3F800000u | (w_hi >> 9)) - 1.0f;
 }
 
 // FP32 mode: gamma from p32 and the leading 23 bits of phi.
