@@ -245,15 +245,18 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n);
 
 /* Evaluate, for n pairs (v1[i], v2[i]) with multiplicities (xi1[i], xi2[i]) in
  * a cell of n_cell_sd live SDs and volume dv, the collision kernel and eq.
- * (p) both ways: p64[i] is the FP64 value the library uses when it
- * re-evaluates a pair (bit-identical to the documented operation order), and
- * p32[i], err32[i] the FP32 value and its error bound, |p64 - p32| <= err32.
- * All arrays are device pointers.  Exposes Step 2 alone for testing
- * (dependency injection, Sec. 5). */
+ * (p) the ways the library does: p64[i] is the FP64 value the library uses
+ * when it re-evaluates a pair (bit-identical to the documented operation
+ * order); p32[i], err32[i] the FP32 value and its error bound,
+ * |p64 - p32| <= err32; plite[i], errlite[i] (nullable; gravitational kernel)
+ * the second filter's FP64 value from refined FP32 seeds and its bound,
+ * |p64 - plite| <= errlite (errlite < 0: not applicable to this pair).  All
+ * arrays are device pointers.  Exposes Step 2 alone for testing (dependency
+ * injection, Sec. 5). */
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2,
                           const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd,
                           double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32);
+                          double* p64, float* p32, float* err32, double* plite, double* errlite);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free single-box step.  (No counterpart in the paper: this is a

@@ -1058,14 +1058,15 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n)
 
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2, const uint64_t* xi1,
                           const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32)
+                          double* p64, float* p32, float* err32, double* plite, double* errlite)
 {
     if (!st || !v1 || !v2 || !xi1 || !xi2 || !p64 || !p32 || !err32) return SDM_EINVAL;
     if (kernel_id > SDM_KERNEL_GRAVITATIONAL || n_cell_sd < 2 || !(dv > 0) || !(dt > 0)) return SDM_EINVAL;
     if (n == 0) return SDM_OK;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 8 * (uint64_t)st->n_sm);
+    if ((plite == nullptr) != (errlite == nullptr)) return SDM_EINVAL;
     eval_pairs_kernel<<<grid, 256, 0, st->stream>>>(kernel_id, v1, v2, xi1, xi2, n, n_cell_sd, dv, dt, golovin_b, p64,
-                                                    p32, err32);
+                                                    p32, err32, plite, errlite);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }

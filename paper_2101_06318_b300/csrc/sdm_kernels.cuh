@@ -116,7 +116,8 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
     if (a.precision == PREC_FP32) {
         g = gamma_tilde_f(pe.p, u53, xj, xk);
     } else if (!gamma_tilde_certified(pe, u53, xj, xk, &g)) {
-        g = gamma_tilde_fp64_path(c.kid, v1, v2, a.golovin_b, c.n, a.dt, c.dv, u53, xj, xk);
+        if (c.kid == 0 || !gamma_tilde_lite(v1, v2, c.n, a.dt, c.dv, u53, xj, xk, &g))
+            g = gamma_tilde_fp64_path(c.kid, v1, v2, a.golovin_b, c.n, a.dt, c.dv, u53, xj, xk);
         ls.fp64++;
     }
     ls.pairs++;
@@ -1274,7 +1275,8 @@ __global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* _
 
 __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* v2, const uint64_t* xi1,
                                   const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt,
-                                  double golovin_b, double* p64, float* p32, float* err32)
+                                  double golovin_b, double* p64, float* p32, float* err32, double* plite,
+                                  double* errlite)
 {
     __shared__ EffTab tab;
     load_eff_tab(&tab);
@@ -1287,6 +1289,12 @@ __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* 
         const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b);
         p32[i] = pe.p;
         err32[i] = pe.err;
+        if (plite) {
+            double pl = 0.0, el = -1.0;
+            if (kid == 1) pair_prob_lite(v1[i], v2[i], xmax, n_cell_sd, dt, dv, pl, el);
+            plite[i] = pl;
+            errlite[i] = el;
+        }
     }
 }
 

@@ -240,6 +240,16 @@ __device__ __forceinline__ double vt_d(double r)
     return __dmul_rn(VT_K3, __dsqrt_rn(r));
 }
 
+// interval index i with R[i] <= R < R[i+1], for R[0] < R < R[EFF_NR-1]: the
+// comparisons are independent (FP64 compares have long latency on B300)
+__device__ __forceinline__ int eff_interval_d(double R)
+{
+    int i = 0;
+#pragma unroll
+    for (int k = 1; k < EFF_NR - 1; ++k) i += (R >= c_eff_R[k]) ? 1 : 0;
+    return i;
+}
+
 __device__ __forceinline__ double efficiency_d(double R, double q)
 {
     int i;
@@ -249,12 +259,11 @@ __device__ __forceinline__ double efficiency_d(double R, double q)
     } else if (R >= c_eff_R[EFF_NR - 1]) {
         i = EFF_NR - 2; t = 1.0;
     } else {
-        i = 0;
-        while (c_eff_R[i + 1] <= R) ++i;
+        i = eff_interval_d(R);
         t = __ddiv_rn(__dsub_rn(R, c_eff_R[i]), __dsub_rn(c_eff_R[i + 1], c_eff_R[i]));
     }
     const double s = __dmul_rn(q, 10.0);
-    int j = (int)floor(s);
+    int j = __double2int_rz(s);                        // floor: s >= 0
     double w;
     if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.0; }
     else w = __dsub_rn(s, (double)j);
@@ -326,6 +335,120 @@ __device__ __noinline__ uint64_t gamma_tilde_fp64_path(uint32_t kid, double v1, 
     const double K = kernel_d(kid, v1, v2, golovin_b);
     const double p = pair_prob_d(K, xi_j, n, dt, dv);
     return gamma_tilde_d(p, u53, xi_j, xi_k);
+}
+
+// ---------------------------------------------------------------------------
+// Second filter for the gravitational kernel: p in FP64 from FP32 seeds refined
+// by Newton steps -- multiplications and FMAs only, a short dependency chain
+// (B300 runs FP64 with long latency, and a division costs several hundred
+// cycles) -- with a bound on its distance to the exact sequence's value.  The
+// exact sequence above runs only when this interval cannot decide gamma.
+//   Error budget relative to B = scale pi (r1+r2)^2 (vt1 + vt2) (u = 2^-53):
+//   radii after two Newton steps from cbrtf (|r0/r - 1| <= 2^-21): within
+//   ~8u of the true cube root (the exact sequence: 1 ulp); (r1+r2)^2, the
+//   fall speeds and their difference: ~40u B; q = rs (1/R) with a refined
+//   reciprocal and t = (R - R_i) (1/dR_i): weights off by ~200u, times table
+//   steps <= 1 -> ~250u B; scale with a refined reciprocal of dV: ~10u.  In
+//   all well below 1000u B = 2^-43 B; the bound used is 2^-36 B.
+// ---------------------------------------------------------------------------
+constexpr double LITE_REL_BOUND = 0x1p-36;
+__constant__ double c_eff_invdR[EFF_NR] = {
+    1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (20e-6),
+    1.0 / (20e-6), 1.0 / (50e-6), 1.0 / (50e-6), 1.0 / (100e-6), 1.0 / (700e-6), 0.0};
+
+// 1/d to about 2^-46 relative (d a normal float-range double)
+__device__ __forceinline__ double rcp_lite(double d)
+{
+    const double y0 = (double)__frcp_rn((float)d);
+    const double e = __fma_rn(-d, y0, 1.0);
+    return __fma_rn(y0, e, y0);
+}
+
+__device__ __forceinline__ double cbrt_lite(double x)
+{
+    const float xf = (float)x;
+    double r = (double)cbrtf(xf);
+    const double h = (double)__frcp_rn(3.0f * __fmul_rn((float)r, (float)r));   // ~ 1 / (3 r^2)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) r = __fma_rn(-__fma_rn(r * r, r, -x), h, r);
+    return r;
+}
+
+__device__ __forceinline__ double vt_lite(double r)
+{
+    if (r < VT_R12) return VT_K1 * r * r;
+    if (r < VT_R23) return VT_K2 * r;
+    double y = (double)rsqrtf((float)r);               // 1 / sqrt(r)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) y = __fma_rn(0.5 * y, __fma_rn(-r * y, y, 1.0), y);
+    return VT_K3 * (r * y);
+}
+
+__device__ __forceinline__ double efficiency_lite(double R, double q)
+{
+    int i;
+    double t;
+    if (R <= c_eff_R[0]) { i = 0; t = 0.0; }
+    else if (R >= c_eff_R[EFF_NR - 1]) { i = EFF_NR - 2; t = 1.0; }
+    else {
+        i = eff_interval_d(R);
+        t = (R - c_eff_R[i]) * c_eff_invdR[i];
+    }
+    const double s = q * 10.0;
+    int j = __double2int_rz(s);
+    double w;
+    if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.0; }
+    else w = s - (double)j;
+    const double* E = c_eff_E;
+    const double e0 = E[i * EFF_NQ + j] + w * (E[i * EFF_NQ + j + 1] - E[i * EFF_NQ + j]);
+    const double e1 = E[(i + 1) * EFF_NQ + j] + w * (E[(i + 1) * EFF_NQ + j + 1] - E[(i + 1) * EFF_NQ + j]);
+    return e0 + t * (e1 - e0);
+}
+
+// p of the gravitational kernel and its bound (err < 0: not applicable, use the exact sequence)
+__device__ __forceinline__ void pair_prob_lite(double v1, double v2, uint64_t xmax, uint32_t n, double dt, double dv,
+                                               double& p, double& err)
+{
+    err = -1.0;
+    p = 0.0;
+    const double vmin = fmin(v1, v2), vmax = fmax(v1, v2);
+    if (!(vmin >= 0x1p-110) || !(vmax <= 0x1p+60) || !(dv >= 0x1p-100) || !(dv <= 0x1p+100)) return;
+    const double r1 = cbrt_lite(__dmul_rn(v1, THREE_OVER_FOUR_PI)), r2 = cbrt_lite(__dmul_rn(v2, THREE_OVER_FOUR_PI));
+    const double vt1 = vt_lite(r1), vt2 = vt_lite(r2);
+    const double R = fmax(r1, r2), rs = fmin(r1, r2);
+    const double E = efficiency_lite(R, rs * rcp_lite(R));
+    const double sr = r1 + r2;
+    const double a = PI_D * (sr * sr);
+    const double scale = ((double)xmax * (double)(n - 1u + (n & 1u))) * (dt * rcp_lite(dv));
+    p = ((a * fabs(vt1 - vt2)) * E) * scale;
+    err = ((a * (vt1 + vt2)) * scale) * LITE_REL_BOUND + 0x1p-1000;
+}
+
+// gamma~ from the second filter; false when the interval does not settle it
+__device__ __noinline__ bool gamma_tilde_lite(double v1, double v2, uint32_t n, double dt, double dv, uint64_t u53,
+                                              uint64_t xi_j, uint64_t xi_k, uint64_t* g)
+{
+    double p, err;
+    pair_prob_lite(v1, v2, xi_j, n, dt, dv, p, err);
+    if (!(err >= 0.0) || !(p >= 0.0)) return false;
+    const double lo = fmax(__dsub_rd(p, err), 0.0), hi = __dadd_ru(p, err);
+    if (!(hi < 0x1p52)) return false;
+    // floors of non-negative doubles below 2^52 by a round-down add of 2^52
+    const double fl = __dsub_rn(__dadd_rd(lo, 0x1p52), 0x1p52);
+    if (__dsub_rn(__dadd_rd(hi, 0x1p52), 0x1p52) != fl) {
+        const uint64_t cap = xi_j / xi_k;
+        if (fl >= 1.0 && (uint64_t)fl >= cap) { *g = cap; return true; }   // floor(p) >= floor(lo) >= cap
+        return false;
+    }
+    const double phi = (double)u53 * 0x1p-53;      // exact
+    uint64_t d;
+    if (phi < lo - fl) d = 1;                      // phi < frac(p)   (lo - fl, hi - fl are exact)
+    else if (phi >= hi - fl) d = 0;                // phi >= frac(p)
+    else return false;
+    const uint64_t gam = (uint64_t)fl + d;
+    const uint64_t cap = gam <= 1 ? gam : xi_j / xi_k;
+    *g = gam < cap ? gam : cap;
+    return true;
 }
 
 // ---------------------------------------------------------------------------

@@ -98,7 +98,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_sync.argtypes = [vp]
         L.sdm_free.argtypes = [vp]
         L.sdm_free.restype = None
-        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp]
+        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp, vp, vp]
         L.sdm_set_profiling.argtypes = [vp, i32]
         L.sdm_get_profile.argtypes = [vp, vp, vp]
         L.sdm_launches_per_step.argtypes = [vp, vp]
@@ -285,18 +285,23 @@ class State:
         return int(n.value)
 
     # -- Step 2 alone (testing) ---------------------------------------------------
-    def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0):
-        """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors."""
+    def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0, lite=False):
+        """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors, and with lite=True
+        also the second filter's (plite, errlite)."""
         torch = _torch()
         n = v1.numel()
         p64 = torch.empty(n, dtype=torch.float64, device=v1.device)
         p32 = torch.empty(n, dtype=torch.float32, device=v1.device)
         e32 = torch.empty(n, dtype=torch.float32, device=v1.device)
+        pl = torch.empty(n, dtype=torch.float64, device=v1.device) if lite else None
+        el = torch.empty(n, dtype=torch.float64, device=v1.device) if lite else None
         _check(self._L.sdm_eval_pairs(self._h, int(kernel_id), C.c_void_p(v1.data_ptr()), C.c_void_p(v2.data_ptr()),
                                       C.c_void_p(xi1.data_ptr()), C.c_void_p(xi2.data_ptr()), n, int(n_cell_sd),
                                       float(dv), float(dt), float(golovin_b), C.c_void_p(p64.data_ptr()),
-                                      C.c_void_p(p32.data_ptr()), C.c_void_p(e32.data_ptr())), "sdm_eval_pairs")
-        return p64, p32, e32
+                                      C.c_void_p(p32.data_ptr()), C.c_void_p(e32.data_ptr()),
+                                      C.c_void_p(pl.data_ptr() if lite else None),
+                                      C.c_void_p(el.data_ptr() if lite else None)), "sdm_eval_pairs")
+        return (p64, p32, e32, pl, el) if lite else (p64, p32, e32)
 
 
 def from_inputs(s, n_attr=1, extra_attrs=None, stream=None, device_arrays=False):

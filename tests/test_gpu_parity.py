@@ -228,6 +228,17 @@ def test_fp32_bound_holds_and_fp64_matches_oracle():
         assert np.all(np.abs(p64 - p32) <= e32), (kid, ratio.max())
     # the bound is not vacuous either: it is used at well under its full width
     assert worst < 0.5, worst
+    # the second filter (gravitational kernel): its FP64 value from refined FP32 seeds stays within
+    # its bound of the exact sequence's value, also at regime joins, table nodes and near-equal radii
+    worst_lite = 0.0
+    for ncell, dv in ((1 << 20, 1e6), (127, 1e3)):
+        p64, _, _, pl, el = g.eval_pairs(1, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv, lite=True)
+        p64, pl, el = p64.cpu().numpy(), pl.cpu().numpy(), el.cpu().numpy()
+        ok = el >= 0
+        assert ok.mean() > 0.99
+        assert np.all(np.abs(p64[ok] - pl[ok]) <= el[ok])
+        worst_lite = max(worst_lite, float((np.abs(p64[ok] - pl[ok]) / el[ok]).max()))
+    assert worst_lite < 0.01, worst_lite
 
 
 def test_fp32_mode_close_to_fp64():
