@@ -19,7 +19,6 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
-import glob
 import json
 import os
 import statistics
@@ -108,10 +107,9 @@ class ClockSampler:
 
 
 def _source_hash():
-    """sha256 over the per-file sha256 lines of the CUDA sources and the C header."""
+    """sha256 over the per-file sha256 lines of the device-code headers (the kernels' source)."""
     import hashlib
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2101_06318_b300", "csrc", "*")))
-    files.append(os.path.join(ROOT, "include", "sdm.h"))
+    files = [os.path.join(ROOT, "paper_2101_06318_b300", "csrc", f) for f in ("sdm_kernels.cuh", "sdm_math.cuh")]
     lines = []
     for f in files:
         with open(f, "rb") as fh:

@@ -240,8 +240,9 @@ sdm_status sdm_set_profiling(sdm_state* st, int enable);
 sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms);
 
 /* Number of kernel launches one timestep enqueues with the current schedule
- * (a d_step step adds one more for the counter). */
-sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n);
+ * and the given shuffle contract (sdm_shuffle); a d_step step adds one more
+ * for the counter.  SDM_EINVAL for a null pointer or an unknown contract. */
+sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n);
 
 /* Evaluate, for n pairs (v1[i], v2[i]) with multiplicities (xi1[i], xi2[i]) in
  * a cell of n_cell_sd live SDs and volume dv, the collision kernel and eq.

@@ -250,7 +250,8 @@ uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
 sdm_status refresh_big_bounds(sdm_state* st)
 {
     if (!st->n_big) return SDM_OK;
-    big_xpow_kernel<<<st->n_big, 256, 0, st->stream>>>(st->d_xi, st->d_big, st->d_big_xpow);
+    SDM_CUDA(cudaMemsetAsync(st->d_big_xpow, 0, sizeof(float) * st->n_big, st->stream));
+    big_xpow_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_big, st->d_chunks, (uint32_t*)st->d_big_xpow);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }
@@ -1049,10 +1050,11 @@ sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms)
     return SDM_OK;
 }
 
-sdm_status sdm_launches_per_step(sdm_state* st, uint32_t* n)
+sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 {
-    if (!st || !n) return SDM_EINVAL;
-    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? 2u : 0u);   // PRP contract: 1 large-cell kernel
+    if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
+    // tiles: one kernel; large cells: one kernel (PRP contract) or scatter + finish (SORT contract)
+    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);
     return SDM_OK;
 }
 
@@ -1174,8 +1176,11 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
     float* d_xpow = (float*)(base + NA_OFF_XPOW);
-    if (p->shuffle == SDM_SHUFFLE_PRP)
-        big_xpow_kernel<<<1, 256, 0, stream>>>(xi, (const BigCell*)(base + NA_OFF_CELL), d_xpow);
+    if (p->shuffle == SDM_SHUFFLE_PRP) {
+        SDM_CUDA(cudaMemsetAsync(d_xpow, 0, sizeof(float), stream));
+        big_xpow_kernel<<<n_chunks, 256, 0, stream>>>(xi, (const BigCell*)(base + NA_OFF_CELL),
+                                                      (const BigChunk*)(base + NA_OFF_CHUNKS), (uint32_t*)d_xpow);
+    }
 
     StepArgs a{};
     a.xi = xi;

@@ -648,8 +648,12 @@ constexpr uint32_t PRP_WARPS = PRP_THREADS / 32;
 #ifndef SDM_PRP_MIN_BLOCKS
 #define SDM_PRP_MIN_BLOCKS 2
 #endif
+#ifndef SDM_PRP_QPT
+#define SDM_PRP_QPT 4
+#endif
+constexpr uint32_t PRP_QPT = SDM_PRP_QPT;      // quads per thread and iteration
 constexpr uint32_t BIG_PARAM_CELLS = 8;        // large cells passed by value in the launch
-constexpr uint32_t PQ_CAP = 160;               // queued pairs per warp (< 32 left + 4 x 32 new)
+constexpr uint32_t PQ_CAP = 32 + 2 * 32 * PRP_QPT;   // queued pairs per warp (< 32 left + 2 per quad)
 
 struct BigLaunch {
     uint32_t n_big, n_quads;
@@ -664,38 +668,40 @@ struct PairQueue {
     unsigned long long u[PQ_CAP];
 };
 
-// eight Feistel evaluations with shared round keys (two quads)
-__device__ __forceinline__ void feistel8(const Prp& P, uint32_t (&x)[8])
+// N Feistel evaluations with shared round keys (independent chains)
+template <int N>
+__device__ __forceinline__ void feistel_n(const Prp& P, uint32_t (&x)[N])
 {
-    uint32_t L[8], R[8];
+    uint32_t L[N], R[N];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) { L[i] = x[i] >> P.b; R[i] = x[i] & P.mask_b; }
+    for (int i = 0; i < N; ++i) { L[i] = x[i] >> P.b; R[i] = x[i] & P.mask_b; }
 #pragma unroll
     for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) L[i] ^= lowbias32_tail(R[i] ^ P.K[r]) & P.mask_a;
+        for (int i = 0; i < N; ++i) L[i] ^= lowbias32_tail(R[i] ^ P.K[r]) & P.mask_a;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) R[i] ^= lowbias32_tail(L[i] ^ P.K[r + 1]) & P.mask_b;
+        for (int i = 0; i < N; ++i) R[i] ^= lowbias32_tail(L[i] ^ P.K[r + 1]) & P.mask_b;
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = (L[i] << P.b) | R[i];
+    for (int i = 0; i < N; ++i) x[i] = (L[i] << P.b) | R[i];
 }
 
 // cycle-walking (only when n is not a power of two) of the images whose bit in
 // 'use' is set; the others (positions >= n) never walk
-__device__ __forceinline__ void prp_walk8(const Prp& P, uint32_t use, uint32_t (&e)[8])
+template <int N>
+__device__ __forceinline__ void prp_walk_n(const Prp& P, uint32_t use, uint32_t (&e)[N])
 {
     for (;;) {
         uint32_t walk = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) walk |= (((use >> i) & 1u) && e[i] >= P.n) ? (1u << i) : 0u;
+        for (int i = 0; i < N; ++i) walk |= (((use >> i) & 1u) && e[i] >= P.n) ? (1u << i) : 0u;
         if (!walk) break;
-        uint32_t f[8];
+        uint32_t f[N];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) f[i] = e[i];
-        feistel8(P, f);
+        for (int i = 0; i < N; ++i) f[i] = e[i];
+        feistel_n<N>(P, f);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < N; ++i)
             if ((walk >> i) & 1u) e[i] = f[i];
     }
 }
@@ -790,47 +796,48 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
             const float c_upx =
                 __fmul_ru(__fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, a.golovin_bf) : 1.0f), 1.0f + 0x1p-8f),
                           xpow);
-            // two quads per thread and iteration: g and g + 32 (warp-uniform trip count)
-            for (uint32_t base = sa + warp * 64; base < sb; base += 2 * nt) {
-                uint32_t e[8], qj[2];
+            // PRP_QPT quads per thread and iteration: g, g + 32, ... (warp-uniform trip count)
+            constexpr int NP = 4 * PRP_QPT;            // positions per thread and iteration
+            for (uint32_t base = sa + warp * 32 * PRP_QPT; base < sb; base += PRP_QPT * nt) {
+                uint32_t e[NP], qj[PRP_QPT];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < (int)PRP_QPT; ++j) {
                     qj[j] = base + 32 * j + lane - C.quad_begin;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
                 }
-                feistel8(P, e);
+                feistel_n<NP>(P, e);
                 if (!same_bits) {            // uniform: the live count left the width's power of two
                     prp_set_domain(P, n);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j)
+                    for (int j = 0; j < (int)PRP_QPT; ++j)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
-                    feistel8(P, e);
+                    feistel_n<NP>(P, e);
                 } else {
                     P.n = n;
                 }
-                bool h0[2], h1[2];
+                bool h0[PRP_QPT], h1[PRP_QPT];
                 uint32_t use = 0;
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < (int)PRP_QPT; ++j) {
                     h0[j] = base + 32 * j + lane < sb && 2 * qj[j] < npairs;
                     h1[j] = h0[j] && 2 * qj[j] + 1 < npairs;
                     use |= (h0[j] ? 3u : 0u) << (4 * j);
                     use |= (h1[j] ? 12u : 0u) << (4 * j);
                 }
-                prp_walk8(P, use, e);
+                prp_walk_n<NP>(P, use, e);
                 // gather the volumes' high words (all the early exit needs with the cell's
                 // multiplicity bound), then phi while they are in flight
-                uint32_t vh[8];
+                uint32_t vh[NP];
                 const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < NP; ++i) {
                     e[i] += C.slot_begin;              // slots from here on
                     vh[i] = ((use >> i) & 1u) ? attr_hi[2 * (size_t)e[i]] : 0u;
                 }
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < (int)PRP_QPT; ++j) {
                     U4 w = {0, 0, 0, 0};
                     if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.seed_lo, a.seed_hi);
                     exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
@@ -1208,21 +1215,24 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
 // ---------------------------------------------------------------------------
 // Per large cell: a power of two above the OR (so above the maximum) of the
 // multiplicities in its slots.  Coalescence never raises a multiplicity, so the
-// value bounds every later step until the state is replaced.
-__global__ void big_xpow_kernel(const uint64_t* __restrict__ xi, const BigCell* __restrict__ cells, float* xpow)
+// value bounds every later step until the state is replaced.  One CTA per
+// chunk of a large cell; xpow_bits (float bits, zeroed before) takes the
+// maximum over the chunks (positive floats order as their bit patterns).
+__global__ void big_xpow_kernel(const uint64_t* __restrict__ xi, const BigCell* __restrict__ cells,
+                                const BigChunk* __restrict__ chunks, uint32_t* xpow_bits)
 {
     __shared__ unsigned long long s_or[32];
-    const BigCell C = cells[blockIdx.x];
+    const BigChunk K = chunks[blockIdx.x];
+    const BigCell C = cells[K.big];
     unsigned long long m = 0;
-    for (uint32_t i = threadIdx.x; i < C.width; i += blockDim.x) m |= xi[C.slot_begin + i];
+    for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x) m |= xi[C.slot_begin + i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
     if ((threadIdx.x & 31) == 0) s_or[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (uint32_t w = 1; w < (blockDim.x + 31) / 32; ++w) m |= s_or[w];
-        m |= s_or[0];
-        xpow[blockIdx.x] = m ? __uint_as_float((127u + 64u - (uint32_t)__clzll((long long)m)) << 23) : 1.0f;
+        if (m) atomicMax(&xpow_bits[K.big], (127u + 64u - (uint32_t)__clzll((long long)m)) << 23);
     }
 }
 

@@ -101,7 +101,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp, vp, vp]
         L.sdm_set_profiling.argtypes = [vp, i32]
         L.sdm_get_profile.argtypes = [vp, vp, vp]
-        L.sdm_launches_per_step.argtypes = [vp, vp]
+        L.sdm_launches_per_step.argtypes = [vp, u32, vp]
         L.sdm_coalescence_step_noalloc.argtypes = [vp, vp, u32, u64, u32, f64, u32, C.POINTER(StepParams), vp]
         for name in EXPORTS:
             if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free"):
@@ -279,9 +279,9 @@ class State:
         _check(self._L.sdm_get_profile(self._h, n, ms), "sdm_get_profile")
         return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 
-    def launches_per_step(self):
+    def launches_per_step(self, shuffle="prp"):
         n = C.c_uint32()
-        _check(self._L.sdm_launches_per_step(self._h, C.byref(n)), "sdm_launches_per_step")
+        _check(self._L.sdm_launches_per_step(self._h, SHUFFLE[shuffle], C.byref(n)), "sdm_launches_per_step")
         return int(n.value)
 
     # -- Step 2 alone (testing) ---------------------------------------------------
