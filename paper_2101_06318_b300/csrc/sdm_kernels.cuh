@@ -607,8 +607,12 @@ __device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ c
     __shared__ unsigned long long s_old;
     const bool any = __syncthreads_or(had_removal);
     if (threadIdx.x == 0) {
-        __threadfence();
-        s_old = atomicAdd(bk.ticket, 1ull + (any ? (1ull << 32) : 0ull));
+        // release: this CTA's updates (ordered before by the barrier) become visible to the
+        // CTA that sees the last ticket; acquire: that CTA sees everybody's
+        unsigned long long old;
+        const unsigned long long inc = 1ull + (any ? (1ull << 32) : 0ull);
+        asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(bk.ticket), "l"(inc) : "memory");
+        s_old = old;
     }
     __syncthreads();
     const unsigned long long old = s_old;
@@ -668,19 +672,25 @@ struct PairQueue {
     unsigned long long u[PQ_CAP];
 };
 
-// N Feistel evaluations with shared round keys (independent chains)
+// N Feistel evaluations with shared round keys (independent chains).  The rounds
+// are a loop with the keys rotated through registers, not unrolled: with the
+// state flushed from L2 before every step the instructions are fetched from
+// DRAM each time, and straight-line code of all rounds stalls on the fetch.
 template <int N>
 __device__ __forceinline__ void feistel_n(const Prp& P, uint32_t (&x)[N])
 {
     uint32_t L[N], R[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) { L[i] = x[i] >> P.b; R[i] = x[i] & P.mask_b; }
-#pragma unroll
+    uint32_t k0 = P.K[0], k1 = P.K[1], k2 = P.K[2], k3 = P.K[3], k4 = P.K[4], k5 = P.K[5], k6 = P.K[6],
+             k7 = P.K[7];
+#pragma unroll 1
     for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) L[i] ^= lowbias32_tail(R[i] ^ P.K[r]) & P.mask_a;
+        for (int i = 0; i < N; ++i) L[i] ^= lowbias32_tail(R[i] ^ k0) & P.mask_a;
 #pragma unroll
-        for (int i = 0; i < N; ++i) R[i] ^= lowbias32_tail(L[i] ^ P.K[r + 1]) & P.mask_b;
+        for (int i = 0; i < N; ++i) R[i] ^= lowbias32_tail(L[i] ^ k1) & P.mask_b;
+        k0 = k2; k1 = k3; k2 = k4; k3 = k5; k4 = k6; k5 = k7;
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) x[i] = (L[i] << P.b) | R[i];
@@ -769,6 +779,16 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
     }
     LocalStats ls = {0, 0, 0, 0, 0ull};
     if (tid < 5) red[tid] = 0;
+    // the bound table (read right after the gathers) and the efficiency table (read by the
+    // queued evaluations) are cold after other work evicted L2: start fetching them now
+    if (warp == 0) {
+        constexpr uint32_t PB_LINES = (uint32_t)((sizeof(g_pbound) + 127) / 128);
+        constexpr uint32_t EFF_LINES = (uint32_t)((sizeof(EffTab) + 127) / 128);
+        if (lane < PB_LINES)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(g_pbound) + 128 * lane));
+        else if (lane < PB_LINES + EFF_LINES)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(tab) + 128 * (lane - PB_LINES)));
+    }
     PairQueue& Q = pq[warp];
     uint32_t qcnt = 0;                              // queued pairs of this warp (warp-uniform)
     for (; qa < qb && c < L.n_big; ++c) {
