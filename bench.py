@@ -197,6 +197,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(tot_ms, sd_steps, e2e_s, dist, world, device):
+    """Whole-job figures from every rank's own: the slowest rank's timed span (max), the SD-steps
+    of all ranks (sum) and the slowest end-to-end step (max).  One all_gather; no collective
+    touches the data path."""
+    if not dist or world == 1:
+        return tot_ms, sd_steps, e2e_s
+    import torch
+    t = torch.tensor([tot_ms, sd_steps, e2e_s], dtype=torch.float64, device=device)
+    ts = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(ts, t)
+    return (max(float(x[0]) for x in ts), sum(float(x[1]) for x in ts), max(float(x[2]) for x in ts))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2101_06318_b300 import sdm
@@ -276,17 +289,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         bytes_io = xi_p.numel() * 8 + at_p.numel() * 8
 
-    # max over ranks
-    tot_ms = ms * args.steps
-    if dist:
-        t = torch.tensor([tot_ms, sd_steps, e2e_s], dtype=torch.float64, device=dev)
-        ts = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(ts, t)
-        tot_ms = max(float(x[0]) for x in ts)
-        sd_total = sum(float(x[1]) for x in ts)
-        e2e_s = max(float(x[2]) for x in ts)
-    else:
-        sd_total = sd_steps
+    tot_ms, sd_total, e2e_s = combine_ranks(ms * args.steps, sd_steps, e2e_s, dist, world, dev)
     if rank != 0:
         return
     value = sd_total / (tot_ms * 1e-3)
