@@ -325,7 +325,7 @@ sdm_status build_layout(sdm_state* st)
         const uint32_t need = (st->n_buckets_planned + fl.warps - 1) / fl.warps;
         st->fin_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
     }
-    st->tile_L = tile_layout(S.tile_slots, max_cells);
+    st->tile_L = tile_layout(S.tile_slots, max_cells, S.tile_threads / 32);
     st->max_cells_per_tile = max_cells;
     if (st->tile_L.bytes > 227 * 1024) return SDM_ECAPACITY;
     SDM_TRY(upload(st, &st->d_tiles, tiles));

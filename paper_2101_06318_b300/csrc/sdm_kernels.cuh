@@ -85,6 +85,12 @@ struct CellCtx {
     double dv;
 };
 
+// early-exit scale of a cell without its multiplicity factor (see pb_bin)
+__device__ __forceinline__ float exit_scale(float s32, uint32_t kid, float golovin_bf)
+{
+    return __fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, golovin_bf) : 1.0f), 1.0f + 0x1p-8f);
+}
+
 __device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, float dt_f, double dv)
 {
     // ((n^2 - n)/2) / floor(n/2) is n - 1 (n even) or n (n odd): exact integer
@@ -245,17 +251,23 @@ __host__ __device__ __forceinline__ uint32_t ceil_log2(uint32_t w)
 // ---------------------------------------------------------------------------
 // Tile kernel: whole small cells in shared memory.
 // ---------------------------------------------------------------------------
+constexpr uint32_t TQ_CAP = 96;   // tile kernel: queued pairs per warp (< 32 left + 2 x 32 new)
+struct TileQueue {                 // local slots of the pair, cell index in the tile, phi integer
+    uint32_t ii[TQ_CAP], c[TQ_CAP];
+    unsigned long long u[TQ_CAP];
+};
+
 struct TileLayout {
     uint32_t tile_slots, max_cells;
     // byte offsets
     uint32_t o_xi, o_v, o_key, o_bo, o_cnt, o_tmp, o_srt, o_cs, o_gb, o_bb, o_pb, o_ss, o_nb, o_n, o_rem, o_pp, o_ctx, o_red,
-        o_wt, o_tab;
+        o_wt, o_tab, o_cup, o_q;
     uint32_t bytes;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t max_cells)
+__host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t max_cells, uint32_t n_warps)
 {
     TileLayout L;
     L.tile_slots = tile_slots;
@@ -281,6 +293,8 @@ __host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t 
     L.o_red = o; o = align_up(o + 8 * 8, 16);
     L.o_wt = o;  o = align_up(o + 4 * 40, 16);
     L.o_tab = o; o = align_up(o + (uint32_t)sizeof(EffTab), 16);
+    L.o_cup = o; o = align_up(o + 4 * (max_cells + 1), 16);
+    L.o_q = o;   o = align_up(o + (uint32_t)sizeof(TileQueue) * n_warps, 16);
     L.bytes = o;
     return L;
 }
@@ -367,6 +381,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     CellCtx* ctx = (CellCtx*)(smem + L.o_ctx);
     uint32_t* wt = (uint32_t*)(smem + L.o_wt);
     const EffTab* tab = (const EffTab*)(smem + L.o_tab);
+    float* cup = (float*)(smem + L.o_cup);
 
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t ns = td.slot_end - td.slot_begin, nc = td.n_cells;
@@ -460,6 +475,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         cc.dv = a.dv[gid];
         cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, cc.dv) : 0.f;
         ctx[c] = cc;
+        cup[c] = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf);
         pb[c] = (n >> 1) + 1u >> 1;              // groups of two pairs (one Philox call each)
     }
     __syncthreads();
@@ -474,25 +490,68 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     if (tid < 32) warp0_exclusive_scan(pb, nc);
     __syncthreads();
     const uint32_t P2 = pb[nc];
-    // Steps 2-3 for every candidate pair of the tile, two consecutive pairs per thread
-    for (uint32_t t = tid; t < P2; t += nt) {
-        const uint32_t c = find_segment(pb, nc, t);
-        const uint32_t M = t - pb[c];
+    // Steps 2-3 for every candidate pair of the tile, two consecutive pairs per thread.  Most
+    // pairs are settled by the early exit (phi above a bound of p); the others are queued per
+    // warp and evaluated 32 at a time.
+    const uint32_t lane = tid & 31;
+    TileQueue& Q = ((TileQueue*)(smem + L.o_q))[tid >> 5];
+    uint32_t qcnt = 0;                                         // warp-uniform
+    for (uint32_t base = tid & ~31u; base < P2; base += nt) {  // warp-uniform trip count
+        const uint32_t t = base + lane;
+        const bool valid = t < P2;
+        const uint32_t c = valid ? find_segment(pb, nc, t) : 0u;
+        const uint32_t M = valid ? t - pb[c] : 0u;
         const CellCtx& cc = ctx[c];
-        uint64_t u[2];
-        phi_pair_u53(a, cc.gid, step, M, u[0], u[1]);
+        U4 w = {0, 0, 0, 0};
+        if (valid) w = philox(M, cc.gid, step, 1u, a.seed_lo, a.seed_hi);
+        const float* __restrict__ tb = g_pbound[cc.kid ? 1 : 0];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t m = 2 * M + h;
-            if (m >= (cc.n >> 1)) break;
-            const uint32_t i1 = srt[ss[c] + 2 * m], i2 = srt[ss[c] + 2 * m + 1];
-            process_pair(a, tab, cc, u[h], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2], v_s[i1],
-                         v_s[i2], ls, &rem[c]);
+            const bool has = valid && m < (cc.n >> 1);
+            bool need = false;
+            uint32_t i1 = 0, i2 = 0;
+            const uint32_t whi = h ? w.z : w.x, wlo = h ? w.w : w.y;
+            if (has) {
+                i1 = srt[ss[c] + 2 * m];
+                i2 = srt[ss[c] + 2 * m + 1];
+                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_bin((uint32_t)__double2hiint(v_s[i1]),
+                                                                       (uint32_t)__double2hiint(v_s[i2]))),
+                                                      cup[c]),
+                                            xi_pow2_above(xi_s[i1], xi_s[i2]));
+                need = !(pup <= phi_lo23(whi));
+                ls.pairs += need ? 0u : 1u;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, need);
+            if (need) {
+                const uint32_t k = qcnt + __popc(mk & ((1u << lane) - 1u));
+                Q.ii[k] = i1 | (i2 << 16);
+                Q.c[k] = c;
+                Q.u[k] = ((((uint64_t)whi) << 32) | (uint64_t)wlo) >> 11;
+            }
+            qcnt += __popc(mk);
         }
+        while (qcnt >= 32) {
+            __syncwarp();
+            const uint32_t k = qcnt - 32 + lane;
+            const uint32_t ii = Q.ii[k], cq = Q.c[k];
+            const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
+            process_pair(a, tab, ctx[cq], Q.u[k], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
+                         v_s[i1], v_s[i2], ls, &rem[cq]);
+            __syncwarp();
+            qcnt -= 32;
+        }
+    }
+    __syncwarp();
+    if (lane < qcnt) {
+        const uint32_t ii = Q.ii[lane], cq = Q.c[lane];
+        const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
+        process_pair(a, tab, ctx[cq], Q.u[lane], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
+                     v_s[i1], v_s[i2], ls, &rem[cq]);
     }
     __syncthreads();
     // removals take effect in storage: compact the cells that lost SDs (rare)
-    const uint32_t warp = tid >> 5, nw = nt >> 5, lane = tid & 31;
+    const uint32_t warp = tid >> 5, nw = nt >> 5;
     for (uint32_t c = warp; c < nc; c += nw) {
         if (!rem[c]) continue;
         const uint32_t n_new = warp_compact_cell(a, td.slot_begin + cs[c], ncl[c], lane);
