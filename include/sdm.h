@@ -84,7 +84,13 @@ typedef enum {
     SDM_PREC_FP64 = 0,
     /* The decision is taken from the FP32 value of p and the leading 23 bits of phi;
      * multiplicities stay exact uint64 and the attribute update stays FP64. */
-    SDM_PREC_FP32 = 1
+    SDM_PREC_FP32 = 1,
+    /* As SDM_PREC_FP32, with the gravitational kernel taken from the surrogate
+     * network attached by sdm_attach_surrogate wherever its fallback mask allows
+     * (plain FP32 kernel elsewhere).  Not part of the paper; results are
+     * approximate (see sdm_surrogate_build_mask).  SDM_EINVAL without an attached
+     * surrogate or with the SORT shuffle contract. */
+    SDM_PREC_SURROGATE = 2
 } sdm_precision;
 
 /* Step 1 shuffle contract (see the random number contract above). */
@@ -258,6 +264,72 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
                           const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd,
                           double dv, double dt, double golovin_b,
                           double* p64, float* p32, float* err32, double* plite, double* errlite);
+
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the gravitational kernel (no counterpart in the paper).
+ *
+ * A multilayer perceptron (inputs z = ((ln R - c0)/c1, (ln r - c0)/c1) for the
+ * pair's radii R >= r, three hidden layers of 64 SiLU units, one output y)
+ * stands in for the plain kernel: K^ = exp(mu + sigma y) - k_floor (clamped at
+ * 0), where c0, c1 centre and scale ln r over the training range and mu, sigma
+ * standardise ln(K + k_floor) of the training targets (k_floor = 1e-6 times the
+ * median K of the first 65536 training pairs).  Parameters are kept in FP32 for
+ * the optimiser and used rounded to BF16 in every pass; activations and sums
+ * are FP32.  Training data: pair i has radii drawn log-uniform in
+ * [r_min, r_max] from Philox (counter (i lo, i hi, 0, 3), key = seed), target
+ * from the plain FP64 kernel; the loss is the mean squared error of the
+ * standardised target.  All work runs in the library's own CUDA kernels on the
+ * caller's stream (the state's device).
+ * ------------------------------------------------------------------------- */
+typedef struct sdm_surrogate sdm_surrogate;   /* opaque, owned by the library */
+
+typedef struct {
+    uint64_t n_train;      /* training set size (pairs); sample indices run modulo n_train */
+    uint64_t seed;         /* Philox key of the training pairs and of the initial weights */
+    double r_min, r_max;   /* radius range of the training pairs [m], 0 < r_min < r_max */
+} sdm_surrogate_params;
+
+/* Allocate a surrogate with randomly initialised weights and compute its
+ * normalisation (one pass over 65536 training pairs).  *out NULL on error.
+ * Errors: SDM_EINVAL (bad params), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_surrogate_create(sdm_surrogate** out, const sdm_surrogate_params* p, void* cuda_stream);
+void sdm_surrogate_free(sdm_surrogate* s);
+
+/* Run n_steps Adam steps (lr decaying on a half cosine from lr to lr/20 over
+ * these steps), each on the next 'batch' training pairs (batch a multiple of
+ * 64).  loss (nullable host array of n_steps floats) receives each step's loss.
+ * Blocks until the steps are done. */
+sdm_status sdm_surrogate_train(sdm_surrogate* s, uint32_t n_steps, uint32_t batch, float lr, float* loss);
+
+/* Build the fallback mask on a 256 x 256 grid of z over [-1, 1]^2: a tile uses
+ * the network when its relative error against the FP64 kernel is <= tol at 4 x 4
+ * points inside it; tiles with r > R or vanishing K keep the plain kernel.
+ * frac (nullable host) receives the fraction of tiles with r <= R that use the
+ * network; max_err (nullable host, 65536 floats) each tile's largest error. */
+sdm_status sdm_surrogate_build_mask(sdm_surrogate* s, float tol, double* frac, float* max_err);
+
+/* Copy the FP32 parameters (8577 floats, layout W1[64][2], b1, W2[64][64], b2,
+ * W3[64][64], b3, w4[64], b4) to host memory (set = 0), or set them from host
+ * memory (set = 1; the BF16 copy follows). */
+sdm_status sdm_surrogate_params_io(sdm_surrogate* s, float* host_params, int set);
+
+/* Normalisation constants: out[0..5] = c0, c1, mu, sigma, k_floor, r_max/r_min. */
+sdm_status sdm_surrogate_info(const sdm_surrogate* s, double* out);
+
+/* Loss and gradient at the current parameters for n samples given on the device
+ * (x [n][2] network inputs, t [n] standardised targets): *loss and grad (host,
+ * 8577 floats) receive mean((y - t)^2) and its gradient with respect to the
+ * (BF16-rounded) parameters.  For testing the backward pass. */
+sdm_status sdm_surrogate_loss_grad(sdm_surrogate* s, const float* x, const float* t, uint64_t n, float* loss,
+                                   float* grad);
+
+/* Surrogate kernel values for n pairs of radii (device arrays, metres): K[i] =
+ * K^ where the mask lets the network answer, -1 where the plain kernel is used. */
+sdm_status sdm_surrogate_eval(sdm_surrogate* s, const double* R, const double* r, uint64_t n, float* K);
+
+/* Use s for SDM_PREC_SURROGATE steps of st (NULL detaches).  s must outlive its
+ * use by st and live on the same device. */
+sdm_status sdm_attach_surrogate(sdm_state* st, const sdm_surrogate* s);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free single-box step.  (No counterpart in the paper: this is a

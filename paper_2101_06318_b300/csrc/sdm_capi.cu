@@ -35,6 +35,19 @@ struct DevAlloc {
 
 }  // namespace
 
+struct sdm_surrogate {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    float* buf = nullptr;                    // w32, wbf, grad, m, v, loss: 5 * NP + 1 floats
+    uint8_t* mask = nullptr;                 // [SURR_TILES^2]
+    float* tile_err = nullptr;               // [SURR_TILES^2]
+    sdm::SurrogateDev* d_dev = nullptr;      // device copy of dev
+    sdm::SurrTrainArgs args{};
+    sdm::SurrogateDev dev{};
+    double r_min = 0, r_max = 0;
+    uint32_t steps_done = 0;
+};
+
 struct sdm_state {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -88,6 +101,9 @@ struct sdm_state {
     std::vector<double> h_dv;
     std::vector<uint8_t> h_kid;
     int n_sm = 148;
+
+    // surrogate used by SDM_PREC_SURROGATE steps (device copy of its description)
+    const SurrogateDev* d_surr = nullptr;
 
     // optional per-kernel event timing
     bool profiling = false;
@@ -238,7 +254,7 @@ sdm_status ensure_device_tables()
 uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel, PRP_THREADS, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>, PRP_THREADS, 0) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -369,7 +385,8 @@ sdm_status build_layout(sdm_state* st)
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * max_nb;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
     }
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
     SDM_CUDA(cudaStreamSynchronize(st->stream));
     return SDM_OK;
 }
@@ -583,6 +600,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.n_live = st->d_n_live;
     a.stats = with_stats ? st->d_stats : nullptr;
     a.err = st->d_err;
+    a.surr = st->d_surr;
     const sdm_schedule& S = st->sched;
     const uint32_t scatter_smem = sizeof(uint32_t) * 2 * st->max_nb;
     for (uint32_t s = 0; s < n_steps; ++s) {
@@ -595,14 +613,16 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 work = st->d_work;
             }
             ProfScope ps(st, 0);
-            tile_step_kernel<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
+            auto kern = p->precision == SDM_PREC_SURROGATE ? tile_step_kernel<true> : tile_step_kernel<false>;
+            kern<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
                                                                                     st->tile_L, work);
         }
         const BigBook bb{(unsigned long long*)(st->d_big_removed + big_ticket_word(st->n_big)), st->d_big_removed,
                          st->n_big};
         if (st->n_big && p->shuffle == SDM_SHUFFLE_PRP) {
             ProfScope ps(st, 3);
-            big_prp_kernel<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->prp_launch, bb);
+            auto kern = p->precision == SDM_PREC_SURROGATE ? big_prp_kernel<true> : big_prp_kernel<false>;
+            kern<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->prp_launch, bb);
         } else if (st->n_big) {
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
@@ -815,7 +835,8 @@ sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* p, uint32_
     if (!st || !p) return SDM_EINVAL;
     if (!st->initialised) return SDM_EINVAL;
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return SDM_EINVAL;
-    if (p->precision > SDM_PREC_FP32) return SDM_EINVAL;
+    if (p->precision > SDM_PREC_SURROGATE) return SDM_EINVAL;
+    if (p->precision == SDM_PREC_SURROGATE && (!st->d_surr || p->shuffle != SDM_SHUFFLE_PRP)) return SDM_EINVAL;
     if (p->shuffle > SDM_SHUFFLE_SORT || p->reserved != 0) return SDM_EINVAL;
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
     if (n_steps == 0) return SDM_OK;
@@ -1211,7 +1232,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         BigLaunch L{1, n_quads, d_cell, d_xpow, nullptr, {}};
         L.pc[0] = C;
-        big_prp_kernel<<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
+        big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
@@ -1231,3 +1252,279 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     SDM_CUDA(cudaStreamSynchronize(stream));
     return err_to_status(e);
 }
+
+// ---------------------------------------------------------------------------
+// Learned surrogate of the gravitational kernel
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t SURR_STAT_N = 65536;
+
+size_t surr_pass_smem() { return sizeof(sdm::SurrSmem); }
+
+// initial weights: uniform in +-sqrt(6 / (fan_in + fan_out)) (Glorot), biases 0, from a
+// host Philox stream (purpose 4) so that a seed fixes the whole training
+void surr_init_weights(std::vector<float>& w, uint64_t seed)
+{
+    w.assign(sdm::SURR_NPARAM, 0.0f);
+    uint32_t ctr = 0;
+    auto u01 = [&]() {
+        // Philox4x32-10 on the host (same published algorithm as the device code)
+        uint32_t c0 = ctr++, c1 = 0, c2 = 0, c3 = 4u, k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+            const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+            c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
+        }
+        return ((c0 >> 8) + 0.5) * 0x1p-24;
+    };
+    auto fill = [&](int off, int n, int fan_in, int fan_out) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int i = 0; i < n; ++i) w[off + i] = (float)(a * (2.0 * u01() - 1.0));
+    };
+    fill(sdm::SURR_W1, 2 * sdm::SURR_H, 2, sdm::SURR_H);
+    fill(sdm::SURR_W2, sdm::SURR_H * sdm::SURR_H, sdm::SURR_H, sdm::SURR_H);
+    fill(sdm::SURR_W3, sdm::SURR_H * sdm::SURR_H, sdm::SURR_H, sdm::SURR_H);
+    fill(sdm::SURR_W4, sdm::SURR_H, sdm::SURR_H, 1);
+}
+
+sdm_status surr_check(const sdm_surrogate* s)
+{
+    if (!s) return SDM_EINVAL;
+    int dev = -1;
+    SDM_CUDA(cudaGetDevice(&dev));
+    return dev == s->device ? SDM_OK : SDM_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdm_status sdm_surrogate_create(sdm_surrogate** out, const sdm_surrogate_params* p, void* cuda_stream)
+{
+    using namespace sdm;
+    if (!out) return SDM_EINVAL;
+    *out = nullptr;
+    if (!p || p->n_train == 0 || !(p->r_min > 0.0) || !(p->r_max > p->r_min) || !std::isfinite(p->r_max))
+        return SDM_EINVAL;
+    sdm_surrogate* s = new (std::nothrow) sdm_surrogate();
+    if (!s) return SDM_ENOMEM;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->r_min = p->r_min;
+    s->r_max = p->r_max;
+    sdm_status st = SDM_OK;
+    double* d_K = nullptr;
+    do {
+        if (cudaGetDevice(&s->device) != cudaSuccess) { st = SDM_ECUDA; break; }
+        const size_t nb = sizeof(float) * (5 * (size_t)SURR_NPARAM + 4);
+        if (cudaMalloc(&s->buf, nb) != cudaSuccess ||
+            cudaMalloc(&s->mask, SURR_TILES * SURR_TILES) != cudaSuccess ||
+            cudaMalloc(&s->tile_err, sizeof(float) * SURR_TILES * SURR_TILES) != cudaSuccess ||
+            cudaMalloc(&d_K, sizeof(double) * SURR_STAT_N) != cudaSuccess) {
+            cudaGetLastError();
+            st = SDM_ENOMEM;
+            break;
+        }
+        if (cudaMemsetAsync(s->buf, 0, nb, s->stream) != cudaSuccess ||
+            cudaMemsetAsync(s->mask, 0, SURR_TILES * SURR_TILES, s->stream) != cudaSuccess) { st = SDM_ECUDA; break; }
+        SurrTrainArgs& A = s->args;
+        A.w32 = s->buf;
+        A.wbf = A.w32 + SURR_NPARAM;
+        A.grad = A.wbf + SURR_NPARAM;
+        A.m = A.grad + SURR_NPARAM;
+        A.v = A.m + SURR_NPARAM;
+        A.loss = A.v + SURR_NPARAM;
+        A.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
+        A.seed_hi = (uint32_t)(p->seed >> 32);
+        A.ln_rmin = std::log(p->r_min);
+        A.ln_rmax = std::log(p->r_max);
+        A.c0 = (float)(0.5 * (A.ln_rmin + A.ln_rmax));
+        A.c1 = (float)(0.5 * (A.ln_rmax - A.ln_rmin));
+        A.n_train = p->n_train;
+        A.mu = 0.0f;
+        A.sigma = 1.0f;
+        A.k_floor = 0.0;
+        // target normalisation from the first pairs of the training set
+        surr_targets_kernel<<<256, 256, 0, s->stream>>>(A, SURR_STAT_N, d_K);
+        std::vector<double> K(SURR_STAT_N);
+        if (cudaMemcpyAsync(K.data(), d_K, sizeof(double) * SURR_STAT_N, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess) { st = SDM_ECUDA; break; }
+        std::vector<double> pos;
+        for (double k : K) if (k > 0.0) pos.push_back(k);
+        if (pos.empty()) { st = SDM_EINVAL; break; }
+        std::nth_element(pos.begin(), pos.begin() + pos.size() / 2, pos.end());
+        A.k_floor = 1e-6 * pos[pos.size() / 2];
+        double sum = 0.0, sum2 = 0.0;
+        for (double k : K) { const double l = std::log(k + A.k_floor); sum += l; sum2 += l * l; }
+        const double mean = sum / SURR_STAT_N, var = std::max(sum2 / SURR_STAT_N - mean * mean, 1e-12);
+        A.mu = (float)mean;
+        A.sigma = (float)std::sqrt(var);
+        std::vector<float> w;
+        surr_init_weights(w, p->seed);
+        if (cudaMemcpyAsync(A.w32, w.data(), sizeof(float) * SURR_NPARAM, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+            st = SDM_ECUDA;
+            break;
+        }
+        surr_round_kernel<<<(SURR_NPARAM + 255) / 256, 256, 0, s->stream>>>(A.w32, A.wbf);
+        if (cudaFuncSetAttribute(surr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)surr_pass_smem()) !=
+            cudaSuccess) { st = SDM_ECUDA; break; }
+        SurrogateDev& D = s->dev;
+        D.w = A.wbf;
+        D.mask = s->mask;
+        D.c0 = A.c0;
+        D.c1 = A.c1;
+        D.mu = A.mu;
+        D.sigma = A.sigma;
+        D.k_floor = (float)A.k_floor;
+        D.r_min = (float)p->r_min;
+        D.r_max = (float)p->r_max;
+        if (cudaMalloc(&s->d_dev, sizeof(SurrogateDev)) != cudaSuccess) { cudaGetLastError(); st = SDM_ENOMEM; break; }
+        if (cudaMemcpyAsync(s->d_dev, &D, sizeof D, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) { st = SDM_ECUDA; break; }
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = SDM_ECUDA;
+    } while (false);
+    if (d_K) cudaFree(d_K);
+    if (st != SDM_OK) { sdm_surrogate_free(s); return st; }
+    *out = s;
+    return SDM_OK;
+}
+
+void sdm_surrogate_free(sdm_surrogate* s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->buf) cudaFree(s->buf);
+    if (s->mask) cudaFree(s->mask);
+    if (s->tile_err) cudaFree(s->tile_err);
+    if (s->d_dev) cudaFree(s->d_dev);
+    delete s;
+}
+
+sdm_status sdm_surrogate_train(sdm_surrogate* s, uint32_t n_steps, uint32_t batch, float lr, float* loss)
+{
+    using namespace sdm;
+    SDM_TRY(surr_check(s));
+    if (batch == 0 || batch % SURR_TB != 0 || !(lr > 0.0f)) return SDM_EINVAL;
+    SurrTrainArgs& A = s->args;
+    std::vector<float> hl(n_steps, 0.0f);
+    float* d_loss_hist = nullptr;
+    if (n_steps && cudaMalloc(&d_loss_hist, sizeof(float) * n_steps) != cudaSuccess) { cudaGetLastError(); return SDM_ENOMEM; }
+    sdm_status st = SDM_OK;
+    for (uint32_t k = 0; k < n_steps && st == SDM_OK; ++k) {
+        const double frac = n_steps > 1 ? (double)k / (n_steps - 1) : 0.0;
+        const float lr_k = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * frac))));
+        const uint64_t first = (uint64_t)s->steps_done * batch;
+        if (cudaMemsetAsync(A.loss, 0, sizeof(float), s->stream) != cudaSuccess) { st = SDM_ECUDA; break; }
+        surr_pass_kernel<<<batch / SURR_TB, SURR_THREADS, surr_pass_smem(), s->stream>>>(A, first, batch, nullptr,
+                                                                                          nullptr);
+        if (cudaMemcpyAsync(d_loss_hist + k, A.loss, sizeof(float), cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess) {
+            st = SDM_ECUDA;
+            break;
+        }
+        surr_adam_kernel<<<(SURR_NPARAM + 255) / 256, 256, 0, s->stream>>>(A, lr_k, s->steps_done + 1);
+        if (cudaGetLastError() != cudaSuccess) st = SDM_ECUDA;
+        ++s->steps_done;
+    }
+    if (st == SDM_OK && n_steps) {
+        if (cudaMemcpyAsync(hl.data(), d_loss_hist, sizeof(float) * n_steps, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            st = SDM_ECUDA;
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) st = SDM_ECUDA;
+    if (d_loss_hist) cudaFree(d_loss_hist);
+    if (st == SDM_OK && loss) std::memcpy(loss, hl.data(), sizeof(float) * n_steps);
+    return st;
+}
+
+sdm_status sdm_surrogate_build_mask(sdm_surrogate* s, float tol, double* frac, float* max_err)
+{
+    using namespace sdm;
+    SDM_TRY(surr_check(s));
+    if (!(tol > 0.0f)) return SDM_EINVAL;
+    surr_mask_kernel<<<SURR_TILES * SURR_TILES / 16, 256, 0, s->stream>>>(s->dev, s->args.ln_rmin, s->args.ln_rmax, tol,
+                                                                            s->mask, s->tile_err);
+    SDM_CUDA(cudaGetLastError());
+    std::vector<uint8_t> m(SURR_TILES * SURR_TILES);
+    std::vector<float> e(SURR_TILES * SURR_TILES);
+    SDM_CUDA(cudaMemcpyAsync(m.data(), s->mask, m.size(), cudaMemcpyDeviceToHost, s->stream));
+    SDM_CUDA(cudaMemcpyAsync(e.data(), s->tile_err, sizeof(float) * e.size(), cudaMemcpyDeviceToHost, s->stream));
+    SDM_CUDA(cudaStreamSynchronize(s->stream));
+    if (frac) {
+        size_t used = 0, total = 0;
+        for (int a = 0; a < SURR_TILES; ++a)
+            for (int b = 0; b <= a; ++b) { ++total; used += m[a * SURR_TILES + b]; }
+        *frac = (double)used / (double)total;
+    }
+    if (max_err) std::memcpy(max_err, e.data(), sizeof(float) * e.size());
+    return SDM_OK;
+}
+
+sdm_status sdm_surrogate_params_io(sdm_surrogate* s, float* host_params, int set)
+{
+    using namespace sdm;
+    SDM_TRY(surr_check(s));
+    if (!host_params) return SDM_EINVAL;
+    if (set) {
+        SDM_CUDA(cudaMemcpyAsync(s->args.w32, host_params, sizeof(float) * SURR_NPARAM, cudaMemcpyHostToDevice, s->stream));
+        surr_round_kernel<<<(SURR_NPARAM + 255) / 256, 256, 0, s->stream>>>(s->args.w32, s->args.wbf);
+        SDM_CUDA(cudaGetLastError());
+    } else {
+        SDM_CUDA(cudaMemcpyAsync(host_params, s->args.w32, sizeof(float) * SURR_NPARAM, cudaMemcpyDeviceToHost, s->stream));
+    }
+    SDM_CUDA(cudaStreamSynchronize(s->stream));
+    return SDM_OK;
+}
+
+sdm_status sdm_surrogate_info(const sdm_surrogate* s, double* out)
+{
+    if (!s || !out) return SDM_EINVAL;
+    out[0] = s->args.c0;
+    out[1] = s->args.c1;
+    out[2] = s->args.mu;
+    out[3] = s->args.sigma;
+    out[4] = s->args.k_floor;
+    out[5] = s->r_max / s->r_min;
+    return SDM_OK;
+}
+
+sdm_status sdm_surrogate_loss_grad(sdm_surrogate* s, const float* x, const float* t, uint64_t n, float* loss,
+                                   float* grad)
+{
+    using namespace sdm;
+    SDM_TRY(surr_check(s));
+    if (!x || !t || !loss || !grad || n == 0 || n > (1ull << 30)) return SDM_EINVAL;
+    SurrTrainArgs A = s->args;
+    SDM_CUDA(cudaMemsetAsync(A.grad, 0, sizeof(float) * SURR_NPARAM, s->stream));
+    SDM_CUDA(cudaMemsetAsync(A.loss, 0, sizeof(float), s->stream));
+    surr_pass_kernel<<<(uint32_t)((n + SURR_TB - 1) / SURR_TB), SURR_THREADS, surr_pass_smem(), s->stream>>>(A, 0, n, x, t);
+    SDM_CUDA(cudaGetLastError());
+    SDM_CUDA(cudaMemcpyAsync(grad, A.grad, sizeof(float) * SURR_NPARAM, cudaMemcpyDeviceToHost, s->stream));
+    SDM_CUDA(cudaMemcpyAsync(loss, A.loss, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    SDM_CUDA(cudaMemsetAsync(A.grad, 0, sizeof(float) * SURR_NPARAM, s->stream));   // training expects zeros
+    SDM_CUDA(cudaStreamSynchronize(s->stream));
+    return SDM_OK;
+}
+
+sdm_status sdm_surrogate_eval(sdm_surrogate* s, const double* R, const double* r, uint64_t n, float* K)
+{
+    using namespace sdm;
+    SDM_TRY(surr_check(s));
+    if (!R || !r || !K) return SDM_EINVAL;
+    if (n == 0) return SDM_OK;
+    surr_eval_kernel<<<(uint32_t)std::min<uint64_t>((n + 255) / 256, 4096), 256, 0, s->stream>>>(s->dev, R, r, n, K);
+    SDM_CUDA(cudaGetLastError());
+    return SDM_OK;
+}
+
+sdm_status sdm_attach_surrogate(sdm_state* st, const sdm_surrogate* s)
+{
+    if (!st) return SDM_EINVAL;
+    if (!s) {
+        st->d_surr = nullptr;
+        return SDM_OK;
+    }
+    if (s->device != st->device) return SDM_EINVAL;
+    st->d_surr = s->d_dev;
+    return SDM_OK;
+}
+
+}  // extern "C"

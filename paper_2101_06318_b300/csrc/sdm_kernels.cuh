@@ -22,6 +22,7 @@
 // the tile size, bucket width and launch shape never change a result.
 #pragma once
 #include "sdm_math.cuh"
+#include "sdm_surrogate.cuh"
 
 namespace sdm {
 
@@ -31,7 +32,7 @@ enum : uint32_t {
     ERR_TIMEOUT = 4u,
 };
 
-constexpr uint32_t PREC_FP64 = 0, PREC_FP32 = 1;
+constexpr uint32_t PREC_FP64 = 0, PREC_FP32 = 1, PREC_SURROGATE = 2;
 constexpr uint32_t SHUFFLE_PRP = 0, SHUFFLE_SORT = 1;
 constexpr uint32_t DEAD = 0xffffffffu;
 
@@ -55,6 +56,7 @@ struct StepArgs {
     uint32_t* n_live;           // [n_cell] live SDs per cell (a prefix of its slots)
     unsigned long long* stats;  // [5] or nullptr
     uint32_t* err;
+    const SurrogateDev* surr;   // device copy; used when precision == PREC_SURROGATE
 };
 
 // a cell is shuffled by sorting keys when it is small or the SORT contract is selected
@@ -85,10 +87,12 @@ struct CellCtx {
     double dv;
 };
 
-// early-exit scale of a cell without its multiplicity factor (see pb_bin)
-__device__ __forceinline__ float exit_scale(float s32, uint32_t kid, float golovin_bf)
+// early-exit scale of a cell without its multiplicity factor (see pb_bin); with the
+// surrogate the bound gets a factor 2 of room for the network's error
+__device__ __forceinline__ float exit_scale(float s32, uint32_t kid, float golovin_bf, uint32_t precision)
 {
-    return __fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, golovin_bf) : 1.0f), 1.0f + 0x1p-8f);
+    const float f = precision == PREC_SURROGATE ? 2.0f : 1.0f;
+    return __fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, golovin_bf) : f), 1.0f + 0x1p-8f);
 }
 
 __device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, float dt_f, double dv)
@@ -110,6 +114,7 @@ __device__ __forceinline__ void phi_pair_u53(const StepArgs& a, uint32_t cell, u
 // Step 2 + Step 3 for one candidate pair (first, second) of a cell with phi
 // integer u53.  Writes the updated multiplicities and attributes of the pair to
 // global memory.
+template <bool SURR>
 __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
                                              uint64_t u53, uint64_t g1, uint64_t g2, uint64_t x1, uint64_t x2,
                                              double v1, double v2, LocalStats& ls, uint32_t* removed_flag)
@@ -117,9 +122,11 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
     const bool swap = x1 < x2;                 // j = first unless it has the smaller multiplicity
     const uint64_t xj = swap ? x2 : x1, xk = swap ? x1 : x2;
     const float scale32 = u64_to_f_trunc(xj) * c.s_dtdv32;
-    const P32 pe = pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf);
     uint64_t g;
-    if (a.precision == PREC_FP32) {
+    float Kh = -1.0f;
+    if (SURR && a.precision == PREC_SURROGATE && c.kid == 1) Kh = surr_pair_kernel(a.surr, v1, v2);
+    const P32 pe = Kh >= 0.0f ? P32{Kh * scale32, 0.0f} : pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf);
+    if (a.precision != PREC_FP64) {
         g = gamma_tilde_f(pe.p, u53, xj, xk);
     } else if (!gamma_tilde_certified(pe, u53, xj, xk, &g)) {
         if (c.kid == 0 || !gamma_tilde_lite(v1, v2, c.n, a.dt, c.dv, u53, xj, xk, &g))
@@ -359,6 +366,7 @@ __device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t
     return dst;
 }
 
+template <bool SURR>
 __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLayout& L, unsigned char* smem,
                              uint32_t step, LocalStats& ls)
 {
@@ -475,7 +483,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         cc.dv = a.dv[gid];
         cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, cc.dv) : 0.f;
         ctx[c] = cc;
-        cup[c] = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf);
+        cup[c] = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision);
         pb[c] = (n >> 1) + 1u >> 1;              // groups of two pairs (one Philox call each)
     }
     __syncthreads();
@@ -536,7 +544,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             const uint32_t k = qcnt - 32 + lane;
             const uint32_t ii = Q.ii[k], cq = Q.c[k];
             const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
-            process_pair(a, tab, ctx[cq], Q.u[k], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
+            process_pair<SURR>(a, tab, ctx[cq], Q.u[k], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
                          v_s[i1], v_s[i2], ls, &rem[cq]);
             __syncwarp();
             qcnt -= 32;
@@ -546,7 +554,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     if (lane < qcnt) {
         const uint32_t ii = Q.ii[lane], cq = Q.c[lane];
         const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
-        process_pair(a, tab, ctx[cq], Q.u[lane], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
+        process_pair<SURR>(a, tab, ctx[cq], Q.u[lane], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
                      v_s[i1], v_s[i2], ls, &rem[cq]);
     }
     __syncthreads();
@@ -559,6 +567,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     }
 }
 
+template <bool SURR>
 __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDesc* __restrict__ tiles,
                                                          uint32_t n_tiles, TileLayout L, uint32_t* work)
 {
@@ -568,7 +577,7 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
     unsigned long long* red = (unsigned long long*)(smem + L.o_red);
     load_eff_tab((EffTab*)(smem + L.o_tab));   // read after the first __syncthreads of tile_process
     if (work == nullptr) {
-        tile_process(a, tiles[blockIdx.x], L, smem, step, ls);
+        tile_process<SURR>(a, tiles[blockIdx.x], L, smem, step, ls);
     } else {
         __shared__ uint32_t t_s;
         for (;;) {
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDe
             const uint32_t t = t_s;
             __syncthreads();
             if (t >= n_tiles) break;
-            tile_process(a, tiles[t], L, smem, step, ls);
+            tile_process<SURR>(a, tiles[t], L, smem, step, ls);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
@@ -776,6 +785,7 @@ __device__ __forceinline__ void prp_walk_n(const Prp& P, uint32_t use, uint32_t 
 }
 
 // Evaluate the top 'take' queued pairs of this warp (lanes < take) and pop them.
+template <bool SURR>
 __device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& cc,
                                             PairQueue& Q, uint32_t& qcnt, uint32_t take, LocalStats& ls,
                                             uint32_t* removed_flag, uint32_t lane)
@@ -784,7 +794,7 @@ __device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __r
     if (lane < take) {
         const uint32_t k = qcnt - take + lane;
         const uint32_t s1 = Q.s1[k], s2 = Q.s2[k];
-        process_pair(a, T, cc, Q.u[k], s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls, removed_flag);
+        process_pair<SURR>(a, T, cc, Q.u[k], s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls, removed_flag);
     }
     __syncwarp();
     qcnt -= take;
@@ -815,6 +825,7 @@ __device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, u
     qcnt += __popc(m);
 }
 
+template <bool SURR>
 __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kernel(StepArgs a, BigLaunch L,
                                                                                  BigBook bk)
 {
@@ -872,9 +883,7 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         if (n >= PRP_MIN_N) {
             const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
             const CellCtx cc{C.cell, n, kid, s32, dv};
-            const float c_upx =
-                __fmul_ru(__fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, a.golovin_bf) : 1.0f), 1.0f + 0x1p-8f),
-                          xpow);
+            const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xpow);
             // PRP_QPT quads per thread and iteration: g, g + 32, ... (warp-uniform trip count)
             constexpr int NP = 4 * PRP_QPT;            // positions per thread and iteration
             for (uint32_t base = sa + warp * 32 * PRP_QPT; base < sb; base += PRP_QPT * nt) {
@@ -924,9 +933,9 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
                     exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
                                   w.w, tb, c_upx, ls, lane);
                 }
-                while (qcnt >= 32) drain_queue(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
+                while (qcnt >= 32) drain_queue<SURR>(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
             }
-            if (qcnt > 0) drain_queue(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
+            if (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
         } else if (n >= 2 && C.quad_begin >= qa) {
             // few live SDs left in a large cell: sorted by key by the CTA holding the cell's
             // first quad (n, qa and the cell are the same in all threads: a uniform branch)
@@ -944,7 +953,7 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
             const CellCtx cc{C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
             for (uint32_t mm = tid; mm < npairs; mm += nt) {
                 const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
-                process_pair(a, tab, cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
+                process_pair<SURR>(a, tab, cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
                              a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
             }
         }
@@ -1258,7 +1267,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h)
             if (ok[h])
-                process_pair(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls,
+                process_pair<false>(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls,
                              &removed[big]);
     }
 }

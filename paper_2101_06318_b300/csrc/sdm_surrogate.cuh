@@ -1,0 +1,335 @@
+// sdm_surrogate.cuh -- learned stand-in for the gravitational collision kernel.
+//
+// Not in the paper: a small multilayer perceptron maps the pair's radii to the
+// kernel value, trained on the GPU by the kernels below on pairs whose targets
+// come from the plain FP64 kernel, with the plain kernel kept as the fallback
+// wherever the network's relative error on a validation grid exceeds a threshold.
+//
+//   z = ((ln R - c0) / c1, (ln r - c0) / c1)      R >= r the pair's radii,
+//       c0, c1 the centre and half-width of ln r over the training range
+//   h1 = silu(W1 z + b1), h2 = silu(W2 h1 + b2), h3 = silu(W3 h2 + b3)   (64 each)
+//   y  = w4 . h3 + b4
+//   K^ = exp(mu + sigma y) - K_floor, clamped at 0  (the network fits the
+//        standardised ln(K + K_floor); K_floor keeps the target finite where
+//        vt(R) = vt(r) makes K vanish)
+//
+// Weights are kept in FP32 for the optimiser and used rounded to BF16 (round to
+// nearest even) in every forward and backward pass; activations and sums are FP32.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace sdm {
+
+constexpr int SURR_H = 64;                 // hidden width
+constexpr int SURR_W1 = 0;                 // [64][2]
+constexpr int SURR_B1 = SURR_W1 + SURR_H * 2;
+constexpr int SURR_W2 = SURR_B1 + SURR_H;  // [64][64], row j = inputs of unit j
+constexpr int SURR_B2 = SURR_W2 + SURR_H * SURR_H;
+constexpr int SURR_W3 = SURR_B2 + SURR_H;
+constexpr int SURR_B3 = SURR_W3 + SURR_H * SURR_H;
+constexpr int SURR_W4 = SURR_B3 + SURR_H;  // [64]
+constexpr int SURR_B4 = SURR_W4 + SURR_H;
+constexpr int SURR_NPARAM = SURR_B4 + 1;   // 8577
+constexpr int SURR_TILES = 256;            // fallback mask: tiles per input axis over [-1, 1]
+
+// What a step needs of a trained surrogate (device pointers).
+struct SurrogateDev {
+    const float* w;          // [SURR_NPARAM] BF16-rounded parameters, stored as float
+    const uint8_t* mask;     // [SURR_TILES][SURR_TILES] 1: use the network, 0: plain kernel
+    float c0, c1;            // input normalisation of ln r
+    float mu, sigma;         // target standardisation
+    float k_floor;           // [m^3/s]
+    float r_min, r_max;      // training range of the radii [m]
+};
+
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + __expf(-x)); }
+
+// silu'(x) = s (1 + x (1 - s)), s = 1 / (1 + e^-x)
+__device__ __forceinline__ float silu_grad_f(float x)
+{
+    const float s = 1.0f / (1.0f + __expf(-x));
+    return s * (1.0f + x * (1.0f - s));
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Network output y for inputs (z0, z1); w are the BF16-rounded parameters in global
+// memory (read through L1).  Rolled loops keep the code small.
+__device__ __noinline__ float surr_forward(const float* __restrict__ w, float z0, float z1)
+{
+    float h[SURR_H], g[SURR_H];
+#pragma unroll 4
+    for (int j = 0; j < SURR_H; ++j)
+        h[j] = silu_f(fmaf(__ldg(w + SURR_W1 + 2 * j), z0, fmaf(__ldg(w + SURR_W1 + 2 * j + 1), z1, __ldg(w + SURR_B1 + j))));
+#pragma unroll 1
+    for (int j = 0; j < SURR_H; ++j) {
+        const float* row = w + SURR_W2 + SURR_H * j;
+        float acc = __ldg(w + SURR_B2 + j);
+#pragma unroll
+        for (int k = 0; k < SURR_H; ++k) acc = fmaf(__ldg(row + k), h[k], acc);
+        g[j] = silu_f(acc);
+    }
+#pragma unroll 1
+    for (int j = 0; j < SURR_H; ++j) {
+        const float* row = w + SURR_W3 + SURR_H * j;
+        float acc = __ldg(w + SURR_B3 + j);
+#pragma unroll
+        for (int k = 0; k < SURR_H; ++k) acc = fmaf(__ldg(row + k), g[k], acc);
+        h[j] = silu_f(acc);
+    }
+    float y = __ldg(w + SURR_B4);
+#pragma unroll
+    for (int k = 0; k < SURR_H; ++k) y = fmaf(__ldg(w + SURR_W4 + k), h[k], y);
+    return y;
+}
+
+// Surrogate kernel value for radii R >= r, or a negative number when the pair must use
+// the plain kernel (outside the training range or in a masked tile).
+__device__ __forceinline__ float surr_kernel(const SurrogateDev& S, float R, float r)
+{
+    if (!(r >= S.r_min) || !(R <= S.r_max)) return -1.0f;
+    const float z0 = (__logf(R) - S.c0) / S.c1, z1 = (__logf(r) - S.c0) / S.c1;
+    const int a = min(SURR_TILES - 1, max(0, (int)((z0 + 1.0f) * (0.5f * SURR_TILES))));
+    const int b = min(SURR_TILES - 1, max(0, (int)((z1 + 1.0f) * (0.5f * SURR_TILES))));
+    if (!S.mask[a * SURR_TILES + b]) return -1.0f;
+    const float y = surr_forward(S.w, z0, z1);
+    return fmaxf(__expf(fmaf(S.sigma, y, S.mu)) - S.k_floor, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Training: samples are pairs of radii drawn log-uniform in [r_min, r_max] by
+// Philox (counter (i, 0, 0, 3), key = seed; two words per radius), with
+// targets from the plain FP64 kernel.
+// ---------------------------------------------------------------------------
+struct SurrTrainArgs {
+    float* w32;              // FP32 master parameters
+    float* wbf;              // BF16-rounded copy used by the passes
+    float* grad;             // [SURR_NPARAM] accumulated gradient of the loss
+    float* m;                // Adam moments
+    float* v;
+    float* loss;             // [1] accumulated loss of the current step
+    uint32_t seed_lo, seed_hi;
+    double ln_rmin, ln_rmax;
+    float c0, c1, mu, sigma;
+    double k_floor;
+    uint64_t n_train;        // size of the training set (sample index modulo n_train)
+};
+
+// pair i of the training set: radii R >= r, features and target
+__device__ __forceinline__ void surr_sample(const SurrTrainArgs& A, uint64_t i, float& z0, float& z1, float& t,
+                                            double& K)
+{
+    const U4 x = philox((uint32_t)i, (uint32_t)(i >> 32), 0u, 3u, A.seed_lo, A.seed_hi);
+    const double u1 = ((double)(x.x >> 8) + 0.5) * 0x1p-24, u2 = ((double)(x.y >> 8) + 0.5) * 0x1p-24;
+    double l1 = A.ln_rmin + (A.ln_rmax - A.ln_rmin) * u1, l2 = A.ln_rmin + (A.ln_rmax - A.ln_rmin) * u2;
+    if (l2 > l1) { const double s = l1; l1 = l2; l2 = s; }
+    const double R = exp(l1), r = exp(l2);
+    const double c = 4.0 / 3.0 * PI_D;
+    K = kernel_grav_d(c * R * R * R, c * r * r * r);
+    z0 = (float)((l1 - A.c0) / A.c1);
+    z1 = (float)((l2 - A.c0) / A.c1);
+    t = (float)((log(K + A.k_floor) - A.mu) / A.sigma);
+}
+
+__global__ void surr_targets_kernel(SurrTrainArgs A, uint64_t n, double* K_out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        float z0, z1, t;
+        double K;
+        surr_sample(A, i, z0, z1, t, K);
+        K_out[i] = K;
+    }
+}
+
+constexpr int SURR_TB = 64;                // samples per CTA of the training pass
+constexpr int SURR_THREADS = 256;
+
+// dynamic shared memory of the training pass
+struct SurrSmem {
+    float w[SURR_NPARAM];
+    float z[SURR_TB][2];
+    float t[SURR_TB];
+    float y[SURR_TB];
+    float Z1[SURR_TB][SURR_H], Z2[SURR_TB][SURR_H], Z3[SURR_TB][SURR_H];   // pre-activations
+    float D[SURR_TB][SURR_H];                                             // dL/dZ of the current layer
+    float E[SURR_TB][SURR_H];                                             // dL/dZ of the layer below
+};
+
+// One CTA: forward and backward of SURR_TB samples; adds the loss and the gradient of
+// mean((y - t)^2) over the whole batch (n_batch samples) to A.loss and A.grad.  The
+// samples are given either by index (training set, x_ext == nullptr) or by features
+// and targets in device memory (x_ext [n][2], t_ext [n]; the gradient check).
+__global__ void __launch_bounds__(SURR_THREADS) surr_pass_kernel(SurrTrainArgs A, uint64_t first, uint64_t n_batch,
+                                                                 const float* x_ext, const float* t_ext)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SurrSmem& S = *reinterpret_cast<SurrSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int k = tid; k < SURR_NPARAM; k += SURR_THREADS) S.w[k] = A.wbf[k];
+    const uint64_t s0 = (uint64_t)blockIdx.x * SURR_TB;
+    if (tid < SURR_TB) {
+        float z0 = 0.f, z1 = 0.f, t = 0.f;
+        if (s0 + tid < n_batch) {
+            if (x_ext) {
+                z0 = x_ext[2 * (s0 + tid)];
+                z1 = x_ext[2 * (s0 + tid) + 1];
+                t = t_ext[s0 + tid];
+            } else {
+                double K;
+                surr_sample(A, (first + s0 + tid) % A.n_train, z0, z1, t, K);
+            }
+        }
+        S.z[tid][0] = z0;
+        S.z[tid][1] = z1;
+        S.t[tid] = t;
+    }
+    __syncthreads();
+    // forward: thread (s, jq) computes units jq, jq + 4, ... of sample s
+    const int s = tid >> 2, jq = tid & 3;
+    for (int j = jq; j < SURR_H; j += 4)
+        S.Z1[s][j] = fmaf(S.w[SURR_W1 + 2 * j], S.z[s][0], fmaf(S.w[SURR_W1 + 2 * j + 1], S.z[s][1], S.w[SURR_B1 + j]));
+    __syncthreads();
+    for (int j = jq; j < SURR_H; j += 4) {
+        float acc = S.w[SURR_B2 + j];
+        for (int k = 0; k < SURR_H; ++k) acc = fmaf(S.w[SURR_W2 + SURR_H * j + k], silu_f(S.Z1[s][k]), acc);
+        S.Z2[s][j] = acc;
+    }
+    __syncthreads();
+    for (int j = jq; j < SURR_H; j += 4) {
+        float acc = S.w[SURR_B3 + j];
+        for (int k = 0; k < SURR_H; ++k) acc = fmaf(S.w[SURR_W3 + SURR_H * j + k], silu_f(S.Z2[s][k]), acc);
+        S.Z3[s][j] = acc;
+    }
+    __syncthreads();
+    if (tid < SURR_TB) {
+        float y = S.w[SURR_B4];
+        for (int k = 0; k < SURR_H; ++k) y = fmaf(S.w[SURR_W4 + k], silu_f(S.Z3[tid][k]), y);
+        const bool in = s0 + tid < n_batch;
+        const float d = in ? y - S.t[tid] : 0.0f;
+        S.y[tid] = in ? 2.0f * d / (float)n_batch : 0.0f;        // dL/dy
+        float l = d * d / (float)n_batch;
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((tid & 31) == 0) atomicAdd(A.loss, l);
+    }
+    __syncthreads();
+    // output layer: dL/dZ3 = dy w4 silu'(Z3); gradients of w4, b4
+    for (int j = jq; j < SURR_H; j += 4) S.D[s][j] = S.y[s] * S.w[SURR_W4 + j] * silu_grad_f(S.Z3[s][j]);
+    if (tid < SURR_H) {
+        float g = 0.f;
+        for (int q = 0; q < SURR_TB; ++q) g = fmaf(S.y[q], silu_f(S.Z3[q][tid]), g);
+        atomicAdd(A.grad + SURR_W4 + tid, g);
+    } else if (tid == SURR_H) {
+        float g = 0.f;
+        for (int q = 0; q < SURR_TB; ++q) g += S.y[q];
+        atomicAdd(A.grad + SURR_B4, g);
+    }
+    __syncthreads();
+    // hidden layers 3 and 2: dW[j][k] = sum_s D[s][j] silu(Zbelow[s][k]); dZbelow = (W^T D) silu'(Zbelow)
+    for (int layer = 3; layer >= 2; --layer) {
+        const int OW = layer == 3 ? SURR_W3 : SURR_W2, OB = layer == 3 ? SURR_B3 : SURR_B2;
+        float (*Zb)[SURR_H] = layer == 3 ? S.Z2 : S.Z1;
+        for (int e = tid; e < SURR_H * SURR_H; e += SURR_THREADS) {
+            const int j = e / SURR_H, k = e % SURR_H;
+            float g = 0.f;
+            for (int q = 0; q < SURR_TB; ++q) g = fmaf(S.D[q][j], silu_f(Zb[q][k]), g);
+            atomicAdd(A.grad + OW + e, g);
+        }
+        if (tid < SURR_H) {
+            float g = 0.f;
+            for (int q = 0; q < SURR_TB; ++q) g += S.D[q][tid];
+            atomicAdd(A.grad + OB + tid, g);
+        }
+        for (int k = jq; k < SURR_H; k += 4) {
+            float acc = 0.f;
+            for (int j = 0; j < SURR_H; ++j) acc = fmaf(S.w[OW + SURR_H * j + k], S.D[s][j], acc);
+            S.E[s][k] = acc * silu_grad_f(Zb[s][k]);
+        }
+        __syncthreads();
+        for (int k = jq; k < SURR_H; k += 4) S.D[s][k] = S.E[s][k];
+        __syncthreads();
+    }
+    // first layer: dW1[j][i] = sum_s D[s][j] z[s][i]
+    if (tid < SURR_H * 2) {
+        const int j = tid >> 1, i = tid & 1;
+        float g = 0.f;
+        for (int q = 0; q < SURR_TB; ++q) g = fmaf(S.D[q][j], S.z[q][i], g);
+        atomicAdd(A.grad + SURR_W1 + tid, g);
+    } else if (tid < SURR_H * 3) {
+        const int j = tid - 2 * SURR_H;
+        float g = 0.f;
+        for (int q = 0; q < SURR_TB; ++q) g += S.D[q][j];
+        atomicAdd(A.grad + SURR_B1 + j, g);
+    }
+}
+
+// Adam step t (1-based) on every parameter, then the BF16 copy and a cleared gradient.
+__global__ void surr_adam_kernel(SurrTrainArgs A, float lr, uint32_t t)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < SURR_NPARAM; k += gridDim.x * blockDim.x) {
+        const float g = A.grad[k];
+        const float m = b1 * A.m[k] + (1.0f - b1) * g;
+        const float v = b2 * A.v[k] + (1.0f - b2) * g * g;
+        A.m[k] = m;
+        A.v[k] = v;
+        const float w = A.w32[k] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        A.w32[k] = w;
+        A.wbf[k] = bf16_round(w);
+        A.grad[k] = 0.0f;
+    }
+}
+
+__global__ void surr_round_kernel(const float* w32, float* wbf)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < SURR_NPARAM; k += gridDim.x * blockDim.x)
+        wbf[k] = bf16_round(w32[k]);
+}
+
+// Fallback mask: tile (a, b) of the (z0, z1) grid uses the network when, at 4 x 4
+// points inside it, |K^ - K| <= tol K with K from the FP64 kernel (K > 0).  Tiles
+// with r > R only, or where K vanishes, keep the plain kernel.
+__global__ void surr_mask_kernel(SurrogateDev S, double ln_rmin, double ln_rmax, float tol, uint8_t* mask,
+                                 float* max_err)
+{
+    const int tile = blockIdx.x * (blockDim.x / 16) + threadIdx.x / 16;
+    if (tile >= SURR_TILES * SURR_TILES) return;
+    const int a = tile / SURR_TILES, b = tile % SURR_TILES, q = threadIdx.x % 16;
+    const double za = -1.0 + 2.0 * (a + ((q & 3) + 0.5) / 4.0) / SURR_TILES;
+    const double zb = -1.0 + 2.0 * (b + ((q >> 2) + 0.5) / 4.0) / SURR_TILES;
+    const double c0 = 0.5 * (ln_rmin + ln_rmax), c1 = 0.5 * (ln_rmax - ln_rmin);
+    const double R = exp(c0 + c1 * za), r = exp(c0 + c1 * zb);
+    float err = INFINITY;
+    if (r <= R) {
+        const double c = 4.0 / 3.0 * PI_D;
+        const double K = kernel_grav_d(c * R * R * R, c * r * r * r);
+        const float y = surr_forward(S.w, (float)za, (float)zb);
+        const double Kh = fmax(exp((double)S.mu + (double)S.sigma * (double)y) - (double)S.k_floor, 0.0);
+        if (K > 0.0) err = (float)(fabs(Kh - K) / K);
+    }
+    for (int o = 8; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o, 16));
+    if (q == 0) {
+        mask[tile] = err <= tol ? 1u : 0u;
+        max_err[tile] = err;
+    }
+}
+
+// K^ of a pair of volumes (or -1: use the plain kernel); out of line so that the
+// network's working set stays out of the register allocation of the step kernels
+__device__ __noinline__ float surr_pair_kernel(const SurrogateDev* __restrict__ S, double v1, double v2)
+{
+    const float c = 0.238732414637843f;   // 3 / (4 pi)
+    const float r1 = cbrtf((float)v1 * c), r2 = cbrtf((float)v2 * c);
+    const SurrogateDev D = *S;
+    return surr_kernel(D, fmaxf(r1, r2), fminf(r1, r2));
+}
+
+// Device-side evaluation for tests: K^ (or -1 where the plain kernel is used) per pair.
+__global__ void surr_eval_kernel(SurrogateDev S, const double* R, const double* r, uint64_t n, float* K)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        K[i] = surr_kernel(S, (float)fmax(R[i], r[i]), (float)fmin(R[i], r[i]));
+}
+
+}  // namespace sdm

@@ -20,7 +20,7 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "surrogate": 2}
 KERNEL_GOLOVIN = 0
 KERNEL_GRAVITATIONAL = 1
 
@@ -32,7 +32,13 @@ EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", 
            "sdm_init_state_segmented", "sdm_set_state", "sdm_get_state", "sdm_coalescence_step",
            "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_get_schedule", "sdm_set_schedule",
            "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
-           "sdm_launches_per_step", "sdm_coalescence_step_noalloc"]
+           "sdm_launches_per_step", "sdm_coalescence_step_noalloc", "sdm_surrogate_create", "sdm_surrogate_free",
+           "sdm_surrogate_train", "sdm_surrogate_build_mask", "sdm_surrogate_params_io", "sdm_surrogate_info",
+           "sdm_surrogate_loss_grad", "sdm_surrogate_eval", "sdm_attach_surrogate"]
+
+
+class SurrogateParams(C.Structure):
+    _fields_ = [("n_train", C.c_uint64), ("seed", C.c_uint64), ("r_min", C.c_double), ("r_max", C.c_double)]
 
 
 class SDMError(RuntimeError):
@@ -103,8 +109,18 @@ def lib(build_if_needed: bool = True):
         L.sdm_get_profile.argtypes = [vp, vp, vp]
         L.sdm_launches_per_step.argtypes = [vp, u32, vp]
         L.sdm_coalescence_step_noalloc.argtypes = [vp, vp, u32, u64, u32, f64, u32, C.POINTER(StepParams), vp]
+        L.sdm_surrogate_create.argtypes = [C.POINTER(vp), C.POINTER(SurrogateParams), vp]
+        L.sdm_surrogate_free.argtypes = [vp]
+        L.sdm_surrogate_free.restype = None
+        L.sdm_surrogate_train.argtypes = [vp, u32, u32, C.c_float, vp]
+        L.sdm_surrogate_build_mask.argtypes = [vp, C.c_float, vp, vp]
+        L.sdm_surrogate_params_io.argtypes = [vp, vp, i32]
+        L.sdm_surrogate_info.argtypes = [vp, vp]
+        L.sdm_surrogate_loss_grad.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.sdm_surrogate_eval.argtypes = [vp, vp, vp, u64, vp]
+        L.sdm_attach_surrogate.argtypes = [vp, vp]
         for name in EXPORTS:
-            if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free"):
+            if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free", "sdm_surrogate_free"):
                 getattr(L, name).restype = i32
         _lib = L
         return L
@@ -246,6 +262,13 @@ class State:
         _check(self._L.sdm_totals(self._h, C.byref(n), C.byref(m), C.byref(live)), "sdm_totals")
         return int(n.value), float(m.value), int(live.value)
 
+    def attach_surrogate(self, surrogate):
+        """Use a trained Surrogate for precision="surrogate" steps (None detaches); the State keeps a
+        reference so the surrogate outlives its use."""
+        self._surrogate = surrogate
+        _check(self._L.sdm_attach_surrogate(self._h, surrogate._h if surrogate is not None else None),
+               "sdm_attach_surrogate")
+
     def sync(self):
         _check(self._L.sdm_sync(self._h), "sdm_sync")
 
@@ -302,6 +325,78 @@ class State:
                                       C.c_void_p(pl.data_ptr() if lite else None),
                                       C.c_void_p(el.data_ptr() if lite else None)), "sdm_eval_pairs")
         return (p64, p32, e32, pl, el) if lite else (p64, p32, e32)
+
+
+class Surrogate:
+    """Learned stand-in for the gravitational kernel (sdm_surrogate_*): create, train on the
+    GPU, build the fallback mask, attach to a State for precision="surrogate"."""
+
+    N_PARAM = 8577
+
+    def __init__(self, n_train=10_000_000, seed=7, r_min=1e-6, r_max=3e-3, stream=None):
+        self._L = lib()
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p = SurrogateParams(int(n_train), int(seed), float(r_min), float(r_max))
+        h = C.c_void_p()
+        _check(self._L.sdm_surrogate_create(C.byref(h), C.byref(p), C.c_void_p(self.stream.cuda_stream)),
+               "sdm_surrogate_create")
+        self._h = h
+
+    def train(self, steps, batch=8192, lr=2e-3):
+        loss = np.zeros(steps, np.float32)
+        _check(self._L.sdm_surrogate_train(self._h, int(steps), int(batch), float(lr),
+                                           loss.ctypes.data_as(C.c_void_p)), "sdm_surrogate_train")
+        return loss
+
+    def build_mask(self, tol=0.01):
+        frac = C.c_double()
+        err = np.zeros(256 * 256, np.float32)
+        _check(self._L.sdm_surrogate_build_mask(self._h, float(tol), C.byref(frac), err.ctypes.data_as(C.c_void_p)),
+               "sdm_surrogate_build_mask")
+        return float(frac.value), err.reshape(256, 256)
+
+    def params(self):
+        w = np.zeros(self.N_PARAM, np.float32)
+        _check(self._L.sdm_surrogate_params_io(self._h, w.ctypes.data_as(C.c_void_p), 0), "sdm_surrogate_params_io")
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        _check(self._L.sdm_surrogate_params_io(self._h, w.ctypes.data_as(C.c_void_p), 1), "sdm_surrogate_params_io")
+
+    def info(self):
+        out = np.zeros(6, np.float64)
+        _check(self._L.sdm_surrogate_info(self._h, out.ctypes.data_as(C.c_void_p)), "sdm_surrogate_info")
+        return dict(zip(["c0", "c1", "mu", "sigma", "k_floor", "r_ratio"], out.tolist()))
+
+    def loss_grad(self, x, t):
+        """x: CUDA float32 [n, 2], t: CUDA float32 [n] -> (loss, grad numpy [8577])."""
+        loss = C.c_float()
+        grad = np.zeros(self.N_PARAM, np.float32)
+        _check(self._L.sdm_surrogate_loss_grad(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                               C.byref(loss), grad.ctypes.data_as(C.c_void_p)),
+               "sdm_surrogate_loss_grad")
+        return float(loss.value), grad
+
+    def eval(self, R, r):
+        """R, r: CUDA float64 radii -> CUDA float32 K^ (-1 where the plain kernel is used)."""
+        torch = _torch()
+        K = torch.empty(R.numel(), dtype=torch.float32, device=R.device)
+        _check(self._L.sdm_surrogate_eval(self._h, C.c_void_p(R.data_ptr()), C.c_void_p(r.data_ptr()), R.numel(),
+                                          C.c_void_p(K.data_ptr())), "sdm_surrogate_eval")
+        return K
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sdm_surrogate_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_inputs(s, n_attr=1, extra_attrs=None, stream=None, device_arrays=False):

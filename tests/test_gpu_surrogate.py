@@ -1,0 +1,107 @@
+"""The learned kernel surrogate on the GPU: backward pass, training, fallback mask, and steps that
+use it.
+
+* Loss and gradient of the library's training kernels equal the FP64 oracle's
+  (oracle/surrogate.py, same BF16-rounded parameters) to FP32 accuracy.
+* Training lowers the loss; where the fallback mask lets the network answer, its kernel values
+  are within a few per cent of the oracle's plain FP64 kernel.
+* Steps with precision="surrogate" keep every invariant of the method (mass, multiplicity
+  bookkeeping) and stay statistically close to the FP64 steps of the same seed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate as so
+from paper_2101_06318_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2101_06318_b300 import sdm  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def trained():
+    s = sdm.Surrogate(n_train=10_000_000, seed=11)
+    loss = s.train(8000, batch=8192, lr=5e-3)
+    frac, err = s.build_mask(0.01)
+    return s, loss, frac, err
+
+
+def test_loss_and_gradient_match_oracle():
+    s = sdm.Surrogate(n_train=100_000, seed=3)
+    rng = np.random.default_rng(4)
+    w = rng.normal(0, 0.2, so.N_PARAM).astype(np.float32)
+    s.set_params(w)
+    assert np.array_equal(s.params(), w)
+    n = 1000                                       # not a multiple of the 64-sample tile
+    z = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    t = rng.normal(0, 1, n).astype(np.float32)
+    loss, g = s.loss_grad(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda())
+    lo, go = so.loss_grad(w, z.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-4)
+    scale = np.abs(go).max()
+    assert np.max(np.abs(g - go)) <= 2e-4 * scale, np.max(np.abs(g - go)) / scale
+    # direction as well as size
+    assert np.dot(g, go) / (np.linalg.norm(g) * np.linalg.norm(go)) > 0.99999
+
+
+def test_training_lowers_loss_and_mask_bounds_error(trained):
+    s, loss, frac, err = trained
+    assert loss[-100:].mean() < 0.002 * loss[:10].mean()
+    # the share of the (R >= r) grid within 1% at every probe point: the network is small for a
+    # target spanning 16 orders of magnitude with kinks (regime borders, table nodes)
+    assert frac > 0.05, frac
+    # random pairs in the training range: where the network answers it is close to the plain kernel
+    rng = np.random.default_rng(5)
+    n = 20000
+    lr = rng.uniform(np.log(1e-6), np.log(3e-3), (2, n))
+    R, r = np.exp(lr.max(axis=0)), np.exp(lr.min(axis=0))
+    K = s.eval(torch.from_numpy(R).cuda(), torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    used = K >= 0
+    assert used.mean() > 0.03
+    c = 4.0 / 3.0 * np.pi
+    rel = []
+    for i in np.flatnonzero(used)[:3000]:
+        Ko = oracle.kernel(1, c * R[i] ** 3, c * r[i] ** 3)
+        if Ko > 0:
+            rel.append(abs(K[i] - Ko) / Ko)
+    rel = np.array(rel)
+    assert np.quantile(rel, 0.99) < 0.03, np.quantile(rel, 0.99)
+    assert rel.max() < 0.2, rel.max()
+    # outside the training range the plain kernel is used
+    out = s.eval(torch.tensor([1e-2, 5e-7], dtype=torch.float64).cuda(),
+                 torch.tensor([1e-5, 4e-7], dtype=torch.float64).cuda()).cpu().numpy()
+    assert np.all(out < 0)
+
+
+def test_surrogate_steps_keep_invariants_and_track_fp64(trained):
+    s, _, _, _ = trained
+    box = inputs.gravitational_box(n_sd=1 << 16, seed=9)
+    res = {}
+    for prec in ("fp64", "surrogate"):
+        g = sdm.from_inputs(box)
+        if prec == "surrogate":
+            g.attach_surrogate(s)
+        n0, m0, _ = g.totals()
+        coll = 0
+        for k in range(20):
+            st = g.step(1.0, 42, k, 1, precision=prec, stats=True)
+            coll += st["n_collisions"]
+        n1, m1, live = g.totals()
+        assert m1 == pytest.approx(m0, rel=1e-12)        # coalescence conserves mass in any mode
+        assert n1 <= n0
+        res[prec] = (coll, n1)
+        g.close()
+    c64, cs = res["fp64"][0], res["surrogate"][0]
+    assert abs(cs - c64) <= 0.1 * c64 + 30, (cs, c64)
+
+
+def test_surrogate_precision_needs_an_attached_surrogate():
+    g = sdm.from_inputs(inputs.gravitational_box(n_sd=4096, seed=1))
+    with pytest.raises(sdm.SDMError):
+        g.step(1.0, 1, 0, 1, precision="surrogate")
+    g.close()
