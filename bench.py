@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2101_06318_b300 import inputs  # noqa: E402
 
+SURROGATE_TRAIN_STEPS = 8000
 METRIC = "coalescence super-droplet-steps/s on 1 B300, % HBM roofline; batched/surrogate vs FP64"
 UNIT = "SD-steps/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -222,10 +223,23 @@ def run_ours(args, rank, world, local_rank):
     s = workload(args.workload, rank)
     n = len(s["xi"])
     prec = args.precision
+    surr_info = None
     with torch.cuda.stream(stream):
         st = sdm.from_inputs(s)
         if args.schedule:
             st.set_schedule(**json.loads(args.schedule))
+        if prec == "surrogate":
+            # the network is trained once, outside the timed region, by the library's own kernels
+            t0 = time.perf_counter()
+            surr = sdm.Surrogate(n_train=10_000_000, seed=7, r_min=1e-6, r_max=3e-3, stream=stream)
+            loss = surr.train(SURROGATE_TRAIN_STEPS, batch=8192, lr=5e-3)
+            frac, _ = surr.build_mask(0.01)
+            torch.cuda.synchronize()
+            surr_info = {"train_steps": SURROGATE_TRAIN_STEPS, "train_batch": 8192,
+                         "train_s": round(time.perf_counter() - t0, 3), "final_loss": float(loss[-50:].mean()),
+                         "mask_tiles_within_1pct": frac}
+            st.attach_surrogate(surr)
+            ref = sdm.from_inputs(s)             # plain FP64 steps of the same seed, for the accuracy figures
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         step = 0
         for _ in range(args.warmup):
@@ -273,6 +287,18 @@ def run_ours(args, rank, world, local_rank):
         stats = st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], stats=True)
         step += 1
         launches = st.launches_per_step() * args.steps
+        if surr_info is not None:
+            # accuracy against plain FP64 steps of the same seed and step indices
+            for k in range(step):
+                ref.step(s["dt"], 42, k, 1, precision="fp64", golovin_b=s["golovin_b"])
+            edges = np.geomspace(1e-6, 5e-3, 101)
+            sp_s, sp_r = st.spectrum(edges), ref.spectrum(edges)
+            n_s, _, _ = st.totals()
+            n_r, _, _ = ref.totals()
+            surr_info.update({"steps_compared": step,
+                              "spectrum_l1_vs_fp64": float(np.abs(sp_s - sp_r).sum() / max(sp_r.sum(), 1e-300)),
+                              "droplet_count_rel_diff_vs_fp64": (n_s - n_r) / max(n_r, 1)})
+            ref.close()
 
         # e2e: host (pinned) buffers in, step, host buffers out, through the C ABI
         xi_h, at_h, _ = st.get_state()
@@ -316,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "surrogate": "bf16/f32"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_sd": n, "n_cell": len(s["dv"]), "kernel": "gravitational",
                    "precision": prec, "dt_s": s["dt"], "dV_m3": float(s["dv"][0]), "n0_m3": 1e8,
@@ -330,6 +356,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "stats_per_step": stats,
     }
+    if surr_info is not None:
+        line["surrogate"] = surr_info
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(s)
     print(json.dumps(line), flush=True)
@@ -342,7 +370,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gravitational_box", choices=sorted(inputs.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "surrogate"])
     ap.add_argument("--schedule", default=None, help="JSON of sdm_schedule fields")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
