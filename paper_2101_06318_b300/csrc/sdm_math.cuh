@@ -580,6 +580,45 @@ __device__ __forceinline__ float efficiency_f(const EffTab* __restrict__ T, floa
     return e0 + t * (e1 - e0);
 }
 
+// E together with a bound dE on |E - E_exact| (absolute), E_exact the efficiency of the
+// exact radii (u = 2^-24): the interpolation weight along q is off by at most
+// 10 * 8u * q (radii 3.4u each, the division and the scaling by 10), along R by at
+// most 4.4u R / dR + 2u; the weights multiply the table steps actually used, and the
+// roundings of the interpolation and of the float copy of the table add at most 12u.
+// dE < 0 when R or 10 q lies too close to a table node for the interval to be certain
+// (the caller then uses the pair-independent bound).
+__device__ __forceinline__ float efficiency_f_err(const EffTab* __restrict__ T, float R, float q, float& dE)
+{
+    const float u = 0x1p-24f;
+    int i;
+    float t, dt;
+    bool near = false;
+    if (R <= 10e-6f) { i = 0; t = 0.f; dt = 0.f; near = R >= 10e-6f * (1.0f - 8.0f * u); }
+    else if (R >= 1000e-6f) { i = EFF_NR - 2; t = 1.f; dt = 0.f; near = R <= 1000e-6f * (1.0f + 8.0f * u); }
+    else {
+        i = (R >= 20e-6f) + (R >= 30e-6f) + (R >= 40e-6f) + (R >= 50e-6f) + (R >= 60e-6f) + (R >= 80e-6f) +
+            (R >= 100e-6f) + (R >= 150e-6f) + (R >= 200e-6f) + (R >= 300e-6f);
+        t = (R - T->R[i]) * T->inv_dR[i];
+        dt = (4.4f * u) * (R * T->inv_dR[i]) + 2.0f * u;
+        near = t <= 2.0f * dt || t >= 1.0f - 2.0f * dt;
+    }
+    const float s = q * 10.f;
+    const float sf = __fadd_rd(s, 0x1p23f);
+    int j = (int)(__float_as_uint(sf) - 0x4B000000u);
+    float w;
+    if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.f; }
+    else w = s - (sf - 0x1p23f);
+    const float dw = (80.0f * u) * q + (10.0f * u) * q;
+    near = near || w <= 2.0f * dw || (j < EFF_NQ - 2 && w >= 1.0f - 2.0f * dw);
+    const float* E = T->E + i * EFF_NQ + j;
+    const float d0 = E[1] - E[0], d1 = E[EFF_NQ + 1] - E[EFF_NQ];
+    const float e0 = E[0] + w * d0;
+    const float e1 = E[EFF_NQ] + w * d1;
+    const float Dw = fmaxf(fabsf(d0), fabsf(d1)), Dt = fabsf(e1 - e0) + 4.0f * u;
+    dE = near ? -1.0f : Dw * dw + Dt * dt + 12.0f * u;
+    return e0 + t * (e1 - e0);
+}
+
 // p in FP32 with its bound.  scale32 = max(xi) * S_c * dt / dV in FP32.
 // A non-finite or NaN err marks the pair for the FP64 path.
 __device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_t kid, double v1d, double v2d,
@@ -598,11 +637,25 @@ __device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_
     const float r1 = cbrtf(v1 * c), r2 = cbrtf(v2 * c);
     const float vt1 = vt_f(r1), vt2 = vt_f(r2);
     const float R = fmaxf(r1, r2), rs = fminf(r1, r2);
-    const float E = efficiency_f(T, R, rs / R);
+    float dE;
+    const float E = efficiency_f_err(T, R, rs / R, dE);
     const float s = r1 + r2;
     const float base = scale32 * ((float)PI_D * (s * s));
-    o.p = (base * fabsf(vt1 - vt2)) * E;
-    o.err = (base * (vt1 + vt2)) * GRAV_REL_BOUND + ABS_SLACK;
+    const float dvt = fabsf(vt1 - vt2), svt = vt1 + vt2;
+    o.p = (base * dvt) * E;
+    if (dE >= 0.0f) {
+        // Pair-specific bound (u = 2^-24), relative to base = scale pi (r1+r2)^2:
+        //  scale (9u), (r1+r2)^2 with radii within 3.4u (9.8u), pi and the products (4u) and
+        //  the final roundings: |dvt| E 25u;  fall speeds within 15u of the exact ones
+        //  (regime choice included), so |dvt| is off by 15u (vt1 + vt2) absolute: E 15u svt;
+        //  the efficiency: |dvt| dE;  the exact sequence's own error: 2^-45 svt.
+        // Doubled, and 64u more for evaluating it from the rounded base.
+        const float u = 0x1p-24f;
+        const float e = dvt * (25.0f * u * E + dE) + svt * (15.0f * u * E + 0x1p-45f);
+        o.err = (base * e) * (2.0f + 128.0f * u) + ABS_SLACK;
+    } else {
+        o.err = (base * svt) * GRAV_REL_BOUND + ABS_SLACK;
+    }
     return o;
 }
 

@@ -226,8 +226,8 @@ def test_fp32_bound_holds_and_fp64_matches_oracle():
         ratio = np.abs(p64 - p32) / e32
         worst = max(worst, float(ratio.max()))
         assert np.all(np.abs(p64 - p32) <= e32), (kid, ratio.max())
-    # the bound is not vacuous either: it is used at well under its full width
-    assert worst < 0.5, worst
+    # the bound is not vacuous either: its width is used, but never exceeded
+    assert 0.01 < worst <= 1.0, worst
     # the second filter (gravitational kernel): its FP64 value from refined FP32 seeds stays within
     # its bound of the exact sequence's value, also at regime joins, table nodes and near-equal radii
     worst_lite = 0.0
