@@ -894,17 +894,6 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
 #pragma unroll
                     for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
                 }
-                feistel_n<NP>(P, e);
-                if (!same_bits) {            // uniform: the live count left the width's power of two
-                    prp_set_domain(P, n);
-#pragma unroll
-                    for (int j = 0; j < (int)PRP_QPT; ++j)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
-                    feistel_n<NP>(P, e);
-                } else {
-                    P.n = n;
-                }
                 bool h0[PRP_QPT], h1[PRP_QPT];
                 uint32_t use = 0;
 #pragma unroll
@@ -914,16 +903,34 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
                     use |= (h0[j] ? 3u : 0u) << (4 * j);
                     use |= (h1[j] ? 12u : 0u) << (4 * j);
                 }
-                prp_walk_n<NP>(P, use, e);
-                // gather the volumes' high words (all the early exit needs with the cell's
-                // multiplicity bound), then phi while they are in flight
+                // Two halves: the second half's bijection images are computed while the first
+                // half's gathers are in flight.  Only the volumes' high words are gathered: with
+                // the cell's multiplicity bound they are all the early exit needs.
+                constexpr int NH = NP / 2;
                 uint32_t vh[NP];
                 const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    e[i] += C.slot_begin;              // slots from here on
-                    vh[i] = ((use >> i) & 1u) ? attr_hi[2 * (size_t)e[i]] : 0u;
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t eh[NH];
+#pragma unroll
+                    for (int i = 0; i < NH; ++i) eh[i] = e[NH * hh + i];
+                    feistel_n<NH>(P, eh);
+                    if (!same_bits) {        // uniform: the live count left the width's power of two
+                        if (hh == 0) prp_set_domain(P, n);
+#pragma unroll
+                        for (int i = 0; i < NH; ++i) eh[i] = e[NH * hh + i];
+                        feistel_n<NH>(P, eh);
+                    } else {
+                        P.n = n;
+                    }
+                    prp_walk_n<NH>(P, use >> (NH * hh), eh);
+#pragma unroll
+                    for (int i = 0; i < NH; ++i) {
+                        e[NH * hh + i] = eh[i] + C.slot_begin;   // slots from here on
+                        vh[NH * hh + i] = ((use >> (NH * hh + i)) & 1u) ? attr_hi[2 * (size_t)e[NH * hh + i]] : 0u;
+                    }
                 }
+                // phi while the gathers are in flight, then the early exit
 #pragma unroll
                 for (int j = 0; j < (int)PRP_QPT; ++j) {
                     U4 w = {0, 0, 0, 0};
