@@ -43,8 +43,11 @@
  *       (key, i) ascending (the paper's GPU approach, Sec. 3.2).
  *   SDM_SHUFFLE_PRP: cells with n <= 256 as SORT; larger cells L'[q] = L[P(q)]
  *       with P the keyed bijection of [0, n) given by an eight-round
- *       alternating Feistel network on ceil(log2 n) bits (left half the
- *       smaller), round function lowbias32(v ^ K_r), round keys
+ *       alternating Feistel network on Z_A x Z_B, x = L B + R (n = 2^k:
+ *       A = 2^floor(k/2), B = 2^(k - floor(k/2)); otherwise A = ceil(sqrt n),
+ *       B = ceil(n / A)), rounds L = (L + floor(h A / 2^32)) mod A and
+ *       R = (R + floor(h B / 2^32)) mod B with h = lowbias32(v ^ K_r) of the
+ *       other half v, round keys
  *       K_0..3 = philox(0, c, s, 2), K_4..7 = philox(1, c, s, 2), and
  *       cycle-walking into [0, n).  No sort and no data exchange is needed.
  *   Pair m is (L'[2m], L'[2m+1]) (Sec. 2.2 Step 1, Fig. "pair_flag").

@@ -48,12 +48,14 @@
  *         L'_c = L_c sorted ascending by (key, i)       (the paper's GPU way).
  *   PRP:  cells with n <= 256 are shuffled exactly as by SORT; for n > 256,
  *         L'_c[q] = L_c[P(q)] with P a keyed bijection of [0, n): an
- *         eight-round alternating Feistel network on k = ceil(log2 n) bits
- *         (left half floor(k/2) bits), round function lowbias32(v ^ K_r)
- *         (C. Wellons' 32-bit integer hash), round keys K_0..K_3 =
- *         philox(0, c, s, 2), K_4..K_7 = philox(1, c, s, 2), and
+ *         eight-round alternating Feistel network on Z_A x Z_B (x = L B + R;
+ *         A B = n with halves of floor(k/2) and k - floor(k/2) bits when
+ *         n = 2^k, else A = ceil(sqrt n), B = ceil(n / A)), round function
+ *         h = lowbias32(v ^ K_r) (C. Wellons' 32-bit integer hash) of the other
+ *         half v, added as floor(h M / 2^32) modulo the half's size M, round keys
+ *         K_0..K_3 = philox(0, c, s, 2), K_4..K_7 = philox(1, c, s, 2), and
  *         cycle-walking (apply the network again while the value is >= n) to
- *         stay inside [0, n).  (Below ~256 elements a Feistel network of this
+ *         stay inside [0, n); A B < n + A makes walking rare.  (Below ~256 elements a Feistel network of this
  *         depth is measurably non-uniform; above, the pairings it produces
  *         pass the uniformity tests.)
  *   Pair m is (L'_c[2m], L'_c[2m+1]), m < floor(n/2).
@@ -157,27 +159,51 @@ static uint32_t ceil_log2_u32(uint32_t n)
     return k;
 }
 
-/* One pass of the alternating Feistel network on k bits. */
-static uint32_t feistel(uint32_t q, uint32_t k, const uint32_t K[SDMO_PRP_ROUNDS])
+/* The network's domain for a list of n elements: x = L * B + R with L < A, R < B.
+ *   n a power of two, n = 2^k: A = 2^floor(k/2), B = 2^(k - floor(k/2)) (so A B = n);
+ *   otherwise: A = ceil(sqrt(n)), B = ceil(n / A) (so n <= A B < n + A). */
+static void prp_domain(uint32_t n, uint32_t* A, uint32_t* B)
 {
-    uint32_t a = k >> 1, b = k - a;
-    uint32_t mask_a = a ? (uint32_t)((1ull << a) - 1) : 0u;
-    uint32_t mask_b = (uint32_t)((1ull << b) - 1);
-    uint32_t L = b < 32 ? q >> b : 0u, R = q & mask_b;
-    int r;
-    for (r = 0; r < SDMO_PRP_ROUNDS; ++r) {
-        if ((r & 1) == 0) L ^= lowbias32(R ^ K[r]) & mask_a;
-        else R ^= lowbias32(L ^ K[r]) & mask_b;
+    if (n != 0 && (n & (n - 1)) == 0) {
+        uint32_t k = ceil_log2_u32(n), a = k >> 1;
+        *A = 1u << a;
+        *B = 1u << (k - a);
+        return;
     }
-    return (b < 32 ? (L << b) : 0u) | R;
+    uint32_t a = 1;
+    while ((uint64_t)a * a < n) ++a;
+    *A = a;
+    *B = (n + a - 1) / a;
 }
 
-/* P(q): the keyed bijection of [0, n) (cycle-walking on [0, 2^k)). */
+/* One pass of the alternating Feistel network on Z_A x Z_B: for r = 0..7, with
+ * h = lowbias32(v ^ K_r) of the other half v,
+ *   even r: L = (L + floor(h A / 2^32)) mod A;   odd r: R = (R + floor(h B / 2^32)) mod B.
+ * Each round is a bijection of Z_A x Z_B (it shifts one half by an amount that depends only on
+ * the other half), so the pass is one too. */
+static uint32_t feistel(uint32_t q, uint32_t A, uint32_t B, const uint32_t K[SDMO_PRP_ROUNDS])
+{
+    uint32_t L = q / B, R = q % B;
+    int r;
+    for (r = 0; r < SDMO_PRP_ROUNDS; ++r) {
+        if ((r & 1) == 0) {
+            const uint32_t h = lowbias32(R ^ K[r]);
+            L = (uint32_t)((L + (((uint64_t)h * A) >> 32)) % A);
+        } else {
+            const uint32_t h = lowbias32(L ^ K[r]);
+            R = (uint32_t)((R + (((uint64_t)h * B) >> 32)) % B);
+        }
+    }
+    return L * B + R;
+}
+
+/* P(q): the keyed bijection of [0, n) (cycle-walking on [0, A B)). */
 uint32_t sdmo_prp(uint32_t q, uint32_t n, const uint32_t K[SDMO_PRP_ROUNDS])
 {
-    uint32_t k = ceil_log2_u32(n);
-    uint32_t e = feistel(q, k, K);
-    while (e >= n) e = feistel(e, k, K);
+    uint32_t A, B;
+    prp_domain(n, &A, &B);
+    uint32_t e = feistel(q, A, B, K);
+    while (e >= n) e = feistel(e, A, B, K);
     return e;
 }
 

@@ -725,7 +725,7 @@ constexpr uint32_t PRP_WARPS = PRP_THREADS / 32;
 #endif
 constexpr uint32_t PRP_QPT = SDM_PRP_QPT;      // quads per thread and iteration
 constexpr uint32_t BIG_PARAM_CELLS = 8;        // large cells passed by value in the launch
-constexpr uint32_t PQ_CAP = 32 + 2 * 32 * PRP_QPT;   // queued pairs per warp (< 32 left + 2 per quad)
+constexpr uint32_t PQ_CAP = 2 * 32 * PRP_QPT;   // queued pairs per warp (2 per quad; emptied every iteration)
 
 struct BigLaunch {
     uint32_t n_big, n_quads;
@@ -744,44 +744,111 @@ struct PairQueue {
 // are a loop with the keys rotated through registers, not unrolled: with the
 // state flushed from L2 before every step the instructions are fetched from
 // DRAM each time, and straight-line code of all rounds stalls on the fetch.
-template <int N>
+// N images through the network.  FULL: the domain is a power of two (A = 2^a,
+// B = 2^b), where floor(h M / 2^32) is a shift and the modulo a mask; otherwise
+// the general form (a multiply-high and a conditional subtraction).  Both forms
+// compute the same network on a power-of-two domain.
+template <int N, bool FULL>
 __device__ __forceinline__ void feistel_n(const Prp& P, uint32_t (&x)[N])
 {
     uint32_t L[N], R[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) { L[i] = x[i] >> P.b; R[i] = x[i] & P.mask_b; }
     uint32_t k0 = P.K[0], k1 = P.K[1], k2 = P.K[2], k3 = P.K[3], k4 = P.K[4], k5 = P.K[5], k6 = P.K[6],
              k7 = P.K[7];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (FULL) { L[i] = x[i] >> P.b; R[i] = x[i] & (P.B - 1u); }
+        else prp_split(P, x[i], L[i], R[i]);
+    }
 #pragma unroll 1
     for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) L[i] ^= lowbias32_tail(R[i] ^ k0) & P.mask_a;
-#pragma unroll
-        for (int i = 0; i < N; ++i) R[i] ^= lowbias32_tail(L[i] ^ k1) & P.mask_b;
+        for (int i = 0; i < N; ++i) {
+            if (FULL) prp_round_pair_pow2(P, k0, k1, L[i], R[i]);
+            else prp_round_pair(P, k0, k1, L[i], R[i]);
+        }
         k0 = k2; k1 = k3; k2 = k4; k3 = k5; k4 = k6; k5 = k7;
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) x[i] = (L[i] << P.b) | R[i];
+    for (int i = 0; i < N; ++i) x[i] = FULL ? ((L[i] << P.b) | R[i]) : L[i] * P.B + R[i];
 }
 
-// cycle-walking (only when n is not a power of two) of the images whose bit in
-// 'use' is set; the others (positions >= n) never walk
+// Cycle-walking of a warp's images by a work list instead of per-lane loops.
+// An image outside [0, n) goes through the network again until it lands inside;
+// the network's domain holds fewer than n + sqrt(n) + 1 elements, so few images
+// walk, but a per-lane loop would still keep the whole warp busy for the
+// longest walk of any of its 32 x N images.  Here the images still walking are compacted into a list
+// in shared memory and advanced WALK_ILP per lane per pass, so every pass runs
+// on full lanes.  The results are the same images the per-lane loop gives.
+constexpr int WALK_ILP = 4;
+struct WalkScratch {                       // per warp, two lists of (value, owner) used alternately
+    uint32_t val[2][256], res[256];
+    uint8_t tag[2][256];
+};
+
 template <int N>
-__device__ __forceinline__ void prp_walk_n(const Prp& P, uint32_t use, uint32_t (&e)[N])
+__device__ __forceinline__ void prp_walk_list(const Prp& P, uint32_t use, uint32_t (&e)[N], WalkScratch& W,
+                                              uint32_t lane)
 {
-    for (;;) {
-        uint32_t walk = 0;
+    static_assert(32 * N <= 256, "walk list too small");
+    uint32_t mine = 0;                     // images of this lane still outside [0, n)
 #pragma unroll
-        for (int i = 0; i < N; ++i) walk |= (((use >> i) & 1u) && e[i] >= P.n) ? (1u << i) : 0u;
-        if (!walk) break;
-        uint32_t f[N];
+    for (int i = 0; i < N; ++i) mine |= (((use >> i) & 1u) && e[i] >= P.n) ? (1u << i) : 0u;
+    if (!__any_sync(0xffffffffu, mine != 0)) return;
+    // list the walking images (owner = lane * N + i)
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int i = 0; i < N; ++i) f[i] = e[i];
-        feistel_n<N>(P, f);
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-            if ((walk >> i) & 1u) e[i] = f[i];
+    for (int i = 0; i < N; ++i) {
+        const bool w = (mine >> i) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, w);
+        if (w) {
+            const uint32_t k = cnt + __popc(m & ((1u << lane) - 1u));
+            W.val[0][k] = e[i];
+            W.tag[0][k] = lane * N + i;
+        }
+        cnt += __popc(m);
     }
+    uint32_t cur = 0;
+    for (uint32_t pass = 0; cnt > 0 && pass < 4096; ++pass) {   // each pass strictly shrinks or keeps the list
+        __syncwarp();
+        uint32_t x[WALK_ILP], t[WALK_ILP];
+        bool have[WALK_ILP];
+#pragma unroll
+        for (int w = 0; w < WALK_ILP; ++w) {
+            const uint32_t k = lane + 32 * w;
+            have[w] = k < cnt;
+            x[w] = have[w] ? W.val[cur][k] : 0u;
+            t[w] = have[w] ? W.tag[cur][k] : 0u;
+        }
+        feistel_n<WALK_ILP, false>(P, x);
+        uint32_t nxt = 0;
+#pragma unroll
+        for (int w = 0; w < WALK_ILP; ++w) {
+            const bool again = have[w] && x[w] >= P.n;
+            if (have[w] && !again) W.res[t[w]] = x[w];
+            const unsigned m = __ballot_sync(0xffffffffu, again);
+            if (again) {
+                const uint32_t k = nxt + __popc(m & ((1u << lane) - 1u));
+                W.val[cur ^ 1][k] = x[w];
+                W.tag[cur ^ 1][k] = t[w];
+            }
+            nxt += __popc(m);
+        }
+        // entries beyond 32 * WALK_ILP were not taken this pass: carry them over unchanged
+        for (uint32_t k = 32 * WALK_ILP + lane; k < cnt; k += 32) {
+            // appended after this pass's re-queued images (order does not matter)
+            const uint32_t dst = nxt + (k - 32 * WALK_ILP);
+            W.val[cur ^ 1][dst] = W.val[cur][k];
+            W.tag[cur ^ 1][dst] = W.tag[cur][k];
+        }
+        if (cnt > 32 * WALK_ILP) nxt += cnt - 32 * WALK_ILP;
+        cnt = nxt;
+        cur ^= 1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if ((mine >> i) & 1u) e[i] = W.res[lane * N + i];
+    __syncwarp();
 }
 
 // Evaluate the top 'take' queued pairs of this warp (lanes < take) and pop them.
@@ -825,12 +892,84 @@ __device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, u
     qcnt += __popc(m);
 }
 
+// The quads [sa, sb) of one large cell for one warp: per iteration PRP_QPT quads
+// per lane (quads g, g + 32, ...; a warp-uniform trip count), their bijection
+// images, the gathers of the volumes' high words, the early exit and the queue
+// of pairs that need the kernel.  FULL: n = A B is a power of two, so no image
+// walks and the rounds take their shift-and-mask form.
+template <bool SURR, bool FULL>
+__device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* __restrict__ tab, const CellCtx& cc,
+                                               const Prp& P, const BigCell& C, uint32_t sa, uint32_t sb,
+                                               uint32_t step, const float* __restrict__ tb, float c_upx, PairQueue& Q,
+                                               uint32_t& qcnt, LocalStats& ls, uint32_t* rflag, uint32_t warp,
+                                               uint32_t lane, uint32_t nt)
+{
+    const uint32_t npairs = cc.n >> 1;
+    // PRP_QPT quads per thread and iteration: g, g + 32, ... (warp-uniform trip count)
+    constexpr int NP = 4 * PRP_QPT;            // positions per thread and iteration
+    for (uint32_t base = sa + warp * 32 * PRP_QPT; base < sb; base += PRP_QPT * nt) {
+        uint32_t e[NP], qj[PRP_QPT];
+#pragma unroll
+        for (int j = 0; j < (int)PRP_QPT; ++j) {
+            qj[j] = base + 32 * j + lane - C.quad_begin;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
+        }
+        bool h0[PRP_QPT], h1[PRP_QPT];
+        uint32_t use = 0;
+#pragma unroll
+        for (int j = 0; j < (int)PRP_QPT; ++j) {
+            h0[j] = base + 32 * j + lane < sb && 2 * qj[j] < npairs;
+            h1[j] = h0[j] && 2 * qj[j] + 1 < npairs;
+            use |= (h0[j] ? 3u : 0u) << (4 * j);
+            use |= (h1[j] ? 12u : 0u) << (4 * j);
+        }
+        // Two halves: the second half's bijection images are computed while the first
+        // half's gathers are in flight.  Only the volumes' high words are gathered: with
+        // the cell's multiplicity bound they are all the early exit needs.
+        constexpr int NH = NP / 2;
+        uint32_t vh[NP];
+        const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t eh[NH];
+#pragma unroll
+            for (int i = 0; i < NH; ++i) eh[i] = e[NH * hh + i];
+            feistel_n<NH, FULL>(P, eh);
+            // the pair queue is empty here: its memory holds the walk list
+            if (!FULL) prp_walk_list<NH>(P, use >> (NH * hh), eh, *reinterpret_cast<WalkScratch*>(&Q), lane);
+#pragma unroll
+            for (int i = 0; i < NH; ++i) {
+                e[NH * hh + i] = eh[i] + C.slot_begin;   // slots from here on
+                vh[NH * hh + i] = ((use >> (NH * hh + i)) & 1u) ? attr_hi[2 * (size_t)e[NH * hh + i]] : 0u;
+            }
+        }
+        // phi while the gathers are in flight, then the early exit
+#pragma unroll
+        for (int j = 0; j < (int)PRP_QPT; ++j) {
+            U4 w = {0, 0, 0, 0};
+            if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.seed_lo, a.seed_hi);
+            exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
+                          c_upx, ls, lane);
+            exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
+                          w.w, tb, c_upx, ls, lane);
+        }
+        if (FULL) {
+            while (qcnt >= 32) drain_queue<SURR>(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
+        } else {                      // empty the queue for the next walk list
+            while (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, min(qcnt, 32u), ls, rflag, lane);
+        }
+    }
+    if (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
+}
+
 template <bool SURR>
 __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kernel(StepArgs a, BigLaunch L,
                                                                                  BigBook bk)
 {
     const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
     __shared__ PairQueue pq[PRP_WARPS];
+    static_assert(sizeof(WalkScratch) <= sizeof(PairQueue), "the walk list shares the pair queue's memory");
     __shared__ uint32_t wt[40];
     __shared__ uint32_t key_s[PRP_MIN_N];
     __shared__ uint16_t srt_s[PRP_MIN_N];
@@ -867,16 +1006,14 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         const uint32_t q_end = c + 1 < L.n_big ? (by_value ? L.pc[c + 1].quad_begin : L.cells[c + 1].quad_begin)
                                                : L.n_quads;
         const uint32_t sa = max(qa, C.quad_begin), sb = min(qb, q_end);
-        // the cell's context, in every thread.  The live count n is loading while the round
-        // keys are derived and the first bijection images are computed on the domain of the
-        // cell's width (the same halves whenever ceil(log2 n) = ceil(log2 width))
+        // the cell's context, in every thread; the round keys are derived while the live
+        // count n is loading
         const uint32_t n = min(a.n_live[C.cell], C.width);
         const uint32_t kid = (uint32_t)a.kid[C.cell];
         const double dv = a.dv[C.cell];
         const float xpow = L.xpow[c];
         Prp P;
         prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, C.width);
-        const bool same_bits = prp_bits(n) == prp_bits(C.width);
         const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
         uint32_t* const rflag = &bk.removed[c];
         const uint32_t npairs = n >> 1;
@@ -884,65 +1021,15 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
             const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
             const CellCtx cc{C.cell, n, kid, s32, dv};
             const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xpow);
-            // PRP_QPT quads per thread and iteration: g, g + 32, ... (warp-uniform trip count)
-            constexpr int NP = 4 * PRP_QPT;            // positions per thread and iteration
-            for (uint32_t base = sa + warp * 32 * PRP_QPT; base < sb; base += PRP_QPT * nt) {
-                uint32_t e[NP], qj[PRP_QPT];
-#pragma unroll
-                for (int j = 0; j < (int)PRP_QPT; ++j) {
-                    qj[j] = base + 32 * j + lane - C.quad_begin;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) e[4 * j + i] = 4 * qj[j] + i;
-                }
-                bool h0[PRP_QPT], h1[PRP_QPT];
-                uint32_t use = 0;
-#pragma unroll
-                for (int j = 0; j < (int)PRP_QPT; ++j) {
-                    h0[j] = base + 32 * j + lane < sb && 2 * qj[j] < npairs;
-                    h1[j] = h0[j] && 2 * qj[j] + 1 < npairs;
-                    use |= (h0[j] ? 3u : 0u) << (4 * j);
-                    use |= (h1[j] ? 12u : 0u) << (4 * j);
-                }
-                // Two halves: the second half's bijection images are computed while the first
-                // half's gathers are in flight.  Only the volumes' high words are gathered: with
-                // the cell's multiplicity bound they are all the early exit needs.
-                constexpr int NH = NP / 2;
-                uint32_t vh[NP];
-                const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    uint32_t eh[NH];
-#pragma unroll
-                    for (int i = 0; i < NH; ++i) eh[i] = e[NH * hh + i];
-                    feistel_n<NH>(P, eh);
-                    if (!same_bits) {        // uniform: the live count left the width's power of two
-                        if (hh == 0) prp_set_domain(P, n);
-#pragma unroll
-                        for (int i = 0; i < NH; ++i) eh[i] = e[NH * hh + i];
-                        feistel_n<NH>(P, eh);
-                    } else {
-                        P.n = n;
-                    }
-                    prp_walk_n<NH>(P, use >> (NH * hh), eh);
-#pragma unroll
-                    for (int i = 0; i < NH; ++i) {
-                        e[NH * hh + i] = eh[i] + C.slot_begin;   // slots from here on
-                        vh[NH * hh + i] = ((use >> (NH * hh + i)) & 1u) ? attr_hi[2 * (size_t)e[NH * hh + i]] : 0u;
-                    }
-                }
-                // phi while the gathers are in flight, then the early exit
-#pragma unroll
-                for (int j = 0; j < (int)PRP_QPT; ++j) {
-                    U4 w = {0, 0, 0, 0};
-                    if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.seed_lo, a.seed_hi);
-                    exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
-                                  c_upx, ls, lane);
-                    exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
-                                  w.w, tb, c_upx, ls, lane);
-                }
-                while (qcnt >= 32) drain_queue<SURR>(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
+            if (P.pow2 && n == C.width) {
+                prp_cell_quads<SURR, true>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp, lane,
+                                           nt);
+            } else {
+                if (!prp_same_network(P, n)) prp_set_domain(P, n);
+                P.n = n;
+                prp_cell_quads<SURR, false>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp, lane,
+                                            nt);
             }
-            if (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
         } else if (n >= 2 && C.quad_begin >= qa) {
             // few live SDs left in a large cell: sorted by key by the CTA holding the cell's
             // first quad (n, qa and the cell are the same in all threads: a uniform branch)

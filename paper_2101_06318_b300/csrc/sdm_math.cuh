@@ -54,9 +54,12 @@ __device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, 
 
 // ---------------------------------------------------------------------------
 // PRP shuffle: a keyed bijection P of [0, n) for cells of more than 256 live
-// SDs -- an eight-round alternating Feistel network on k = ceil(log2 n) bits
-// (left half floor(k/2) bits) with round function lowbias32(v ^ K_r)
-// (C. Wellons' 32-bit integer hash), Philox round keys, and cycle-walking.
+// SDs -- an eight-round alternating Feistel network on Z_A x Z_B with round
+// function h = lowbias32(v ^ K_r) (C. Wellons' 32-bit integer hash) of the
+// other half v, added as floor(h M / 2^32) modulo the half's size M.  For
+// n = 2^k the halves have floor(k/2) and k - floor(k/2) bits (A B = n);
+// otherwise A = ceil(sqrt n), B = ceil(n / A).  Philox round keys;
+// cycle-walking into [0, n), rare because A B < n + A.
 // The shuffled list is L'[q] = L[P(q)]: the SDs of pair m are found directly,
 // with no sort and no data movement.
 // ---------------------------------------------------------------------------
@@ -87,7 +90,10 @@ __device__ __forceinline__ uint32_t lowbias32_tail(uint32_t x)
 
 struct Prp {
     uint32_t K[PRP_ROUNDS];       // folded round keys Kx = K ^ (K >> 16)
-    uint32_t n, b, mask_a, mask_b;
+    uint32_t n;                   // list length (walk bound)
+    uint32_t A, B, Binv;          // domain Z_A x Z_B, Binv = ceil(2^32 / B)
+    uint32_t pow2;                // A = 2^a and B = 2^b: the same rounds by shifts and masks
+    uint32_t b, sa, sb;           //   x = L 2^b + R; floor(h A / 2^32) = h >> sa, h B likewise
 };
 
 __device__ __forceinline__ uint32_t prp_bits(uint32_t n)
@@ -96,14 +102,67 @@ __device__ __forceinline__ uint32_t prp_bits(uint32_t n)
 }
 
 // domain [0, n): halves of floor(k/2) and k - floor(k/2) bits, k = ceil(log2 n)
+// Domain of the network for a list of n elements (x = L B + R, L < A, R < B):
+// n = 2^k: A = 2^floor(k/2), B = 2^(k - floor(k/2)); otherwise A = ceil(sqrt n),
+// B = ceil(n / A), so that n <= A B < n + A and cycle-walking is rare.
+__device__ __forceinline__ void prp_domain_of(uint32_t n, uint32_t& A, uint32_t& B)
+{
+    if (n != 0 && (n & (n - 1)) == 0) {
+        const uint32_t k = prp_bits(n), a = k >> 1;
+        A = 1u << a;
+        B = 1u << (k - a);
+    } else {
+        uint32_t r = (uint32_t)ceilf(sqrtf((float)n));
+        while ((uint64_t)r * r < n) ++r;
+        while (r > 1 && (uint64_t)(r - 1) * (r - 1) >= n) --r;
+        A = r;
+        B = (n + r - 1) / r;
+    }
+}
+
 __device__ __forceinline__ void prp_set_domain(Prp& P, uint32_t n)
 {
-    const uint32_t k = prp_bits(n);
-    const uint32_t a = k >> 1;
     P.n = n;
-    P.b = k - a;
-    P.mask_a = a ? (uint32_t)((1ull << a) - 1) : 0u;
-    P.mask_b = (uint32_t)((1ull << P.b) - 1);
+    prp_domain_of(n, P.A, P.B);
+    P.Binv = P.B > 1 ? (uint32_t)((0x100000000ull + P.B - 1) / P.B) : 0u;   // B = 1 only for n = 1
+    P.pow2 = (n != 0 && (n & (n - 1)) == 0) ? 1u : 0u;
+    const uint32_t a = 31u - __clz(P.A);
+    P.b = 31u - __clz(P.B);
+    P.sa = a ? 32u - a : 31u;     // A = 1: the mask A - 1 = 0 clears the shifted hash
+    P.sb = P.b ? 32u - P.b : 31u;
+}
+
+// whether the network for n elements is the one P holds (only the walk bound differs)
+__device__ __forceinline__ bool prp_same_network(const Prp& P, uint32_t n)
+{
+    uint32_t A, B;
+    prp_domain_of(n, A, B);
+    return A == P.A && B == P.B;
+}
+
+// x / B and x mod B for x < A B
+__device__ __forceinline__ void prp_split(const Prp& P, uint32_t x, uint32_t& L, uint32_t& R)
+{
+    uint32_t q = __umulhi(x, P.Binv);            // floor(x / B) or one more
+    if (q * P.B > x) --q;
+    L = q;
+    R = x - q * P.B;
+}
+
+// one round pair of the network: L = (L + floor(h A / 2^32)) mod A, then R likewise mod B
+__device__ __forceinline__ void prp_round_pair(const Prp& P, uint32_t kl, uint32_t kr, uint32_t& L, uint32_t& R)
+{
+    const uint32_t tl = L + __umulhi(lowbias32_tail(R ^ kl), P.A);
+    L = tl >= P.A ? tl - P.A : tl;
+    const uint32_t tr = R + __umulhi(lowbias32_tail(L ^ kr), P.B);
+    R = tr >= P.B ? tr - P.B : tr;
+}
+
+// the same round pair when A and B are powers of two
+__device__ __forceinline__ void prp_round_pair_pow2(const Prp& P, uint32_t kl, uint32_t kr, uint32_t& L, uint32_t& R)
+{
+    L = (L + (lowbias32_tail(R ^ kl) >> P.sa)) & (P.A - 1u);
+    R = (R + (lowbias32_tail(L ^ kr) >> P.sb)) & (P.B - 1u);
 }
 
 __device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
@@ -119,13 +178,11 @@ __device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed
 
 __device__ __forceinline__ uint32_t feistel(const Prp& P, uint32_t q)
 {
-    uint32_t L = q >> P.b, R = q & P.mask_b;
+    uint32_t L, R;
+    prp_split(P, q, L, R);
 #pragma unroll
-    for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
-        L ^= lowbias32_tail(R ^ P.K[r]) & P.mask_a;
-        R ^= lowbias32_tail(L ^ P.K[r + 1]) & P.mask_b;
-    }
-    return (L << P.b) | R;
+    for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) prp_round_pair(P, P.K[r], P.K[r + 1], L, R);
+    return L * P.B + R;
 }
 
 // P(q) for q < n (cycle-walking terminates: q's cycle contains q itself)
