@@ -769,7 +769,8 @@ __device__ __forceinline__ void feistel_n(const Prp& P, uint32_t (&x)[N])
         k0 = k2; k1 = k3; k2 = k4; k3 = k5; k4 = k6; k5 = k7;
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) x[i] = FULL ? ((L[i] << P.b) | R[i]) : L[i] * P.B + R[i];
+    for (int i = 0; i < N; ++i)
+        x[i] = FULL ? (((L[i] & (P.A - 1u)) << P.b) | (R[i] & (P.B - 1u))) : L[i] * P.B + R[i];
 }
 
 // Cycle-walking of a warp's images by a work list instead of per-lane loops.

@@ -88,6 +88,16 @@ __device__ __forceinline__ uint32_t lowbias32_tail(uint32_t x)
     return x;
 }
 
+// lowbias32_tail without its last step x ^= x >> 16, which leaves the top 16
+// bits unchanged: enough wherever only the top 16 bits or fewer are used.
+__device__ __forceinline__ uint32_t lowbias32_top16(uint32_t x)
+{
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    return x;
+}
+
 struct Prp {
     uint32_t K[PRP_ROUNDS];       // folded round keys Kx = K ^ (K >> 16)
     uint32_t n;                   // list length (walk bound)
@@ -101,7 +111,6 @@ __device__ __forceinline__ uint32_t prp_bits(uint32_t n)
     return n <= 1 ? 0u : 32u - (uint32_t)__clz(n - 1u);   // ceil(log2 n)
 }
 
-// domain [0, n): halves of floor(k/2) and k - floor(k/2) bits, k = ceil(log2 n)
 // Domain of the network for a list of n elements (x = L B + R, L < A, R < B):
 // n = 2^k: A = 2^floor(k/2), B = 2^(k - floor(k/2)); otherwise A = ceil(sqrt n),
 // B = ceil(n / A), so that n <= A B < n + A and cycle-walking is rare.
@@ -158,11 +167,14 @@ __device__ __forceinline__ void prp_round_pair(const Prp& P, uint32_t kl, uint32
     R = tr >= P.B ? tr - P.B : tr;
 }
 
-// the same round pair when A and B are powers of two
+// The same round pair when A = 2^a and B = 2^b (a, b <= 16): floor(h A / 2^32) is
+// the top a bits of h, which the hash's last step does not change, and the
+// reduction mod A is deferred -- L and R carry values congruent to the halves
+// (below 2^19 after the four additions of a pass) and are masked where read.
 __device__ __forceinline__ void prp_round_pair_pow2(const Prp& P, uint32_t kl, uint32_t kr, uint32_t& L, uint32_t& R)
 {
-    L = (L + (lowbias32_tail(R ^ kl) >> P.sa)) & (P.A - 1u);
-    R = (R + (lowbias32_tail(L ^ kr) >> P.sb)) & (P.B - 1u);
+    L += lowbias32_top16((R & (P.B - 1u)) ^ kl) >> P.sa;
+    R += lowbias32_top16((L & (P.A - 1u)) ^ kr) >> P.sb;
 }
 
 __device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
