@@ -215,6 +215,18 @@ sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live);
 sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, uint32_t cell,
                         double* out, int out_on_device);
 
+/* Consistency check of the state's invariants (a diagnostic; Step 0 of
+ * Fig. "fig:algo" relies on the first, the early exit on the second):
+ *   *n_bad_live = slots that break the live-prefix rule: within every cell the
+ *                 slots [0, n_live) hold xi > 0 and the rest xi = 0;
+ *   *n_bad_key  = slots of the large cells whose stored volume key (the top 14
+ *                 bits of the volume's high word, kept beside the volumes so
+ *                 that the large-cell step gathers 2 bytes per SD) differs
+ *                 from the volume's.
+ * Both are 0 for any state the library produced.  SDM_EINVAL for a NULL
+ * pointer or an uninitialised state.  Synchronises. */
+sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_key);
+
 /* Totals over live SDs: *n_total = sum xi (exact), *mass = sum xi v (FP64,
  * summation order unspecified), *n_live.  Any pointer may be NULL.
  * Synchronises. */
@@ -260,13 +272,16 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n);
  * order); p32[i], err32[i] the FP32 value and its error bound,
  * |p64 - p32| <= err32; plite[i], errlite[i] (nullable; gravitational kernel)
  * the second filter's FP64 value from refined FP32 seeds and its bound,
- * |p64 - plite| <= errlite (errlite < 0: not applicable to this pair).  All
- * arrays are device pointers.  Exposes Step 2 alone for testing (dependency
- * injection, Sec. 5). */
+ * |p64 - plite| <= errlite (errlite < 0: not applicable to this pair); pup[i]
+ * (nullable) the early exit's upper bound of p from the table of the two
+ * volumes' bins and the power of two above max(xi1, xi2), >= p64 and >= p32
+ * (+inf for volumes beyond the table).  All arrays are device pointers.
+ * Exposes Step 2 alone for testing (dependency injection, Sec. 5). */
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2,
                           const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd,
                           double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32, double* plite, double* errlite);
+                          double* p64, float* p32, float* err32, double* plite, double* errlite,
+                          float* pup);
 
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the gravitational kernel (no counterpart in the paper).

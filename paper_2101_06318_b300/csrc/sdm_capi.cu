@@ -64,6 +64,7 @@ struct sdm_state {
     // state arrays
     uint64_t* d_xi = nullptr;
     double* d_attr = nullptr;
+    uint16_t* d_vkey = nullptr;              // [cap] early-exit key of each slot's volume
     uint32_t* d_cell_start = nullptr;
     double* d_dv = nullptr;
     uint8_t* d_kid = nullptr;
@@ -91,7 +92,7 @@ struct sdm_state {
     uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
     uint32_t n_quads = 0, prp_grid = 0;      // PRP contract: quads of all large cells, grid size
     uint32_t* d_cta_first = nullptr;         // [prp_grid] first large cell of each CTA (many large cells)
-    float* d_big_xpow = nullptr;             // [n_big] power of two above every multiplicity of the cell
+    unsigned long long* d_big_xmax = nullptr;   // [n_big] largest multiplicity of the cell
     BigLaunch prp_launch{};
     FinishLayout fin_L{};
     uint32_t fin_grid = 0, n_buckets_planned = 0;
@@ -163,7 +164,7 @@ void free_layout(sdm_state* st)
     if (st->ws) st->ws_used = st->ws_fixed;
     st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
-    st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xpow = nullptr;
+    st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
 }
 
@@ -199,38 +200,48 @@ sdm_status check_schedule(const sdm_schedule& s)
 // double: [0][b] the bin's upper volume edge, [1][b] pi (2 r)^2 vt(r) Emax (1 + 2^-10)
 // at the bin's upper radius r, Emax the largest efficiency of the table rows that
 // radii in the bin interpolate between; both rounded up to float.
-void fill_pbound_host(float (*t)[PB_NB + 1])
+void fill_pbound_host(float (*t)[PB_SIZE])
 {
     constexpr double E_h[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
-    double rowmax[EFF_NR];
-    for (int i = 0; i < EFF_NR; ++i) {
-        rowmax[i] = 0.0;
-        for (int j = 0; j < EFF_NQ; ++j) rowmax[i] = std::max(rowmax[i], E_h[i * EFF_NQ + j]);
-    }
-    auto row_of = [](double r) {   // interpolation interval index of radius r, as in the kernels
+    auto v_lo = [](uint32_t b) {                 // bin 0 also holds every smaller volume
+        return b == 0 ? 0.0 : std::ldexp(1.0 + (double)(b % 4) / 4.0, PB_EMIN + (int)(b / 4));
+    };
+    auto v_hi = [](uint32_t b) { return std::ldexp(1.0 + (double)(b % 4 + 1) / 4.0, PB_EMIN + (int)(b / 4)); };
+    auto radius = [](double v, double f) { return v > 0.0 ? std::cbrt(v * THREE_OVER_FOUR_PI) * f : 0.0; };
+    auto vt = [](double r) {
+        return r < VT_R12 ? VT_K1 * r * r : (r < VT_R23 ? VT_K2 * r : VT_K3 * std::sqrt(r));
+    };
+    auto row_of = [](double R) {   // interpolation interval of R, clamped as in the kernels
         int i = 0;
-        while (i < EFF_NR - 2 && c_eff_R_h[i + 1] <= r) ++i;
+        while (i < EFF_NR - 2 && c_eff_R_h[i + 1] <= R) ++i;
         return i;
     };
+    auto col_of = [](double q) { return std::min(EFF_NQ - 2, std::max(0, (int)std::floor(q * 10.0))); };
     auto up = [](double x) {
         float f = (float)x;
         if ((double)f < x) f = std::nextafter(f, INFINITY);
         return f;
     };
-    for (uint32_t b = 0; b < PB_NB; ++b) {
-        const int e = PB_EMIN + (int)(b / 4);
-        const double m = (double)(b % 4);
-        const double v_lo = std::ldexp(1.0 + m / 4.0, e), v_hi = std::ldexp(1.0 + (m + 1.0) / 4.0, e);
-        t[0][b] = up(v_hi);
-        const double r_lo = std::cbrt(v_lo * THREE_OVER_FOUR_PI) * (1.0 - 1e-12);
-        const double r_hi = std::cbrt(v_hi * THREE_OVER_FOUR_PI) * (1.0 + 1e-12);
-        const int i0 = row_of(r_lo), i1 = std::min(EFF_NR - 1, row_of(r_hi) + 1);
-        double emax = 0.0;
-        for (int i = i0; i <= i1; ++i) emax = std::max(emax, rowmax[i]);
-        const double vt = r_hi < VT_R12 ? VT_K1 * r_hi * r_hi : (r_hi < VT_R23 ? VT_K2 * r_hi : VT_K3 * std::sqrt(r_hi));
-        t[1][b] = up(PI_D * (4.0 * r_hi * r_hi) * vt * emax * (1.0 + 0x1p-10));
+    for (uint32_t b1 = 0; b1 < PB_NB; ++b1) {
+        const double R_lo = radius(v_lo(b1), 1.0 - 1e-12), R_hi = radius(v_hi(b1), 1.0 + 1e-12);
+        for (uint32_t d = 0; d <= PB_ND; ++d) {
+            // the smaller volume's range; distances beyond b1 cannot occur (filled as bin 0)
+            const uint32_t b2 = d < PB_ND ? (d <= b1 ? b1 - d : 0u) : (b1 >= PB_ND ? b1 - PB_ND : 0u);
+            const double s_lo = d < PB_ND ? v_lo(b2) : 0.0, s_hi = v_hi(b2);
+            t[0][b1 * PB_ROW + d] = up(v_hi(b1) + s_hi);
+            const double r_lo = radius(s_lo, 1.0 - 1e-12), r_hi = std::min(radius(s_hi, 1.0 + 1e-12), R_hi);
+            const double q_lo = r_lo / R_hi, q_hi = R_lo > 0.0 ? std::min(1.0, r_hi / R_lo) : 1.0;
+            const int i0 = row_of(R_lo), i1 = std::min(EFF_NR - 1, row_of(R_hi) + 1);
+            const int j0 = col_of(q_lo), j1 = std::min(EFF_NQ - 1, col_of(q_hi) + 1);
+            double emax = 0.0;
+            for (int i = i0; i <= i1; ++i)
+                for (int j = j0; j <= j1; ++j) emax = std::max(emax, E_h[i * EFF_NQ + j]);
+            const double dvt = std::max(0.0, vt(R_hi) - vt(r_lo)) + 0x1p-12 * (vt(R_hi) + vt(r_hi));
+            const double sr = R_hi + r_hi;
+            t[1][b1 * PB_ROW + d] = up(PI_D * sr * sr * dvt * emax * (1.0 + 0x1p-10));
+        }
     }
-    t[0][PB_NB] = t[1][PB_NB] = INFINITY;   // beyond the table: no bound
+    for (uint32_t d = 0; d <= PB_ND; ++d) t[0][PB_NB * PB_ROW + d] = t[1][PB_NB * PB_ROW + d] = INFINITY;
 }
 
 // Upload the device tables once per device (first use).
@@ -243,7 +254,7 @@ sdm_status ensure_device_tables()
     if (dev < 0 || dev >= 64) return SDM_ENOTSUP;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return SDM_OK;
-    static float t[2][PB_NB + 1];
+    static float t[2][PB_SIZE];
     fill_pbound_host(t);
     SDM_CUDA(cudaMemcpyToSymbol(g_pbound, t, sizeof t));
     done[dev] = true;
@@ -266,8 +277,9 @@ uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
 sdm_status refresh_big_bounds(sdm_state* st)
 {
     if (!st->n_big) return SDM_OK;
-    SDM_CUDA(cudaMemsetAsync(st->d_big_xpow, 0, sizeof(float) * st->n_big, st->stream));
-    big_xpow_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_big, st->d_chunks, (uint32_t*)st->d_big_xpow);
+    SDM_CUDA(cudaMemsetAsync(st->d_big_xmax, 0, sizeof(unsigned long long) * st->n_big, st->stream));
+    big_xmax_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_vkey, st->d_big, st->d_chunks,
+                                                          st->d_big_xmax);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }
@@ -366,8 +378,9 @@ sdm_status build_layout(sdm_state* st)
     }
     st->n_tiles = (uint32_t)tiles.size();
     st->n_big = (uint32_t)bigs.size();
-    if (!bigs.empty()) SDM_TRY(dev_alloc(st, (void**)&st->d_big_xpow, sizeof(float) * bigs.size(), true));
-    st->prp_launch = BigLaunch{st->n_big, n_quads, st->d_big, st->d_big_xpow, st->d_cta_first, {}};
+    if (!bigs.empty())
+        SDM_TRY(dev_alloc(st, (void**)&st->d_big_xmax, sizeof(unsigned long long) * bigs.size(), true));
+    st->prp_launch = BigLaunch{st->n_big, n_quads, st->d_big, st->d_big_xmax, st->d_cta_first, {}};
     for (uint32_t b = 0; b < st->n_big && b < BIG_PARAM_CELLS; ++b) st->prp_launch.pc[b] = bigs[b];
     st->n_chunks = (uint32_t)chunks.size();
     st->n_buckets = (uint32_t)bucket_big.size();
@@ -506,6 +519,32 @@ __global__ void validate_kernel(const uint64_t* __restrict__ xi, const double* _
     if (bad) atomicOr(err, bad);
 }
 
+// state checks (sdm_check_state): slots breaking the live-prefix rule of their cell
+__global__ void check_live_kernel(const uint64_t* __restrict__ xi, uint64_t n, const uint32_t* __restrict__ cs,
+                                  uint32_t n_cell, const uint32_t* __restrict__ n_live, unsigned long long* bad)
+{
+    unsigned long long b = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cell_of(cs, n_cell, i);
+        const bool expect_live = i - cs[c] < n_live[c];
+        b += (xi[i] != 0) != expect_live;
+    }
+    if (b) atomicAdd(bad, b);
+}
+
+// state checks: slots of the large cells whose stored volume key is stale
+__global__ void check_keys_kernel(const double* __restrict__ vol, const uint16_t* __restrict__ vkey,
+                                  const BigCell* __restrict__ cells, const BigChunk* __restrict__ chunks,
+                                  unsigned long long* bad)
+{
+    const BigChunk K = chunks[blockIdx.x];
+    const BigCell C = cells[K.big];
+    unsigned long long b = 0;
+    for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x)
+        b += vkey[C.slot_begin + i] != (uint16_t)vkey_of(vol[C.slot_begin + i]);
+    if (b) atomicAdd(bad, b);
+}
+
 // live count of every cell: the length of the live prefix of its slots
 __global__ void live_count_kernel(const uint64_t* __restrict__ xi, const uint32_t* __restrict__ cs, uint32_t n_cell,
                                   uint32_t* n_live)
@@ -583,6 +622,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     StepArgs a{};
     a.xi = st->d_xi;
     a.attr = st->d_attr;
+    a.vkey = st->d_vkey;
     a.stride = st->cap;
     a.n_attr = st->n_attr;
     a.precision = p->precision;
@@ -666,7 +706,7 @@ const char* sdm_status_str(sdm_status s)
 size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
 {
     size_t b = 0;
-    b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256);
+    b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256) + round256(2 * cap + 256);
     b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
     b += 4 * round256(512) + round256(4 * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 260);
@@ -705,6 +745,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
     if (s == SDM_OK) s = ensure_device_tables();
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_xi, sizeof(uint64_t) * cap, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_attr, sizeof(double) * cap * n_attr, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_vkey, sizeof(uint16_t) * cap, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_cell_start, sizeof(uint32_t) * ((size_t)n_cell + 1), false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_dv, sizeof(double) * n_cell, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_kid, n_cell, false);
@@ -875,6 +916,29 @@ sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live)
     SDM_CUDA(cudaMemcpyAsync(&h, st->d_acc, sizeof h, cudaMemcpyDeviceToHost, st->stream));
     SDM_CUDA(cudaStreamSynchronize(st->stream));
     *n_live = h;
+    return SDM_OK;
+}
+
+sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_key)
+{
+    if (!st || !st->initialised || !n_bad_live || !n_bad_key) return SDM_EINVAL;
+    SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, 2 * sizeof(unsigned long long), st->stream));
+    if (st->n_sd) {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
+        check_live_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->n_sd, st->d_cell_start, st->n_cell,
+                                                        st->d_n_live, st->d_acc);
+        SDM_CUDA(cudaGetLastError());
+    }
+    if (st->n_big) {
+        check_keys_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_attr, st->d_vkey, st->d_big, st->d_chunks,
+                                                                st->d_acc + 1);
+        SDM_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[2] = {0, 0};
+    SDM_CUDA(cudaMemcpyAsync(h, st->d_acc, sizeof h, cudaMemcpyDeviceToHost, st->stream));
+    SDM_CUDA(cudaStreamSynchronize(st->stream));
+    *n_bad_live = h[0];
+    *n_bad_key = h[1];
     return SDM_OK;
 }
 
@@ -1081,7 +1145,7 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2, const uint64_t* xi1,
                           const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32, double* plite, double* errlite)
+                          double* p64, float* p32, float* err32, double* plite, double* errlite, float* pup)
 {
     if (!st || !v1 || !v2 || !xi1 || !xi2 || !p64 || !p32 || !err32) return SDM_EINVAL;
     if (kernel_id > SDM_KERNEL_GRAVITATIONAL || n_cell_sd < 2 || !(dv > 0) || !(dt > 0)) return SDM_EINVAL;
@@ -1089,7 +1153,7 @@ sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, c
     const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 8 * (uint64_t)st->n_sm);
     if ((plite == nullptr) != (errlite == nullptr)) return SDM_EINVAL;
     eval_pairs_kernel<<<grid, 256, 0, st->stream>>>(kernel_id, v1, v2, xi1, xi2, n, n_cell_sd, dv, dt, golovin_b, p64,
-                                                    p32, err32, plite, errlite);
+                                                    p32, err32, plite, errlite, pup);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }
@@ -1111,7 +1175,7 @@ constexpr size_t NA_OFF_DV = 64;         // double dv
 constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
 constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
 constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, removal flag, end-of-step ticket
-constexpr size_t NA_OFF_XPOW = 192;      // float multiplicity bound of the box
+constexpr size_t NA_OFF_XMAX = 192;      // uint64 largest multiplicity of the box
 constexpr size_t NA_OFF_CHUNKS = 256;
 constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
 constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
@@ -1196,11 +1260,11 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
     uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
-    float* d_xpow = (float*)(base + NA_OFF_XPOW);
+    unsigned long long* d_xmax = (unsigned long long*)(base + NA_OFF_XMAX);
     if (p->shuffle == SDM_SHUFFLE_PRP) {
-        SDM_CUDA(cudaMemsetAsync(d_xpow, 0, sizeof(float), stream));
-        big_xpow_kernel<<<n_chunks, 256, 0, stream>>>(xi, (const BigCell*)(base + NA_OFF_CELL),
-                                                      (const BigChunk*)(base + NA_OFF_CHUNKS), (uint32_t*)d_xpow);
+        SDM_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned long long), stream));
+        big_xmax_kernel<<<n_chunks, 256, 0, stream>>>(xi, attr, nullptr, (const BigCell*)(base + NA_OFF_CELL),
+                                                      (const BigChunk*)(base + NA_OFF_CHUNKS), d_xmax);
     }
 
     StepArgs a{};
@@ -1230,7 +1294,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         int dev = 0, n_sm = 148;
         SDM_CUDA(cudaGetDevice(&dev));
         SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        BigLaunch L{1, n_quads, d_cell, d_xpow, nullptr, {}};
+        BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
         big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
     } else {

@@ -39,6 +39,8 @@ constexpr uint32_t DEAD = 0xffffffffu;
 struct StepArgs {
     uint64_t* xi;
     double* attr;               // [n_attr][stride], attr 0 = volume
+    uint16_t* vkey;             // [stride] vkey_of(volume) of every slot of the large cells, kept
+                                // current by every writer of the volumes; nullptr: not kept
     uint64_t stride;
     uint32_t n_attr;
     uint32_t precision;
@@ -92,7 +94,7 @@ struct CellCtx {
 __device__ __forceinline__ float exit_scale(float s32, uint32_t kid, float golovin_bf, uint32_t precision)
 {
     const float f = precision == PREC_SURROGATE ? 2.0f : 1.0f;
-    return __fmul_ru(__fmul_ru(s32, kid == 0 ? __fmul_ru(2.0f, golovin_bf) : f), 1.0f + 0x1p-8f);
+    return __fmul_ru(__fmul_ru(s32, kid == 0 ? golovin_bf : f), 1.0f + 0x1p-8f);
 }
 
 __device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, float dt_f, double dv)
@@ -141,7 +143,9 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
     const uint64_t new_n = xj - g * xk;
     if (new_n > 0) {                                          // case 1, eq. (coal_attr_0)
         a.xi[gj] = new_n;
-        a.attr[gk] = __dadd_rn(__dmul_rn(gd, vj), vk);
+        const double nv = __dadd_rn(__dmul_rn(gd, vj), vk);
+        a.attr[gk] = nv;
+        if (a.vkey) a.vkey[gk] = (uint16_t)vkey_of(nv);
         for (uint32_t i = 1; i < a.n_attr; ++i) {
             double* A = a.attr + (uint64_t)i * a.stride;
             A[gk] = __dadd_rn(__dmul_rn(gd, A[gj]), A[gk]);
@@ -153,6 +157,11 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
         const double nv = __dadd_rn(__dmul_rn(gd, vj), vk);
         a.attr[gj] = nv;
         a.attr[gk] = nv;
+        if (a.vkey) {
+            const uint16_t k = (uint16_t)vkey_of(nv);
+            a.vkey[gj] = k;
+            a.vkey[gk] = k;
+        }
         for (uint32_t i = 1; i < a.n_attr; ++i) {
             double* A = a.attr + (uint64_t)i * a.stride;
             const double t = __dadd_rn(__dmul_rn(gd, A[gj]), A[gk]);
@@ -349,7 +358,10 @@ __device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t
                 double* A = a.attr + (uint64_t)r * a.stride + base;
                 const double v = in ? A[i] : 0.0;
                 __syncwarp();
-                if (live) A[pos] = v;
+                if (live) {
+                    A[pos] = v;
+                    if (r == 0 && a.vkey) a.vkey[base + pos] = (uint16_t)vkey_of(v);
+                }
             } else {
                 __syncwarp();
                 if (live) a.xi[base + pos] = x;
@@ -361,6 +373,7 @@ __device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t
     for (uint32_t i = dst + lane; i < n_old; i += 32) {
         a.xi[base + i] = 0ull;
         for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
+        if (a.vkey) a.vkey[base + i] = 0;
     }
     __syncwarp();
     return dst;
@@ -523,8 +536,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             if (has) {
                 i1 = srt[ss[c] + 2 * m];
                 i2 = srt[ss[c] + 2 * m + 1];
-                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_bin((uint32_t)__double2hiint(v_s[i1]),
-                                                                       (uint32_t)__double2hiint(v_s[i2]))),
+                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(vkey_of(v_s[i1]), vkey_of(v_s[i2]))),
                                                       cup[c]),
                                             xi_pow2_above(xi_s[i1], xi_s[i2]));
                 need = !(pup <= phi_lo23(whi));
@@ -648,7 +660,10 @@ __device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_
                 double* A = a.attr + (uint64_t)r * a.stride + base;
                 const double v = in ? A[i] : 0.0;
                 __syncthreads();
-                if (live) A[pos] = v;
+                if (live) {
+                    A[pos] = v;
+                    if (r == 0 && a.vkey) a.vkey[base + pos] = (uint16_t)vkey_of(v);
+                }
             } else {
                 __syncthreads();
                 if (live) a.xi[base + pos] = x;
@@ -660,6 +675,7 @@ __device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_
     for (uint32_t i = dst + tid; i < n_old; i += nt) {
         a.xi[base + i] = 0ull;
         for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
+        if (a.vkey) a.vkey[base + i] = 0;
     }
     __syncthreads();
     return dst;
@@ -730,7 +746,7 @@ constexpr uint32_t PQ_CAP = 2 * 32 * PRP_QPT;   // queued pairs per warp (2 per 
 struct BigLaunch {
     uint32_t n_big, n_quads;
     const BigCell* cells;                      // [n_big] (device)
-    const float* xpow;                         // [n_big] power of two above every multiplicity of the cell
+    const unsigned long long* xmax;            // [n_big] largest multiplicity of the cell (since the upload)
     const uint32_t* cta_first;                 // [grid] first large cell of each CTA (n_big > BIG_PARAM_CELLS)
     BigCell pc[BIG_PARAM_CELLS];               // the large cells when n_big <= BIG_PARAM_CELLS
 };
@@ -868,16 +884,17 @@ __device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __r
     qcnt -= take;
 }
 
-// Settle pair (s1, s2) by the early exit or queue it (warp-collective).  c_upx is
-// the cell's early-exit scale times its multiplicity bound.
+// Settle pair (s1, s2) by the early exit or queue it (warp-collective).  k1, k2 are
+// the volumes' keys (vkey_of); c_upx is the cell's early-exit scale times its
+// multiplicity bound.
 __device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, uint32_t& qcnt, bool has, uint32_t s1,
-                                              uint32_t s2, uint32_t vh1, uint32_t vh2, uint32_t w_hi, uint32_t w_lo,
+                                              uint32_t s2, uint32_t k1, uint32_t k2, uint32_t w_hi, uint32_t w_lo,
                                               const float* __restrict__ tb, float c_upx, LocalStats& ls,
                                               uint32_t lane)
 {
     bool need = false;
     if (has) {
-        need = !(__fmul_ru(__ldg(tb + pb_bin(vh1, vh2)), c_upx) <= phi_lo23(w_hi));
+        need = !(__fmul_ru(__ldg(tb + pb_index(k1, k2)), c_upx) <= phi_lo23(w_hi));
         ls.pairs += need ? 0u : 1u;
     }
     const unsigned m = __ballot_sync(0xffffffffu, need);
@@ -926,11 +943,13 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
             use |= (h1[j] ? 12u : 0u) << (4 * j);
         }
         // Two halves: the second half's bijection images are computed while the first
-        // half's gathers are in flight.  Only the volumes' high words are gathered: with
-        // the cell's multiplicity bound they are all the early exit needs.
+        // half's gathers are in flight.  Only the volumes' keys are gathered (2 bytes per
+        // SD from the key array, else the volume's high word): with the cell's
+        // multiplicity bound they are all the early exit needs.
         constexpr int NH = NP / 2;
         uint32_t vh[NP];
         const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
+        const uint16_t* __restrict__ vkey = a.vkey;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             uint32_t eh[NH];
@@ -942,7 +961,9 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
 #pragma unroll
             for (int i = 0; i < NH; ++i) {
                 e[NH * hh + i] = eh[i] + C.slot_begin;   // slots from here on
-                vh[NH * hh + i] = ((use >> (NH * hh + i)) & 1u) ? attr_hi[2 * (size_t)e[NH * hh + i]] : 0u;
+                const uint32_t ei = e[NH * hh + i];
+                vh[NH * hh + i] = !((use >> (NH * hh + i)) & 1u) ? 0u
+                                  : vkey ? (uint32_t)vkey[ei] : attr_hi[2 * (size_t)ei] >> 18;
             }
         }
         // phi while the gathers are in flight, then the early exit
@@ -990,14 +1011,16 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
     LocalStats ls = {0, 0, 0, 0, 0ull};
     if (tid < 5) red[tid] = 0;
     // the bound table (read right after the gathers) and the efficiency table (read by the
-    // queued evaluations) are cold after other work evicted L2: start fetching them now
-    if (warp == 0) {
+    // queued evaluations) are cold after other work evicted L2: start fetching them now --
+    // the bound table into L2, a slice per CTA, the efficiency table into every SM's L1
+    {
         constexpr uint32_t PB_LINES = (uint32_t)((sizeof(g_pbound) + 127) / 128);
+        for (uint32_t l = blockIdx.x * nt + tid; l < PB_LINES; l += gridDim.x * nt)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(g_pbound) + 128 * l));
         constexpr uint32_t EFF_LINES = (uint32_t)((sizeof(EffTab) + 127) / 128);
-        if (lane < PB_LINES)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(g_pbound) + 128 * lane));
-        else if (lane < PB_LINES + EFF_LINES)
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(tab) + 128 * (lane - PB_LINES)));
+        static_assert(EFF_LINES <= 32, "one line per lane");
+        if (warp == 0 && lane < EFF_LINES)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(tab) + 128 * lane));
     }
     PairQueue& Q = pq[warp];
     uint32_t qcnt = 0;                              // queued pairs of this warp (warp-uniform)
@@ -1012,7 +1035,7 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         const uint32_t n = min(a.n_live[C.cell], C.width);
         const uint32_t kid = (uint32_t)a.kid[C.cell];
         const double dv = a.dv[C.cell];
-        const float xpow = L.xpow[c];
+        const float xup = __ull2float_ru(L.xmax[c]);
         Prp P;
         prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, C.width);
         const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
@@ -1021,7 +1044,7 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         if (n >= PRP_MIN_N) {
             const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
             const CellCtx cc{C.cell, n, kid, s32, dv};
-            const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xpow);
+            const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xup);
             if (P.pow2 && n == C.width) {
                 prp_cell_quads<SURR, true>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp, lane,
                                            nt);
@@ -1396,26 +1419,30 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
 // ---------------------------------------------------------------------------
 // small utility kernels
 // ---------------------------------------------------------------------------
-// Per large cell: a power of two above the OR (so above the maximum) of the
-// multiplicities in its slots.  Coalescence never raises a multiplicity, so the
-// value bounds every later step until the state is replaced.  One CTA per
-// chunk of a large cell; xpow_bits (float bits, zeroed before) takes the
-// maximum over the chunks (positive floats order as their bit patterns).
-__global__ void big_xpow_kernel(const uint64_t* __restrict__ xi, const BigCell* __restrict__ cells,
-                                const BigChunk* __restrict__ chunks, uint32_t* xpow_bits)
+// Per large cell: the largest multiplicity in its slots.  Coalescence never
+// raises a multiplicity, so the value bounds every later step until the state
+// is replaced.  One CTA per chunk of a large cell; xmax (zeroed before) takes
+// the maximum over the chunks.  With vkey, also (re)writes the volume key of
+// every slot of the large cells.
+__global__ void big_xmax_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ vol,
+                                uint16_t* __restrict__ vkey, const BigCell* __restrict__ cells,
+                                const BigChunk* __restrict__ chunks, unsigned long long* xmax)
 {
-    __shared__ unsigned long long s_or[32];
+    __shared__ unsigned long long s_max[32];
     const BigChunk K = chunks[blockIdx.x];
     const BigCell C = cells[K.big];
     unsigned long long m = 0;
-    for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x) m |= xi[C.slot_begin + i];
+    for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x) {
+        m = max(m, (unsigned long long)xi[C.slot_begin + i]);
+        if (vkey) vkey[C.slot_begin + i] = (uint16_t)vkey_of(vol[C.slot_begin + i]);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-    if ((threadIdx.x & 31) == 0) s_or[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (uint32_t w = 1; w < (blockDim.x + 31) / 32; ++w) m |= s_or[w];
-        if (m) atomicMax(&xpow_bits[K.big], (127u + 64u - (uint32_t)__clzll((long long)m)) << 23);
+        for (uint32_t w = 1; w < (blockDim.x + 31) / 32; ++w) m = max(m, s_max[w]);
+        if (m) atomicMax(&xmax[K.big], m);
     }
 }
 
@@ -1469,7 +1496,7 @@ __global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* _
 __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* v2, const uint64_t* xi1,
                                   const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt,
                                   double golovin_b, double* p64, float* p32, float* err32, double* plite,
-                                  double* errlite)
+                                  double* errlite, float* pup)
 {
     __shared__ EffTab tab;
     load_eff_tab(&tab);
@@ -1482,6 +1509,11 @@ __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* 
         const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b);
         p32[i] = pe.p;
         err32[i] = pe.err;
+        if (pup) {
+            const float cup = exit_scale(pair_ratio_dtdv_f(n_cell_sd, (float)dt, dv), kid, (float)golovin_b, PREC_FP64);
+            pup[i] = __fmul_ru(__fmul_ru(__ldg(&g_pbound[kid ? 1 : 0][pb_index(vkey_of(v1[i]), vkey_of(v2[i]))]), cup),
+                               xi_pow2_above(xi1[i], xi2[i]));
+        }
         if (plite) {
             double pl = 0.0, el = -1.0;
             if (kid == 1) pair_prob_lite(v1[i], v2[i], xmax, n_cell_sd, dt, dv, pl, el);

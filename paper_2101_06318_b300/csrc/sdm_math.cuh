@@ -772,35 +772,58 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
 }
 
 // ---------------------------------------------------------------------------
-// Early exit of Step 3: an upper bound of p from the larger volume and the
-// larger multiplicity of a pair.  When phi >= bound >= p (and so p < 1),
+// Early exit of Step 3: an upper bound of p from the bins of the pair's two
+// volumes and its larger multiplicity.  When phi >= bound >= p (and so p < 1),
 // gamma = floor(p) + [phi < p] = 0 and the pair needs no kernel evaluation.
 // The bound holds for the FP64 value and for the FP32 value alike.
-//   bins of the larger volume v: its double exponent e and two leading
-//   mantissa bits m, bin = 4 (e - PB_EMIN) + m covering
-//   [2^e (1 + m/4), 2^e (1 + (m+1)/4)); volumes below the first bin share
-//   its bound (both kernels grow with v), volumes above the last have none.
-//   table[kind][bin]:  Golovin: the bin's upper edge (K = b (v1 + v2) <= 2 b v);
-//   gravitational: pi (2 r)^2 vt(r) max E over the table rows the bin's radii
-//   touch, r the bin's upper radius (r1 + r2 <= 2 r, |vt1 - vt2| <= vt(r)),
+//   bin of a volume v: its double exponent e and two leading mantissa bits m,
+//   bin = 4 (e - PB_EMIN) + m covering [2^e (1 + m/4), 2^e (1 + (m+1)/4));
+//   volumes below the first bin join it (its lower edge is 0), volumes above
+//   the last have no bound.
+//   table[kind][b1][d]: b1 the larger volume's bin, d = b1 - b2 the distance to
+//   the smaller one's, the last column (d = PB_ND) for every b2 <= b1 - PB_ND
+//   (smaller volume anywhere in [0, upper edge of bin b1 - PB_ND)):
+//     Golovin: the sum of the two upper edges (K = b (v1 + v2));
+//     gravitational: pi (R+ + r+)^2 (vt(R+) - vt(r-) + 2^-12 (vt(R+) + vt(r+)))
+//     Emax, with R+- and r+- the radii at the bins' edges (vt grows with the
+//     radius, so |vt1 - vt2| <= vt(R+) - vt(r-); the 2^-12 term covers the
+//     FP32 path's error, which is relative to vt1 + vt2) and Emax the largest
+//     efficiency node of the table rows and columns the interpolation can
+//     reach for R in [R-, R+], q = r/R in [r-/R+, min(1, r+/R-)];
 //   times 1 + 2^-10, rounded up to float.  Filled by the host once per device.
-//   p <= table * c_up * X with c_up = S dt/dV (* 2b for Golovin) * (1 + 2^-8)
-//   rounded up and X a power of two above max(xi1, xi2) -- per pair
-//   2^(64 - clz(xi1 | xi2)), or per cell 2^(64 - clz(OR of its multiplicities)),
-//   which stays valid for every later step because coalescence never raises a
-//   multiplicity; the margins cover the FP32 scale's roundings and the FP32
-//   path's own error.
+//   p <= table * c_up * X with c_up = S dt/dV (* b for Golovin) * (1 + 2^-8)
+//   rounded up and X >= max(xi1, xi2) -- per pair the power of two
+//   2^(64 - clz(xi1 | xi2)), or per cell its largest multiplicity rounded up
+//   to float, which stays valid for every later step because coalescence
+//   never raises a multiplicity; the margins cover the FP32 scale's roundings
+//   and the FP32 path's own error.
 // ---------------------------------------------------------------------------
 constexpr int PB_EMIN = -80;
 constexpr uint32_t PB_NB = 4 * 72;                               // exponents -80 .. -9
 constexpr uint32_t PB_HI0 = (uint32_t)(1023 + PB_EMIN) << 2;      // (high word >> 18) of bin 0
-__device__ float g_pbound[2][PB_NB + 1];                          // [kind][PB_NB] = +inf
+constexpr uint32_t PB_ND = 32;                                    // bin distances 0 .. PB_ND - 1, then the rest
+constexpr uint32_t PB_ROW = PB_ND + 1;
+constexpr uint32_t PB_SIZE = (PB_NB + 1) * PB_ROW;                // row PB_NB: +inf
+__device__ float g_pbound[2][PB_SIZE];
 
-// bin of the larger of two non-negative volumes from their high words (PB_NB: no bound)
-__device__ __forceinline__ uint32_t pb_bin(uint32_t hi1, uint32_t hi2)
+// Early-exit key of a volume: the top 14 bits of its high word (sign, exponent, two
+// mantissa bits).  Non-negative doubles order as their keys.
+__device__ __forceinline__ uint32_t vkey_of(double v)
 {
-    const uint32_t h = max(hi1, hi2) >> 18;      // non-negative doubles order as their high words
-    return h < PB_HI0 ? 0u : min(h - PB_HI0, PB_NB);
+    return (uint32_t)__double2hiint(v) >> 18;
+}
+
+// bin of a non-negative volume from its key (PB_NB: beyond the table)
+__device__ __forceinline__ uint32_t pb_bin_key(uint32_t k)
+{
+    return k < PB_HI0 ? 0u : min(k - PB_HI0, PB_NB);
+}
+
+// entry of the bound table for two volumes' keys
+__device__ __forceinline__ uint32_t pb_index(uint32_t k1, uint32_t k2)
+{
+    const uint32_t b1 = pb_bin_key(max(k1, k2)), b2 = pb_bin_key(min(k1, k2));
+    return b1 * PB_ROW + min(b1 - b2, PB_ND);
 }
 
 // 2^(64 - clz(x1 | x2)) > max(x1, x2) as a float (x1 | x2 != 0, both < 2^53)

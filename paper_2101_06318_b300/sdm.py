@@ -30,7 +30,7 @@ STATUS = {0: "SDM_OK", 1: "SDM_EINVAL", 2: "SDM_ENOMEM", 3: "SDM_ECAPACITY", 4: 
 # every entry point declared in include/sdm.h
 EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", "sdm_init_state",
            "sdm_init_state_segmented", "sdm_set_state", "sdm_get_state", "sdm_coalescence_step",
-           "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_get_schedule", "sdm_set_schedule",
+           "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_check_state", "sdm_get_schedule", "sdm_set_schedule",
            "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
            "sdm_launches_per_step", "sdm_coalescence_step_noalloc", "sdm_surrogate_create", "sdm_surrogate_free",
            "sdm_surrogate_train", "sdm_surrogate_build_mask", "sdm_surrogate_params_io", "sdm_surrogate_info",
@@ -98,13 +98,14 @@ def lib(build_if_needed: bool = True):
         L.sdm_remove_zero.argtypes = [vp, vp]
         L.sdm_spectrum.argtypes = [vp, vp, u32, u32, vp, i32]
         L.sdm_totals.argtypes = [vp, vp, vp, vp]
+        L.sdm_check_state.argtypes = [vp, vp, vp]
         L.sdm_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.sdm_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.sdm_autotune.argtypes = [vp, C.POINTER(StepParams), u32, C.POINTER(Schedule)]
         L.sdm_sync.argtypes = [vp]
         L.sdm_free.argtypes = [vp]
         L.sdm_free.restype = None
-        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp, vp, vp]
+        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp, vp, vp, vp]
         L.sdm_set_profiling.argtypes = [vp, i32]
         L.sdm_get_profile.argtypes = [vp, vp, vp]
         L.sdm_launches_per_step.argtypes = [vp, u32, vp]
@@ -262,6 +263,12 @@ class State:
         _check(self._L.sdm_totals(self._h, C.byref(n), C.byref(m), C.byref(live)), "sdm_totals")
         return int(n.value), float(m.value), int(live.value)
 
+    def check(self):
+        """Counts of slots breaking the state's invariants: (live-prefix rule, stale volume keys)."""
+        bl, bk = C.c_uint64(), C.c_uint64()
+        _check(self._L.sdm_check_state(self._h, C.byref(bl), C.byref(bk)), "sdm_check_state")
+        return int(bl.value), int(bk.value)
+
     def attach_surrogate(self, surrogate):
         """Use a trained Surrogate for precision="surrogate" steps (None detaches); the State keeps a
         reference so the surrogate outlives its use."""
@@ -308,9 +315,10 @@ class State:
         return int(n.value)
 
     # -- Step 2 alone (testing) ---------------------------------------------------
-    def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0, lite=False):
-        """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors, and with lite=True
-        also the second filter's (plite, errlite)."""
+    def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0, lite=False,
+                   bound=False):
+        """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors, with lite=True
+        also the second filter's (plite, errlite), with bound=True also the early exit's bound."""
         torch = _torch()
         n = v1.numel()
         p64 = torch.empty(n, dtype=torch.float64, device=v1.device)
@@ -318,13 +326,16 @@ class State:
         e32 = torch.empty(n, dtype=torch.float32, device=v1.device)
         pl = torch.empty(n, dtype=torch.float64, device=v1.device) if lite else None
         el = torch.empty(n, dtype=torch.float64, device=v1.device) if lite else None
+        pu = torch.empty(n, dtype=torch.float32, device=v1.device) if bound else None
         _check(self._L.sdm_eval_pairs(self._h, int(kernel_id), C.c_void_p(v1.data_ptr()), C.c_void_p(v2.data_ptr()),
                                       C.c_void_p(xi1.data_ptr()), C.c_void_p(xi2.data_ptr()), n, int(n_cell_sd),
                                       float(dv), float(dt), float(golovin_b), C.c_void_p(p64.data_ptr()),
                                       C.c_void_p(p32.data_ptr()), C.c_void_p(e32.data_ptr()),
                                       C.c_void_p(pl.data_ptr() if lite else None),
-                                      C.c_void_p(el.data_ptr() if lite else None)), "sdm_eval_pairs")
-        return (p64, p32, e32, pl, el) if lite else (p64, p32, e32)
+                                      C.c_void_p(el.data_ptr() if lite else None),
+                                      C.c_void_p(pu.data_ptr() if bound else None)), "sdm_eval_pairs")
+        out = (p64, p32, e32) + ((pl, el) if lite else ()) + ((pu,) if bound else ())
+        return out
 
 
 class Surrogate:

@@ -47,6 +47,9 @@ def _run_both(s, n_steps, seed=42, step0=0, attr=None, schedule=None, precision=
                  shuffle=shuffle)
     g.sync()
     xi, at, cs = g.get_state()
+    # invariants the steps keep: live prefixes, and the volume keys the large-cell step gathers
+    # (written by every collision and compaction under either contract)
+    assert g.check() == (0, 0)
     g.close()
     return o, ost, xi, at, gst
 
@@ -239,6 +242,44 @@ def test_fp32_bound_holds_and_fp64_matches_oracle():
         assert np.all(np.abs(p64[ok] - pl[ok]) <= el[ok])
         worst_lite = max(worst_lite, float((np.abs(p64[ok] - pl[ok]) / el[ok]).max()))
     assert worst_lite < 0.01, worst_lite
+
+
+def test_early_exit_bound_holds():
+    """The early exit's bound of p (table of the two volumes' bins) is above the FP64 value and the
+    FP32 value of every pair: wide random pairs, near-equal pairs, volumes on and just below the
+    bins' edges, radii at the fall-speed regime joins and at efficiency table nodes."""
+    rng = np.random.default_rng(12)
+    n = 300000
+    r1 = np.exp(rng.uniform(np.log(0.01e-6), np.log(3e-3), n))
+    r2 = np.exp(rng.uniform(np.log(0.01e-6), np.log(3e-3), n))
+    near = rng.random(n) < 0.2
+    r2[near] = r1[near] * (1 + rng.normal(0, 1e-3, near.sum()))
+    joins = np.array([8e3 / 1.19e8, (201 / 8e3) ** 2, 10e-6, 20e-6, 30e-6, 60e-6, 100e-6, 150e-6, 300e-6, 1e-3])
+    r1[:10000] = np.repeat(joins, 1000) * (1 + rng.normal(0, 1e-7, 10000))
+    v1 = 4 / 3 * np.pi * r1 ** 3
+    v2 = 4 / 3 * np.pi * r2 ** 3
+    # volumes on a bin edge 2^e (1 + m/4) and one ulp below it
+    e = rng.integers(-75, -10, 20000)
+    m = rng.integers(0, 4, 20000)
+    edge = np.ldexp(1.0 + m / 4.0, e)
+    v1[10000:30000] = np.where(rng.random(20000) < 0.5, edge, np.nextafter(edge, 0.0))
+    v2[30000:50000] = np.where(rng.random(20000) < 0.5, edge, np.nextafter(edge, 0.0))
+    xi1 = rng.integers(1, 10 ** 9, n).astype(np.uint64)
+    xi2 = rng.integers(1, 10 ** 9, n).astype(np.uint64)
+    g = sdm.State(16, 1)
+    dev = lambda a: torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
+    for kid, ncell, dv in ((1, 1 << 20, 1e6), (0, 8192, 1e6), (1, 300, 1e3)):
+        p64, p32, _, pup = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv, bound=True)
+        p64, p32, pup = p64.cpu().numpy(), p32.cpu().numpy().astype(np.float64), pup.cpu().numpy().astype(np.float64)
+        assert np.all(pup >= p64), (kid, np.flatnonzero(pup < p64)[:5])
+        assert np.all(pup >= p32), (kid, np.flatnonzero(pup < p32)[:5])
+        # not vacuous: within a small factor of p (the multiplicity's power of two alone gives up to 2)
+        # for pairs of volumes within a few bins of each other; very unequal or nearly equal radii
+        # (fall speeds far apart or nearly the same) leave more room, but there p is small anyway
+        q = np.minimum(v1, v2) / np.maximum(v1, v2)
+        sel = (p64 > 0) & (q > 0.03) & (q < 0.7) if kid else p64 > 0
+        ratio = np.median(pup[sel] / p64[sel])
+        assert ratio < 4.0, (kid, ratio)
 
 
 def test_fp32_mode_close_to_fp64():
