@@ -219,10 +219,10 @@ sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, u
  * Fig. "fig:algo" relies on the first, the early exit on the second):
  *   *n_bad_live = slots that break the live-prefix rule: within every cell the
  *                 slots [0, n_live) hold xi > 0 and the rest xi = 0;
- *   *n_bad_key  = slots of the large cells whose stored volume key (the top 14
- *                 bits of the volume's high word, kept beside the volumes so
- *                 that the large-cell step gathers 2 bytes per SD) differs
- *                 from the volume's.
+ *   *n_bad_key  = slots of the large cells whose stored volume bin (the
+ *                 early exit's quarter-octave bin of the volume, kept beside
+ *                 the volumes so that the large-cell step gathers 1 byte per
+ *                 SD) differs from the volume's.
  * Both are 0 for any state the library produced.  SDM_EINVAL for a NULL
  * pointer or an uninitialised state.  Synchronises. */
 sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_key);

@@ -64,7 +64,7 @@ struct sdm_state {
     // state arrays
     uint64_t* d_xi = nullptr;
     double* d_attr = nullptr;
-    uint16_t* d_vkey = nullptr;              // [cap] early-exit key of each slot's volume
+    uint8_t* d_vbin = nullptr;               // [cap] early-exit bin of each slot's volume
     uint32_t* d_cell_start = nullptr;
     double* d_dv = nullptr;
     uint8_t* d_kid = nullptr;
@@ -278,7 +278,7 @@ sdm_status refresh_big_bounds(sdm_state* st)
 {
     if (!st->n_big) return SDM_OK;
     SDM_CUDA(cudaMemsetAsync(st->d_big_xmax, 0, sizeof(unsigned long long) * st->n_big, st->stream));
-    big_xmax_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_vkey, st->d_big, st->d_chunks,
+    big_xmax_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_vbin, st->d_big, st->d_chunks,
                                                           st->d_big_xmax);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
@@ -532,8 +532,8 @@ __global__ void check_live_kernel(const uint64_t* __restrict__ xi, uint64_t n, c
     if (b) atomicAdd(bad, b);
 }
 
-// state checks: slots of the large cells whose stored volume key is stale
-__global__ void check_keys_kernel(const double* __restrict__ vol, const uint16_t* __restrict__ vkey,
+// state checks: slots of the large cells whose stored volume bin is stale
+__global__ void check_keys_kernel(const double* __restrict__ vol, const uint8_t* __restrict__ vbin,
                                   const BigCell* __restrict__ cells, const BigChunk* __restrict__ chunks,
                                   unsigned long long* bad)
 {
@@ -541,7 +541,7 @@ __global__ void check_keys_kernel(const double* __restrict__ vol, const uint16_t
     const BigCell C = cells[K.big];
     unsigned long long b = 0;
     for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x)
-        b += vkey[C.slot_begin + i] != (uint16_t)vkey_of(vol[C.slot_begin + i]);
+        b += vbin[C.slot_begin + i] != (uint8_t)vbin_of(vol[C.slot_begin + i]);
     if (b) atomicAdd(bad, b);
 }
 
@@ -622,7 +622,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     StepArgs a{};
     a.xi = st->d_xi;
     a.attr = st->d_attr;
-    a.vkey = st->d_vkey;
+    a.vbin = st->d_vbin;
     a.stride = st->cap;
     a.n_attr = st->n_attr;
     a.precision = p->precision;
@@ -706,7 +706,7 @@ const char* sdm_status_str(sdm_status s)
 size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
 {
     size_t b = 0;
-    b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256) + round256(2 * cap + 256);
+    b += round256(8 * cap + 256) + round256(8 * cap * n_attr + 256) + round256(cap + 256);
     b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
     b += 4 * round256(512) + round256(4 * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 260);
@@ -745,7 +745,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
     if (s == SDM_OK) s = ensure_device_tables();
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_xi, sizeof(uint64_t) * cap, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_attr, sizeof(double) * cap * n_attr, false);
-    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_vkey, sizeof(uint16_t) * cap, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_vbin, sizeof(uint8_t) * cap, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_cell_start, sizeof(uint32_t) * ((size_t)n_cell + 1), false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_dv, sizeof(double) * n_cell, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_kid, n_cell, false);
@@ -930,7 +930,7 @@ sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_
         SDM_CUDA(cudaGetLastError());
     }
     if (st->n_big) {
-        check_keys_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_attr, st->d_vkey, st->d_big, st->d_chunks,
+        check_keys_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_attr, st->d_vbin, st->d_big, st->d_chunks,
                                                                 st->d_acc + 1);
         SDM_CUDA(cudaGetLastError());
     }

@@ -39,7 +39,7 @@ constexpr uint32_t DEAD = 0xffffffffu;
 struct StepArgs {
     uint64_t* xi;
     double* attr;               // [n_attr][stride], attr 0 = volume
-    uint16_t* vkey;             // [stride] vkey_of(volume) of every slot of the large cells, kept
+    uint8_t* vbin;              // [stride] vbin_of(volume) of every slot of the large cells, kept
                                 // current by every writer of the volumes; nullptr: not kept
     uint64_t stride;
     uint32_t n_attr;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
         a.xi[gj] = new_n;
         const double nv = __dadd_rn(__dmul_rn(gd, vj), vk);
         a.attr[gk] = nv;
-        if (a.vkey) a.vkey[gk] = (uint16_t)vkey_of(nv);
+        if (a.vbin) a.vbin[gk] = (uint8_t)vbin_of(nv);
         for (uint32_t i = 1; i < a.n_attr; ++i) {
             double* A = a.attr + (uint64_t)i * a.stride;
             A[gk] = __dadd_rn(__dmul_rn(gd, A[gj]), A[gk]);
@@ -157,10 +157,10 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
         const double nv = __dadd_rn(__dmul_rn(gd, vj), vk);
         a.attr[gj] = nv;
         a.attr[gk] = nv;
-        if (a.vkey) {
-            const uint16_t k = (uint16_t)vkey_of(nv);
-            a.vkey[gj] = k;
-            a.vkey[gk] = k;
+        if (a.vbin) {
+            const uint8_t k = (uint8_t)vbin_of(nv);
+            a.vbin[gj] = k;
+            a.vbin[gk] = k;
         }
         for (uint32_t i = 1; i < a.n_attr; ++i) {
             double* A = a.attr + (uint64_t)i * a.stride;
@@ -360,7 +360,7 @@ __device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t
                 __syncwarp();
                 if (live) {
                     A[pos] = v;
-                    if (r == 0 && a.vkey) a.vkey[base + pos] = (uint16_t)vkey_of(v);
+                    if (r == 0 && a.vbin) a.vbin[base + pos] = (uint8_t)vbin_of(v);
                 }
             } else {
                 __syncwarp();
@@ -373,7 +373,7 @@ __device__ uint32_t warp_compact_cell(const StepArgs& a, uint64_t base, uint32_t
     for (uint32_t i = dst + lane; i < n_old; i += 32) {
         a.xi[base + i] = 0ull;
         for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
-        if (a.vkey) a.vkey[base + i] = 0;
+        if (a.vbin) a.vbin[base + i] = 0;
     }
     __syncwarp();
     return dst;
@@ -536,7 +536,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             if (has) {
                 i1 = srt[ss[c] + 2 * m];
                 i2 = srt[ss[c] + 2 * m + 1];
-                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(vkey_of(v_s[i1]), vkey_of(v_s[i2]))),
+                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(vbin_of(v_s[i1]), vbin_of(v_s[i2]))),
                                                       cup[c]),
                                             xi_pow2_above(xi_s[i1], xi_s[i2]));
                 need = !(pup <= phi_lo23(whi));
@@ -662,7 +662,7 @@ __device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_
                 __syncthreads();
                 if (live) {
                     A[pos] = v;
-                    if (r == 0 && a.vkey) a.vkey[base + pos] = (uint16_t)vkey_of(v);
+                    if (r == 0 && a.vbin) a.vbin[base + pos] = (uint8_t)vbin_of(v);
                 }
             } else {
                 __syncthreads();
@@ -675,7 +675,7 @@ __device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_
     for (uint32_t i = dst + tid; i < n_old; i += nt) {
         a.xi[base + i] = 0ull;
         for (uint32_t r = 0; r < a.n_attr; ++r) a.attr[(uint64_t)r * a.stride + base + i] = 0.0;
-        if (a.vkey) a.vkey[base + i] = 0;
+        if (a.vbin) a.vbin[base + i] = 0;
     }
     __syncthreads();
     return dst;
@@ -885,7 +885,7 @@ __device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __r
 }
 
 // Settle pair (s1, s2) by the early exit or queue it (warp-collective).  k1, k2 are
-// the volumes' keys (vkey_of); c_upx is the cell's early-exit scale times its
+// the volumes' bins (vbin_of); c_upx is the cell's early-exit scale times its
 // multiplicity bound.
 __device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, uint32_t& qcnt, bool has, uint32_t s1,
                                               uint32_t s2, uint32_t k1, uint32_t k2, uint32_t w_hi, uint32_t w_lo,
@@ -943,13 +943,13 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
             use |= (h1[j] ? 12u : 0u) << (4 * j);
         }
         // Two halves: the second half's bijection images are computed while the first
-        // half's gathers are in flight.  Only the volumes' keys are gathered (2 bytes per
-        // SD from the key array, else the volume's high word): with the cell's
+        // half's gathers are in flight.  Only the volumes' bins are gathered (1 byte per
+        // SD from the bin array, else the volume's high word): with the cell's
         // multiplicity bound they are all the early exit needs.
         constexpr int NH = NP / 2;
         uint32_t vh[NP];
         const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
-        const uint16_t* __restrict__ vkey = a.vkey;
+        const uint8_t* __restrict__ vbin = a.vbin;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             uint32_t eh[NH];
@@ -963,7 +963,7 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
                 e[NH * hh + i] = eh[i] + C.slot_begin;   // slots from here on
                 const uint32_t ei = e[NH * hh + i];
                 vh[NH * hh + i] = !((use >> (NH * hh + i)) & 1u) ? 0u
-                                  : vkey ? (uint32_t)vkey[ei] : attr_hi[2 * (size_t)ei] >> 18;
+                                  : vbin ? (uint32_t)vbin[ei] : pb_bin_key(attr_hi[2 * (size_t)ei] >> 18);
             }
         }
         // phi while the gathers are in flight, then the early exit
@@ -1422,10 +1422,10 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
 // Per large cell: the largest multiplicity in its slots.  Coalescence never
 // raises a multiplicity, so the value bounds every later step until the state
 // is replaced.  One CTA per chunk of a large cell; xmax (zeroed before) takes
-// the maximum over the chunks.  With vkey, also (re)writes the volume key of
+// the maximum over the chunks.  With vbin, also (re)writes the volume bin of
 // every slot of the large cells.
 __global__ void big_xmax_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ vol,
-                                uint16_t* __restrict__ vkey, const BigCell* __restrict__ cells,
+                                uint8_t* __restrict__ vbin, const BigCell* __restrict__ cells,
                                 const BigChunk* __restrict__ chunks, unsigned long long* xmax)
 {
     __shared__ unsigned long long s_max[32];
@@ -1434,7 +1434,7 @@ __global__ void big_xmax_kernel(const uint64_t* __restrict__ xi, const double* _
     unsigned long long m = 0;
     for (uint32_t i = K.l_begin + threadIdx.x; i < K.l_end; i += blockDim.x) {
         m = max(m, (unsigned long long)xi[C.slot_begin + i]);
-        if (vkey) vkey[C.slot_begin + i] = (uint16_t)vkey_of(vol[C.slot_begin + i]);
+        if (vbin) vbin[C.slot_begin + i] = (uint8_t)vbin_of(vol[C.slot_begin + i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -1511,7 +1511,7 @@ __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* 
         err32[i] = pe.err;
         if (pup) {
             const float cup = exit_scale(pair_ratio_dtdv_f(n_cell_sd, (float)dt, dv), kid, (float)golovin_b, PREC_FP64);
-            pup[i] = __fmul_ru(__fmul_ru(__ldg(&g_pbound[kid ? 1 : 0][pb_index(vkey_of(v1[i]), vkey_of(v2[i]))]), cup),
+            pup[i] = __fmul_ru(__fmul_ru(__ldg(&g_pbound[kid ? 1 : 0][pb_index(vbin_of(v1[i]), vbin_of(v2[i]))]), cup),
                                xi_pow2_above(xi1[i], xi2[i]));
         }
         if (plite) {

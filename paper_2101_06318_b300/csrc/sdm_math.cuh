@@ -799,7 +799,7 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
 //   and the FP32 path's own error.
 // ---------------------------------------------------------------------------
 constexpr int PB_EMIN = -80;
-constexpr uint32_t PB_NB = 4 * 72;                               // exponents -80 .. -9
+constexpr uint32_t PB_NB = 255;                                  // exponents -80 .. -17 (a bin fits a byte)
 constexpr uint32_t PB_HI0 = (uint32_t)(1023 + PB_EMIN) << 2;      // (high word >> 18) of bin 0
 constexpr uint32_t PB_ND = 32;                                    // bin distances 0 .. PB_ND - 1, then the rest
 constexpr uint32_t PB_ROW = PB_ND + 1;
@@ -819,11 +819,16 @@ __device__ __forceinline__ uint32_t pb_bin_key(uint32_t k)
     return k < PB_HI0 ? 0u : min(k - PB_HI0, PB_NB);
 }
 
-// entry of the bound table for two volumes' keys
-__device__ __forceinline__ uint32_t pb_index(uint32_t k1, uint32_t k2)
+__device__ __forceinline__ uint32_t vbin_of(double v)
 {
-    const uint32_t b1 = pb_bin_key(max(k1, k2)), b2 = pb_bin_key(min(k1, k2));
-    return b1 * PB_ROW + min(b1 - b2, PB_ND);
+    return pb_bin_key(vkey_of(v));
+}
+
+// entry of the bound table for two volumes' bins
+__device__ __forceinline__ uint32_t pb_index(uint32_t b1, uint32_t b2)
+{
+    const uint32_t hi = max(b1, b2);
+    return hi * PB_ROW + min(hi - min(b1, b2), PB_ND);
 }
 
 // 2^(64 - clz(x1 | x2)) > max(x1, x2) as a float (x1 | x2 != 0, both < 2^53)
