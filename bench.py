@@ -254,9 +254,10 @@ def run_ours(args, rank, world, local_rank):
         st.sync()
         kinds = [k for k, v in st.profile().items() if v[0]]
         st.set_profiling(False)
-        # a step of a single launch is timed by the step's own events (they bracket exactly that
-        # kernel); otherwise each kernel is bracketed by events of its own inside the timed region
-        single = st.launches_per_step() == 1 and len(kinds) == 1
+        # a step of a single kernel kind (the large-cell kernel and the compaction launched right
+        # behind it count as one) is timed by the step's own events, which bracket exactly those
+        # launches; otherwise each kind is bracketed by events of its own inside the timed region
+        single = len(kinds) == 1
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if not single:
             st.set_profiling(True)

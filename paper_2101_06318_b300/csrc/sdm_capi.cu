@@ -284,6 +284,25 @@ sdm_status refresh_big_bounds(sdm_state* st)
     return SDM_OK;
 }
 
+// The compaction that follows a PRP step (big_compact_kernel), as a programmatic
+// dependent launch so that its start overlaps the end of the step.
+sdm_status launch_big_compact(const StepArgs& a, const BigCell* cells, uint32_t* removed, uint32_t n_big, int n_sm,
+                              cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::max<uint32_t>(1, std::min<uint32_t>(n_big, (uint32_t)std::max(n_sm, 1))));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    SDM_CUDA(cudaLaunchKernelEx(&cfg, big_compact_kernel, a, cells, removed, n_big));
+    return SDM_OK;
+}
+
 // the 64-bit ticket follows the removal flags at an 8-byte aligned word
 size_t big_ticket_word(size_t n_big) { return (n_big + 1) & ~(size_t)1; }
 
@@ -663,6 +682,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             ProfScope ps(st, 3);
             auto kern = p->precision == SDM_PREC_SURROGATE ? big_prp_kernel<true> : big_prp_kernel<false>;
             kern<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->prp_launch, bb);
+            SDM_TRY(launch_big_compact(a, st->d_big, st->d_big_removed, st->n_big, st->n_sm, st->stream));
         } else if (st->n_big) {
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
@@ -1138,8 +1158,8 @@ sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms)
 sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 {
     if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
-    // tiles: one kernel; large cells: one kernel (PRP contract) or scatter + finish (SORT contract)
-    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);
+    // tiles: one kernel; large cells: the step and its compaction (PRP contract) or scatter + finish (SORT)
+    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? 2u : 0u);   // PRP: step + compaction; SORT: scatter + finish
     return SDM_OK;
 }
 
@@ -1297,6 +1317,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
         big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
+        SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]

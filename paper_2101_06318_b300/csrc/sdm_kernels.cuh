@@ -990,9 +990,10 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
                                                                                  BigBook bk)
 {
     const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
+    // the compaction kernel that follows may start launching (it waits for this grid's end)
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ PairQueue pq[PRP_WARPS];
     static_assert(sizeof(WalkScratch) <= sizeof(PairQueue), "the walk list shares the pair queue's memory");
-    __shared__ uint32_t wt[40];
     __shared__ uint32_t key_s[PRP_MIN_N];
     __shared__ uint16_t srt_s[PRP_MIN_N];
     __shared__ unsigned long long red[8];
@@ -1080,7 +1081,33 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    big_end_of_step(a, L.cells, bk, wt, ls.removed != 0);
+    // cells that lost SDs are compacted by big_compact_kernel, launched right after
+}
+
+// Step 0 for the large cells of the PRP contract: compacts, stably, the cells
+// that lost SDs in the step just run and resets their flags.  Launched after
+// big_prp_kernel as a programmatic dependent: its blocks may be scheduled while
+// the step's last blocks finish, and griddepcontrol.wait returns once the step
+// grid has completed and its memory operations are visible.  Without such a
+// dependency (a plain launch) the wait returns at once and stream order gives
+// the same guarantee.
+__global__ void __launch_bounds__(256) big_compact_kernel(StepArgs a, const BigCell* __restrict__ cells,
+                                                          uint32_t* removed, uint32_t n_big)
+{
+    __shared__ uint32_t wt[40];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (uint32_t b = blockIdx.x; b < n_big; b += gridDim.x) {
+        const uint32_t flag = *(volatile uint32_t*)&removed[b];   // the same in every thread
+        if (!flag) continue;
+        const BigCell C = cells[b];
+        const uint32_t n_old = min(a.n_live[C.cell], C.width);
+        const uint32_t n_new = block_compact_cell(a, C.slot_begin, n_old, wt);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            a.n_live[C.cell] = n_new;
+            removed[b] = 0;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
