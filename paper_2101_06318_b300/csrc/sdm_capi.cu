@@ -311,7 +311,7 @@ sdm_status build_layout(sdm_state* st)
     free_layout(st);
     const sdm_schedule& S = st->sched;
     const std::vector<uint32_t>& cs = st->h_cell_start;
-    const uint32_t max_cells = std::min<uint32_t>(256, S.tile_slots);
+    const uint32_t max_cells = std::min<uint32_t>(128, S.tile_slots);
     std::vector<TileDesc> tiles;
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
@@ -417,8 +417,14 @@ sdm_status build_layout(sdm_state* st)
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * max_nb;
         SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
     }
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  st->tile_L.bytes));
+    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  st->tile_L.bytes));
     SDM_CUDA(cudaStreamSynchronize(st->stream));
     return SDM_OK;
 }
@@ -672,7 +678,9 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 work = st->d_work;
             }
             ProfScope ps(st, 0);
-            auto kern = p->precision == SDM_PREC_SURROGATE ? tile_step_kernel<true> : tile_step_kernel<false>;
+            const bool surr = p->precision == SDM_PREC_SURROGATE;
+            auto kern = S.tile_threads <= 256 ? (surr ? tile_step_kernel<true, 256> : tile_step_kernel<false, 256>)
+                                              : (surr ? tile_step_kernel<true, 512> : tile_step_kernel<false, 512>);
             kern<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
                                                                                     st->tile_L, work);
         }

@@ -277,7 +277,7 @@ struct TileLayout {
     uint32_t tile_slots, max_cells;
     // byte offsets
     uint32_t o_xi, o_v, o_key, o_bo, o_cnt, o_tmp, o_srt, o_cs, o_gb, o_bb, o_pb, o_ss, o_nb, o_n, o_rem, o_pp, o_ctx, o_red,
-        o_wt, o_tab, o_cup, o_q;
+        o_wt, o_tab, o_cup, o_q, o_prp;
     uint32_t bytes;
 };
 
@@ -310,7 +310,16 @@ __host__ __device__ inline TileLayout tile_layout(uint32_t tile_slots, uint32_t 
     L.o_wt = o;  o = align_up(o + 4 * 40, 16);
     L.o_tab = o; o = align_up(o + (uint32_t)sizeof(EffTab), 16);
     L.o_cup = o; o = align_up(o + 4 * (max_cells + 1), 16);
-    L.o_q = o;   o = align_up(o + (uint32_t)sizeof(TileQueue) * n_warps, 16);
+    // the bijections of the tile's cells above PRP_MIN_N SDs (at most tile_slots / PRP_MIN_N)
+    L.o_prp = o; o = align_up(o + (uint32_t)sizeof(Prp) * (tile_slots / PRP_MIN_N + 1), 16);
+    // the pair queues live in the sort scratch (keys, bucket offsets, counts, tmp), which is
+    // dead once the shuffled lists are built
+    const uint32_t qbytes = (uint32_t)sizeof(TileQueue) * n_warps;
+    if (qbytes <= L.o_srt - L.o_key) {
+        L.o_q = L.o_key;
+    } else {
+        L.o_q = o;   o = align_up(o + qbytes, 16);
+    }
     L.bytes = o;
     return L;
 }
@@ -410,6 +419,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     // per cell: slot offset, live count (the live SDs are the first n slots), and
     // what Step 1 needs: key groups and buckets for sorted cells, the list length
     // for PRP-shuffled cells
+    if (tid == 0) wt[39] = 0;       // PRP cells of the tile, counted when their bijections are set up
     for (uint32_t c = tid; c <= nc; c += nt) {
         cs[c] = a.cell_start[td.cell_begin + c] - td.slot_begin;
         if (c < nc) {
@@ -485,9 +495,17 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         srt[st + r] = (uint16_t)i;
     }
     // where each cell's shuffled list starts in srt; per-cell constants of eq. (p)
+    Prp* prp_s = (Prp*)(smem + L.o_prp);
     for (uint32_t c = tid; c < nc; c += nt) {
         const uint32_t n = ncl[c];
         ss[c] = sorts(a, n) ? cnt[bb[c]] : NB ? cnt[NB] + pp[c] : pp[c];
+        if (!sorts(a, n)) {
+            // the cell's bijection, once: its index among the tile's PRP cells replaces the
+            // bucket bit count, which only sorted cells use
+            const uint32_t k = atomicAdd(&wt[39], 1u);
+            prp_init(prp_s[k], a.seed_lo, a.seed_hi, td.cell_begin + c, step, n);
+            nbit[c] = k;
+        }
         const uint32_t gid = td.cell_begin + c;
         CellCtx cc;
         cc.gid = gid;
@@ -500,13 +518,13 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         pb[c] = (n >> 1) + 1u >> 1;              // groups of two pairs (one Philox call each)
     }
     __syncthreads();
-    // Step 1 for the larger cells under the PRP contract: L'[q] = L[P(q)]
-    for (uint32_t c = 0; c < nc; ++c) {
-        const uint32_t n = ncl[c];
-        if (sorts(a, n)) continue;
-        Prp P;
-        prp_init(P, a.seed_lo, a.seed_hi, td.cell_begin + c, step, n);
-        for (uint32_t q = tid; q < n; q += nt) srt[ss[c] + q] = (uint16_t)(cs[c] + prp_map(P, q));
+    // Step 1 for the larger cells under the PRP contract: L'[q] = L[P(q)], every position of
+    // every such cell of the tile in one pass
+    const uint32_t NPE = pp[nc];
+    for (uint32_t t = tid; t < NPE; t += nt) {
+        const uint32_t c = find_segment(pp, nc, t);
+        const uint32_t q = t - pp[c];
+        srt[ss[c] + q] = (uint16_t)(cs[c] + prp_map(prp_s[nbit[c]], q));
     }
     if (tid < 32) warp0_exclusive_scan(pb, nc);
     __syncthreads();
@@ -579,8 +597,13 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     }
 }
 
-template <bool SURR>
-__global__ void __launch_bounds__(512) tile_step_kernel(StepArgs a, const TileDesc* __restrict__ tiles,
+#ifndef SDM_TILE_MIN_BLOCKS
+#define SDM_TILE_MIN_BLOCKS 4
+#endif
+// MAXT: the largest block the instantiation takes (256: SDM_TILE_MIN_BLOCKS resident blocks of
+// 256 threads per SM, registers permitting; 512: one block)
+template <bool SURR, uint32_t MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? SDM_TILE_MIN_BLOCKS : 1) tile_step_kernel(StepArgs a, const TileDesc* __restrict__ tiles,
                                                          uint32_t n_tiles, TileLayout L, uint32_t* work)
 {
     extern __shared__ __align__(16) unsigned char smem[];
