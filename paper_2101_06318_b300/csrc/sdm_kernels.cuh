@@ -433,11 +433,31 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             gb[c] = srt_c ? (n + 3) >> 2 : 0u;
             bb[c] = (srt_c && n) ? 1u << nb : 0u;      // 2^ceil(log2 n) <= 2n buckets
             pp[c] = srt_c ? 0u : n;
+            ctx[c].kid = a.kid[td.cell_begin + c];      // loaded with the slots, used after the sort
+            ctx[c].dv = a.dv[td.cell_begin + c];
         }
     }
-    for (uint32_t i = tid; i < ns; i += nt) {
-        xi_s[i] = a.xi[td.slot_begin + i];
-        v_s[i] = a.attr[td.slot_begin + i];
+    // the tile's multiplicities and volumes: every load of a thread in flight before its stores
+    constexpr uint32_t LB = 4;
+    for (uint32_t i0 = tid; i0 < ns; i0 += LB * nt) {
+        uint64_t xr[LB];
+        double vr[LB];
+#pragma unroll
+        for (uint32_t k = 0; k < LB; ++k) {
+            const uint32_t i = i0 + k * nt;
+            if (i < ns) {
+                xr[k] = a.xi[td.slot_begin + i];
+                vr[k] = a.attr[td.slot_begin + i];
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < LB; ++k) {
+            const uint32_t i = i0 + k * nt;
+            if (i < ns) {
+                xi_s[i] = xr[k];
+                v_s[i] = vr[k];
+            }
+        }
     }
     __syncthreads();
     if (tid < 32) {
@@ -507,11 +527,9 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             nbit[c] = k;
         }
         const uint32_t gid = td.cell_begin + c;
-        CellCtx cc;
+        CellCtx cc = ctx[c];                         // kid and dv, loaded with the slots
         cc.gid = gid;
         cc.n = n;
-        cc.kid = a.kid[gid];
-        cc.dv = a.dv[gid];
         cc.s_dtdv32 = n >= 2 ? pair_ratio_dtdv_f(n, a.dt_f, cc.dv) : 0.f;
         ctx[c] = cc;
         cup[c] = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision);
