@@ -345,6 +345,31 @@ __device__ __forceinline__ void warp0_exclusive_scan(uint32_t* a, uint32_t n)
     if (lane == 0) a[n] = carry;
 }
 
+// the same for three arrays at once (independent shuffle chains, one pass)
+__device__ __forceinline__ void warp0_exclusive_scan3(uint32_t* a, uint32_t* b, uint32_t* c, uint32_t n)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    uint32_t ca = 0, cb = 0, cc = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t va = i < n ? a[i] : 0u, vb = i < n ? b[i] : 0u, vc = i < n ? c[i] : 0u;
+        uint32_t ia = va, ib = vb, ic = vc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ta = __shfl_up_sync(0xffffffffu, ia, o);
+            const uint32_t tb = __shfl_up_sync(0xffffffffu, ib, o);
+            const uint32_t tc = __shfl_up_sync(0xffffffffu, ic, o);
+            if (lane >= o) { ia += ta; ib += tb; ic += tc; }
+        }
+        if (i < n) { a[i] = ca + ia - va; b[i] = cb + ib - vb; c[i] = cc + ic - vc; }
+        ca += __shfl_sync(0xffffffffu, ia, 31);
+        cb += __shfl_sync(0xffffffffu, ib, 31);
+        cc += __shfl_sync(0xffffffffu, ic, 31);
+    }
+    if (lane == 0) { a[n] = ca; b[n] = cb; c[n] = cc; }
+}
+
 // Stable compaction of one cell by one warp: the live SDs of slots
 // [base, base + n_old) move, in order, to the front; the freed slots get xi = 0
 // and attributes 0.  Attribute rows move first (liveness is read from xi, which
@@ -419,7 +444,10 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     // per cell: slot offset, live count (the live SDs are the first n slots), and
     // what Step 1 needs: key groups and buckets for sorted cells, the list length
     // for PRP-shuffled cells
-    if (tid == 0) wt[39] = 0;       // PRP cells of the tile, counted when their bijections are set up
+    if (tid == 0) {
+        wt[39] = 0;                 // PRP cells of the tile, counted when their bijections are set up
+        wt[38] = 0;                 // their positions whose first image walks
+    }
     for (uint32_t c = tid; c <= nc; c += nt) {
         cs[c] = a.cell_start[td.cell_begin + c] - td.slot_begin;
         if (c < nc) {
@@ -460,13 +488,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         }
     }
     __syncthreads();
-    if (tid < 32) {
-        warp0_exclusive_scan(gb, nc);
-        __syncwarp();
-        warp0_exclusive_scan(bb, nc);
-        __syncwarp();
-        warp0_exclusive_scan(pp, nc);
-    }
+    if (tid < 32) warp0_exclusive_scan3(gb, bb, pp, nc);
     __syncthreads();
     const uint32_t G = gb[nc], NB = bb[nc];
     for (uint32_t b = tid; b < NB; b += nt) cnt[b] = 0;
@@ -538,11 +560,28 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
     __syncthreads();
     // Step 1 for the larger cells under the PRP contract: L'[q] = L[P(q)], every position of
     // every such cell of the tile in one pass
+    // every position of every such cell of the tile in one pass.  A first image outside [0, n)
+    // goes to a list (position | image << 13; the bucket offsets' memory is free by now) that
+    // full warps walk afterwards, instead of holding its warp for a second pass of the network
     const uint32_t NPE = pp[nc];
+    uint32_t* walk = bo_s;
     for (uint32_t t = tid; t < NPE; t += nt) {
         const uint32_t c = find_segment(pp, nc, t);
         const uint32_t q = t - pp[c];
-        srt[ss[c] + q] = (uint16_t)(cs[c] + prp_map(prp_s[nbit[c]], q));
+        const Prp& P = prp_s[nbit[c]];
+        const uint32_t e = feistel(P, q);
+        if (e < P.n) srt[ss[c] + q] = (uint16_t)(cs[c] + e);
+        else walk[atomicAdd(&wt[38], 1u)] = t | (e << 13);
+    }
+    __syncthreads();
+    const uint32_t NW = wt[38];
+    for (uint32_t k = tid; k < NW; k += nt) {
+        const uint32_t t = walk[k] & 0x1fffu;
+        uint32_t e = walk[k] >> 13;
+        const uint32_t c = find_segment(pp, nc, t);
+        const Prp& P = prp_s[nbit[c]];
+        do e = feistel(P, e); while (e >= P.n);
+        srt[ss[c] + t - pp[c]] = (uint16_t)(cs[c] + e);
     }
     if (tid < 32) warp0_exclusive_scan(pb, nc);
     __syncthreads();
