@@ -78,6 +78,8 @@ struct sdm_state {
     sdm_schedule sched{};
     TileDesc* d_tiles = nullptr;
     uint32_t n_tiles = 0, max_cells_per_tile = 0;
+    uint32_t* d_wcells = nullptr;            // cells of at most WC_MAX slots, one warp each
+    uint32_t n_wcells = 0, wc_grid = 0;
     TileLayout tile_L{};
     BigCell* d_big = nullptr;
     uint32_t n_big = 0;
@@ -166,6 +168,7 @@ void free_layout(sdm_state* st)
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
     st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
+    st->d_wcells = nullptr; st->n_wcells = st->wc_grid = 0;
 }
 
 template <typename T>
@@ -313,6 +316,7 @@ sdm_status build_layout(sdm_state* st)
     const std::vector<uint32_t>& cs = st->h_cell_start;
     const uint32_t max_cells = std::min<uint32_t>(128, S.tile_slots);
     std::vector<TileDesc> tiles;
+    std::vector<uint32_t> wcells;
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
     std::vector<uint32_t> bucket_big;
@@ -354,6 +358,11 @@ sdm_status build_layout(sdm_state* st)
             bigs.push_back(b);
             continue;
         }
+        if (w <= WC_MAX) {                   // a warp's cell (below two slots: never a pair)
+            flush();
+            if (w >= 2) wcells.push_back(c);
+            continue;
+        }
         if (cur.n_cells && (cur_slots + w > S.tile_slots || cur.n_cells == max_cells)) flush();
         if (cur.n_cells == 0) { cur.slot_begin = cs[c]; cur.cell_begin = c; }
         cur.n_cells++;
@@ -376,6 +385,14 @@ sdm_status build_layout(sdm_state* st)
     st->max_cells_per_tile = max_cells;
     if (st->tile_L.bytes > 227 * 1024) return SDM_ECAPACITY;
     SDM_TRY(upload(st, &st->d_tiles, tiles));
+    SDM_TRY(upload(st, &st->d_wcells, wcells));
+    st->n_wcells = (uint32_t)wcells.size();
+    if (st->n_wcells) {
+        int per_sm = 0;
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false>, 32 * WC_WARPS, 0));
+        const uint32_t need = (st->n_wcells + WC_WARPS - 1) / WC_WARPS;
+        st->wc_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
+    }
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
     SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
@@ -670,19 +687,26 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     const uint32_t scatter_smem = sizeof(uint32_t) * 2 * st->max_nb;
     for (uint32_t s = 0; s < n_steps; ++s) {
         a.step = p->step + s;
-        if (st->n_tiles) {
-            uint32_t grid = st->n_tiles;
-            uint32_t* work = nullptr;
-            if (S.persistent) {
-                grid = std::min<uint32_t>(st->n_tiles, S.persistent * (uint32_t)st->n_sm);
-                work = st->d_work;
-            }
+        if (st->n_wcells || st->n_tiles) {
             ProfScope ps(st, 0);
             const bool surr = p->precision == SDM_PREC_SURROGATE;
-            auto kern = S.tile_threads <= 256 ? (surr ? tile_step_kernel<true, 256> : tile_step_kernel<false, 256>)
-                                              : (surr ? tile_step_kernel<true, 512> : tile_step_kernel<false, 512>);
-            kern<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles,
-                                                                                    st->tile_L, work);
+            if (st->n_wcells) {
+                auto wk = surr ? warp_cells_kernel<true> : warp_cells_kernel<false>;
+                wk<<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
+            }
+            if (st->n_tiles) {
+                uint32_t grid = st->n_tiles;
+                uint32_t* work = nullptr;
+                if (S.persistent) {
+                    grid = std::min<uint32_t>(st->n_tiles, S.persistent * (uint32_t)st->n_sm);
+                    work = st->d_work;
+                }
+                auto kern = S.tile_threads <= 256
+                                ? (surr ? tile_step_kernel<true, 256> : tile_step_kernel<false, 256>)
+                                : (surr ? tile_step_kernel<true, 512> : tile_step_kernel<false, 512>);
+                kern<<<grid, S.tile_threads, st->tile_L.bytes, st->stream>>>(a, st->d_tiles, st->n_tiles, st->tile_L,
+                                                                            work);
+            }
         }
         const BigBook bb{(unsigned long long*)(st->d_big_removed + big_ticket_word(st->n_big)), st->d_big_removed,
                          st->n_big};
@@ -740,6 +764,7 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(4 * (size_t)n_cell + 260);
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
+    b += round256(4 * (size_t)n_cell + 256);   // cells stepped by one warp each
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
@@ -1167,7 +1192,8 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 {
     if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
     // tiles: one kernel; large cells: the step and its compaction (PRP contract) or scatter + finish (SORT)
-    *n = (st->n_tiles ? 1u : 0u) + (st->n_big ? 2u : 0u);   // PRP: step + compaction; SORT: scatter + finish
+    *n = (st->n_wcells ? 1u : 0u) + (st->n_tiles ? 1u : 0u) +
+         (st->n_big ? 2u : 0u);   // PRP: step + compaction; SORT: scatter + finish
     return SDM_OK;
 }
 

@@ -696,6 +696,244 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? SDM_TILE_MIN_BLOCKS : 1) t
 }
 
 // ---------------------------------------------------------------------------
+// Small cells, one warp per cell.  A cell of at most WC_MAX slots is stepped by
+// one warp from start to end, with no block barrier: the warp reads the cell's
+// multiplicities and volumes once (what the early exit needs of them -- the
+// volume's bin and the multiplicity's bit length -- goes to shared memory),
+// builds the shuffled list (a counting sort of the Philox keys by their top
+// bits with an exact rank inside each bucket, or the keyed bijection for a
+// cell above 256 SDs under the PRP contract), settles pairs by the early exit,
+// queues the others and evaluates them 32 at a time, and compacts the cell if
+// it lost an SD.  Many independent warps per SM hide each other's latencies.
+// ---------------------------------------------------------------------------
+constexpr uint32_t WC_MAX = 512;          // slots of a cell stepped by one warp
+constexpr uint32_t WC_WARPS = 4;          // warps per block
+constexpr uint32_t WC_QCAP = 96;          // queued pairs (< 32 left + 2 x 32 new)
+#ifndef SDM_WC_MIN_BLOCKS
+#define SDM_WC_MIN_BLOCKS 6
+#endif
+
+struct WarpCellSmem {
+    union {
+        uint32_t key[WC_MAX];             // sort keys; then the bijection's walk list
+        struct {
+            uint32_t ii[WC_QCAP];         // queued pairs: offsets i1 | i2 << 16
+            unsigned long long u[WC_QCAP];  // and their phi integers
+        } q;
+    };
+    uint32_t cnt[WC_MAX / 2 + 1];         // bucket counts, then their offsets; cnt[buckets] = n
+    uint16_t off[WC_MAX];                 // a position's place in its bucket's arrival order
+    uint16_t tmp[WC_MAX];                 // positions grouped by bucket
+    uint16_t srt[WC_MAX];                 // the shuffled list: offsets in the cell
+    uint8_t vb[WC_MAX];                   // bin of the volume (vbin_of)
+    uint8_t xe[WC_MAX];                   // bit length of the multiplicity: 2^xe > xi
+    uint32_t rem;                         // an SD of the cell was removed
+};
+
+
+// exclusive scan of a[0..n) by one warp; a[n] = total
+__device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uint32_t lane)
+{
+    const uint32_t per = (n + 31) >> 5;
+    const uint32_t b0 = min(n, lane * per), b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += a[i];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    uint32_t run = inc - s;
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t t = a[i];
+        a[i] = run;
+        run += t;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) a[n] = tot;
+    __syncwarp();
+}
+
+template <bool SURR>
+__device__ __forceinline__ void warp_cell_drain(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& cc,
+                                                WarpCellSmem& S, uint64_t s0, uint32_t& qcnt, uint32_t take,
+                                                LocalStats& ls, uint32_t lane)
+{
+    __syncwarp();
+    if (lane < take) {
+        const uint32_t k = qcnt - take + lane;
+        const uint32_t ii = S.q.ii[k];
+        const uint64_t g1 = s0 + (ii & 0xffffu), g2 = s0 + (ii >> 16);
+        process_pair<SURR>(a, T, cc, S.q.u[k], g1, g2, a.xi[g1], a.xi[g2], a.attr[g1], a.attr[g2], ls, &S.rem);
+    }
+    __syncwarp();
+    qcnt -= take;
+}
+
+template <bool SURR>
+__device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem& S, uint32_t cell,
+                               uint32_t step, LocalStats& ls, uint32_t lane)
+{
+    const uint64_t s0 = a.cell_start[cell];
+    const uint32_t w = a.cell_start[cell + 1] - (uint32_t)s0;
+    const uint32_t n = min(a.n_live[cell], w);
+    if (n < 2) return;                                       // uniform
+    const uint32_t kid = (uint32_t)a.kid[cell];
+    const double dv = a.dv[cell];
+    if (lane == 0) S.rem = 0;
+    // the early exit's data of every SD: all of a lane's loads in flight before its stores
+    for (uint32_t base = 0; base < n; base += 128) {
+        uint64_t xr[4];
+        double vr[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = base + 32 * k + lane;
+            if (i < n) {
+                xr[k] = a.xi[s0 + i];
+                vr[k] = a.attr[s0 + i];
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t i = base + 32 * k + lane;
+            if (i < n) {
+                S.vb[i] = (uint8_t)vbin_of(vr[k]);
+                S.xe[i] = (uint8_t)(64u - (uint32_t)__clzll((long long)xr[k]));
+            }
+        }
+    }
+    // Step 1: the shuffled list
+    if (sorts(a, n)) {
+        const uint32_t nb = ceil_log2(n) - 1u;                 // n >= 2: 2^nb >= n / 2 buckets
+        const uint32_t NBK = 1u << nb;
+        for (uint32_t b = lane; b < NBK; b += 32) S.cnt[b] = 0;
+        __syncwarp();
+        for (uint32_t g = lane; 4 * g < n; g += 32) {
+            const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t l = 4 * g + k;
+                if (l < n) {
+                    const uint32_t key = u4_word(x, k);
+                    const uint32_t b = nb ? key >> (32u - nb) : 0u;
+                    S.key[l] = key;
+                    S.off[l] = (uint16_t)atomicAdd(&S.cnt[b], 1u);
+                }
+            }
+        }
+        __syncwarp();
+        warp_exclusive_scan(S.cnt, NBK, lane);
+        for (uint32_t l = lane; l < n; l += 32) {
+            const uint32_t b = nb ? S.key[l] >> (32u - nb) : 0u;
+            S.tmp[S.cnt[b] + S.off[l]] = (uint16_t)l;
+        }
+        __syncwarp();
+        // exact rank inside the bucket: order by (key, list position)
+        for (uint32_t l = lane; l < n; l += 32) {
+            const uint32_t key = S.key[l];
+            const uint32_t b = nb ? key >> (32u - nb) : 0u;
+            const uint32_t st = S.cnt[b], en = S.cnt[b + 1];
+            uint32_t r = 0;
+            for (uint32_t p = st; p < en; ++p) {
+                const uint32_t o = S.tmp[p];
+                const uint32_t ko = S.key[o];
+                r += (ko < key) || (ko == key && o < l);
+            }
+            S.srt[st + r] = (uint16_t)l;
+        }
+    } else {
+        Prp P;
+        prp_init(P, a.seed_lo, a.seed_hi, cell, step, n);
+        uint32_t nwalk = 0;                                    // images outside [0, n), listed
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t q = base + lane;
+            const uint32_t e = q < n ? feistel(P, q) : 0u;
+            const bool walks = q < n && e >= n;
+            if (q < n && !walks) S.srt[q] = (uint16_t)e;
+            const unsigned m = __ballot_sync(0xffffffffu, walks);
+            if (walks) S.key[nwalk + __popc(m & ((1u << lane) - 1u))] = q | (e << 16);
+            nwalk += __popc(m);
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < nwalk; k += 32) {          // full lanes for the rare walks
+            const uint32_t q = S.key[k] & 0xffffu;
+            uint32_t e = S.key[k] >> 16;
+            do e = feistel(P, e); while (e >= n);
+            S.srt[q] = (uint16_t)e;
+        }
+    }
+    __syncwarp();
+    // Steps 2-3: two pairs per lane and Philox call, early exit, the others queued
+    const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
+    const CellCtx cc{cell, n, kid, s32, dv};
+    const float c_up = exit_scale(s32, kid, a.golovin_bf, a.precision);
+    const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
+    const uint32_t npairs = n >> 1, G2 = (npairs + 1) >> 1;
+    uint32_t qcnt = 0;
+    for (uint32_t base = 0; base < G2; base += 32) {           // warp-uniform trip count
+        const uint32_t M = base + lane;
+        const bool valid = M < G2;
+        U4 wv = {0, 0, 0, 0};
+        if (valid) wv = philox(M, cell, step, 1u, a.seed_lo, a.seed_hi);
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t m = 2 * M + h;
+            const bool has = valid && m < npairs;
+            const uint32_t whi = h ? wv.z : wv.x, wlo = h ? wv.w : wv.y;
+            bool need = false;
+            uint32_t i1 = 0, i2 = 0;
+            if (has) {
+                i1 = S.srt[2 * m];
+                i2 = S.srt[2 * m + 1];
+                const float x_up = __uint_as_float((127u + max((uint32_t)S.xe[i1], (uint32_t)S.xe[i2])) << 23);
+                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(S.vb[i1], S.vb[i2])), c_up), x_up);
+                need = !(pup <= phi_lo23(whi));
+                ls.pairs += need ? 0u : 1u;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, need);
+            if (need) {
+                const uint32_t k = qcnt + __popc(mk & ((1u << lane) - 1u));
+                S.q.ii[k] = i1 | (i2 << 16);
+                S.q.u[k] = ((((uint64_t)whi) << 32) | (uint64_t)wlo) >> 11;
+            }
+            qcnt += __popc(mk);
+        }
+        while (qcnt >= 32) warp_cell_drain<SURR>(a, T, cc, S, s0, qcnt, 32, ls, lane);
+    }
+    if (qcnt > 0) warp_cell_drain<SURR>(a, T, cc, S, s0, qcnt, qcnt, ls, lane);
+    __syncwarp();
+    // Step 0 of the next step: removals take effect in storage
+    if (*(volatile uint32_t*)&S.rem) {
+        const uint32_t n_new = warp_compact_cell(a, s0, n, lane);
+        if (lane == 0) a.n_live[cell] = n_new;
+    }
+    __syncwarp();
+}
+
+template <bool SURR>
+__global__ void __launch_bounds__(32 * WC_WARPS, SDM_WC_MIN_BLOCKS) warp_cells_kernel(StepArgs a,
+                                                                                    const uint32_t* __restrict__ cells,
+                                                                                    uint32_t n_cells)
+{
+    __shared__ WarpCellSmem ws[WC_WARPS];
+    __shared__ EffTab tab;
+    __shared__ unsigned long long red[8];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t step = step_index(a);
+    LocalStats ls = {0, 0, 0, 0, 0ull};
+    load_eff_tab(&tab);
+    if (threadIdx.x < 5) red[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t k = blockIdx.x * WC_WARPS + warp; k < n_cells; k += gridDim.x * WC_WARPS)
+        warp_cell_step<SURR>(a, &tab, ws[warp], cells[k], step, ls, lane);
+    if (a.stats) {
+        __syncthreads();
+        flush_stats(a, ls, red);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Large cells: bookkeeping shared by their kernels and the end-of-step
 // compaction done by the last CTA of the step's final large-cell kernel.
 // ---------------------------------------------------------------------------
@@ -1354,29 +1592,6 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-// exclusive scan of a[0..n) by one warp; a[n] = total
-__device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uint32_t lane)
-{
-    const uint32_t per = (n + 31) >> 5;
-    const uint32_t b0 = min(n, lane * per), b1 = min(n, b0 + per);
-    uint32_t s = 0;
-    for (uint32_t i = b0; i < b1; ++i) s += a[i];
-    uint32_t inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= (uint32_t)o) inc += t;
-    }
-    uint32_t run = inc - s;
-    for (uint32_t i = b0; i < b1; ++i) {
-        const uint32_t t = a[i];
-        a[i] = run;
-        run += t;
-    }
-    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane == 0) a[n] = tot;
-    __syncwarp();
-}
 
 __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
                                               const BigCell* __restrict__ cells,
