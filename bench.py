@@ -138,9 +138,12 @@ def _profiled_traffic(kernel, workload_name, n_sd):
         return None
 
 
-def workload(name, rank=0):
-    s = inputs.WORKLOADS[name]() if name != "gravitational_box" else inputs.gravitational_box(seed=42 + rank)
-    return s
+def workload(name, rank=0, grid_ny=None):
+    if name == "gravitational_box":
+        return inputs.gravitational_box(seed=42 + rank)
+    if grid_ny and name.startswith("grid_"):
+        return inputs.WORKLOADS[name](ny=grid_ny)       # a smaller grid (profiling captures)
+    return inputs.WORKLOADS[name]()
 
 
 def cpu_baseline(s, budget_s=12.0):
@@ -165,7 +168,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    s = workload(args.workload)
+    s = workload(args.workload, grid_ny=args.grid_ny)
     n = len(s["xi"])
     # bound the run to a few minutes: a full step of the oracle on this workload
     probe = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
@@ -220,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    s = workload(args.workload, rank)
+    s = workload(args.workload, rank, args.grid_ny)
     n = len(s["xi"])
     prec = args.precision
     surr_info = None
@@ -374,6 +377,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gravitational_box", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--grid-ny", type=int, default=None,
+                    help="rows of a grid workload (default 256); smaller grids for profiling captures")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "surrogate"])
     ap.add_argument("--schedule", default=None, help="JSON of sdm_schedule fields")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -251,7 +251,8 @@ void sdm_free(sdm_state* st);
 
 /* Kernel profiling.  While enabled, every kernel launch of the coalescence step
  * is bracketed by CUDA events on the state's stream; sdm_get_profile
- * synchronises and reports, per kernel kind (0 = small-cell tile kernel,
+ * synchronises and reports, per kernel kind (0 = small-cell kernels: one warp
+ * per cell up to 512 slots, tiles of cells above,
  * 1 = large-cell scatter, 2 = large-cell finish), the number of launches and
  * their summed device time in ms since profiling was enabled.  Arrays have
  * SDM_N_KERNEL_KINDS entries (kind 3 = large-cell kernel of the PRP contract).

@@ -297,7 +297,7 @@ class State:
         return s.as_dict()
 
     # -- profiling ----------------------------------------------------------------
-    KERNEL_KINDS = ("tile_step_kernel", "big_scatter_kernel", "big_finish_kernel", "big_prp_kernel")
+    KERNEL_KINDS = ("small_cell_kernels", "big_scatter_kernel", "big_finish_kernel", "big_prp_kernel")
 
     def set_profiling(self, on=True):
         _check(self._L.sdm_set_profiling(self._h, int(bool(on))), "sdm_set_profiling")
