@@ -168,7 +168,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    s = workload(args.workload, grid_ny=args.grid_ny)
+    s = workload(args.workload, grid_ny=getattr(args, "grid_ny", None))
     n = len(s["xi"])
     # bound the run to a few minutes: a full step of the oracle on this workload
     probe = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
@@ -223,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    s = workload(args.workload, rank, args.grid_ny)
+    s = workload(args.workload, rank, getattr(args, "grid_ny", None))
     n = len(s["xi"])
     prec = args.precision
     surr_info = None
