@@ -198,7 +198,14 @@ sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* ce
  * indices params->step .. params->step + n_steps - 1 (or read from
  * params->d_step).  stats (nullable) receives the sums over the steps; when
  * non-NULL the call synchronises to read them.  Without stats the call is
- * asynchronous and capturable in a CUDA graph (use d_step for replays). */
+ * asynchronous and capturable in a CUDA graph (use d_step for replays).
+ * Step 0 (removal of xi = 0 SDs) of a large cell under the PRP contract runs
+ * at the start of the next step: a PRP step compacts the large cells the
+ * previous one flagged (its launch is cooperative, every block resident, so
+ * that its blocks can wait for that compaction), and every call that reads or
+ * re-lays out the state (sdm_get_state, sdm_totals, sdm_spectrum,
+ * sdm_remove_zero, sdm_check_state, sdm_set_schedule, sdm_autotune, a SORT
+ * step) compacts them first, so no caller sees the difference. */
 sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
                                 sdm_step_stats* stats);
 

@@ -267,11 +267,14 @@ sdm_status ensure_device_tables()
 // Grid of the PRP kernel: one wave of resident CTAs, at most one CTA per warp's worth of quads.
 uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
 {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>, PRP_THREADS, 0) != cudaSuccess) {
+    // one wave of resident blocks of either instantiation (the launch is cooperative)
+    int per_sm = 0, per_sm_s = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>, PRP_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true>, PRP_THREADS, 0) != cudaSuccess) {
         cudaGetLastError();
-        per_sm = 1;
+        per_sm = per_sm_s = 1;
     }
+    per_sm = std::min(per_sm, per_sm_s);
     const uint32_t wave = (uint32_t)std::max(per_sm, 1) * (uint32_t)std::max(n_sm, 1);
     return std::max<uint32_t>(1, std::min<uint32_t>(wave, (n_quads + 31) / 32));
 }
@@ -289,8 +292,8 @@ sdm_status refresh_big_bounds(sdm_state* st)
 
 // The compaction that follows a PRP step (big_compact_kernel), as a programmatic
 // dependent launch so that its start overlaps the end of the step.
-sdm_status launch_big_compact(const StepArgs& a, const BigCell* cells, uint32_t* removed, uint32_t n_big, int n_sm,
-                              cudaStream_t stream)
+sdm_status launch_big_compact(const StepArgs& a, const BigCell* cells, uint32_t* removed, uint32_t n_big,
+                              uint32_t* sync, int n_sm, cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(std::max<uint32_t>(1, std::min<uint32_t>(n_big, (uint32_t)std::max(n_sm, 1))));
@@ -302,12 +305,47 @@ sdm_status launch_big_compact(const StepArgs& a, const BigCell* cells, uint32_t*
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    SDM_CUDA(cudaLaunchKernelEx(&cfg, big_compact_kernel, a, cells, removed, n_big));
+    SDM_CUDA(cudaLaunchKernelEx(&cfg, big_compact_kernel, a, cells, removed, n_big, sync));
     return SDM_OK;
 }
 
-// the 64-bit ticket follows the removal flags at an 8-byte aligned word
+// the 64-bit ticket follows the removal flags at an 8-byte aligned word, then the PRP sync words
 size_t big_ticket_word(size_t n_big) { return (n_big + 1) & ~(size_t)1; }
+
+BigBook big_book(const sdm_state* st)
+{
+    uint32_t* tw = st->d_big_removed + big_ticket_word(st->n_big);
+    return BigBook{(unsigned long long*)tw, st->d_big_removed, st->n_big, tw + 2};
+}
+
+// the state arrays a kernel that moves SDs needs
+StepArgs state_args(const sdm_state* st)
+{
+    StepArgs a{};
+    a.xi = st->d_xi;
+    a.attr = st->d_attr;
+    a.vbin = st->d_vbin;
+    a.stride = st->cap;
+    a.n_attr = st->n_attr;
+    a.cell_start = st->d_cell_start;
+    a.dv = st->d_dv;
+    a.kid = st->d_kid;
+    a.n_live = st->d_n_live;
+    a.err = st->d_err;
+    return a;
+}
+
+// Compacts the large cells a PRP step left flagged (a PRP step does it itself at its start):
+// before the state is read, re-laid out, or stepped under the SORT contract.
+sdm_status flush_big_compaction(sdm_state* st)
+{
+    if (!st->n_big || !st->d_big_removed) return SDM_OK;
+    const BigBook bb = big_book(st);
+    big_compact_kernel<<<std::max<uint32_t>(1, std::min<uint32_t>(st->n_big, (uint32_t)std::max(st->n_sm, 1))), 256,
+                         0, st->stream>>>(state_args(st), st->d_big, bb.removed, st->n_big, bb.sync);
+    SDM_CUDA(cudaGetLastError());
+    return SDM_OK;
+}
 
 sdm_status build_layout(sdm_state* st)
 {
@@ -408,7 +446,7 @@ sdm_status build_layout(sdm_state* st)
         SDM_TRY(upload(st, &st->d_cta_first, first));
     }
     if (!bigs.empty()) {
-        const size_t words = big_ticket_word(bigs.size()) + 2;
+        const size_t words = big_ticket_word(bigs.size()) + 2 + 4;   // flags, ticket, PRP sync words
         SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * words, true));
         SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * words, st->stream));
     }
@@ -708,14 +746,27 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                                                                             work);
             }
         }
-        const BigBook bb{(unsigned long long*)(st->d_big_removed + big_ticket_word(st->n_big)), st->d_big_removed,
-                         st->n_big};
+        const BigBook bb = big_book(st);
         if (st->n_big && p->shuffle == SDM_SHUFFLE_PRP) {
+            // cooperative: a step that finds cells flagged by the previous one compacts them first,
+            // behind a grid barrier (every block resident)
             ProfScope ps(st, 3);
-            auto kern = p->precision == SDM_PREC_SURROGATE ? big_prp_kernel<true> : big_prp_kernel<false>;
-            kern<<<st->prp_grid, PRP_THREADS, 0, st->stream>>>(a, st->prp_launch, bb);
-            SDM_TRY(launch_big_compact(a, st->d_big, st->d_big_removed, st->n_big, st->n_sm, st->stream));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(st->prp_grid);
+            cfg.blockDim = dim3(PRP_THREADS);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = st->stream;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;
+            at[0].val.cooperative = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (p->precision == SDM_PREC_SURROGATE)
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, big_prp_kernel<true>, a, st->prp_launch, bb));
+            else
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, big_prp_kernel<false>, a, st->prp_launch, bb));
         } else if (st->n_big) {
+            SDM_TRY(flush_big_compaction(st));      // cells left flagged by a PRP step
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
                 ProfScope ps(st, 1);
@@ -896,6 +947,9 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
                                                       st->n_cell, st->d_err);
         SDM_CUDA(cudaGetLastError());
     }
+    if (st->d_big_removed)    // the new state is compact: no large cell awaits compaction
+        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (big_ticket_word(st->n_big) + 2 + 4),
+                                 st->stream));
     const uint32_t cgrid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm));
     live_count_kernel<<<cgrid, 256, 0, st->stream>>>(st->d_xi, st->d_cell_start, st->n_cell, st->d_n_live);
     SDM_CUDA(cudaGetLastError());
@@ -905,6 +959,7 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
 sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* cell_start, uint64_t* n_sd, int on_dev)
 {
     if (!st || !st->initialised) return SDM_EINVAL;
+    SDM_TRY(flush_big_compaction(st));
     const uint64_t n = st->n_sd;
     const cudaMemcpyKind k = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (xi) SDM_CUDA(cudaMemcpyAsync(xi, st->d_xi, sizeof(uint64_t) * n, k, st->stream));
@@ -959,6 +1014,7 @@ sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live)
 {
     if (!st || !st->initialised) return SDM_EINVAL;
     if (!n_live) return SDM_OK;
+    SDM_TRY(flush_big_compaction(st));
     SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, sizeof(unsigned long long), st->stream));
     if (st->n_sd) {
         const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
@@ -975,6 +1031,7 @@ sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live)
 sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_key)
 {
     if (!st || !st->initialised || !n_bad_live || !n_bad_key) return SDM_EINVAL;
+    SDM_TRY(flush_big_compaction(st));
     SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, 2 * sizeof(unsigned long long), st->stream));
     if (st->n_sd) {
         const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
@@ -998,6 +1055,7 @@ sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_
 sdm_status sdm_totals(sdm_state* st, uint64_t* n_total, double* mass, uint64_t* n_live)
 {
     if (!st || !st->initialised) return SDM_EINVAL;
+    SDM_TRY(flush_big_compaction(st));
     SDM_CUDA(cudaMemsetAsync(st->d_acc, 0, 4 * sizeof(unsigned long long), st->stream));
     if (st->n_sd) {
         const uint32_t grid = (uint32_t)std::min<uint64_t>((st->n_sd + 255) / 256, 4 * (uint64_t)st->n_sm);
@@ -1020,6 +1078,7 @@ sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, u
     if (!st || !st->initialised || !r_edges || !out || n_bins == 0) return SDM_EINVAL;
     for (uint32_t b = 0; b < n_bins; ++b)
         if (!(r_edges[b] > 0.0) || !(r_edges[b + 1] > r_edges[b])) return SDM_EINVAL;
+    SDM_TRY(flush_big_compaction(st));
     uint32_t c0 = 0, c1 = st->n_cell;
     if (cell != UINT32_MAX) {
         if (cell >= st->n_cell) return SDM_EINVAL;
@@ -1079,6 +1138,7 @@ sdm_status sdm_set_schedule(sdm_state* st, const sdm_schedule* s)
 {
     if (!st || !s) return SDM_EINVAL;
     SDM_TRY(check_schedule(*s));
+    if (st->initialised) SDM_TRY(flush_big_compaction(st));   // the flags live in the layout
     const sdm_schedule old = st->sched;
     st->sched = *s;
     if (st->initialised) {
@@ -1097,6 +1157,7 @@ sdm_status sdm_set_schedule(sdm_state* st, const sdm_schedule* s)
 sdm_status sdm_autotune(sdm_state* st, const sdm_step_params* p, uint32_t n_steps, sdm_schedule* best)
 {
     if (!st || !p || !st->initialised || n_steps == 0) return SDM_EINVAL;
+    SDM_TRY(flush_big_compaction(st));
     const uint64_t n = st->n_sd;
     // save the state so that every trial starts from it
     uint64_t* sx = nullptr;
@@ -1191,9 +1252,10 @@ sdm_status sdm_get_profile(sdm_state* st, uint32_t* launches, double* ms)
 sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 {
     if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
-    // tiles: one kernel; large cells: the step and its compaction (PRP contract) or scatter + finish (SORT)
+    // small cells: one kernel per kind; large cells: one kernel (PRP contract; it compacts the
+    // cells the previous step left flagged) or scatter + finish (SORT contract)
     *n = (st->n_wcells ? 1u : 0u) + (st->n_tiles ? 1u : 0u) +
-         (st->n_big ? 2u : 0u);   // PRP: step + compaction; SORT: scatter + finish
+         (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);   // SORT: scatter + finish
     return SDM_OK;
 }
 
@@ -1343,7 +1405,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.stats = nullptr;
     a.err = (uint32_t*)(base + NA_OFF_ERR);
     const BigCell* d_cell = (const BigCell*)(base + NA_OFF_CELL);
-    const BigBook bb{(unsigned long long*)(live + 4), live + 3, 1};
+    const BigBook bb{(unsigned long long*)(live + 4), live + 3, 1, live + 6};
     if (p->shuffle == SDM_SHUFFLE_PRP) {
         int dev = 0, n_sm = 148;
         SDM_CUDA(cudaGetDevice(&dev));
@@ -1351,7 +1413,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
         big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
-        SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, n_sm, stream));
+        SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, live + 6, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]

@@ -938,11 +938,50 @@ __global__ void __launch_bounds__(32 * WC_WARPS, SDM_WC_MIN_BLOCKS) warp_cells_k
 // compaction done by the last CTA of the step's final large-cell kernel.
 // ---------------------------------------------------------------------------
 struct BigBook {
-    unsigned long long* ticket;   // low word: CTAs of the current kernel that finished; high word:
-                                  // how many of them removed an SD (reset by the last CTA)
+    unsigned long long* ticket;   // SORT contract: low word: CTAs of the current kernel that
+                                  // finished; high word: how many of them removed an SD
     uint32_t* removed;            // [n_big] an SD of this cell was removed during the step
     uint32_t n_big;
+    uint32_t* sync;               // PRP contract: [0] some large cell awaits compaction (its
+                                  // flag in removed[] is set); [1], [2] grid barrier count and
+                                  // generation
 };
+
+constexpr uint32_t GRID_BARRIER_SPIN_LIMIT = 1u << 22;   // ~0.4 s of polling at >= 100 ns each
+
+// Barrier of a cooperatively launched grid (every block resident).  Thread 0 of each block
+// arrives on the counter; the last arrival resets it and advances the generation the others
+// poll.  The poll gives up after GRID_BARRIER_SPIN_LIMIT rounds: the error word gets
+// ERR_TIMEOUT and false is returned (the caller then ends the kernel).
+__device__ bool grid_barrier(uint32_t* count, uint32_t* gen, uint32_t* err)
+{
+    __shared__ uint32_t ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        const uint32_t g = *(volatile uint32_t*)gen;              // read before arriving
+        __threadfence();                                          // release this block's writes
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *(volatile uint32_t*)count = 0;
+            __threadfence();
+            atomicExch(gen, g + 1u);
+        } else {
+            uint32_t it = 0;
+            while (*(volatile uint32_t*)gen == g) {
+                if (++it > GRID_BARRIER_SPIN_LIMIT) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();                                          // acquire the others' writes
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
 
 // Stable compaction of one cell by the whole block (chunks of blockDim slots;
 // see warp_compact_cell).  wt needs 33 words of shared memory.
@@ -1308,9 +1347,10 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
                                                                                  BigBook bk)
 {
     const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
-    // the compaction kernel that follows may start launching (it waits for this grid's end)
+    // a compaction kernel that follows (allocation-free step) may start launching
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ PairQueue pq[PRP_WARPS];
+    __shared__ uint32_t wt[40];
     static_assert(sizeof(WalkScratch) <= sizeof(PairQueue), "the walk list shares the pair queue's memory");
     __shared__ uint32_t key_s[PRP_MIN_N];
     __shared__ uint16_t srt_s[PRP_MIN_N];
@@ -1341,6 +1381,23 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         if (warp == 0 && lane < EFF_LINES)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(tab) + 128 * lane));
     }
+    // Step 0 for the large cells that lost SDs in the previous step: each such cell is compacted
+    // by one block while the grid waits at a barrier (the launch is cooperative).  The flag is
+    // the same word for every thread and nobody clears it before the barrier.
+    if (__ldcg(bk.sync) != 0u) {
+        for (uint32_t b = blockIdx.x; b < L.n_big; b += gridDim.x) {
+            if (!__ldcg(&bk.removed[b])) continue;
+            const BigCell C = L.cells[b];
+            const uint32_t n_old = min(__ldcg(&a.n_live[C.cell]), C.width);
+            const uint32_t n_new = block_compact_cell(a, C.slot_begin, n_old, wt);
+            if (tid == 0) {
+                a.n_live[C.cell] = n_new;
+                bk.removed[b] = 0;
+            }
+        }
+        if (!grid_barrier(bk.sync + 1, bk.sync + 2, a.err)) return;
+        if (blockIdx.x == 0 && tid == 0) *(volatile uint32_t*)bk.sync = 0u;
+    }
     PairQueue& Q = pq[warp];
     uint32_t qcnt = 0;                              // queued pairs of this warp (warp-uniform)
     for (; qa < qb && c < L.n_big; ++c) {
@@ -1351,7 +1408,7 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         const uint32_t sa = max(qa, C.quad_begin), sb = min(qb, q_end);
         // the cell's context, in every thread; the round keys are derived while the live
         // count n is loading
-        const uint32_t n = min(a.n_live[C.cell], C.width);
+        const uint32_t n = min(__ldcg(&a.n_live[C.cell]), C.width);
         const uint32_t kid = (uint32_t)a.kid[C.cell];
         const double dv = a.dv[C.cell];
         const float xup = __ull2float_ru(L.xmax[c]);
@@ -1399,21 +1456,24 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    // cells that lost SDs are compacted by big_compact_kernel, launched right after
+    // cells that lost SDs are compacted at the start of the next step (or by big_compact_kernel)
+    if (__any_sync(0xffffffffu, ls.removed != 0) && lane == 0) atomicOr(bk.sync, 1u);
 }
 
-// Step 0 for the large cells of the PRP contract: compacts, stably, the cells
-// that lost SDs in the step just run and resets their flags.  Launched after
-// big_prp_kernel as a programmatic dependent: its blocks may be scheduled while
-// the step's last blocks finish, and griddepcontrol.wait returns once the step
-// grid has completed and its memory operations are visible.  Without such a
-// dependency (a plain launch) the wait returns at once and stream order gives
-// the same guarantee.
+// Step 0 for the large cells of the PRP contract outside a PRP step: compacts,
+// stably, the cells flagged by the last step and resets the flags -- before the
+// state is read or stepped under the SORT contract, and after every
+// allocation-free step.  There it is launched as a programmatic dependent: its
+// blocks may be scheduled while the step's last blocks finish, and
+// griddepcontrol.wait returns once the step grid has completed and its memory
+// operations are visible.  After a plain launch the wait returns at once and
+// stream order gives the same guarantee.
 __global__ void __launch_bounds__(256) big_compact_kernel(StepArgs a, const BigCell* __restrict__ cells,
-                                                          uint32_t* removed, uint32_t n_big)
+                                                          uint32_t* removed, uint32_t n_big, uint32_t* sync)
 {
     __shared__ uint32_t wt[40];
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sync = 0u;         // every flagged cell is handled below
     for (uint32_t b = blockIdx.x; b < n_big; b += gridDim.x) {
         const uint32_t flag = *(volatile uint32_t*)&removed[b];   // the same in every thread
         if (!flag) continue;

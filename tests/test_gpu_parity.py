@@ -123,6 +123,35 @@ def test_large_cells_with_removals_bitexact(shuffle):
     assert min(live) < 257
 
 
+def test_removals_across_contracts_and_state_reads_bitexact():
+    """Large cells that lose SDs in a PRP step are compacted at the next step's start, or before a
+    state read or a SORT step: PRP steps, a totals() read, SORT steps, PRP steps again -- the
+    state equals the oracle's after each leg and the invariants hold."""
+    rng = np.random.default_rng(18)
+    counts = np.array([2600, 1900, 900])
+    n = int(counts.sum())
+    xi = rng.integers(1, 4, n).astype(np.uint64)
+    v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
+    s = inputs._state(xi, v, counts, 1e-14, [0, 1, 1], "removals_mixed")
+    o = _oracle_system(s, None, "prp")
+    g = _gpu_state(s, None, dict(tile_slots=512))
+    removed = 0
+    step = 0
+    for shuffle, k in (("prp", 15), ("sort", 6), ("prp", 12)):
+        o.shuffle = shuffle
+        o.run(s["dt"], 7, step, k)
+        st = g.step(s["dt"], 7, step, k, golovin_b=s["golovin_b"], stats=True, shuffle=shuffle)
+        removed += st["n_removed"]
+        step += k
+        n_tot, _, live = g.totals()                      # a state read between the legs
+        assert live == int(np.count_nonzero(o.xi))
+        xi_g, at_g, _ = g.get_state()
+        _assert_bitexact(o, xi_g, at_g)
+        assert g.check() == (0, 0)
+    assert removed > 300
+    g.close()
+
+
 @pytest.mark.parametrize("shuffle", SHUFFLES)
 def test_multiple_attributes_bitexact(shuffle):
     s = inputs.random_cells(n_cell=200, mean_per_cell=30, seed=9, xi_max=1000, dv=1e-11)
