@@ -91,6 +91,26 @@ def test_random_cells_bitexact(seed, shuffle):
 
 
 @pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_cell_sizes_at_the_kernel_borders_bitexact(shuffle):
+    """Cells on both sides of each border between code paths: 256 / 257 live SDs (sorted list or
+    bijection), 512 / 513 slots (one warp per cell or a tile), 1024 / 1025 slots (tile or large
+    cell), with dead slots so that the live count sits below the width, and small multiplicities
+    so that removals (and compaction) happen in every kind of cell."""
+    rng = np.random.default_rng(21)
+    counts = np.array([2, 3, 255, 256, 257, 258, 300, 511, 512, 513, 600, 1023, 1024, 1025, 1100])
+    n = int(counts.sum())
+    xi = rng.integers(1, 6, n).astype(np.uint64)
+    xi[rng.random(n) < 0.04] = 0                       # dead slots: live counts below the widths
+    v = inputs.lognormal_volumes(rng, n, 15e-6, 1.8)
+    kid = (np.arange(len(counts)) % 2).astype(np.uint8)
+    s = inputs._state(xi, v, counts, 3e-14, kid, "borders")
+    o, ost, xi_g, at, gst = _run_both(s, 30, seed=5, schedule=dict(tile_slots=1024), shuffle=shuffle)
+    _assert_bitexact(o, xi_g, at)
+    assert ost == {k: gst[k] for k in ost}
+    assert gst["n_removed"] > 50
+
+
+@pytest.mark.parametrize("shuffle", SHUFFLES)
 def test_big_cells_many_buckets_bitexact(shuffle):
     rng = np.random.default_rng(5)
     parts = []
