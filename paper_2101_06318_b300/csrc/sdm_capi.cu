@@ -38,7 +38,7 @@ struct DevAlloc {
 struct sdm_surrogate {
     int device = 0;
     cudaStream_t stream = nullptr;
-    float* buf = nullptr;                    // w32, wbf, grad, m, v, loss: 5 * NP + 1 floats
+    float* buf = nullptr;                    // w32, wbf, grad, m, v (SURR_NPS floats apart), loss
     uint8_t* mask = nullptr;                 // [SURR_TILES^2]
     float* tile_err = nullptr;               // [SURR_TILES^2]
     sdm::SurrogateDev* d_dev = nullptr;      // device copy of dev
@@ -1498,7 +1498,7 @@ sdm_status sdm_surrogate_create(sdm_surrogate** out, const sdm_surrogate_params*
     double* d_K = nullptr;
     do {
         if (cudaGetDevice(&s->device) != cudaSuccess) { st = SDM_ECUDA; break; }
-        const size_t nb = sizeof(float) * (5 * (size_t)SURR_NPARAM + 4);
+        const size_t nb = sizeof(float) * (5 * (size_t)SURR_NPS + 4);
         if (cudaMalloc(&s->buf, nb) != cudaSuccess ||
             cudaMalloc(&s->mask, SURR_TILES * SURR_TILES) != cudaSuccess ||
             cudaMalloc(&s->tile_err, sizeof(float) * SURR_TILES * SURR_TILES) != cudaSuccess ||
@@ -1511,11 +1511,11 @@ sdm_status sdm_surrogate_create(sdm_surrogate** out, const sdm_surrogate_params*
             cudaMemsetAsync(s->mask, 0, SURR_TILES * SURR_TILES, s->stream) != cudaSuccess) { st = SDM_ECUDA; break; }
         SurrTrainArgs& A = s->args;
         A.w32 = s->buf;
-        A.wbf = A.w32 + SURR_NPARAM;
-        A.grad = A.wbf + SURR_NPARAM;
-        A.m = A.grad + SURR_NPARAM;
-        A.v = A.m + SURR_NPARAM;
-        A.loss = A.v + SURR_NPARAM;
+        A.wbf = A.w32 + SURR_NPS;       // each array 16-byte aligned (vector loads of the weights)
+        A.grad = A.wbf + SURR_NPS;
+        A.m = A.grad + SURR_NPS;
+        A.v = A.m + SURR_NPS;
+        A.loss = A.v + SURR_NPS;
         A.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
         A.seed_hi = (uint32_t)(p->seed >> 32);
         A.ln_rmin = std::log(p->r_min);
@@ -1691,7 +1691,8 @@ sdm_status sdm_surrogate_eval(sdm_surrogate* s, const double* R, const double* r
     SDM_TRY(surr_check(s));
     if (!R || !r || !K) return SDM_EINVAL;
     if (n == 0) return SDM_OK;
-    surr_eval_kernel<<<(uint32_t)std::min<uint64_t>((n + 255) / 256, 4096), 256, 0, s->stream>>>(s->dev, R, r, n, K);
+    surr_eval_warp_kernel<<<(uint32_t)std::min<uint64_t>((n + 255) / 256, 4096), 256, 0, s->stream>>>(s->dev, R, r, n,
+                                                                                                      K);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }

@@ -116,17 +116,22 @@ __device__ __forceinline__ void phi_pair_u53(const StepArgs& a, uint32_t cell, u
 // Step 2 + Step 3 for one candidate pair (first, second) of a cell with phi
 // integer u53.  Writes the updated multiplicities and attributes of the pair to
 // global memory.
+// Kh_in: the surrogate's K^ of the pair when the caller evaluated it for the whole warp (-1: the
+// plain kernel), or SURR_PER_LANE to evaluate it here
+constexpr float SURR_PER_LANE = -2.0f;
 template <bool SURR>
 __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& c,
                                              uint64_t u53, uint64_t g1, uint64_t g2, uint64_t x1, uint64_t x2,
-                                             double v1, double v2, LocalStats& ls, uint32_t* removed_flag)
+                                             double v1, double v2, LocalStats& ls, uint32_t* removed_flag,
+                                             float Kh_in = SURR_PER_LANE)
 {
     const bool swap = x1 < x2;                 // j = first unless it has the smaller multiplicity
     const uint64_t xj = swap ? x2 : x1, xk = swap ? x1 : x2;
     const float scale32 = u64_to_f_trunc(xj) * c.s_dtdv32;
     uint64_t g;
     float Kh = -1.0f;
-    if (SURR && a.precision == PREC_SURROGATE && c.kid == 1) Kh = surr_pair_kernel(a.surr, v1, v2);
+    if (SURR && a.precision == PREC_SURROGATE && c.kid == 1)
+        Kh = Kh_in != SURR_PER_LANE ? Kh_in : surr_pair_kernel(a.surr, v1, v2);
     const P32 pe = Kh >= 0.0f ? P32{Kh * scale32, 0.0f} : pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf);
     if (a.precision != PREC_FP64) {
         g = gamma_tilde_f(pe.p, u53, xj, xk);
@@ -631,18 +636,26 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             const uint32_t k = qcnt - 32 + lane;
             const uint32_t ii = Q.ii[k], cq = Q.c[k];
             const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
+            float Kh = SURR_PER_LANE;
+            if (SURR && a.precision == PREC_SURROGATE)        // the warp's pairs on the tensor cores
+                Kh = surr_pair_kernel_warp(a.surr, v_s[i1], v_s[i2], ctx[cq].kid == 1);
             process_pair<SURR>(a, tab, ctx[cq], Q.u[k], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
-                         v_s[i1], v_s[i2], ls, &rem[cq]);
+                         v_s[i1], v_s[i2], ls, &rem[cq], Kh);
             __syncwarp();
             qcnt -= 32;
         }
     }
     __syncwarp();
-    if (lane < qcnt) {
-        const uint32_t ii = Q.ii[lane], cq = Q.c[lane];
+    {
+        const bool act = lane < qcnt;
+        const uint32_t ii = act ? Q.ii[lane] : 0u, cq = act ? Q.c[lane] : 0u;
         const uint32_t i1 = ii & 0xffffu, i2 = ii >> 16;
-        process_pair<SURR>(a, tab, ctx[cq], Q.u[lane], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1], xi_s[i2],
-                     v_s[i1], v_s[i2], ls, &rem[cq]);
+        float Kh = SURR_PER_LANE;
+        if (SURR && a.precision == PREC_SURROGATE)
+            Kh = surr_pair_kernel_warp(a.surr, v_s[i1], v_s[i2], act && ctx[cq].kid == 1);
+        if (act)
+            process_pair<SURR>(a, tab, ctx[cq], Q.u[lane], td.slot_begin + i1, td.slot_begin + i2, xi_s[i1],
+                               xi_s[i2], v_s[i1], v_s[i2], ls, &rem[cq], Kh);
     }
     __syncthreads();
     // removals take effect in storage: compact the cells that lost SDs (rare)
@@ -761,12 +774,15 @@ __device__ __forceinline__ void warp_cell_drain(const StepArgs& a, const EffTab*
                                                 LocalStats& ls, uint32_t lane)
 {
     __syncwarp();
-    if (lane < take) {
-        const uint32_t k = qcnt - take + lane;
-        const uint32_t ii = S.q.ii[k];
-        const uint64_t g1 = s0 + (ii & 0xffffu), g2 = s0 + (ii >> 16);
-        process_pair<SURR>(a, T, cc, S.q.u[k], g1, g2, a.xi[g1], a.xi[g2], a.attr[g1], a.attr[g2], ls, &S.rem);
-    }
+    const bool act = lane < take;
+    const uint32_t k = qcnt - take + lane;
+    const uint32_t ii = act ? S.q.ii[k] : 0u;
+    const uint64_t g1 = s0 + (ii & 0xffffu), g2 = s0 + (ii >> 16);
+    const double v1 = act ? a.attr[g1] : 0.0, v2 = act ? a.attr[g2] : 0.0;
+    float Kh = SURR_PER_LANE;
+    if (SURR && a.precision == PREC_SURROGATE && cc.kid == 1)
+        Kh = surr_pair_kernel_warp(a.surr, v1, v2, act);         // the warp's pairs on the tensor cores
+    if (act) process_pair<SURR>(a, T, cc, S.q.u[k], g1, g2, a.xi[g1], a.xi[g2], v1, v2, ls, &S.rem, Kh);
     __syncwarp();
     qcnt -= take;
 }
@@ -1232,11 +1248,14 @@ __device__ __forceinline__ void drain_queue(const StepArgs& a, const EffTab* __r
                                             uint32_t* removed_flag, uint32_t lane)
 {
     __syncwarp();
-    if (lane < take) {
-        const uint32_t k = qcnt - take + lane;
-        const uint32_t s1 = Q.s1[k], s2 = Q.s2[k];
-        process_pair<SURR>(a, T, cc, Q.u[k], s1, s2, a.xi[s1], a.xi[s2], a.attr[s1], a.attr[s2], ls, removed_flag);
-    }
+    const bool act = lane < take;
+    const uint32_t k = qcnt - take + lane;
+    const uint32_t s1 = act ? Q.s1[k] : 0u, s2 = act ? Q.s2[k] : 0u;
+    const double v1 = act ? a.attr[s1] : 0.0, v2 = act ? a.attr[s2] : 0.0;
+    float Kh = SURR_PER_LANE;
+    if (SURR && a.precision == PREC_SURROGATE && cc.kid == 1)
+        Kh = surr_pair_kernel_warp(a.surr, v1, v2, act);         // the warp's pairs on the tensor cores
+    if (act) process_pair<SURR>(a, T, cc, Q.u[k], s1, s2, a.xi[s1], a.xi[s2], v1, v2, ls, removed_flag, Kh);
     __syncwarp();
     qcnt -= take;
 }

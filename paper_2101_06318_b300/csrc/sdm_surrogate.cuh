@@ -31,6 +31,7 @@ constexpr int SURR_B3 = SURR_W3 + SURR_H * SURR_H;
 constexpr int SURR_W4 = SURR_B3 + SURR_H;  // [64]
 constexpr int SURR_B4 = SURR_W4 + SURR_H;
 constexpr int SURR_NPARAM = SURR_B4 + 1;   // 8577
+constexpr int SURR_NPS = (SURR_NPARAM + 3) & ~3;   // stride of the parameter-sized device arrays
 constexpr int SURR_TILES = 256;            // fallback mask: tiles per input axis over [-1, 1]
 
 // What a step needs of a trained surrogate (device pointers).
@@ -323,6 +324,175 @@ __device__ __noinline__ float surr_pair_kernel(const SurrogateDev* __restrict__ 
     const float r1 = cbrtf((float)v1 * c), r2 = cbrtf((float)v2 * c);
     const SurrogateDev D = *S;
     return surr_kernel(D, fmaxf(r1, r2), fminf(r1, r2));
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores for a warp's 32 pairs at once (the queued pairs a
+// step evaluates together).  The samples are the rows of the activation matrix
+// (M = 32: two m16 tiles), the 64 hidden units its columns; the 64 x 64 layers are
+// mma.sync m16n8k16 products with BF16 operands and FP32 accumulation.  An FP32
+// activation x enters as hi + lo with hi = bf16(x), lo = bf16(x - hi), two products
+// per tile, so that the result keeps ~16 bits of each activation (the weights are
+// BF16 already).  The accumulator layout of two adjacent n8 tiles is the operand
+// layout of one k16 slab, so a layer's output feeds the next layer from registers.
+//   fragments (lane = 4 g + t): A regs {(g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..),
+//   (g+8, 2t+8..)}; B regs {(k = 2t..2t+1, n = g), (k = 2t+8.., n = g)};
+//   C/D {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo_elem, float hi_elem)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// hi and lo BF16 operand registers of four FP32 values laid out as one A register pair set
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo)
+{
+    const float h0 = bf16_round(x0), h1 = bf16_round(x1);
+    hi = bf16x2_bits(h0, h1);
+    lo = bf16x2_bits(x0 - h0, x1 - h1);
+}
+
+// One 64 x 64 layer for one m16 tile: out = silu(W in + b), in given as hi/lo A operand
+// registers per k16 slab, out as FP32 accumulators per n8 tile.
+__device__ __forceinline__ void surr_layer_mma(const float* __restrict__ W, const float* __restrict__ bias,
+                                               const uint32_t (&ahi)[4][4], const uint32_t (&alo)[4][4],
+                                               float (&out)[8][4], uint32_t g, uint32_t t)
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2 bb = __ldg(reinterpret_cast<const float2*>(bias + 8 * j + 2 * t));
+        out[j][0] = bb.x; out[j][1] = bb.y; out[j][2] = bb.x; out[j][3] = bb.y;
+        const float* row = W + SURR_H * (8 * j + g);               // unit n = 8 j + g
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            const float2 w0 = __ldg(reinterpret_cast<const float2*>(row + 16 * ks + 2 * t));
+            const float2 w1 = __ldg(reinterpret_cast<const float2*>(row + 16 * ks + 2 * t + 8));
+            const uint32_t b0 = bf16x2_bits(w0.x, w0.y), b1 = bf16x2_bits(w1.x, w1.y);   // exact: BF16 values
+            mma_bf16_16816(out[j], ahi[ks], b0, b1);
+            mma_bf16_16816(out[j], alo[ks], b0, b1);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) out[j][e] = silu_f(out[j][e]);
+    }
+}
+
+// accumulators of the n8 tiles 2 ks, 2 ks + 1 -> hi/lo operands of k16 slab ks
+__device__ __forceinline__ void acc_to_operand(const float (&d)[8][4], uint32_t (&ahi)[4][4], uint32_t (&alo)[4][4])
+{
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        split_bf16(d[2 * ks][0], d[2 * ks][1], ahi[ks][0], alo[ks][0]);          // (g, 2t..)
+        split_bf16(d[2 * ks][2], d[2 * ks][3], ahi[ks][1], alo[ks][1]);          // (g+8, 2t..)
+        split_bf16(d[2 * ks + 1][0], d[2 * ks + 1][1], ahi[ks][2], alo[ks][2]);  // (g, 2t+8..)
+        split_bf16(d[2 * ks + 1][2], d[2 * ks + 1][3], ahi[ks][3], alo[ks][3]);  // (g+8, 2t+8..)
+    }
+}
+
+// Network output y of the sample (z0, z1) of every lane; all 32 lanes take part.
+__device__ __noinline__ float surr_forward_warp(const float* __restrict__ w, float z0, float z1)
+{
+    const uint32_t lane = threadIdx.x & 31u, g = lane >> 2, t = lane & 3u;
+    float ysel[2][2];
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        // layer 1 in operand layout: rows 16 mt + g and 16 mt + g + 8 of h1 = silu(W1 z + b1)
+        const float za0 = __shfl_sync(0xffffffffu, z0, 16 * mt + g), za1 = __shfl_sync(0xffffffffu, z1, 16 * mt + g);
+        const float zb0 = __shfl_sync(0xffffffffu, z0, 16 * mt + g + 8),
+                    zb1 = __shfl_sync(0xffffffffu, z1, 16 * mt + g + 8);
+        uint32_t ahi[4][4], alo[4][4];
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {               // columns 16 ks + 2t (+8 half)
+                const int k = 16 * ks + 2 * t + 8 * half;
+                const float4 wk = __ldg(reinterpret_cast<const float4*>(w + SURR_W1 + 2 * k));   // units k, k+1
+                const float2 bk = __ldg(reinterpret_cast<const float2*>(w + SURR_B1 + k));
+                const float pa0 = silu_f(fmaf(wk.x, za0, fmaf(wk.y, za1, bk.x)));
+                const float pa1 = silu_f(fmaf(wk.z, za0, fmaf(wk.w, za1, bk.y)));
+                const float pb0 = silu_f(fmaf(wk.x, zb0, fmaf(wk.y, zb1, bk.x)));
+                const float pb1 = silu_f(fmaf(wk.z, zb0, fmaf(wk.w, zb1, bk.y)));
+                split_bf16(pa0, pa1, ahi[ks][2 * half], alo[ks][2 * half]);
+                split_bf16(pb0, pb1, ahi[ks][2 * half + 1], alo[ks][2 * half + 1]);
+            }
+        }
+        float d[8][4];
+        surr_layer_mma(w + SURR_W2, w + SURR_B2, ahi, alo, d, g, t);
+        acc_to_operand(d, ahi, alo);
+        surr_layer_mma(w + SURR_W3, w + SURR_B3, ahi, alo, d, g, t);
+        // output unit: partial dot products over this lane's 16 columns, summed over the group
+        float ya = 0.0f, yb = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 w4 = __ldg(reinterpret_cast<const float2*>(w + SURR_W4 + 8 * j + 2 * t));
+            ya = fmaf(w4.x, d[j][0], fmaf(w4.y, d[j][1], ya));
+            yb = fmaf(w4.x, d[j][2], fmaf(w4.y, d[j][3], yb));
+        }
+        ya += __shfl_xor_sync(0xffffffffu, ya, 1);
+        ya += __shfl_xor_sync(0xffffffffu, ya, 2);
+        yb += __shfl_xor_sync(0xffffffffu, yb, 1);
+        yb += __shfl_xor_sync(0xffffffffu, yb, 2);
+        ysel[mt][0] = ya;                                        // sample 16 mt + g
+        ysel[mt][1] = yb;                                        // sample 16 mt + g + 8
+    }
+    // sample `lane` = 16 mt + 8 h + g' sits in lanes 4 g' .. 4 g' + 3
+    const uint32_t src = 4u * (lane & 7u);
+    const float y00 = __shfl_sync(0xffffffffu, ysel[0][0], src), y01 = __shfl_sync(0xffffffffu, ysel[0][1], src);
+    const float y10 = __shfl_sync(0xffffffffu, ysel[1][0], src), y11 = __shfl_sync(0xffffffffu, ysel[1][1], src);
+    const uint32_t mt = lane >> 4, h = (lane >> 3) & 1u;
+    const float y = mt ? (h ? y11 : y10) : (h ? y01 : y00);
+    return y + __ldg(w + SURR_B4);
+}
+
+// K^ of each lane's pair of volumes (or -1: the plain kernel is used, also for inactive lanes);
+// every lane of the warp calls it, converged
+__device__ __forceinline__ float surr_pair_kernel_warp(const SurrogateDev* __restrict__ Sp, double v1, double v2,
+                                                       bool active)
+{
+    const float c = 0.238732414637843f;   // 3 / (4 pi)
+    const SurrogateDev S = *Sp;
+    float z0 = 0.0f, z1 = 0.0f;
+    bool use = false;
+    if (active) {
+        const float r1 = cbrtf((float)v1 * c), r2 = cbrtf((float)v2 * c);
+        const float R = fmaxf(r1, r2), r = fminf(r1, r2);
+        if (r >= S.r_min && R <= S.r_max) {
+            z0 = (__logf(R) - S.c0) / S.c1;
+            z1 = (__logf(r) - S.c0) / S.c1;
+            const int ta = min(SURR_TILES - 1, max(0, (int)((z0 + 1.0f) * (0.5f * SURR_TILES))));
+            const int tb = min(SURR_TILES - 1, max(0, (int)((z1 + 1.0f) * (0.5f * SURR_TILES))));
+            use = S.mask[ta * SURR_TILES + tb] != 0;
+        }
+    }
+    if (!__any_sync(0xffffffffu, use)) return -1.0f;
+    const float y = surr_forward_warp(S.w, use ? z0 : 0.0f, use ? z1 : 0.0f);
+    return use ? fmaxf(__expf(fmaf(S.sigma, y, S.mu)) - S.k_floor, 0.0f) : -1.0f;
+}
+
+// Device-side evaluation through the step's tensor-core path: K^ (or -1) per pair, one warp per
+// 32 pairs.
+__global__ void surr_eval_warp_kernel(SurrogateDev S, const double* R, const double* r, uint64_t n, float* K)
+{
+    __shared__ SurrogateDev Ss;
+    if (threadIdx.x == 0) Ss = S;
+    __syncthreads();
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n; base += 32 * nw) {
+        const uint64_t i = base + (threadIdx.x & 31u);
+        const bool act = i < n;
+        const double Ri = act ? fmax(R[i], r[i]) : 1.0, ri = act ? fmin(R[i], r[i]) : 1.0;
+        const double c = 4.0 / 3.0 * 3.14159265358979311600;
+        const float k = surr_pair_kernel_warp(&Ss, c * Ri * Ri * Ri, c * ri * ri * ri, act);
+        if (act) K[i] = k;
+    }
 }
 
 // Device-side evaluation for tests: K^ (or -1 where the plain kernel is used) per pair.

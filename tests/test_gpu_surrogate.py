@@ -78,6 +78,29 @@ def test_training_lowers_loss_and_mask_bounds_error(trained):
     assert np.all(out < 0)
 
 
+def test_tensor_core_inference_matches_the_oracle_network(trained):
+    """The steps evaluate the network for a warp's 32 pairs at once on the tensor cores (BF16
+    operands, the activations split into two BF16 terms, FP32 sums); sdm_surrogate_eval runs the
+    same path. Its K^ equals the FP64 oracle's network with the same BF16-rounded weights to well
+    within the fallback threshold, for batches of every fill (n not a multiple of 32)."""
+    s, _, _, _ = trained
+    info = s.info()
+    wb = so.bf16_round(s.params()).astype(np.float64)
+    rng = np.random.default_rng(23)
+    n = 20000 + 17
+    lr = rng.uniform(np.log(1.2e-6), np.log(2.9e-3), (2, n))
+    R, r = np.exp(lr.max(axis=0)), np.exp(lr.min(axis=0))
+    K = s.eval(torch.from_numpy(R).cuda(), torch.from_numpy(r).cuda()).cpu().numpy().astype(np.float64)
+    used = K >= 0
+    assert used.mean() > 0.03
+    z = np.stack([(np.log(R) - info["c0"]) / info["c1"], (np.log(r) - info["c0"]) / info["c1"]], axis=1)
+    y = so.forward(wb, z[used])
+    Ko = np.maximum(np.exp(info["mu"] + info["sigma"] * y) - info["k_floor"], 0.0)
+    big = Ko > 1e-3 * np.median(Ko)
+    rel = np.abs(K[used][big] - Ko[big]) / Ko[big]
+    assert np.quantile(rel, 0.999) < 2e-3, np.quantile(rel, 0.999)
+
+
 def test_surrogate_steps_keep_invariants_and_track_fp64(trained):
     s, _, _, _ = trained
     box = inputs.gravitational_box(n_sd=1 << 16, seed=9)
