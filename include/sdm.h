@@ -47,7 +47,7 @@
  *       A = 2^floor(k/2), B = 2^(k - floor(k/2)); otherwise A = ceil(sqrt n),
  *       B = ceil(n / A)), rounds L = (L + floor(h A / 2^32)) mod A and
  *       R = (R + floor(h B / 2^32)) mod B with h = lowbias32(v ^ K_r) of the
- *       other half v, round keys
+ *       other half v without the hash's last step x ^= x >> 16, round keys
  *       K_0..3 = philox(0, c, s, 2), K_4..7 = philox(1, c, s, 2), and
  *       cycle-walking into [0, n).  No sort and no data exchange is needed.
  *   Pair m is (L'[2m], L'[2m+1]) (Sec. 2.2 Step 1, Fig. "pair_flag").

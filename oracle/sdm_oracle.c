@@ -51,8 +51,9 @@
  *         eight-round alternating Feistel network on Z_A x Z_B (x = L B + R;
  *         A B = n with halves of floor(k/2) and k - floor(k/2) bits when
  *         n = 2^k, else A = ceil(sqrt n), B = ceil(n / A)), round function
- *         h = lowbias32(v ^ K_r) (C. Wellons' 32-bit integer hash) of the other
- *         half v, added as floor(h M / 2^32) modulo the half's size M, round keys
+ *         h = lowbias32(v ^ K_r) without its last step x ^= x >> 16 (C. Wellons'
+ *         32-bit integer hash) of the other half v, added as floor(h M / 2^32)
+ *         modulo the half's size M, round keys
  *         K_0..K_3 = philox(0, c, s, 2), K_4..K_7 = philox(1, c, s, 2), and
  *         cycle-walking (apply the network again while the value is >= n) to
  *         stay inside [0, n); A B < n + A makes walking rare.  (Below ~256 elements a Feistel network of this
@@ -127,14 +128,16 @@ uint32_t sdmo_shuffle_key(uint64_t seed, uint32_t cell, uint32_t step, uint32_t 
     return x[l & 3];
 }
 
-/* lowbias32 (C. Wellons, "Prospecting for hash functions", 2018) */
-static uint32_t lowbias32(uint32_t x)
+/* The Feistel round function: lowbias32 (C. Wellons, "Prospecting for hash functions",
+ * 2018) without its last step x ^= x >> 16.  A round uses floor(h M / 2^32) with M < 2^16,
+ * which the top bits of h decide (alone when M is a power of two); that last step leaves the
+ * top 16 bits unchanged. */
+static uint32_t round_hash(uint32_t x)
 {
     x ^= x >> 16;
     x *= 0x7feb352du;
     x ^= x >> 15;
     x *= 0x846ca68bu;
-    x ^= x >> 16;
     return x;
 }
 
@@ -177,7 +180,7 @@ static void prp_domain(uint32_t n, uint32_t* A, uint32_t* B)
 }
 
 /* One pass of the alternating Feistel network on Z_A x Z_B: for r = 0..7, with
- * h = lowbias32(v ^ K_r) of the other half v,
+ * h = round_hash(v ^ K_r) of the other half v,
  *   even r: L = (L + floor(h A / 2^32)) mod A;   odd r: R = (R + floor(h B / 2^32)) mod B.
  * Each round is a bijection of Z_A x Z_B (it shifts one half by an amount that depends only on
  * the other half), so the pass is one too. */
@@ -187,10 +190,10 @@ static uint32_t feistel(uint32_t q, uint32_t A, uint32_t B, const uint32_t K[SDM
     int r;
     for (r = 0; r < SDMO_PRP_ROUNDS; ++r) {
         if ((r & 1) == 0) {
-            const uint32_t h = lowbias32(R ^ K[r]);
+            const uint32_t h = round_hash(R ^ K[r]);
             L = (uint32_t)((L + (((uint64_t)h * A) >> 32)) % A);
         } else {
-            const uint32_t h = lowbias32(L ^ K[r]);
+            const uint32_t h = round_hash(L ^ K[r]);
             R = (uint32_t)((R + (((uint64_t)h * B) >> 32)) % B);
         }
     }

@@ -55,8 +55,9 @@ __device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, 
 // ---------------------------------------------------------------------------
 // PRP shuffle: a keyed bijection P of [0, n) for cells of more than 256 live
 // SDs -- an eight-round alternating Feistel network on Z_A x Z_B with round
-// function h = lowbias32(v ^ K_r) (C. Wellons' 32-bit integer hash) of the
-// other half v, added as floor(h M / 2^32) modulo the half's size M.  For
+// function h = lowbias32(v ^ K_r) without its last xor-shift (C. Wellons'
+// 32-bit integer hash) of the other half v, added as floor(h M / 2^32) modulo
+// the half's size M.  For
 // n = 2^k the halves have floor(k/2) and k - floor(k/2) bits (A B = n);
 // otherwise A = ceil(sqrt n), B = ceil(n / A).  Philox round keys;
 // cycle-walking into [0, n), rare because A B < n + A.
@@ -66,30 +67,12 @@ __device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, 
 constexpr uint32_t PRP_ROUNDS = 8;
 constexpr uint32_t PRP_MIN_N = 257;      // smaller cells are shuffled by sorting keys
 
-__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-// lowbias32 after its first step (x ^= x >> 16).  The Feistel halves have at most
-// 16 bits, so (v ^ K) >> 16 = K >> 16 and lowbias32(v ^ K) = lowbias32_tail(v ^ Kx)
-// with Kx = K ^ (K >> 16): the first step is folded into the round key.
-__device__ __forceinline__ uint32_t lowbias32_tail(uint32_t x)
-{
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-// lowbias32_tail without its last step x ^= x >> 16, which leaves the top 16
-// bits unchanged: enough wherever only the top 16 bits or fewer are used.
+// The round function h(v ^ K) of the bijection: lowbias32 (C. Wellons' 32-bit
+// integer hash) without its last step x ^= x >> 16 -- a round uses floor(h M /
+// 2^32), M < 2^16, which the top bits of h decide (alone when M is a power of
+// two), and that step leaves the top 16 bits unchanged.  The halves have at most
+// 16 bits, so (v ^ K) >> 16 = K >> 16 and the hash's first step x ^= x >> 16 is
+// folded into the round key: h = lowbias32_top16(v ^ Kx), Kx = K ^ (K >> 16).
 __device__ __forceinline__ uint32_t lowbias32_top16(uint32_t x)
 {
     x *= 0x7feb352du;
@@ -161,16 +144,16 @@ __device__ __forceinline__ void prp_split(const Prp& P, uint32_t x, uint32_t& L,
 // one round pair of the network: L = (L + floor(h A / 2^32)) mod A, then R likewise mod B
 __device__ __forceinline__ void prp_round_pair(const Prp& P, uint32_t kl, uint32_t kr, uint32_t& L, uint32_t& R)
 {
-    const uint32_t tl = L + __umulhi(lowbias32_tail(R ^ kl), P.A);
+    const uint32_t tl = L + __umulhi(lowbias32_top16(R ^ kl), P.A);
     L = tl >= P.A ? tl - P.A : tl;
-    const uint32_t tr = R + __umulhi(lowbias32_tail(L ^ kr), P.B);
+    const uint32_t tr = R + __umulhi(lowbias32_top16(L ^ kr), P.B);
     R = tr >= P.B ? tr - P.B : tr;
 }
 
 // The same round pair when A = 2^a and B = 2^b (a, b <= 16): floor(h A / 2^32) is
-// the top a bits of h, which the hash's last step does not change, and the
-// reduction mod A is deferred -- L and R carry values congruent to the halves
-// (below 2^19 after the four additions of a pass) and are masked where read.
+// the top a bits of h, and the reduction mod A is deferred -- L and R carry values
+// congruent to the halves (below 2^19 after the four additions of a pass) and are
+// masked where read.
 __device__ __forceinline__ void prp_round_pair_pow2(const Prp& P, uint32_t kl, uint32_t kr, uint32_t& L, uint32_t& R)
 {
     L += lowbias32_top16((R & (P.B - 1u)) ^ kl) >> P.sa;
