@@ -268,5 +268,36 @@ class System:
             raise RuntimeError("sdmo_spectrum failed")
         return out
 
+    def rebucket(self, cell_id):
+        """Displacement between steps: every live SD moves to the cell ``cell_id[slot]`` names.
+
+        The paper keeps a cell index per SD and regroups the SDs by it (its cell_start array,
+        Sec. 3); the slot model here keeps each cell's slot range fixed, so a cell's width is its
+        capacity.  Within a cell the SDs keep their old slot order (a stable sort by the new cell
+        index, numpy's stable argsort being the sort), the live ones first.  Returns False, with
+        the state unchanged, when an index is out of range or a cell receives more SDs than its
+        width; True otherwise.
+        """
+        cell_id = np.asarray(cell_id, np.int64)
+        live = np.flatnonzero(self.xi)
+        newc = cell_id[live]
+        if len(newc) and (newc.min() < 0 or newc.max() >= self.n_cell):
+            return False
+        counts = np.bincount(newc, minlength=self.n_cell)
+        width = np.diff(self.cell_start.astype(np.int64))
+        if np.any(counts > width):
+            return False
+        order = np.argsort(newc, kind="stable")
+        src = live[order]
+        cells = newc[order]
+        first = np.concatenate([[0], np.cumsum(counts)[:-1]])      # position of each cell's first SD
+        dest = self.cell_start[cells].astype(np.int64) + (np.arange(len(order)) - first[cells])
+        xi = np.zeros_like(self.xi)
+        attr = np.zeros_like(self.attr)
+        xi[dest] = self.xi[src]
+        attr[:, dest] = self.attr[:, src]
+        self.xi, self.attr = xi, attr
+        return True
+
     def copy(self):
         return System(self.xi, self.attr, self.cell_start, self.dv, self.kernel_id, self.golovin_b, self.shuffle)
