@@ -222,6 +222,19 @@ sdm_status sdm_remove_zero(sdm_state* st, uint64_t* n_live);
 sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, uint32_t cell,
                         double* out, int out_on_device);
 
+/* Displacement between steps: every live SD moves to the cell cell_id[i]
+ * names (cell_id[n_sd], one entry per slot of the current layout, read for
+ * live slots only; host or device pointer).  The paper keeps a cell index per
+ * SD and regroups the SDs by it (Sec. 3, cell_start); here each cell keeps its
+ * slot range, so its width is its capacity -- allocate spare slots for cells
+ * that may gain SDs.  Within a cell the SDs keep their old slot order, live
+ * ones first (a stable sort by the new index: radix passes of 8 bits, then a
+ * gather).  SDM_EINVAL for an index >= n_cell, SDM_ECAPACITY when a cell would
+ * receive more SDs than its width -- the state is unchanged in both cases;
+ * SDM_ENOTSUP for a state on a caller's workspace (the sort needs scratch).
+ * Synchronises once (to read the checks). */
+sdm_status sdm_rebucket(sdm_state* st, const uint32_t* cell_id, int ptrs_on_device);
+
 /* Consistency check of the state's invariants (a diagnostic; Step 0 of
  * Fig. "fig:algo" relies on the first, the early exit on the second):
  *   *n_bad_live = slots that break the live-prefix rule: within every cell the

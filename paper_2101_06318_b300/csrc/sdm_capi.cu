@@ -1052,6 +1052,81 @@ sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_
     return SDM_OK;
 }
 
+sdm_status sdm_rebucket(sdm_state* st, const uint32_t* cell_id, int ptrs_on_device)
+{
+    if (!st || !st->initialised || !cell_id) return SDM_EINVAL;
+    if (st->ws) return SDM_ENOTSUP;                  // needs scratch beyond a caller's workspace
+    const uint64_t n = st->n_sd;
+    if (n == 0) return SDM_OK;
+    if (n >= (1ull << 32)) return SDM_ENOTSUP;
+    SDM_TRY(flush_big_compaction(st));
+    cudaStream_t s = st->stream;
+    const uint32_t n_tiles = (uint32_t)((n + RB_TILE - 1) / RB_TILE);
+    // scratch: cid | key 2 | val 2 | count | first | hist | tot | base | err | xi_new | attr_new
+    const size_t b_u32 = sizeof(uint32_t) * (5 * n + 2 * (size_t)st->n_cell + 1 + 256 * (size_t)n_tiles + 512 + 4);
+    const size_t b_new = sizeof(uint64_t) * st->cap + sizeof(double) * st->cap * st->n_attr;
+    char* buf = nullptr;
+    SDM_CUDA(cudaMallocAsync((void**)&buf, b_new + b_u32 + 256, s));
+    uint64_t* xi_new = (uint64_t*)buf;
+    double* attr_new = (double*)(buf + sizeof(uint64_t) * st->cap);
+    uint32_t* u = (uint32_t*)(buf + b_new);
+    uint32_t* cid = u;
+    uint32_t* key0 = cid + n;
+    uint32_t* key1 = key0 + n;
+    uint32_t* val0 = key1 + n;
+    uint32_t* val1 = val0 + n;
+    uint32_t* count = val1 + n;
+    uint32_t* first = count + st->n_cell;
+    uint32_t* hist = first + st->n_cell + 1;
+    uint32_t* tot = hist + 256 * (size_t)n_tiles;
+    uint32_t* base = tot + 256;
+    uint32_t* err = base + 256;
+    sdm_status rs = SDM_OK;
+    auto fail = [&](sdm_status e) { cudaFreeAsync(buf, s); return e; };
+    if (cudaMemcpyAsync(cid, cell_id, sizeof(uint32_t) * n,
+                        ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(count, 0, sizeof(uint32_t) * st->n_cell, s) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess)
+        return fail(SDM_ECUDA);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 8 * (uint64_t)st->n_sm);
+    rb_keys_kernel<<<grid, 256, 0, s>>>(st->d_xi, cid, n, st->n_cell, key0, val0, count, err);
+    rb_capacity_kernel<<<std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm)), 256, 0,
+                         s>>>(count, st->d_cell_start, st->n_cell, err);
+    uint32_t h_err = 0;
+    if (cudaMemcpyAsync(&h_err, err, sizeof h_err, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(SDM_ECUDA);
+    if (h_err & 1u) return fail(SDM_EINVAL);              // a live SD's index is not a cell
+    if (h_err & ERR_CAPACITY) return fail(SDM_ECAPACITY);  // a cell would overflow: state unchanged
+    // the stable sort by new cell, 8 bits per pass (the dead slots' key n_cell included)
+    const uint32_t bits = std::max<uint32_t>(1, ceil_log2_h((uint64_t)st->n_cell + 1));
+    uint32_t *kin = key0, *kout = key1, *vin = val0, *vout = val1;
+    for (uint32_t shift = 0; shift < bits; shift += 8) {
+        rb_hist_kernel<<<n_tiles, RB_THREADS, 0, s>>>(kin, n, shift, n_tiles, hist);
+        rb_scan_rows_kernel<<<256, RB_THREADS, 0, s>>>(hist, n_tiles, tot);
+        rb_scan_digits_kernel<<<1, 256, 0, s>>>(tot, base);
+        rb_scatter_kernel<<<n_tiles, RB_THREADS, 0, s>>>(kin, vin, n, shift, n_tiles, hist, base, kout, vout);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    rb_first_kernel<<<1, 1024, 0, s>>>(count, st->n_cell, first);
+    if (cudaMemsetAsync(buf, 0, b_new, s) != cudaSuccess) return fail(SDM_ECUDA);
+    rb_gather_kernel<<<grid, 256, 0, s>>>(kin, vin, n, st->n_cell, first, st->d_cell_start, st->d_xi, st->d_attr, st->cap,
+                                          st->n_attr, xi_new, attr_new);
+    if (cudaMemcpyAsync(st->d_xi, xi_new, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(SDM_ECUDA);
+    for (uint32_t a = 0; a < st->n_attr; ++a)
+        if (cudaMemcpyAsync(st->d_attr + (uint64_t)a * st->cap, attr_new + (uint64_t)a * st->cap, sizeof(double) * n,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(SDM_ECUDA);
+    if (cudaMemcpyAsync(st->d_n_live, count, sizeof(uint32_t) * st->n_cell, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(SDM_ECUDA);
+    if (cudaGetLastError() != cudaSuccess) return fail(SDM_ECUDA);
+    rs = refresh_big_bounds(st);                           // multiplicity bounds and volume bins
+    cudaFreeAsync(buf, s);
+    return rs;
+}
+
 sdm_status sdm_totals(sdm_state* st, uint64_t* n_total, double* mass, uint64_t* n_live)
 {
     if (!st || !st->initialised) return SDM_EINVAL;

@@ -207,9 +207,9 @@ __device__ __forceinline__ void flush_stats(const StepArgs& a, LocalStats& ls, u
     if (threadIdx.x < 5 && red[threadIdx.x]) atomicAdd(&a.stats[threadIdx.x], red[threadIdx.x]);
 }
 
-// Exclusive scan of a[0..n) in place (block-wide); a[n] receives the total.
-// 'warp_tot' needs 33 entries of shared memory.
-__device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* warp_tot)
+// Exclusive scan of a[0..n) in place (block-wide); warp_tot[32] receives the total, and a[n]
+// too when store_total.  'warp_tot' needs 33 entries of shared memory.
+__device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* warp_tot, bool store_total = true)
 {
     const uint32_t nt = blockDim.x, tid = threadIdx.x;
     const uint32_t per = (n + nt - 1) / nt;
@@ -245,7 +245,7 @@ __device__ void block_exclusive_scan(uint32_t* a, uint32_t n, uint32_t* warp_tot
         a[i] = run;
         run += t;
     }
-    if (tid == 0) a[n] = warp_tot[32];
+    if (tid == 0 && store_total) a[n] = warp_tot[32];
     __syncthreads();
 }
 
@@ -1844,6 +1844,164 @@ __global__ void big_xmax_kernel(const uint64_t* __restrict__ xi, const double* _
     if (threadIdx.x == 0) {
         for (uint32_t w = 1; w < (blockDim.x + 31) / 32; ++w) m = max(m, s_max[w]);
         if (m) atomicMax(&xmax[K.big], m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Displacement (sdm_rebucket): every live SD moves to the cell its new index names;
+// within a cell the SDs keep their old slot order.  A stable sort of the slots by
+// new cell -- least-significant-digit radix passes of 8 bits over the cell index,
+// each a per-tile digit count, a scan over (digit, tile) and a stable scatter --
+// then a gather into the cells' slot ranges.  Dead slots sort last (key n_cell).
+// ---------------------------------------------------------------------------
+constexpr uint32_t RB_TILE = 2048;            // slots per block of a radix pass
+constexpr uint32_t RB_THREADS = 256;
+constexpr uint32_t RB_WARPS = RB_THREADS / 32;
+constexpr uint32_t RB_PER_WARP = RB_TILE / RB_WARPS;
+constexpr uint32_t ERR_CAPACITY = 8u;         // a cell would receive more SDs than its width
+
+__global__ void rb_keys_kernel(const uint64_t* __restrict__ xi, const uint32_t* __restrict__ cell_id, uint64_t n,
+                               uint32_t n_cell, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                               uint32_t* __restrict__ count, uint32_t* err)
+{
+    uint32_t bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t k = n_cell;
+        if (xi[i] != 0) {
+            const uint32_t c = cell_id[i];
+            if (c < n_cell) {
+                k = c;
+                atomicAdd(&count[c], 1u);
+            } else {
+                bad = 1;
+            }
+        }
+        key[i] = k;
+        val[i] = (uint32_t)i;
+    }
+    if (bad) atomicOr(err, 1u);
+}
+
+__global__ void rb_capacity_kernel(const uint32_t* __restrict__ count, const uint32_t* __restrict__ cs,
+                                   uint32_t n_cell, uint32_t* err)
+{
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cell; c += gridDim.x * blockDim.x)
+        if (count[c] > cs[c + 1] - cs[c]) atomicOr(err, ERR_CAPACITY);
+}
+
+__global__ void __launch_bounds__(RB_THREADS) rb_hist_kernel(const uint32_t* __restrict__ key, uint64_t n,
+                                                             uint32_t shift, uint32_t n_tiles,
+                                                             uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * RB_TILE;
+    for (uint32_t k = threadIdx.x; k < RB_TILE; k += RB_THREADS)
+        if (t0 + k < n) atomicAdd(&h[(key[t0 + k] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of each digit's row of tile counts (one block per digit); tot[d] = row sum
+__global__ void __launch_bounds__(RB_THREADS) rb_scan_rows_kernel(uint32_t* __restrict__ hist, uint32_t n_tiles,
+                                                                  uint32_t* __restrict__ tot)
+{
+    __shared__ uint32_t wt[40];
+    uint32_t* row = hist + (uint64_t)blockIdx.x * n_tiles;
+    block_exclusive_scan(row, n_tiles, wt, false);
+    if (threadIdx.x == 0) tot[blockIdx.x] = wt[32];
+}
+
+// base[d] = sum of the rows of the digits below d (one block of 256 threads)
+__global__ void rb_scan_digits_kernel(const uint32_t* __restrict__ tot, uint32_t* __restrict__ base)
+{
+    __shared__ uint32_t s[257];
+    s[threadIdx.x] = tot[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int d = 0; d < 256; ++d) {
+            const uint32_t v = s[d];
+            s[d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    base[threadIdx.x] = s[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RB_THREADS) rb_scatter_kernel(const uint32_t* __restrict__ key_in,
+                                                                const uint32_t* __restrict__ val_in, uint64_t n,
+                                                                uint32_t shift, uint32_t n_tiles,
+                                                                const uint32_t* __restrict__ hist,
+                                                                const uint32_t* __restrict__ base,
+                                                                uint32_t* __restrict__ key_out,
+                                                                uint32_t* __restrict__ val_out)
+{
+    __shared__ uint32_t wc[RB_WARPS][256];       // per warp and digit: count, then offset in the tile
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (uint32_t k = threadIdx.x; k < RB_WARPS * 256; k += RB_THREADS) (&wc[0][0])[k] = 0;
+    __syncthreads();
+    const uint64_t w0 = (uint64_t)blockIdx.x * RB_TILE + (uint64_t)warp * RB_PER_WARP;
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint32_t off = 0; off < RB_PER_WARP; off += 32) {              // the warp's digit counts
+        const uint64_t i = w0 + off + lane;
+        const uint32_t d = i < n ? (key_in[i] >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (peers & lt) == 0) wc[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {                                                                    // warps in slot order
+        uint32_t run = 0;
+        for (uint32_t w = 0; w < RB_WARPS; ++w) {
+            const uint32_t c = wc[w][threadIdx.x];
+            wc[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t off = 0; off < RB_PER_WARP; off += 32) {              // stable places
+        const uint64_t i = w0 + off + lane;
+        const bool in = i < n;
+        const uint32_t kk = in ? key_in[i] : 0u;
+        const uint32_t d = in ? (kk >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (in) {
+            const uint32_t pos = base[d] + hist[(uint64_t)d * n_tiles + blockIdx.x] + wc[warp][d] + __popc(peers & lt);
+            key_out[pos] = kk;
+            val_out[pos] = val_in[i];
+        }
+        __syncwarp();
+        if (in && (peers & lt) == 0) wc[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// first[c] = exclusive prefix of count (one block); first[n_cell] = the live total
+__global__ void rb_first_kernel(const uint32_t* __restrict__ count, uint32_t n_cell, uint32_t* __restrict__ first)
+{
+    __shared__ uint32_t wt[40];
+    for (uint32_t c = threadIdx.x; c < n_cell; c += blockDim.x) first[c] = count[c];
+    __syncthreads();
+    block_exclusive_scan(first, n_cell, wt);
+}
+
+// sorted position p -> slot cs[c] + (p - first[c]) of the new cell c = key[p]; new arrays
+// pre-zeroed (dead slots)
+__global__ void rb_gather_kernel(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val, uint64_t n,
+                                 uint32_t n_cell,
+                                 const uint32_t* __restrict__ first, const uint32_t* __restrict__ cs,
+                                 const uint64_t* __restrict__ xi, const double* __restrict__ attr, uint64_t stride,
+                                 uint32_t n_attr, uint64_t* __restrict__ xi_new, double* __restrict__ attr_new)
+{
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = key[p], src = val[p];
+        if (c >= n_cell) continue;                           // dead slots sort last
+        const uint64_t dst = cs[c] + (p - first[c]);
+        xi_new[dst] = xi[src];
+        for (uint32_t r = 0; r < n_attr; ++r) attr_new[(uint64_t)r * stride + dst] = attr[(uint64_t)r * stride + src];
     }
 }
 

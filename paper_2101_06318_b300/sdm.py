@@ -30,7 +30,8 @@ STATUS = {0: "SDM_OK", 1: "SDM_EINVAL", 2: "SDM_ENOMEM", 3: "SDM_ECAPACITY", 4: 
 # every entry point declared in include/sdm.h
 EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", "sdm_init_state",
            "sdm_init_state_segmented", "sdm_set_state", "sdm_get_state", "sdm_coalescence_step",
-           "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_check_state", "sdm_get_schedule", "sdm_set_schedule",
+           "sdm_remove_zero", "sdm_spectrum", "sdm_totals", "sdm_check_state", "sdm_rebucket",
+           "sdm_get_schedule", "sdm_set_schedule",
            "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
            "sdm_launches_per_step", "sdm_coalescence_step_noalloc", "sdm_surrogate_create", "sdm_surrogate_free",
            "sdm_surrogate_train", "sdm_surrogate_build_mask", "sdm_surrogate_params_io", "sdm_surrogate_info",
@@ -99,6 +100,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_spectrum.argtypes = [vp, vp, u32, u32, vp, i32]
         L.sdm_totals.argtypes = [vp, vp, vp, vp]
         L.sdm_check_state.argtypes = [vp, vp, vp]
+        L.sdm_rebucket.argtypes = [vp, vp, i32]
         L.sdm_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.sdm_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.sdm_autotune.argtypes = [vp, C.POINTER(StepParams), u32, C.POINTER(Schedule)]
@@ -262,6 +264,15 @@ class State:
         n, m, live = C.c_uint64(), C.c_double(), C.c_uint64()
         _check(self._L.sdm_totals(self._h, C.byref(n), C.byref(m), C.byref(live)), "sdm_totals")
         return int(n.value), float(m.value), int(live.value)
+
+    def rebucket(self, cell_id):
+        """Move every live SD to the cell cell_id[slot] names (numpy uint32 on the host or a CUDA
+        int32/uint32 tensor); within a cell SDs keep their old slot order."""
+        if hasattr(cell_id, "data_ptr"):
+            _check(self._L.sdm_rebucket(self._h, C.c_void_p(cell_id.data_ptr()), 1), "sdm_rebucket")
+        else:
+            c = np.ascontiguousarray(cell_id, np.uint32)
+            _check(self._L.sdm_rebucket(self._h, c.ctypes.data_as(C.c_void_p), 0), "sdm_rebucket")
 
     def check(self):
         """Counts of slots breaking the state's invariants: (live-prefix rule, stale volume keys)."""

@@ -501,3 +501,73 @@ def test_autotune_keeps_results():
     o = _oracle_system(s)
     o.run(1.0, 2, 0, 6)
     _assert_bitexact(o, xa, aa)
+
+
+def _displacement_state(seed, n_cell, mean, spare, big=()):
+    """Cells with spare slots (capacity to receive SDs), a few large ones, small multiplicities."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(mean, n_cell)
+    for k, nbig in big:
+        counts[k] = nbig
+    width = counts + spare
+    n = int(width.sum())
+    cs = np.concatenate([[0], np.cumsum(width)]).astype(np.uint32)
+    xi = np.zeros(n, np.uint64)
+    for c in range(n_cell):
+        xi[cs[c]:cs[c] + counts[c]] = rng.integers(1, 50, counts[c])
+    v = inputs.lognormal_volumes(rng, n, 15e-6, 1.8)
+    kid = (np.arange(n_cell) % 2).astype(np.uint8)
+    return inputs._state(xi, v, width, 1e-13, kid, "displacement"), rng
+
+
+def test_rebucket_then_steps_bitexact():
+    """Displacement between steps (SDs moved to neighbouring or random cells, into the cells' spare
+    slots), then steps: the state equals the oracle's after each displacement and each leg of
+    steps, for small cells, tiles and large cells alike."""
+    s, rng = _displacement_state(31, 300, 60, 40, big=((7, 3000), (150, 1800), (299, 700)))
+    o = _oracle_system(s, None, "prp")
+    g = _gpu_state(s, None, dict(tile_slots=1024))
+    cs = s["cell_start"].astype(np.int64)
+    cell_of = np.repeat(np.arange(len(cs) - 1), np.diff(cs))
+    step = 0
+    for rnd in range(4):
+        xi_g, at_g, _ = g.get_state()
+        _assert_bitexact(o, xi_g, at_g)
+        live = np.flatnonzero(o.xi)
+        cid = cell_of.copy()
+        move = rng.random(len(live)) < 0.25
+        dst = cell_of[live] + rng.integers(-2, 3, len(live))
+        far = rng.random(len(live)) < 0.02
+        dst = np.where(far, rng.integers(0, len(cs) - 1, len(live)), dst)
+        cid[live[move]] = np.clip(dst[move], 0, len(cs) - 2)
+        # keep the capacities: drop moves into cells that would overflow (in slot order)
+        counts = np.bincount(cid[live], minlength=len(cs) - 1)
+        over = counts > np.diff(cs)
+        if over.any():
+            back = np.isin(cid[live], np.flatnonzero(over))
+            cid[live[back]] = cell_of[live[back]]
+        assert o.rebucket(cid)
+        g.rebucket(cid.astype(np.uint32))
+        xi_g, at_g, _ = g.get_state()
+        _assert_bitexact(o, xi_g, at_g)
+        assert g.check() == (0, 0)
+        o.run(s["dt"], 11, step, 6)
+        g.step(s["dt"], 11, step, 6, golovin_b=s["golovin_b"])
+        step += 6
+    xi_g, at_g, _ = g.get_state()
+    _assert_bitexact(o, xi_g, at_g)
+    g.close()
+
+
+def test_rebucket_rejects_overflow_and_bad_indices():
+    s, rng = _displacement_state(32, 40, 20, 2)
+    g = _gpu_state(s)
+    x0, a0, _ = g.get_state()
+    n = len(s["xi"])
+    with pytest.raises(sdm.SDMError):
+        g.rebucket(np.zeros(n, np.uint32))                  # everything into cell 0: over its width
+    with pytest.raises(sdm.SDMError):
+        g.rebucket(np.full(n, 40, np.uint32))               # no cell 40
+    x1, a1, _ = g.get_state()
+    assert np.array_equal(x0, x1) and np.array_equal(a0.view(np.uint64), a1.view(np.uint64))
+    g.close()
