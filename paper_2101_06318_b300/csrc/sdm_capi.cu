@@ -79,6 +79,8 @@ struct sdm_state {
     TileDesc* d_tiles = nullptr;
     uint32_t n_tiles = 0, max_cells_per_tile = 0;
     uint32_t* d_wcells = nullptr;            // cells of at most WC_MAX slots, one warp each
+    char* rb_buf = nullptr;                  // scratch of sdm_rebucket, kept between calls
+    size_t rb_bytes = 0;
     uint32_t n_wcells = 0, wc_grid = 0;
     TileLayout tile_L{};
     BigCell* d_big = nullptr;
@@ -874,6 +876,7 @@ void sdm_free(sdm_state* st)
     if (st->stream) cudaStreamSynchronize(st->stream);
     free_layout(st);
     for (auto& a : st->owned_fixed) cudaFree(a.p);
+    if (st->rb_buf) cudaFree(st->rb_buf);
     collect_profile(st);
     for (auto e : st->ev_pool) cudaEventDestroy(e);
     delete st;
@@ -1065,8 +1068,20 @@ sdm_status sdm_rebucket(sdm_state* st, const uint32_t* cell_id, int ptrs_on_devi
     // scratch: cid | key 2 | val 2 | count | first | hist | tot | base | err | xi_new | attr_new
     const size_t b_u32 = sizeof(uint32_t) * (5 * n + 2 * (size_t)st->n_cell + 1 + 256 * (size_t)n_tiles + 512 + 4);
     const size_t b_new = sizeof(uint64_t) * st->cap + sizeof(double) * st->cap * st->n_attr;
-    char* buf = nullptr;
-    SDM_CUDA(cudaMallocAsync((void**)&buf, b_new + b_u32 + 256, s));
+    if (st->rb_bytes < b_new + b_u32 + 256) {             // grown on demand, freed by sdm_free
+        if (st->rb_buf) {
+            SDM_CUDA(cudaStreamSynchronize(s));
+            cudaFree(st->rb_buf);
+            st->rb_buf = nullptr;
+            st->rb_bytes = 0;
+        }
+        if (cudaMalloc((void**)&st->rb_buf, b_new + b_u32 + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return SDM_ENOMEM;
+        }
+        st->rb_bytes = b_new + b_u32 + 256;
+    }
+    char* buf = st->rb_buf;
     uint64_t* xi_new = (uint64_t*)buf;
     double* attr_new = (double*)(buf + sizeof(uint64_t) * st->cap);
     uint32_t* u = (uint32_t*)(buf + b_new);
@@ -1082,7 +1097,7 @@ sdm_status sdm_rebucket(sdm_state* st, const uint32_t* cell_id, int ptrs_on_devi
     uint32_t* base = tot + 256;
     uint32_t* err = base + 256;
     sdm_status rs = SDM_OK;
-    auto fail = [&](sdm_status e) { cudaFreeAsync(buf, s); return e; };
+    auto fail = [&](sdm_status e) { return e; };
     if (cudaMemcpyAsync(cid, cell_id, sizeof(uint32_t) * n,
                         ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(count, 0, sizeof(uint32_t) * st->n_cell, s) != cudaSuccess ||
@@ -1123,7 +1138,6 @@ sdm_status sdm_rebucket(sdm_state* st, const uint32_t* cell_id, int ptrs_on_devi
         return fail(SDM_ECUDA);
     if (cudaGetLastError() != cudaSuccess) return fail(SDM_ECUDA);
     rs = refresh_big_bounds(st);                           // multiplicity bounds and volume bins
-    cudaFreeAsync(buf, s);
     return rs;
 }
 
