@@ -1631,11 +1631,17 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
 // after the table is staged), so the loads of one warp overlap the arithmetic
 // of the others.
 // ---------------------------------------------------------------------------
+constexpr uint32_t FQ_CAP = 64;    // finishing pass: queued pairs per warp (< 32 left + 32 new)
+struct FinQueue {                  // offsets of the pair's SDs in the cell, phi integer
+    uint32_t s1[FQ_CAP], s2[FQ_CAP];
+    unsigned long long u[FQ_CAP];
+};
+
 struct FinishLayout {
     uint32_t cap;          // records per bucket
     uint32_t nsub_max;     // sub-bucket counters per warp
     uint32_t warps;        // warps (buckets in flight) per CTA
-    uint32_t o_key, o_slot, o_off, o_cnt, o_tmp, o_srt, warp_bytes;   // per-warp region layout
+    uint32_t o_key, o_slot, o_off, o_cnt, o_tmp, o_srt, o_q, warp_bytes;   // per-warp region layout
     uint32_t o_tab, bytes;
 };
 
@@ -1651,6 +1657,7 @@ __host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max
     L.o_cnt = o; o = align_up(o + 4 * (L.nsub_max + 1), 16);
     L.o_tmp = o; o = align_up(o + 2 * cap, 16);
     L.o_srt = o; o = align_up(o + 2 * cap, 16);
+    L.o_q = o; o = align_up(o + (uint32_t)sizeof(FinQueue), 16);
     L.warp_bytes = o;
     L.o_tab = 0;
     const uint32_t tab = align_up((uint32_t)sizeof(EffTab), 16);
@@ -1752,43 +1759,76 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell], pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]),
                         a.dv[C.cell]};
     // pairs m whose first SD (cell position 2m) lies in this bucket: 2m in [S, S+k), 2m+1 < n;
-    // each lane takes two consecutive pairs (one Philox call)
+    // each lane takes two consecutive pairs (one Philox call).  Most pairs are settled by the
+    // early exit; the others are queued per warp and evaluated 32 at a time.
     const uint32_t m_lo = (S + 1) >> 1;
     const uint32_t m_hi = min((S + k - 1) >> 1, (n >> 1) - 1);      // inclusive
     if (m_lo > m_hi) return;
-    for (uint32_t M = (m_lo >> 1) + lane; M <= (m_hi >> 1); M += 32) {
+    const float c_up = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision);
+    const float* __restrict__ tb = g_pbound[cc.kid ? 1 : 0];
+    FinQueue& Q = *(FinQueue*)(ws + L.o_q);
+    uint32_t qcnt = 0;                                               // warp-uniform
+    auto drain = [&](uint32_t take) {
+        __syncwarp();
+        if (lane < take) {
+            const uint32_t q = qcnt - take + lane;
+            const uint64_t g1 = C.slot_begin + Q.s1[q], g2 = C.slot_begin + Q.s2[q];
+            process_pair<false>(a, tab, cc, Q.u[q], g1, g2, a.xi[g1], a.xi[g2], a.attr[g1], a.attr[g2], ls,
+                                &removed[big]);
+        }
+        __syncwarp();
+        qcnt -= take;
+    };
+    for (uint32_t Mb = m_lo >> 1; Mb <= (m_hi >> 1); Mb += 32) {    // warp-uniform trip count
+        const uint32_t M = Mb + lane;
         // gather both pairs' records first (one round trip), then the arithmetic
-        uint64_t sl[2][2], xg[2][2];
+        uint32_t sl[2][2];
+        uint64_t xg[2][2];
         double vg[2][2];
         bool ok[2];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t m = 2 * M + h;
-            ok[h] = m >= m_lo && m <= m_hi;
+            ok[h] = M <= (m_hi >> 1) && m >= m_lo && m <= m_hi;
             const uint32_t r = ok[h] ? 2 * m - S : 0u;
             const uint32_t i1 = srt[r];
             const bool last = r + 1 >= k;              // partner is the first SD of the next bucket
             const uint32_t i2 = last ? i1 : srt[r + 1];
-            sl[h][0] = C.slot_begin + slot[i1];
-            sl[h][1] = C.slot_begin + (last ? (uint32_t)nxt : slot[i2]);
+            sl[h][0] = slot[i1];
+            sl[h][1] = last ? (uint32_t)nxt : slot[i2];
             xg[h][0] = R[cap + i1];
             vg[h][0] = __longlong_as_double((long long)R[2 * cap + i1]);
             if (ok[h] && last) {
-                xg[h][1] = a.xi[sl[h][1]];
-                vg[h][1] = a.attr[sl[h][1]];
+                xg[h][1] = a.xi[C.slot_begin + sl[h][1]];
+                vg[h][1] = a.attr[C.slot_begin + sl[h][1]];
             } else {
                 xg[h][1] = R[cap + i2];
                 vg[h][1] = __longlong_as_double((long long)R[2 * cap + i2]);
             }
         }
-        uint64_t u[2];
-        phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
+        uint64_t u[2] = {0, 0};
+        if (M <= (m_hi >> 1)) phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
 #pragma unroll
-        for (uint32_t h = 0; h < 2; ++h)
-            if (ok[h])
-                process_pair<false>(a, tab, cc, u[h], sl[h][0], sl[h][1], xg[h][0], xg[h][1], vg[h][0], vg[h][1], ls,
-                             &removed[big]);
+        for (uint32_t h = 0; h < 2; ++h) {
+            bool need = false;
+            if (ok[h]) {
+                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(vbin_of(vg[h][0]), vbin_of(vg[h][1]))), c_up),
+                                            xi_pow2_above(xg[h][0], xg[h][1]));
+                need = !(pup <= phi_lo23((uint32_t)(u[h] >> 21)));
+                ls.pairs += need ? 0u : 1u;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, need);
+            if (need) {
+                const uint32_t q = qcnt + __popc(mk & ((1u << lane) - 1u));
+                Q.s1[q] = sl[h][0];
+                Q.s2[q] = sl[h][1];
+                Q.u[q] = u[h];
+            }
+            qcnt += __popc(mk);
+            if (qcnt >= 32) drain(32);
+        }
     }
+    if (qcnt > 0) drain(qcnt);
 }
 
 __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
