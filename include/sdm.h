@@ -132,7 +132,7 @@ typedef struct {
 typedef struct {
     uint32_t tile_slots;      /* max slots of the cells packed into one CTA (power of 2, 256..4096) */
     uint32_t tile_threads;    /* threads per tile CTA (64..512, multiple of 32) */
-    uint32_t bucket_target;   /* mean SDs per bucket in the large-cell sort (256..4096, power of 2) */
+    uint32_t bucket_target;   /* mean SDs per bucket in the large-cell sort (64..2048, power of 2) */
     uint32_t persistent;      /* 0: one CTA per tile; k > 0: k CTAs per SM pulling tiles */
 } sdm_schedule;
 
@@ -382,7 +382,7 @@ sdm_status sdm_attach_surrogate(sdm_state* st, const sdm_surrogate* s);
  * suit them, so this entry point performs one coalescence timestep of a single
  * box (one cell, cell index 0 of the random-number contract) directly on the
  * caller's device arrays, with all scratch memory taken from a fixed array
- * compiled into the library (about 13 MB of device memory, held by every GPU
+ * compiled into the library (about 5 MB of device memory, held by every GPU
  * that loads the library until the process exits).  It calls no allocating
  * routine.
  *

@@ -26,7 +26,20 @@ constexpr double RHO_WATER = 1000.0;
 constexpr double FOUR_PI_OVER_THREE = 4.18879020478639053;
 constexpr uint32_t ERR_INVALID = 1u << 8;
 constexpr uint32_t ERR_RANGE = 1u << 9;
-constexpr uint32_t FINISH_SMEM = 200 * 1024;   // dynamic shared memory budget of the finishing pass
+constexpr uint32_t FINISH_SMEM = 72 * 1024;    // dynamic shared memory of a finishing CTA, three per SM
+constexpr uint32_t FINISH_SMEM_WAVE = 110 * 1024;   // the same, two per SM (all buckets in one wave)
+constexpr uint32_t FINISH_SMEM_MAX = 200 * 1024;   // a single-warp CTA for very wide buckets
+constexpr uint32_t SCATTER_SMEM_MAX = 2 * sizeof(uint32_t) * (1u << BIG_MAX_BUCKET_BITS);
+constexpr uint32_t TILE_SMEM_MAX = 227 * 1024;
+
+// records a bucket holds: its mean count plus ten standard deviations of the count (a
+// binomial of mean m, standard deviation below sqrt(m)) plus 32; an overflow is reported
+// as SDM_ECAPACITY (for m = 256: probability below 1e-20 per bucket and step)
+uint32_t bucket_capacity(uint32_t mean)
+{
+    const uint32_t c = mean + (uint32_t)std::ceil(10.0 * std::sqrt((double)mean)) + 32;
+    return (c + 31) & ~31u;
+}
 
 struct DevAlloc {
     void* p;
@@ -90,16 +103,19 @@ struct sdm_state {
     uint32_t* d_bucket_big = nullptr;
     uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
     uint32_t* d_cursor = nullptr;            // [n_buckets] appends per bucket (zero between steps)
-    uint32_t* d_bstart = nullptr;            // [n_buckets + 1] bucket offsets of the current step
-    uint32_t* d_ticket = nullptr;            // [1] CTAs of the scatter pass that finished
+    uint32_t* d_bstart = nullptr;            // [n_buckets + n_big] per-cell bucket offsets of the current step
+    uint32_t* d_ticket = nullptr;            // [n_big] scatter CTAs of each large cell that finished
     uint64_t* d_scratch = nullptr;
     uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
     uint32_t n_quads = 0, prp_grid = 0;      // PRP contract: quads of all large cells, grid size
     uint32_t* d_cta_first = nullptr;         // [prp_grid] first large cell of each CTA (many large cells)
     unsigned long long* d_big_xmax = nullptr;   // [n_big] largest multiplicity of the cell
+    // a PRP step may have left large cells flagged for Step 0 since the last compaction;
+    // always assumed once a PRP step was captured into a graph (its replays are not seen here)
+    bool big_deferred = false, big_deferred_always = false;
     BigLaunch prp_launch{};
     FinishLayout fin_L{};
-    uint32_t fin_grid = 0, n_buckets_planned = 0;
+    uint32_t fin_grid = 0, n_buckets_planned = 0, fin_minb = 3;
 
     // host copies of the layout
     std::vector<uint32_t> h_cell_start;
@@ -137,6 +153,34 @@ sdm_status cuda_status(cudaError_t e)
         sdm_status s_ = (call);                          \
         if (s_ != SDM_OK) return s_;                     \
     } while (0)
+
+// Each kernel's opt-in shared memory limit is set to the largest any layout uses (the
+// setting is per function and process-wide; a launch uses what its own layout needs), so
+// states with different layouts and the allocation-free step never undercut each other.
+template <typename K>
+sdm_status set_dyn_smem_limit(K* kernel, uint32_t want)
+{
+    int dev = 0, optin = 0;
+    SDM_CUDA(cudaGetDevice(&dev));
+    SDM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    SDM_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int lim = std::min<int>((int)want, optin - (int)fa.sharedSizeBytes);   // static + dynamic <= opt-in
+    SDM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return SDM_OK;
+}
+
+sdm_status set_smem_limits()
+{
+    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<2>, FINISH_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<3>, FINISH_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(big_scatter_kernel, SCATTER_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(tile_step_kernel<false, 256>, TILE_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(tile_step_kernel<true, 256>, TILE_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(tile_step_kernel<false, 512>, TILE_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(tile_step_kernel<true, 512>, TILE_SMEM_MAX));
+    return SDM_OK;
+}
 
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -342,10 +386,12 @@ StepArgs state_args(const sdm_state* st)
 sdm_status flush_big_compaction(sdm_state* st)
 {
     if (!st->n_big || !st->d_big_removed) return SDM_OK;
+    if (!st->big_deferred && !st->big_deferred_always) return SDM_OK;   // no PRP step since the last one
     const BigBook bb = big_book(st);
     big_compact_kernel<<<std::max<uint32_t>(1, std::min<uint32_t>(st->n_big, (uint32_t)std::max(st->n_sm, 1))), 256,
                          0, st->stream>>>(state_args(st), st->d_big, bb.removed, st->n_big, bb.sync);
     SDM_CUDA(cudaGetLastError());
+    st->big_deferred = false;
     return SDM_OK;
 }
 
@@ -389,10 +435,11 @@ sdm_status build_layout(sdm_state* st)
             const uint32_t nb = 1u << nbits;
             for (uint32_t k = 0; k < nb; ++k) bucket_big.push_back((uint32_t)bigs.size());
             const uint32_t mean = (w + nb - 1) / nb;
-            bucket_cap = std::max(bucket_cap, 2 * mean + 64);
+            bucket_cap = std::max(bucket_cap, bucket_capacity(mean));
             max_nb = std::max(max_nb, nb);
+            const uint32_t n_of_cell = (w + BIG_CHUNK - 1) / BIG_CHUNK;
             for (uint32_t l = 0; l < w; l += BIG_CHUNK)
-                chunks.push_back(BigChunk{(uint32_t)bigs.size(), l, std::min(w, l + BIG_CHUNK), 0});
+                chunks.push_back(BigChunk{(uint32_t)bigs.size(), l, std::min(w, l + BIG_CHUNK), n_of_cell});
             b.quad_begin = n_quads;
             n_quads += (w / 2 + 1) / 2;                       // quads at full occupancy
             bigs.push_back(b);
@@ -412,18 +459,29 @@ sdm_status build_layout(sdm_state* st)
     bucket_cap = (bucket_cap + 31) & ~31u;
     st->n_buckets_planned = (uint32_t)bucket_big.size();
     if (!bigs.empty()) {
-        const FinishLayout fl = finish_layout(bucket_cap, FINISH_SMEM);
-        if (fl.bytes > FINISH_SMEM) return SDM_ECAPACITY;   // a cell too large for this bucket width
+        SDM_TRY(set_smem_limits());
+        // two CTAs per SM (more registers: a shorter latency per bucket) unless three CTAs per SM
+        // (more warps in flight) take fewer rounds of buckets per warp
+        const uint32_t nbk = st->n_buckets_planned;
+        const FinishLayout f2 = finish_layout(bucket_cap, FINISH_SMEM_WAVE);
+        const FinishLayout f3 = finish_layout(bucket_cap, FINISH_SMEM);
+        int per2 = 0, per3 = 0;
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, big_finish_kernel<2>, 32 * f2.warps, f2.bytes));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, big_finish_kernel<3>, 32 * f3.warps, f3.bytes));
+        const uint64_t w2 = (uint64_t)std::max(per2, 1) * st->n_sm * f2.warps;
+        const uint64_t w3 = (uint64_t)std::max(per3, 1) * st->n_sm * f3.warps;
+        const bool three = (nbk + w3 - 1) / w3 < (nbk + w2 - 1) / w2;
+        const FinishLayout fl = three ? f3 : f2;
+        const int per_sm = three ? per3 : per2;
+        st->fin_minb = three ? 3 : 2;
+        if (fl.bytes > FINISH_SMEM_MAX) return SDM_ECAPACITY;   // a cell too large for this bucket width
         st->fin_L = fl;
-        int per_sm = 0;
-        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_finish_kernel, 32 * fl.warps, fl.bytes));
-        const uint32_t need = (st->n_buckets_planned + fl.warps - 1) / fl.warps;
+        const uint32_t need = (nbk + fl.warps - 1) / fl.warps;
         st->fin_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
     }
     st->tile_L = tile_layout(S.tile_slots, max_cells, S.tile_threads / 32);
     st->max_cells_per_tile = max_cells;
-    if (st->tile_L.bytes > 227 * 1024) return SDM_ECAPACITY;
+    if (st->tile_L.bytes > TILE_SMEM_MAX) return SDM_ECAPACITY;
     SDM_TRY(upload(st, &st->d_tiles, tiles));
     SDM_TRY(upload(st, &st->d_wcells, wcells));
     st->n_wcells = (uint32_t)wcells.size();
@@ -452,6 +510,7 @@ sdm_status build_layout(sdm_state* st)
         SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * words, true));
         SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * words, st->stream));
     }
+    st->big_deferred = false;
     st->n_tiles = (uint32_t)tiles.size();
     st->n_big = (uint32_t)bigs.size();
     if (!bigs.empty())
@@ -463,25 +522,17 @@ sdm_status build_layout(sdm_state* st)
     st->bucket_cap = bucket_cap;
     st->max_nb = max_nb;
     if (st->n_buckets) {
-        // cursors (n_buckets), the ticket, then the offsets (n_buckets + 1), all zeroed once here;
-        // afterwards the scatter pass leaves cursors and ticket at zero at the end of every step
-        const size_t words = 2 * (size_t)st->n_buckets + 2;
+        // cursors (n_buckets), the per-cell tickets (n_big), then the per-cell offsets
+        // (n_buckets + n_big), all zeroed once here; afterwards the scatter pass leaves cursors
+        // and tickets at zero at the end of every step
+        const size_t words = 2 * (size_t)st->n_buckets + 2 * (size_t)st->n_big;
         SDM_TRY(dev_alloc(st, (void**)&st->d_cursor, sizeof(uint32_t) * words, true));
         SDM_CUDA(cudaMemsetAsync(st->d_cursor, 0, sizeof(uint32_t) * words, st->stream));
         st->d_ticket = st->d_cursor + st->n_buckets;
-        st->d_bstart = st->d_ticket + 1;
-        SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, 3 * sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
-        const uint32_t scatter_smem = sizeof(uint32_t) * 2 * max_nb;
-        SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
+        st->d_bstart = st->d_ticket + st->n_big;
+        SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
     }
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  st->tile_L.bytes));
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  st->tile_L.bytes));
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  st->tile_L.bytes));
-    SDM_CUDA(cudaFuncSetAttribute(tile_step_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  st->tile_L.bytes));
+    SDM_TRY(set_smem_limits());
     SDM_CUDA(cudaStreamSynchronize(st->stream));
     return SDM_OK;
 }
@@ -753,6 +804,10 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             // cooperative: a step that finds cells flagged by the previous one compacts them first,
             // behind a grid barrier (every block resident)
             ProfScope ps(st, 3);
+            st->big_deferred = true;
+            cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+            SDM_CUDA(cudaStreamIsCapturing(st->stream, &cap_status));
+            if (cap_status != cudaStreamCaptureStatusNone) st->big_deferred_always = true;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(st->prp_grid);
             cfg.blockDim = dim3(PRP_THREADS);
@@ -777,8 +832,10 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             }
             {
                 ProfScope ps(st, 2);
-                big_finish_kernel<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->fin_L, bb);
+                auto fk = st->fin_minb == 2 ? big_finish_kernel<2> : big_finish_kernel<3>;
+                fk<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
+                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->d_big_xmax,
+                    st->fin_L, bb);
             }
         }
         if (p->d_step) advance_step_kernel<<<1, 32, 0, st->stream>>>(p->d_step, 1u);
@@ -821,8 +878,8 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
-    b += round256(4 * max_buckets + 256) + round256(8 * max_buckets + 256);
-    b += round256(3 * 8 * max_buckets * max_cap + 256);
+    b += round256(4 * max_buckets + 256) + round256(16 * max_buckets + 256);
+    b += round256(8 * max_buckets * max_cap + 256);
     return b;
 }
 
@@ -953,6 +1010,7 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
     if (st->d_big_removed)    // the new state is compact: no large cell awaits compaction
         SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (big_ticket_word(st->n_big) + 2 + 4),
                                  st->stream));
+    st->big_deferred = false;
     const uint32_t cgrid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm));
     live_count_kernel<<<cgrid, 256, 0, st->stream>>>(st->d_xi, st->d_cell_start, st->n_cell, st->d_n_live);
     SDM_CUDA(cudaGetLastError());
@@ -1372,7 +1430,7 @@ namespace {
 
 constexpr uint32_t NA_TARGET_BITS = 8;                                    // 256 SDs per bucket on average
 constexpr uint32_t NA_MAX_BUCKETS = SDM_NOALLOC_MAX_SD >> NA_TARGET_BITS; // 1024
-constexpr uint32_t NA_MAX_CAP = 2 * (1u << NA_TARGET_BITS) + 64;          // 576 records per bucket
+constexpr uint32_t NA_MAX_CAP = 448;     // bucket_capacity(256): mean 256 + 160 + 32 records
 constexpr uint32_t NA_MAX_CHUNKS = (SDM_NOALLOC_MAX_SD + BIG_CHUNK - 1) / BIG_CHUNK;
 // byte offsets inside the scratch array
 constexpr size_t NA_OFF_CELL = 0;        // BigCell
@@ -1386,7 +1444,7 @@ constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
 constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
 constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
 constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
-constexpr size_t NA_BYTES = NA_OFF_RECORDS + 3 * sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
+constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
 
 // one per loaded library and device; its contents persist between calls
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -1406,10 +1464,7 @@ sdm_status noalloc_scratch(unsigned char** out)
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) return SDM_ECUDA;
-        const FinishLayout fl = finish_layout(NA_MAX_CAP, FINISH_SMEM);
-        const uint32_t scatter_smem = sizeof(uint32_t) * 2 * NA_MAX_BUCKETS;
-        SDM_CUDA(cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scatter_smem));
-        SDM_CUDA(cudaFuncSetAttribute(big_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fl.bytes));
+        SDM_TRY(set_smem_limits());
         SDM_TRY(ensure_device_tables());
         g_na_ptr[dev] = (unsigned char*)p;
     }
@@ -1443,10 +1498,13 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     C.nbits = ceil_log2_h(n_sd) > NA_TARGET_BITS ? ceil_log2_h(n_sd) - NA_TARGET_BITS : 0;
     C.bucket_base = 0;
     const uint32_t nb = 1u << C.nbits;
-    const uint32_t cap = ((2 * ((n_sd + nb - 1) / nb) + 64) + 31) & ~31u;
+    const uint32_t cap = bucket_capacity((n_sd + nb - 1) / nb);
+    if (cap > NA_MAX_CAP) return SDM_ECAPACITY;      // not reached: at most 256 SDs per bucket on average
     BigChunk chunks[NA_MAX_CHUNKS];
     uint32_t n_chunks = 0;
-    for (uint32_t l = 0; l < n_sd; l += BIG_CHUNK) chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), 0};
+    const uint32_t n_of_cell = (n_sd + BIG_CHUNK - 1) / BIG_CHUNK;
+    for (uint32_t l = 0; l < n_sd; l += BIG_CHUNK)
+        chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), n_of_cell};
     C.quad_begin = 0;
     const uint32_t n_quads = (n_sd / 2 + 1) / 2;
     uint32_t bucket_big[NA_MAX_BUCKETS] = {};
@@ -1465,12 +1523,10 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
     uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
-    unsigned long long* d_xmax = (unsigned long long*)(base + NA_OFF_XMAX);
-    if (p->shuffle == SDM_SHUFFLE_PRP) {
-        SDM_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned long long), stream));
-        big_xmax_kernel<<<n_chunks, 256, 0, stream>>>(xi, attr, nullptr, (const BigCell*)(base + NA_OFF_CELL),
-                                                      (const BigChunk*)(base + NA_OFF_CHUNKS), d_xmax);
-    }
+    unsigned long long* d_xmax = (unsigned long long*)(base + NA_OFF_XMAX);      // the early exit's bound
+    SDM_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned long long), stream));
+    big_xmax_kernel<<<n_chunks, 256, 0, stream>>>(xi, attr, nullptr, (const BigCell*)(base + NA_OFF_CELL),
+                                                  (const BigChunk*)(base + NA_OFF_CHUNKS), d_xmax);
 
     StepArgs a{};
     a.xi = xi;
@@ -1508,12 +1564,12 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
         const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
         uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
-        const FinishLayout fl = finish_layout(cap, FINISH_SMEM);
+        const FinishLayout fl = finish_layout(cap, FINISH_SMEM_WAVE);   // at most 1024 buckets: one wave
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
         big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
             a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
-        big_finish_kernel<<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
-            a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, fl, bb);
+        big_finish_kernel<2><<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
+            a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb);
     }
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());

@@ -69,7 +69,7 @@ __device__ __forceinline__ bool sorts(const StepArgs& a, uint32_t n)
 
 struct TileDesc { uint32_t slot_begin, slot_end, cell_begin, n_cells; };
 struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, quad_begin; };   // quad_begin: PRP contract
-struct BigChunk { uint32_t big, l_begin, l_end, pad; };
+struct BigChunk { uint32_t big, l_begin, l_end, n_of_cell; };   // n_of_cell: chunks of the same cell
 
 __device__ __forceinline__ uint32_t step_index(const StepArgs& a)
 {
@@ -1508,18 +1508,21 @@ __global__ void __launch_bounds__(256) big_compact_kernel(StepArgs a, const BigC
 }
 
 // ---------------------------------------------------------------------------
-// Large cells, pass 1: scatter (key, slot) into fixed-capacity buckets.
+// Large cells, pass 1: scatter (key, position) into fixed-capacity buckets.
 // ---------------------------------------------------------------------------
 constexpr uint32_t BIG_CHUNK = 2048;          // slots per scatter CTA (multiple of 4)
 constexpr uint32_t BIG_SCATTER_THREADS = 256;
 constexpr uint32_t BIG_GROUPS_PER_THREAD = BIG_CHUNK / 4 / BIG_SCATTER_THREADS;
 constexpr uint32_t BIG_MAX_BUCKET_BITS = 13;  // <= 8192 buckets per cell
+constexpr uint32_t BIG_ATOMIC_ILP = 4;        // bucket reservations in flight per thread
 
 // Bucket bookkeeping shared by the two passes.
-//   cursor[b]  records appended to bucket b in this step (zero between steps)
-//   bstart[b]  exclusive prefix of the (capacity-clamped) counts over all
-//              buckets, bstart[n_buckets] = total; written by the last CTA of
-//              pass 1, which also clears cursor[] and the ticket.
+//   cursor[g]        records appended to bucket g in this step (zero between steps)
+//   ticket[c]        scatter CTAs of large cell c that finished (zero between steps)
+//   bstart[g + c]    for bucket g of large cell c: exclusive prefix of the cell's
+//                    (capacity-clamped) bucket counts; bstart[base_c + c + nb_c] is the
+//                    cell's total.  Written by the last scatter CTA of the cell, which
+//                    also clears the cell's cursors and ticket.
 struct BucketBook {
     uint32_t* cursor;
     uint32_t* bstart;
@@ -1528,11 +1531,68 @@ struct BucketBook {
     uint32_t cap;
 };
 
-// Records of bucket b (capacity cap) live at rec + b * 3 * cap:
-//   [0, cap)      (key << 32) | local slot
-//   [cap, 2cap)   multiplicity xi
-//   [2cap, 3cap)  volume v (bits)
-// so that the finishing pass reads its bucket contiguously and never gathers.
+// The last scatter CTA of a cell: offsets of its nb buckets (nb a power of two, at most
+// 8192; blockDim.x == BIG_SCATTER_THREADS).  Each thread takes nb / 256 consecutive
+// buckets (at least one), loading them eight at a time with all eight loads in flight
+// (so 4096 buckets cost two round trips to L2), staging the clamped counts in
+// shared memory tmp[nb]; then a block scan of the thread sums.
+__device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __restrict__ out, uint32_t nb,
+                                    uint32_t cap, uint32_t* tmp, uint32_t* wt, uint32_t* err)
+{
+    constexpr uint32_t BATCH = 8;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t per = nb > BIG_SCATTER_THREADS ? nb / BIG_SCATTER_THREADS : 1u;
+    const uint32_t b0 = tid * per, b1 = min(nb, b0 + per);
+    uint32_t over = 0, s = 0;
+    for (uint32_t j0 = b0; j0 < b1; j0 += BATCH) {
+        uint32_t v[BATCH];
+#pragma unroll
+        for (uint32_t j = 0; j < BATCH; ++j) v[j] = j0 + j < b1 ? __ldcg(&cursor[j0 + j]) : 0u;
+#pragma unroll
+        for (uint32_t j = 0; j < BATCH; ++j) {
+            if (j0 + j < b1) {
+                cursor[j0 + j] = 0u;
+                over |= v[j] > cap;
+                tmp[j0 + j] = min(v[j], cap);
+                s += min(v[j], cap);
+            }
+        }
+    }
+    if (over) atomicOr(err, ERR_BUCKET_OVERFLOW);
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) wt[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t nw = BIG_SCATTER_THREADS / 32;
+        const uint32_t w = lane < nw ? wt[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (uint32_t)o) wi += t;
+        }
+        if (lane < nw) wt[lane] = wi - w;
+        if (lane == 31) out[nb] = wi;                 // the cell's total
+    }
+    __syncthreads();
+    uint32_t run = wt[wid] + inc - s;
+    for (uint32_t j = b0; j < b1; ++j) {
+        const uint32_t c = tmp[j];
+        out[j] = run;
+        run += c;
+    }
+}
+
+// Records of bucket b (capacity cap) live at rec + b * cap, one 8-byte word
+// each: (key << 32) | position in the cell's live list.  The live SDs of a cell
+// are the prefix [0, n_live) of its slots (Step 0 ran before), so the pass reads
+// no SD data at all: the keys come from the counter-based generator, the bucket
+// is the key's top bits.  The finishing pass gathers what it needs per pair.
 __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepArgs a, const BigCell* __restrict__ cells,
                                                                          const BigChunk* __restrict__ chunks,
                                                                          uint64_t* __restrict__ rec, BucketBook bk)
@@ -1547,42 +1607,39 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
     uint32_t* base = hist + nb;                    // nb
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t step = step_index(a);
-
-    // multiplicities and volumes of this thread's groups first (one memory round trip)
-    uint64_t xv[BIG_GROUPS_PER_THREAD][4];
-    double vv[BIG_GROUPS_PER_THREAD][4];
-#pragma unroll
-    for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
-        const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const bool in = l0 + k < ch.l_end;
-            xv[q][k] = in ? a.xi[C.slot_begin + l0 + k] : 0ull;
-            vv[q][k] = in ? a.attr[C.slot_begin + l0 + k] : 0.0;
-        }
-    }
+    const uint32_t l_end = min(ch.l_end, min(__ldcg(&a.n_live[C.cell]), C.width));
     for (uint32_t b = tid; b < nb; b += nt) hist[b] = 0;
     __syncthreads();
-    uint32_t kb[BIG_GROUPS_PER_THREAD][4];        // key, then bucket << 16 | offset
+    uint32_t kb[BIG_GROUPS_PER_THREAD][4];        // bucket << 16 | arrival index in the bucket
     uint32_t keys[BIG_GROUPS_PER_THREAD][4];
 #pragma unroll
     for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
         const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
-        const U4 x = philox(l0 >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi);
+        U4 x = {0, 0, 0, 0};
+        if (l0 < l_end) x = philox(l0 >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi);
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             keys[q][k] = u4_word(x, k);
             kb[q][k] = DEAD;
-            if (l0 + k < ch.l_end && xv[q][k] != 0) {
+            if (l0 + k < l_end) {
                 const uint32_t b = C.nbits ? keys[q][k] >> (32u - C.nbits) : 0u;
                 kb[q][k] = (b << 16) | atomicAdd(&hist[b], 1u);
             }
         }
     }
     __syncthreads();
-    for (uint32_t b = tid; b < nb; b += nt) {
-        const uint32_t h = hist[b];
-        if (h) base[b] = atomicAdd(&bk.cursor[C.bucket_base + b], h);
+    // reserve each bucket's run with one global atomic, several in flight per thread
+    for (uint32_t b0 = tid; b0 < nb; b0 += BIG_ATOMIC_ILP * nt) {
+        uint32_t r[BIG_ATOMIC_ILP];
+#pragma unroll
+        for (uint32_t j = 0; j < BIG_ATOMIC_ILP; ++j) {
+            const uint32_t b = b0 + j * nt;
+            const uint32_t h = b < nb ? hist[b] : 0u;
+            r[j] = h ? atomicAdd(&bk.cursor[C.bucket_base + b], h) : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < BIG_ATOMIC_ILP; ++j)
+            if (b0 + j * nt < nb) base[b0 + j * nt] = r[j];
     }
     __syncthreads();
 #pragma unroll
@@ -1594,35 +1651,22 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
             if (bo == DEAD) continue;
             const uint32_t b = bo >> 16;
             const uint32_t pos = base[b] + (bo & 0xffffu);
-            if (pos < bk.cap) {
-                uint64_t* r = rec + (uint64_t)(C.bucket_base + b) * 3 * bk.cap + pos;
-                r[0] = (((uint64_t)keys[q][k]) << 32) | (uint64_t)(l0 + k);
-                r[bk.cap] = xv[q][k];
-                r[2 * bk.cap] = (uint64_t)__double_as_longlong(vv[q][k]);
-            }
+            if (pos < bk.cap)
+                rec[(uint64_t)(C.bucket_base + b) * bk.cap + pos] = (((uint64_t)keys[q][k]) << 32) | (uint64_t)(l0 + k);
         }
     }
-    // the last CTA to finish turns the bucket counts into offsets and clears them (the
-    // cursor atomics above returned, so they are complete before the ticket is taken)
+    // the cell's last CTA to finish turns its bucket counts into offsets and clears them
+    // (the cursor atomics above returned, so they are complete before the ticket is taken)
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        s_last = (atomicAdd(bk.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+        s_last = (atomicAdd(&bk.ticket[ch.big], 1u) == ch.n_of_cell - 1) ? 1u : 0u;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    uint32_t over = 0;
-    for (uint32_t b = tid; b < bk.n_buckets; b += nt) {
-        const uint32_t c = *(volatile uint32_t*)&bk.cursor[b];
-        over |= c > bk.cap;
-        bk.bstart[b] = min(c, bk.cap);
-        bk.cursor[b] = 0;
-    }
-    if (over) atomicOr(a.err, ERR_BUCKET_OVERFLOW);
-    __syncthreads();
-    block_exclusive_scan(bk.bstart, bk.n_buckets, wt);
-    if (tid == 0) *bk.ticket = 0;
+    cell_bucket_offsets(bk.cursor + C.bucket_base, bk.bstart + C.bucket_base + ch.big, nb, bk.cap, hist, wt, a.err);
+    if (tid == 0) bk.ticket[ch.big] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1632,7 +1676,7 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
 // of the others.
 // ---------------------------------------------------------------------------
 constexpr uint32_t FQ_CAP = 64;    // finishing pass: queued pairs per warp (< 32 left + 32 new)
-struct FinQueue {                  // offsets of the pair's SDs in the cell, phi integer
+struct FinQueue {                  // slots of the pair's SDs, phi integer
     uint32_t s1[FQ_CAP], s2[FQ_CAP];
     unsigned long long u[FQ_CAP];
 };
@@ -1679,12 +1723,30 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 }
 
 
+// Evaluate the top 'take' queued pairs of a finishing warp (lanes < take) and pop them;
+// the queue holds global slots, all of the cell whose context is cc.
+__device__ __forceinline__ void fin_drain(const StepArgs& a, const EffTab* __restrict__ tab, FinQueue& Q,
+                                          uint32_t& qcnt, uint32_t take, const CellCtx& cc, uint32_t* rflag,
+                                          LocalStats& ls, uint32_t lane)
+{
+    __syncwarp();
+    if (lane < take) {
+        const uint32_t q = qcnt - take + lane;
+        const uint64_t g1 = Q.s1[q], g2 = Q.s2[q];
+        process_pair<false>(a, tab, cc, Q.u[q], g1, g2, a.xi[g1], a.xi[g2], a.attr[g1], a.attr[g2], ls, rflag);
+    }
+    __syncwarp();
+    qcnt -= take;
+}
+
 __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
                                               const BigCell* __restrict__ cells,
                                               const uint32_t* __restrict__ bucket_big,
                                               const uint64_t* __restrict__ rec, const uint32_t* __restrict__ bstart,
-                                              const FinishLayout& L, unsigned char* ws, uint32_t g, uint32_t lane,
-                                              uint32_t step, LocalStats& ls, uint32_t* removed)
+                                              const unsigned long long* __restrict__ xmax, const FinishLayout& L,
+                                              unsigned char* ws, uint32_t g, uint32_t lane, uint32_t step,
+                                              LocalStats& ls, uint32_t* removed, FinQueue& Q, uint32_t& qcnt,
+                                              CellCtx& qcc, uint32_t& qbig)
 {
     uint32_t* key = (uint32_t*)(ws + L.o_key);
     uint32_t* slot = (uint32_t*)(ws + L.o_slot);
@@ -1697,11 +1759,13 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const BigCell C = cells[big];
     const uint32_t nb = 1u << C.nbits;
     // where this bucket starts in the cell's sorted list, its size, the cell's live count
-    const uint32_t b0 = bstart[C.bucket_base];
-    const uint32_t S = bstart[g] - b0;
-    const uint32_t k = bstart[g + 1] - bstart[g];
-    const uint32_t n = bstart[C.bucket_base + nb] - b0;
-    const uint64_t* R = rec + (uint64_t)g * 3 * cap;
+    // (the cell's offsets: bstart[bucket + cell index], its total after its last bucket)
+    const uint32_t* __restrict__ off_c = bstart + C.bucket_base + big;    // [nb + 1]
+    const uint32_t gl = g - C.bucket_base;                                 // bucket in the cell
+    const uint32_t S = off_c[gl];
+    const uint32_t k = off_c[gl + 1] - S;
+    const uint32_t n = off_c[nb];
+    const uint64_t* R = rec + (uint64_t)g * cap;
     for (uint32_t i = lane; i < k; i += 32) {
         const uint64_t e = R[i];
         key[i] = (uint32_t)(e >> 32);
@@ -1741,12 +1805,12 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     // the partner of this bucket's last SD may be the first SD of the next non-empty bucket
     unsigned long long nxt = ~0ull;
     if (((S + k) & 1u) && (S + k < n)) {
-        uint32_t b2 = g - C.bucket_base + 1;
-        while (b2 < nb && bstart[C.bucket_base + b2 + 1] == bstart[C.bucket_base + b2]) ++b2;
+        uint32_t b2 = gl + 1;
+        while (b2 < nb && off_c[b2 + 1] == off_c[b2]) ++b2;
         if (b2 < nb) {
             const uint32_t g2 = C.bucket_base + b2;
-            const uint32_t k2 = bstart[g2 + 1] - bstart[g2];
-            const uint64_t* R2 = rec + (uint64_t)g2 * 3 * cap;
+            const uint32_t k2 = off_c[b2 + 1] - off_c[b2];
+            const uint64_t* R2 = rec + (uint64_t)g2 * cap;
             for (uint32_t i = lane; i < k2; i += 32) {
                 const unsigned long long e = R2[i];
                 nxt = e < nxt ? e : nxt;
@@ -1759,51 +1823,40 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell], pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]),
                         a.dv[C.cell]};
     // pairs m whose first SD (cell position 2m) lies in this bucket: 2m in [S, S+k), 2m+1 < n;
-    // each lane takes two consecutive pairs (one Philox call).  Most pairs are settled by the
-    // early exit; the others are queued per warp and evaluated 32 at a time.
+    // each lane takes two consecutive pairs (one Philox call).  The early exit needs the two
+    // volumes' bins (one byte each from the bin array, else the volume's high word) and the
+    // cell's multiplicity bound; the pairs it does not settle are queued per warp and
+    // evaluated 32 at a time.
     const uint32_t m_lo = (S + 1) >> 1;
     const uint32_t m_hi = min((S + k - 1) >> 1, (n >> 1) - 1);      // inclusive
     if (m_lo > m_hi) return;
-    const float c_up = exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision);
+    const float c_upx = __fmul_ru(exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision),
+                                  __ull2float_ru(xmax[big]));
     const float* __restrict__ tb = g_pbound[cc.kid ? 1 : 0];
-    FinQueue& Q = *(FinQueue*)(ws + L.o_q);
-    uint32_t qcnt = 0;                                               // warp-uniform
-    auto drain = [&](uint32_t take) {
-        __syncwarp();
-        if (lane < take) {
-            const uint32_t q = qcnt - take + lane;
-            const uint64_t g1 = C.slot_begin + Q.s1[q], g2 = C.slot_begin + Q.s2[q];
-            process_pair<false>(a, tab, cc, Q.u[q], g1, g2, a.xi[g1], a.xi[g2], a.attr[g1], a.attr[g2], ls,
-                                &removed[big]);
-        }
-        __syncwarp();
-        qcnt -= take;
-    };
+    const uint8_t* __restrict__ vbin = a.vbin;
+    const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
+    // the warp's queue carries over from bucket to bucket of one cell (fewer, fuller drains)
+    if (qcnt > 0 && qbig != big) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &removed[qbig], ls, lane);
+    qcc = cc;
+    qbig = big;
     for (uint32_t Mb = m_lo >> 1; Mb <= (m_hi >> 1); Mb += 32) {    // warp-uniform trip count
         const uint32_t M = Mb + lane;
-        // gather both pairs' records first (one round trip), then the arithmetic
-        uint32_t sl[2][2];
-        uint64_t xg[2][2];
-        double vg[2][2];
+        // the four slots and their bins first (one round trip), then the arithmetic
+        uint32_t sl[2][2], kv[2][2];
         bool ok[2];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t m = 2 * M + h;
             ok[h] = M <= (m_hi >> 1) && m >= m_lo && m <= m_hi;
             const uint32_t r = ok[h] ? 2 * m - S : 0u;
-            const uint32_t i1 = srt[r];
             const bool last = r + 1 >= k;              // partner is the first SD of the next bucket
-            const uint32_t i2 = last ? i1 : srt[r + 1];
+            const uint32_t i1 = srt[r], i2 = srt[last ? r : r + 1];
             sl[h][0] = slot[i1];
             sl[h][1] = last ? (uint32_t)nxt : slot[i2];
-            xg[h][0] = R[cap + i1];
-            vg[h][0] = __longlong_as_double((long long)R[2 * cap + i1]);
-            if (ok[h] && last) {
-                xg[h][1] = a.xi[C.slot_begin + sl[h][1]];
-                vg[h][1] = a.attr[C.slot_begin + sl[h][1]];
-            } else {
-                xg[h][1] = R[cap + i2];
-                vg[h][1] = __longlong_as_double((long long)R[2 * cap + i2]);
+#pragma unroll
+            for (uint32_t j = 0; j < 2; ++j) {
+                const uint64_t e = C.slot_begin + sl[h][j];
+                kv[h][j] = !ok[h] ? 0u : vbin ? (uint32_t)vbin[e] : pb_bin_key(attr_hi[2 * e] >> 18);
             }
         }
         uint64_t u[2] = {0, 0};
@@ -1812,29 +1865,30 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
         for (uint32_t h = 0; h < 2; ++h) {
             bool need = false;
             if (ok[h]) {
-                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(vbin_of(vg[h][0]), vbin_of(vg[h][1]))), c_up),
-                                            xi_pow2_above(xg[h][0], xg[h][1]));
-                need = !(pup <= phi_lo23((uint32_t)(u[h] >> 21)));
+                need = !(__fmul_ru(__ldg(tb + pb_index(kv[h][0], kv[h][1])), c_upx) <= phi_lo23((uint32_t)(u[h] >> 21)));
                 ls.pairs += need ? 0u : 1u;
             }
             const unsigned mk = __ballot_sync(0xffffffffu, need);
             if (need) {
                 const uint32_t q = qcnt + __popc(mk & ((1u << lane) - 1u));
-                Q.s1[q] = sl[h][0];
-                Q.s2[q] = sl[h][1];
+                Q.s1[q] = C.slot_begin + sl[h][0];
+                Q.s2[q] = C.slot_begin + sl[h][1];
                 Q.u[q] = u[h];
             }
             qcnt += __popc(mk);
-            if (qcnt >= 32) drain(32);
+            if (qcnt >= 32) fin_drain(a, tab, Q, qcnt, 32, cc, &removed[big], ls, lane);
         }
     }
-    if (qcnt > 0) drain(qcnt);
 }
 
-__global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
+// MINB: CTAs per SM the registers are sized for -- 2 when all buckets fit one wave of warps
+// (each bucket's latency is what counts), 3 when the warps take several buckets each.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
                                                          const uint32_t* __restrict__ bucket_big,
                                                          const uint64_t* __restrict__ rec,
                                                          const uint32_t* __restrict__ bstart, uint32_t n_buckets,
+                                                         const unsigned long long* __restrict__ xmax,
                                                          FinishLayout L, BigBook bb)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1848,8 +1902,13 @@ __global__ void __launch_bounds__(256) big_finish_kernel(StepArgs a, const BigCe
     load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;
     __syncthreads();
+    FinQueue& Q = *(FinQueue*)(ws + L.o_q);
+    uint32_t qcnt = 0, qbig = 0;                   // warp-uniform
+    CellCtx qcc{};
     for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
-        finish_bucket(a, tab, cells, bucket_big, rec, bstart, L, ws, g, lane, step, ls, bb.removed);
+        finish_bucket(a, tab, cells, bucket_big, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q, qcnt,
+                      qcc, qbig);
+    if (qcnt > 0) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &bb.removed[qbig], ls, lane);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);

@@ -221,6 +221,16 @@ def test_gravitational_box_full_size_bitexact(shuffle):
     assert gst["n_fp64"] < 1e-3 * gst["n_pairs"]
 
 
+def test_sort_contract_many_bucket_rounds_bitexact():
+    """2^20 SDs in 8192 buckets of 128: the finishing pass takes several buckets per warp (its
+    three-CTAs-per-SM form); the queues of surviving pairs carry over from bucket to bucket."""
+    s = inputs.gravitational_box()
+    o, ost, xi, at, gst = _run_both(s, 2, seed=11, shuffle="sort",
+                                    schedule=dict(tile_slots=1024, bucket_target=128))
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"] > 500
+
+
 @pytest.mark.parametrize("shuffle", SHUFFLES)
 def test_grid_bimodal_sample_bitexact(shuffle):
     s = inputs.grid_bimodal(nx=32, ny=32)      # the 2D-grid workload on a 32 x 32 patch
