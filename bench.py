@@ -146,10 +146,10 @@ def workload(name, rank=0, grid_ny=None):
     return inputs.WORKLOADS[name]()
 
 
-def cpu_baseline(s, budget_s=12.0):
+def cpu_baseline(s, budget_s=12.0, shuffle="prp"):
     """The oracle as it stands, single-threaded on a host core, on a bounded sample of steps."""
     import oracle
-    o = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    o = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle=shuffle)
     n_live = int(np.count_nonzero(o.xi))
     t0 = time.perf_counter()
     steps = 0
@@ -171,7 +171,8 @@ def run_reference(args, rank, world):
     s = workload(args.workload, grid_ny=getattr(args, "grid_ny", None))
     n = len(s["xi"])
     # bound the run to a few minutes: a full step of the oracle on this workload
-    probe = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"])
+    shuf = getattr(args, "shuffle", "prp")
+    probe = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle=shuf)
     t0 = time.perf_counter()
     probe.step(s["dt"], 42, 0)
     t_step = time.perf_counter() - t0
@@ -180,7 +181,7 @@ def run_reference(args, rank, world):
         n_sub = 1 << int(np.floor(np.log2(max(1024, n * 150.0 / ((args.steps + args.warmup) * t_step)))))
         sample = inputs.gravitational_box(n_sd=n_sub)
     o = oracle.System(sample["xi"], sample["v"], sample["cell_start"], sample["dv"], sample["kernel_id"],
-                      sample["golovin_b"])
+                      sample["golovin_b"], shuffle=shuf)
     for w in range(args.warmup):
         o.step(sample["dt"], 42, w)
     n_live = int(np.count_nonzero(o.xi))
@@ -195,7 +196,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "n_sd": len(sample["xi"]), "n_cell": 1,
-                                            "kernel": "gravitational", "precision": "fp64"},
+                                            "kernel": "gravitational", "precision": "fp64", "shuffle": shuf},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -226,6 +227,7 @@ def run_ours(args, rank, world, local_rank):
     s = workload(args.workload, rank, getattr(args, "grid_ny", None))
     n = len(s["xi"])
     prec = args.precision
+    shuf = getattr(args, "shuffle", "prp")
     surr_info = None
     with torch.cuda.stream(stream):
         st = sdm.from_inputs(s)
@@ -246,13 +248,13 @@ def run_ours(args, rank, world, local_rank):
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         step = 0
         for _ in range(args.warmup):
-            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
             step += 1
         st.sync()
         live0 = st.remove_zero()
         # which kernels one step launches (one profiled step, outside the timed region)
         st.set_profiling(True)
-        st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+        st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
         step += 1
         st.sync()
         kinds = [k for k, v in st.profile().items() if v[0]]
@@ -274,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
             for k in range(args.steps):
                 flush.fill_(float(k))                    # evict the state from L2 between steps
                 ev[k][0].record(stream)
-                st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+                st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
                 ev[k][1].record(stream)
                 step += 1
             torch.cuda.synchronize()
@@ -291,9 +293,10 @@ def run_ours(args, rank, world, local_rank):
         ms = float(np.mean(times))
         sd_steps = 0.5 * (live0 + live1) * args.steps
         # collisions per step (for the write part of the algorithmic bytes), one extra stats step
-        stats = st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], stats=True)
+        stats = st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], stats=True,
+                        shuffle=shuf)
         step += 1
-        launches = st.launches_per_step() * args.steps
+        launches = st.launches_per_step(shuf) * args.steps
         if surr_info is not None:
             # accuracy against plain FP64 steps of the same seed and step indices
             for k in range(step):
@@ -316,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             st.set_state(xi_p, at_p)
-            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"])
+            st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
             st.get_state(xi_p, at_p)
             step += 1
         e2e_s = (time.perf_counter() - t0) / e2e_steps
@@ -352,7 +355,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "surrogate": "bf16/f32"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload, "n_sd": n, "n_cell": len(s["dv"]), "kernel": "gravitational",
-                   "precision": prec, "dt_s": s["dt"], "dV_m3": float(s["dv"][0]), "n0_m3": 1e8,
+                   "precision": prec, "shuffle": shuf, "dt_s": s["dt"], "dV_m3": float(s["dv"][0]), "n0_m3": 1e8,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}",
                    "schedule": st.schedule},
         "roofline": roofline,
@@ -366,7 +369,7 @@ def run_ours(args, rank, world, local_rank):
     if surr_info is not None:
         line["surrogate"] = surr_info
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(s)
+        line["cpu_baseline"] = cpu_baseline(s, shuffle=shuf)
     print(json.dumps(line), flush=True)
 
 
@@ -380,11 +383,15 @@ def main():
     ap.add_argument("--grid-ny", type=int, default=None,
                     help="rows of a grid workload (default 256); smaller grids for profiling captures")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "surrogate"])
+    ap.add_argument("--shuffle", default="prp", choices=["prp", "sort"],
+                    help="Step 1 contract: keyed bijection above 256 SDs (prp) or sort by key (sort)")
     ap.add_argument("--schedule", default=None, help="JSON of sdm_schedule fields")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.precision == "surrogate" and args.shuffle != "prp":
+        ap.error("the surrogate precision runs under the prp contract only")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
