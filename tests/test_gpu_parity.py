@@ -437,6 +437,42 @@ def test_cuda_graph_replay_with_device_step_counter():
     assert np.array_equal(xr, xg) and np.array_equal(ar, ag)
 
 
+def test_graph_replayed_prp_steps_then_sort_step_bitexact():
+    """PRP steps replayed from a CUDA graph can leave large cells flagged for Step 0 where the
+    host does not see it; a SORT step after them (with a state read between capture and replay)
+    still compacts those cells first."""
+    rng = np.random.default_rng(21)
+    counts = np.array([2600, 1900, 900])
+    n = int(counts.sum())
+    xi = rng.integers(1, 4, n).astype(np.uint64)
+    v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
+    s = inputs._state(xi, v, counts, 1e-14, [0, 1, 1], "removals_graph")
+    o = _oracle_system(s, None, "prp")
+    o.run(s["dt"], 7, 0, 4)
+    o.shuffle = "sort"
+    o.run(s["dt"], 7, 4, 2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = _gpu_state(s, None, dict(tile_slots=512))
+        d_step = torch.zeros(1, dtype=torch.int32, device="cuda")
+        g.step(s["dt"], 7, 0, 1, golovin_b=s["golovin_b"], d_step=d_step)      # step 0
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            g.step(s["dt"], 7, 0, 3, golovin_b=s["golovin_b"], d_step=d_step)  # steps 1..3, not run here
+        torch.cuda.synchronize()
+        g.get_state()                                    # a state read between capture and replay
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(d_step.item()) == 4
+        g.step(s["dt"], 7, 4, 2, golovin_b=s["golovin_b"], shuffle="sort")
+        g.sync()
+        xg, ag, _ = g.get_state()
+        assert g.check() == (0, 0)
+    _assert_bitexact(o, xg, ag)
+    assert int(np.count_nonzero(xg)) < n - 100          # SDs were removed along the way
+
+
 def test_invalid_inputs_raise():
     s = inputs.random_cells(n_cell=4, mean_per_cell=5, seed=1, min_per_cell=1)
     n = len(s["xi"])
@@ -484,9 +520,9 @@ def test_device_pointer_init_and_workspace():
     ws_bytes = sdm.lib().sdm_workspace_bytes(n, 64, 1)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     g = sdm.State(n, 64, 1, workspace=ws)
-    g.init(torch.from_numpy(s["xi"].view(np.int64)).cuda(), torch.from_numpy(s["v"][None].copy()).cuda(),
-           torch.from_numpy(s["dv"]).cuda(), torch.from_numpy(s["kernel_id"]).cuda(),
-           cell_start=torch.from_numpy(s["cell_start"].view(np.int32)).cuda())
+    g.init(torch.from_numpy(s["xi"].view(np.int64).copy()).cuda(), torch.from_numpy(s["v"][None].copy()).cuda(),
+           torch.from_numpy(s["dv"].copy()).cuda(), torch.from_numpy(s["kernel_id"].copy()).cuda(),
+           cell_start=torch.from_numpy(s["cell_start"].view(np.int32).copy()).cuda())
     g.step(1.0, 1, 0, 5)
     o = _oracle_system(s)
     o.run(1.0, 1, 0, 5)
