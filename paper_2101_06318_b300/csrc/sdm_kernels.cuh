@@ -1685,22 +1685,23 @@ struct FinishLayout {
     uint32_t cap;          // records per bucket
     uint32_t nsub_max;     // sub-bucket counters per warp
     uint32_t warps;        // warps (buckets in flight) per CTA
-    uint32_t o_key, o_slot, o_off, o_cnt, o_tmp, o_srt, o_q, warp_bytes;   // per-warp region layout
+    uint32_t o_rec, o_off, o_cnt, o_trec, o_q, warp_bytes;   // per-warp region layout
     uint32_t o_tab, bytes;
 };
 
+// Per warp: the bucket's records in arrival order (later: its positions in sorted order), their
+// arrival index within their sub-bucket, the sub-bucket counters, the records grouped by
+// sub-bucket, the queue of surviving pairs.
 __host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max_smem)
 {
     FinishLayout L;
     L.cap = cap;
     L.nsub_max = 1u << (ceil_log2(cap > 2 ? cap : 2) - 1);          // about two records per counter
     uint32_t o = 0;
-    L.o_key = o; o = align_up(o + 4 * cap, 16);
-    L.o_slot = o; o = align_up(o + 4 * cap, 16);
+    L.o_rec = o; o = align_up(o + 8 * cap, 16);
     L.o_off = o; o = align_up(o + 2 * cap, 16);
     L.o_cnt = o; o = align_up(o + 4 * (L.nsub_max + 1), 16);
-    L.o_tmp = o; o = align_up(o + 2 * cap, 16);
-    L.o_srt = o; o = align_up(o + 2 * cap, 16);
+    L.o_trec = o; o = align_up(o + 8 * cap, 16);
     L.o_q = o; o = align_up(o + (uint32_t)sizeof(FinQueue), 16);
     L.warp_bytes = o;
     L.o_tab = 0;
@@ -1748,12 +1749,11 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
                                               LocalStats& ls, uint32_t* removed, FinQueue& Q, uint32_t& qcnt,
                                               CellCtx& qcc, uint32_t& qbig)
 {
-    uint32_t* key = (uint32_t*)(ws + L.o_key);
-    uint32_t* slot = (uint32_t*)(ws + L.o_slot);
+    uint64_t* rs = (uint64_t*)(ws + L.o_rec);       // records in arrival order
+    uint32_t* ssl = (uint32_t*)(ws + L.o_rec);      // then: the bucket's positions in sorted order
     uint16_t* off = (uint16_t*)(ws + L.o_off);
     uint32_t* cnt = (uint32_t*)(ws + L.o_cnt);
-    uint16_t* tmp = (uint16_t*)(ws + L.o_tmp);
-    uint16_t* srt = (uint16_t*)(ws + L.o_srt);
+    uint64_t* trec = (uint64_t*)(ws + L.o_trec);    // records grouped by sub-bucket
     const uint32_t cap = L.cap;
     const uint32_t big = bucket_big[g];
     const BigCell C = cells[big];
@@ -1766,41 +1766,49 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const uint32_t k = off_c[gl + 1] - S;
     const uint32_t n = off_c[nb];
     const uint64_t* R = rec + (uint64_t)g * cap;
-    for (uint32_t i = lane; i < k; i += 32) {
-        const uint64_t e = R[i];
-        key[i] = (uint32_t)(e >> 32);
-        slot[i] = (uint32_t)e;
-    }
-    // counting sort on the key bits below the bucket's, then exact rank by (key, slot)
+#pragma unroll 4
+    for (uint32_t i = lane; i < k; i += 32) rs[i] = R[i];
+    // counting sort on the key bits below the bucket's, then the exact rank by (key, position)
+    // within each sub-bucket: a record is (key << 32) | position, so that order is the records'
+    // integer order (positions differ, so no two records are equal)
     uint32_t sb = ceil_log2(k > 2 ? k : 2) - 1;
     if (sb > 32u - C.nbits) sb = 32u - C.nbits;
     const uint32_t nsub = 1u << sb;
     for (uint32_t t = lane; t <= nsub; t += 32) cnt[t] = 0;
     __syncwarp();
     const uint32_t sh = 32u - sb;
-    for (uint32_t i = lane; i < k; i += 32) {
-        const uint32_t sub = sb ? (key[i] << C.nbits) >> sh : 0u;
-        off[i] = (uint16_t)atomicAdd(&cnt[sub], 1u);
-    }
+    auto sub_of = [&](uint64_t e) { return sb ? ((uint32_t)(e >> 32) << C.nbits) >> sh : 0u; };
+    for (uint32_t i = lane; i < k; i += 32) off[i] = (uint16_t)atomicAdd(&cnt[sub_of(rs[i])], 1u);
     __syncwarp();
     warp_exclusive_scan(cnt, nsub, lane);
     for (uint32_t i = lane; i < k; i += 32) {
-        const uint32_t sub = sb ? (key[i] << C.nbits) >> sh : 0u;
-        tmp[cnt[sub] + off[i]] = (uint16_t)i;
+        const uint64_t e = rs[i];
+        trec[cnt[sub_of(e)] + off[i]] = e;
     }
-    __syncwarp();
-    for (uint32_t i = lane; i < k; i += 32) {
-        const uint32_t ki = key[i];
-        const uint32_t sub = sb ? (ki << C.nbits) >> sh : 0u;
-        const uint32_t st = cnt[sub], en = cnt[sub + 1];
-        uint32_t r = 0;
-        const uint32_t si = slot[i];
-        for (uint32_t p = st; p < en; ++p) {
-            const uint32_t o = tmp[p];
-            const uint32_t ko = key[o];
-            r += (ko < ki) || (ko == ki && slot[o] < si);     // equal keys: lower slot first
+    __syncwarp();                                   // rs is dead from here: ssl takes its place
+    // FR grouped records per lane at once, so that their sub-bucket scans overlap
+    constexpr uint32_t FR = 4;
+    for (uint32_t p0 = 0; p0 < k; p0 += 32 * FR) {
+        uint64_t e[FR];
+        uint32_t st[FR], len[FR], r[FR], lmax = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < FR; ++j) {
+            const uint32_t p = p0 + lane + 32 * j;
+            e[j] = p < k ? trec[p] : 0ull;
+            const uint32_t sub = sub_of(e[j]);
+            st[j] = p < k ? cnt[sub] : 0u;
+            len[j] = p < k ? cnt[sub + 1] - st[j] : 0u;
+            r[j] = 0;
+            lmax = max(lmax, len[j]);
         }
-        srt[st + r] = (uint16_t)i;
+        for (uint32_t t = 0; t < lmax; ++t) {
+#pragma unroll
+            for (uint32_t j = 0; j < FR; ++j)
+                if (t < len[j]) r[j] += trec[st[j] + t] < e[j] ? 1u : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < FR; ++j)
+            if (p0 + lane + 32 * j < k) ssl[st[j] + r[j]] = (uint32_t)e[j];
     }
     // the partner of this bucket's last SD may be the first SD of the next non-empty bucket
     unsigned long long nxt = ~0ull;
@@ -1850,9 +1858,8 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
             ok[h] = M <= (m_hi >> 1) && m >= m_lo && m <= m_hi;
             const uint32_t r = ok[h] ? 2 * m - S : 0u;
             const bool last = r + 1 >= k;              // partner is the first SD of the next bucket
-            const uint32_t i1 = srt[r], i2 = srt[last ? r : r + 1];
-            sl[h][0] = slot[i1];
-            sl[h][1] = last ? (uint32_t)nxt : slot[i2];
+            sl[h][0] = ssl[r];
+            sl[h][1] = last ? (uint32_t)nxt : ssl[last ? r : r + 1];
 #pragma unroll
             for (uint32_t j = 0; j < 2; ++j) {
                 const uint64_t e = C.slot_begin + sl[h][j];
