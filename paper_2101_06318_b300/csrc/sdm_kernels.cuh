@@ -1533,13 +1533,13 @@ struct BucketBook {
 
 // The last scatter CTA of a cell: offsets of its nb buckets (nb a power of two, at most
 // 8192; blockDim.x == BIG_SCATTER_THREADS).  Each thread takes nb / 256 consecutive
-// buckets (at least one), loading them eight at a time with all eight loads in flight
-// (so 4096 buckets cost two round trips to L2), staging the clamped counts in
+// buckets (at least one), loading them sixteen at a time with all sixteen loads in flight
+// (so 4096 buckets cost one round trip to L2), staging the clamped counts in
 // shared memory tmp[nb]; then a block scan of the thread sums.
 __device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __restrict__ out, uint32_t nb,
                                     uint32_t cap, uint32_t* tmp, uint32_t* wt, uint32_t* err)
 {
-    constexpr uint32_t BATCH = 8;
+    constexpr uint32_t BATCH = 16;
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint32_t per = nb > BIG_SCATTER_THREADS ? nb / BIG_SCATTER_THREADS : 1u;
     const uint32_t b0 = tid * per, b1 = min(nb, b0 + per);
