@@ -1399,6 +1399,15 @@ __global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kerne
         static_assert(EFF_LINES <= 32, "one line per lane");
         if (warp == 0 && lane < EFF_LINES)
             asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(tab) + 128 * lane));
+        // the second filter's FP64 tables, into L2 (a few pairs per step read them)
+        constexpr uint32_t ED_LINES = (uint32_t)((sizeof(g_eff_Ed) + 127) / 128);
+        static_assert(ED_LINES + 2 <= 32, "one line per lane");
+        if (blockIdx.x == 0 && warp == 1) {
+            const char* line = lane < ED_LINES ? reinterpret_cast<const char*>(g_eff_Ed) + 128 * lane
+                               : lane == ED_LINES  ? reinterpret_cast<const char*>(g_eff_Rd)
+                                                   : reinterpret_cast<const char*>(g_eff_invdRd);
+            if (lane < ED_LINES + 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+        }
     }
     // Step 0 for the large cells that lost SDs in the previous step: each such cell is compacted
     // by one block while the grid waits at a barrier (the launch is cooperative).  The flag is

@@ -396,15 +396,23 @@ __device__ __noinline__ uint64_t gamma_tilde_fp64_path(uint32_t kid, double v1, 
 // cycles) -- with a bound on its distance to the exact sequence's value.  The
 // exact sequence above runs only when this interval cannot decide gamma.
 //   Error budget relative to B = scale pi (r1+r2)^2 (vt1 + vt2) (u = 2^-53):
-//   radii after two Newton steps from cbrtf (|r0/r - 1| <= 2^-21): within
-//   ~8u of the true cube root (the exact sequence: 1 ulp); (r1+r2)^2, the
-//   fall speeds and their difference: ~40u B; q = rs (1/R) with a refined
-//   reciprocal and t = (R - R_i) (1/dR_i): weights off by ~200u, times table
-//   steps <= 1 -> ~250u B; scale with a refined reciprocal of dV: ~10u.  In
-//   all well below 1000u B = 2^-43 B; the bound used is 2^-36 B.
+//   a radius after one Newton step from cbrtf (seed within 1 ulp of the float
+//   cube root of the float-rounded argument: |e0| <= 2^-22.7) with a step
+//   factor h = 1/(3 r0^2) from float arithmetic (|eta| <= 2^-21.4): relative
+//   error ~ e0^2 + |eta e0| <= 2^-43 ~ 1000u; 1/sqrt(r) after one Newton step
+//   from rsqrtf (2 ulp): 1.5 e0^2 ~ 1000u.  (r1+r2)^2, the fall speeds and
+//   their difference: ~6000u B; q = rs (1/R) with a refined reciprocal and
+//   t = (R - R_i) (1/dR_i), R / dR_i <= 6: weights off by ~12000u, times table
+//   steps <= 1 -> ~15000u B; scale with a refined reciprocal of dV: ~10u.  In
+//   all below 25000u B ~ 2^-38.4 B; the bound used is 2^-36 B.
 // ---------------------------------------------------------------------------
 constexpr double LITE_REL_BOUND = 0x1p-36;
-__constant__ double c_eff_invdR[EFF_NR] = {
+// The second filter reads its tables through L1 from global memory: its lookups use
+// indices known only at run time, which serialise on the constant cache, and a cold
+// constant bank is fetched line by line on the filter's critical path.
+__device__ const double g_eff_Rd[EFF_NR] = {SDM_EFF_RADII(SDM_AS_DOUBLE)};
+__device__ const double g_eff_Ed[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
+__device__ const double g_eff_invdRd[EFF_NR] = {
     1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (10e-6), 1.0 / (20e-6),
     1.0 / (20e-6), 1.0 / (50e-6), 1.0 / (50e-6), 1.0 / (100e-6), 1.0 / (700e-6), 0.0};
 
@@ -419,20 +427,18 @@ __device__ __forceinline__ double rcp_lite(double d)
 __device__ __forceinline__ double cbrt_lite(double x)
 {
     const float xf = (float)x;
-    double r = (double)cbrtf(xf);
-    const double h = (double)__frcp_rn(3.0f * __fmul_rn((float)r, (float)r));   // ~ 1 / (3 r^2)
-#pragma unroll
-    for (int i = 0; i < 2; ++i) r = __fma_rn(-__fma_rn(r * r, r, -x), h, r);
-    return r;
+    const float rf = cbrtf(xf);
+    const double r = (double)rf;
+    const double h = (double)__frcp_rn(3.0f * __fmul_rn(rf, rf));   // ~ 1 / (3 r^2)
+    return __fma_rn(-__fma_rn(r * r, r, -x), h, r);                 // one Newton step
 }
 
 __device__ __forceinline__ double vt_lite(double r)
 {
     if (r < VT_R12) return VT_K1 * r * r;
     if (r < VT_R23) return VT_K2 * r;
-    double y = (double)rsqrtf((float)r);               // 1 / sqrt(r)
-#pragma unroll
-    for (int i = 0; i < 2; ++i) y = __fma_rn(0.5 * y, __fma_rn(-r * y, y, 1.0), y);
+    const double y0 = (double)rsqrtf((float)r);         // 1 / sqrt(r)
+    const double y = __fma_rn(0.5 * y0, __fma_rn(-r * y0, y0, 1.0), y0);   // one Newton step
     return VT_K3 * (r * y);
 }
 
@@ -440,20 +446,21 @@ __device__ __forceinline__ double efficiency_lite(double R, double q)
 {
     int i;
     double t;
-    if (R <= c_eff_R[0]) { i = 0; t = 0.0; }
+    if (R <= c_eff_R[0]) { i = 0; t = 0.0; }                  // fixed indices: constant operands
     else if (R >= c_eff_R[EFF_NR - 1]) { i = EFF_NR - 2; t = 1.0; }
     else {
         i = eff_interval_d(R);
-        t = (R - c_eff_R[i]) * c_eff_invdR[i];
+        t = (R - __ldg(&g_eff_Rd[i])) * __ldg(&g_eff_invdRd[i]);
     }
     const double s = q * 10.0;
     int j = __double2int_rz(s);
     double w;
     if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.0; }
     else w = s - (double)j;
-    const double* E = c_eff_E;
-    const double e0 = E[i * EFF_NQ + j] + w * (E[i * EFF_NQ + j + 1] - E[i * EFF_NQ + j]);
-    const double e1 = E[(i + 1) * EFF_NQ + j] + w * (E[(i + 1) * EFF_NQ + j + 1] - E[(i + 1) * EFF_NQ + j]);
+    const double* E = g_eff_Ed + i * EFF_NQ + j;
+    const double E00 = __ldg(E), E01 = __ldg(E + 1), E10 = __ldg(E + EFF_NQ), E11 = __ldg(E + EFF_NQ + 1);
+    const double e0 = E00 + w * (E01 - E00);
+    const double e1 = E10 + w * (E11 - E10);
     return e0 + t * (e1 - e0);
 }
 
