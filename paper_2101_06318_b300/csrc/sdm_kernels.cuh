@@ -1104,10 +1104,10 @@ __device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ c
 // time, so the long evaluation runs on full warps instead of diverging the
 // common path.
 // ---------------------------------------------------------------------------
-constexpr uint32_t PRP_THREADS = 256;
+constexpr uint32_t PRP_THREADS = 128;
 constexpr uint32_t PRP_WARPS = PRP_THREADS / 32;
 #ifndef SDM_PRP_MIN_BLOCKS
-#define SDM_PRP_MIN_BLOCKS 2
+#define SDM_PRP_MIN_BLOCKS 4
 #endif
 #ifndef SDM_PRP_QPT
 #define SDM_PRP_QPT 4
