@@ -205,7 +205,13 @@ sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* ce
  * that its blocks can wait for that compaction), and every call that reads or
  * re-lays out the state (sdm_get_state, sdm_totals, sdm_spectrum,
  * sdm_remove_zero, sdm_check_state, sdm_set_schedule, sdm_autotune, a SORT
- * step) compacts them first, so no caller sees the difference. */
+ * step) compacts them first, so no caller sees the difference.
+ * Under SDM_SHUFFLE_SORT a large cell's SDs are distributed over buckets of
+ * about bucket_target SDs by the top bits of their keys; a bucket holds its
+ * mean count plus ten standard deviations plus 32 records.  A step whose keys
+ * overflow a bucket (probability below 1e-20 per bucket and step) records
+ * SDM_ECAPACITY in the device error word, read by sdm_sync or the next call
+ * that synchronises; the state is then invalid. */
 sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
                                 sdm_step_stats* stats);
 
