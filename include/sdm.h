@@ -211,7 +211,8 @@ sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* ce
  * mean count plus ten standard deviations plus 32 records.  A step whose keys
  * overflow a bucket (probability below 1e-20 per bucket and step) records
  * SDM_ECAPACITY in the device error word, read by sdm_sync or the next call
- * that synchronises; the state is then invalid. */
+ * that synchronises; SDs that did not fit sat that step out, so the step
+ * does not follow the random-number contract (no memory is overrun). */
 sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
                                 sdm_step_stats* stats);
 
