@@ -108,6 +108,7 @@ struct sdm_state {
     uint64_t* d_scratch = nullptr;
     uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
     uint32_t n_quads = 0, prp_grid = 0;      // PRP contract: quads of all large cells, grid size
+    uint32_t prp_threads = PRP_THREADS;      // and CTA size
     uint32_t* d_cta_first = nullptr;         // [prp_grid] first large cell of each CTA (many large cells)
     unsigned long long* d_big_xmax = nullptr;   // [n_big] largest multiplicity of the cell
     // a PRP step may have left large cells flagged for Step 0 since the last compaction;
@@ -310,13 +311,24 @@ sdm_status ensure_device_tables()
     return SDM_OK;
 }
 
+// CTA size of the PRP kernel for a layout with n_big large cells
+uint32_t prp_threads_for(uint32_t n_big) { return n_big >= PRP_MANY_CELLS ? PRP_THREADS_MANY : PRP_THREADS; }
+
 // Grid of the PRP kernel: one wave of resident CTAs, at most one CTA per warp's worth of quads.
-uint32_t prp_grid_size(uint32_t n_quads, int n_sm)
+uint32_t prp_grid_size(uint32_t n_quads, int n_sm, uint32_t threads)
 {
     // one wave of resident blocks of either instantiation (the launch is cooperative)
     int per_sm = 0, per_sm_s = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>, PRP_THREADS, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true>, PRP_THREADS, 0) != cudaSuccess) {
+    const bool many = threads == PRP_THREADS_MANY;
+    const cudaError_t e1 = many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                      &per_sm, big_prp_kernel<false, PRP_THREADS_MANY>, (int)threads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>,
+                                                                               (int)threads, 0);
+    const cudaError_t e2 = many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                      &per_sm_s, big_prp_kernel<true, PRP_THREADS_MANY>, (int)threads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true>,
+                                                                               (int)threads, 0);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
         per_sm = per_sm_s = 1;
     }
@@ -496,7 +508,8 @@ sdm_status build_layout(sdm_state* st)
     SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
     st->n_quads = n_quads;
     if (n_quads) {
-        st->prp_grid = prp_grid_size(n_quads, st->n_sm);
+        st->prp_threads = prp_threads_for((uint32_t)bigs.size());
+        st->prp_grid = prp_grid_size(n_quads, st->n_sm, st->prp_threads);
         std::vector<uint32_t> first(st->prp_grid);
         for (uint32_t b = 0, c = 0; b < st->prp_grid; ++b) {
             const uint32_t qa = (uint32_t)(((uint64_t)b * n_quads) / st->prp_grid);
@@ -810,7 +823,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             if (cap_status != cudaStreamCaptureStatusNone) st->big_deferred_always = true;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(st->prp_grid);
-            cfg.blockDim = dim3(PRP_THREADS);
+            cfg.blockDim = dim3(st->prp_threads);
             cfg.dynamicSmemBytes = 0;
             cfg.stream = st->stream;
             cudaLaunchAttribute at[1];
@@ -818,10 +831,14 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             at[0].val.cooperative = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            if (p->precision == SDM_PREC_SURROGATE)
-                SDM_CUDA(cudaLaunchKernelEx(&cfg, big_prp_kernel<true>, a, st->prp_launch, bb));
+            const bool surr = p->precision == SDM_PREC_SURROGATE;
+            if (st->prp_threads == PRP_THREADS_MANY)
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? big_prp_kernel<true, PRP_THREADS_MANY>
+                                                       : big_prp_kernel<false, PRP_THREADS_MANY>,
+                                            a, st->prp_launch, bb));
             else
-                SDM_CUDA(cudaLaunchKernelEx(&cfg, big_prp_kernel<false>, a, st->prp_launch, bb));
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? big_prp_kernel<true> : big_prp_kernel<false>, a,
+                                            st->prp_launch, bb));
         } else if (st->n_big) {
             SDM_TRY(flush_big_compaction(st));      // cells left flagged by a PRP step
             const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
@@ -1557,7 +1574,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
-        big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm), PRP_THREADS, 0, stream>>>(a, L, bb);
+        big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm, PRP_THREADS), PRP_THREADS, 0, stream>>>(a, L, bb);
         SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, live + 6, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);

@@ -1104,7 +1104,9 @@ __device__ void big_end_of_step(const StepArgs& a, const BigCell* __restrict__ c
 // time, so the long evaluation runs on full warps instead of diverging the
 // common path.
 // ---------------------------------------------------------------------------
-constexpr uint32_t PRP_THREADS = 128;
+constexpr uint32_t PRP_THREADS = 128;           // threads per CTA (one or a few large cells)
+constexpr uint32_t PRP_THREADS_MANY = 64;       // threads per CTA with many large cells: finer ranges
+constexpr uint32_t PRP_MANY_CELLS = 64;         // large cells from which the finer CTAs are used
 constexpr uint32_t PRP_WARPS = PRP_THREADS / 32;
 #ifndef SDM_PRP_MIN_BLOCKS
 #define SDM_PRP_MIN_BLOCKS 4
@@ -1361,14 +1363,16 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
     if (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
 }
 
-template <bool SURR>
-__global__ void __launch_bounds__(PRP_THREADS, SDM_PRP_MIN_BLOCKS) big_prp_kernel(StepArgs a, BigLaunch L,
-                                                                                 BigBook bk)
+// THREADS: CTA size (the same registers and warps per SM for both sizes)
+template <bool SURR, uint32_t THREADS = PRP_THREADS>
+__global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / THREADS) big_prp_kernel(StepArgs a,
+                                                                                                     BigLaunch L,
+                                                                                                     BigBook bk)
 {
     const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
     // a compaction kernel that follows (allocation-free step) may start launching
     asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ PairQueue pq[PRP_WARPS];
+    __shared__ PairQueue pq[THREADS / 32];
     __shared__ uint32_t wt[40];
     static_assert(sizeof(WalkScratch) <= sizeof(PairQueue), "the walk list shares the pair queue's memory");
     __shared__ uint32_t key_s[PRP_MIN_N];

@@ -245,6 +245,15 @@ def test_ensemble_sample_bitexact(shuffle):
     _assert_bitexact(o, xi, at)
 
 
+def test_many_large_cells_bitexact():
+    """80 boxes of 2^10 .. 2^13 SDs, each a large cell: the PRP step runs in its finer CTAs
+    (64 threads) when a layout holds this many large cells."""
+    s = inputs.ensemble(n_members=80, log2_lo=10, log2_hi=13, seed=5)
+    o, ost, xi, at, gst = _run_both(s, 6, seed=3)
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"]
+
+
 def test_edge_cases():
     # n_sd = 2 (one pair), 3 (odd), all-dead cell, huge p (caps bind), xi near 2^53
     xi = np.array([5, 5, 7, 1, 9, 0, 0, (1 << 53) - 1, 3], np.uint64)
