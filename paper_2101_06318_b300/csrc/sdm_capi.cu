@@ -100,7 +100,7 @@ struct sdm_state {
     uint32_t n_big = 0;
     BigChunk* d_chunks = nullptr;
     uint32_t n_chunks = 0;
-    uint32_t* d_bucket_big = nullptr;
+    BucketDesc* d_bucket_desc = nullptr;      // [n_buckets] the cell of each SORT bucket
     uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
     uint32_t* d_cursor = nullptr;            // [n_buckets] appends per bucket (zero between steps)
     uint32_t* d_bstart = nullptr;            // [n_buckets + n_big] per-cell bucket offsets of the current step
@@ -211,7 +211,7 @@ void free_layout(sdm_state* st)
     for (auto& a : st->owned_layout) cudaFree(a.p);
     st->owned_layout.clear();
     if (st->ws) st->ws_used = st->ws_fixed;
-    st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_big = nullptr;
+    st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_desc = nullptr;
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
     st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
@@ -417,7 +417,7 @@ sdm_status build_layout(sdm_state* st)
     std::vector<uint32_t> wcells;
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
-    std::vector<uint32_t> bucket_big;
+    std::vector<BucketDesc> bucket_desc;
     uint32_t n_quads = 0;
     TileDesc cur{0, 0, 0, 0};
     uint32_t cur_slots = 0;
@@ -443,9 +443,10 @@ sdm_status build_layout(sdm_state* st)
             uint32_t nbits = lw > tbits ? lw - tbits : 0;
             nbits = std::min<uint32_t>(nbits, BIG_MAX_BUCKET_BITS);
             b.nbits = nbits;
-            b.bucket_base = (uint32_t)bucket_big.size();
+            b.bucket_base = (uint32_t)bucket_desc.size();
             const uint32_t nb = 1u << nbits;
-            for (uint32_t k = 0; k < nb; ++k) bucket_big.push_back((uint32_t)bigs.size());
+            for (uint32_t k = 0; k < nb; ++k)
+                bucket_desc.push_back(BucketDesc{c, b.slot_begin, b.bucket_base, nbits, (uint32_t)bigs.size(), 0, 0, 0});
             const uint32_t mean = (w + nb - 1) / nb;
             bucket_cap = std::max(bucket_cap, bucket_capacity(mean));
             max_nb = std::max(max_nb, nb);
@@ -469,7 +470,7 @@ sdm_status build_layout(sdm_state* st)
     }
     flush();
     bucket_cap = (bucket_cap + 31) & ~31u;
-    st->n_buckets_planned = (uint32_t)bucket_big.size();
+    st->n_buckets_planned = (uint32_t)bucket_desc.size();
     if (!bigs.empty()) {
         SDM_TRY(set_smem_limits());
         // two CTAs per SM (more registers: a shorter latency per bucket) unless three CTAs per SM
@@ -505,7 +506,7 @@ sdm_status build_layout(sdm_state* st)
     }
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
-    SDM_TRY(upload(st, &st->d_bucket_big, bucket_big));
+    SDM_TRY(upload(st, &st->d_bucket_desc, bucket_desc));
     st->n_quads = n_quads;
     if (n_quads) {
         st->prp_threads = prp_threads_for((uint32_t)bigs.size());
@@ -531,7 +532,7 @@ sdm_status build_layout(sdm_state* st)
     st->prp_launch = BigLaunch{st->n_big, n_quads, st->d_big, st->d_big_xmax, st->d_cta_first, {}};
     for (uint32_t b = 0; b < st->n_big && b < BIG_PARAM_CELLS; ++b) st->prp_launch.pc[b] = bigs[b];
     st->n_chunks = (uint32_t)chunks.size();
-    st->n_buckets = (uint32_t)bucket_big.size();
+    st->n_buckets = (uint32_t)bucket_desc.size();
     st->bucket_cap = bucket_cap;
     st->max_nb = max_nb;
     if (st->n_buckets) {
@@ -851,7 +852,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 ProfScope ps(st, 2);
                 auto fk = st->fin_minb == 2 ? big_finish_kernel<2> : big_finish_kernel<3>;
                 fk<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_big, st->d_scratch, st->d_bstart, st->n_buckets, st->d_big_xmax,
+                    a, st->d_big, st->d_bucket_desc, st->d_scratch, st->d_bstart, st->n_buckets, st->d_big_xmax,
                     st->fin_L, bb);
             }
         }
@@ -895,7 +896,7 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
-    b += round256(4 * max_buckets + 256) + round256(16 * max_buckets + 256);
+    b += round256(sizeof(BucketDesc) * max_buckets + 256) + round256(16 * max_buckets + 256);
     b += round256(8 * max_buckets * max_cap + 256);
     return b;
 }
@@ -1458,7 +1459,7 @@ constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, remova
 constexpr size_t NA_OFF_XMAX = 192;      // uint64 largest multiplicity of the box
 constexpr size_t NA_OFF_CHUNKS = 256;
 constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
-constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + 4 * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
+constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + sizeof(BucketDesc) * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
 constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
 constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
 constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
@@ -1524,7 +1525,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         chunks[n_chunks++] = BigChunk{0, l, std::min(n_sd, l + BIG_CHUNK), n_of_cell};
     C.quad_begin = 0;
     const uint32_t n_quads = (n_sd / 2 + 1) / 2;
-    uint32_t bucket_big[NA_MAX_BUCKETS] = {};
+    BucketDesc bucket_desc[NA_MAX_BUCKETS];
     unsigned char head[256] = {};
     const uint8_t kid = (uint8_t)kernel_id;
     const uint32_t cell_start[2] = {0, n_sd};
@@ -1536,7 +1537,9 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     // descriptors in; cursors, tickets, flags and the error word start at zero on every call
     SDM_CUDA(cudaMemcpyAsync(base, head, sizeof head, cudaMemcpyHostToDevice, stream));
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_CHUNKS, chunks, sizeof(BigChunk) * n_chunks, cudaMemcpyHostToDevice, stream));
-    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_big, 4 * nb, cudaMemcpyHostToDevice, stream));
+    for (uint32_t k = 0; k < nb; ++k) bucket_desc[k] = BucketDesc{0, 0, 0, C.nbits, 0, 0, 0, 0};
+    SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_desc, sizeof(BucketDesc) * nb, cudaMemcpyHostToDevice,
+                             stream));
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
     uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
@@ -1586,7 +1589,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
             a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
         big_finish_kernel<2><<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
-            a, d_cell, (const uint32_t*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb);
+            a, d_cell, (const BucketDesc*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb);
     }
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());

@@ -70,6 +70,8 @@ __device__ __forceinline__ bool sorts(const StepArgs& a, uint32_t n)
 struct TileDesc { uint32_t slot_begin, slot_end, cell_begin, n_cells; };
 struct BigCell { uint32_t cell, slot_begin, width, bucket_base, nbits, quad_begin; };   // quad_begin: PRP contract
 struct BigChunk { uint32_t big, l_begin, l_end, n_of_cell; };   // n_of_cell: chunks of the same cell
+// per bucket of the SORT contract: what its finishing warp needs of its cell, in one 32-byte read
+struct __align__(16) BucketDesc { uint32_t cell, slot_begin, bucket_base, nbits, big, pad0, pad1, pad2; };
 
 __device__ __forceinline__ uint32_t step_index(const StepArgs& a)
 {
@@ -1755,7 +1757,7 @@ __device__ __forceinline__ void fin_drain(const StepArgs& a, const EffTab* __res
 
 __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
                                               const BigCell* __restrict__ cells,
-                                              const uint32_t* __restrict__ bucket_big,
+                                              const BucketDesc* __restrict__ bucket_desc,
                                               const uint64_t* __restrict__ rec, const uint32_t* __restrict__ bstart,
                                               const unsigned long long* __restrict__ xmax, const FinishLayout& L,
                                               unsigned char* ws, uint32_t g, uint32_t lane, uint32_t step,
@@ -1768,8 +1770,8 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     uint32_t* cnt = (uint32_t*)(ws + L.o_cnt);
     uint64_t* trec = (uint64_t*)(ws + L.o_trec);    // records grouped by sub-bucket
     const uint32_t cap = L.cap;
-    const uint32_t big = bucket_big[g];
-    const BigCell C = cells[big];
+    const BucketDesc C = bucket_desc[g];
+    const uint32_t big = C.big;
     const uint32_t nb = 1u << C.nbits;
     // where this bucket starts in the cell's sorted list, its size, the cell's live count
     // (the cell's offsets: bstart[bucket + cell index], its total after its last bucket)
@@ -1905,7 +1907,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
 // (each bucket's latency is what counts), 3 when the warps take several buckets each.
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
-                                                         const uint32_t* __restrict__ bucket_big,
+                                                         const BucketDesc* __restrict__ bucket_desc,
                                                          const uint64_t* __restrict__ rec,
                                                          const uint32_t* __restrict__ bstart, uint32_t n_buckets,
                                                          const unsigned long long* __restrict__ xmax,
@@ -1926,7 +1928,7 @@ __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const
     uint32_t qcnt = 0, qbig = 0;                   // warp-uniform
     CellCtx qcc{};
     for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
-        finish_bucket(a, tab, cells, bucket_big, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q, qcnt,
+        finish_bucket(a, tab, cells, bucket_desc, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q, qcnt,
                       qcc, qbig);
     if (qcnt > 0) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &bb.removed[qbig], ls, lane);
     if (a.stats) {
