@@ -1,20 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the SDM coalescence step on one B300 (per rank).
 
-Workload (default): the gravitational box -- one cell of 2^20 super-droplets,
-lognormal radii (median 15 um, sigma_g 1.4), n0 = 1e8 m^-3, dV = 1e6 m^3,
-dt = 1 s, FP64-exact decisions.  A "step" is one coalescence timestep over all
-super-droplets (Fig. "fig:algo": removal, shuffle, pairing, eq. (p), gamma,
-update).  Metric: super-droplet-steps per second (live SDs x steps / time).
+Workload (default): the 256 x 256 lognormal grid -- 65 536 cells of dV = 1e3
+m^3 holding Poisson(256) super-droplets each (1.68e7 SDs), radii lognormal
+(median 15 um, sigma_g 1.4), n0 = 1e8 m^-3, gravitational kernel, dt = 1 s,
+FP64-exact decisions: the largest of the workloads that fits one GPU.  A
+"step" is one coalescence timestep over all super-droplets (Fig. "fig:algo":
+removal, shuffle, pairing, eq. (p), gamma, update).  Metric: super-droplet-steps
+per second (live SDs x steps / time).
 
-The 16 MB state fits in the 126 MB L2, so L2 is flushed (a 256 MB write)
-between timed steps and each step is timed alone with CUDA events on the
-library's stream; ms_per_step is their mean.
+Each step is timed alone with CUDA events on the library's stream, after a
+256 MB write that evicts L2 (the 268 MB state is larger than L2 as well);
+ms_per_step is their mean.  With --graph G, G steps are captured into one CUDA
+graph (a device step counter advances the random-number stream) and the
+replays are timed instead (the batched-ensemble form: --workload ensemble
+--precision fp32 --graph 100).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload W] [--precision P] [--shuffle S] [--graph G]
 
-Under torchrun each rank runs its own box (independent problems: weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+Under torchrun each rank runs its own copy of the workload (independent
+problems: weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -141,26 +148,57 @@ def _profiled_traffic(kernel, workload_name, n_sd):
 def workload(name, rank=0, grid_ny=None):
     if name == "gravitational_box":
         return inputs.gravitational_box(seed=42 + rank)
-    if grid_ny and name.startswith("grid_"):
-        return inputs.WORKLOADS[name](ny=grid_ny)       # a smaller grid (profiling captures)
+    if name.startswith("grid_"):
+        return inputs.WORKLOADS[name](ny=grid_ny or 256, seed=42 + rank)   # grid_ny: a smaller grid
+    if name == "ensemble":
+        return inputs.ensemble(seed=42 + rank)
     return inputs.WORKLOADS[name]()
 
 
-def cpu_baseline(s, budget_s=12.0, shuffle="prp"):
-    """The oracle as it stands, single-threaded on a host core, on a bounded sample of steps."""
+def sample_of(name, s, frac):
+    """A bounded sample of workload s holding about frac of its SDs, of the same kind: fewer
+    grid rows, fewer ensemble members, or a smaller box (the CPU legs' samples)."""
+    if frac >= 1.0:
+        return s
+    if name.startswith("grid_"):
+        ny = max(1, int(s["meta"]["ny"] * frac))
+        return inputs.WORKLOADS[name](ny=ny)
+    if name == "ensemble":
+        return inputs.ensemble(n_members=max(2, int(1024 * frac)))
+    if name == "gravitational_box":
+        return inputs.gravitational_box(n_sd=1 << max(10, int(np.floor(np.log2(len(s["xi"]) * frac)))))
+    return s
+
+
+def cpu_baseline(s, budget_s=12.0, shuffle="prp", name=None):
+    """The oracle as it stands, single-threaded on a host core, on a bounded sample of steps (a
+    smaller sample of the same workload when one full step would take more than the budget)."""
     import oracle
-    o = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle=shuffle)
+
+    def system(t):
+        return oracle.System(t["xi"], t["v"], t["cell_start"], t["dv"], t["kernel_id"], t["golovin_b"],
+                             shuffle=shuffle)
+    o = system(s)
+    t0 = time.perf_counter()
+    o.step(s["dt"], 42, 0)
+    t1 = time.perf_counter() - t0
+    first = 1
+    if name and t1 > budget_s / 4:
+        s = sample_of(name, s, budget_s / 8 / t1)
+        o = system(s)
+        first = 0
     n_live = int(np.count_nonzero(o.xi))
     t0 = time.perf_counter()
     steps = 0
     while True:
-        o.step(s["dt"], 42, steps)
+        o.step(s["dt"], 42, first + steps)
         steps += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     return {"value": n_live * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the {s['name']} workload ({n_live} SDs), single-threaded C, FP64"}
+            "sample": f"{steps} steps of the {s['name']} workload ({n_live} SDs, {len(s['dv'])} cells), "
+                      f"single-threaded C, FP64"}
 
 
 def run_reference(args, rank, world):
@@ -177,9 +215,8 @@ def run_reference(args, rank, world):
     probe.step(s["dt"], 42, 0)
     t_step = time.perf_counter() - t0
     sample = s
-    if (args.steps + args.warmup) * t_step > 150.0 and args.workload == "gravitational_box":
-        n_sub = 1 << int(np.floor(np.log2(max(1024, n * 150.0 / ((args.steps + args.warmup) * t_step)))))
-        sample = inputs.gravitational_box(n_sd=n_sub)
+    if (args.steps + args.warmup) * t_step > 150.0:
+        sample = sample_of(args.workload, s, 150.0 / ((args.steps + args.warmup) * t_step))
     o = oracle.System(sample["xi"], sample["v"], sample["cell_start"], sample["dv"], sample["kernel_id"],
                       sample["golovin_b"], shuffle=shuf)
     for w in range(args.warmup):
@@ -195,11 +232,17 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "n_sd": len(sample["xi"]), "n_cell": 1,
-                                            "kernel": "gravitational", "precision": "fp64", "shuffle": shuf},
+            "data": "synthetic", "config": {"workload": args.workload, "n_sd": len(sample["xi"]),
+                                            "n_cell": len(sample["dv"]), "kernel": _kernels(sample),
+                                            "precision": "fp64", "shuffle": shuf},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _kernels(s):
+    k = set(int(x) for x in np.unique(s["kernel_id"]))
+    return {0: "golovin", 1: "gravitational"}[k.pop()] if len(k) == 1 else "golovin+gravitational"
 
 
 def combine_ranks(tot_ms, sd_steps, e2e_s, dist, world, device):
@@ -263,40 +306,68 @@ def run_ours(args, rank, world, local_rank):
         # behind it count as one) is timed by the step's own events, which bracket exactly those
         # launches; otherwise each kind is bracketed by events of its own inside the timed region
         single = len(kinds) == 1
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if not single:
-            st.set_profiling(True)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        with ClockSampler(local_rank) as clk:
-            # hold the stream briefly so that every timed iteration is queued before the first one
-            # runs: the steps then run back to back and no step waits for the host to submit it
-            torch.cuda._sleep(int(2e8))
-            for k in range(args.steps):
-                flush.fill_(float(k))                    # evict the state from L2 between steps
-                ev[k][0].record(stream)
-                st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
-                ev[k][1].record(stream)
-                step += 1
+        if args.graph:
+            # G steps captured once into a CUDA graph; the device step counter advances the
+            # random-number stream from replay to replay; the replays are timed
+            G = args.graph
+            n_rep = max(1, args.steps // G)
+            n_timed = n_rep * G
+            d_step = torch.full((1,), step, dtype=torch.int32, device=dev)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                st.step(s["dt"], 42, 0, G, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf, d_step=d_step)
+            graph.replay()                               # one untimed replay
             torch.cuda.synchronize()
-        if single:
-            prof = {kinds[0]: (args.steps, sum(a.elapsed_time(b) for a, b in ev))}
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_rep)]
+            with ClockSampler(local_rank) as clk:
+                torch.cuda._sleep(int(2e8))
+                for k in range(n_rep):
+                    flush.fill_(float(k))
+                    ev[k][0].record(stream)
+                    graph.replay()
+                    ev[k][1].record(stream)
+                torch.cuda.synchronize()
+            step = int(d_step.item())
+            total = sum(a.elapsed_time(b) for a, b in ev)
+            prof = {(kinds[0] if single else "cuda_graph_step"): (n_timed, total)}
+            times = [total / n_timed]
         else:
-            prof = st.profile()
-            st.set_profiling(False)
+            n_timed = args.steps
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            if not single:
+                st.set_profiling(True)
+            with ClockSampler(local_rank) as clk:
+                # hold the stream briefly so that every timed iteration is queued before the first one
+                # runs: the steps then run back to back and no step waits for the host to submit it
+                torch.cuda._sleep(int(2e8))
+                for k in range(args.steps):
+                    flush.fill_(float(k))                    # evict the state from L2 between steps
+                    ev[k][0].record(stream)
+                    st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], shuffle=shuf)
+                    ev[k][1].record(stream)
+                    step += 1
+                torch.cuda.synchronize()
+            if single:
+                prof = {kinds[0]: (args.steps, sum(a.elapsed_time(b) for a, b in ev))}
+            else:
+                prof = st.profile()
+                st.set_profiling(False)
+            times = [a.elapsed_time(b) for a, b in ev]
         st.sync()
         if dist:
             dist.barrier()
-        times = [a.elapsed_time(b) for a, b in ev]
         live1 = st.remove_zero()
         ms = float(np.mean(times))
-        sd_steps = 0.5 * (live0 + live1) * args.steps
+        sd_steps = 0.5 * (live0 + live1) * n_timed
         # collisions per step (for the write part of the algorithmic bytes), one extra stats step
         stats = st.step(s["dt"], 42, step, 1, precision=prec, golovin_b=s["golovin_b"], stats=True,
                         shuffle=shuf)
         step += 1
-        launches = st.launches_per_step(shuf) * args.steps
+        launches = (st.launches_per_step(shuf) + (1 if args.graph else 0)) * n_timed
         if surr_info is not None:
             # accuracy against plain FP64 steps of the same seed and step indices
             for k in range(step):
@@ -325,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         bytes_io = xi_p.numel() * 8 + at_p.numel() * 8
 
-    tot_ms, sd_total, e2e_s = combine_ranks(ms * args.steps, sd_steps, e2e_s, dist, world, dev)
+    tot_ms, sd_total, e2e_s = combine_ranks(ms * n_timed, sd_steps, e2e_s, dist, world, dev)
     if rank != 0:
         return
     value = sd_total / (tot_ms * 1e-3)
@@ -340,27 +411,35 @@ def run_ours(args, rank, world, local_rank):
     for v in kern.values():
         v["share"] = v["ms_total"] / tot_k
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    # one launch of the dominant kernel processes every SD of the step (the large-cell kernel holds
-    # the whole box; with tiles only, the tile kernel does), so its algorithmic bytes are the step's
-    achieved = bytes_step / (kern[dom]["ms_per_launch"] * 1e-3) / 1e9
+    # a step of one kernel kind: one launch of it processes every SD of the step, so its algorithmic
+    # bytes are the step's; a step of several kinds: the step's bytes over the whole step's time
+    # (a lower figure than the dominant kernel's own)
+    t_launch = kern[dom]["ms_per_launch"] if len(kern) == 1 else tot_ms / n_timed
+    achieved = bytes_step / (t_launch * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "traffic": _profiled_traffic(dom, args.workload, n),
                 "algorithmic_bytes_per_launch": bytes_step, "bytes_per_unit": 32,
                 "min_bytes_touched_per_launch": bytes_touched,
-                "ms_per_launch": kern[dom]["ms_per_launch"]}
+                "ms_per_launch": kern[dom]["ms_per_launch"],
+                "time_basis": "the kernel's launches" if len(kern) == 1 else "whole step (several kernel kinds)"}
+    state_mb = (16.0 + 1.0) * n / 2 ** 20
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_timed,
+        "warmup": args.warmup, "ms_per_step": tot_ms / n_timed, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "surrogate": "bf16/f32"}[prec],
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_sd": n, "n_cell": len(s["dv"]), "kernel": "gravitational",
+        "config": {"workload": args.workload, "n_sd": n, "n_cell": len(s["dv"]), "kernel": _kernels(s),
                    "precision": prec, "shuffle": shuf, "dt_s": s["dt"], "dV_m3": float(s["dv"][0]), "n0_m3": 1e8,
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}",
-                   "schedule": st.schedule},
+                   "l2": (f"state of {state_mb:.0f} MB " + ("larger than" if state_mb > 126 else "within")
+                          + " the 126 MB L2; flushed between timed " + ("replays" if args.graph else "steps")
+                          + " (256 MB write)"),
+                   "parallelism": f"replicas{world}", "schedule": st.schedule,
+                   "timing": (f"CUDA graph of {args.graph} steps, replays timed" if args.graph
+                              else "each step timed alone")},
         "roofline": roofline,
         "kernels": kern,
-        "e2e": {"value": (sd_total / args.steps) / e2e_s, "unit": UNIT,
+        "e2e": {"value": (sd_total / n_timed) / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -369,7 +448,7 @@ def run_ours(args, rank, world, local_rank):
     if surr_info is not None:
         line["surrogate"] = surr_info
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(s, shuffle=shuf)
+        line["cpu_baseline"] = cpu_baseline(s, shuffle=shuf, name=args.workload)
     print(json.dumps(line), flush=True)
 
 
@@ -379,17 +458,21 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gravitational_box", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="grid_lognormal", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--grid-ny", type=int, default=None,
                     help="rows of a grid workload (default 256); smaller grids for profiling captures")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "surrogate"])
     ap.add_argument("--shuffle", default="prp", choices=["prp", "sort"],
                     help="Step 1 contract: keyed bijection above 256 SDs (prp) or sort by key (sort)")
     ap.add_argument("--schedule", default=None, help="JSON of sdm_schedule fields")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="capture this many steps into one CUDA graph and time its replays")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.graph < 0 or (args.graph and args.steps < args.graph):
+        ap.error("--graph G needs 0 < G <= --steps")
     if args.precision == "surrogate" and args.shuffle != "prp":
         ap.error("the surrogate precision runs under the prp contract only")
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -381,12 +381,12 @@ sdm_status sdm_attach_surrogate(sdm_state* st, const sdm_surrogate* s);
  * Allocation-free single-box step.  (No counterpart in the paper: this is a
  * deployment convenience of the library.)
  *
- * Some callers cannot allocate device memory at all: code that runs where the
- * CUDA allocator may not be called (for example from a host callback enqueued
- * on a stream), processes whose device memory is fully owned by another pool
- * or framework with a hard cap, and latency-critical loops that must not hit
- * the implicit synchronisation of cudaMalloc/cudaFree.  sdm_alloc does not
- * suit them, so this entry point performs one coalescence timestep of a single
+ * Some callers cannot allocate device memory at all: processes whose device
+ * memory is fully owned by another pool or framework with a hard cap (a
+ * cudaMalloc there fails or takes memory the pool counts on), and
+ * latency-critical loops that must not hit the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  sdm_alloc does not suit them, so
+ * this entry point performs one coalescence timestep of a single
  * box (one cell, cell index 0 of the random-number contract) directly on the
  * caller's device arrays, with all scratch memory taken from a fixed array
  * compiled into the library (about 5 MB of device memory, held by every GPU
@@ -404,13 +404,17 @@ sdm_status sdm_attach_surrogate(sdm_state* st, const sdm_surrogate* s);
  * The live SDs must come first in the arrays (as sdm_get_state returns them);
  * removals compact them at the end of the step.  Results are identical to
  * sdm_coalescence_step on a one-cell state holding the same arrays, for both
- * shuffle contracts.  The call enqueues the step, then waits for the stream to
- * read the step's error word, and returns it (SDM_ECAPACITY on a bucket
- * overflow).  The first call on each device looks up the device address of
- * the fixed scratch array (once per device, under a lock); make that first
- * call before capturing any stream.  All calls share the one scratch array:
- * calls that overlap on the GPU (different streams, or several host threads)
- * race with each other and must be serialised by the caller. */
+ * shuffle contracts.  The call copies its small descriptors from host memory,
+ * enqueues the step, then blocks until the stream has drained to read the
+ * step's error word, and returns it (SDM_ECAPACITY on a bucket overflow).
+ * Because it synchronises the stream, it cannot be called while that stream
+ * is being captured into a CUDA graph, nor from a host function or callback
+ * enqueued on a stream (CUDA calls are not allowed there).  Every call looks
+ * up the device address of the fixed scratch array in the current context
+ * and, the first time in a context, uploads the library's constant tables.
+ * All calls share the one scratch array, which keeps the last call's
+ * contents: calls that overlap on the GPU (different streams, or several host
+ * threads) race with each other and must be serialised by the caller. */
 #define SDM_NOALLOC_MAX_SD (1u << 18)
 sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, uint32_t n_attr, uint64_t attr_stride,
                                         uint32_t n_sd, double dv, uint32_t kernel_id,

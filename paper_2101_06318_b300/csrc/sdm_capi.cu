@@ -295,19 +295,51 @@ void fill_pbound_host(float (*t)[PB_SIZE])
 }
 
 // Upload the device tables once per device (first use).
+// Identity of the current device's context (a fresh one after cudaDeviceReset, which reloads the
+// library's module and so its __device__ arrays), from the driver's cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime so that the library links no driver stub.
+sdm_status current_context_id(unsigned long long* id)
+{
+    typedef int (*GetCurrent)(void**);
+    typedef int (*GetId)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    SDM_CUDA(cudaFree(nullptr));                 // makes the device's primary context current
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0) return SDM_ECUDA;
+    return SDM_OK;
+}
+
+// The early exit's bound table (g_pbound) and the dynamic shared-memory limits, set once per
+// context of each device: a context created after cudaDeviceReset gets them again.
 sdm_status ensure_device_tables()
 {
     static std::mutex mu;
-    static bool done[64] = {};
+    static unsigned long long done_ctx[64] = {};   // context id + 1 (0: none yet)
     int dev = 0;
     SDM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SDM_ENOTSUP;
+    unsigned long long ctx = 0;
+    SDM_TRY(current_context_id(&ctx));
     std::lock_guard<std::mutex> lock(mu);
-    if (done[dev]) return SDM_OK;
+    if (done_ctx[dev] == ctx + 1) return SDM_OK;
     static float t[2][PB_SIZE];
     fill_pbound_host(t);
     SDM_CUDA(cudaMemcpyToSymbol(g_pbound, t, sizeof t));
-    done[dev] = true;
+    SDM_TRY(set_smem_limits());
+    done_ctx[dev] = ctx + 1;
     return SDM_OK;
 }
 
@@ -374,6 +406,17 @@ BigBook big_book(const sdm_state* st)
 {
     uint32_t* tw = st->d_big_removed + big_ticket_word(st->n_big);
     return BigBook{(unsigned long long*)tw, st->d_big_removed, st->n_big, tw + 2};
+}
+
+// Clears the device error word after the host has read it.  A grid barrier that gave up
+// (ERR_TIMEOUT) left its arrival count behind, which would release the next barrier early:
+// it is reset too (the step that timed out left the state unspecified; see sdm.h).
+sdm_status clear_device_error(sdm_state* st, uint32_t e)
+{
+    SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+    if ((e & ERR_TIMEOUT) && st->d_big_removed)
+        SDM_CUDA(cudaMemsetAsync(big_book(st).sync + 2, 0, 2 * sizeof(uint32_t), st->stream));
+    return SDM_OK;
 }
 
 // the state arrays a kernel that moves SDs needs
@@ -520,7 +563,7 @@ sdm_status build_layout(sdm_state* st)
         SDM_TRY(upload(st, &st->d_cta_first, first));
     }
     if (!bigs.empty()) {
-        const size_t words = big_ticket_word(bigs.size()) + 2 + 4;   // flags, ticket, PRP sync words
+        const size_t words = big_ticket_word(bigs.size()) + 2 + BIG_SYNC_WORDS;   // flags, ticket, PRP sync words
         SDM_TRY(dev_alloc(st, (void**)&st->d_big_removed, sizeof(uint32_t) * words, true));
         SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * words, st->stream));
     }
@@ -1026,7 +1069,7 @@ sdm_status sdm_set_state(sdm_state* st, const uint64_t* xi, const double* attr, 
         SDM_CUDA(cudaGetLastError());
     }
     if (st->d_big_removed)    // the new state is compact: no large cell awaits compaction
-        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (big_ticket_word(st->n_big) + 2 + 4),
+        SDM_CUDA(cudaMemsetAsync(st->d_big_removed, 0, sizeof(uint32_t) * (big_ticket_word(st->n_big) + 2 + BIG_SYNC_WORDS),
                                  st->stream));
     st->big_deferred = false;
     const uint32_t cgrid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_cell + 255) / 256, 4 * st->n_sm));
@@ -1082,7 +1125,7 @@ sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* p, uint32_
         stats->sum_gamma = h[3];
         stats->n_fp64 = h[4];
         if (e) {
-            SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+            SDM_TRY(clear_device_error(st, e));
             return err_to_status(e);
         }
     }
@@ -1387,7 +1430,7 @@ sdm_status sdm_sync(sdm_state* st)
     SDM_CUDA(cudaMemcpyAsync(&e, st->d_err, sizeof e, cudaMemcpyDeviceToHost, st->stream));
     SDM_CUDA(cudaStreamSynchronize(st->stream));
     if (e) {
-        SDM_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(uint32_t), st->stream));
+        SDM_TRY(clear_device_error(st, e));
         SDM_CUDA(cudaStreamSynchronize(st->stream));
         return err_to_status(e);
     }
@@ -1455,7 +1498,7 @@ constexpr size_t NA_OFF_CELL = 0;        // BigCell
 constexpr size_t NA_OFF_DV = 64;         // double dv
 constexpr size_t NA_OFF_KID = 72;        // uint8 kernel id
 constexpr size_t NA_OFF_ERR = 128;       // uint32 error word
-constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, removal flag, end-of-step ticket
+constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, removal flag, end-of-step ticket, sync words
 constexpr size_t NA_OFF_XMAX = 192;      // uint64 largest multiplicity of the box
 constexpr size_t NA_OFF_CHUNKS = 256;
 constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
@@ -1467,26 +1510,16 @@ constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_B
 // one per loaded library and device; its contents persist between calls
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
-
-// device address of the scratch array on the current device (looked up once per device)
+// Device address of the scratch array in the current device's context, looked up on every call
+// (a context created after cudaDeviceReset holds the array at a new address), after the
+// per-context set-up of the bound table and the shared-memory limits.
 sdm_status noalloc_scratch(unsigned char** out)
 {
-    int dev = 0;
-    SDM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return SDM_ENOTSUP;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return SDM_ECUDA;
-        SDM_TRY(set_smem_limits());
-        SDM_TRY(ensure_device_tables());
-        g_na_ptr[dev] = (unsigned char*)p;
-    }
-    *out = g_na_ptr[dev];
+    SDM_TRY(ensure_device_tables());
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) return SDM_ECUDA;
+    *out = (unsigned char*)p;
     return SDM_OK;
 }
 
@@ -1541,7 +1574,9 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     SDM_CUDA(cudaMemcpyAsync(base + NA_OFF_BBIG, bucket_desc, sizeof(BucketDesc) * nb, cudaMemcpyHostToDevice,
                              stream));
     SDM_CUDA(cudaMemsetAsync(base + NA_OFF_CURSOR, 0, 4 * (NA_MAX_BUCKETS + 1), stream));   // cursors and ticket
-    uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);        // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket
+    // [0..1] cell_start, [2] n_live, [3] flag, [4..5] 64-bit ticket, [6..13] the PRP sync words
+    uint32_t* live = (uint32_t*)(base + NA_OFF_LIVE);
+    static_assert(NA_OFF_LIVE + 4 * (6 + BIG_SYNC_WORDS) <= NA_OFF_XMAX, "sync words overlap the bound");
     live_count_kernel<<<1, 32, 0, stream>>>(xi, live, 1, live + 2);
     unsigned long long* d_xmax = (unsigned long long*)(base + NA_OFF_XMAX);      // the early exit's bound
     SDM_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned long long), stream));
@@ -1577,7 +1612,8 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         SDM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
-        big_prp_kernel<false><<<prp_grid_size(n_quads, n_sm, PRP_THREADS), PRP_THREADS, 0, stream>>>(a, L, bb);
+        big_prp_kernel<false, PRP_THREADS, false><<<prp_grid_size(n_quads, n_sm, PRP_THREADS), PRP_THREADS, 0, stream>>>(
+            a, L, bb);
         SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, live + 6, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);

@@ -960,10 +960,14 @@ struct BigBook {
                                   // finished; high word: how many of them removed an SD
     uint32_t* removed;            // [n_big] an SD of this cell was removed during the step
     uint32_t n_big;
-    uint32_t* sync;               // PRP contract: [0] some large cell awaits compaction (its
-                                  // flag in removed[] is set); [1], [2] grid barrier count and
-                                  // generation
+    uint32_t* sync;               // PRP contract, eight words (see big_prp_kernel):
+                                  // [0], [1] some large cell awaits compaction, written by the
+                                  //   launches of even and odd serial number respectively;
+                                  // [2], [3] grid barrier count and generation;
+                                  // [4..5] 64-bit arrival word: high half the serial number of
+                                  //   the current launch, low half its CTAs that started
 };
+constexpr uint32_t BIG_SYNC_WORDS = 8;
 
 constexpr uint32_t GRID_BARRIER_SPIN_LIMIT = 1u << 22;   // ~0.4 s of polling at >= 100 ns each
 
@@ -1366,7 +1370,10 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
 }
 
 // THREADS: CTA size (the same registers and warps per SM for both sizes)
-template <bool SURR, uint32_t THREADS = PRP_THREADS>
+// STEP0: the launch may find cells flagged by the previous launch and compact them first (the
+// allocating path); false where a compaction kernel always follows the step (the
+// allocation-free call), so no launch ever starts with a flagged cell.
+template <bool SURR, uint32_t THREADS = PRP_THREADS, bool STEP0 = true>
 __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / THREADS) big_prp_kernel(StepArgs a,
                                                                                                      BigLaunch L,
                                                                                                      BigBook bk)
@@ -1415,22 +1422,41 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
             if (lane < ED_LINES + 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
         }
     }
-    // Step 0 for the large cells that lost SDs in the previous step: each such cell is compacted
-    // by one block while the grid waits at a barrier (the launch is cooperative).  The flag is
-    // the same word for every thread and nobody clears it before the barrier.
-    if (__ldcg(bk.sync) != 0u) {
-        for (uint32_t b = blockIdx.x; b < L.n_big; b += gridDim.x) {
-            if (!__ldcg(&bk.removed[b])) continue;
-            const BigCell C = L.cells[b];
-            const uint32_t n_old = min(__ldcg(&a.n_live[C.cell]), C.width);
-            const uint32_t n_new = block_compact_cell(a, C.slot_begin, n_old, wt);
-            if (tid == 0) {
-                a.n_live[C.cell] = n_new;
-                bk.removed[b] = 0;
-            }
+    // Step 0 for the large cells that lost SDs in the previous launch: each such cell is compacted
+    // by one block while the grid waits at a barrier (the launch is cooperative).  CTAs of this
+    // launch may finish, and flag their cells, before other CTAs of it have started, so the
+    // pending word a launch reads is never one it writes: launch number k (taken from the arrival
+    // word: every CTA adds one, the last to arrive moves the count into the serial number) reads
+    // the word of parity k+1, written by launch k-1, and writes the word of parity k.  Nobody
+    // writes the word it reads before every CTA has passed the barrier; then block 0 clears it.
+    __shared__ uint32_t par_s, pend_s;
+    uint32_t par = 0;
+    if (STEP0) {
+        if (tid == 0) {
+            const uint32_t p0 = __ldcg(bk.sync), p1 = __ldcg(bk.sync + 1);
+            unsigned long long* arr = reinterpret_cast<unsigned long long*>(bk.sync + 4);
+            const unsigned long long old = atomicAdd(arr, 1ull);
+            if ((uint32_t)old == gridDim.x - 1u) atomicAdd(arr, (1ull << 32) - gridDim.x);
+            const uint32_t k = (uint32_t)(old >> 32) & 1u;
+            par_s = k;
+            pend_s = k ? p0 : p1;
         }
-        if (!grid_barrier(bk.sync + 1, bk.sync + 2, a.err)) return;
-        if (blockIdx.x == 0 && tid == 0) *(volatile uint32_t*)bk.sync = 0u;
+        __syncthreads();
+        par = par_s;
+        if (pend_s != 0u) {
+            for (uint32_t b = blockIdx.x; b < L.n_big; b += gridDim.x) {
+                if (!__ldcg(&bk.removed[b])) continue;
+                const BigCell C = L.cells[b];
+                const uint32_t n_old = min(__ldcg(&a.n_live[C.cell]), C.width);
+                const uint32_t n_new = block_compact_cell(a, C.slot_begin, n_old, wt);
+                if (tid == 0) {
+                    a.n_live[C.cell] = n_new;
+                    bk.removed[b] = 0;
+                }
+            }
+            if (!grid_barrier(bk.sync + 2, bk.sync + 3, a.err)) return;
+            if (blockIdx.x == 0 && tid == 0) *(volatile uint32_t*)(bk.sync + (par ^ 1u)) = 0u;
+        }
     }
     PairQueue& Q = pq[warp];
     uint32_t qcnt = 0;                              // queued pairs of this warp (warp-uniform)
@@ -1490,8 +1516,8 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    // cells that lost SDs are compacted at the start of the next step (or by big_compact_kernel)
-    if (__any_sync(0xffffffffu, ls.removed != 0) && lane == 0) atomicOr(bk.sync, 1u);
+    // cells that lost SDs are compacted at the start of the next launch (or by big_compact_kernel)
+    if (__any_sync(0xffffffffu, ls.removed != 0) && lane == 0) atomicOr(bk.sync + par, 1u);
 }
 
 // Step 0 for the large cells of the PRP contract outside a PRP step: compacts,
@@ -1507,7 +1533,7 @@ __global__ void __launch_bounds__(256) big_compact_kernel(StepArgs a, const BigC
 {
     __shared__ uint32_t wt[40];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (blockIdx.x == 0 && threadIdx.x == 0) *sync = 0u;         // every flagged cell is handled below
+    if (blockIdx.x == 0 && threadIdx.x == 0) sync[0] = sync[1] = 0u;   // every flagged cell is handled below
     for (uint32_t b = blockIdx.x; b < n_big; b += gridDim.x) {
         const uint32_t flag = *(volatile uint32_t*)&removed[b];   // the same in every thread
         if (!flag) continue;

@@ -151,6 +151,35 @@ def random_cells(n_cell, mean_per_cell, seed, kernel_mix=True, dead_fraction=0.0
     return _state(xi, v, counts, dv, kid, "random_cells", seed=seed)
 
 
+def removal_box(n_sd, seed, xi_max=3, p_median=0.5, kernel_id=GOLOVIN, golovin_b=GOLOVIN_B):
+    """One cell of small multiplicities (uniform in 1..xi_max) and lognormal
+    volumes (median radius 15 um, sigma_g 1.4), its volume dV chosen so that
+    the median pair's scaled probability is about p_median: coalescences of
+    two SDs of multiplicity 1 remove an SD, so removals happen every step."""
+    rng = np.random.default_rng(seed)
+    xi = rng.integers(1, xi_max + 1, n_sd).astype(np.uint64)
+    v = lognormal_volumes(rng, n_sd, 15e-6, 1.4)
+    v_med = FOUR_PI_OVER_THREE * (15e-6) ** 3
+    if kernel_id == GOLOVIN:
+        k_med = golovin_b * 2.0 * v_med
+    else:  # a gravitational pair of median radius and a 1.4x larger partner, roughly 1e-12 m^3/s
+        k_med = 1.0e-12
+    dv = k_med * xi_max * max(n_sd - 1, 1) / p_median
+    return _state(xi, v, [n_sd], dv, kernel_id, "removal_box", golovin_b=golovin_b, seed=seed, n_sd=n_sd)
+
+
+def concat_states(states, name="concat"):
+    """One multi-cell state holding the cells of several states in order."""
+    xi = np.concatenate([t["xi"] for t in states])
+    v = np.concatenate([t["v"] for t in states])
+    counts = np.concatenate([np.diff(t["cell_start"].astype(np.int64)) for t in states])
+    dv = np.concatenate([t["dv"] for t in states])
+    kid = np.concatenate([t["kernel_id"] for t in states])
+    b = {t["golovin_b"] for t in states}
+    assert len(b) == 1, "one Golovin constant per state"
+    return _state(xi, v, counts, dv, kid, name, dt=states[0]["dt"], golovin_b=b.pop())
+
+
 WORKLOADS = {
     "golovin_box": golovin_box,
     "gravitational_box": gravitational_box,

@@ -254,6 +254,32 @@ def test_many_large_cells_bitexact():
     assert ost["n_collisions"] == gst["n_collisions"]
 
 
+@pytest.mark.parametrize("layout", ["few", "many"])
+def test_prp_steps_with_removals_every_step(layout):
+    """Large cells that lose SDs in every step, under the PRP contract: each launch compacts the
+    cells the previous launch flagged (Step 0) behind its grid barrier.  Thirty one-step calls,
+    then thirty steps in one call; the device error word is read after each call (a barrier
+    that gave up would show as SDM_ETIMEOUT) and the state matches the oracle bit for bit."""
+    if layout == "few":       # four large cells (CTAs of 128 threads) and one small cell
+        parts = [inputs.removal_box(n, seed=n, p_median=0.2) for n in (300, 2000, 5000, 70000)]
+    else:                     # 70 large cells (CTAs of 64 threads)
+        parts = [inputs.removal_box(1100 + 29 * k, seed=k, p_median=0.2) for k in range(70)]
+    s = inputs.concat_states(parts)
+    o = _oracle_system(s)
+    g = _gpu_state(s, schedule=dict(tile_slots=256))
+    for step in range(30):
+        g.step(s["dt"], 42, step, 1, golovin_b=s["golovin_b"])
+        g.sync()                                   # raises on a device error
+    g.step(s["dt"], 42, 30, 30, golovin_b=s["golovin_b"])
+    g.sync()
+    ost = o.run(s["dt"], 42, 0, 60)
+    xi, at, _ = g.get_state()
+    assert g.check() == (0, 0)
+    g.close()
+    _assert_bitexact(o, xi, at)
+    assert ost["n_removed"] > len(s["xi"]) // 4
+
+
 def test_edge_cases():
     # n_sd = 2 (one pair), 3 (odd), all-dead cell, huge p (caps bind), xi near 2^53
     xi = np.array([5, 5, 7, 1, 9, 0, 0, (1 << 53) - 1, 3], np.uint64)
