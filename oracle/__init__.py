@@ -98,6 +98,7 @@ def lib():
             L.sdmo_prp_keys.argtypes = [u64, u32, u32, _p(u32)]
             L.sdmo_prp.argtypes = [u32, u32, _p(u32)]
             L.sdmo_prp.restype = u32
+            L.sdmo_prp_perm.argtypes = [u32, _p(u32), _p(u32)]
             L.sdmo_spectrum.argtypes = [u64, u32, _p(u32), _p(u64), _p(f64), _p(f64), u32, u32,
                                         _p(f64), u32, f64, _p(f64)]
             L.sdmo_spectrum.restype = i32
@@ -189,6 +190,14 @@ def prp_keys(seed, cell, step):
 def prp(q, n, K):
     K = np.ascontiguousarray(K, np.uint32)
     return int(lib().sdmo_prp(int(q), int(n), _ptr(K, C.c_uint32)))
+
+
+def prp_perm(n, K):
+    """The PRP shuffle's whole permutation of [0, n): out[q] = prp(q, n, K)."""
+    K = np.ascontiguousarray(K, np.uint32)
+    out = np.empty(int(n), np.uint32)
+    lib().sdmo_prp_perm(int(n), _ptr(K, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
 
 
 def i1e(x):

@@ -210,6 +210,13 @@ uint32_t sdmo_prp(uint32_t q, uint32_t n, const uint32_t K[SDMO_PRP_ROUNDS])
     return e;
 }
 
+/* The whole permutation: out[q] = P(q) for q < n (a loop over sdmo_prp, for tests at large n). */
+void sdmo_prp_perm(uint32_t n, const uint32_t K[SDMO_PRP_ROUNDS], uint32_t* out)
+{
+    uint32_t q;
+    for (q = 0; q < n; ++q) out[q] = sdmo_prp(q, n, K);
+}
+
 uint64_t sdmo_phi_u53(uint64_t seed, uint32_t cell, uint32_t step, uint32_t m)
 {
     uint32_t key[2], ctr[4], x[4];

@@ -8,9 +8,9 @@
 * Exact outcome distribution of a 3-SD cell (one candidate pair, any p) by
   enumeration: pair chosen uniformly, gamma = floor(p) + 1 with probability
   frac(p) (Step 3).
-* Golovin closed forms (Sec. 4): I1e against scipy.special.ive, the analytic
-  pdf's normalisation and mass, total number N0 V exp(-N0 b vbar t), and the
-  SDM mass spectrum against the analytic one.
+* Golovin closed forms (Sec. 4): I1e against scipy.special.ive and the
+  analytic pdf's normalisation and mass (the SDM's number and spectrum against
+  them, one ensemble per shuffle contract, are in test_oracle_prp_pins.py).
 """
 import math
 from collections import Counter
@@ -146,54 +146,6 @@ def test_golovin_pdf_initial_condition_and_moments():
         mass = np.trapezoid(f * v * v, np.log(v))
         assert num == pytest.approx(1 - tau, rel=2e-3)
         assert mass == pytest.approx(vbar, rel=2e-3)
-
-
-def _golovin_run(seed, t_end, shuffle):
-    s = inputs.golovin_box()
-    sys_ = oracle.System(s["xi"], s["v"], s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle)
-    sys_.run(1.0, seed, 0, t_end)
-    return sys_
-
-
-def _smooth_twice(y):
-    """Centred 5-bin running mean applied twice (window shrinks at the edges)."""
-    for _ in range(2):
-        out = np.empty_like(y)
-        for i in range(len(y)):
-            lo, hi = max(0, i - 2), min(len(y), i + 3)
-            out[i] = y[lo:hi].mean()
-        y = out
-    return y
-
-
-@pytest.mark.slow
-def test_golovin_sdm_matches_analytic_spectrum_and_number():
-    vbar, n0, b, V = inputs.GOLOVIN_VBAR, inputs.GOLOVIN_N0, inputs.GOLOVIN_B, inputs.GOLOVIN_DV
-    r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 101))
-    rc = np.sqrt(r_edges[1:] * r_edges[:-1])
-    t = 3600
-    specs, numbers = [], []
-    for seed, shuffle in ((42, "prp"), (43, "sort")):
-        sys_ = _golovin_run(seed, t, shuffle)
-        specs.append(sys_.spectrum(r_edges))
-        numbers.append(sys_.totals()[0])
-        assert sys_.totals()[2] == pytest.approx(
-            float(np.sum(inputs.golovin_box()["xi"].astype(float) * inputs.golovin_box()["v"])), rel=1e-12)
-    tau_decay = math.exp(-n0 * b * vbar * t)
-    for N in numbers:
-        assert N / (n0 * V) == pytest.approx(tau_decay, rel=0.1)
-    sdm = _smooth_twice(np.mean(specs, axis=0))
-    vc = 4 / 3 * math.pi * rc ** 3
-    ana = np.array([3 * 1000.0 * x * x * n0 * oracle.golovin_phi(x, t, vbar, n0, b) for x in vc])
-    # tolerances from an ensemble of oracle runs (4 pairs of seeds): the median relative
-    # deviation over bins above 5 % of the peak was 0.045-0.10, the maximum over bins
-    # above 20 % of the peak 0.16-0.25 (the far tails are shot-noise dominated)
-    sel = ana > 0.05 * ana.max()
-    rel = np.abs(sdm[sel] - ana[sel]) / ana[sel]
-    core = ana[sel] > 0.2 * ana.max()
-    assert np.median(rel) < 0.15 and rel[core].max() < 0.4, (np.median(rel), rel[core].max())
-    # the peak sits in the same place
-    assert abs(int(np.argmax(sdm)) - int(np.argmax(ana))) <= 4
 
 
 # --------------------------------------------------------------------------
