@@ -209,10 +209,10 @@ sdm_status sdm_get_state(sdm_state* st, uint64_t* xi, double* attr, uint32_t* ce
  * Under SDM_SHUFFLE_SORT a large cell's SDs are distributed over buckets of
  * about bucket_target SDs by the top bits of their keys; a bucket holds its
  * mean count plus ten standard deviations plus 32 records.  A step whose keys
- * overflow a bucket (probability below 1e-20 per bucket and step) records
- * SDM_ECAPACITY in the device error word, read by sdm_sync or the next call
- * that synchronises; SDs that did not fit sat that step out, so the step
- * does not follow the random-number contract (no memory is overrun). */
+ * overflow a bucket of a cell (probability below 1e-20 per bucket and step)
+ * records SDM_ECAPACITY in the device error word, read by sdm_sync or the
+ * next call that synchronises, and leaves that cell unchanged in that step
+ * (no memory is overrun; the other cells are stepped). */
 sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* params, uint32_t n_steps,
                                 sdm_step_stats* stats);
 
@@ -272,6 +272,26 @@ sdm_status sdm_autotune(sdm_state* st, const sdm_step_params* params, uint32_t n
 /* Wait for all work enqueued on the state's stream; returns the first error
  * latched by a kernel since the last sdm_sync (then clears it), or SDM_ECUDA. */
 sdm_status sdm_sync(sdm_state* st);
+
+/* Failure-path self-tests (no counterpart in the paper; they exercise the
+ * library's own error handling without faulting the GPU).
+ *
+ * sdm_debug_wait_timeout: a cooperative launch of a few blocks meets at the
+ * library's grid barrier (the bounded wait a PRP step uses before its Step 0
+ * compaction), giving up after spin_limit polls of at least 100 ns each; with
+ * withhold != 0 the last block never arrives, so the others' wait runs out,
+ * records SDM_ETIMEOUT in the state's device error word and returns.  The
+ * next sdm_sync reports it (and clears it); the state's contents are not
+ * touched and the state stays usable.  Asynchronous.  SDM_EINVAL for a NULL
+ * state or spin_limit 0.
+ *
+ * sdm_debug_bucket_capacity: lower the SORT contract's records per bucket of
+ * the current layout to cap (a multiple of 32, at least 32, at most the
+ * current capacity; SDM_EINVAL otherwise), so that a test can make a bucket
+ * overflow.  The next layout change (sdm_set_schedule, sdm_init_state*)
+ * restores the computed capacity. */
+sdm_status sdm_debug_wait_timeout(sdm_state* st, uint32_t spin_limit, int withhold);
+sdm_status sdm_debug_bucket_capacity(sdm_state* st, uint32_t cap);
 
 /* Release the state and the device memory the library allocated. NULL is a no-op. */
 void sdm_free(sdm_state* st);

@@ -78,6 +78,7 @@ struct sdm_state {
     uint64_t* d_xi = nullptr;
     double* d_attr = nullptr;
     uint8_t* d_vbin = nullptr;               // [cap] early-exit bin of each slot's volume
+    unsigned long long* d_cell_xmax = nullptr;   // [n_cell] multiplicity bound of the cells stepped by one warp
     uint32_t* d_cell_start = nullptr;
     double* d_dv = nullptr;
     uint8_t* d_kid = nullptr;
@@ -94,7 +95,7 @@ struct sdm_state {
     uint32_t* d_wcells = nullptr;            // cells of at most WC_MAX slots, one warp each
     char* rb_buf = nullptr;                  // scratch of sdm_rebucket, kept between calls
     size_t rb_bytes = 0;
-    uint32_t n_wcells = 0, wc_grid = 0;
+    uint32_t n_wcells = 0, wc_grid = 0, wc_grid_sort = 0;
     TileLayout tile_L{};
     BigCell* d_big = nullptr;
     uint32_t n_big = 0;
@@ -215,7 +216,7 @@ void free_layout(sdm_state* st)
     st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
     st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
-    st->d_wcells = nullptr; st->n_wcells = st->wc_grid = 0;
+    st->d_wcells = nullptr; st->n_wcells = st->wc_grid = st->wc_grid_sort = 0;
 }
 
 template <typename T>
@@ -369,9 +370,16 @@ uint32_t prp_grid_size(uint32_t n_quads, int n_sm, uint32_t threads)
     return std::max<uint32_t>(1, std::min<uint32_t>(wave, (n_quads + 31) / 32));
 }
 
-// per large cell: the multiplicity bound of the early exit, from the current state
+// the early exit's data from the current state: per large cell and per cell stepped by one warp,
+// the multiplicity bound; the volume bin of every slot of both
 sdm_status refresh_big_bounds(sdm_state* st)
 {
+    if (st->n_wcells) {
+        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_wcells + 7) / 8, 8 * st->n_sm));
+        cell_bounds_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_cell_start, st->d_wcells,
+                                                        st->n_wcells, st->d_cell_xmax, st->d_vbin);
+        SDM_CUDA(cudaGetLastError());
+    }
     if (!st->n_big) return SDM_OK;
     SDM_CUDA(cudaMemsetAsync(st->d_big_xmax, 0, sizeof(unsigned long long) * st->n_big, st->stream));
     big_xmax_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_vbin, st->d_big, st->d_chunks,
@@ -543,9 +551,13 @@ sdm_status build_layout(sdm_state* st)
     st->n_wcells = (uint32_t)wcells.size();
     if (st->n_wcells) {
         int per_sm = 0;
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false>, 32 * WC_WARPS, 0));
         const uint32_t need = (st->n_wcells + WC_WARPS - 1) / WC_WARPS;
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false, WC_SORT_PRP>,
+                                                               32 * WC_WARPS, 0));
         st->wc_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false, WC_MAX>,
+                                                               32 * WC_WARPS, 0));
+        st->wc_grid_sort = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
     }
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
@@ -735,6 +747,23 @@ __global__ void check_keys_kernel(const double* __restrict__ vol, const uint8_t*
     if (b) atomicAdd(bad, b);
 }
 
+// the cells stepped by one warp: slots whose stored volume bin differs from the volume's, or whose
+// multiplicity exceeds the cell's bound (one warp per cell)
+__global__ void check_wcell_keys_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ vol,
+                                        const uint8_t* __restrict__ vbin, const uint32_t* __restrict__ cs,
+                                        const uint32_t* __restrict__ cells, uint32_t n_cells,
+                                        const unsigned long long* __restrict__ xmax, unsigned long long* bad)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long b = 0;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_cells; k += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t c = cells[k];
+        for (uint32_t i = cs[c] + lane; i < cs[c + 1]; i += 32)
+            b += (vbin[i] != (uint8_t)vbin_of(vol[i])) || (xi[i] > xmax[c]);
+    }
+    if (b) atomicAdd(bad, b);
+}
+
 // live count of every cell: the length of the live prefix of its slots
 __global__ void live_count_kernel(const uint64_t* __restrict__ xi, const uint32_t* __restrict__ cs, uint32_t n_cell,
                                   uint32_t* n_live)
@@ -828,6 +857,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.d_step = p->d_step;
     a.shuffle = p->shuffle;
     a.n_live = st->d_n_live;
+    a.cell_xmax = st->d_cell_xmax;
     a.stats = with_stats ? st->d_stats : nullptr;
     a.err = st->d_err;
     a.surr = st->d_surr;
@@ -839,8 +869,13 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             ProfScope ps(st, 0);
             const bool surr = p->precision == SDM_PREC_SURROGATE;
             if (st->n_wcells) {
-                auto wk = surr ? warp_cells_kernel<true> : warp_cells_kernel<false>;
-                wk<<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
+                if (p->shuffle == SDM_SHUFFLE_SORT) {     // lists up to 512 SDs sorted by key
+                    auto wk = surr ? warp_cells_kernel<true, WC_MAX> : warp_cells_kernel<false, WC_MAX>;
+                    wk<<<st->wc_grid_sort, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
+                } else {                                  // above 256 SDs the keyed bijection
+                    auto wk = surr ? warp_cells_kernel<true, WC_SORT_PRP> : warp_cells_kernel<false, WC_SORT_PRP>;
+                    wk<<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
+                }
             }
             if (st->n_tiles) {
                 uint32_t grid = st->n_tiles;
@@ -933,6 +968,7 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(4 * ((size_t)n_cell + 1) + 256) + round256(8 * (size_t)n_cell + 256) + round256(n_cell + 256);
     b += 4 * round256(512) + round256(4 * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 260);
+    b += round256(8 * (size_t)n_cell + 256);                    // multiplicity bound per cell
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 256);   // cells stepped by one warp each
@@ -978,6 +1014,7 @@ sdm_status sdm_alloc(sdm_state** out, uint64_t cap, uint32_t n_cell, uint32_t n_
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_acc, 64, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_work, 64, false);
     if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_n_live, sizeof(uint32_t) * n_cell, false);
+    if (s == SDM_OK) s = dev_alloc(st, (void**)&st->d_cell_xmax, sizeof(unsigned long long) * n_cell, false);
     if (s == SDM_OK && cudaMemsetAsync(st->d_err, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
     if (s == SDM_OK && cudaMemsetAsync(st->d_work, 0, 64, st->stream) != cudaSuccess) s = SDM_ECUDA;
     if (s == SDM_OK && cudaMemsetAsync(st->d_xi, 0, sizeof(uint64_t) * cap, st->stream) != cudaSuccess) s = SDM_ECUDA;
@@ -1164,6 +1201,13 @@ sdm_status sdm_check_state(sdm_state* st, uint64_t* n_bad_live, uint64_t* n_bad_
     if (st->n_big) {
         check_keys_kernel<<<st->n_chunks, 256, 0, st->stream>>>(st->d_attr, st->d_vbin, st->d_big, st->d_chunks,
                                                                 st->d_acc + 1);
+        SDM_CUDA(cudaGetLastError());
+    }
+    if (st->n_wcells) {
+        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((st->n_wcells + 7) / 8, 8 * st->n_sm));
+        check_wcell_keys_kernel<<<grid, 256, 0, st->stream>>>(st->d_xi, st->d_attr, st->d_vbin, st->d_cell_start,
+                                                              st->d_wcells, st->n_wcells, st->d_cell_xmax,
+                                                              st->d_acc + 1);
         SDM_CUDA(cudaGetLastError());
     }
     unsigned long long h[2] = {0, 0};
@@ -1434,6 +1478,36 @@ sdm_status sdm_sync(sdm_state* st)
         SDM_CUDA(cudaStreamSynchronize(st->stream));
         return err_to_status(e);
     }
+    return SDM_OK;
+}
+
+// The self-test's barrier words are words 8 and 9 of the state's 64-byte error block (word 0 is
+// the error word; the others are unused).
+sdm_status sdm_debug_wait_timeout(sdm_state* st, uint32_t spin_limit, int withhold)
+{
+    if (!st || spin_limit == 0) return SDM_EINVAL;
+    uint32_t* words = st->d_err + 8;
+    SDM_CUDA(cudaMemsetAsync(words, 0, 2 * sizeof(uint32_t), st->stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4);
+    cfg.blockDim = dim3(32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    SDM_CUDA(cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, words, words + 1, st->d_err, spin_limit,
+                                (uint32_t)(withhold != 0)));
+    return SDM_OK;
+}
+
+sdm_status sdm_debug_bucket_capacity(sdm_state* st, uint32_t cap)
+{
+    if (!st || !st->initialised || cap < 32 || (cap & 31u) || cap > st->bucket_cap) return SDM_EINVAL;
+    st->bucket_cap = cap;
+    st->fin_L.cap = cap;
     return SDM_OK;
 }
 

@@ -1,25 +1,38 @@
 // sdm_kernels.cuh -- CUDA kernels of one SDM coalescence timestep (sm_103a).
 //
-// A timestep (Fig. "fig:algo") is executed by two kinds of launches, both
-// fusing Steps 0-3 so that the state is read once and only changed
-// super-droplets are written:
+// A timestep (Fig. "fig:algo") runs each cell's Steps 0-3 inside one kernel
+// kind chosen by the cell's width, so that only the data a decision needs is
+// read and only changed super-droplets are written:
 //
-//  tile_step_kernel   one CTA per tile of consecutive small cells (all slots
-//                     of the tile fit in shared memory): load xi and v,
-//                     generate the Philox keys, sort each cell's live SDs by
-//                     (key, slot) with a counting sort on the key's top bits
-//                     plus an exact rank inside each bucket, pair neighbours,
-//                     evaluate eq. (p) and gamma, and write the updated pairs.
+//  warp_cells_kernel  one warp per cell of at most 512 slots (the grid
+//                     workloads): the cell's one-byte volume bins into shared
+//                     memory, the shuffled list (Philox keys and a counting
+//                     sort for up to 256 live SDs, else the keyed bijection
+//                     from per-cell round tables), then per pair phi, the early
+//                     exit against a bound of p, and a queue of the surviving
+//                     pairs that the warp evaluates 32 at a time across its
+//                     cells; cells that lost an SD are compacted stably once
+//                     their queued pairs are done.
+//  tile_step_kernel   one CTA per run of cells between 512 slots and the
+//                     schedule's tile size: the same steps with the tile's
+//                     multiplicities and volumes in shared memory.
+//  big_prp_kernel     cells above the tile size under the PRP contract: one
+//                     cooperative wave over all of them, each thread mapping
+//                     list positions through the keyed bijection, gathering the
+//                     volume bins, settling most pairs by the early exit and
+//                     queueing the rest per warp; Step 0 of cells flagged by the
+//                     previous launch runs first, behind a bounded grid barrier.
 //  big_scatter_kernel / big_finish_kernel
-//                     cells too large for one CTA: the first pass scatters
-//                     (key, slot) records into fixed-capacity buckets given by
-//                     the key's top bits (no global scan needed), the second
-//                     sorts each bucket in shared memory, works out the
-//                     bucket's offset in the cell's sorted list from the bucket
-//                     counts, and processes the pairs (gathering xi and v).
+//                     the same cells under the SORT contract: the first pass
+//                     scatters (key, position) records into fixed-capacity
+//                     buckets by the key's top bits, the second orders each
+//                     bucket, locates it in the cell's order from the bucket
+//                     offsets, and processes the pairs (gathering the volume
+//                     bins, then multiplicity and volume of the queued pairs).
 //
-// Both orders are the same total order of the cell, (key, slot) ascending, so
-// the tile size, bucket width and launch shape never change a result.
+// Every path realises the same shuffled list of the random-number contract
+// (sort by (key, position), or the keyed bijection), so the tile size, bucket
+// width and launch shape never change a result.
 #pragma once
 #include "sdm_math.cuh"
 #include "sdm_surrogate.cuh"
@@ -39,8 +52,8 @@ constexpr uint32_t DEAD = 0xffffffffu;
 struct StepArgs {
     uint64_t* xi;
     double* attr;               // [n_attr][stride], attr 0 = volume
-    uint8_t* vbin;              // [stride] vbin_of(volume) of every slot of the large cells, kept
-                                // current by every writer of the volumes; nullptr: not kept
+    uint8_t* vbin;              // [stride] vbin_of(volume) of every slot, kept current by every
+                                // writer of the volumes; nullptr: not kept
     uint64_t stride;
     uint32_t n_attr;
     uint32_t precision;
@@ -56,6 +69,7 @@ struct StepArgs {
     uint32_t shuffle;           // SHUFFLE_PRP or SHUFFLE_SORT
     const uint32_t* d_step;
     uint32_t* n_live;           // [n_cell] live SDs per cell (a prefix of its slots)
+    const unsigned long long* cell_xmax;   // [n_cell] bound of the cell's multiplicities (small cells)
     unsigned long long* stats;  // [5] or nullptr
     uint32_t* err;
     const SurrogateDev* surr;   // device copy; used when precision == PREC_SURROGATE
@@ -723,26 +737,44 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? SDM_TILE_MIN_BLOCKS : 1) t
 // ---------------------------------------------------------------------------
 constexpr uint32_t WC_MAX = 512;          // slots of a cell stepped by one warp
 constexpr uint32_t WC_WARPS = 4;          // warps per block
-constexpr uint32_t WC_QCAP = 96;          // queued pairs (< 32 left + 2 x 32 new)
+constexpr uint32_t WC_QCAP = 64;          // queued pairs (< 32 left + 32 new)
+constexpr uint32_t WC_TAB = 32;           // entries per round table of the bijection (A, B <= 32 for n <= 512)
+constexpr uint32_t WC_SORT_PRP = PRP_MIN_N - 1;   // longest list sorted by key under the PRP contract
 #ifndef SDM_WC_MIN_BLOCKS
 #define SDM_WC_MIN_BLOCKS 6
 #endif
 
-struct WarpCellSmem {
-    union {
-        uint32_t key[WC_MAX];             // sort keys; then the bijection's walk list
-        struct {
-            uint32_t ii[WC_QCAP];         // queued pairs: offsets i1 | i2 << 16
-            unsigned long long u[WC_QCAP];  // and their phi integers
-        } q;
+// Per-warp shared memory of the small-cell step.  SMAX: the longest list the warp sorts by key
+// (PRP_MIN_N - 1 under the PRP contract, whose longer lists take the bijection; WC_MAX under the
+// SORT contract).  The queue of pairs that passed the early exit is kept across the warp's cells
+// and evaluated 32 pairs at a time, each entry carrying its cell; a cell that lost an SD is
+// compacted once none of its pairs is left in the queue (at a cell boundary, when the list of
+// such cells passes WC_CFLUSH, and at the end).
+constexpr uint32_t WC_CCAP = 96;          // cells awaiting compaction
+constexpr uint32_t WC_CFLUSH = 32;        // list length that triggers a flush at a cell boundary
+template <uint32_t SMAX>
+struct __align__(16) WarpCellSmem {
+    union __align__(16) {
+        struct {                          // Step 1 by sorting keys (n <= SMAX)
+            uint32_t key[SMAX];
+            uint16_t cnt[SMAX + 2];       // counts of the 2^ceil(log2 n) top-bit buckets, then offsets
+            uint16_t off[SMAX];           // a position's place in its bucket's arrival order
+            uint16_t tmp[SMAX];           // positions grouped by bucket
+        } s;
+        struct {                          // Step 1 by the keyed bijection (257 <= n <= WC_MAX)
+            uint8_t tab[PRP_ROUNDS][WC_TAB];   // round r: floor(h(v ^ Kx_r) M_r / 2^32) for v < 32
+            uint32_t walk[WC_TAB];        // positions whose image lies outside [0, n) (fewer than A)
+        } p;
     };
-    uint32_t cnt[WC_MAX / 2 + 1];         // bucket counts, then their offsets; cnt[buckets] = n
-    uint16_t off[WC_MAX];                 // a position's place in its bucket's arrival order
-    uint16_t tmp[WC_MAX];                 // positions grouped by bucket
+    unsigned long long qu[WC_QCAP];       // queued pairs: phi integer,
+    uint32_t qg1[WC_QCAP], qg2[WC_QCAP];  // slots of the two SDs,
+    uint32_t qcell[WC_QCAP];              // their cell,
+    uint16_t qn[WC_QCAP];                 // its live count
+    uint32_t comp[WC_CCAP];               // cells to compact after their queued pairs
+    uint32_t ncomp;
+    uint32_t rem_cur;                     // the cell being stepped lost an SD
     uint16_t srt[WC_MAX];                 // the shuffled list: offsets in the cell
-    uint8_t vb[WC_MAX];                   // bin of the volume (vbin_of)
-    uint8_t xe[WC_MAX];                   // bit length of the multiplicity: 2^xe > xi
-    uint32_t rem;                         // an SD of the cell was removed
+    uint8_t vb[WC_MAX];                   // bin of each SD's volume (the state's vbin)
 };
 
 
@@ -770,28 +802,218 @@ __device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uin
     __syncwarp();
 }
 
-template <bool SURR>
-__device__ __forceinline__ void warp_cell_drain(const StepArgs& a, const EffTab* __restrict__ T, const CellCtx& cc,
-                                                WarpCellSmem& S, uint64_t s0, uint32_t& qcnt, uint32_t take,
-                                                LocalStats& ls, uint32_t lane)
+// Evaluates the newest `take` queued pairs, one per lane: the pair's data and its cell's constants
+// are gathered together, then Steps 2-3 (process_pair).  A removal marks the current cell, or
+// lists an earlier cell for compaction.
+// the same on 16-bit entries (totals below 2^16)
+__device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, uint32_t lane)
+{
+    const uint32_t per = (n + 31) >> 5;
+    const uint32_t b0 = min(n, lane * per), b1 = min(n, b0 + per);
+    uint32_t s = 0;
+    for (uint32_t i = b0; i < b1; ++i) s += a[i];
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    uint32_t run = inc - s;
+    for (uint32_t i = b0; i < b1; ++i) {
+        const uint32_t t = a[i];
+        a[i] = (uint16_t)run;
+        run += t;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) a[n] = (uint16_t)tot;
+    __syncwarp();
+}
+
+template <bool SURR, uint32_t SMAX>
+__device__ __forceinline__ void wc_drain(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S,
+                                         uint32_t& qcnt, uint32_t take, uint32_t cur_cell, LocalStats& ls,
+                                         uint32_t lane)
 {
     __syncwarp();
     const bool act = lane < take;
     const uint32_t k = qcnt - take + lane;
-    const uint32_t ii = act ? S.q.ii[k] : 0u;
-    const uint64_t g1 = s0 + (ii & 0xffffu), g2 = s0 + (ii >> 16);
+    uint64_t g1 = 0, g2 = 0;
+    uint32_t cell = 0, n = 2;
+    if (act) {
+        g1 = S.qg1[k];
+        g2 = S.qg2[k];
+        cell = S.qcell[k];
+        n = S.qn[k];
+    }
     const double v1 = act ? a.attr[g1] : 0.0, v2 = act ? a.attr[g2] : 0.0;
+    const uint64_t x1 = act ? a.xi[g1] : 1ull, x2 = act ? a.xi[g2] : 1ull;
+    const uint32_t kid = act ? (uint32_t)a.kid[cell] : 0u;
+    const double dv = act ? a.dv[cell] : 1.0;
+    const CellCtx cc{cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
     float Kh = SURR_PER_LANE;
-    if (SURR && a.precision == PREC_SURROGATE && cc.kid == 1)
-        Kh = surr_pair_kernel_warp(a.surr, v1, v2, act);         // the warp's pairs on the tensor cores
-    if (act) process_pair<SURR>(a, T, cc, S.q.u[k], g1, g2, a.xi[g1], a.xi[g2], v1, v2, ls, &S.rem, Kh);
+    if (SURR && a.precision == PREC_SURROGATE)
+        Kh = surr_pair_kernel_warp(a.surr, v1, v2, act && kid == 1);   // the warp's pairs on the tensor cores
+    uint32_t rflag = 0;
+    if (act) process_pair<SURR>(a, T, cc, S.qu[k], g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
+    if (rflag) {
+        if (cell == cur_cell) S.rem_cur = 1u;
+        else S.comp[atomicAdd(&S.ncomp, 1u)] = cell;
+    }
     __syncwarp();
     qcnt -= take;
 }
 
-template <bool SURR>
-__device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem& S, uint32_t cell,
-                               uint32_t step, LocalStats& ls, uint32_t lane)
+// Every queued pair evaluated, then the listed cells compacted (stably; Step 0 of the next step).
+template <bool SURR, uint32_t SMAX>
+__device__ void wc_flush(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S, uint32_t& qcnt,
+                         LocalStats& ls, uint32_t lane)
+{
+    while (qcnt > 0) wc_drain<SURR>(a, T, S, qcnt, min(qcnt, 32u), 0xffffffffu, ls, lane);
+    __syncwarp();
+    const uint32_t nc = *(volatile uint32_t*)&S.ncomp;
+    for (uint32_t i = 0; i < nc; ++i) {
+        const uint32_t c = S.comp[i];
+        const uint32_t s0 = a.cell_start[c], w = a.cell_start[c + 1] - s0;
+        const uint32_t n_new = warp_compact_cell(a, s0, min(a.n_live[c], w), lane);
+        __syncwarp();
+        if (lane == 0) a.n_live[c] = n_new;
+        __syncwarp();
+    }
+    if (lane == 0) S.ncomp = 0;
+    __syncwarp();
+}
+
+// Step 1 by sorting keys: the list ordered by (key, position), key(l) = philox(l >> 2, c, s, 0)[l & 3].
+// Counting sort on the top ceil(log2 n) bits (about one key per bucket), then each position's
+// exact rank inside its bucket -- a position alone in its bucket (the usual case) needs none.
+template <typename SM>
+__device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_t cell, uint32_t step, uint32_t n,
+                                               uint32_t lane)
+{
+    const uint32_t nbb = ceil_log2(n);                         // n >= 2: 2^nbb >= n buckets
+    const uint32_t sh = 32u - nbb;
+    const uint32_t NBK = 1u << nbb;
+    uint32_t* cw = reinterpret_cast<uint32_t*>(S.s.cnt);      // two 16-bit counts per word (n <= 512)
+    for (uint32_t b = lane; 2 * b < NBK; b += 32) cw[b] = 0;
+    __syncwarp();
+    for (uint32_t g = lane; 4 * g < n; g += 32) {
+        const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
+        if (4 * g + 3 < n) *reinterpret_cast<uint4*>(&S.s.key[4 * g]) = make_uint4(x.x, x.y, x.z, x.w);
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t l = 4 * g + k;
+            if (l < n) {
+                const uint32_t key = u4_word(x, k);
+                if (4 * g + 3 >= n) S.s.key[l] = key;
+                const uint32_t b = key >> sh, hs = (b & 1u) << 4;   // count b: half b & 1 of word b >> 1
+                S.s.off[l] = (uint16_t)(atomicAdd(&cw[b >> 1], 1u << hs) >> hs);
+            }
+        }
+    }
+    __syncwarp();
+    warp_exclusive_scan16(S.s.cnt, NBK, lane);
+    for (uint32_t l = lane; l < n; l += 32) S.s.tmp[S.s.cnt[S.s.key[l] >> sh] + S.s.off[l]] = (uint16_t)l;
+    __syncwarp();
+    for (uint32_t l = lane; l < n; l += 32) {
+        const uint32_t key = S.s.key[l];
+        const uint32_t b = key >> sh;
+        const uint32_t st = S.s.cnt[b], en = S.s.cnt[b + 1];
+        uint32_t r = 0;
+        if (en - st > 1) {
+            for (uint32_t p = st; p < en; ++p) {
+                const uint32_t o = S.s.tmp[p];
+                const uint32_t ko = S.s.key[o];
+                r += (ko < key) || (ko == key && o < l);
+            }
+        }
+        S.srt[st + r] = (uint16_t)l;
+    }
+}
+
+// Step 1 by the keyed bijection (257 <= n <= 512): the eight round keys come from one Philox call
+// in each of lanes 0-7; the round function of round r takes at most 32 distinct inputs (the other
+// half, below A or B), so its values are tabulated once per cell in shared memory, and each
+// position's image is eight table lookups, four positions per lane in flight.  The result is
+// the same bijection as feistel(): L' = L + floor(h(R ^ Kx_r) A / 2^32) mod A, and likewise R.
+template <typename SM>
+__device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t cell, uint32_t step, uint32_t n,
+                                              uint32_t lane)
+{
+    uint32_t A, B;
+    prp_domain_of(n, A, B);
+    const uint32_t Binv = (uint32_t)((0x100000000ull + B - 1) / B);
+    {
+        const U4 x = philox((lane >> 2) & 1u, cell, step, 2u, a.seed_lo, a.seed_hi);
+        const uint32_t K = u4_word(x, lane & 3u);
+        const uint32_t Kx = K ^ (K >> 16);
+#pragma unroll
+        for (uint32_t r = 0; r < PRP_ROUNDS; ++r) {
+            const uint32_t kr = __shfl_sync(0xffffffffu, Kx, r);
+            const uint32_t M = (r & 1u) ? B : A, lim = (r & 1u) ? A : B;
+            if (lane < lim) S.p.tab[r][lane] = (uint8_t)__umulhi(lowbias32_top16(lane ^ kr), M);
+        }
+    }
+    __syncwarp();
+    uint32_t nwalk = 0;
+    for (uint32_t base = 0; base < n; base += 128) {
+        uint32_t L[4], R[4];
+#pragma unroll
+        for (uint32_t t = 0; t < 4; ++t) {
+            const uint32_t q = min(base + 32 * t + lane, n - 1);
+            uint32_t h = __umulhi(q, Binv);
+            if (h * B > q) --h;
+            L[t] = h;
+            R[t] = q - h * B;
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
+#pragma unroll
+            for (uint32_t t = 0; t < 4; ++t) {
+                const uint32_t tl = L[t] + S.p.tab[r][R[t]];
+                L[t] = tl >= A ? tl - A : tl;
+            }
+#pragma unroll
+            for (uint32_t t = 0; t < 4; ++t) {
+                const uint32_t tr = R[t] + S.p.tab[r + 1][L[t]];
+                R[t] = tr >= B ? tr - B : tr;
+            }
+        }
+#pragma unroll
+        for (uint32_t t = 0; t < 4; ++t) {
+            const uint32_t q = base + 32 * t + lane;
+            const uint32_t e = L[t] * B + R[t];
+            const bool walks = q < n && e >= n;
+            if (q < n && !walks) S.srt[q] = (uint16_t)e;
+            const unsigned m = __ballot_sync(0xffffffffu, walks);
+            if (walks) S.p.walk[nwalk + __popc(m & ((1u << lane) - 1u))] = q | (e << 16);
+            nwalk += __popc(m);
+        }
+    }
+    __syncwarp();
+    if (lane < nwalk) {                                        // nwalk < A <= 32: one lane each
+        const uint32_t q = S.p.walk[lane] & 0xffffu;
+        uint32_t e = S.p.walk[lane] >> 16;
+        do {
+            uint32_t h = __umulhi(e, Binv);
+            if (h * B > e) --h;
+            uint32_t Lw = h, Rw = e - h * B;
+#pragma unroll
+            for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
+                const uint32_t tl = Lw + S.p.tab[r][Rw];
+                Lw = tl >= A ? tl - A : tl;
+                const uint32_t tr = Rw + S.p.tab[r + 1][Lw];
+                Rw = tr >= B ? tr - B : tr;
+            }
+            e = Lw * B + Rw;
+        } while (e >= n);
+        S.srt[q] = (uint16_t)e;
+    }
+}
+
+// One cell's step (Steps 1-3; the queued pairs may be evaluated later, see WarpCellSmem).
+template <bool SURR, uint32_t SMAX>
+__device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S, uint32_t cell,
+                               uint32_t step, uint32_t& qcnt, LocalStats& ls, uint32_t lane)
 {
     const uint64_t s0 = a.cell_start[cell];
     const uint32_t w = a.cell_start[cell + 1] - (uint32_t)s0;
@@ -799,96 +1021,40 @@ __device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, 
     if (n < 2) return;                                       // uniform
     const uint32_t kid = (uint32_t)a.kid[cell];
     const double dv = a.dv[cell];
-    if (lane == 0) S.rem = 0;
-    // the early exit's data of every SD: all of a lane's loads in flight before its stores
-    for (uint32_t base = 0; base < n; base += 128) {
-        uint64_t xr[4];
-        double vr[4];
+    const float xup = __ull2float_ru(a.cell_xmax[cell]);     // no multiplicity of the cell is larger
+    if (lane == 0) S.rem_cur = 0;
+    // the early exit's data of every SD: its volume bin, one byte (all of a lane's loads first)
+    for (uint32_t base = 0; base < n; base += 256) {
+        uint32_t b8[8];
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
+        for (uint32_t k = 0; k < 8; ++k) {
             const uint32_t i = base + 32 * k + lane;
-            if (i < n) {
-                xr[k] = a.xi[s0 + i];
-                vr[k] = a.attr[s0 + i];
-            }
+            b8[k] = i < n ? (uint32_t)__ldcs(a.vbin + s0 + i) : 0u;
         }
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
+        for (uint32_t k = 0; k < 8; ++k) {
             const uint32_t i = base + 32 * k + lane;
-            if (i < n) {
-                S.vb[i] = (uint8_t)vbin_of(vr[k]);
-                S.xe[i] = (uint8_t)(64u - (uint32_t)__clzll((long long)xr[k]));
-            }
+            if (i < n) S.vb[i] = (uint8_t)b8[k];
         }
     }
     // Step 1: the shuffled list
     if (sorts(a, n)) {
-        const uint32_t nb = ceil_log2(n) - 1u;                 // n >= 2: 2^nb >= n / 2 buckets
-        const uint32_t NBK = 1u << nb;
-        for (uint32_t b = lane; b < NBK; b += 32) S.cnt[b] = 0;
-        __syncwarp();
-        for (uint32_t g = lane; 4 * g < n; g += 32) {
-            const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
-                const uint32_t l = 4 * g + k;
-                if (l < n) {
-                    const uint32_t key = u4_word(x, k);
-                    const uint32_t b = nb ? key >> (32u - nb) : 0u;
-                    S.key[l] = key;
-                    S.off[l] = (uint16_t)atomicAdd(&S.cnt[b], 1u);
-                }
-            }
+        if (n > SMAX) {                                      // the host launches the SORT contract's
+            if (lane == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);   // instantiation: not reached
+            return;
         }
-        __syncwarp();
-        warp_exclusive_scan(S.cnt, NBK, lane);
-        for (uint32_t l = lane; l < n; l += 32) {
-            const uint32_t b = nb ? S.key[l] >> (32u - nb) : 0u;
-            S.tmp[S.cnt[b] + S.off[l]] = (uint16_t)l;
-        }
-        __syncwarp();
-        // exact rank inside the bucket: order by (key, list position)
-        for (uint32_t l = lane; l < n; l += 32) {
-            const uint32_t key = S.key[l];
-            const uint32_t b = nb ? key >> (32u - nb) : 0u;
-            const uint32_t st = S.cnt[b], en = S.cnt[b + 1];
-            uint32_t r = 0;
-            for (uint32_t p = st; p < en; ++p) {
-                const uint32_t o = S.tmp[p];
-                const uint32_t ko = S.key[o];
-                r += (ko < key) || (ko == key && o < l);
-            }
-            S.srt[st + r] = (uint16_t)l;
-        }
+        warp_sort_keys(a, S, cell, step, n, lane);
     } else {
-        Prp P;
-        prp_init(P, a.seed_lo, a.seed_hi, cell, step, n);
-        uint32_t nwalk = 0;                                    // images outside [0, n), listed
-        for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t q = base + lane;
-            const uint32_t e = q < n ? feistel(P, q) : 0u;
-            const bool walks = q < n && e >= n;
-            if (q < n && !walks) S.srt[q] = (uint16_t)e;
-            const unsigned m = __ballot_sync(0xffffffffu, walks);
-            if (walks) S.key[nwalk + __popc(m & ((1u << lane) - 1u))] = q | (e << 16);
-            nwalk += __popc(m);
-        }
-        __syncwarp();
-        for (uint32_t k = lane; k < nwalk; k += 32) {          // full lanes for the rare walks
-            const uint32_t q = S.key[k] & 0xffffu;
-            uint32_t e = S.key[k] >> 16;
-            do e = feistel(P, e); while (e >= n);
-            S.srt[q] = (uint16_t)e;
-        }
+        warp_prp_list(a, S, cell, step, n, lane);
     }
     __syncwarp();
-    // Steps 2-3: two pairs per lane and Philox call, early exit, the others queued
+    // Steps 2-3: two pairs per lane and Philox call, early exit, the others queued (evaluated 32 at
+    // a time, possibly together with later cells' pairs)
     const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
-    const CellCtx cc{cell, n, kid, s32, dv};
-    const float c_up = exit_scale(s32, kid, a.golovin_bf, a.precision);
+    const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xup);
     const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
     const uint32_t npairs = n >> 1, G2 = (npairs + 1) >> 1;
-    uint32_t qcnt = 0;
+    const uint32_t* __restrict__ srt2 = reinterpret_cast<const uint32_t*>(S.srt);   // pair m = srt2[m]
     for (uint32_t base = 0; base < G2; base += 32) {           // warp-uniform trip count
         const uint32_t M = base + lane;
         const bool valid = M < G2;
@@ -900,41 +1066,38 @@ __device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, 
             const bool has = valid && m < npairs;
             const uint32_t whi = h ? wv.z : wv.x, wlo = h ? wv.w : wv.y;
             bool need = false;
-            uint32_t i1 = 0, i2 = 0;
+            uint32_t ii = 0;
             if (has) {
-                i1 = S.srt[2 * m];
-                i2 = S.srt[2 * m + 1];
-                const float x_up = __uint_as_float((127u + max((uint32_t)S.xe[i1], (uint32_t)S.xe[i2])) << 23);
-                const float pup = __fmul_ru(__fmul_ru(__ldg(tb + pb_index(S.vb[i1], S.vb[i2])), c_up), x_up);
+                ii = srt2[m];
+                const float pup = __fmul_ru(__ldg(tb + pb_index(S.vb[ii & 0xffffu], S.vb[ii >> 16])), c_upx);
                 need = !(pup <= phi_lo23(whi));
                 ls.pairs += need ? 0u : 1u;
             }
             const unsigned mk = __ballot_sync(0xffffffffu, need);
             if (need) {
                 const uint32_t k = qcnt + __popc(mk & ((1u << lane) - 1u));
-                S.q.ii[k] = i1 | (i2 << 16);
-                S.q.u[k] = ((((uint64_t)whi) << 32) | (uint64_t)wlo) >> 11;
+                S.qg1[k] = (uint32_t)s0 + (ii & 0xffffu);
+                S.qg2[k] = (uint32_t)s0 + (ii >> 16);
+                S.qcell[k] = cell;
+                S.qn[k] = (uint16_t)n;
+                S.qu[k] = ((((uint64_t)whi) << 32) | (uint64_t)wlo) >> 11;
             }
             qcnt += __popc(mk);
+            if (qcnt >= 32) wc_drain<SURR>(a, T, S, qcnt, 32, cell, ls, lane);
         }
-        while (qcnt >= 32) warp_cell_drain<SURR>(a, T, cc, S, s0, qcnt, 32, ls, lane);
     }
-    if (qcnt > 0) warp_cell_drain<SURR>(a, T, cc, S, s0, qcnt, qcnt, ls, lane);
     __syncwarp();
-    // Step 0 of the next step: removals take effect in storage
-    if (*(volatile uint32_t*)&S.rem) {
-        const uint32_t n_new = warp_compact_cell(a, s0, n, lane);
-        if (lane == 0) a.n_live[cell] = n_new;
-    }
+    // a removal: the cell is compacted once its queued pairs are evaluated
+    if (lane == 0 && *(volatile uint32_t*)&S.rem_cur) S.comp[S.ncomp++] = cell;
     __syncwarp();
 }
 
-template <bool SURR>
-__global__ void __launch_bounds__(32 * WC_WARPS, SDM_WC_MIN_BLOCKS) warp_cells_kernel(StepArgs a,
-                                                                                    const uint32_t* __restrict__ cells,
-                                                                                    uint32_t n_cells)
+// SMAX: see WarpCellSmem (the SORT contract's instantiation sorts lists up to WC_MAX)
+template <bool SURR, uint32_t SMAX>
+__global__ void __launch_bounds__(32 * WC_WARPS, SMAX < WC_MAX ? SDM_WC_MIN_BLOCKS : 5) warp_cells_kernel(
+    StepArgs a, const uint32_t* __restrict__ cells, uint32_t n_cells)
 {
-    __shared__ WarpCellSmem ws[WC_WARPS];
+    __shared__ WarpCellSmem<SMAX> ws[WC_WARPS];
     __shared__ EffTab tab;
     __shared__ unsigned long long red[8];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -942,12 +1105,42 @@ __global__ void __launch_bounds__(32 * WC_WARPS, SDM_WC_MIN_BLOCKS) warp_cells_k
     LocalStats ls = {0, 0, 0, 0, 0ull};
     load_eff_tab(&tab);
     if (threadIdx.x < 5) red[threadIdx.x] = 0;
+    WarpCellSmem<SMAX>& S = ws[warp];
+    if (lane == 0) S.ncomp = 0;
     __syncthreads();
-    for (uint32_t k = blockIdx.x * WC_WARPS + warp; k < n_cells; k += gridDim.x * WC_WARPS)
-        warp_cell_step<SURR>(a, &tab, ws[warp], cells[k], step, ls, lane);
+    uint32_t qcnt = 0;                                        // queued pairs (warp-uniform)
+    const uint32_t stride = gridDim.x * WC_WARPS;
+    for (uint32_t k = blockIdx.x * WC_WARPS + warp; k < n_cells; k += stride) {
+        warp_cell_step<SURR>(a, &tab, S, cells[k], step, qcnt, ls, lane);
+        if (*(volatile uint32_t*)&S.ncomp > WC_CFLUSH) wc_flush<SURR>(a, &tab, S, qcnt, ls, lane);
+    }
+    wc_flush<SURR>(a, &tab, S, qcnt, ls, lane);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
+    }
+}
+
+// Per cell stepped by one warp: the largest multiplicity (an upper bound for the early exit of
+// every later step until the state is replaced: coalescence never raises a multiplicity), and
+// the volume bin of every slot.  One warp per cell of the list.
+__global__ void cell_bounds_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ vol,
+                                   const uint32_t* __restrict__ cell_start, const uint32_t* __restrict__ cells,
+                                   uint32_t n_cells, unsigned long long* __restrict__ xmax,
+                                   uint8_t* __restrict__ vbin)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_cells; k += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t c = cells[k];
+        const uint32_t s0 = cell_start[c], s1 = cell_start[c + 1];
+        unsigned long long m = 0;
+        for (uint32_t i = s0 + lane; i < s1; i += 32) {
+            m = max(m, (unsigned long long)xi[i]);
+            vbin[i] = (uint8_t)vbin_of(vol[i]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) xmax[c] = m;
     }
 }
 
@@ -973,9 +1166,10 @@ constexpr uint32_t GRID_BARRIER_SPIN_LIMIT = 1u << 22;   // ~0.4 s of polling at
 
 // Barrier of a cooperatively launched grid (every block resident).  Thread 0 of each block
 // arrives on the counter; the last arrival resets it and advances the generation the others
-// poll.  The poll gives up after GRID_BARRIER_SPIN_LIMIT rounds: the error word gets
-// ERR_TIMEOUT and false is returned (the caller then ends the kernel).
-__device__ bool grid_barrier(uint32_t* count, uint32_t* gen, uint32_t* err)
+// poll.  The poll gives up after spin_limit rounds: the error word gets ERR_TIMEOUT and false
+// is returned (the caller then ends the kernel).
+__device__ bool grid_barrier(uint32_t* count, uint32_t* gen, uint32_t* err,
+                             uint32_t spin_limit = GRID_BARRIER_SPIN_LIMIT)
 {
     __shared__ uint32_t ok_s;
     __syncthreads();
@@ -990,7 +1184,7 @@ __device__ bool grid_barrier(uint32_t* count, uint32_t* gen, uint32_t* err)
         } else {
             uint32_t it = 0;
             while (*(volatile uint32_t*)gen == g) {
-                if (++it > GRID_BARRIER_SPIN_LIMIT) {
+                if (++it > spin_limit) {
                     atomicOr(err, ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -1548,6 +1742,16 @@ __global__ void __launch_bounds__(256) big_compact_kernel(StepArgs a, const BigC
     }
 }
 
+// Self-test of the bounded wait: the grid meets at grid_barrier with the given spin limit;
+// with withhold set, the last block never arrives (returns at once), so the others' wait runs
+// out, they record ERR_TIMEOUT and return.  Launched cooperatively with a few blocks.
+__global__ void barrier_selftest_kernel(uint32_t* count, uint32_t* gen, uint32_t* err, uint32_t spin_limit,
+                                        uint32_t withhold)
+{
+    if (withhold && blockIdx.x == gridDim.x - 1) return;
+    grid_barrier(count, gen, err, spin_limit);
+}
+
 // ---------------------------------------------------------------------------
 // Large cells, pass 1: scatter (key, position) into fixed-capacity buckets.
 // ---------------------------------------------------------------------------
@@ -1562,8 +1766,11 @@ constexpr uint32_t BIG_ATOMIC_ILP = 4;        // bucket reservations in flight p
 //   ticket[c]        scatter CTAs of large cell c that finished (zero between steps)
 //   bstart[g + c]    for bucket g of large cell c: exclusive prefix of the cell's
 //                    (capacity-clamped) bucket counts; bstart[base_c + c + nb_c] is the
-//                    cell's total.  Written by the last scatter CTA of the cell, which
+//                    cell's total, or BUCKET_OVERFLOWED when a bucket of the cell received
+//                    more records than its capacity (the finishing pass then leaves the
+//                    cell unchanged).  Written by the last scatter CTA of the cell, which
 //                    also clears the cell's cursors and ticket.
+constexpr uint32_t BUCKET_OVERFLOWED = 0xffffffffu;
 struct BucketBook {
     uint32_t* cursor;
     uint32_t* bstart;
@@ -1600,6 +1807,7 @@ __device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __r
         }
     }
     if (over) atomicOr(err, ERR_BUCKET_OVERFLOW);
+    const bool cell_over = __syncthreads_or(over) != 0;
     uint32_t inc = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1618,7 +1826,7 @@ __device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __r
             if (lane >= (uint32_t)o) wi += t;
         }
         if (lane < nw) wt[lane] = wi - w;
-        if (lane == 31) out[nb] = wi;                 // the cell's total
+        if (lane == 31) out[nb] = cell_over ? BUCKET_OVERFLOWED : wi;   // the cell's total
     }
     __syncthreads();
     uint32_t run = wt[wid] + inc - s;
@@ -1803,9 +2011,10 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     // (the cell's offsets: bstart[bucket + cell index], its total after its last bucket)
     const uint32_t* __restrict__ off_c = bstart + C.bucket_base + big;    // [nb + 1]
     const uint32_t gl = g - C.bucket_base;                                 // bucket in the cell
+    const uint32_t n = off_c[nb];
+    if (n == BUCKET_OVERFLOWED) return;            // records were lost: the cell stays as it is
     const uint32_t S = off_c[gl];
     const uint32_t k = off_c[gl + 1] - S;
-    const uint32_t n = off_c[nb];
     const uint64_t* R = rec + (uint64_t)g * cap;
 #pragma unroll 4
     for (uint32_t i = lane; i < k; i += 32) rs[i] = R[i];

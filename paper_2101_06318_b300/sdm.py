@@ -35,7 +35,8 @@ EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", 
            "sdm_autotune", "sdm_sync", "sdm_free", "sdm_eval_pairs", "sdm_set_profiling", "sdm_get_profile",
            "sdm_launches_per_step", "sdm_coalescence_step_noalloc", "sdm_surrogate_create", "sdm_surrogate_free",
            "sdm_surrogate_train", "sdm_surrogate_build_mask", "sdm_surrogate_params_io", "sdm_surrogate_info",
-           "sdm_surrogate_loss_grad", "sdm_surrogate_eval", "sdm_attach_surrogate"]
+           "sdm_surrogate_loss_grad", "sdm_surrogate_eval", "sdm_attach_surrogate", "sdm_debug_wait_timeout",
+           "sdm_debug_bucket_capacity"]
 
 
 class SurrogateParams(C.Structure):
@@ -122,6 +123,8 @@ def lib(build_if_needed: bool = True):
         L.sdm_surrogate_loss_grad.argtypes = [vp, vp, vp, u64, vp, vp]
         L.sdm_surrogate_eval.argtypes = [vp, vp, vp, u64, vp]
         L.sdm_attach_surrogate.argtypes = [vp, vp]
+        L.sdm_debug_wait_timeout.argtypes = [vp, u32, i32]
+        L.sdm_debug_bucket_capacity.argtypes = [vp, u32]
         for name in EXPORTS:
             if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free", "sdm_surrogate_free"):
                 getattr(L, name).restype = i32
@@ -289,6 +292,14 @@ class State:
 
     def sync(self):
         _check(self._L.sdm_sync(self._h), "sdm_sync")
+
+    # -- failure-path self-tests -------------------------------------------------
+    def debug_wait_timeout(self, spin_limit, withhold=True):
+        _check(self._L.sdm_debug_wait_timeout(self._h, int(spin_limit), int(bool(withhold))),
+               "sdm_debug_wait_timeout")
+
+    def debug_bucket_capacity(self, cap):
+        _check(self._L.sdm_debug_bucket_capacity(self._h, int(cap)), "sdm_debug_bucket_capacity")
 
     # -- schedule ------------------------------------------------------------------
     @property

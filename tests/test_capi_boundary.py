@@ -45,6 +45,8 @@ def test_host_only_calls():
     assert L.sdm_alloc(C.byref(h), 1 << 32, 1, 1, None, None, 0) == 1
     assert L.sdm_coalescence_step(None, None, 1, None) == 1
     assert L.sdm_sync(None) == 1
+    assert L.sdm_debug_wait_timeout(None, 100, 1) == 1
+    assert L.sdm_debug_bucket_capacity(None, 64) == 1
     L.sdm_free(None)
 
 
