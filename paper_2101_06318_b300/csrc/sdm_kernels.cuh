@@ -914,19 +914,72 @@ __device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_
     warp_exclusive_scan16(S.s.cnt, NBK, lane);
     for (uint32_t l = lane; l < n; l += 32) S.s.tmp[S.s.cnt[S.s.key[l] >> sh] + S.s.off[l]] = (uint16_t)l;
     __syncwarp();
-    for (uint32_t l = lane; l < n; l += 32) {
+    // a key alone in its bucket is placed at once; the others (keys sharing a bucket, about a
+    // third of them) are listed, compacted, and ranked exactly inside their bucket, a lane each
+    uint32_t nwork = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t l = base + lane;
+        bool multi = false;
+        if (l < n) {
+            const uint32_t b = S.s.key[l] >> sh;
+            const uint32_t st = S.s.cnt[b];
+            multi = S.s.cnt[b + 1] - st > 1;
+            if (!multi) S.srt[st] = (uint16_t)l;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, multi);
+        if (multi) S.s.off[nwork + __popc(m & ((1u << lane) - 1u))] = (uint16_t)l;   // off is free now
+        nwork += __popc(m);
+    }
+    __syncwarp();
+    for (uint32_t w = lane; w < nwork; w += 32) {
+        const uint32_t l = S.s.off[w];
         const uint32_t key = S.s.key[l];
         const uint32_t b = key >> sh;
         const uint32_t st = S.s.cnt[b], en = S.s.cnt[b + 1];
         uint32_t r = 0;
-        if (en - st > 1) {
-            for (uint32_t p = st; p < en; ++p) {
-                const uint32_t o = S.s.tmp[p];
-                const uint32_t ko = S.s.key[o];
-                r += (ko < key) || (ko == key && o < l);
-            }
+        for (uint32_t p = st; p < en; ++p) {
+            const uint32_t o = S.s.tmp[p];
+            const uint32_t ko = S.s.key[o];
+            r += (ko < key) || (ko == key && o < l);
         }
         S.srt[st + r] = (uint16_t)l;
+    }
+}
+
+// x mod M for x < 2 M, without a branch: x - M wraps around (becomes larger) when x < M
+__device__ __forceinline__ uint32_t sub_mod(uint32_t x, uint32_t M) { return min(x, x - M); }
+
+// The bijection's images of positions base + lane + 32 t, t < NT (the rounds of warp_prp_list;
+// an image outside [0, n) goes to the walk list)
+template <uint32_t NT, typename SM>
+__device__ __forceinline__ void prp_positions(SM& S, uint32_t base, uint32_t n, uint32_t A, uint32_t B,
+                                              uint32_t Binv, uint32_t& nwalk, uint32_t lane)
+{
+    uint32_t L[NT], R[NT];
+#pragma unroll
+    for (uint32_t t = 0; t < NT; ++t) {
+        const uint32_t q = min(base + 32 * t + lane, n - 1);
+        uint32_t h = __umulhi(q, Binv);
+        if (h * B > q) --h;
+        L[t] = h;
+        R[t] = q - h * B;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
+#pragma unroll
+        for (uint32_t t = 0; t < NT; ++t) L[t] = sub_mod(L[t] + S.p.tab[r][R[t]], A);
+#pragma unroll
+        for (uint32_t t = 0; t < NT; ++t) R[t] = sub_mod(R[t] + S.p.tab[r + 1][L[t]], B);
+    }
+#pragma unroll
+    for (uint32_t t = 0; t < NT; ++t) {
+        const uint32_t q = base + 32 * t + lane;
+        const uint32_t e = L[t] * B + R[t];
+        const bool walks = q < n && e >= n;
+        if (q < n && !walks) S.srt[q] = (uint16_t)e;
+        const unsigned m = __ballot_sync(0xffffffffu, walks);
+        if (walks) S.p.walk[nwalk + __popc(m & ((1u << lane) - 1u))] = q | (e << 16);
+        nwalk += __popc(m);
     }
 }
 
@@ -955,39 +1008,11 @@ __device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t
     }
     __syncwarp();
     uint32_t nwalk = 0;
-    for (uint32_t base = 0; base < n; base += 128) {
-        uint32_t L[4], R[4];
-#pragma unroll
-        for (uint32_t t = 0; t < 4; ++t) {
-            const uint32_t q = min(base + 32 * t + lane, n - 1);
-            uint32_t h = __umulhi(q, Binv);
-            if (h * B > q) --h;
-            L[t] = h;
-            R[t] = q - h * B;
-        }
-#pragma unroll
-        for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
-#pragma unroll
-            for (uint32_t t = 0; t < 4; ++t) {
-                const uint32_t tl = L[t] + S.p.tab[r][R[t]];
-                L[t] = tl >= A ? tl - A : tl;
-            }
-#pragma unroll
-            for (uint32_t t = 0; t < 4; ++t) {
-                const uint32_t tr = R[t] + S.p.tab[r + 1][L[t]];
-                R[t] = tr >= B ? tr - B : tr;
-            }
-        }
-#pragma unroll
-        for (uint32_t t = 0; t < 4; ++t) {
-            const uint32_t q = base + 32 * t + lane;
-            const uint32_t e = L[t] * B + R[t];
-            const bool walks = q < n && e >= n;
-            if (q < n && !walks) S.srt[q] = (uint16_t)e;
-            const unsigned m = __ballot_sync(0xffffffffu, walks);
-            if (walks) S.p.walk[nwalk + __popc(m & ((1u << lane) - 1u))] = q | (e << 16);
-            nwalk += __popc(m);
-        }
+    for (uint32_t base = 0; base < n; base += 128) {          // 4, 2 or 1 positions per lane
+        const uint32_t rest = n - base;
+        if (rest > 64) prp_positions<4>(S, base, n, A, B, Binv, nwalk, lane);
+        else if (rest > 32) prp_positions<2>(S, base, n, A, B, Binv, nwalk, lane);
+        else prp_positions<1>(S, base, n, A, B, Binv, nwalk, lane);
     }
     __syncwarp();
     if (lane < nwalk) {                                        // nwalk < A <= 32: one lane each
@@ -999,10 +1024,8 @@ __device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t
             uint32_t Lw = h, Rw = e - h * B;
 #pragma unroll
             for (uint32_t r = 0; r < PRP_ROUNDS; r += 2) {
-                const uint32_t tl = Lw + S.p.tab[r][Rw];
-                Lw = tl >= A ? tl - A : tl;
-                const uint32_t tr = Rw + S.p.tab[r + 1][Lw];
-                Rw = tr >= B ? tr - B : tr;
+                Lw = sub_mod(Lw + S.p.tab[r][Rw], A);
+                Rw = sub_mod(Rw + S.p.tab[r + 1][Lw], B);
             }
             e = Lw * B + Rw;
         } while (e >= n);
