@@ -93,6 +93,9 @@ struct sdm_state {
     TileDesc* d_tiles = nullptr;
     uint32_t n_tiles = 0, max_cells_per_tile = 0;
     uint32_t* d_wcells = nullptr;            // cells of at most WC_MAX slots, one warp each
+    WcQueue wq{};                            // their queue of pairs past the early exit
+    uint32_t* d_wq_ticket = nullptr;         // the compaction kernel's ticket
+    uint32_t wq_grid = 0;                    // grid of the queue's pair and compaction kernels
     char* rb_buf = nullptr;                  // scratch of sdm_rebucket, kept between calls
     size_t rb_bytes = 0;
     uint32_t n_wcells = 0, wc_grid = 0, wc_grid_sort = 0;
@@ -217,6 +220,7 @@ void free_layout(sdm_state* st)
     st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
     st->d_wcells = nullptr; st->n_wcells = st->wc_grid = st->wc_grid_sort = 0;
+    st->wq = WcQueue{}; st->d_wq_ticket = nullptr; st->wq_grid = 0;
 }
 
 template <typename T>
@@ -552,12 +556,23 @@ sdm_status build_layout(sdm_state* st)
     if (st->n_wcells) {
         int per_sm = 0;
         const uint32_t need = (st->n_wcells + WC_WARPS - 1) / WC_WARPS;
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false, WC_SORT_PRP>,
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<WC_SORT_PRP>,
                                                                32 * WC_WARPS, 0));
         st->wc_grid = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<false, WC_MAX>,
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<WC_MAX>,
                                                                32 * WC_WARPS, 0));
         st->wc_grid_sort = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
+        // the queue: at most one entry per candidate pair of these cells
+        uint64_t qcap = 32;
+        for (uint32_t c : wcells) qcap += (cs[c + 1] - cs[c]) / 2;
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.q, sizeof(uint4) * qcap, true));
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.count, sizeof(uint32_t) * 4, true));   // pairs, cells, ticket
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.cells, sizeof(uint32_t) * st->n_wcells, true));
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.flag, sizeof(uint32_t) * st->n_cell, true));
+        SDM_CUDA(cudaMemsetAsync(st->wq.count, 0, sizeof(uint32_t) * 4, st->stream));
+        SDM_CUDA(cudaMemsetAsync(st->wq.flag, 0, sizeof(uint32_t) * st->n_cell, st->stream));
+        st->d_wq_ticket = st->wq.count + 2;
+        st->wq_grid = 8 * st->n_sm;
     }
     SDM_TRY(upload(st, &st->d_big, bigs));
     SDM_TRY(upload(st, &st->d_chunks, chunks));
@@ -869,13 +884,16 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             ProfScope ps(st, 0);
             const bool surr = p->precision == SDM_PREC_SURROGATE;
             if (st->n_wcells) {
-                if (p->shuffle == SDM_SHUFFLE_SORT) {     // lists up to 512 SDs sorted by key
-                    auto wk = surr ? warp_cells_kernel<true, WC_MAX> : warp_cells_kernel<false, WC_MAX>;
-                    wk<<<st->wc_grid_sort, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
-                } else {                                  // above 256 SDs the keyed bijection
-                    auto wk = surr ? warp_cells_kernel<true, WC_SORT_PRP> : warp_cells_kernel<false, WC_SORT_PRP>;
-                    wk<<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(a, st->d_wcells, st->n_wcells);
-                }
+                // shuffle and early exit per cell, then the queued pairs, then the cells that lost SDs
+                if (p->shuffle == SDM_SHUFFLE_SORT)       // lists up to 512 SDs sorted by key
+                    warp_cells_kernel<WC_MAX><<<st->wc_grid_sort, 32 * WC_WARPS, 0, st->stream>>>(
+                        a, st->wq, st->d_wcells, st->n_wcells);
+                else                                      // above 256 SDs the keyed bijection
+                    warp_cells_kernel<WC_SORT_PRP><<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(
+                        a, st->wq, st->d_wcells, st->n_wcells);
+                auto pk = surr ? wc_pairs_kernel<true> : wc_pairs_kernel<false>;
+                pk<<<st->wq_grid, 256, 0, st->stream>>>(a, st->wq);
+                wc_compact_kernel<<<st->wq_grid, 256, 0, st->stream>>>(a, st->wq, st->d_wq_ticket);
             }
             if (st->n_tiles) {
                 uint32_t grid = st->n_tiles;
@@ -972,6 +990,8 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     // layout: tiles and big cells (<= n_cell each), chunks, buckets, cursors, scratch
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 256);   // cells stepped by one warp each
+    // their queue (an entry per candidate pair), its counters, listed cells and flags
+    b += round256(16 * (cap / 2 + 32) + 256) + round256(16 + 256) + 2 * round256(4 * (size_t)n_cell + 256);
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
@@ -1536,7 +1556,7 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
     if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
     // small cells: one kernel per kind; large cells: one kernel (PRP contract; it compacts the
     // cells the previous step left flagged) or scatter + finish (SORT contract)
-    *n = (st->n_wcells ? 1u : 0u) + (st->n_tiles ? 1u : 0u) +
+    *n = (st->n_wcells ? 3u : 0u) + (st->n_tiles ? 1u : 0u) +   // cells, queued pairs, compaction
          (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);   // SORT: scatter + finish
     return SDM_OK;
 }

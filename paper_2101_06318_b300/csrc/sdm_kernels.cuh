@@ -737,21 +737,15 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? SDM_TILE_MIN_BLOCKS : 1) t
 // ---------------------------------------------------------------------------
 constexpr uint32_t WC_MAX = 512;          // slots of a cell stepped by one warp
 constexpr uint32_t WC_WARPS = 4;          // warps per block
-constexpr uint32_t WC_QCAP = 64;          // queued pairs (< 32 left + 32 new)
 constexpr uint32_t WC_TAB = 32;           // entries per round table of the bijection (A, B <= 32 for n <= 512)
 constexpr uint32_t WC_SORT_PRP = PRP_MIN_N - 1;   // longest list sorted by key under the PRP contract
 #ifndef SDM_WC_MIN_BLOCKS
-#define SDM_WC_MIN_BLOCKS 6
+#define SDM_WC_MIN_BLOCKS 9
 #endif
 
 // Per-warp shared memory of the small-cell step.  SMAX: the longest list the warp sorts by key
 // (PRP_MIN_N - 1 under the PRP contract, whose longer lists take the bijection; WC_MAX under the
-// SORT contract).  The queue of pairs that passed the early exit is kept across the warp's cells
-// and evaluated 32 pairs at a time, each entry carrying its cell; a cell that lost an SD is
-// compacted once none of its pairs is left in the queue (at a cell boundary, when the list of
-// such cells passes WC_CFLUSH, and at the end).
-constexpr uint32_t WC_CCAP = 96;          // cells awaiting compaction
-constexpr uint32_t WC_CFLUSH = 32;        // list length that triggers a flush at a cell boundary
+// SORT contract).
 template <uint32_t SMAX>
 struct __align__(16) WarpCellSmem {
     union __align__(16) {
@@ -766,15 +760,19 @@ struct __align__(16) WarpCellSmem {
             uint32_t walk[WC_TAB];        // positions whose image lies outside [0, n) (fewer than A)
         } p;
     };
-    unsigned long long qu[WC_QCAP];       // queued pairs: phi integer,
-    uint32_t qg1[WC_QCAP], qg2[WC_QCAP];  // slots of the two SDs,
-    uint32_t qcell[WC_QCAP];              // their cell,
-    uint16_t qn[WC_QCAP];                 // its live count
-    uint32_t comp[WC_CCAP];               // cells to compact after their queued pairs
-    uint32_t ncomp;
-    uint32_t rem_cur;                     // the cell being stepped lost an SD
     uint16_t srt[WC_MAX];                 // the shuffled list: offsets in the cell
     uint8_t vb[WC_MAX];                   // bin of each SD's volume (the state's vbin)
+};
+
+// The queue of the small-cell step: pairs that passed the early exit, 16 bytes each (cell,
+// offsets i1 | i2 << 16 of the two SDs in the cell, and the pair's phi integer), appended by
+// warp_cells_kernel and evaluated by wc_pairs_kernel; cells that lost an SD are listed for
+// wc_compact_kernel.  The counters are zero between steps (the compaction kernel resets them).
+struct WcQueue {
+    uint4* q;                 // [capacity] (cell, i1 | i2 << 16, phi low word, phi high word)
+    uint32_t* count;          // [0] queued pairs, [1] listed cells
+    uint32_t* cells;          // [n_cell] cells to compact
+    uint32_t* flag;           // [n_cell] the cell is listed
 };
 
 
@@ -802,9 +800,6 @@ __device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uin
     __syncwarp();
 }
 
-// Evaluates the newest `take` queued pairs, one per lane: the pair's data and its cell's constants
-// are gathered together, then Steps 2-3 (process_pair).  A removal marks the current cell, or
-// lists an earlier cell for compaction.
 // the same on 16-bit entries (totals below 2^16)
 __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, uint32_t lane)
 {
@@ -826,60 +821,6 @@ __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, u
     }
     const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
     if (lane == 0) a[n] = (uint16_t)tot;
-    __syncwarp();
-}
-
-template <bool SURR, uint32_t SMAX>
-__device__ __forceinline__ void wc_drain(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S,
-                                         uint32_t& qcnt, uint32_t take, uint32_t cur_cell, LocalStats& ls,
-                                         uint32_t lane)
-{
-    __syncwarp();
-    const bool act = lane < take;
-    const uint32_t k = qcnt - take + lane;
-    uint64_t g1 = 0, g2 = 0;
-    uint32_t cell = 0, n = 2;
-    if (act) {
-        g1 = S.qg1[k];
-        g2 = S.qg2[k];
-        cell = S.qcell[k];
-        n = S.qn[k];
-    }
-    const double v1 = act ? a.attr[g1] : 0.0, v2 = act ? a.attr[g2] : 0.0;
-    const uint64_t x1 = act ? a.xi[g1] : 1ull, x2 = act ? a.xi[g2] : 1ull;
-    const uint32_t kid = act ? (uint32_t)a.kid[cell] : 0u;
-    const double dv = act ? a.dv[cell] : 1.0;
-    const CellCtx cc{cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
-    float Kh = SURR_PER_LANE;
-    if (SURR && a.precision == PREC_SURROGATE)
-        Kh = surr_pair_kernel_warp(a.surr, v1, v2, act && kid == 1);   // the warp's pairs on the tensor cores
-    uint32_t rflag = 0;
-    if (act) process_pair<SURR>(a, T, cc, S.qu[k], g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
-    if (rflag) {
-        if (cell == cur_cell) S.rem_cur = 1u;
-        else S.comp[atomicAdd(&S.ncomp, 1u)] = cell;
-    }
-    __syncwarp();
-    qcnt -= take;
-}
-
-// Every queued pair evaluated, then the listed cells compacted (stably; Step 0 of the next step).
-template <bool SURR, uint32_t SMAX>
-__device__ void wc_flush(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S, uint32_t& qcnt,
-                         LocalStats& ls, uint32_t lane)
-{
-    while (qcnt > 0) wc_drain<SURR>(a, T, S, qcnt, min(qcnt, 32u), 0xffffffffu, ls, lane);
-    __syncwarp();
-    const uint32_t nc = *(volatile uint32_t*)&S.ncomp;
-    for (uint32_t i = 0; i < nc; ++i) {
-        const uint32_t c = S.comp[i];
-        const uint32_t s0 = a.cell_start[c], w = a.cell_start[c + 1] - s0;
-        const uint32_t n_new = warp_compact_cell(a, s0, min(a.n_live[c], w), lane);
-        __syncwarp();
-        if (lane == 0) a.n_live[c] = n_new;
-        __syncwarp();
-    }
-    if (lane == 0) S.ncomp = 0;
     __syncwarp();
 }
 
@@ -1033,10 +974,11 @@ __device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t
     }
 }
 
-// One cell's step (Steps 1-3; the queued pairs may be evaluated later, see WarpCellSmem).
-template <bool SURR, uint32_t SMAX>
-__device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, WarpCellSmem<SMAX>& S, uint32_t cell,
-                               uint32_t step, uint32_t& qcnt, LocalStats& ls, uint32_t lane)
+// One cell's Steps 1-3 up to the early exit; the pairs it cannot settle are appended to the
+// queue (WcQueue) for wc_pairs_kernel.
+template <uint32_t SMAX>
+__device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem<SMAX>& S, uint32_t cell,
+                               uint32_t step, LocalStats& ls, uint32_t lane)
 {
     const uint64_t s0 = a.cell_start[cell];
     const uint32_t w = a.cell_start[cell + 1] - (uint32_t)s0;
@@ -1045,7 +987,6 @@ __device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, 
     const uint32_t kid = (uint32_t)a.kid[cell];
     const double dv = a.dv[cell];
     const float xup = __ull2float_ru(a.cell_xmax[cell]);     // no multiplicity of the cell is larger
-    if (lane == 0) S.rem_cur = 0;
     // the early exit's data of every SD: its volume bin, one byte (all of a lane's loads first)
     for (uint32_t base = 0; base < n; base += 256) {
         uint32_t b8[8];
@@ -1071,8 +1012,7 @@ __device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, 
         warp_prp_list(a, S, cell, step, n, lane);
     }
     __syncwarp();
-    // Steps 2-3: two pairs per lane and Philox call, early exit, the others queued (evaluated 32 at
-    // a time, possibly together with later cells' pairs)
+    // Steps 2-3 up to the early exit: two pairs per lane and Philox call
     const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
     const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xup);
     const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
@@ -1083,64 +1023,137 @@ __device__ void warp_cell_step(const StepArgs& a, const EffTab* __restrict__ T, 
         const bool valid = M < G2;
         U4 wv = {0, 0, 0, 0};
         if (valid) wv = philox(M, cell, step, 1u, a.seed_lo, a.seed_hi);
+        bool need[2];
+        uint32_t ii[2];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t m = 2 * M + h;
-            const bool has = valid && m < npairs;
-            const uint32_t whi = h ? wv.z : wv.x, wlo = h ? wv.w : wv.y;
-            bool need = false;
-            uint32_t ii = 0;
-            if (has) {
-                ii = srt2[m];
-                const float pup = __fmul_ru(__ldg(tb + pb_index(S.vb[ii & 0xffffu], S.vb[ii >> 16])), c_upx);
-                need = !(pup <= phi_lo23(whi));
-                ls.pairs += need ? 0u : 1u;
+            need[h] = false;
+            ii[h] = 0;
+            if (valid && m < npairs) {
+                ii[h] = srt2[m];
+                const float pup = __fmul_ru(__ldg(tb + pb_index(S.vb[ii[h] & 0xffffu], S.vb[ii[h] >> 16])), c_upx);
+                need[h] = !(pup <= phi_lo23(h ? wv.z : wv.x));
+                ls.pairs += need[h] ? 0u : 1u;
             }
-            const unsigned mk = __ballot_sync(0xffffffffu, need);
-            if (need) {
-                const uint32_t k = qcnt + __popc(mk & ((1u << lane) - 1u));
-                S.qg1[k] = (uint32_t)s0 + (ii & 0xffffu);
-                S.qg2[k] = (uint32_t)s0 + (ii >> 16);
-                S.qcell[k] = cell;
-                S.qn[k] = (uint16_t)n;
-                S.qu[k] = ((((uint64_t)whi) << 32) | (uint64_t)wlo) >> 11;
+        }
+        // the lanes' surviving pairs go to the queue in one reservation per warp
+        const uint32_t mine = (uint32_t)need[0] + (uint32_t)need[1];
+        uint32_t pre = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= (uint32_t)o) pre += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, pre, 31);
+        if (tot) {
+            uint32_t qb = 0;
+            if (lane == 0) qb = atomicAdd(W.count, tot);
+            qb = __shfl_sync(0xffffffffu, qb, 0) + pre - mine;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                if (need[h]) {
+                    W.q[qb++] = make_uint4(cell, ii[h], h ? wv.w : wv.y, h ? wv.z : wv.x);
+                }
             }
-            qcnt += __popc(mk);
-            if (qcnt >= 32) wc_drain<SURR>(a, T, S, qcnt, 32, cell, ls, lane);
         }
     }
-    __syncwarp();
-    // a removal: the cell is compacted once its queued pairs are evaluated
-    if (lane == 0 && *(volatile uint32_t*)&S.rem_cur) S.comp[S.ncomp++] = cell;
-    __syncwarp();
 }
 
-// SMAX: see WarpCellSmem (the SORT contract's instantiation sorts lists up to WC_MAX)
-template <bool SURR, uint32_t SMAX>
-__global__ void __launch_bounds__(32 * WC_WARPS, SMAX < WC_MAX ? SDM_WC_MIN_BLOCKS : 5) warp_cells_kernel(
-    StepArgs a, const uint32_t* __restrict__ cells, uint32_t n_cells)
+// One warp per cell of at most 512 slots (see warp_cell_step).  SMAX: see WarpCellSmem (the SORT
+// contract's instantiation sorts lists up to WC_MAX).
+template <uint32_t SMAX>
+__global__ void __launch_bounds__(32 * WC_WARPS, SMAX < WC_MAX ? SDM_WC_MIN_BLOCKS : 6) warp_cells_kernel(
+    StepArgs a, WcQueue W, const uint32_t* __restrict__ cells, uint32_t n_cells)
 {
     __shared__ WarpCellSmem<SMAX> ws[WC_WARPS];
-    __shared__ EffTab tab;
     __shared__ unsigned long long red[8];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t step = step_index(a);
     LocalStats ls = {0, 0, 0, 0, 0ull};
-    load_eff_tab(&tab);
     if (threadIdx.x < 5) red[threadIdx.x] = 0;
-    WarpCellSmem<SMAX>& S = ws[warp];
-    if (lane == 0) S.ncomp = 0;
     __syncthreads();
-    uint32_t qcnt = 0;                                        // queued pairs (warp-uniform)
-    const uint32_t stride = gridDim.x * WC_WARPS;
-    for (uint32_t k = blockIdx.x * WC_WARPS + warp; k < n_cells; k += stride) {
-        warp_cell_step<SURR>(a, &tab, S, cells[k], step, qcnt, ls, lane);
-        if (*(volatile uint32_t*)&S.ncomp > WC_CFLUSH) wc_flush<SURR>(a, &tab, S, qcnt, ls, lane);
-    }
-    wc_flush<SURR>(a, &tab, S, qcnt, ls, lane);
+    for (uint32_t k = blockIdx.x * WC_WARPS + warp; k < n_cells; k += gridDim.x * WC_WARPS)
+        warp_cell_step(a, W, ws[warp], cells[k], step, ls, lane);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
+    }
+}
+
+// The queued pairs of the small-cell step, one per thread (a warp takes 32 consecutive entries, so
+// that the surrogate evaluates them together on the tensor cores): the pair's SDs and its cell's
+// constants are gathered, then Step 2 and Step 3 (process_pair).  A cell that lost an SD is listed
+// once for wc_compact_kernel.
+template <bool SURR>
+__global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
+{
+    __shared__ unsigned long long red[8];
+    const EffTab* __restrict__ T = &g_eff_tab;
+    if (threadIdx.x < 5) red[threadIdx.x] = 0;
+    __syncthreads();
+    LocalStats ls = {0, 0, 0, 0, 0ull};
+    const uint32_t nq = *(volatile uint32_t*)W.count;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < nq; base += gridDim.x * blockDim.x) {
+        const uint32_t e = base + lane;
+        const bool act = e < nq;
+        uint4 q = make_uint4(0, 0, 0, 0);
+        if (act) q = __ldcs(W.q + e);
+        const uint32_t cell = q.x;
+        uint64_t g1 = 0, g2 = 0;
+        uint32_t n = 2, kid = 0;
+        double dv = 1.0;
+        if (act) {
+            const uint32_t s0 = a.cell_start[cell];
+            g1 = s0 + (q.y & 0xffffu);
+            g2 = s0 + (q.y >> 16);
+            n = min(a.n_live[cell], a.cell_start[cell + 1] - s0);
+            kid = (uint32_t)a.kid[cell];
+            dv = a.dv[cell];
+        }
+        const double v1 = act ? a.attr[g1] : 0.0, v2 = act ? a.attr[g2] : 0.0;
+        const uint64_t x1 = act ? a.xi[g1] : 1ull, x2 = act ? a.xi[g2] : 1ull;
+        const CellCtx cc{cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
+        float Kh = SURR_PER_LANE;
+        if (SURR && a.precision == PREC_SURROGATE)
+            Kh = surr_pair_kernel_warp(a.surr, v1, v2, act && kid == 1);   // the warp's pairs on the tensor cores
+        uint32_t rflag = 0;
+        const uint64_t u53 = ((((uint64_t)q.w) << 32) | (uint64_t)q.z) >> 11;
+        if (act) process_pair<SURR>(a, T, cc, u53, g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
+        if (rflag && atomicExch(&W.flag[cell], 1u) == 0u) W.cells[atomicAdd(W.count + 1, 1u)] = cell;
+    }
+    if (a.stats) {
+        __syncthreads();
+        flush_stats(a, ls, red);
+    }
+}
+
+// Step 0 of the next step for the cells the queued pairs emptied slots of: each listed cell is
+// compacted stably by one warp.  Resets the queue's counters and flags for the next step (the
+// counts are read once, by every warp, before any is cleared: block 0 clears them after a ticket
+// shows every block has read them).
+__global__ void __launch_bounds__(256) wc_compact_kernel(StepArgs a, WcQueue W, uint32_t* ticket)
+{
+    const uint32_t nc = *(volatile uint32_t*)(W.count + 1);
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nc; k += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t c = W.cells[k];
+        const uint32_t s0 = a.cell_start[c], w = a.cell_start[c + 1] - s0;
+        const uint32_t n_new = warp_compact_cell(a, s0, min(a.n_live[c], w), lane);
+        if (lane == 0) {
+            a.n_live[c] = n_new;
+            W.flag[c] = 0;
+        }
+    }
+    __shared__ uint32_t last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        W.count[0] = 0;
+        W.count[1] = 0;
+        *ticket = 0;
     }
 }
 
