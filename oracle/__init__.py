@@ -28,6 +28,7 @@ _lib = None
 
 KERNEL_GOLOVIN = 0
 KERNEL_GRAVITATIONAL = 1
+KERNEL_ELECTRIC = 2
 SHUFFLE = {"sort": 0, "prp": 1}
 
 
@@ -78,8 +79,12 @@ def lib():
             L.sdmo_efficiency.restype = f64
             L.sdmo_kernel_gravitational.argtypes = [f64, f64]
             L.sdmo_kernel_gravitational.restype = f64
-            L.sdmo_kernel.argtypes = [i32, f64, f64, f64]
+            L.sdmo_kernel.argtypes = [i32, f64, f64, f64, f64]
             L.sdmo_kernel.restype = f64
+            L.sdmo_kernel_electric.argtypes = [f64, f64, f64]
+            L.sdmo_kernel_electric.restype = f64
+            L.sdmo_efficiency_field.argtypes = [f64, f64, f64]
+            L.sdmo_efficiency_field.restype = f64
             L.sdmo_pair_scale.argtypes = [u64]
             L.sdmo_pair_scale.restype = f64
             L.sdmo_pair_prob.argtypes = [f64, u64, u64, f64, f64, f64]
@@ -89,7 +94,7 @@ def lib():
             L.sdmo_update_pair.argtypes = [_p(u64), _p(f64), u32, u64, u64, u64, f64, f64]
             L.sdmo_update_pair.restype = u64
             step_args = [u64, u32, _p(u32), _p(u64), _p(f64), u32, _p(f64), _p(C.c_uint8),
-                         f64, f64, u64, u32]
+                         f64, f64, f64, u64, u32]
             L.sdmo_step.argtypes = step_args + [i32, _p(Stats)]
             L.sdmo_step.restype = i32
             L.sdmo_run.argtypes = step_args + [u32, i32, _p(Stats)]
@@ -139,8 +144,12 @@ def phi(seed, cell, step, m):
     return float(lib().sdmo_phi(seed, cell, step, m))
 
 
-def kernel(kid, v1, v2, golovin_b=1500.0):
-    return float(lib().sdmo_kernel(int(kid), float(v1), float(v2), float(golovin_b)))
+def kernel(kid, v1, v2, golovin_b=1500.0, efield=0.0):
+    return float(lib().sdmo_kernel(int(kid), float(v1), float(v2), float(golovin_b), float(efield)))
+
+
+def efficiency_field(R, q, eps):
+    return float(lib().sdmo_efficiency_field(float(R), float(q), float(eps)))
 
 
 def cbrt(x):
@@ -215,7 +224,7 @@ class System:
     after every step; ``shuffle`` selects the Step 1 contract ("sort" or "prp").
     """
 
-    def __init__(self, xi, attr, cell_start, dv, kernel_id=None, golovin_b=1500.0, shuffle="prp"):
+    def __init__(self, xi, attr, cell_start, dv, kernel_id=None, golovin_b=1500.0, shuffle="prp", efield=0.0):
         self.xi = np.ascontiguousarray(xi, dtype=np.uint64).copy()
         attr = np.asarray(attr, dtype=np.float64)
         if attr.ndim == 1:
@@ -229,6 +238,7 @@ class System:
         self.kernel_id = np.ascontiguousarray(
             np.broadcast_to(np.asarray(kernel_id, np.uint8), (self.n_cell,))).copy()
         self.golovin_b = float(golovin_b)
+        self.efield = float(efield)           # field parameter of the electric-field kernel
         self.shuffle = shuffle
         assert self.attr.shape[1] == self.xi.shape[0]
         lib().sdmo_compact(self.xi.shape[0], self.n_cell, _ptr(self.cell_start, C.c_uint32),
@@ -241,7 +251,7 @@ class System:
     def _args(self):
         return (self.xi.shape[0], self.n_cell, _ptr(self.cell_start, C.c_uint32),
                 _ptr(self.xi, C.c_uint64), _ptr(self.attr, C.c_double), self.attr.shape[0],
-                _ptr(self.dv, C.c_double), _ptr(self.kernel_id, C.c_uint8), self.golovin_b)
+                _ptr(self.dv, C.c_double), _ptr(self.kernel_id, C.c_uint8), self.golovin_b, self.efield)
 
     def step(self, dt, seed, step):
         st = Stats()
@@ -309,4 +319,5 @@ class System:
         return True
 
     def copy(self):
-        return System(self.xi, self.attr, self.cell_start, self.dv, self.kernel_id, self.golovin_b, self.shuffle)
+        return System(self.xi, self.attr, self.cell_start, self.dv, self.kernel_id, self.golovin_b, self.shuffle,
+                      self.efield)

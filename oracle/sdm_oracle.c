@@ -24,6 +24,9 @@
  *                      the paper's listing of the Numba update routine (tie
  *                      rule, g == 0 skip, case-2 attribute expression).
  *   golovin kernel     Sec. 4, a(v1, v2) = b (v1 + v2).
+ *   electric field     Sec. 4 names a parametric kernel for electric-field
+ *                      effects without a formula: project definition below
+ *                      (sdmo_efficiency_field), parity unpinned against physics.
  *   gravitational      Sec. 4 names a "gravitational kernel with parametric
  *                      terminal velocity" but gives no formula; the project
  *                      definition used here is pi (r1+r2)^2 |vt1 - vt2| E(r1,r2)
@@ -238,6 +241,7 @@ double sdmo_phi(uint64_t seed, uint32_t cell, uint32_t step, uint32_t m)
 /* ------------------------------------------------------------------------ */
 #define KERNEL_GOLOVIN 0
 #define KERNEL_GRAVITATIONAL 1
+#define KERNEL_ELECTRIC 2
 
 /* Golovin additive kernel, Sec. 4: a = b (v1 + v2). */
 double sdmo_kernel_golovin(double v1, double v2, double b)
@@ -387,16 +391,30 @@ double sdmo_efficiency(double R, double q)
     }
 }
 
+/* Collision efficiency under an electric field (project definition).  Sec. 4 compares
+ * with a case of Berry (1966) run with a parametric kernel for electric-field effects on
+ * the collision probability, and gives no formula; here the field raises the efficiency
+ * toward one: E_eps = E + eps (1 - E), field parameter eps in [0, 1] (eps = 0: E itself;
+ * eps = 1: every geometric encounter coalesces). */
+double sdmo_efficiency_field(double R, double q, double eps)
+{
+    double E = sdmo_efficiency(R, q);
+    double g = 1.0 - E;
+    g = eps * g;
+    return E + g;
+}
+
 #define SDMO_PI 3.14159265358979311600
-/* Gravitational (hydrodynamic) kernel: pi (r1 + r2)^2 |vt1 - vt2| E. */
-double sdmo_kernel_gravitational(double v1, double v2)
+/* Hydrodynamic kernel pi (r1 + r2)^2 |vt1 - vt2| E, with E the table efficiency
+ * (field = 0) or the field-raised one (field = 1, parameter eps). */
+static double hydro_kernel(double v1, double v2, int field, double eps)
 {
     double r1 = sdmo_radius(v1), r2 = sdmo_radius(v2);
     double vt1 = sdmo_terminal_velocity(r1), vt2 = sdmo_terminal_velocity(r2);
     double R = r1 > r2 ? r1 : r2;
     double rs = r1 > r2 ? r2 : r1;
     double q = rs / R;
-    double E = sdmo_efficiency(R, q);
+    double E = field ? sdmo_efficiency_field(R, q, eps) : sdmo_efficiency(R, q);
     double s = r1 + r2;
     double a = s * s;
     double dv = vt1 - vt2;
@@ -407,9 +425,22 @@ double sdmo_kernel_gravitational(double v1, double v2)
     return K * E;
 }
 
-double sdmo_kernel(int kid, double v1, double v2, double golovin_b)
+/* Gravitational (hydrodynamic) kernel: pi (r1 + r2)^2 |vt1 - vt2| E. */
+double sdmo_kernel_gravitational(double v1, double v2)
+{
+    return hydro_kernel(v1, v2, 0, 0.0);
+}
+
+/* Electric-field kernel: the gravitational kernel with the efficiency E_eps. */
+double sdmo_kernel_electric(double v1, double v2, double eps)
+{
+    return hydro_kernel(v1, v2, 1, eps);
+}
+
+double sdmo_kernel(int kid, double v1, double v2, double golovin_b, double efield)
 {
     if (kid == KERNEL_GOLOVIN) return sdmo_kernel_golovin(v1, v2, golovin_b);
+    if (kid == KERNEL_ELECTRIC) return sdmo_kernel_electric(v1, v2, efield);
     return sdmo_kernel_gravitational(v1, v2);
 }
 
@@ -539,7 +570,7 @@ void sdmo_compact(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
  */
 int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
               uint64_t* xi, double* attr, uint32_t n_attr,
-              const double* dv, const uint8_t* kernel_id, double golovin_b,
+              const double* dv, const uint8_t* kernel_id, double golovin_b, double efield,
               double dt, uint64_t seed, uint32_t step, int shuffle, sdmo_stats* stats)
 {
     uint32_t c;
@@ -585,7 +616,7 @@ int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
         for (m = 0; m < npairs; ++m) {
             double v1 = attr[order[2 * m]];
             double v2 = attr[order[2 * m + 1]];
-            pair_prob[m] = sdmo_kernel(kernel_id ? kernel_id[c] : KERNEL_GOLOVIN, v1, v2, golovin_b);
+            pair_prob[m] = sdmo_kernel(kernel_id ? kernel_id[c] : KERNEL_GOLOVIN, v1, v2, golovin_b, efield);
         }
         scale = sdmo_pair_scale(n);
         for (m = 0; m < npairs; ++m) {
@@ -618,14 +649,14 @@ int sdmo_step(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
 /* Many steps: step indices step0 .. step0 + n_steps - 1. */
 int sdmo_run(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
              uint64_t* xi, double* attr, uint32_t n_attr,
-             const double* dv, const uint8_t* kernel_id, double golovin_b,
+             const double* dv, const uint8_t* kernel_id, double golovin_b, double efield,
              double dt, uint64_t seed, uint32_t step0, uint32_t n_steps, int shuffle, sdmo_stats* total)
 {
     uint32_t s;
     sdmo_stats acc = {0, 0, 0, 0}, st;
     for (s = 0; s < n_steps; ++s) {
         int rc = sdmo_step(n_slots, n_cell, cell_start, xi, attr, n_attr, dv, kernel_id,
-                           golovin_b, dt, seed, step0 + s, shuffle, &st);
+                           golovin_b, efield, dt, seed, step0 + s, shuffle, &st);
         if (rc) return rc;
         acc.n_pairs += st.n_pairs;
         acc.n_collisions += st.n_collisions;
