@@ -76,7 +76,15 @@ typedef enum {
 /* Coalescence kernel a(v1, v2) selected per cell (Sec. 4). */
 typedef enum {
     SDM_KERNEL_GOLOVIN = 0,        /* a = b (v1 + v2), b = sdm_step_params.golovin_b */
-    SDM_KERNEL_GRAVITATIONAL = 1   /* pi (r1+r2)^2 |vt(r1) - vt(r2)| E(r1, r2) */
+    SDM_KERNEL_GRAVITATIONAL = 1,  /* pi (r1+r2)^2 |vt(r1) - vt(r2)| E(r1, r2) */
+    /* Electric-field kernel.  Sec. 4 compares with Berry's case run with a
+     * parametric kernel for electric-field effects on the collision
+     * probability, without giving it; project definition: the gravitational
+     * kernel with the efficiency raised toward one by the field parameter
+     * eps = sdm_step_params.efield in [0, 1], E_eps = E + eps (1 - E)
+     * (eps = 0: the gravitational kernel; eps = 1: the geometric sweep-out
+     * kernel pi (r1+r2)^2 |vt(r1) - vt(r2)|). */
+    SDM_KERNEL_ELECTRIC = 2
 } sdm_kernel_id;
 
 /* Arithmetic of the collision decision (Steps 2-3). */
@@ -117,6 +125,7 @@ typedef struct {
      * 'step' field is ignored), so a captured CUDA graph advances the random
      * stream on every replay. */
     uint32_t* d_step;
+    double efield;             /* field parameter of SDM_KERNEL_ELECTRIC, in [0, 1] (else SDM_EINVAL) */
 } sdm_step_params;
 
 typedef struct {
@@ -323,13 +332,13 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n);
  * |p64 - plite| <= errlite (errlite < 0: not applicable to this pair); pup[i]
  * (nullable) the early exit's upper bound of p from the table of the two
  * volumes' bins and the power of two above max(xi1, xi2), >= p64 and >= p32
- * (+inf for volumes beyond the table).  All arrays are device pointers.
+ * (+inf for volumes beyond the table).  efield: the electric-field kernel's
+ * parameter (SDM_EINVAL outside [0, 1]).  All arrays are device pointers.
  * Exposes Step 2 alone for testing (dependency injection, Sec. 5). */
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2,
-                          const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd,
-                          double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32, double* plite, double* errlite,
-                          float* pup);
+                          const uint64_t* xi1, const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv,
+                          double dt, double golovin_b, double efield, double* p64, float* p32, float* err32,
+                          double* plite, double* errlite, float* pup);
 
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the gravitational kernel (no counterpart in the paper).

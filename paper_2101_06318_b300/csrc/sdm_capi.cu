@@ -255,7 +255,7 @@ sdm_status check_schedule(const sdm_schedule& s)
 // double: [0][b] the bin's upper volume edge, [1][b] pi (2 r)^2 vt(r) Emax (1 + 2^-10)
 // at the bin's upper radius r, Emax the largest efficiency of the table rows that
 // radii in the bin interpolate between; both rounded up to float.
-void fill_pbound_host(float (*t)[PB_SIZE])
+void fill_pbound_host(float (*t)[PB_SIZE])   // t[PB_KINDS]
 {
     constexpr double E_h[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
     auto v_lo = [](uint32_t b) {                 // bin 0 also holds every smaller volume
@@ -294,9 +294,11 @@ void fill_pbound_host(float (*t)[PB_SIZE])
             const double dvt = std::max(0.0, vt(R_hi) - vt(r_lo)) + 0x1p-12 * (vt(R_hi) + vt(r_hi));
             const double sr = R_hi + r_hi;
             t[1][b1 * PB_ROW + d] = up(PI_D * sr * sr * dvt * emax * (1.0 + 0x1p-10));
+            t[2][b1 * PB_ROW + d] = up(PI_D * sr * sr * dvt * (1.0 + 0x1p-10));   // E_eps <= 1
         }
     }
-    for (uint32_t d = 0; d <= PB_ND; ++d) t[0][PB_NB * PB_ROW + d] = t[1][PB_NB * PB_ROW + d] = INFINITY;
+    for (uint32_t d = 0; d <= PB_ND; ++d)
+        for (uint32_t k = 0; k < PB_KINDS; ++k) t[k][PB_NB * PB_ROW + d] = INFINITY;
 }
 
 // Upload the device tables once per device (first use).
@@ -340,7 +342,7 @@ sdm_status ensure_device_tables()
     SDM_TRY(current_context_id(&ctx));
     std::lock_guard<std::mutex> lock(mu);
     if (done_ctx[dev] == ctx + 1) return SDM_OK;
-    static float t[2][PB_SIZE];
+    static float t[PB_KINDS][PB_SIZE];
     fill_pbound_host(t);
     SDM_CUDA(cudaMemcpyToSymbol(g_pbound, t, sizeof t));
     SDM_TRY(set_smem_limits());
@@ -643,7 +645,7 @@ sdm_status set_cells(sdm_state* st, const std::vector<uint32_t>& cs, const doubl
     if (kid) st->h_kid.assign(kid, kid + st->n_cell);
     for (uint32_t c = 0; c < st->n_cell; ++c) {
         if (!(st->h_dv[c] > 0.0) || !std::isfinite(st->h_dv[c])) return SDM_EINVAL;
-        if (st->h_kid[c] > SDM_KERNEL_GRAVITATIONAL) return SDM_EINVAL;
+        if (st->h_kid[c] > SDM_KERNEL_ELECTRIC) return SDM_EINVAL;
     }
     SDM_CUDA(cudaMemcpyAsync(st->d_cell_start, cs.data(), sizeof(uint32_t) * (st->n_cell + 1), cudaMemcpyHostToDevice,
                              st->stream));
@@ -867,6 +869,8 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.golovin_b = p->golovin_b;
     a.dt_f = (float)p->dt;
     a.golovin_bf = (float)p->golovin_b;
+    a.efield = p->efield;
+    a.efield_f = (float)p->efield;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.d_step = p->d_step;
@@ -1167,6 +1171,7 @@ sdm_status sdm_coalescence_step(sdm_state* st, const sdm_step_params* p, uint32_
     if (p->precision == SDM_PREC_SURROGATE && (!st->d_surr || p->shuffle != SDM_SHUFFLE_PRP)) return SDM_EINVAL;
     if (p->shuffle > SDM_SHUFFLE_SORT || p->reserved != 0) return SDM_EINVAL;
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
+    if (!(p->efield >= 0.0 && p->efield <= 1.0)) return SDM_EINVAL;
     if (n_steps == 0) return SDM_OK;
     if (stats) SDM_CUDA(cudaMemsetAsync(st->d_stats, 0, 5 * sizeof(unsigned long long), st->stream));
     SDM_TRY(launch_steps(st, p, n_steps, stats != nullptr));
@@ -1563,15 +1568,17 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
 
 sdm_status sdm_eval_pairs(sdm_state* st, uint32_t kernel_id, const double* v1, const double* v2, const uint64_t* xi1,
                           const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt, double golovin_b,
-                          double* p64, float* p32, float* err32, double* plite, double* errlite, float* pup)
+                          double efield, double* p64, float* p32, float* err32, double* plite, double* errlite,
+                          float* pup)
 {
     if (!st || !v1 || !v2 || !xi1 || !xi2 || !p64 || !p32 || !err32) return SDM_EINVAL;
-    if (kernel_id > SDM_KERNEL_GRAVITATIONAL || n_cell_sd < 2 || !(dv > 0) || !(dt > 0)) return SDM_EINVAL;
+    if (kernel_id > SDM_KERNEL_ELECTRIC || n_cell_sd < 2 || !(dv > 0) || !(dt > 0)) return SDM_EINVAL;
+    if (!(efield >= 0.0 && efield <= 1.0)) return SDM_EINVAL;
     if (n == 0) return SDM_OK;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 8 * (uint64_t)st->n_sm);
     if ((plite == nullptr) != (errlite == nullptr)) return SDM_EINVAL;
-    eval_pairs_kernel<<<grid, 256, 0, st->stream>>>(kernel_id, v1, v2, xi1, xi2, n, n_cell_sd, dv, dt, golovin_b, p64,
-                                                    p32, err32, plite, errlite, pup);
+    eval_pairs_kernel<<<grid, 256, 0, st->stream>>>(kernel_id, v1, v2, xi1, xi2, n, n_cell_sd, dv, dt, golovin_b,
+                                                    efield, p64, p32, err32, plite, errlite, pup);
     SDM_CUDA(cudaGetLastError());
     return SDM_OK;
 }
@@ -1626,10 +1633,11 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
 {
     if (!p || (n_sd && (!xi || !attr)) || n_attr == 0 || attr_stride < n_sd) return SDM_EINVAL;
     if (n_sd > SDM_NOALLOC_MAX_SD) return SDM_ECAPACITY;
-    if (kernel_id > SDM_KERNEL_GRAVITATIONAL || !(dv > 0.0) || !std::isfinite(dv)) return SDM_EINVAL;
+    if (kernel_id > SDM_KERNEL_ELECTRIC || !(dv > 0.0) || !std::isfinite(dv)) return SDM_EINVAL;
     if (!(p->dt > 0.0) || !std::isfinite(p->dt) || p->precision > SDM_PREC_FP32) return SDM_EINVAL;
     if (p->shuffle > SDM_SHUFFLE_SORT || p->reserved != 0) return SDM_EINVAL;
     if (!(p->golovin_b >= 0.0) || !std::isfinite(p->golovin_b)) return SDM_EINVAL;
+    if (!(p->efield >= 0.0 && p->efield <= 1.0)) return SDM_EINVAL;
     if (n_sd < 2) return SDM_OK;
     unsigned char* base = nullptr;
     SDM_TRY(noalloc_scratch(&base));
@@ -1690,6 +1698,8 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.golovin_b = p->golovin_b;
     a.dt_f = (float)p->dt;
     a.golovin_bf = (float)p->golovin_b;
+    a.efield = p->efield;
+    a.efield_f = (float)p->efield;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.step = p->step;

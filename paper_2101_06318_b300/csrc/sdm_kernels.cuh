@@ -62,8 +62,10 @@ struct StepArgs {
     const uint8_t* kid;         // [n_cell]
     double dt;
     double golovin_b;
-    float dt_f;                 // dt and golovin_b rounded to float on the host
+    double efield;              // field parameter of the electric-field kernel, in [0, 1]
+    float dt_f;                 // dt, golovin_b and efield rounded to float on the host
     float golovin_bf;
+    float efield_f;
     uint32_t seed_lo, seed_hi;
     uint32_t step;              // used when d_step == nullptr
     uint32_t shuffle;           // SHUFFLE_PRP or SHUFFLE_SORT
@@ -148,12 +150,14 @@ __device__ __forceinline__ void process_pair(const StepArgs& a, const EffTab* __
     float Kh = -1.0f;
     if (SURR && a.precision == PREC_SURROGATE && c.kid == 1)
         Kh = Kh_in != SURR_PER_LANE ? Kh_in : surr_pair_kernel(a.surr, v1, v2);
-    const P32 pe = Kh >= 0.0f ? P32{Kh * scale32, 0.0f} : pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf);
+    const P32 pe = Kh >= 0.0f ? P32{Kh * scale32, 0.0f}
+                              : pair_prob_f(T, c.kid, v1, v2, scale32, a.golovin_bf, a.efield_f);
     if (a.precision != PREC_FP64) {
         g = gamma_tilde_f(pe.p, u53, xj, xk);
     } else if (!gamma_tilde_certified(pe, u53, xj, xk, &g)) {
-        if (c.kid == 0 || !gamma_tilde_lite(v1, v2, c.n, a.dt, c.dv, u53, xj, xk, &g))
-            g = gamma_tilde_fp64_path(c.kid, v1, v2, a.golovin_b, c.n, a.dt, c.dv, u53, xj, xk);
+        // the second filter serves the gravitational kernel; the others go to the exact sequence
+        if (c.kid != 1 || !gamma_tilde_lite(v1, v2, c.n, a.dt, c.dv, u53, xj, xk, &g))
+            g = gamma_tilde_fp64_path(c.kid, v1, v2, a.golovin_b, a.efield, c.n, a.dt, c.dv, u53, xj, xk);
         ls.fp64++;
     }
     ls.pairs++;
@@ -621,7 +625,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         const CellCtx& cc = ctx[c];
         U4 w = {0, 0, 0, 0};
         if (valid) w = philox(M, cc.gid, step, 1u, a.seed_lo, a.seed_hi);
-        const float* __restrict__ tb = g_pbound[cc.kid ? 1 : 0];
+        const float* __restrict__ tb = g_pbound[cc.kid];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t m = 2 * M + h;
@@ -1015,7 +1019,7 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
     // Steps 2-3 up to the early exit: two pairs per lane and Philox call
     const float s32 = pair_ratio_dtdv_f(n, a.dt_f, dv);
     const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xup);
-    const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
+    const float* __restrict__ tb = g_pbound[kid];
     const uint32_t npairs = n >> 1, G2 = (npairs + 1) >> 1;
     const uint32_t* __restrict__ srt2 = reinterpret_cast<const uint32_t*>(S.srt);   // pair m = srt2[m]
     for (uint32_t base = 0; base < G2; base += 32) {           // warp-uniform trip count
@@ -1704,7 +1708,7 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
         const float xup = __ull2float_ru(L.xmax[c]);
         Prp P;
         prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, C.width);
-        const float* __restrict__ tb = g_pbound[kid ? 1 : 0];
+        const float* __restrict__ tb = g_pbound[kid];
         uint32_t* const rflag = &bk.removed[c];
         const uint32_t npairs = n >> 1;
         if (n >= PRP_MIN_N) {
@@ -2126,7 +2130,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     if (m_lo > m_hi) return;
     const float c_upx = __fmul_ru(exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision),
                                   __ull2float_ru(xmax[big]));
-    const float* __restrict__ tb = g_pbound[cc.kid ? 1 : 0];
+    const float* __restrict__ tb = g_pbound[cc.kid];
     const uint8_t* __restrict__ vbin = a.vbin;
     const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
     // the warp's queue carries over from bucket to bucket of one cell (fewer, fuller drains)
@@ -2446,23 +2450,23 @@ __global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* _
 
 __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* v2, const uint64_t* xi1,
                                   const uint64_t* xi2, uint64_t n, uint32_t n_cell_sd, double dv, double dt,
-                                  double golovin_b, double* p64, float* p32, float* err32, double* plite,
-                                  double* errlite, float* pup)
+                                  double golovin_b, double efield, double* p64, float* p32, float* err32,
+                                  double* plite, double* errlite, float* pup)
 {
     __shared__ EffTab tab;
     load_eff_tab(&tab);
     __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t xmax = xi1[i] > xi2[i] ? xi1[i] : xi2[i];
-        const double K = kernel_d(kid, v1[i], v2[i], golovin_b);
+        const double K = kernel_d(kid, v1[i], v2[i], golovin_b, efield);
         p64[i] = pair_prob_d(K, xmax, n_cell_sd, dt, dv);
         const float scale32 = u64_to_f_trunc(xmax) * pair_ratio_dtdv_f(n_cell_sd, (float)dt, dv);
-        const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b);
+        const P32 pe = pair_prob_f(&tab, kid, v1[i], v2[i], scale32, (float)golovin_b, (float)efield);
         p32[i] = pe.p;
         err32[i] = pe.err;
         if (pup) {
             const float cup = exit_scale(pair_ratio_dtdv_f(n_cell_sd, (float)dt, dv), kid, (float)golovin_b, PREC_FP64);
-            pup[i] = __fmul_ru(__fmul_ru(__ldg(&g_pbound[kid ? 1 : 0][pb_index(vbin_of(v1[i]), vbin_of(v2[i]))]), cup),
+            pup[i] = __fmul_ru(__fmul_ru(__ldg(&g_pbound[kid][pb_index(vbin_of(v1[i]), vbin_of(v2[i]))]), cup),
                                xi_pow2_above(xi1[i], xi2[i]));
         }
         if (plite) {

@@ -327,19 +327,26 @@ __device__ __forceinline__ double efficiency_d(double R, double q)
     return __dadd_rn(e0, __dmul_rn(t, __dsub_rn(e1, e0)));
 }
 
-__device__ __noinline__ double kernel_grav_d(double v1, double v2)
+// Hydrodynamic kernel pi (r1+r2)^2 |vt1 - vt2| E: the gravitational kernel (field = false), or the
+// electric-field kernel (project definition; Sec. 4 names a parametric kernel for electric-field
+// effects without a formula), whose efficiency the field parameter eps in [0, 1] raises toward
+// one: E_eps = E + eps (1 - E).
+__device__ __noinline__ double kernel_hydro_d(double v1, double v2, bool field, double eps)
 {
     const double r1 = radius_d(v1), r2 = radius_d(v2);
     const double vt1 = vt_d(r1), vt2 = vt_d(r2);
     const double R = r1 > r2 ? r1 : r2;
     const double rs = r1 > r2 ? r2 : r1;
-    const double E = efficiency_d(R, __ddiv_rn(rs, R));
+    double E = efficiency_d(R, __ddiv_rn(rs, R));
+    if (field) E = __dadd_rn(E, __dmul_rn(eps, __dsub_rn(1.0, E)));
     const double s = __dadd_rn(r1, r2);
     double a = __dmul_rn(s, s);
     a = __dmul_rn(PI_D, a);
     const double dv = fabs(__dsub_rn(vt1, vt2));
     return __dmul_rn(__dmul_rn(a, dv), E);
 }
+
+__device__ __forceinline__ double kernel_grav_d(double v1, double v2) { return kernel_hydro_d(v1, v2, false, 0.0); }
 
 __device__ __forceinline__ double kernel_golovin_d(double v1, double v2, double b)
 {
@@ -373,18 +380,18 @@ __device__ __forceinline__ uint64_t gamma_tilde_d(double p, uint64_t u53, uint64
     return g < cap ? g : cap;
 }
 
-__device__ __forceinline__ double kernel_d(uint32_t kid, double v1, double v2, double golovin_b)
+__device__ __forceinline__ double kernel_d(uint32_t kid, double v1, double v2, double golovin_b, double efield)
 {
-    return kid == 0 ? kernel_golovin_d(v1, v2, golovin_b) : kernel_grav_d(v1, v2);
+    return kid == 0 ? kernel_golovin_d(v1, v2, golovin_b) : kernel_hydro_d(v1, v2, kid == 2, efield);
 }
 
 // The whole FP64 decision of one pair: kernel, eq. (p), gamma~.  Kept out of line so
 // that none of its (slow on B300) FP64 work is hoisted into the common path.
 __device__ __noinline__ uint64_t gamma_tilde_fp64_path(uint32_t kid, double v1, double v2, double golovin_b,
-                                                       uint32_t n, double dt, double dv, uint64_t u53,
+                                                       double efield, uint32_t n, double dt, double dv, uint64_t u53,
                                                        uint64_t xi_j, uint64_t xi_k)
 {
-    const double K = kernel_d(kid, v1, v2, golovin_b);
+    const double K = kernel_d(kid, v1, v2, golovin_b, efield);
     const double p = pair_prob_d(K, xi_j, n, dt, dv);
     return gamma_tilde_d(p, u53, xi_j, xi_k);
 }
@@ -678,10 +685,11 @@ __device__ __forceinline__ float efficiency_f_err(const EffTab* __restrict__ T, 
     return e0 + t * (e1 - e0);
 }
 
-// p in FP32 with its bound.  scale32 = max(xi) * S_c * dt / dV in FP32.
-// A non-finite or NaN err marks the pair for the FP64 path.
+// p in FP32 with its bound.  scale32 = max(xi) * S_c * dt / dV in FP32; efield_f the electric-field
+// kernel's field parameter rounded to float.  A non-finite or NaN err marks the pair for the FP64
+// path.
 __device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_t kid, double v1d, double v2d,
-                                           float scale32, float golovin_bf)
+                                           float scale32, float golovin_bf, float efield_f = 0.0f)
 {
     const float v1 = d2f_trunc(v1d), v2 = d2f_trunc(v2d);
     P32 o;
@@ -697,7 +705,13 @@ __device__ __forceinline__ P32 pair_prob_f(const EffTab* __restrict__ T, uint32_
     const float vt1 = vt_f(r1), vt2 = vt_f(r2);
     const float R = fmaxf(r1, r2), rs = fminf(r1, r2);
     float dE;
-    const float E = efficiency_f_err(T, R, rs / R, dE);
+    float E = efficiency_f_err(T, R, rs / R, dE);
+    if (kid == 2) {
+        // E_eps = E + eps (1 - E): the error of E passes times 1 - eps <= 1; the three roundings
+        // and the rounding of eps add at most 4u (u = 2^-24; E_eps <= 1), so dE + 5u bounds it
+        E = E + efield_f * (1.0f - E);
+        if (dE >= 0.0f) dE += 5.0f * 0x1p-24f;
+    }
     const float s = r1 + r2;
     const float base = scale32 * ((float)PI_D * (s * s));
     const float dvt = fabsf(vt1 - vt2), svt = vt1 + vt2;
@@ -775,7 +789,8 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
 //   (smaller volume anywhere in [0, upper edge of bin b1 - PB_ND)):
 //     Golovin: the sum of the two upper edges (K = b (v1 + v2));
 //     gravitational: pi (R+ + r+)^2 (vt(R+) - vt(r-) + 2^-12 (vt(R+) + vt(r+)))
-//     Emax, with R+- and r+- the radii at the bins' edges (vt grows with the
+//     Emax (electric field: Emax = 1, the bound of E_eps for every field parameter),
+//     with R+- and r+- the radii at the bins' edges (vt grows with the
 //     radius, so |vt1 - vt2| <= vt(R+) - vt(r-); the 2^-12 term covers the
 //     FP32 path's error, which is relative to vt1 + vt2) and Emax the largest
 //     efficiency node of the table rows and columns the interpolation can
@@ -794,7 +809,8 @@ constexpr uint32_t PB_HI0 = (uint32_t)(1023 + PB_EMIN) << 2;      // (high word 
 constexpr uint32_t PB_ND = 32;                                    // bin distances 0 .. PB_ND - 1, then the rest
 constexpr uint32_t PB_ROW = PB_ND + 1;
 constexpr uint32_t PB_SIZE = (PB_NB + 1) * PB_ROW;                // row PB_NB: +inf
-__device__ float g_pbound[2][PB_SIZE];
+constexpr uint32_t PB_KINDS = 3;                                  // Golovin, gravitational, electric field
+__device__ float g_pbound[PB_KINDS][PB_SIZE];
 
 // Early-exit key of a volume: the top 14 bits of its high word (sign, exponent, two
 // mantissa bits).  Non-negative doubles order as their keys.

@@ -23,6 +23,7 @@ _lib = None
 PREC = {"fp64": 0, "fp32": 1, "surrogate": 2}
 KERNEL_GOLOVIN = 0
 KERNEL_GRAVITATIONAL = 1
+KERNEL_ELECTRIC = 2
 
 STATUS = {0: "SDM_OK", 1: "SDM_EINVAL", 2: "SDM_ENOMEM", 3: "SDM_ECAPACITY", 4: "SDM_ERANGE",
           5: "SDM_ECUDA", 6: "SDM_ETIMEOUT", 7: "SDM_ENOTSUP"}
@@ -55,7 +56,7 @@ SHUFFLE = {"prp": 0, "sort": 1}
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("golovin_b", C.c_double), ("seed", C.c_uint64), ("step", C.c_uint32),
                 ("precision", C.c_uint32), ("shuffle", C.c_uint32), ("reserved", C.c_uint32),
-                ("d_step", C.c_void_p)]
+                ("d_step", C.c_void_p), ("efield", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -108,7 +109,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_sync.argtypes = [vp]
         L.sdm_free.argtypes = [vp]
         L.sdm_free.restype = None
-        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, vp, vp, vp, vp, vp, vp]
+        L.sdm_eval_pairs.argtypes = [vp, u32, vp, vp, vp, vp, u64, u32, f64, f64, f64, f64, vp, vp, vp, vp, vp, vp]
         L.sdm_set_profiling.argtypes = [vp, i32]
         L.sdm_get_profile.argtypes = [vp, vp, vp]
         L.sdm_launches_per_step.argtypes = [vp, u32, vp]
@@ -242,9 +243,9 @@ class State:
 
     # -- the step ----------------------------------------------------------------
     def step(self, dt=1.0, seed=42, step=0, n_steps=1, precision="fp64", golovin_b=1500.0, d_step=None,
-             stats=False, shuffle="prp"):
+             stats=False, shuffle="prp", efield=0.0):
         p = StepParams(float(dt), float(golovin_b), int(seed), int(step), PREC[precision], SHUFFLE[shuffle], 0,
-                       None if d_step is None else d_step.data_ptr())
+                       None if d_step is None else d_step.data_ptr(), float(efield))
         st = StepStats()
         _check(self._L.sdm_coalescence_step(self._h, C.byref(p), int(n_steps), C.byref(st) if stats else None),
                "sdm_coalescence_step")
@@ -338,7 +339,7 @@ class State:
 
     # -- Step 2 alone (testing) ---------------------------------------------------
     def eval_pairs(self, kernel_id, v1, v2, xi1, xi2, n_cell_sd, dv, dt=1.0, golovin_b=1500.0, lite=False,
-                   bound=False):
+                   bound=False, efield=0.0):
         """All arguments are CUDA tensors; returns (p64, p32, err32) CUDA tensors, with lite=True
         also the second filter's (plite, errlite), with bound=True also the early exit's bound."""
         torch = _torch()
@@ -351,7 +352,8 @@ class State:
         pu = torch.empty(n, dtype=torch.float32, device=v1.device) if bound else None
         _check(self._L.sdm_eval_pairs(self._h, int(kernel_id), C.c_void_p(v1.data_ptr()), C.c_void_p(v2.data_ptr()),
                                       C.c_void_p(xi1.data_ptr()), C.c_void_p(xi2.data_ptr()), n, int(n_cell_sd),
-                                      float(dv), float(dt), float(golovin_b), C.c_void_p(p64.data_ptr()),
+                                      float(dv), float(dt), float(golovin_b), float(efield),
+                                      C.c_void_p(p64.data_ptr()),
                                       C.c_void_p(p32.data_ptr()), C.c_void_p(e32.data_ptr()),
                                       C.c_void_p(pl.data_ptr() if lite else None),
                                       C.c_void_p(el.data_ptr() if lite else None),

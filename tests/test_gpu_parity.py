@@ -24,9 +24,9 @@ from paper_2101_06318_b300 import sdm  # noqa: E402
 SHUFFLES = ["prp", "sort"]
 
 
-def _oracle_system(s, attr=None, shuffle="prp"):
+def _oracle_system(s, attr=None, shuffle="prp", efield=0.0):
     a = s["v"][None, :] if attr is None else attr
-    return oracle.System(s["xi"], a, s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle)
+    return oracle.System(s["xi"], a, s["cell_start"], s["dv"], s["kernel_id"], s["golovin_b"], shuffle, efield)
 
 
 def _gpu_state(s, attr=None, schedule=None):
@@ -254,6 +254,29 @@ def test_many_large_cells_bitexact():
     assert ost["n_collisions"] == gst["n_collisions"]
 
 
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_electric_field_kernel_bitexact(shuffle):
+    """The electric-field kernel (project definition: the gravitational kernel with efficiency
+    E + eps (1 - E)) on every path: cells of one warp, tiles, large cells; two field parameters
+    in turn; against the oracle with the same parameter."""
+    rng = np.random.default_rng(17)
+    counts = np.r_[rng.poisson(120, 300), rng.poisson(380, 100), [700, 900], [5000, 20000]]
+    n = int(counts.sum())
+    xi = np.floor(np.exp(rng.random(n) * np.log(1e6))).astype(np.uint64) + 1
+    v = inputs.lognormal_volumes(rng, n, 14e-6, 1.8)
+    s = inputs._state(xi, v, counts, 1e-3, 2, "electric_cells")
+    for eps, step0 in ((0.35, 0), (1.0, 6)):
+        o = _oracle_system(s, shuffle=shuffle, efield=eps)
+        ost = o.run(s["dt"], 9, step0, 6)
+        g = _gpu_state(s)
+        gst = g.step(s["dt"], 9, step0, 6, stats=True, shuffle=shuffle, efield=eps)
+        xg, ag, _ = g.get_state()
+        assert g.check() == (0, 0)
+        g.close()
+        _assert_bitexact(o, xg, ag)
+        assert gst["n_collisions"] == ost["n_collisions"] > 1000
+
+
 @pytest.mark.parametrize("layout", ["few", "many"])
 def test_prp_steps_with_removals_every_step(layout):
     """Large cells that lose SDs in every step, under the PRP contract: each launch compacts the
@@ -312,12 +335,13 @@ def test_fp32_bound_holds_and_fp64_matches_oracle():
     g = sdm.State(16, 1)
     dev = lambda a: torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
     worst = 0.0
-    for kid, ncell, dv in ((1, 1 << 20, 1e6), (0, 8192, 1e6), (1, 127, 1e3)):
-        p64, p32, e32 = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv)
+    for kid, ncell, dv, eps in ((1, 1 << 20, 1e6, 0.0), (0, 8192, 1e6, 0.0), (1, 127, 1e3, 0.0),
+                                (2, 1 << 20, 1e6, 0.4), (2, 300, 1e3, 1.0), (2, 999, 1e3, 0.0)):
+        p64, p32, e32 = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv, efield=eps)
         p64, p32, e32 = p64.cpu().numpy(), p32.cpu().numpy().astype(np.float64), e32.cpu().numpy().astype(np.float64)
         # FP64 value equals the oracle's bit for bit (sampled)
         for i in rng.choice(n, 2000, replace=False):
-            K = oracle.kernel(kid, v1[i], v2[i], 1500.0)
+            K = oracle.kernel(kid, v1[i], v2[i], 1500.0, eps)
             po = oracle.pair_prob(K, xi1[i], xi2[i], oracle.pair_scale(ncell), 1.0, dv)
             assert p64[i] == po, (kid, i)
         ratio = np.abs(p64 - p32) / e32
@@ -362,8 +386,10 @@ def test_early_exit_bound_holds():
     xi2 = rng.integers(1, 10 ** 9, n).astype(np.uint64)
     g = sdm.State(16, 1)
     dev = lambda a: torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
-    for kid, ncell, dv in ((1, 1 << 20, 1e6), (0, 8192, 1e6), (1, 300, 1e3)):
-        p64, p32, _, pup = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv, bound=True)
+    for kid, ncell, dv, eps in ((1, 1 << 20, 1e6, 0.0), (0, 8192, 1e6, 0.0), (1, 300, 1e3, 0.0),
+                                (2, 1 << 20, 1e6, 0.5), (2, 300, 1e3, 1.0)):
+        p64, p32, _, pup = g.eval_pairs(kid, dev(v1), dev(v2), dev(xi1), dev(xi2), ncell, dv, bound=True,
+                                        efield=eps)
         p64, p32, pup = p64.cpu().numpy(), p32.cpu().numpy().astype(np.float64), pup.cpu().numpy().astype(np.float64)
         assert np.all(pup >= p64), (kid, np.flatnonzero(pup < p64)[:5])
         assert np.all(pup >= p32), (kid, np.flatnonzero(pup < p32)[:5])
@@ -373,7 +399,8 @@ def test_early_exit_bound_holds():
         q = np.minimum(v1, v2) / np.maximum(v1, v2)
         sel = (p64 > 0) & (q > 0.03) & (q < 0.7) if kid else p64 > 0
         ratio = np.median(pup[sel] / p64[sel])
-        assert ratio < 4.0, (kid, ratio)
+        # the electric-field kernel's rows bound its efficiency by 1 (E_eps >= eps >= 0.5 here)
+        assert ratio < (4.0 if kid < 2 else 8.0), (kid, ratio)
 
 
 def _spectrum_l1(a, b):
