@@ -12,6 +12,7 @@ stated in the C file's header.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -104,9 +105,6 @@ def lib():
             L.sdmo_prp.argtypes = [u32, u32, _p(u32)]
             L.sdmo_prp.restype = u32
             L.sdmo_prp_perm.argtypes = [u32, _p(u32), _p(u32)]
-            L.sdmo_spectrum.argtypes = [u64, u32, _p(u32), _p(u64), _p(f64), _p(f64), u32, u32,
-                                        _p(f64), u32, f64, _p(f64)]
-            L.sdmo_spectrum.restype = i32
             L.sdmo_totals.argtypes = [u64, _p(u64), _p(f64), _p(u64), _p(u64), _p(f64)]
             L.sdmo_i1e.argtypes = [f64]
             L.sdmo_i1e.restype = f64
@@ -188,6 +186,7 @@ def update_pair(xi, attr, first, second, p, phi_):
 
 
 PRP_MIN_N = 257          # smaller cells are shuffled by sorting keys
+FOUR_PI_OVER_THREE = 4.18879020478639053
 
 
 def prp_keys(seed, cell, step):
@@ -275,16 +274,31 @@ class System:
         return int(nt.value), int(nl.value), float(m.value)
 
     def spectrum(self, r_edges, rho=1000.0, cell_lo=0, cell_hi=None):
-        r_edges = np.ascontiguousarray(r_edges, np.float64)
-        nb = len(r_edges) - 1
-        out = np.zeros(nb, np.float64)
+        """Mass spectrum dm/dln r (Sec. 4) of the cells [cell_lo, cell_hi): bin b holds the live SDs
+        with ve[b] <= v < ve[b+1], ve = (4 pi/3) r^3 (evaluated as ((4 pi/3) r) r) r);
+        out[b] = rho S_b / (V (ln r[b+1] - ln r[b])) with S_b the sum of the bin's terms xi v (each
+        product rounded once) taken exactly and rounded once (math.fsum), V the cells' dV summed in
+        cell order."""
+        r = np.ascontiguousarray(r_edges, np.float64)
+        nb = len(r) - 1
+        ve = ((FOUR_PI_OVER_THREE * r) * r) * r
         cell_hi = self.n_cell if cell_hi is None else cell_hi
-        rc = lib().sdmo_spectrum(self.xi.shape[0], self.n_cell, _ptr(self.cell_start, C.c_uint32),
-                                 _ptr(self.xi, C.c_uint64), _ptr(self.attr, C.c_double),
-                                 _ptr(self.dv, C.c_double), cell_lo, cell_hi,
-                                 _ptr(r_edges, C.c_double), nb, float(rho), _ptr(out, C.c_double))
-        if rc:
-            raise RuntimeError("sdmo_spectrum failed")
+        s0, s1 = int(self.cell_start[cell_lo]), int(self.cell_start[cell_hi])
+        xi = self.xi[s0:s1]
+        v = self.attr[0, s0:s1]
+        sel = (xi != 0) & (ve[0] <= v) & (v < ve[nb])
+        t = xi[sel].astype(np.float64) * v[sel]
+        b = np.searchsorted(ve, v[sel], side="right") - 1          # ve[b] <= v < ve[b + 1]
+        order = np.argsort(b, kind="stable")
+        bounds = np.searchsorted(b[order], np.arange(nb + 1))
+        V = 0.0
+        for c in range(cell_lo, cell_hi):
+            V = V + float(self.dv[c])
+        out = np.zeros(nb, np.float64)
+        for k in range(nb):
+            msum = math.fsum(t[order[bounds[k]:bounds[k + 1]]].tolist())
+            dlnr = math.log(float(r[k + 1])) - math.log(float(r[k]))
+            out[k] = rho * msum / (V * dlnr)
         return out
 
     def rebucket(self, cell_id):

@@ -33,7 +33,9 @@
  *                      with a three-regime power-law vt and a tabulated,
  *                      bilinearly interpolated efficiency E (parity unpinned
  *                      against physics: the paper's comparison data are absent).
- *   spectrum           Sec. 4: mass per unit ln r, rho = 1000 kg/m^3.
+ *   spectrum           Sec. 4: mass per unit ln r, rho = 1000 kg/m^3 (in
+ *                      __init__.py: per bin the exact sum of the terms xi v,
+ *                      rounded once, by math.fsum).
  *   golovin_phi, i1e   Sec. 4, analytic Golovin solution (eq. 36 of Golovin
  *                      1963 as restated in the paper); I1e written from the
  *                      power series of I1 and the large-argument expansion
@@ -670,51 +672,6 @@ int sdmo_run(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
 /* ------------------------------------------------------------------------ */
 /* Diagnostics.                                                              */
 /* ------------------------------------------------------------------------ */
-
-/* Mass spectrum dm/dlnr per bin (Sec. 4): bin b holds live SDs with
- * ve[b] <= v < ve[b+1], ve = (4 pi / 3) r_edge^3;
- * out[b] = rho * sum(xi v) / (V * (ln r[b+1] - ln r[b])).  Slots are summed
- * in slot order; cells with index in [cell_lo, cell_hi) are included and V is
- * the sum of their dV. */
-#define SDMO_FOUR_PI_OVER_THREE 4.18879020478639053
-int sdmo_spectrum(uint64_t n_slots, uint32_t n_cell, const uint32_t* cell_start,
-                  const uint64_t* xi, const double* v, const double* dv,
-                  uint32_t cell_lo, uint32_t cell_hi,
-                  const double* r_edges, uint32_t n_bins, double rho, double* out)
-{
-    uint32_t b, c;
-    double V = 0.0;
-    double* ve = (double*)malloc((n_bins + 1) * sizeof(double));
-    double* msum = (double*)calloc(n_bins, sizeof(double));
-    (void)n_slots; (void)n_cell;
-    if (!ve || !msum) { free(ve); free(msum); return SDMO_ENOMEM; }
-    for (b = 0; b <= n_bins; ++b) {
-        double t = SDMO_FOUR_PI_OVER_THREE * r_edges[b];
-        t = t * r_edges[b];
-        ve[b] = t * r_edges[b];
-    }
-    for (c = cell_lo; c < cell_hi; ++c) {
-        uint64_t i;
-        V = V + dv[c];
-        for (i = cell_start[c]; i < cell_start[c + 1]; ++i) {
-            if (xi[i] == 0) continue;
-            for (b = 0; b < n_bins; ++b) {
-                if (ve[b] <= v[i] && v[i] < ve[b + 1]) {
-                    double t = (double)xi[i] * v[i];
-                    msum[b] = msum[b] + t;
-                    break;
-                }
-            }
-        }
-    }
-    for (b = 0; b < n_bins; ++b) {
-        double dlnr = log(r_edges[b + 1]) - log(r_edges[b]);
-        out[b] = rho * msum[b] / (V * dlnr);
-    }
-    free(ve);
-    free(msum);
-    return SDMO_OK;
-}
 
 /* Totals over live SDs: sums[0] = sum xi (exact, returned via n_total),
  * sums[1] = sum xi * v (compensated summation), n_live. */

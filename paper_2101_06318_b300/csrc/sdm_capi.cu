@@ -31,6 +31,7 @@ constexpr uint32_t FINISH_SMEM_WAVE = 110 * 1024;   // the same, two per SM (all
 constexpr uint32_t FINISH_SMEM_MAX = 200 * 1024;   // a single-warp CTA for very wide buckets
 constexpr uint32_t SCATTER_SMEM_MAX = 2 * sizeof(uint32_t) * (1u << BIG_MAX_BUCKET_BITS);
 constexpr uint32_t TILE_SMEM_MAX = 227 * 1024;
+constexpr uint32_t SPECTRUM_SMEM_MAX = 96 * 1024;   // the exact per-bin sums of one block
 
 // records a bucket holds: its mean count plus ten standard deviations of the count (a
 // binomial of mean m, standard deviation below sqrt(m)) plus 32; an overflow is reported
@@ -420,6 +421,48 @@ BigBook big_book(const sdm_state* st)
 {
     uint32_t* tw = st->d_big_removed + big_ticket_word(st->n_big);
     return BigBook{(unsigned long long*)tw, st->d_big_removed, st->n_big, tw + 2};
+}
+
+// The value of sum_k words[k] 2^(lsb + 32 k) (words below 2^64), rounded once to the nearest double
+// (ties to even): the digits are carried into base 2^32, the leading 64 bits taken with a sticky bit
+// for the rest, and the 53-bit significand rounded from them.
+double exact_words_to_double(const unsigned long long* words, uint32_t W, int lsb)
+{
+    std::vector<uint32_t> d(W + 2, 0u);
+    unsigned __int128 carry = 0;
+    for (uint32_t k = 0; k < W + 2; ++k) {
+        const unsigned __int128 x = carry + (k < W ? (unsigned __int128)words[k] : 0);
+        d[k] = (uint32_t)x;
+        carry = x >> 32;
+    }
+    int top = (int)W + 1;
+    while (top >= 0 && d[top] == 0) --top;
+    if (top < 0) return 0.0;
+    // the leading 64 bits: digits top, top-1 and the high part of top-2; everything below is sticky
+    const int lz = __builtin_clz(d[top]);
+    const int nbits = 32 * top + (32 - lz);                 // bit length of the integer
+    unsigned __int128 acc = 0;
+    for (int k = top; k >= 0 && k >= top - 2; --k) acc = (acc << 32) | d[k];
+    int below = 32 * std::max(0, top - 2);                  // bits of the integer not in acc
+    bool sticky = false;
+    for (int k = top - 3; k >= 0; --k) sticky = sticky || d[k] != 0;
+    const int acc_bits = nbits - below;                     // significant bits held in acc
+    uint64_t sig;
+    int exp2;                                               // value = sig 2^exp2 (before rounding)
+    if (acc_bits <= 53) {
+        sig = (uint64_t)acc << (53 - acc_bits);
+        exp2 = lsb + below - (53 - acc_bits);
+    } else {
+        const int drop = acc_bits - 53;
+        sig = (uint64_t)(acc >> drop);
+        const unsigned __int128 rest = acc & (((unsigned __int128)1 << drop) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (drop - 1);
+        const bool st = sticky || (rest & (half - 1)) != 0;
+        if ((rest & half) && (st || (sig & 1u))) ++sig;     // round half to even
+        exp2 = lsb + below + drop;
+        if (sig >> 53) { sig >>= 1; ++exp2; }               // the rounding carried into a new bit
+    }
+    return std::ldexp((double)sig, exp2);
 }
 
 // Clears the device error word after the host has read it.  A grid barrier that gave up
@@ -1354,7 +1397,8 @@ sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, u
 {
     if (!st || !st->initialised || !r_edges || !out || n_bins == 0) return SDM_EINVAL;
     for (uint32_t b = 0; b < n_bins; ++b)
-        if (!(r_edges[b] > 0.0) || !(r_edges[b + 1] > r_edges[b])) return SDM_EINVAL;
+        if (!(r_edges[b] > 0.0) || !(r_edges[b + 1] > r_edges[b]) || !std::isfinite(r_edges[b + 1]))
+            return SDM_EINVAL;
     SDM_TRY(flush_big_compaction(st));
     uint32_t c0 = 0, c1 = st->n_cell;
     if (cell != UINT32_MAX) {
@@ -1368,26 +1412,38 @@ sdm_status sdm_spectrum(sdm_state* st, const double* r_edges, uint32_t n_bins, u
         t = t * r_edges[b];
         ve[b] = t * r_edges[b];
     }
+    // the fixed-point grid of the exact sums (see spectrum_exact_kernel)
+    if (!(ve[0] >= 0x1p-1000) || !std::isfinite(ve[n_bins])) return SDM_EINVAL;
+    int e_lo = 0, e_hi = 0;
+    std::frexp(ve[0], &e_lo);                       // ve[0] in [2^(e_lo-1), 2^e_lo)
+    std::frexp(ve[n_bins], &e_hi);                  // ve[n] < 2^e_hi, so a term < 2^(e_hi + 53)
+    const int lsb = (e_lo - 1) - 52;
+    const uint32_t W = (uint32_t)((e_hi - lsb) >> 5) + 3;
+    const size_t smem = sizeof(unsigned long long) * (size_t)n_bins * W;
+    if (smem > SPECTRUM_SMEM_MAX) return SDM_EINVAL;   // edges spanning an absurd range of volumes
+    SDM_CUDA(cudaFuncSetAttribute(spectrum_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SPECTRUM_SMEM_MAX));
     double* d_ve = nullptr;
-    double* d_sum = nullptr;
-    SDM_CUDA(cudaMallocAsync((void**)&d_ve, sizeof(double) * (2 * n_bins + 1), st->stream));
-    d_sum = d_ve + n_bins + 1;
+    SDM_CUDA(cudaMallocAsync((void**)&d_ve, sizeof(double) * (n_bins + 1) + smem, st->stream));
+    unsigned long long* d_acc = (unsigned long long*)(d_ve + n_bins + 1);
+    std::vector<unsigned long long> words((size_t)n_bins * W);
     sdm_status rs = SDM_OK;
     do {
         if (cudaMemcpyAsync(d_ve, ve.data(), sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice, st->stream) ||
-            cudaMemsetAsync(d_sum, 0, sizeof(double) * n_bins, st->stream)) { rs = SDM_ECUDA; break; }
+            cudaMemsetAsync(d_acc, 0, smem, st->stream)) { rs = SDM_ECUDA; break; }
         const uint64_t s0 = st->h_cell_start[c0], s1 = st->h_cell_start[c1];
         if (s1 > s0) {
             const uint32_t grid = (uint32_t)std::min<uint64_t>((s1 - s0 + 255) / 256, 2 * (uint64_t)st->n_sm);
-            spectrum_kernel<<<grid, 256, sizeof(double) * n_bins, st->stream>>>(st->d_xi, st->d_attr, s0, s1, d_ve,
-                                                                               n_bins, d_sum);
+            spectrum_exact_kernel<<<grid, 256, smem, st->stream>>>(st->d_xi, st->d_attr, s0, s1, d_ve, n_bins, lsb,
+                                                                  W, d_acc);
             if (cudaGetLastError() != cudaSuccess) { rs = SDM_ECUDA; break; }
         }
-        if (cudaMemcpyAsync(msum.data(), d_sum, sizeof(double) * n_bins, cudaMemcpyDeviceToHost, st->stream) ||
+        if (cudaMemcpyAsync(words.data(), d_acc, smem, cudaMemcpyDeviceToHost, st->stream) ||
             cudaStreamSynchronize(st->stream)) { rs = SDM_ECUDA; break; }
     } while (0);
     cudaFreeAsync(d_ve, st->stream);
     if (rs != SDM_OK) return rs;
+    for (uint32_t b = 0; b < n_bins; ++b) msum[b] = exact_words_to_double(&words[(size_t)b * W], W, lsb);
     double V = 0.0;
     for (uint32_t c = c0; c < c1; ++c) V = V + st->h_dv[c];
     std::vector<double> res(n_bins);

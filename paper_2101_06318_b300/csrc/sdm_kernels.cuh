@@ -2423,12 +2423,19 @@ __global__ void totals_kernel(const uint64_t* __restrict__ xi, const double* __r
     }
 }
 
-// mass per bin: bin b holds ve[b] <= v < ve[b+1]
-__global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ v, uint64_t s0,
-                                uint64_t s1, const double* __restrict__ ve, uint32_t n_bins, double* out)
+// Mass per bin, exactly: bin b holds the live SDs with ve[b] <= v < ve[b+1].  Each term xi v is
+// rounded once (the definition's terms) and is an integer multiple of 2^lsb (lsb: the unit of the
+// last place of the smallest edge volume's binade); its 53-bit significand, shifted into place, is
+// added as up to three 32-bit digits to 64-bit words (W per bin, word k weighing 2^(lsb + 32 k)).
+// The additions are integer, so the sums do not depend on their order: per block in shared memory,
+// then into acc[n_bins * W] in global memory (zeroed before); the host carries and rounds once.
+// No word overflows: each holds digits below 2^32 of at most 2^32 terms.
+__global__ void spectrum_exact_kernel(const uint64_t* __restrict__ xi, const double* __restrict__ v, uint64_t s0,
+                                      uint64_t s1, const double* __restrict__ ve, uint32_t n_bins, int lsb,
+                                      uint32_t W, unsigned long long* __restrict__ acc)
 {
-    extern __shared__ double bins[];
-    for (uint32_t b = threadIdx.x; b < n_bins; b += blockDim.x) bins[b] = 0.0;
+    extern __shared__ unsigned long long sacc[];   // [n_bins * W]
+    for (uint32_t k = threadIdx.x; k < n_bins * W; k += blockDim.x) sacc[k] = 0ull;
     __syncthreads();
     for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -2441,11 +2448,20 @@ __global__ void spectrum_kernel(const uint64_t* __restrict__ xi, const double* _
             const uint32_t mid = (lo + hi) >> 1;
             if (ve[mid] <= vi) lo = mid; else hi = mid;
         }
-        atomicAdd(&bins[lo], __dmul_rn(__ull2double_rn(x), vi));
+        const double t = __dmul_rn(__ull2double_rn(x), vi);
+        const uint64_t bits = (uint64_t)__double_as_longlong(t);
+        const uint64_t m = (bits & ((1ull << 52) - 1ull)) | (1ull << 52);   // t >= ve[0]: a normal number
+        const uint32_t o = (uint32_t)((int)((bits >> 52) & 0x7ff) - 1075 - lsb);   // t = m 2^(lsb + o)
+        const uint32_t w0 = o >> 5, sh = o & 31u;
+        const uint64_t lo64 = m << sh, hi64 = sh ? (m >> (64u - sh)) : 0ull;
+        unsigned long long* w = sacc + lo * W + w0;
+        atomicAdd(w, lo64 & 0xffffffffull);
+        if (lo64 >> 32) atomicAdd(w + 1, lo64 >> 32);
+        if (hi64) atomicAdd(w + 2, hi64);
     }
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < n_bins; b += blockDim.x)
-        if (bins[b] != 0.0) atomicAdd(&out[b], bins[b]);
+    for (uint32_t k = threadIdx.x; k < n_bins * W; k += blockDim.x)
+        if (sacc[k]) atomicAdd(&acc[k], sacc[k]);
 }
 
 __global__ void eval_pairs_kernel(uint32_t kid, const double* v1, const double* v2, const uint64_t* xi1,

@@ -467,7 +467,9 @@ def test_spectrum_and_totals_match_oracle():
     r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 101))
     so = o.spectrum(r_edges)
     sg = g.spectrum(r_edges)
-    np.testing.assert_allclose(sg, so, rtol=1e-12, atol=0)
+    # both sides sum each bin exactly and round once: equal, and the same on every call
+    assert np.array_equal(sg, so)
+    assert np.array_equal(g.spectrum(r_edges), sg)
     nt, nl, mo = o.totals()
     gn, gm, gl = g.totals()
     assert gn == nt and gl == nl
@@ -475,8 +477,17 @@ def test_spectrum_and_totals_match_oracle():
     # multi-cell spectrum of a single cell and of all
     s2 = inputs.random_cells(n_cell=50, mean_per_cell=100, seed=3)
     o2, g2 = _oracle_system(s2), _gpu_state(s2)
-    np.testing.assert_allclose(g2.spectrum(r_edges, cell=7), o2.spectrum(r_edges, cell_lo=7, cell_hi=8), rtol=1e-12)
-    np.testing.assert_allclose(g2.spectrum(r_edges), o2.spectrum(r_edges), rtol=1e-12)
+    assert np.array_equal(g2.spectrum(r_edges, cell=7), o2.spectrum(r_edges, cell_lo=7, cell_hi=8))
+    assert np.array_equal(g2.spectrum(r_edges), o2.spectrum(r_edges))
+    # a large state whose terms span many binades (multiplicities 1 .. 2^52), volumes on the edges
+    rng = np.random.default_rng(3)
+    s3 = inputs.random_cells(n_cell=64, mean_per_cell=4000, seed=5, xi_max=2 ** 52)
+    ve = ((oracle.FOUR_PI_OVER_THREE * r_edges) * r_edges) * r_edges
+    s3["v"][:500] = ve[rng.integers(0, len(ve), 500)]
+    o3, g3 = _oracle_system(s3), _gpu_state(s3)
+    assert np.array_equal(g3.spectrum(r_edges), o3.spectrum(r_edges))
+    g2.close()
+    g3.close()
 
 
 def test_mass_conservation_and_remove_zero():

@@ -230,3 +230,40 @@ def test_gravitational_kernel_symmetry_and_zero_on_diagonal():
     E = 0.179  # table node R = 100 um, q = 0.1
     want = math.pi * (r1 + r2) ** 2 * abs(vt2 - vt1) * E
     assert oracle.kernel(1, v1, v2) == pytest.approx(want, rel=1e-12)
+
+
+def test_spectrum_is_the_exactly_summed_definition():
+    """Sec. 4 mass spectrum: per bin rho * sum(xi v) / (V dln r), the sum taken exactly over the
+    bin's terms (each xi v rounded once) and rounded once -- checked against exact rational
+    arithmetic (fractions.Fraction, whose float() rounds correctly), on terms of very different
+    magnitudes, with volumes on bin edges (an edge belongs to the bin above it), dead slots and a
+    cell range."""
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 41))
+    ve = ((oracle.FOUR_PI_OVER_THREE * r_edges) * r_edges) * r_edges
+    counts = [300, 0, 500, 200]
+    n = sum(counts)
+    v = np.exp(rng.uniform(np.log(ve[0] * 0.5), np.log(ve[-1] * 1.5), n))
+    v[:40] = ve[rng.integers(0, len(ve), 40)]                      # exactly on edges
+    xi = np.floor(np.exp(rng.uniform(0, np.log(2.0 ** 52), n))).astype(np.uint64) + 1
+    xi[rng.random(n) < 0.1] = 0
+    cs = np.r_[0, np.cumsum(counts)].astype(np.uint32)
+    dv = np.array([1.5e3, 2.0e3, 0.7e3, 1.1e3])
+    s = oracle.System(xi, v, cs, dv)
+    for lo, hi in ((0, 4), (2, 3)):
+        got = s.spectrum(r_edges, cell_lo=lo, cell_hi=hi)
+        a, b = int(s.cell_start[lo]), int(s.cell_start[hi])
+        V = 0.0
+        for c in range(lo, hi):
+            V += float(dv[c])
+        exact = [Fraction(0)] * (len(r_edges) - 1)
+        for i in range(a, b):
+            x, vi = int(s.xi[i]), float(s.v[i])
+            if x == 0 or not (ve[0] <= vi < ve[-1]):
+                continue
+            k = max(j for j in range(len(ve) - 1) if ve[j] <= vi)
+            exact[k] += Fraction(float(x) * vi)                        # the term, rounded once
+        for k in range(len(exact)):
+            dlnr = math.log(r_edges[k + 1]) - math.log(r_edges[k])
+            assert got[k] == 1000.0 * float(exact[k]) / (V * dlnr), k
