@@ -143,8 +143,45 @@ __global__ void surr_targets_kernel(SurrTrainArgs A, uint64_t n, double* K_out)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores for a warp's 32 pairs at once (the queued pairs a
+// step evaluates together).  The samples are the rows of the activation matrix
+// (M = 32: two m16 tiles), the 64 hidden units its columns; the 64 x 64 layers are
+// mma.sync m16n8k16 products with BF16 operands and FP32 accumulation.  An FP32
+// activation x enters as hi + lo with hi = bf16(x), lo = bf16(x - hi), two products
+// per tile, so that the result keeps ~16 bits of each activation (the weights are
+// BF16 already).  The accumulator layout of two adjacent n8 tiles is the operand
+// layout of one k16 slab, so a layer's output feeds the next layer from registers.
+//   fragments (lane = 4 g + t): A regs {(g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..),
+//   (g+8, 2t+8..)}; B regs {(k = 2t..2t+1, n = g), (k = 2t+8.., n = g)};
+//   C/D {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo_elem, float hi_elem)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// hi and lo BF16 operand registers of four FP32 values laid out as one A register pair set
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo)
+{
+    const float h0 = bf16_round(x0), h1 = bf16_round(x1);
+    hi = bf16x2_bits(h0, h1);
+    lo = bf16x2_bits(x0 - h0, x1 - h1);
+}
+
 constexpr int SURR_TB = 64;                // samples per CTA of the training pass
 constexpr int SURR_THREADS = 256;
+
+constexpr int SURR_ZS = SURR_H + 1;         // row stride of the activation arrays (no bank conflicts)
 
 // dynamic shared memory of the training pass
 struct SurrSmem {
@@ -152,21 +189,135 @@ struct SurrSmem {
     float z[SURR_TB][2];
     float t[SURR_TB];
     float y[SURR_TB];
-    float Z1[SURR_TB][SURR_H], Z2[SURR_TB][SURR_H], Z3[SURR_TB][SURR_H];   // pre-activations
-    float D[SURR_TB][SURR_H];                                             // dL/dZ of the current layer
-    float E[SURR_TB][SURR_H];                                             // dL/dZ of the layer below
+    float Z1[SURR_TB][SURR_ZS], Z2[SURR_TB][SURR_ZS], Z3[SURR_TB][SURR_ZS];   // pre-activations
+    float D[SURR_TB][SURR_ZS];                                             // dL/dZ of the current layer
+    float E[SURR_TB][SURR_ZS];                                             // dL/dZ of the layer below
 };
+
+// The 64 x 64 products of the training pass on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 sums).  Each product's output is 4 m16 x 8 n8 tiles; warp w of the 8 takes row
+// tile w & 3 and column tiles 4 (w >> 2) .. + 3.  An FP32 operand x enters as hi + lo (hi =
+// bf16(x), lo = bf16(x - hi)); the weights are BF16 already.  Fragment layout (lane = 4 g + t):
+// A regs (row g, cols 2t..2t+1), (g + 8, 2t..), (g, 2t + 8..), (g + 8, 2t + 8..); B regs
+// (k = 2t..2t+1, col g), (k = 2t + 8.., col g); C (g, 2t), (g, 2t+1), (g + 8, 2t), (g + 8, 2t+1).
+
+// Zout[s][j] = b[j] + sum_k W[j][k] silu(Zin[s][k])  (forward of a hidden layer; rows: samples)
+__device__ __forceinline__ void surr_tc_forward(const float* __restrict__ W, const float* __restrict__ b,
+                                                const float (*Zin)[SURR_ZS], float (*Zout)[SURR_ZS], int warp,
+                                                int lane)
+{
+    const int g = lane >> 2, t = lane & 3, r0 = 16 * (warp & 3) + g, n0 = 32 * (warp >> 2);
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float b0 = b[n0 + 8 * j + 2 * t], b1 = b[n0 + 8 * j + 2 * t + 1];
+        acc[j][0] = b0; acc[j][1] = b1; acc[j][2] = b0; acc[j][3] = b1;
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        const int c = 16 * ks + 2 * t;
+        uint32_t ahi[4], alo[4];
+        split_bf16(silu_f(Zin[r0][c]), silu_f(Zin[r0][c + 1]), ahi[0], alo[0]);
+        split_bf16(silu_f(Zin[r0 + 8][c]), silu_f(Zin[r0 + 8][c + 1]), ahi[1], alo[1]);
+        split_bf16(silu_f(Zin[r0][c + 8]), silu_f(Zin[r0][c + 9]), ahi[2], alo[2]);
+        split_bf16(silu_f(Zin[r0 + 8][c + 8]), silu_f(Zin[r0 + 8][c + 9]), ahi[3], alo[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float* row = W + SURR_H * (n0 + 8 * j + g);          // B(k, n) = W[n][k]
+            const uint32_t b0 = bf16x2_bits(row[c], row[c + 1]), b1 = bf16x2_bits(row[c + 8], row[c + 9]);
+            mma_bf16_16816(acc[j], ahi, b0, b1);
+            mma_bf16_16816(acc[j], alo, b0, b1);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = n0 + 8 * j + 2 * t;
+        Zout[r0][col] = acc[j][0];
+        Zout[r0][col + 1] = acc[j][1];
+        Zout[r0 + 8][col] = acc[j][2];
+        Zout[r0 + 8][col + 1] = acc[j][3];
+    }
+}
+
+// E[s][k] = (sum_j D[s][j] W[j][k]) silu'(Zb[s][k])  (dL/dZ of the layer below)
+__device__ __forceinline__ void surr_tc_backprop(const float* __restrict__ W, const float (*D)[SURR_ZS],
+                                                 const float (*Zb)[SURR_ZS], float (*E)[SURR_ZS], int warp, int lane)
+{
+    const int g = lane >> 2, t = lane & 3, r0 = 16 * (warp & 3) + g, n0 = 32 * (warp >> 2);
+    float acc[4][4] = {};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        const int c = 16 * ks + 2 * t;
+        uint32_t ahi[4], alo[4];
+        split_bf16(D[r0][c], D[r0][c + 1], ahi[0], alo[0]);
+        split_bf16(D[r0 + 8][c], D[r0 + 8][c + 1], ahi[1], alo[1]);
+        split_bf16(D[r0][c + 8], D[r0][c + 9], ahi[2], alo[2]);
+        split_bf16(D[r0 + 8][c + 8], D[r0 + 8][c + 9], ahi[3], alo[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + 8 * j + g;                                 // B(k = j', n) = W[j'][n]
+            const uint32_t b0 = bf16x2_bits(W[SURR_H * c + n], W[SURR_H * (c + 1) + n]);
+            const uint32_t b1 = bf16x2_bits(W[SURR_H * (c + 8) + n], W[SURR_H * (c + 9) + n]);
+            mma_bf16_16816(acc[j], ahi, b0, b1);
+            mma_bf16_16816(acc[j], alo, b0, b1);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = n0 + 8 * j + 2 * t;
+        E[r0][col] = acc[j][0] * silu_grad_f(Zb[r0][col]);
+        E[r0][col + 1] = acc[j][1] * silu_grad_f(Zb[r0][col + 1]);
+        E[r0 + 8][col] = acc[j][2] * silu_grad_f(Zb[r0 + 8][col]);
+        E[r0 + 8][col + 1] = acc[j][3] * silu_grad_f(Zb[r0 + 8][col + 1]);
+    }
+}
+
+// grad[j][k] += sum_s D[s][j] silu(Zb[s][k])  (the layer's weight gradient; K = the 64 samples)
+__device__ __forceinline__ void surr_tc_weight_grad(float* __restrict__ grad, const float (*D)[SURR_ZS],
+                                                    const float (*Zb)[SURR_ZS], int warp, int lane)
+{
+    const int g = lane >> 2, t = lane & 3, m0 = 16 * (warp & 3), n0 = 32 * (warp >> 2);
+    float acc[4][4] = {};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        const int s = 16 * ks + 2 * t;                                   // sample (the K index)
+        uint32_t ahi[4], alo[4];                                          // A(m = j, k = s) = D[s][j]
+        split_bf16(D[s][m0 + g], D[s + 1][m0 + g], ahi[0], alo[0]);
+        split_bf16(D[s][m0 + g + 8], D[s + 1][m0 + g + 8], ahi[1], alo[1]);
+        split_bf16(D[s + 8][m0 + g], D[s + 9][m0 + g], ahi[2], alo[2]);
+        split_bf16(D[s + 8][m0 + g + 8], D[s + 9][m0 + g + 8], ahi[3], alo[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + 8 * j + g;                                 // B(k = s, n) = silu(Zb[s][n])
+            uint32_t bhi0, blo0, bhi1, blo1;
+            split_bf16(silu_f(Zb[s][n]), silu_f(Zb[s + 1][n]), bhi0, blo0);
+            split_bf16(silu_f(Zb[s + 8][n]), silu_f(Zb[s + 9][n]), bhi1, blo1);
+            mma_bf16_16816(acc[j], ahi, bhi0, bhi1);
+            mma_bf16_16816(acc[j], ahi, blo0, blo1);
+            mma_bf16_16816(acc[j], alo, bhi0, bhi1);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = n0 + 8 * j + 2 * t;
+        atomicAdd(grad + SURR_H * (m0 + g) + col, acc[j][0]);
+        atomicAdd(grad + SURR_H * (m0 + g) + col + 1, acc[j][1]);
+        atomicAdd(grad + SURR_H * (m0 + g + 8) + col, acc[j][2]);
+        atomicAdd(grad + SURR_H * (m0 + g + 8) + col + 1, acc[j][3]);
+    }
+}
 
 // One CTA: forward and backward of SURR_TB samples; adds the loss and the gradient of
 // mean((y - t)^2) over the whole batch (n_batch samples) to A.loss and A.grad.  The
 // samples are given either by index (training set, x_ext == nullptr) or by features
-// and targets in device memory (x_ext [n][2], t_ext [n]; the gradient check).
+// and targets in device memory (x_ext [n][2], t_ext [n]; the gradient check).  The two
+// 64 x 64 layers' products (forward, backward, weight gradients) run on the tensor cores.
 __global__ void __launch_bounds__(SURR_THREADS) surr_pass_kernel(SurrTrainArgs A, uint64_t first, uint64_t n_batch,
                                                                  const float* x_ext, const float* t_ext)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SurrSmem& S = *reinterpret_cast<SurrSmem*>(smem_raw);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int k = tid; k < SURR_NPARAM; k += SURR_THREADS) S.w[k] = A.wbf[k];
     const uint64_t s0 = (uint64_t)blockIdx.x * SURR_TB;
     if (tid < SURR_TB) {
@@ -186,22 +337,14 @@ __global__ void __launch_bounds__(SURR_THREADS) surr_pass_kernel(SurrTrainArgs A
         S.t[tid] = t;
     }
     __syncthreads();
-    // forward: thread (s, jq) computes units jq, jq + 4, ... of sample s
+    // forward: the first layer (two inputs) on the FP32 pipe, the others on the tensor cores
     const int s = tid >> 2, jq = tid & 3;
     for (int j = jq; j < SURR_H; j += 4)
         S.Z1[s][j] = fmaf(S.w[SURR_W1 + 2 * j], S.z[s][0], fmaf(S.w[SURR_W1 + 2 * j + 1], S.z[s][1], S.w[SURR_B1 + j]));
     __syncthreads();
-    for (int j = jq; j < SURR_H; j += 4) {
-        float acc = S.w[SURR_B2 + j];
-        for (int k = 0; k < SURR_H; ++k) acc = fmaf(S.w[SURR_W2 + SURR_H * j + k], silu_f(S.Z1[s][k]), acc);
-        S.Z2[s][j] = acc;
-    }
+    surr_tc_forward(S.w + SURR_W2, S.w + SURR_B2, S.Z1, S.Z2, warp, lane);
     __syncthreads();
-    for (int j = jq; j < SURR_H; j += 4) {
-        float acc = S.w[SURR_B3 + j];
-        for (int k = 0; k < SURR_H; ++k) acc = fmaf(S.w[SURR_W3 + SURR_H * j + k], silu_f(S.Z2[s][k]), acc);
-        S.Z3[s][j] = acc;
-    }
+    surr_tc_forward(S.w + SURR_W3, S.w + SURR_B3, S.Z2, S.Z3, warp, lane);
     __syncthreads();
     if (tid < SURR_TB) {
         float y = S.w[SURR_B4];
@@ -226,26 +369,18 @@ __global__ void __launch_bounds__(SURR_THREADS) surr_pass_kernel(SurrTrainArgs A
         atomicAdd(A.grad + SURR_B4, g);
     }
     __syncthreads();
-    // hidden layers 3 and 2: dW[j][k] = sum_s D[s][j] silu(Zbelow[s][k]); dZbelow = (W^T D) silu'(Zbelow)
+    // hidden layers 3 and 2: dW = D^T silu(Zbelow), dZbelow = (D W) silu'(Zbelow), both on the
+    // tensor cores; the bias gradients are column sums of D
     for (int layer = 3; layer >= 2; --layer) {
         const int OW = layer == 3 ? SURR_W3 : SURR_W2, OB = layer == 3 ? SURR_B3 : SURR_B2;
-        float (*Zb)[SURR_H] = layer == 3 ? S.Z2 : S.Z1;
-        for (int e = tid; e < SURR_H * SURR_H; e += SURR_THREADS) {
-            const int j = e / SURR_H, k = e % SURR_H;
-            float g = 0.f;
-            for (int q = 0; q < SURR_TB; ++q) g = fmaf(S.D[q][j], silu_f(Zb[q][k]), g);
-            atomicAdd(A.grad + OW + e, g);
-        }
+        const float (*Zb)[SURR_ZS] = layer == 3 ? S.Z2 : S.Z1;
+        surr_tc_weight_grad(A.grad + OW, S.D, Zb, warp, lane);
         if (tid < SURR_H) {
             float g = 0.f;
             for (int q = 0; q < SURR_TB; ++q) g += S.D[q][tid];
             atomicAdd(A.grad + OB + tid, g);
         }
-        for (int k = jq; k < SURR_H; k += 4) {
-            float acc = 0.f;
-            for (int j = 0; j < SURR_H; ++j) acc = fmaf(S.w[OW + SURR_H * j + k], S.D[s][j], acc);
-            S.E[s][k] = acc * silu_grad_f(Zb[s][k]);
-        }
+        surr_tc_backprop(S.w + OW, S.D, Zb, S.E, warp, lane);
         __syncthreads();
         for (int k = jq; k < SURR_H; k += 4) S.D[s][k] = S.E[s][k];
         __syncthreads();
@@ -324,41 +459,6 @@ __device__ __noinline__ float surr_pair_kernel(const SurrogateDev* __restrict__ 
     const float r1 = cbrtf((float)v1 * c), r2 = cbrtf((float)v2 * c);
     const SurrogateDev D = *S;
     return surr_kernel(D, fmaxf(r1, r2), fminf(r1, r2));
-}
-
-// ---------------------------------------------------------------------------
-// Inference on the tensor cores for a warp's 32 pairs at once (the queued pairs a
-// step evaluates together).  The samples are the rows of the activation matrix
-// (M = 32: two m16 tiles), the 64 hidden units its columns; the 64 x 64 layers are
-// mma.sync m16n8k16 products with BF16 operands and FP32 accumulation.  An FP32
-// activation x enters as hi + lo with hi = bf16(x), lo = bf16(x - hi), two products
-// per tile, so that the result keeps ~16 bits of each activation (the weights are
-// BF16 already).  The accumulator layout of two adjacent n8 tiles is the operand
-// layout of one k16 slab, so a layer's output feeds the next layer from registers.
-//   fragments (lane = 4 g + t): A regs {(g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..),
-//   (g+8, 2t+8..)}; B regs {(k = 2t..2t+1, n = g), (k = 2t+8.., n = g)};
-//   C/D {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)}.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t bf16x2_bits(float lo_elem, float hi_elem)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
-    return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// hi and lo BF16 operand registers of four FP32 values laid out as one A register pair set
-__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo)
-{
-    const float h0 = bf16_round(x0), h1 = bf16_round(x1);
-    hi = bf16x2_bits(h0, h1);
-    lo = bf16x2_bits(x0 - h0, x1 - h1);
 }
 
 // One 64 x 64 layer for one m16 tile: out = silu(W in + b), in given as hi/lo A operand

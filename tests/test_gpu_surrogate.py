@@ -128,3 +128,55 @@ def test_surrogate_precision_needs_an_attached_surrogate():
     with pytest.raises(sdm.SDMError):
         g.step(1.0, 1, 0, 1, precision="surrogate")
     g.close()
+
+
+def _timed_steps(st, s, precision, n_steps, step0):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    st.step(s["dt"], 42, step0, n_steps, precision=precision, golovin_b=s["golovin_b"])
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n_steps
+
+
+def test_what_the_surrogate_gains(trained):
+    """What the trained network gains over the method without it, on a lognormal grid like the
+    surrogate configuration's (96 x 96 cells of Poisson(256) SDs, 2.4e6 SDs): 30 steps with
+    precision="surrogate" and 30 FP64 steps of the same seed, timed with CUDA events, each
+    compared with the oracle's FP64 run.  The figures the design states: the FP64 steps equal the
+    oracle; the surrogate's mass spectrum stays within 1e-3 (L1, relative) of it and its droplet
+    number within 1e-4; and the surrogate steps are slower (the early exit and the FP32
+    certificate leave the plain kernel only ~1.5 % of the pairs, for which the network's
+    tensor-core inference costs more than the ~100 FP32 instructions it replaces), by a factor
+    above 1.2."""
+    net = trained[0]
+    g = inputs.grid_lognormal(nx=96, ny=96)
+    n_steps = 30
+    o0 = oracle.System(g["xi"], g["v"][None, :], g["cell_start"], g["dv"], g["kernel_id"], g["golovin_b"])
+    o0.run(g["dt"], 42, 0, 1 + n_steps)                   # step 0 is the untimed warm-up of both runs
+    r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 101))
+    ref = o0.spectrum(r_edges)
+    n_ref = o0.totals()[0]
+    times, spectra, numbers = {}, {}, {}
+    for prec in ("fp64", "surrogate"):
+        st = sdm.from_inputs(g)
+        if prec == "surrogate":
+            st.attach_surrogate(net)
+        st.step(g["dt"], 42, 0, 1, precision=prec, golovin_b=g["golovin_b"])   # warm-up
+        times[prec] = _timed_steps(st, g, prec, n_steps, 1)
+        spectra[prec] = st.spectrum(r_edges)
+        numbers[prec] = st.totals()[0]
+        if prec == "fp64":
+            xi, at, _ = st.get_state()
+            assert np.array_equal(xi, o0.xi) and np.array_equal(at.view(np.uint64), o0.attr.view(np.uint64))
+        st.close()
+    l1 = {p: float(np.abs(spectra[p] - ref).sum() / ref.sum()) for p in spectra}
+    dn = {p: (numbers[p] - n_ref) / n_ref for p in numbers}
+    ratio = times["surrogate"] / times["fp64"]
+    print(f"\nsurrogate vs plain FP64 on 2.4e6 SDs: {times['surrogate']:.4f} vs {times['fp64']:.4f} ms/step "
+          f"(x{ratio:.2f}); spectrum L1 vs oracle {l1['surrogate']:.2e} (FP64 {l1['fp64']:.0e}); "
+          f"droplet number {dn['surrogate']:+.2e}")
+    assert l1["fp64"] == 0.0 and dn["fp64"] == 0.0
+    assert l1["surrogate"] < 1e-3 and abs(dn["surrogate"]) < 1e-4
+    assert ratio > 1.2
