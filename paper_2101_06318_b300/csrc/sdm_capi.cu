@@ -938,9 +938,20 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 else                                      // above 256 SDs the keyed bijection
                     warp_cells_kernel<WC_SORT_PRP><<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(
                         a, st->wq, st->d_wcells, st->n_wcells);
-                auto pk = surr ? wc_pairs_kernel<true> : wc_pairs_kernel<false>;
-                pk<<<st->wq_grid, 256, 0, st->stream>>>(a, st->wq);
-                wc_compact_kernel<<<st->wq_grid, 256, 0, st->stream>>>(a, st->wq, st->d_wq_ticket);
+                // the pair and compaction kernels as programmatic dependents: their blocks may be
+                // scheduled while the previous kernel drains; each waits for it (griddepcontrol.wait)
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                at[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                cfg.stream = st->stream;
+                cfg.blockDim = dim3(256);
+                cfg.gridDim = dim3(st->wq_grid);
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? wc_pairs_kernel<true> : wc_pairs_kernel<false>, a, st->wq));
+                cfg.gridDim = dim3(std::max(st->n_sm, 1));       // one block per SM: one ticket each
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, wc_compact_kernel, a, st->wq, st->d_wq_ticket));
             }
             if (st->n_tiles) {
                 uint32_t grid = st->n_tiles;

@@ -1072,6 +1072,8 @@ __global__ void __launch_bounds__(32 * WC_WARPS, SMAX < WC_MAX ? SDM_WC_MIN_BLOC
 {
     __shared__ WarpCellSmem<SMAX> ws[WC_WARPS];
     __shared__ unsigned long long red[8];
+    // the pair kernel that follows may be scheduled as this grid drains (it waits for it to finish)
+    asm volatile("griddepcontrol.launch_dependents;");
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t step = step_index(a);
     LocalStats ls = {0, 0, 0, 0, 0ull};
@@ -1095,6 +1097,9 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
     __shared__ unsigned long long red[8];
     const EffTab* __restrict__ T = &g_eff_tab;
     if (threadIdx.x < 5) red[threadIdx.x] = 0;
+    // launched as a programmatic dependent of the cell kernel: wait until its queue is complete
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     __syncthreads();
     LocalStats ls = {0, 0, 0, 0, 0ull};
     const uint32_t nq = *(volatile uint32_t*)W.count;
@@ -1139,6 +1144,7 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
 // shows every block has read them).
 __global__ void __launch_bounds__(256) wc_compact_kernel(StepArgs a, WcQueue W, uint32_t* ticket)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");      // the pair kernel has completed
     const uint32_t nc = *(volatile uint32_t*)(W.count + 1);
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nc; k += (gridDim.x * blockDim.x) >> 5) {
