@@ -178,8 +178,9 @@ sdm_status set_dyn_smem_limit(K* kernel, uint32_t want)
 
 sdm_status set_smem_limits()
 {
-    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<2>, FINISH_SMEM_MAX));
-    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<3>, FINISH_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<2, true>, FINISH_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<3, true>, FINISH_SMEM_MAX));
+    SDM_TRY(set_dyn_smem_limit(big_finish_kernel<2, false>, FINISH_SMEM_MAX));
     SDM_TRY(set_dyn_smem_limit(big_scatter_kernel, SCATTER_SMEM_MAX));
     SDM_TRY(set_dyn_smem_limit(tile_step_kernel<false, 256>, TILE_SMEM_MAX));
     SDM_TRY(set_dyn_smem_limit(tile_step_kernel<true, 256>, TILE_SMEM_MAX));
@@ -576,11 +577,13 @@ sdm_status build_layout(sdm_state* st)
         // two CTAs per SM (more registers: a shorter latency per bucket) unless three CTAs per SM
         // (more warps in flight) take fewer rounds of buckets per warp
         const uint32_t nbk = st->n_buckets_planned;
-        const FinishLayout f2 = finish_layout(bucket_cap, FINISH_SMEM_WAVE);
-        const FinishLayout f3 = finish_layout(bucket_cap, FINISH_SMEM);
+        const FinishLayout f2 = finish_layout(bucket_cap, FINISH_SMEM_WAVE, true);
+        const FinishLayout f3 = finish_layout(bucket_cap, FINISH_SMEM, true);
         int per2 = 0, per3 = 0;
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, big_finish_kernel<2>, 32 * f2.warps, f2.bytes));
-        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, big_finish_kernel<3>, 32 * f3.warps, f3.bytes));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, big_finish_kernel<2, true>, 32 * f2.warps,
+                                                               f2.bytes));
+        SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, big_finish_kernel<3, true>, 32 * f3.warps,
+                                                               f3.bytes));
         const uint64_t w2 = (uint64_t)std::max(per2, 1) * st->n_sm * f2.warps;
         const uint64_t w3 = (uint64_t)std::max(per3, 1) * st->n_sm * f3.warps;
         const bool three = (nbk + w3 - 1) / w3 < (nbk + w2 - 1) / w2;
@@ -607,12 +610,17 @@ sdm_status build_layout(sdm_state* st)
         SDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cells_kernel<WC_MAX>,
                                                                32 * WC_WARPS, 0));
         st->wc_grid_sort = std::max<uint32_t>(1, std::min<uint32_t>(need, (uint32_t)std::max(per_sm, 1) * st->n_sm));
-        // the queue: at most one entry per candidate pair of these cells
+    }
+    if (!wcells.empty() || !bigs.empty()) {
+        // the queue of pairs past the early exit (the cells of one warp; the large cells under the
+        // SORT contract): at most one entry per candidate pair
         uint64_t qcap = 32;
         for (uint32_t c : wcells) qcap += (cs[c + 1] - cs[c]) / 2;
+        for (const BigCell& b : bigs) qcap += b.width / 2;
         SDM_TRY(dev_alloc(st, (void**)&st->wq.q, sizeof(uint4) * qcap, true));
-        SDM_TRY(dev_alloc(st, (void**)&st->wq.count, sizeof(uint32_t) * 4, true));   // pairs, cells, ticket
-        SDM_TRY(dev_alloc(st, (void**)&st->wq.cells, sizeof(uint32_t) * st->n_wcells, true));
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.count, sizeof(uint32_t) * 4, true));   // pairs, cells, ticket, bigs
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.cells, sizeof(uint32_t) * std::max<size_t>(1, wcells.size()), true));
+        SDM_TRY(dev_alloc(st, (void**)&st->wq.bigcells, sizeof(uint32_t) * std::max<size_t>(1, bigs.size()), true));
         SDM_TRY(dev_alloc(st, (void**)&st->wq.flag, sizeof(uint32_t) * st->n_cell, true));
         SDM_CUDA(cudaMemsetAsync(st->wq.count, 0, sizeof(uint32_t) * 4, st->stream));
         SDM_CUDA(cudaMemsetAsync(st->wq.flag, 0, sizeof(uint32_t) * st->n_cell, st->stream));
@@ -927,31 +935,38 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     const uint32_t scatter_smem = sizeof(uint32_t) * 2 * st->max_nb;
     for (uint32_t s = 0; s < n_steps; ++s) {
         a.step = p->step + s;
+        // the queued pairs, then the cells that lost SDs: launched once per step, after the kernels
+        // that fill the queue, as programmatic dependents (their blocks may be scheduled while the
+        // previous kernel drains; each waits for it with griddepcontrol.wait)
+        const bool sort_big = st->n_big && p->shuffle == SDM_SHUFFLE_SORT;
+        auto launch_queue = [&]() -> sdm_status {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cfg.stream = st->stream;
+            cfg.blockDim = dim3(256);
+            cfg.gridDim = dim3(st->wq_grid);
+            const bool surr = p->precision == SDM_PREC_SURROGATE;
+            SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? wc_pairs_kernel<true> : wc_pairs_kernel<false>, a, st->wq));
+            cfg.gridDim = dim3(std::max(st->n_sm, 1));           // one block per SM: one ticket each
+            SDM_CUDA(cudaLaunchKernelEx(&cfg, wc_compact_kernel, a, st->wq, st->d_wq_ticket));
+            return SDM_OK;
+        };
         if (st->n_wcells || st->n_tiles) {
             ProfScope ps(st, 0);
             const bool surr = p->precision == SDM_PREC_SURROGATE;
             if (st->n_wcells) {
-                // shuffle and early exit per cell, then the queued pairs, then the cells that lost SDs
+                // shuffle and early exit per cell; the pairs it cannot settle go to the queue
                 if (p->shuffle == SDM_SHUFFLE_SORT)       // lists up to 512 SDs sorted by key
                     warp_cells_kernel<WC_MAX><<<st->wc_grid_sort, 32 * WC_WARPS, 0, st->stream>>>(
                         a, st->wq, st->d_wcells, st->n_wcells);
                 else                                      // above 256 SDs the keyed bijection
                     warp_cells_kernel<WC_SORT_PRP><<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(
                         a, st->wq, st->d_wcells, st->n_wcells);
-                // the pair and compaction kernels as programmatic dependents: their blocks may be
-                // scheduled while the previous kernel drains; each waits for it (griddepcontrol.wait)
-                cudaLaunchConfig_t cfg = {};
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-                at[0].val.programmaticStreamSerializationAllowed = 1;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                cfg.stream = st->stream;
-                cfg.blockDim = dim3(256);
-                cfg.gridDim = dim3(st->wq_grid);
-                SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? wc_pairs_kernel<true> : wc_pairs_kernel<false>, a, st->wq));
-                cfg.gridDim = dim3(std::max(st->n_sm, 1));       // one block per SM: one ticket each
-                SDM_CUDA(cudaLaunchKernelEx(&cfg, wc_compact_kernel, a, st->wq, st->d_wq_ticket));
+                if (!sort_big) SDM_TRY(launch_queue());
             }
             if (st->n_tiles) {
                 uint32_t grid = st->n_tiles;
@@ -1004,10 +1019,11 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             }
             {
                 ProfScope ps(st, 2);
-                auto fk = st->fin_minb == 2 ? big_finish_kernel<2> : big_finish_kernel<3>;
+                auto fk = st->fin_minb == 2 ? big_finish_kernel<2, true> : big_finish_kernel<3, true>;
                 fk<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
                     a, st->d_big, st->d_bucket_desc, st->d_scratch, st->d_bstart, st->n_buckets, st->d_big_xmax,
-                    st->fin_L, bb);
+                    st->fin_L, bb, st->wq);
+                SDM_TRY(launch_queue());                 // the large cells' (and small cells') queued pairs
             }
         }
         if (p->d_step) advance_step_kernel<<<1, 32, 0, st->stream>>>(p->d_step, 1u);
@@ -1049,7 +1065,7 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(sizeof(TileDesc) * (size_t)n_cell + 256) + round256(sizeof(BigCell) * (size_t)n_cell + 256);
     b += round256(4 * (size_t)n_cell + 256);   // cells stepped by one warp each
     // their queue (an entry per candidate pair), its counters, listed cells and flags
-    b += round256(16 * (cap / 2 + 32) + 256) + round256(16 + 256) + 2 * round256(4 * (size_t)n_cell + 256);
+    b += round256(16 * (cap / 2 + 32) + 256) + round256(16 + 256) + 3 * round256(4 * (size_t)n_cell + 256);
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
@@ -1628,8 +1644,11 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
     if (!st || !n || shuffle > SDM_SHUFFLE_SORT) return SDM_EINVAL;
     // small cells: one kernel per kind; large cells: one kernel (PRP contract; it compacts the
     // cells the previous step left flagged) or scatter + finish (SORT contract)
-    *n = (st->n_wcells ? 3u : 0u) + (st->n_tiles ? 1u : 0u) +   // cells, queued pairs, compaction
-         (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);   // SORT: scatter + finish
+    // small cells: one kernel per kind; large cells: one kernel (PRP contract) or scatter + finish
+    // (SORT contract); the queue's pair and compaction kernels once when any kernel fills it
+    const bool queue = st->n_wcells || (st->n_big && shuffle == SDM_SHUFFLE_SORT);
+    *n = (st->n_wcells ? 1u : 0u) + (st->n_tiles ? 1u : 0u) + (queue ? 2u : 0u) +
+         (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);
     return SDM_OK;
 }
 
@@ -1791,12 +1810,12 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
         const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
         uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
-        const FinishLayout fl = finish_layout(cap, FINISH_SMEM_WAVE);   // at most 1024 buckets: one wave
+        const FinishLayout fl = finish_layout(cap, FINISH_SMEM_WAVE, false);   // at most 1024 buckets: one wave
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
         big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
             a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
-        big_finish_kernel<2><<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
-            a, d_cell, (const BucketDesc*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb);
+        big_finish_kernel<2, false><<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
+            a, d_cell, (const BucketDesc*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb, WcQueue{});
     }
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());

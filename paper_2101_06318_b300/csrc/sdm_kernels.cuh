@@ -772,12 +772,17 @@ struct __align__(16) WarpCellSmem {
 // offsets i1 | i2 << 16 of the two SDs in the cell, and the pair's phi integer), appended by
 // warp_cells_kernel and evaluated by wc_pairs_kernel; cells that lost an SD are listed for
 // wc_compact_kernel.  The counters are zero between steps (the compaction kernel resets them).
+constexpr uint32_t WQ_BIG = 0x80000000u;    // pair index flag: a large cell's pair
 struct WcQueue {
-    uint4* q;                 // [capacity] (cell, i1 | i2 << 16, phi low word, phi high word)
-    uint32_t* count;          // [0] queued pairs, [1] listed cells
-    uint32_t* cells;          // [n_cell] cells to compact
+    uint4* q;                 // [capacity] (cell, slot of the first SD, slot of the second, pair index m
+                              // of the cell | WQ_BIG for a large cell); phi_m is recomputed from m
+    uint32_t* count;          // [0] queued pairs, [1] listed cells of one warp, [2] the compaction
+                              // kernel's ticket, [3] listed large cells
+    uint32_t* cells;          // [cells of one warp] cells to compact
+    uint32_t* bigcells;       // [large cells] large cells to compact
     uint32_t* flag;           // [n_cell] the cell is listed
 };
+__device__ uint32_t block_compact_cell(const StepArgs& a, uint64_t base, uint32_t n_old, uint32_t* wt);
 
 
 // exclusive scan of a[0..n) by one warp; a[n] = total
@@ -1055,11 +1060,10 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
             if (lane == 0) qb = atomicAdd(W.count, tot);
             qb = __shfl_sync(0xffffffffu, qb, 0) + pre - mine;
 #pragma unroll
-            for (uint32_t h = 0; h < 2; ++h) {
-                if (need[h]) {
-                    W.q[qb++] = make_uint4(cell, ii[h], h ? wv.w : wv.y, h ? wv.z : wv.x);
-                }
-            }
+            for (uint32_t h = 0; h < 2; ++h)
+                if (need[h])
+                    W.q[qb++] = make_uint4(cell, (uint32_t)s0 + (ii[h] & 0xffffu), (uint32_t)s0 + (ii[h] >> 16),
+                                           2 * M + h);
         }
     }
 }
@@ -1104,19 +1108,18 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
     LocalStats ls = {0, 0, 0, 0, 0ull};
     const uint32_t nq = *(volatile uint32_t*)W.count;
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t step = step_index(a);
     for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < nq; base += gridDim.x * blockDim.x) {
         const uint32_t e = base + lane;
         const bool act = e < nq;
         uint4 q = make_uint4(0, 0, 0, 0);
         if (act) q = __ldcs(W.q + e);
         const uint32_t cell = q.x;
-        uint64_t g1 = 0, g2 = 0;
+        const uint64_t g1 = q.y, g2 = q.z;
         uint32_t n = 2, kid = 0;
         double dv = 1.0;
         if (act) {
             const uint32_t s0 = a.cell_start[cell];
-            g1 = s0 + (q.y & 0xffffu);
-            g2 = s0 + (q.y >> 16);
             n = min(a.n_live[cell], a.cell_start[cell + 1] - s0);
             kid = (uint32_t)a.kid[cell];
             dv = a.dv[cell];
@@ -1128,9 +1131,14 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
         if (SURR && a.precision == PREC_SURROGATE)
             Kh = surr_pair_kernel_warp(a.surr, v1, v2, act && kid == 1);   // the warp's pairs on the tensor cores
         uint32_t rflag = 0;
-        const uint64_t u53 = ((((uint64_t)q.w) << 32) | (uint64_t)q.z) >> 11;
-        if (act) process_pair<SURR>(a, T, cc, u53, g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
-        if (rflag && atomicExch(&W.flag[cell], 1u) == 0u) W.cells[atomicAdd(W.count + 1, 1u)] = cell;
+        if (act) {
+            const uint64_t u53 = phi_u53(a.seed_lo, a.seed_hi, cell, step, q.w & ~WQ_BIG);
+            process_pair<SURR>(a, T, cc, u53, g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
+        }
+        if (rflag && atomicExch(&W.flag[cell], 1u) == 0u) {
+            if (q.w & WQ_BIG) W.bigcells[atomicAdd(W.count + 3, 1u)] = cell;
+            else W.cells[atomicAdd(W.count + 1, 1u)] = cell;
+        }
     }
     if (a.stats) {
         __syncthreads();
@@ -1138,14 +1146,16 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
     }
 }
 
-// Step 0 of the next step for the cells the queued pairs emptied slots of: each listed cell is
-// compacted stably by one warp.  Resets the queue's counters and flags for the next step (the
-// counts are read once, by every warp, before any is cleared: block 0 clears them after a ticket
-// shows every block has read them).
+// Step 0 of the next step for the cells the queued pairs emptied slots of: each listed cell of
+// one warp is compacted stably by one warp, each listed large cell by a whole block.  Resets the
+// queue's counters and flags for the next step (the counts are read once, by every block, before
+// any is cleared: the last block to take the ticket clears them).
 __global__ void __launch_bounds__(256) wc_compact_kernel(StepArgs a, WcQueue W, uint32_t* ticket)
 {
+    __shared__ uint32_t wt[40];
+    __shared__ uint32_t last;
     asm volatile("griddepcontrol.wait;" ::: "memory");      // the pair kernel has completed
-    const uint32_t nc = *(volatile uint32_t*)(W.count + 1);
+    const uint32_t nc = *(volatile uint32_t*)(W.count + 1), nbg = *(volatile uint32_t*)(W.count + 3);
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nc; k += (gridDim.x * blockDim.x) >> 5) {
         const uint32_t c = W.cells[k];
@@ -1156,13 +1166,24 @@ __global__ void __launch_bounds__(256) wc_compact_kernel(StepArgs a, WcQueue W, 
             W.flag[c] = 0;
         }
     }
-    __shared__ uint32_t last;
+    __syncthreads();
+    for (uint32_t k = blockIdx.x; k < nbg; k += gridDim.x) {   // block-uniform
+        const uint32_t c = W.bigcells[k];
+        const uint32_t s0 = a.cell_start[c], w = a.cell_start[c + 1] - s0;
+        const uint32_t n_new = block_compact_cell(a, s0, min(a.n_live[c], w), wt);
+        if (threadIdx.x == 0) {
+            a.n_live[c] = n_new;
+            W.flag[c] = 0;
+        }
+        __syncthreads();
+    }
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
     __syncthreads();
     if (last && threadIdx.x == 0) {
         W.count[0] = 0;
         W.count[1] = 0;
+        W.count[3] = 0;
         *ticket = 0;
     }
 }
@@ -1980,24 +2001,25 @@ struct FinishLayout {
     uint32_t cap;          // records per bucket
     uint32_t nsub_max;     // sub-bucket counters per warp
     uint32_t warps;        // warps (buckets in flight) per CTA
-    uint32_t o_rec, o_off, o_cnt, o_trec, o_q, warp_bytes;   // per-warp region layout
+    uint32_t o_pos, o_cnt, o_trec, o_q, warp_bytes;   // per-warp region layout
     uint32_t o_tab, bytes;
 };
 
-// Per warp: the bucket's records in arrival order (later: its positions in sorted order), their
-// arrival index within their sub-bucket, the sub-bucket counters, the records grouped by
-// sub-bucket, the queue of surviving pairs.
-__host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max_smem)
+// Per warp: a record's arrival index within its sub-bucket (16 bits; later, in the same bytes,
+// the bucket's positions in sorted order, 32 bits), the sub-bucket counters, the records grouped
+// by sub-bucket, and -- when the warp evaluates its pairs itself (queue = false) -- its queue of
+// surviving pairs.
+__host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max_smem, bool queue = false)
 {
     FinishLayout L;
     L.cap = cap;
     L.nsub_max = 1u << (ceil_log2(cap > 2 ? cap : 2) - 1);          // about two records per counter
     uint32_t o = 0;
-    L.o_rec = o; o = align_up(o + 8 * cap, 16);
-    L.o_off = o; o = align_up(o + 2 * cap, 16);
+    L.o_pos = o; o = align_up(o + 4 * cap, 16);
     L.o_cnt = o; o = align_up(o + 4 * (L.nsub_max + 1), 16);
     L.o_trec = o; o = align_up(o + 8 * cap, 16);
-    L.o_q = o; o = align_up(o + (uint32_t)sizeof(FinQueue), 16);
+    L.o_q = o;
+    if (!queue) o = align_up(o + (uint32_t)sizeof(FinQueue), 16);
     L.warp_bytes = o;
     L.o_tab = 0;
     const uint32_t tab = align_up((uint32_t)sizeof(EffTab), 16);
@@ -2035,6 +2057,11 @@ __device__ __forceinline__ void fin_drain(const StepArgs& a, const EffTab* __res
     qcnt -= take;
 }
 
+// One bucket of a large cell under the SORT contract: order its records by (key, position), locate
+// it in the cell's order, and take its pairs through the early exit.  QUEUE: the surviving pairs
+// go to the step's queue (evaluated by wc_pairs_kernel); otherwise to the warp's queue, evaluated
+// here 32 at a time.
+template <bool QUEUE>
 __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
                                               const BigCell* __restrict__ cells,
                                               const BucketDesc* __restrict__ bucket_desc,
@@ -2042,11 +2069,10 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
                                               const unsigned long long* __restrict__ xmax, const FinishLayout& L,
                                               unsigned char* ws, uint32_t g, uint32_t lane, uint32_t step,
                                               LocalStats& ls, uint32_t* removed, FinQueue& Q, uint32_t& qcnt,
-                                              CellCtx& qcc, uint32_t& qbig)
+                                              CellCtx& qcc, uint32_t& qbig, const WcQueue& W)
 {
-    uint64_t* rs = (uint64_t*)(ws + L.o_rec);       // records in arrival order
-    uint32_t* ssl = (uint32_t*)(ws + L.o_rec);      // then: the bucket's positions in sorted order
-    uint16_t* off = (uint16_t*)(ws + L.o_off);
+    uint16_t* off = (uint16_t*)(ws + L.o_pos);      // arrival index in the sub-bucket
+    uint32_t* ssl = (uint32_t*)(ws + L.o_pos);      // then: the bucket's positions in sorted order
     uint32_t* cnt = (uint32_t*)(ws + L.o_cnt);
     uint64_t* trec = (uint64_t*)(ws + L.o_trec);    // records grouped by sub-bucket
     const uint32_t cap = L.cap;
@@ -2062,11 +2088,10 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const uint32_t S = off_c[gl];
     const uint32_t k = off_c[gl + 1] - S;
     const uint64_t* R = rec + (uint64_t)g * cap;
-#pragma unroll 4
-    for (uint32_t i = lane; i < k; i += 32) rs[i] = R[i];
-    // counting sort on the key bits below the bucket's, then the exact rank by (key, position)
-    // within each sub-bucket: a record is (key << 32) | position, so that order is the records'
-    // integer order (positions differ, so no two records are equal)
+    // counting sort on the key bits below the bucket's (the records are read twice from L2, where
+    // the scatter pass left them), then the exact rank by (key, position) within each sub-bucket:
+    // a record is (key << 32) | position, so that order is the records' integer order (positions
+    // differ, so no two records are equal)
     uint32_t sb = ceil_log2(k > 2 ? k : 2) - 1;
     if (sb > 32u - C.nbits) sb = 32u - C.nbits;
     const uint32_t nsub = 1u << sb;
@@ -2074,14 +2099,16 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     __syncwarp();
     const uint32_t sh = 32u - sb;
     auto sub_of = [&](uint64_t e) { return sb ? ((uint32_t)(e >> 32) << C.nbits) >> sh : 0u; };
-    for (uint32_t i = lane; i < k; i += 32) off[i] = (uint16_t)atomicAdd(&cnt[sub_of(rs[i])], 1u);
+#pragma unroll 4
+    for (uint32_t i = lane; i < k; i += 32) off[i] = (uint16_t)atomicAdd(&cnt[sub_of(__ldcg(R + i))], 1u);
     __syncwarp();
     warp_exclusive_scan(cnt, nsub, lane);
+#pragma unroll 4
     for (uint32_t i = lane; i < k; i += 32) {
-        const uint64_t e = rs[i];
+        const uint64_t e = __ldcg(R + i);
         trec[cnt[sub_of(e)] + off[i]] = e;
     }
-    __syncwarp();                                   // rs is dead from here: ssl takes its place
+    __syncwarp();                                   // off is dead from here: ssl takes its place
     // FR grouped records per lane at once, so that their sub-bucket scans overlap
     constexpr uint32_t FR = 4;
     for (uint32_t p0 = 0; p0 < k; p0 += 32 * FR) {
@@ -2102,6 +2129,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
             for (uint32_t j = 0; j < FR; ++j)
                 if (t < len[j]) r[j] += trec[st[j] + t] < e[j] ? 1u : 0u;
         }
+        __syncwarp();
 #pragma unroll
         for (uint32_t j = 0; j < FR; ++j)
             if (p0 + lane + 32 * j < k) ssl[st[j] + r[j]] = (uint32_t)e[j];
@@ -2129,8 +2157,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     // pairs m whose first SD (cell position 2m) lies in this bucket: 2m in [S, S+k), 2m+1 < n;
     // each lane takes two consecutive pairs (one Philox call).  The early exit needs the two
     // volumes' bins (one byte each from the bin array, else the volume's high word) and the
-    // cell's multiplicity bound; the pairs it does not settle are queued per warp and
-    // evaluated 32 at a time.
+    // cell's multiplicity bound; the pairs it does not settle are queued.
     const uint32_t m_lo = (S + 1) >> 1;
     const uint32_t m_hi = min((S + k - 1) >> 1, (n >> 1) - 1);      // inclusive
     if (m_lo > m_hi) return;
@@ -2139,10 +2166,12 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     const float* __restrict__ tb = g_pbound[cc.kid];
     const uint8_t* __restrict__ vbin = a.vbin;
     const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
-    // the warp's queue carries over from bucket to bucket of one cell (fewer, fuller drains)
-    if (qcnt > 0 && qbig != big) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &removed[qbig], ls, lane);
-    qcc = cc;
-    qbig = big;
+    if (!QUEUE) {
+        // the warp's queue carries over from bucket to bucket of one cell (fewer, fuller drains)
+        if (qcnt > 0 && qbig != big) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &removed[qbig], ls, lane);
+        qcc = cc;
+        qbig = big;
+    }
     for (uint32_t Mb = m_lo >> 1; Mb <= (m_hi >> 1); Mb += 32) {    // warp-uniform trip count
         const uint32_t M = Mb + lane;
         // the four slots and their bins first (one round trip), then the arithmetic
@@ -2164,35 +2193,64 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
         }
         uint64_t u[2] = {0, 0};
         if (M <= (m_hi >> 1)) phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
+        bool need[2];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
-            bool need = false;
+            need[h] = false;
             if (ok[h]) {
-                need = !(__fmul_ru(__ldg(tb + pb_index(kv[h][0], kv[h][1])), c_upx) <= phi_lo23((uint32_t)(u[h] >> 21)));
-                ls.pairs += need ? 0u : 1u;
+                need[h] = !(__fmul_ru(__ldg(tb + pb_index(kv[h][0], kv[h][1])), c_upx) <=
+                            phi_lo23((uint32_t)(u[h] >> 21)));
+                ls.pairs += need[h] ? 0u : 1u;
             }
-            const unsigned mk = __ballot_sync(0xffffffffu, need);
-            if (need) {
-                const uint32_t q = qcnt + __popc(mk & ((1u << lane) - 1u));
-                Q.s1[q] = C.slot_begin + sl[h][0];
-                Q.s2[q] = C.slot_begin + sl[h][1];
-                Q.u[q] = u[h];
+        }
+        if (QUEUE) {
+            // (cell, slots, pair index m | BIG) to the step's queue, one reservation per warp
+            const uint32_t mine = (uint32_t)need[0] + (uint32_t)need[1];
+            uint32_t pre = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= (uint32_t)o) pre += t;
             }
-            qcnt += __popc(mk);
-            if (qcnt >= 32) fin_drain(a, tab, Q, qcnt, 32, cc, &removed[big], ls, lane);
+            const uint32_t tot = __shfl_sync(0xffffffffu, pre, 31);
+            if (tot) {
+                uint32_t qb = 0;
+                if (lane == 0) qb = atomicAdd(W.count, tot);
+                qb = __shfl_sync(0xffffffffu, qb, 0) + pre - mine;
+#pragma unroll
+                for (uint32_t h = 0; h < 2; ++h)
+                    if (need[h])
+                        W.q[qb++] = make_uint4(C.cell, C.slot_begin + sl[h][0], C.slot_begin + sl[h][1],
+                                               (2 * M + h) | WQ_BIG);
+            }
+        } else {
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const unsigned mk = __ballot_sync(0xffffffffu, need[h]);
+                if (need[h]) {
+                    const uint32_t q = qcnt + __popc(mk & ((1u << lane) - 1u));
+                    Q.s1[q] = C.slot_begin + sl[h][0];
+                    Q.s2[q] = C.slot_begin + sl[h][1];
+                    Q.u[q] = u[h];
+                }
+                qcnt += __popc(mk);
+                if (qcnt >= 32) fin_drain(a, tab, Q, qcnt, 32, cc, &removed[big], ls, lane);
+            }
         }
     }
 }
 
 // MINB: CTAs per SM the registers are sized for -- 2 when all buckets fit one wave of warps
-// (each bucket's latency is what counts), 3 when the warps take several buckets each.
-template <int MINB>
+// (each bucket's latency is what counts), 3 when the warps take several buckets each.  QUEUE: see
+// finish_bucket; the pairs' evaluation, removals and compaction then belong to wc_pairs_kernel and
+// wc_compact_kernel, else to this kernel (its last CTA compacts the cells that lost SDs).
+template <int MINB, bool QUEUE>
 __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
                                                          const BucketDesc* __restrict__ bucket_desc,
                                                          const uint64_t* __restrict__ rec,
                                                          const uint32_t* __restrict__ bstart, uint32_t n_buckets,
                                                          const unsigned long long* __restrict__ xmax,
-                                                         FinishLayout L, BigBook bb)
+                                                         FinishLayout L, BigBook bb, WcQueue W)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long red[8];
@@ -2202,21 +2260,21 @@ __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const
     unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
     const uint32_t step = step_index(a);
     LocalStats ls = {0, 0, 0, 0, 0ull};
-    load_eff_tab(tab);
+    if (!QUEUE) load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;
     __syncthreads();
-    FinQueue& Q = *(FinQueue*)(ws + L.o_q);
+    FinQueue& Q = *(FinQueue*)(ws + L.o_q);         // used only without QUEUE
     uint32_t qcnt = 0, qbig = 0;                   // warp-uniform
     CellCtx qcc{};
     for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
-        finish_bucket(a, tab, cells, bucket_desc, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q, qcnt,
-                      qcc, qbig);
-    if (qcnt > 0) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &bb.removed[qbig], ls, lane);
+        finish_bucket<QUEUE>(a, tab, cells, bucket_desc, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q,
+                             qcnt, qcc, qbig, W);
+    if (!QUEUE && qcnt > 0) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &bb.removed[qbig], ls, lane);
     if (a.stats) {
         __syncthreads();
         flush_stats(a, ls, red);
     }
-    big_end_of_step(a, cells, bb, wt, ls.removed != 0);
+    if (!QUEUE) big_end_of_step(a, cells, bb, wt, ls.removed != 0);
 }
 
 // ---------------------------------------------------------------------------
