@@ -34,6 +34,8 @@
 // (sort by (key, position), or the keyed bijection), so the tile size, bucket
 // width and launch shape never change a result.
 #pragma once
+#include <utility>
+
 #include "sdm_math.cuh"
 #include "sdm_surrogate.cuh"
 
@@ -834,67 +836,105 @@ __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, u
 }
 
 // Step 1 by sorting keys: the list ordered by (key, position), key(l) = philox(l >> 2, c, s, 0)[l & 3].
-// Counting sort on the top ceil(log2 n) bits (about one key per bucket), then each position's
-// exact rank inside its bucket -- a position alone in its bucket (the usual case) needs none.
-template <typename SM>
+// Counting sort on the top ceil(log2 n) bits (about one key per bucket): a key alone in its bucket
+// goes straight to its place; the keys of a bucket holding several are grouped, the bucket is
+// listed once, and each listed bucket is ordered by (key, position) with an insertion sort by one
+// lane.  SMAX: the longest list (n <= SMAX), so that the per-key loops have fixed trip counts.
+template <uint32_t SMAX, typename SM>
 __device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_t cell, uint32_t step, uint32_t n,
                                                uint32_t lane)
 {
+    constexpr uint32_t NI = (SMAX + 31) / 32;                  // keys per lane at most
+    constexpr uint32_t NG = (SMAX + 127) / 128;                // Philox groups of four keys per lane at most
     const uint32_t nbb = ceil_log2(n);                         // n >= 2: 2^nbb >= n buckets
     const uint32_t sh = 32u - nbb;
     const uint32_t NBK = 1u << nbb;
     uint32_t* cw = reinterpret_cast<uint32_t*>(S.s.cnt);      // two 16-bit counts per word (n <= 512)
     for (uint32_t b = lane; 2 * b < NBK; b += 32) cw[b] = 0;
     __syncwarp();
-    for (uint32_t g = lane; 4 * g < n; g += 32) {
-        const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
-        if (4 * g + 3 < n) *reinterpret_cast<uint4*>(&S.s.key[4 * g]) = make_uint4(x.x, x.y, x.z, x.w);
 #pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t l = 4 * g + k;
-            if (l < n) {
-                const uint32_t key = u4_word(x, k);
-                if (4 * g + 3 >= n) S.s.key[l] = key;
-                const uint32_t b = key >> sh, hs = (b & 1u) << 4;   // count b: half b & 1 of word b >> 1
-                S.s.off[l] = (uint16_t)(atomicAdd(&cw[b >> 1], 1u << hs) >> hs);
+    for (uint32_t j = 0; j < NG; ++j) {
+        const uint32_t g = lane + 32 * j;
+        if (4 * g < n) {
+            const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
+            if (4 * g + 3 < n) *reinterpret_cast<uint4*>(&S.s.key[4 * g]) = make_uint4(x.x, x.y, x.z, x.w);
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t l = 4 * g + k;
+                if (l < n) {
+                    const uint32_t key = u4_word(x, k);
+                    if (4 * g + 3 >= n) S.s.key[l] = key;
+                    const uint32_t b = key >> sh, hs = (b & 1u) << 4;   // count b: half b & 1 of word b >> 1
+                    S.s.off[l] = (uint16_t)(atomicAdd(&cw[b >> 1], 1u << hs) >> hs);
+                }
             }
         }
     }
     __syncwarp();
     warp_exclusive_scan16(S.s.cnt, NBK, lane);
-    for (uint32_t l = lane; l < n; l += 32) S.s.tmp[S.s.cnt[S.s.key[l] >> sh] + S.s.off[l]] = (uint16_t)l;
-    __syncwarp();
-    // a key alone in its bucket is placed at once; the others (keys sharing a bucket, about a
-    // third of them) are listed, compacted, and ranked exactly inside their bucket, a lane each
+    // singletons to their place; the others grouped by bucket in tmp, each such bucket listed once
+    // (by its first arrival) in off: a list entry never lands on an arrival index still to be read
     uint32_t nwork = 0;
-    for (uint32_t base = 0; base < n; base += 32) {
-        const uint32_t l = base + lane;
-        bool multi = false;
+#pragma unroll
+    for (uint32_t j = 0; j < NI; ++j) {
+        const uint32_t l = lane + 32 * j;
+        bool lead = false;
+        uint32_t b = 0;
         if (l < n) {
-            const uint32_t b = S.s.key[l] >> sh;
-            const uint32_t st = S.s.cnt[b];
-            multi = S.s.cnt[b + 1] - st > 1;
-            if (!multi) S.srt[st] = (uint16_t)l;
+            b = S.s.key[l] >> sh;
+            const uint32_t st = S.s.cnt[b], c = S.s.cnt[b + 1] - st;
+            const uint32_t o = S.s.off[l];
+            if (c == 1) S.srt[st] = (uint16_t)l;
+            else S.s.tmp[st + o] = (uint16_t)l;
+            lead = c > 1 && o == 0;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, multi);
-        if (multi) S.s.off[nwork + __popc(m & ((1u << lane) - 1u))] = (uint16_t)l;   // off is free now
+        const unsigned m = __ballot_sync(0xffffffffu, lead);
+        if (lead) S.s.off[nwork + __popc(m & ((1u << lane) - 1u))] = (uint16_t)b;
         nwork += __popc(m);
     }
     __syncwarp();
     for (uint32_t w = lane; w < nwork; w += 32) {
-        const uint32_t l = S.s.off[w];
-        const uint32_t key = S.s.key[l];
-        const uint32_t b = key >> sh;
+        const uint32_t b = S.s.off[w];
         const uint32_t st = S.s.cnt[b], en = S.s.cnt[b + 1];
-        uint32_t r = 0;
-        for (uint32_t p = st; p < en; ++p) {
-            const uint32_t o = S.s.tmp[p];
-            const uint32_t ko = S.s.key[o];
-            r += (ko < key) || (ko == key && o < l);
+        for (uint32_t i = st; i < en; ++i) {
+            const uint32_t p = S.s.tmp[i], kp = S.s.key[p];
+            uint32_t j = i;
+            for (; j > st; --j) {
+                const uint32_t q = S.srt[j - 1], kq = S.s.key[q];
+                if (kq < kp || (kq == kp && q < p)) break;
+                S.srt[j] = (uint16_t)q;
+            }
+            S.srt[j] = (uint16_t)p;
         }
-        S.srt[st + r] = (uint16_t)l;
     }
 }
+
+// The domain of the bijection (prp_domain_of) and ceil(2^32 / B) for every list length the
+// small-cell step maps by it (PRP_MIN_N <= n <= WC_MAX), worked out at compile time: one
+// constant-cache read per cell instead of a square root and two divisions.
+struct PrpDom { uint32_t ab, binv; };      // ab = A | B << 16
+constexpr PrpDom prp_dom_entry(uint32_t n)
+{
+    uint32_t A = 1, B = n;
+    if ((n & (n - 1)) == 0) {
+        uint32_t k = 0;
+        while ((1u << k) < n) ++k;
+        A = 1u << (k >> 1);
+        B = 1u << (k - (k >> 1));
+    } else {
+        while (A * A < n) ++A;                 // ceil(sqrt n)
+        B = (n + A - 1) / A;
+    }
+    return PrpDom{A | (B << 16), (uint32_t)((0x100000000ull + B - 1) / B)};
+}
+constexpr uint32_t PRP_DOM_N = WC_MAX - PRP_MIN_N + 1;
+struct PrpDomTab { PrpDom e[PRP_DOM_N]; };
+template <size_t... I>
+constexpr PrpDomTab make_prp_dom_tab(std::index_sequence<I...>)
+{
+    return PrpDomTab{{prp_dom_entry(PRP_MIN_N + (uint32_t)I)...}};
+}
+__constant__ PrpDomTab c_prp_dom = make_prp_dom_tab(std::make_index_sequence<PRP_DOM_N>{});
 
 // x mod M for x < 2 M, without a branch: x - M wraps around (becomes larger) when x < M
 __device__ __forceinline__ uint32_t sub_mod(uint32_t x, uint32_t M) { return min(x, x - M); }
@@ -942,9 +982,8 @@ template <typename SM>
 __device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t cell, uint32_t step, uint32_t n,
                                               uint32_t lane)
 {
-    uint32_t A, B;
-    prp_domain_of(n, A, B);
-    const uint32_t Binv = (uint32_t)((0x100000000ull + B - 1) / B);
+    const PrpDom dom = c_prp_dom.e[n - PRP_MIN_N];             // PRP_MIN_N <= n <= WC_MAX
+    const uint32_t A = dom.ab & 0xffffu, B = dom.ab >> 16, Binv = dom.binv;
     {
         const U4 x = philox((lane >> 2) & 1u, cell, step, 2u, a.seed_lo, a.seed_hi);
         const uint32_t K = u4_word(x, lane & 3u);
@@ -1016,7 +1055,7 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
             if (lane == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);   // instantiation: not reached
             return;
         }
-        warp_sort_keys(a, S, cell, step, n, lane);
+        warp_sort_keys<SMAX>(a, S, cell, step, n, lane);
     } else {
         warp_prp_list(a, S, cell, step, n, lane);
     }
@@ -1046,19 +1085,14 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
                 ls.pairs += need[h] ? 0u : 1u;
             }
         }
-        // the lanes' surviving pairs go to the queue in one reservation per warp
-        const uint32_t mine = (uint32_t)need[0] + (uint32_t)need[1];
-        uint32_t pre = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= (uint32_t)o) pre += t;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, pre, 31);
+        // the lanes' surviving pairs go to the queue in one reservation per warp, lane by lane
+        const unsigned m0 = __ballot_sync(0xffffffffu, need[0]), m1 = __ballot_sync(0xffffffffu, need[1]);
+        const uint32_t tot = __popc(m0) + __popc(m1);
         if (tot) {
             uint32_t qb = 0;
             if (lane == 0) qb = atomicAdd(W.count, tot);
-            qb = __shfl_sync(0xffffffffu, qb, 0) + pre - mine;
+            const unsigned lt = (1u << lane) - 1u;
+            qb = __shfl_sync(0xffffffffu, qb, 0) + __popc(m0 & lt) + __popc(m1 & lt);
 #pragma unroll
             for (uint32_t h = 0; h < 2; ++h)
                 if (need[h])

@@ -231,6 +231,17 @@ def test_sort_contract_many_bucket_rounds_bitexact():
     assert ost["n_collisions"] == gst["n_collisions"] > 500
 
 
+def test_sort_contract_sparse_buckets_bitexact():
+    """A large cell of multiplicities 1 (every coalescence removes an SD) that loses about a third
+    of its SDs every step, until its 1024 buckets hold a record or less on average: many buckets
+    are empty, so a bucket's last position often pairs with the first of a bucket several further
+    on, and the scatter's chunks past the live count hold no records."""
+    s = inputs.removal_box(1 << 16, seed=3, xi_max=1, p_median=0.5)
+    o, ost, xi, at, gst = _run_both(s, 16, shuffle="sort", schedule=dict(tile_slots=1024, bucket_target=64))
+    _assert_bitexact(o, xi, at)
+    assert 50 < int(np.count_nonzero(xi)) < 300
+
+
 @pytest.mark.parametrize("shuffle", SHUFFLES)
 def test_grid_bimodal_sample_bitexact(shuffle):
     s = inputs.grid_bimodal(nx=32, ny=32)      # the 2D-grid workload on a 32 x 32 patch
