@@ -255,8 +255,8 @@ sdm_status check_schedule(const sdm_schedule& s)
 // Plan tiles (runs of consecutive small cells) and the large-cell buckets.
 // Early-exit bound table (see pb_bin in sdm_math.cuh), computed on the host in
 // double: [0][b] the bin's upper volume edge, [1][b] pi (2 r)^2 vt(r) Emax (1 + 2^-10)
-// at the bin's upper radius r, Emax the largest efficiency of the table rows that
-// radii in the bin interpolate between; both rounded up to float.
+// at the bin's upper radius r, Emax the largest value the interpolated efficiency takes
+// over the radii and radius ratios the bins allow; both rounded up to float.
 void fill_pbound_host(float (*t)[PB_SIZE])   // t[PB_KINDS]
 {
     constexpr double E_h[EFF_NR * EFF_NQ] = {SDM_EFF_VALUES(SDM_AS_DOUBLE)};
@@ -268,12 +268,26 @@ void fill_pbound_host(float (*t)[PB_SIZE])   // t[PB_KINDS]
     auto vt = [](double r) {
         return r < VT_R12 ? VT_K1 * r * r : (r < VT_R23 ? VT_K2 * r : VT_K3 * std::sqrt(r));
     };
-    auto row_of = [](double R) {   // interpolation interval of R, clamped as in the kernels
+    // the kernels' interpolated efficiency (efficiency_d): bilinear on each table cell, the radius
+    // clamped to the nodes' range, q to [0, 1]
+    auto eff = [&](double R, double q) {
         int i = 0;
-        while (i < EFF_NR - 2 && c_eff_R_h[i + 1] <= R) ++i;
-        return i;
+        double t = 0.0;
+        if (R >= c_eff_R_h[EFF_NR - 1]) {
+            i = EFF_NR - 2;
+            t = 1.0;
+        } else if (R > c_eff_R_h[0]) {
+            while (i < EFF_NR - 2 && c_eff_R_h[i + 1] <= R) ++i;
+            t = (R - c_eff_R_h[i]) / (c_eff_R_h[i + 1] - c_eff_R_h[i]);
+        }
+        const double s = q * 10.0;
+        int j = (int)s;
+        double w = s - j;
+        if (j >= EFF_NQ - 1) { j = EFF_NQ - 2; w = 1.0; }
+        const double e0 = E_h[i * EFF_NQ + j] + w * (E_h[i * EFF_NQ + j + 1] - E_h[i * EFF_NQ + j]);
+        const double e1 = E_h[(i + 1) * EFF_NQ + j] + w * (E_h[(i + 1) * EFF_NQ + j + 1] - E_h[(i + 1) * EFF_NQ + j]);
+        return e0 + t * (e1 - e0);
     };
-    auto col_of = [](double q) { return std::min(EFF_NQ - 2, std::max(0, (int)std::floor(q * 10.0))); };
     auto up = [](double x) {
         float f = (float)x;
         if ((double)f < x) f = std::nextafter(f, INFINITY);
@@ -288,11 +302,23 @@ void fill_pbound_host(float (*t)[PB_SIZE])   // t[PB_KINDS]
             t[0][b1 * PB_ROW + d] = up(v_hi(b1) + s_hi);
             const double r_lo = radius(s_lo, 1.0 - 1e-12), r_hi = std::min(radius(s_hi, 1.0 + 1e-12), R_hi);
             const double q_lo = r_lo / R_hi, q_hi = R_lo > 0.0 ? std::min(1.0, r_hi / R_lo) : 1.0;
-            const int i0 = row_of(R_lo), i1 = std::min(EFF_NR - 1, row_of(R_hi) + 1);
-            const int j0 = col_of(q_lo), j1 = std::min(EFF_NQ - 1, col_of(q_hi) + 1);
+            // the interpolant's largest value on [R_lo, R_hi] x [q_lo, q_hi]: bilinear (or constant
+            // in R) on every piece the node lines cut the rectangle into, so it is reached at a
+            // corner of a piece -- a point whose radius is R_lo, R_hi or a node between them and
+            // whose q is q_lo, q_hi or a node between them
+            double Rs[EFF_NR + 2], qs[EFF_NQ + 2];
+            int nr = 0, nq = 0;
+            Rs[nr++] = R_lo;
+            Rs[nr++] = R_hi;
+            for (int i = 0; i < EFF_NR; ++i)
+                if (c_eff_R_h[i] > R_lo && c_eff_R_h[i] < R_hi) Rs[nr++] = c_eff_R_h[i];
+            qs[nq++] = q_lo;
+            qs[nq++] = q_hi;
+            for (int j = 1; j < EFF_NQ - 1; ++j)
+                if (0.1 * j > q_lo && 0.1 * j < q_hi) qs[nq++] = 0.1 * j;
             double emax = 0.0;
-            for (int i = i0; i <= i1; ++i)
-                for (int j = j0; j <= j1; ++j) emax = std::max(emax, E_h[i * EFF_NQ + j]);
+            for (int a = 0; a < nr; ++a)
+                for (int c = 0; c < nq; ++c) emax = std::max(emax, eff(Rs[a], qs[c]));
             const double dvt = std::max(0.0, vt(R_hi) - vt(r_lo)) + 0x1p-12 * (vt(R_hi) + vt(r_hi));
             const double sr = R_hi + r_hi;
             t[1][b1 * PB_ROW + d] = up(PI_D * sr * sr * dvt * emax * (1.0 + 0x1p-10));

@@ -793,8 +793,9 @@ __device__ __forceinline__ bool gamma_tilde_certified(P32 pe, uint64_t u53, uint
 //     with R+- and r+- the radii at the bins' edges (vt grows with the
 //     radius, so |vt1 - vt2| <= vt(R+) - vt(r-); the 2^-12 term covers the
 //     FP32 path's error, which is relative to vt1 + vt2) and Emax the largest
-//     efficiency node of the table rows and columns the interpolation can
-//     reach for R in [R-, R+], q = r/R in [r-/R+, min(1, r+/R-)];
+//     value of the interpolated efficiency for R in [R-, R+], q = r/R in
+//     [r-/R+, min(1, r+/R-)] (bilinear on each table cell, so taken at the
+//     rectangle's corners and where node lines cut its edges or cross inside);
 //   times 1 + 2^-10, rounded up to float.  Filled by the host once per device.
 //   p <= table * c_up * X with c_up = S dt/dV (* b for Golovin) * (1 + 2^-8)
 //   rounded up and X >= max(xi1, xi2) -- per pair the power of two

@@ -376,7 +376,8 @@ def test_fp32_bound_holds_and_fp64_matches_oracle():
 def test_early_exit_bound_holds():
     """The early exit's bound of p (table of the two volumes' bins) is above the FP64 value and the
     FP32 value of every pair: wide random pairs, near-equal pairs, volumes on and just below the
-    bins' edges, radii at the fall-speed regime joins and at efficiency table nodes."""
+    bins' edges, radii at the fall-speed regime joins and at efficiency table nodes, radius ratios
+    at the table's ratio nodes."""
     rng = np.random.default_rng(12)
     n = 300000
     r1 = np.exp(rng.uniform(np.log(0.01e-6), np.log(3e-3), n))
@@ -385,6 +386,10 @@ def test_early_exit_bound_holds():
     r2[near] = r1[near] * (1 + rng.normal(0, 1e-3, near.sum()))
     joins = np.array([8e3 / 1.19e8, (201 / 8e3) ** 2, 10e-6, 20e-6, 30e-6, 60e-6, 100e-6, 150e-6, 300e-6, 1e-3])
     r1[:10000] = np.repeat(joins, 1000) * (1 + rng.normal(0, 1e-7, 10000))
+    # radius ratios at and next to the efficiency table's q nodes (the bound's efficiency factor is
+    # the interpolant's largest value over the bins' rectangle of radius and ratio)
+    qn = np.repeat(np.arange(1, 10) / 10.0, 1000) * (1 + rng.normal(0, 1e-4, 9000))
+    r2[50000:59000] = r1[50000:59000] * qn
     v1 = 4 / 3 * np.pi * r1 ** 3
     v2 = 4 / 3 * np.pi * r2 ** 3
     # volumes on a bin edge 2^e (1 + m/4) and one ulp below it
@@ -410,6 +415,7 @@ def test_early_exit_bound_holds():
         q = np.minimum(v1, v2) / np.maximum(v1, v2)
         sel = (p64 > 0) & (q > 0.03) & (q < 0.7) if kid else p64 > 0
         ratio = np.median(pup[sel] / p64[sel])
+        print("kernel", kid, "cell", ncell, "median bound / p", ratio)
         # the electric-field kernel's rows bound its efficiency by 1 (E_eps >= eps >= 0.5 here)
         assert ratio < (4.0 if kid < 2 else 8.0), (kid, ratio)
 
