@@ -143,6 +143,53 @@ def test_large_cells_with_removals_bitexact(shuffle):
     assert min(live) < 257
 
 
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_small_cells_with_removals_and_reads_bitexact(shuffle):
+    """Cells of one warp (2 to 512 SDs) that lose SDs every step (compacted stably right after the
+    step's queued pairs).  Several steps in one call, then single steps with a different read after
+    each (state, totals, Step 0 alone, spectrum), then steps again: the state equals the oracle's
+    after every leg and the invariants hold."""
+    rng = np.random.default_rng(31)
+    counts = rng.integers(2, 513, 500)
+    n = int(counts.sum())
+    xi = rng.integers(1, 4, n).astype(np.uint64)
+    v = inputs.lognormal_volumes(rng, n, 20e-6, 2.0)
+    s = inputs._state(xi, v, counts, 1e-14, (np.arange(len(counts)) % 2).astype(np.uint8), "small_removals")
+    o = _oracle_system(s, None, shuffle)
+    g = _gpu_state(s, None, dict(tile_slots=512))
+    removed = 0
+    step = 0
+
+    def both(k):
+        nonlocal step, removed
+        o.run(s["dt"], 9, step, k)
+        st = g.step(s["dt"], 9, step, k, golovin_b=s["golovin_b"], stats=True, shuffle=shuffle)
+        removed += st["n_removed"]
+        step += k
+
+    both(6)
+    xi_g, at_g, _ = g.get_state()
+    _assert_bitexact(o, xi_g, at_g)
+    r_edges = np.exp(np.linspace(np.log(1e-6), np.log(5e-3), 41))
+    for read in ("state", "totals", "remove_zero", "spectrum"):
+        both(1)
+        if read == "state":
+            xi_g, at_g, _ = g.get_state()
+            _assert_bitexact(o, xi_g, at_g)
+        elif read == "totals":
+            assert g.totals()[2] == int(np.count_nonzero(o.xi))
+        elif read == "remove_zero":
+            assert g.remove_zero() == int(np.count_nonzero(o.xi))
+        else:
+            assert np.array_equal(g.spectrum(r_edges), o.spectrum(r_edges))
+    both(5)
+    xi_g, at_g, _ = g.get_state()
+    _assert_bitexact(o, xi_g, at_g)
+    assert g.check() == (0, 0)
+    g.close()
+    assert removed > 2000
+
+
 def test_removals_across_contracts_and_state_reads_bitexact():
     """Large cells that lose SDs in a PRP step are compacted at the next step's start, or before a
     state read or a SORT step: PRP steps, a totals() read, SORT steps, PRP steps again -- the
