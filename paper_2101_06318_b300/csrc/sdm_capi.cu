@@ -950,6 +950,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.efield_f = (float)p->efield;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.pk = philox_keys_host(a.seed_lo, a.seed_hi);
     a.d_step = p->d_step;
     a.shuffle = p->shuffle;
     a.n_live = st->d_n_live;
@@ -1814,6 +1815,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
     a.efield_f = (float)p->efield;
     a.seed_lo = (uint32_t)(p->seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.pk = philox_keys_host(a.seed_lo, a.seed_hi);
     a.step = p->step;
     a.shuffle = p->shuffle;
     a.d_step = p->d_step;

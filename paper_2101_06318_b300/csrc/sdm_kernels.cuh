@@ -69,6 +69,7 @@ struct StepArgs {
     float golovin_bf;
     float efield_f;
     uint32_t seed_lo, seed_hi;
+    PhiloxKeys pk;              // the key schedule of (seed_lo, seed_hi)
     uint32_t step;              // used when d_step == nullptr
     uint32_t shuffle;           // SHUFFLE_PRP or SHUFFLE_SORT
     const uint32_t* d_step;
@@ -128,7 +129,7 @@ __device__ __forceinline__ float pair_ratio_dtdv_f(uint32_t n, float dt_f, doubl
 __device__ __forceinline__ void phi_pair_u53(const StepArgs& a, uint32_t cell, uint32_t step, uint32_t M,
                                              uint64_t& u0, uint64_t& u1)
 {
-    const U4 x = philox(M, cell, step, 1u, a.seed_lo, a.seed_hi);
+    const U4 x = philox(M, cell, step, 1u, a.pk);
     u0 = ((((uint64_t)x.x) << 32) | (uint64_t)x.y) >> 11;
     u1 = ((((uint64_t)x.z) << 32) | (uint64_t)x.w) >> 11;
 }
@@ -527,7 +528,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         const uint32_t c = find_segment(gb, nc, g);
         const uint32_t grp = g - gb[c];
         const uint32_t n = ncl[c];
-        const U4 x = philox(grp, td.cell_begin + c, step, 0u, a.seed_lo, a.seed_hi);
+        const U4 x = philox(grp, td.cell_begin + c, step, 0u, a.pk);
         const uint32_t nb = nbit[c];
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
@@ -572,7 +573,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
             // the cell's bijection, once: its index among the tile's PRP cells replaces the
             // bucket bit count, which only sorted cells use
             const uint32_t k = atomicAdd(&wt[39], 1u);
-            prp_init(prp_s[k], a.seed_lo, a.seed_hi, td.cell_begin + c, step, n);
+            prp_init(prp_s[k], a.pk, td.cell_begin + c, step, n);
             nbit[c] = k;
         }
         const uint32_t gid = td.cell_begin + c;
@@ -626,7 +627,7 @@ __device__ void tile_process(const StepArgs& a, const TileDesc td, const TileLay
         const uint32_t M = valid ? t - pb[c] : 0u;
         const CellCtx& cc = ctx[c];
         U4 w = {0, 0, 0, 0};
-        if (valid) w = philox(M, cc.gid, step, 1u, a.seed_lo, a.seed_hi);
+        if (valid) w = philox(M, cc.gid, step, 1u, a.pk);
         const float* __restrict__ tb = g_pbound[cc.kid];
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
@@ -856,7 +857,7 @@ __device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_
     for (uint32_t j = 0; j < NG; ++j) {
         const uint32_t g = lane + 32 * j;
         if (4 * g < n) {
-            const U4 x = philox(g, cell, step, 0u, a.seed_lo, a.seed_hi);
+            const U4 x = philox(g, cell, step, 0u, a.pk);
             if (4 * g + 3 < n) *reinterpret_cast<uint4*>(&S.s.key[4 * g]) = make_uint4(x.x, x.y, x.z, x.w);
 #pragma unroll
             for (uint32_t k = 0; k < 4; ++k) {
@@ -985,7 +986,7 @@ __device__ __forceinline__ void warp_prp_list(const StepArgs& a, SM& S, uint32_t
     const PrpDom dom = c_prp_dom.e[n - PRP_MIN_N];             // PRP_MIN_N <= n <= WC_MAX
     const uint32_t A = dom.ab & 0xffffu, B = dom.ab >> 16, Binv = dom.binv;
     {
-        const U4 x = philox((lane >> 2) & 1u, cell, step, 2u, a.seed_lo, a.seed_hi);
+        const U4 x = philox((lane >> 2) & 1u, cell, step, 2u, a.pk);
         const uint32_t K = u4_word(x, lane & 3u);
         const uint32_t Kx = K ^ (K >> 16);
 #pragma unroll
@@ -1070,7 +1071,7 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
         const uint32_t M = base + lane;
         const bool valid = M < G2;
         U4 wv = {0, 0, 0, 0};
-        if (valid) wv = philox(M, cell, step, 1u, a.seed_lo, a.seed_hi);
+        if (valid) wv = philox(M, cell, step, 1u, a.pk);
         bool need[2];
         uint32_t ii[2];
 #pragma unroll
@@ -1166,7 +1167,7 @@ __global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
             Kh = surr_pair_kernel_warp(a.surr, v1, v2, act && kid == 1);   // the warp's pairs on the tensor cores
         uint32_t rflag = 0;
         if (act) {
-            const uint64_t u53 = phi_u53(a.seed_lo, a.seed_hi, cell, step, q.w & ~WQ_BIG);
+            const uint64_t u53 = phi_u53(a.pk, cell, step, q.w & ~WQ_BIG);
             process_pair<SURR>(a, T, cc, u53, g1, g2, x1, x2, v1, v2, ls, &rflag, Kh);
         }
         if (rflag && atomicExch(&W.flag[cell], 1u) == 0u) {
@@ -1649,7 +1650,7 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
 #pragma unroll
         for (int j = 0; j < (int)PRP_QPT; ++j) {
             U4 w = {0, 0, 0, 0};
-            if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.seed_lo, a.seed_hi);
+            if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.pk);
             exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
                           c_upx, ls, lane);
             exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
@@ -1768,7 +1769,7 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
         const double dv = a.dv[C.cell];
         const float xup = __ull2float_ru(L.xmax[c]);
         Prp P;
-        prp_init(P, a.seed_lo, a.seed_hi, C.cell, step, C.width);
+        prp_init(P, a.pk, C.cell, step, C.width);
         const float* __restrict__ tb = g_pbound[kid];
         uint32_t* const rflag = &bk.removed[c];
         const uint32_t npairs = n >> 1;
@@ -1790,7 +1791,7 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
             // first quad (n, qa and the cell are the same in all threads: a uniform branch)
             __syncthreads();
             for (uint32_t t = tid; t < n; t += nt)
-                key_s[t] = u4_word(philox(t >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi), t & 3u);
+                key_s[t] = u4_word(philox(t >> 2, C.cell, step, 0u, a.pk), t & 3u);
             __syncthreads();
             for (uint32_t t = tid; t < n; t += nt) {
                 const uint32_t kt = key_s[t];
@@ -1802,7 +1803,7 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
             const CellCtx cc{C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
             for (uint32_t mm = tid; mm < npairs; mm += nt) {
                 const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
-                process_pair<SURR>(a, tab, cc, phi_u53(a.seed_lo, a.seed_hi, C.cell, step, mm), s1, s2, a.xi[s1],
+                process_pair<SURR>(a, tab, cc, phi_u53(a.pk, C.cell, step, mm), s1, s2, a.xi[s1],
                              a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
             }
         }
@@ -1966,7 +1967,7 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
     for (uint32_t q = 0; q < BIG_GROUPS_PER_THREAD; ++q) {
         const uint32_t l0 = ch.l_begin + 4 * (tid + q * nt);
         U4 x = {0, 0, 0, 0};
-        if (l0 < l_end) x = philox(l0 >> 2, C.cell, step, 0u, a.seed_lo, a.seed_hi);
+        if (l0 < l_end) x = philox(l0 >> 2, C.cell, step, 0u, a.pk);
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             keys[q][k] = u4_word(x, k);

@@ -37,16 +37,44 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     return U4{c0, c1, c2, c3};
 }
 
+// The key schedule of Philox4x32-10 for one key: round r uses (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85) mod 2^32.  Worked out once on the host and passed with a launch's
+// arguments, so that every round reads its two key words as operands instead of adding them.
+struct PhiloxKeys { uint32_t k0[10], k1[10]; };
+
+inline PhiloxKeys philox_keys_host(uint32_t k0, uint32_t k1)
+{
+    PhiloxKeys K{};
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        K.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+
+// philox() with the schedule of the key given beforehand (the same result)
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const PhiloxKeys& K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ K.k0[r];
+        const uint32_t n2 = hi0 ^ c3 ^ K.k1[r];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
 __device__ __forceinline__ uint32_t u4_word(const U4& x, uint32_t i)
 {
     return i == 0 ? x.x : i == 1 ? x.y : i == 2 ? x.z : x.w;
 }
 
 // 53-bit integer of phi for candidate pair m (phi = u53 * 2^-53).
-__device__ __forceinline__ uint64_t phi_u53(uint32_t seed_lo, uint32_t seed_hi, uint32_t cell,
-                                            uint32_t step, uint32_t m)
+__device__ __forceinline__ uint64_t phi_u53(const PhiloxKeys& K, uint32_t cell, uint32_t step, uint32_t m)
 {
-    const U4 x = philox(m >> 1, cell, step, 1u, seed_lo, seed_hi);
+    const U4 x = philox(m >> 1, cell, step, 1u, K);
     const uint32_t hi = (m & 1u) ? x.z : x.x;
     const uint32_t lo = (m & 1u) ? x.w : x.y;
     return ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 11;
@@ -160,11 +188,10 @@ __device__ __forceinline__ void prp_round_pair_pow2(const Prp& P, uint32_t kl, u
     R += lowbias32_top16((L & (P.A - 1u)) ^ kr) >> P.sb;
 }
 
-__device__ __forceinline__ void prp_init(Prp& P, uint32_t seed_lo, uint32_t seed_hi, uint32_t cell, uint32_t step,
-                                         uint32_t n)
+__device__ __forceinline__ void prp_init(Prp& P, const PhiloxKeys& Kp, uint32_t cell, uint32_t step, uint32_t n)
 {
-    const U4 x = philox(0u, cell, step, 2u, seed_lo, seed_hi);
-    const U4 y = philox(1u, cell, step, 2u, seed_lo, seed_hi);
+    const U4 x = philox(0u, cell, step, 2u, Kp);
+    const U4 y = philox(1u, cell, step, 2u, Kp);
     const uint32_t K[PRP_ROUNDS] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
 #pragma unroll
     for (int r = 0; r < (int)PRP_ROUNDS; ++r) P.K[r] = K[r] ^ (K[r] >> 16);
