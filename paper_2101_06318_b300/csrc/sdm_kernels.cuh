@@ -1131,7 +1131,7 @@ __global__ void __launch_bounds__(32 * WC_WARPS, SMAX < WC_MAX ? SDM_WC_MIN_BLOC
 // constants are gathered, then Step 2 and Step 3 (process_pair).  A cell that lost an SD is listed
 // once for wc_compact_kernel.
 template <bool SURR>
-__global__ void __launch_bounds__(256) wc_pairs_kernel(StepArgs a, WcQueue W)
+__global__ void __launch_bounds__(256, SURR ? 2 : 3) wc_pairs_kernel(StepArgs a, WcQueue W)
 {
     __shared__ unsigned long long red[8];
     const EffTab* __restrict__ T = &g_eff_tab;
