@@ -878,6 +878,7 @@ __device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_
     uint32_t nwork = 0;
 #pragma unroll
     for (uint32_t j = 0; j < NI; ++j) {
+        if (32 * j >= n) break;                                 // uniform: the rest of the list is empty
         const uint32_t l = lane + 32 * j;
         bool lead = false;
         uint32_t b = 0;
