@@ -8,11 +8,12 @@
 //                     workloads): the cell's one-byte volume bins into shared
 //                     memory, the shuffled list (Philox keys and a counting
 //                     sort for up to 256 live SDs, else the keyed bijection
-//                     from per-cell round tables), then per pair phi, the early
-//                     exit against a bound of p, and a queue of the surviving
-//                     pairs that the warp evaluates 32 at a time across its
-//                     cells; cells that lost an SD are compacted stably once
-//                     their queued pairs are done.
+//                     from per-cell round tables), then per pair phi and the
+//                     early exit against a bound of p; the pairs it cannot
+//                     settle go to the step's queue.
+//  wc_pairs_kernel    the queued pairs, one per thread: Steps 2-3 (certified
+//                     FP32 interval, FP64 filters) and the update.
+//  wc_compact_kernel  Step 0 of the cells the queued pairs emptied slots of.
 //  tile_step_kernel   one CTA per run of cells between 512 slots and the
 //                     schedule's tile size: the same steps with the tile's
 //                     multiplicities and volumes in shared memory.
@@ -27,8 +28,9 @@
 //                     scatters (key, position) records into fixed-capacity
 //                     buckets by the key's top bits, the second orders each
 //                     bucket, locates it in the cell's order from the bucket
-//                     offsets, and processes the pairs (gathering the volume
-//                     bins, then multiplicity and volume of the queued pairs).
+//                     offsets and takes its pairs through the early exit; the
+//                     surviving pairs go to the step's queue (the allocation-free
+//                     step's form evaluates them in the finishing warps).
 //
 // Every path realises the same shuffled list of the random-number contract
 // (sort by (key, position), or the keyed bijection), so the tile size, bucket
@@ -733,14 +735,14 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? SDM_TILE_MIN_BLOCKS : 1) t
 
 // ---------------------------------------------------------------------------
 // Small cells, one warp per cell.  A cell of at most WC_MAX slots is stepped by
-// one warp from start to end, with no block barrier: the warp reads the cell's
-// multiplicities and volumes once (what the early exit needs of them -- the
-// volume's bin and the multiplicity's bit length -- goes to shared memory),
-// builds the shuffled list (a counting sort of the Philox keys by their top
-// bits with an exact rank inside each bucket, or the keyed bijection for a
-// cell above 256 SDs under the PRP contract), settles pairs by the early exit,
-// queues the others and evaluates them 32 at a time, and compacts the cell if
-// it lost an SD.  Many independent warps per SM hide each other's latencies.
+// one warp with no block barrier: the warp reads the volume bins of the cell's
+// SDs (one byte each) into shared memory, builds the shuffled list (a counting
+// sort of the Philox keys by their top bits, the keys sharing a bucket ordered
+// within it, or the keyed bijection for a cell above 256 SDs under the PRP
+// contract), settles pairs by the early exit against the cell's multiplicity
+// bound and appends the others to the step's queue, which wc_pairs_kernel
+// evaluates (wc_compact_kernel then compacts the cells that lost an SD).  Many
+// independent warps per SM hide each other's latencies.
 // ---------------------------------------------------------------------------
 constexpr uint32_t WC_MAX = 512;          // slots of a cell stepped by one warp
 constexpr uint32_t WC_WARPS = 4;          // warps per block
