@@ -268,6 +268,26 @@ def test_gravitational_box_full_size_bitexact(shuffle):
     assert gst["n_fp64"] < 1e-3 * gst["n_pairs"]
 
 
+@pytest.mark.parametrize("shuffle", SHUFFLES)
+def test_grid_lognormal_full_size_bitexact(shuffle):
+    """The default benchmark workload at full size (256 x 256 cells, 1.68e7 SDs) in the launch
+    configuration bench.py times (the default schedule): two steps against the oracle's, every
+    multiplicity and volume."""
+    s = inputs.grid_lognormal()
+    o, ost, xi, at, gst = _run_both(s, 2, seed=42, shuffle=shuffle)
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"] > 50000
+
+
+def test_ensemble_full_size_bitexact():
+    """The batched ensemble at full size (1024 boxes, 1.59e7 SDs, Golovin and gravitational
+    kernels mixed) in one step, as the bench launches it."""
+    s = inputs.ensemble()
+    o, ost, xi, at, gst = _run_both(s, 1, seed=42)
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] == gst["n_collisions"] > 0
+
+
 def test_sort_contract_many_bucket_rounds_bitexact():
     """2^20 SDs in 8192 buckets of 128: the finishing pass takes several buckets per warp (its
     three-CTAs-per-SM form); the queues of surviving pairs carry over from bucket to bucket."""
