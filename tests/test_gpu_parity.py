@@ -288,6 +288,33 @@ def test_ensemble_full_size_bitexact():
     assert ost["n_collisions"] == gst["n_collisions"] > 0
 
 
+def test_ensemble_graph_replay_full_size_bitexact():
+    """The ensemble at full size as its benchmark line runs it: steps captured into a CUDA graph
+    with the device step counter and replayed (one step outside the capture, two captured and
+    replayed twice), against five oracle steps."""
+    s = inputs.ensemble()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = _gpu_state(s)
+        d_step = torch.zeros(1, dtype=torch.int32, device="cuda")
+        g.step(s["dt"], 42, 0, 1, golovin_b=s["golovin_b"], d_step=d_step)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            g.step(s["dt"], 42, 0, 2, golovin_b=s["golovin_b"], d_step=d_step)
+        torch.cuda.synchronize()
+        graph.replay()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(d_step.item()) == 5
+        xi, at, _ = g.get_state()
+        g.close()
+    o = _oracle_system(s)
+    ost = o.run(s["dt"], 42, 0, 5)
+    _assert_bitexact(o, xi, at)
+    assert ost["n_collisions"] > 0
+
+
 def test_sort_contract_many_bucket_rounds_bitexact():
     """2^20 SDs in 8192 buckets of 128: the finishing pass takes several buckets per warp (its
     three-CTAs-per-SM form); the queues of surviving pairs carry over from bucket to bucket."""
