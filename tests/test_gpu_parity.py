@@ -279,6 +279,20 @@ def test_grid_lognormal_full_size_bitexact(shuffle):
     assert ost["n_collisions"] == gst["n_collisions"] > 50000
 
 
+def test_grid_lognormal_full_size_fp32_mode():
+    """FP32 mode on the default workload at full size: two steps against the FP64 oracle's; the
+    SDs whose outcome differs stay within the mode's stated bound (2e-5 per SD and step), mass is
+    conserved to 1e-12."""
+    s = inputs.grid_lognormal()
+    o, ost, xi, at, gst = _run_both(s, 2, seed=42, precision="fp32")
+    differing = int(np.count_nonzero((xi != o.xi) | (at[0] != o.attr[0])))
+    print(f"\nFP32 mode, full grid, 2 steps: {differing} of {len(xi)} SDs differ from the FP64 oracle")
+    assert differing <= 2e-5 * 2 * len(xi)
+    m_o = float(np.sum(o.xi.astype(np.float64) * o.attr[0]))
+    m_g = float(np.sum(xi.astype(np.float64) * at[0]))
+    assert m_g == pytest.approx(m_o, rel=1e-12)
+
+
 def test_ensemble_full_size_bitexact():
     """The batched ensemble at full size (1024 boxes, 1.59e7 SDs, Golovin and gravitational
     kernels mixed) in one step, as the bench launches it."""
