@@ -108,7 +108,7 @@ struct sdm_state {
     BucketDesc* d_bucket_desc = nullptr;      // [n_buckets] the cell of each SORT bucket
     uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
     uint32_t* d_cursor = nullptr;            // [n_buckets] appends per bucket (zero between steps)
-    uint32_t* d_bstart = nullptr;            // [n_buckets + n_big] per-cell bucket offsets of the current step
+    uint4* d_plan = nullptr;                 // [n_buckets] each bucket's start, records and cell total this step
     uint32_t* d_ticket = nullptr;            // [n_big] scatter CTAs of each large cell that finished
     uint64_t* d_scratch = nullptr;
     uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
@@ -218,7 +218,7 @@ void free_layout(sdm_state* st)
     st->owned_layout.clear();
     if (st->ws) st->ws_used = st->ws_fixed;
     st->d_tiles = nullptr; st->d_big = nullptr; st->d_chunks = nullptr; st->d_bucket_desc = nullptr;
-    st->d_cursor = nullptr; st->d_bstart = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
+    st->d_cursor = nullptr; st->d_plan = nullptr; st->d_ticket = nullptr; st->d_scratch = nullptr;
     st->d_big_removed = nullptr; st->n_quads = 0; st->d_cta_first = nullptr; st->d_big_xmax = nullptr;
     st->n_tiles = st->n_big = st->n_chunks = st->n_buckets = 0;
     st->d_wcells = nullptr; st->n_wcells = st->wc_grid = st->wc_grid_sort = 0;
@@ -685,14 +685,15 @@ sdm_status build_layout(sdm_state* st)
     st->bucket_cap = bucket_cap;
     st->max_nb = max_nb;
     if (st->n_buckets) {
-        // cursors (n_buckets), the per-cell tickets (n_big), then the per-cell offsets
-        // (n_buckets + n_big), all zeroed once here; afterwards the scatter pass leaves cursors
-        // and tickets at zero at the end of every step
-        const size_t words = 2 * (size_t)st->n_buckets + 2 * (size_t)st->n_big;
+        // cursors (n_buckets) and the per-cell tickets (n_big), zeroed once here; afterwards the
+        // scatter pass leaves them at zero at the end of every step; the buckets' plan; the
+        // records
+        const size_t words = (size_t)st->n_buckets + (size_t)st->n_big;
         SDM_TRY(dev_alloc(st, (void**)&st->d_cursor, sizeof(uint32_t) * words, true));
         SDM_CUDA(cudaMemsetAsync(st->d_cursor, 0, sizeof(uint32_t) * words, st->stream));
         st->d_ticket = st->d_cursor + st->n_buckets;
-        st->d_bstart = st->d_ticket + st->n_big;
+        SDM_TRY(dev_alloc(st, (void**)&st->d_plan, sizeof(uint4) * (size_t)st->n_buckets, true));
+        SDM_CUDA(cudaMemsetAsync(st->d_plan, 0, sizeof(uint4) * (size_t)st->n_buckets, st->stream));
         SDM_TRY(dev_alloc(st, (void**)&st->d_scratch, sizeof(uint64_t) * (size_t)st->n_buckets * bucket_cap, true));
     }
     SDM_TRY(set_smem_limits());
@@ -1038,7 +1039,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                                             st->prp_launch, bb));
         } else if (st->n_big) {
             SDM_TRY(flush_big_compaction(st));      // cells left flagged by a PRP step
-            const BucketBook bk{st->d_cursor, st->d_bstart, st->d_ticket, st->n_buckets, st->bucket_cap};
+            const BucketBook bk{st->d_cursor, st->d_plan, st->d_ticket, st->n_buckets, st->bucket_cap};
             {
                 ProfScope ps(st, 1);
                 big_scatter_kernel<<<st->n_chunks, BIG_SCATTER_THREADS, scatter_smem, st->stream>>>(
@@ -1048,7 +1049,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 ProfScope ps(st, 2);
                 auto fk = st->fin_minb == 2 ? big_finish_kernel<2, true> : big_finish_kernel<3, true>;
                 fk<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_desc, st->d_scratch, st->d_bstart, st->n_buckets, st->d_big_xmax,
+                    a, st->d_big, st->d_bucket_desc, st->d_scratch, st->d_plan, st->n_buckets, st->d_big_xmax,
                     st->fin_L, bb, st->wq);
                 SDM_TRY(launch_queue());                 // the large cells' (and small cells') queued pairs
             }
@@ -1096,7 +1097,8 @@ size_t sdm_workspace_bytes(uint64_t cap, uint32_t n_cell, uint32_t n_attr)
     b += round256(sizeof(BigChunk) * (cap / BIG_CHUNK + n_cell + 1) + 256);
     const size_t max_buckets = 3 * cap / 64 + 1;
     const size_t max_cap = 2 * 2048 + 64 + 32;
-    b += round256(sizeof(BucketDesc) * max_buckets + 256) + round256(16 * max_buckets + 256);
+    b += round256(sizeof(BucketDesc) * max_buckets + 256) + round256(16 * max_buckets + 256);   // descriptors, cursors
+    b += round256(sizeof(uint4) * max_buckets + 256);                                           // plan
     b += round256(8 * max_buckets * max_cap + 256);
     return b;
 }
@@ -1716,10 +1718,12 @@ constexpr size_t NA_OFF_LIVE = 136;      // uint32 cell_start[2], n_live, remova
 constexpr size_t NA_OFF_XMAX = 192;      // uint64 largest multiplicity of the box
 constexpr size_t NA_OFF_CHUNKS = 256;
 constexpr size_t NA_OFF_BBIG = NA_OFF_CHUNKS + sizeof(BigChunk) * NA_MAX_CHUNKS;
-constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + sizeof(BucketDesc) * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket, offsets
-constexpr size_t NA_BOOK_WORDS = 2 * (size_t)NA_MAX_BUCKETS + 2;
-constexpr size_t NA_OFF_RECORDS = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;
+constexpr size_t NA_OFF_CURSOR = (NA_OFF_BBIG + sizeof(BucketDesc) * NA_MAX_BUCKETS + 255) / 256 * 256;  // cursors, ticket
+constexpr size_t NA_BOOK_WORDS = (size_t)NA_MAX_BUCKETS + 1;
+constexpr size_t NA_OFF_PLAN = (NA_OFF_CURSOR + 4 * NA_BOOK_WORDS + 255) / 256 * 256;          // uint4 per bucket
+constexpr size_t NA_OFF_RECORDS = (NA_OFF_PLAN + sizeof(uint4) * NA_MAX_BUCKETS + 255) / 256 * 256;
 constexpr size_t NA_BYTES = NA_OFF_RECORDS + sizeof(uint64_t) * (size_t)NA_MAX_BUCKETS * NA_MAX_CAP;
+static_assert(NA_OFF_RECORDS % 256 == 0, "bulk copies read the records from 16-byte aligned rows");
 
 // one per loaded library and device; its contents persist between calls
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -1835,15 +1839,15 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, live + 6, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);
-        // cursors [NA_MAX_BUCKETS], ticket [1], offsets [NA_MAX_BUCKETS + 1]
-        const BucketBook bk{cursor, cursor + NA_MAX_BUCKETS + 1, cursor + NA_MAX_BUCKETS, nb, cap};
+        // cursors [NA_MAX_BUCKETS], ticket [1]; the plan; the records
+        const BucketBook bk{cursor, (uint4*)(base + NA_OFF_PLAN), cursor + NA_MAX_BUCKETS, nb, cap};
         uint64_t* rec = (uint64_t*)(base + NA_OFF_RECORDS);
         const FinishLayout fl = finish_layout(cap, FINISH_SMEM_WAVE, false);   // at most 1024 buckets: one wave
         const uint32_t scatter_smem = sizeof(uint32_t) * 2 * nb;
         big_scatter_kernel<<<n_chunks, BIG_SCATTER_THREADS, scatter_smem, stream>>>(
             a, d_cell, (const BigChunk*)(base + NA_OFF_CHUNKS), rec, bk);
         big_finish_kernel<2, false><<<(nb + fl.warps - 1) / fl.warps, 32 * fl.warps, fl.bytes, stream>>>(
-            a, d_cell, (const BucketDesc*)(base + NA_OFF_BBIG), rec, bk.bstart, nb, d_xmax, fl, bb, WcQueue{});
+            a, d_cell, (const BucketDesc*)(base + NA_OFF_BBIG), rec, bk.plan, nb, d_xmax, fl, bb, WcQueue{});
     }
     if (p->d_step) advance_step_kernel<<<1, 32, 0, stream>>>(p->d_step, 1u);
     SDM_CUDA(cudaGetLastError());

@@ -814,9 +814,67 @@ __device__ __forceinline__ void warp_exclusive_scan(uint32_t* a, uint32_t n, uin
     __syncwarp();
 }
 
-// the same on 16-bit entries (totals below 2^16)
+// The same on 16-bit entries whose total is below 2^15, for n = 32 * 2 W (W 32-bit words of two
+// entries per lane, 16-byte aligned for W >= 4): one vector load and store per lane, the two halves
+// of each word summed together (no carry between them, the total being below 2^15).
+template <uint32_t W>
+__device__ __forceinline__ void warp_exclusive_scan16_words(uint16_t* a, uint32_t n, uint32_t lane)
+{
+    uint32_t* base = reinterpret_cast<uint32_t*>(a) + lane * W;
+    uint32_t w[W];
+    if constexpr (W >= 4) {
+#pragma unroll
+        for (uint32_t c = 0; c < W / 4; ++c) {
+            const uint4 v = reinterpret_cast<const uint4*>(base)[c];
+            w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+        }
+    } else if constexpr (W == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(base);
+        w[0] = v.x; w[1] = v.y;
+    } else {
+        w[0] = base[0];
+    }
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < W; ++i) t += w[i];
+    const uint32_t s = (t & 0xffffu) + (t >> 16);
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+    }
+    uint32_t run = inc - s;
+#pragma unroll
+    for (uint32_t i = 0; i < W; ++i) {
+        const uint32_t lo = w[i] & 0xffffu, hi = w[i] >> 16;
+        w[i] = run | ((run + lo) << 16);
+        run += lo + hi;
+    }
+    if constexpr (W >= 4) {
+#pragma unroll
+        for (uint32_t c = 0; c < W / 4; ++c)
+            reinterpret_cast<uint4*>(base)[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2*>(base) = make_uint2(w[0], w[1]);
+    } else {
+        base[0] = w[0];
+    }
+    if (lane == 31) a[n] = (uint16_t)run;
+    __syncwarp();
+}
+
+// The same on 16-bit entries (totals below 2^15; a 16-byte aligned array when n >= 256): powers
+// of two from 64 to 512 take the vector form above.
 __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, uint32_t lane)
 {
+    switch (n) {
+    case 64: warp_exclusive_scan16_words<1>(a, n, lane); return;
+    case 128: warp_exclusive_scan16_words<2>(a, n, lane); return;
+    case 256: warp_exclusive_scan16_words<4>(a, n, lane); return;
+    case 512: warp_exclusive_scan16_words<8>(a, n, lane); return;
+    default: break;
+    }
     const uint32_t per = (n + 31) >> 5;
     const uint32_t b0 = min(n, lane * per), b1 = min(n, b0 + per);
     uint32_t s = 0;
@@ -1869,28 +1927,28 @@ constexpr uint32_t BIG_ATOMIC_ILP = 4;        // bucket reservations in flight p
 // Bucket bookkeeping shared by the two passes.
 //   cursor[g]        records appended to bucket g in this step (zero between steps)
 //   ticket[c]        scatter CTAs of large cell c that finished (zero between steps)
-//   bstart[g + c]    for bucket g of large cell c: exclusive prefix of the cell's
-//                    (capacity-clamped) bucket counts; bstart[base_c + c + nb_c] is the
-//                    cell's total, or BUCKET_OVERFLOWED when a bucket of the cell received
-//                    more records than its capacity (the finishing pass then leaves the
-//                    cell unchanged).  Written by the last scatter CTA of the cell, which
+//   plan[g]          for bucket g: (start of the bucket in its cell's sorted list, its
+//                    capacity-clamped record count, the cell's total, 0); the total is
+//                    BUCKET_OVERFLOWED in every bucket of a cell when one of its buckets
+//                    received more records than its capacity (the finishing pass then leaves
+//                    the cell unchanged).  Written by the last scatter CTA of the cell, which
 //                    also clears the cell's cursors and ticket.
 constexpr uint32_t BUCKET_OVERFLOWED = 0xffffffffu;
 struct BucketBook {
     uint32_t* cursor;
-    uint32_t* bstart;
+    uint4* plan;
     uint32_t* ticket;
     uint32_t n_buckets;
     uint32_t cap;
 };
 
-// The last scatter CTA of a cell: offsets of its nb buckets (nb a power of two, at most
+// The last scatter CTA of a cell: the plan of its nb buckets (nb a power of two, at most
 // 8192; blockDim.x == BIG_SCATTER_THREADS).  Each thread takes nb / 256 consecutive
 // buckets (at least one), loading them sixteen at a time with all sixteen loads in flight
 // (so 4096 buckets cost one round trip to L2), staging the clamped counts in
 // shared memory tmp[nb]; then a block scan of the thread sums.
-__device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __restrict__ out, uint32_t nb,
-                                    uint32_t cap, uint32_t* tmp, uint32_t* wt, uint32_t* err)
+__device__ void cell_bucket_plan(uint32_t* __restrict__ cursor, uint4* __restrict__ plan, uint32_t nb,
+                                 uint32_t cap, uint32_t* tmp, uint32_t* wt, uint32_t* err)
 {
     constexpr uint32_t BATCH = 16;
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1931,13 +1989,14 @@ __device__ void cell_bucket_offsets(uint32_t* __restrict__ cursor, uint32_t* __r
             if (lane >= (uint32_t)o) wi += t;
         }
         if (lane < nw) wt[lane] = wi - w;
-        if (lane == 31) out[nb] = cell_over ? BUCKET_OVERFLOWED : wi;   // the cell's total
+        if (lane == 31) wt[32] = cell_over ? BUCKET_OVERFLOWED : wi;   // the cell's total
     }
     __syncthreads();
+    const uint32_t total = wt[32];
     uint32_t run = wt[wid] + inc - s;
     for (uint32_t j = b0; j < b1; ++j) {
         const uint32_t c = tmp[j];
-        out[j] = run;
+        plan[j] = make_uint4(run, c, total, 0u);
         run += c;
     }
 }
@@ -2009,8 +2068,8 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
                 rec[(uint64_t)(C.bucket_base + b) * bk.cap + pos] = (((uint64_t)keys[q][k]) << 32) | (uint64_t)(l0 + k);
         }
     }
-    // the cell's last CTA to finish turns its bucket counts into offsets and clears them
-    // (the cursor atomics above returned, so they are complete before the ticket is taken)
+    // the cell's last CTA to finish turns its bucket counts into the buckets' plan and clears
+    // them (the cursor atomics above returned, so they are complete before the ticket is taken)
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -2019,15 +2078,73 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    cell_bucket_offsets(bk.cursor + C.bucket_base, bk.bstart + C.bucket_base + ch.big, nb, bk.cap, hist, wt, a.err);
+    cell_bucket_plan(bk.cursor + C.bucket_base, bk.plan + C.bucket_base, nb, bk.cap, hist, wt, a.err);
     if (tid == 0) bk.ticket[ch.big] = 0;
 }
 
 // ---------------------------------------------------------------------------
+// One-dimensional bulk copies (TMA) from global into shared memory, completed on
+// an mbarrier: both addresses 16-byte aligned, the size a multiple of 16 bytes.
+// Every wait is bounded: after ASYNC_WAIT_CYCLES of polling the waiter gives up
+// (the caller records ERR_TIMEOUT and stops).
+// ---------------------------------------------------------------------------
+constexpr long long ASYNC_WAIT_CYCLES = 1ll << 31;   // ~1 s at the 2.03 GHz SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// the phase's single arrival, announcing the bytes its copies deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// this thread's earlier generic-proxy accesses of shared memory before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > ASYNC_WAIT_CYCLES) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Large cells, pass 2: one warp per bucket -- sort it, locate it in the cell's
-// order, process its pairs.  Warps never wait for each other (no block barrier
-// after the table is staged), so the loads of one warp overlap the arithmetic
-// of the others.
+// order from its plan, process its pairs.  A warp takes the buckets g, g + W,
+// g + 2W, ... (W warps in the grid); while one is paired, the bulk copy of the
+// next one's records is in flight into the warp's record buffer.  Warps never
+// wait for each other (no block barrier after the table is staged), so the
+// loads of one warp overlap the arithmetic of the others.
 // ---------------------------------------------------------------------------
 constexpr uint32_t FQ_CAP = 64;    // finishing pass: queued pairs per warp (< 32 left + 32 new)
 struct FinQueue {                  // slots of the pair's SDs, phi integer
@@ -2036,26 +2153,32 @@ struct FinQueue {                  // slots of the pair's SDs, phi integer
 };
 
 struct FinishLayout {
-    uint32_t cap;          // records per bucket
-    uint32_t nsub_max;     // sub-bucket counters per warp
+    uint32_t cap;          // records per bucket (a multiple of 32, below 2^15)
+    uint32_t nsub_max;     // sub-buckets of a full bucket (a power of two >= cap)
     uint32_t warps;        // warps (buckets in flight) per CTA
-    uint32_t o_pos, o_cnt, o_trec, o_q, warp_bytes;   // per-warp region layout
+    uint32_t o_rec, o_off, o_tmp, o_srt, o_cnt, o_bar, o_q, warp_bytes;   // per-warp region layout
     uint32_t o_tab, bytes;
 };
 
-// Per warp: a record's arrival index within its sub-bucket (16 bits; later, in the same bytes,
-// the bucket's positions in sorted order, 32 bits), the sub-bucket counters, the records grouped
-// by sub-bucket, and -- when the warp evaluates its pairs itself (queue = false) -- its queue of
-// surviving pairs.
+// Per warp: the bucket's records in arrival order (the bulk copies' destination), each record's
+// arrival index within its sub-bucket (16 bits; later, in the same bytes, the list of sub-buckets
+// holding several records), the arrival indices of those records grouped by sub-bucket, the arrival
+// indices in sorted order, the sub-bucket counters (16 bits, two per word), the copies' mbarrier,
+// and -- when the warp evaluates its pairs itself (queue = false) -- its queue of surviving pairs.
+// Once sorted, the positions in sorted order (32 bits) take the bytes of the arrival indices and
+// the grouped records, and the volume bins in sorted order those of the sorted arrival indices.
 __host__ __device__ inline FinishLayout finish_layout(uint32_t cap, uint32_t max_smem, bool queue = false)
 {
     FinishLayout L;
     L.cap = cap;
-    L.nsub_max = 1u << (ceil_log2(cap > 2 ? cap : 2) - 1);          // about two records per counter
+    L.nsub_max = 1u << ceil_log2(cap > 2 ? cap : 2);                // about one record per sub-bucket
     uint32_t o = 0;
-    L.o_pos = o; o = align_up(o + 4 * cap, 16);
-    L.o_cnt = o; o = align_up(o + 4 * (L.nsub_max + 1), 16);
-    L.o_trec = o; o = align_up(o + 8 * cap, 16);
+    L.o_rec = o; o = align_up(o + 8 * cap, 16);
+    L.o_off = o; o = o + 2 * cap;                                   // cap is even: off and tmp are
+    L.o_tmp = o; o = align_up(o + 2 * cap, 16);                     // contiguous (the positions' 4 cap)
+    L.o_srt = o; o = align_up(o + 2 * cap, 16);
+    L.o_cnt = o; o = align_up(o + 2 * (L.nsub_max + 2), 16);
+    L.o_bar = o; o = align_up(o + 8, 16);
     L.o_q = o;
     if (!queue) o = align_up(o + (uint32_t)sizeof(FinQueue), 16);
     L.warp_bytes = o;
@@ -2095,115 +2218,198 @@ __device__ __forceinline__ void fin_drain(const StepArgs& a, const EffTab* __res
     qcnt -= take;
 }
 
-// One bucket of a large cell under the SORT contract: order its records by (key, position), locate
-// it in the cell's order, and take its pairs through the early exit.  QUEUE: the surviving pairs
-// go to the step's queue (evaluated by wc_pairs_kernel); otherwise to the warp's queue, evaluated
-// here 32 at a time.
-template <bool QUEUE>
-__device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
-                                              const BigCell* __restrict__ cells,
-                                              const BucketDesc* __restrict__ bucket_desc,
-                                              const uint64_t* __restrict__ rec, const uint32_t* __restrict__ bstart,
-                                              const unsigned long long* __restrict__ xmax, const FinishLayout& L,
-                                              unsigned char* ws, uint32_t g, uint32_t lane, uint32_t step,
-                                              LocalStats& ls, uint32_t* removed, FinQueue& Q, uint32_t& qcnt,
-                                              CellCtx& qcc, uint32_t& qbig, const WcQueue& W)
+// The warp's record buffer and its mbarrier; 'pending' while a copy into it is in flight.
+struct FinStage {
+    uint64_t* rec;
+    uint64_t* bar;
+    uint32_t phase;
+    bool pending;
+};
+
+// Start the bulk copy of bucket g's records (plan P) into the record buffer (lane 0 issues it);
+// nothing for an empty bucket or a cell that lost records.  k <= cap and cap even, so the size
+// rounded up to 16 bytes stays inside the bucket's capacity.
+__device__ __forceinline__ void fin_stage(FinStage& F, const uint4& P, uint32_t g, const uint64_t* __restrict__ rec,
+                                          uint32_t cap, uint32_t lane)
 {
-    uint16_t* off = (uint16_t*)(ws + L.o_pos);      // arrival index in the sub-bucket
-    uint32_t* ssl = (uint32_t*)(ws + L.o_pos);      // then: the bucket's positions in sorted order
-    uint32_t* cnt = (uint32_t*)(ws + L.o_cnt);
-    uint64_t* trec = (uint64_t*)(ws + L.o_trec);    // records grouped by sub-bucket
+    if (P.z == BUCKET_OVERFLOWED || P.y == 0) return;
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t bytes = 8u * ((P.y + 1u) & ~1u);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(F.bar, bytes);
+        bulk_copy_g2s(F.rec, rec + (uint64_t)g * cap, bytes, F.bar);
+    }
+    F.pending = true;
+}
+
+// Wait for the copy in flight; false (ERR_TIMEOUT recorded) if it did not land in time, after a
+// second bounded wait for it.
+__device__ __forceinline__ bool fin_wait(FinStage& F, uint32_t* err, uint32_t lane)
+{
+    if (!F.pending) return true;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(F.bar, F.phase));
+    if (!ok) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        mbar_wait_bounded(F.bar, F.phase);
+    }
+    F.pending = false;
+    F.phase ^= 1u;
+    return ok;
+}
+
+// One bucket of a large cell under the SORT contract: order its records by (key, position), locate
+// it in the cell's order, and take its pairs through the early exit.  Its records are in the
+// record buffer or on their way; once the bucket is sorted, the copy of the warp's next bucket gn
+// (plan Pn; has_next) starts.  QUEUE: the surviving pairs go to the step's queue (evaluated by
+// wc_pairs_kernel); otherwise to the warp's queue, evaluated here 32 at a time.  False: a copy did
+// not land in time.
+template <bool QUEUE>
+__device__ __forceinline__ bool finish_bucket(const StepArgs& a, const EffTab* __restrict__ tab,
+                                              const BucketDesc* __restrict__ bucket_desc,
+                                              const uint64_t* __restrict__ rec, const uint4* __restrict__ plan,
+                                              const unsigned long long* __restrict__ xmax, const FinishLayout& L,
+                                              unsigned char* ws, uint32_t g, const uint4& P, bool has_next,
+                                              uint32_t gn, const uint4& Pn, FinStage& F, uint32_t lane,
+                                              uint32_t step, LocalStats& ls, uint32_t* removed, FinQueue& Q,
+                                              uint32_t& qcnt, CellCtx& qcc, uint32_t& qbig, const WcQueue& W)
+{
+    uint64_t* srec = F.rec;                         // records in arrival order
+    uint16_t* off = (uint16_t*)(ws + L.o_off);      // arrival index in the sub-bucket, then the work list
+    uint16_t* tmp = (uint16_t*)(ws + L.o_tmp);      // records of shared sub-buckets, grouped
+    uint16_t* srt = (uint16_t*)(ws + L.o_srt);      // arrival indices in sorted order
+    uint16_t* cnt = (uint16_t*)(ws + L.o_cnt);
+    uint32_t* cw = (uint32_t*)(ws + L.o_cnt);       // the counters two per word
+    uint32_t* ssl = (uint32_t*)(ws + L.o_off);      // once sorted: positions in sorted order
+    uint8_t* sbin = (uint8_t*)(ws + L.o_srt);       // once sorted: volume bins in sorted order
     const uint32_t cap = L.cap;
+    const uint32_t S = P.x, k = P.y, n = P.z;
+    if (n == BUCKET_OVERFLOWED || k == 0) {         // records were lost (the cell stays as it is), or none
+        if (has_next) fin_stage(F, Pn, gn, rec, cap, lane);
+        return true;
+    }
+    // the bucket's cell and its context, loaded ahead of the sort
     const BucketDesc C = bucket_desc[g];
     const uint32_t big = C.big;
     const uint32_t nb = 1u << C.nbits;
-    // where this bucket starts in the cell's sorted list, its size, the cell's live count
-    // (the cell's offsets: bstart[bucket + cell index], its total after its last bucket)
-    const uint32_t* __restrict__ off_c = bstart + C.bucket_base + big;    // [nb + 1]
-    const uint32_t gl = g - C.bucket_base;                                 // bucket in the cell
-    const uint32_t n = off_c[nb];
-    if (n == BUCKET_OVERFLOWED) return;            // records were lost: the cell stays as it is
-    const uint32_t S = off_c[gl];
-    const uint32_t k = off_c[gl + 1] - S;
-    const uint64_t* R = rec + (uint64_t)g * cap;
-    // counting sort on the key bits below the bucket's (the records are read twice from L2, where
-    // the scatter pass left them), then the exact rank by (key, position) within each sub-bucket:
-    // a record is (key << 32) | position, so that order is the records' integer order (positions
-    // differ, so no two records are equal)
-    uint32_t sb = ceil_log2(k > 2 ? k : 2) - 1;
-    if (sb > 32u - C.nbits) sb = 32u - C.nbits;
-    const uint32_t nsub = 1u << sb;
-    for (uint32_t t = lane; t <= nsub; t += 32) cnt[t] = 0;
+    const uint32_t gl = g - C.bucket_base;          // bucket in the cell
+    const uint32_t kid = (uint32_t)a.kid[C.cell];
+    const double dvc = a.dv[C.cell];
+    const unsigned long long xm = xmax[big];
+    if (!fin_wait(F, a.err, lane)) return false;
+    // counting sort on the key bits below the bucket's, about one sub-bucket per record: a record
+    // alone in its sub-bucket goes straight to its place; the records of a sub-bucket holding
+    // several are grouped, the sub-bucket listed once (by its first arrival), and each listed
+    // sub-bucket is then ordered by one lane with an insertion sort.  A record is
+    // (key << 32) | position, so the order by (key, position) is the records' integer order
+    // (positions differ, so no two records are equal).
+    uint32_t nbb = ceil_log2(k > 2 ? k : 2);
+    if (nbb > 32u - C.nbits) nbb = 32u - C.nbits;
+    const uint32_t nsub = 1u << nbb;
+    const uint32_t sh = 32u - nbb;
+    auto sub_of = [&](uint64_t e) { return ((uint32_t)(e >> 32) << C.nbits) >> sh; };
+    for (uint32_t t = lane; 2 * t < nsub; t += 32) cw[t] = 0;
     __syncwarp();
-    const uint32_t sh = 32u - sb;
-    auto sub_of = [&](uint64_t e) { return sb ? ((uint32_t)(e >> 32) << C.nbits) >> sh : 0u; };
-#pragma unroll 4
-    for (uint32_t i = lane; i < k; i += 32) off[i] = (uint16_t)atomicAdd(&cnt[sub_of(__ldcg(R + i))], 1u);
-    __syncwarp();
-    warp_exclusive_scan(cnt, nsub, lane);
 #pragma unroll 4
     for (uint32_t i = lane; i < k; i += 32) {
-        const uint64_t e = __ldcg(R + i);
-        trec[cnt[sub_of(e)] + off[i]] = e;
+        const uint32_t b = sub_of(srec[i]), hs = (b & 1u) << 4;
+        off[i] = (uint16_t)(atomicAdd(&cw[b >> 1], 1u << hs) >> hs);
     }
-    __syncwarp();                                   // off is dead from here: ssl takes its place
-    // FR grouped records per lane at once, so that their sub-bucket scans overlap
-    constexpr uint32_t FR = 4;
-    for (uint32_t p0 = 0; p0 < k; p0 += 32 * FR) {
-        uint64_t e[FR];
-        uint32_t st[FR], len[FR], r[FR], lmax = 0;
-#pragma unroll
-        for (uint32_t j = 0; j < FR; ++j) {
-            const uint32_t p = p0 + lane + 32 * j;
-            e[j] = p < k ? trec[p] : 0ull;
-            const uint32_t sub = sub_of(e[j]);
-            st[j] = p < k ? cnt[sub] : 0u;
-            len[j] = p < k ? cnt[sub + 1] - st[j] : 0u;
-            r[j] = 0;
-            lmax = max(lmax, len[j]);
+    __syncwarp();
+    warp_exclusive_scan16(cnt, nsub, lane);
+    uint32_t nwork = 0;
+    for (uint32_t i0 = 0; i0 < k; i0 += 32) {      // warp-uniform
+        const uint32_t i = i0 + lane;
+        bool lead = false;
+        uint32_t b = 0;
+        if (i < k) {
+            b = sub_of(srec[i]);
+            const uint32_t st = cnt[b], c = cnt[b + 1] - st;
+            const uint32_t o = off[i];
+            if (c == 1) srt[st] = (uint16_t)i;
+            else tmp[st + o] = (uint16_t)i;
+            lead = c > 1 && o == 0;
         }
-        for (uint32_t t = 0; t < lmax; ++t) {
-#pragma unroll
-            for (uint32_t j = 0; j < FR; ++j)
-                if (t < len[j]) r[j] += trec[st[j] + t] < e[j] ? 1u : 0u;
+        // a list entry never lands on an arrival index still to be read
+        const unsigned m = __ballot_sync(0xffffffffu, lead);
+        if (lead) off[nwork + __popc(m & ((1u << lane) - 1u))] = (uint16_t)b;
+        nwork += __popc(m);
+    }
+    __syncwarp();
+    for (uint32_t w = lane; w < nwork; w += 32) {
+        const uint32_t b = off[w];
+        const uint32_t st = cnt[b], en = cnt[b + 1];
+        for (uint32_t i = st; i < en; ++i) {
+            const uint32_t p = tmp[i];
+            const uint64_t ep = srec[p];
+            uint32_t j = i;
+            for (; j > st; --j) {
+                const uint32_t q = srt[j - 1];
+                if (srec[q] < ep) break;
+                srt[j] = (uint16_t)q;
+            }
+            srt[j] = (uint16_t)p;
         }
-        __syncwarp();
+    }
+    __syncwarp();
+    // positions in sorted order, and a gather of their volume bins (one byte each from the bin
+    // array, else the volume's high word) put in flight for the pairs below
+    const uint8_t* __restrict__ vbin = a.vbin;
+    const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
+    constexpr uint32_t FB = 8;                      // bins per lane in flight (the rest one by one)
+    uint32_t bins[FB];
 #pragma unroll
-        for (uint32_t j = 0; j < FR; ++j)
-            if (p0 + lane + 32 * j < k) ssl[st[j] + r[j]] = (uint32_t)e[j];
+    for (uint32_t j = 0; j < FB; ++j) {
+        const uint32_t r = lane + 32 * j;
+        bins[j] = 0;
+        if (r < k) {
+            const uint32_t pos = (uint32_t)srec[srt[r]];
+            const uint64_t e = C.slot_begin + pos;
+            bins[j] = vbin ? (uint32_t)vbin[e] : pb_bin_key(attr_hi[2 * e] >> 18);
+            ssl[r] = pos;
+        }
+    }
+    for (uint32_t r = lane + 32 * FB; r < k; r += 32) ssl[r] = (uint32_t)srec[srt[r]];
+    __syncwarp();
+    // the record buffer is free: the next bucket's copy overlaps this one's pairs
+    if (has_next) fin_stage(F, Pn, gn, rec, cap, lane);
+#pragma unroll
+    for (uint32_t j = 0; j < FB; ++j)
+        if (lane + 32 * j < k) sbin[lane + 32 * j] = (uint8_t)bins[j];
+    for (uint32_t r = lane + 32 * FB; r < k; r += 32) {
+        const uint64_t e = C.slot_begin + ssl[r];
+        sbin[r] = (uint8_t)(vbin ? (uint32_t)vbin[e] : pb_bin_key(attr_hi[2 * e] >> 18));
     }
     // the partner of this bucket's last SD may be the first SD of the next non-empty bucket
     unsigned long long nxt = ~0ull;
+    uint32_t nxt_bin = 0;
     if (((S + k) & 1u) && (S + k < n)) {
         uint32_t b2 = gl + 1;
-        while (b2 < nb && off_c[b2 + 1] == off_c[b2]) ++b2;
+        while (b2 < nb && plan[C.bucket_base + b2].y == 0) ++b2;
         if (b2 < nb) {
             const uint32_t g2 = C.bucket_base + b2;
-            const uint32_t k2 = off_c[b2 + 1] - off_c[b2];
+            const uint32_t k2 = plan[g2].y;
             const uint64_t* R2 = rec + (uint64_t)g2 * cap;
             for (uint32_t i = lane; i < k2; i += 32) {
                 const unsigned long long e = R2[i];
                 nxt = e < nxt ? e : nxt;
             }
             nxt = warp_min_u64(nxt);
+            const uint64_t e = C.slot_begin + (uint32_t)nxt;
+            nxt_bin = vbin ? (uint32_t)vbin[e] : pb_bin_key(attr_hi[2 * e] >> 18);
         }
     }
     __syncwarp();
-    if (k == 0 || n < 2) return;
-    const CellCtx cc = {C.cell, n, (uint32_t)a.kid[C.cell], pair_ratio_dtdv_f(n, a.dt_f, a.dv[C.cell]),
-                        a.dv[C.cell]};
+    if (n < 2) return true;
+    const CellCtx cc = {C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dvc), dvc};
     // pairs m whose first SD (cell position 2m) lies in this bucket: 2m in [S, S+k), 2m+1 < n;
     // each lane takes two consecutive pairs (one Philox call).  The early exit needs the two
-    // volumes' bins (one byte each from the bin array, else the volume's high word) and the
-    // cell's multiplicity bound; the pairs it does not settle are queued.
+    // volumes' bins and the cell's multiplicity bound; the pairs it does not settle are queued.
     const uint32_t m_lo = (S + 1) >> 1;
     const uint32_t m_hi = min((S + k - 1) >> 1, (n >> 1) - 1);      // inclusive
-    if (m_lo > m_hi) return;
-    const float c_upx = __fmul_ru(exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision),
-                                  __ull2float_ru(xmax[big]));
+    if (m_lo > m_hi) return true;
+    const float c_upx = __fmul_ru(exit_scale(cc.s_dtdv32, cc.kid, a.golovin_bf, a.precision), __ull2float_ru(xm));
     const float* __restrict__ tb = g_pbound[cc.kid];
-    const uint8_t* __restrict__ vbin = a.vbin;
-    const uint32_t* attr_hi = reinterpret_cast<const uint32_t*>(a.attr) + 1;
     if (!QUEUE) {
         // the warp's queue carries over from bucket to bucket of one cell (fewer, fuller drains)
         if (qcnt > 0 && qbig != big) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &removed[qbig], ls, lane);
@@ -2212,7 +2418,6 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
     }
     for (uint32_t Mb = m_lo >> 1; Mb <= (m_hi >> 1); Mb += 32) {    // warp-uniform trip count
         const uint32_t M = Mb + lane;
-        // the four slots and their bins first (one round trip), then the arithmetic
         uint32_t sl[2][2], kv[2][2];
         bool ok[2];
 #pragma unroll
@@ -2222,12 +2427,9 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
             const uint32_t r = ok[h] ? 2 * m - S : 0u;
             const bool last = r + 1 >= k;              // partner is the first SD of the next bucket
             sl[h][0] = ssl[r];
-            sl[h][1] = last ? (uint32_t)nxt : ssl[last ? r : r + 1];
-#pragma unroll
-            for (uint32_t j = 0; j < 2; ++j) {
-                const uint64_t e = C.slot_begin + sl[h][j];
-                kv[h][j] = !ok[h] ? 0u : vbin ? (uint32_t)vbin[e] : pb_bin_key(attr_hi[2 * e] >> 18);
-            }
+            sl[h][1] = last ? (uint32_t)nxt : ssl[r + 1];
+            kv[h][0] = ok[h] ? (uint32_t)sbin[r] : 0u;
+            kv[h][1] = !ok[h] ? 0u : last ? nxt_bin : (uint32_t)sbin[r + 1];
         }
         uint64_t u[2] = {0, 0};
         if (M <= (m_hi >> 1)) phi_pair_u53(a, C.cell, step, M, u[0], u[1]);
@@ -2276,6 +2478,7 @@ __device__ __forceinline__ void finish_bucket(const StepArgs& a, const EffTab* _
             }
         }
     }
+    return true;
 }
 
 // MINB: CTAs per SM the registers are sized for -- 2 when all buckets fit one wave of warps
@@ -2286,7 +2489,7 @@ template <int MINB, bool QUEUE>
 __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const BigCell* __restrict__ cells,
                                                          const BucketDesc* __restrict__ bucket_desc,
                                                          const uint64_t* __restrict__ rec,
-                                                         const uint32_t* __restrict__ bstart, uint32_t n_buckets,
+                                                         const uint4* __restrict__ plan, uint32_t n_buckets,
                                                          const unsigned long long* __restrict__ xmax,
                                                          FinishLayout L, BigBook bb, WcQueue W)
 {
@@ -2298,15 +2501,30 @@ __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const
     unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
     const uint32_t step = step_index(a);
     LocalStats ls = {0, 0, 0, 0, 0ull};
+    FinStage F{(uint64_t*)(ws + L.o_rec), (uint64_t*)(ws + L.o_bar), 0u, false};
+    if (lane == 0) mbar_init(F.bar);
     if (!QUEUE) load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;
     __syncthreads();
     FinQueue& Q = *(FinQueue*)(ws + L.o_q);         // used only without QUEUE
     uint32_t qcnt = 0, qbig = 0;                   // warp-uniform
     CellCtx qcc{};
-    for (uint32_t g = blockIdx.x * L.warps + warp; g < n_buckets; g += gridDim.x * L.warps)
-        finish_bucket<QUEUE>(a, tab, cells, bucket_desc, rec, bstart, xmax, L, ws, g, lane, step, ls, bb.removed, Q,
-                             qcnt, qcc, qbig, W);
+    const uint32_t stride = gridDim.x * L.warps;
+    uint32_t g = blockIdx.x * L.warps + warp;
+    if (g < n_buckets) {
+        uint4 P = plan[g];
+        fin_stage(F, P, g, rec, L.cap, lane);
+        for (; g < n_buckets; g += stride) {
+            const uint32_t gn = g + stride;
+            const bool has_next = gn < n_buckets;
+            const uint4 Pn = has_next ? plan[gn] : P;
+            if (!finish_bucket<QUEUE>(a, tab, bucket_desc, rec, plan, xmax, L, ws, g, P, has_next, gn, Pn, F, lane,
+                                      step, ls, bb.removed, Q, qcnt, qcc, qbig, W))
+                break;
+            P = Pn;
+        }
+        fin_wait(F, a.err, lane);                   // nothing in flight after the run (a no-op unless it broke off)
+    }
     if (!QUEUE && qcnt > 0) fin_drain(a, tab, Q, qcnt, qcnt, qcc, &bb.removed[qbig], ls, lane);
     if (a.stats) {
         __syncthreads();
