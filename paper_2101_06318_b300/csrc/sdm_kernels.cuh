@@ -760,7 +760,7 @@ struct __align__(16) WarpCellSmem {
     union __align__(16) {
         struct {                          // Step 1 by sorting keys (n <= SMAX)
             uint32_t key[SMAX];
-            uint16_t cnt[SMAX + 2];       // counts of the 2^ceil(log2 n) top-bit buckets, then offsets
+            uint16_t cnt[(SMAX <= 256 ? 2 : 1) * SMAX + 2];   // bucket counts (warp_sort_keys), then offsets
             uint16_t off[SMAX];           // a position's place in its bucket's arrival order
             uint16_t tmp[SMAX];           // positions grouped by bucket
         } s;
@@ -865,7 +865,7 @@ __device__ __forceinline__ void warp_exclusive_scan16_words(uint16_t* a, uint32_
 }
 
 // The same on 16-bit entries (totals below 2^15; a 16-byte aligned array when n >= 256): powers
-// of two from 64 to 512 take the vector form above.
+// of two from 64 to 1024 take the vector form above.
 __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, uint32_t lane)
 {
     switch (n) {
@@ -873,6 +873,7 @@ __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, u
     case 128: warp_exclusive_scan16_words<2>(a, n, lane); return;
     case 256: warp_exclusive_scan16_words<4>(a, n, lane); return;
     case 512: warp_exclusive_scan16_words<8>(a, n, lane); return;
+    case 1024: warp_exclusive_scan16_words<16>(a, n, lane); return;
     default: break;
     }
     const uint32_t per = (n + 31) >> 5;
@@ -897,7 +898,8 @@ __device__ __forceinline__ void warp_exclusive_scan16(uint16_t* a, uint32_t n, u
 }
 
 // Step 1 by sorting keys: the list ordered by (key, position), key(l) = philox(l >> 2, c, s, 0)[l & 3].
-// Counting sort on the top ceil(log2 n) bits (about one key per bucket): a key alone in its bucket
+// Counting sort on the top ceil(log2 n) + 1 bits for SMAX <= 256 (about one key per two buckets), else
+// on the top ceil(log2 n) bits (about one per bucket; fewer registers): a key alone in its bucket
 // goes straight to its place; the keys of a bucket holding several are grouped, the bucket is
 // listed once, and each listed bucket is ordered by (key, position) with an insertion sort by one
 // lane.  SMAX: the longest list (n <= SMAX), so that the per-key loops have fixed trip counts.
@@ -907,7 +909,7 @@ __device__ __forceinline__ void warp_sort_keys(const StepArgs& a, SM& S, uint32_
 {
     constexpr uint32_t NI = (SMAX + 31) / 32;                  // keys per lane at most
     constexpr uint32_t NG = (SMAX + 127) / 128;                // Philox groups of four keys per lane at most
-    const uint32_t nbb = ceil_log2(n);                         // n >= 2: 2^nbb >= n buckets
+    const uint32_t nbb = ceil_log2(n) + (SMAX <= 256 ? 1u : 0u);   // n >= 2: 2^nbb >= n buckets
     const uint32_t sh = 32u - nbb;
     const uint32_t NBK = 1u << nbb;
     uint32_t* cw = reinterpret_cast<uint32_t*>(S.s.cnt);      // two 16-bit counts per word (n <= 512)
