@@ -1048,9 +1048,19 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             {
                 ProfScope ps(st, 2);
                 auto fk = st->fin_minb == 2 ? big_finish_kernel<2, true> : big_finish_kernel<3, true>;
-                fk<<<st->fin_grid, 32 * st->fin_L.warps, st->fin_L.bytes, st->stream>>>(
-                    a, st->d_big, st->d_bucket_desc, st->d_scratch, st->d_plan, st->n_buckets, st->d_big_xmax,
-                    st->fin_L, bb, st->wq);
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // waits for the scatter
+                at[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                cfg.stream = st->stream;
+                cfg.gridDim = dim3(st->fin_grid);
+                cfg.blockDim = dim3(32 * st->fin_L.warps);
+                cfg.dynamicSmemBytes = st->fin_L.bytes;
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, fk, a, (const BigCell*)st->d_big, (const BucketDesc*)st->d_bucket_desc,
+                                            (const uint64_t*)st->d_scratch, (const uint4*)st->d_plan, st->n_buckets,
+                                            (const unsigned long long*)st->d_big_xmax, st->fin_L, bb, st->wq));
                 SDM_TRY(launch_queue());                 // the large cells' (and small cells') queued pairs
             }
         }

@@ -2015,6 +2015,8 @@ __global__ void __launch_bounds__(BIG_SCATTER_THREADS) big_scatter_kernel(StepAr
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_last;
     __shared__ uint32_t wt[40];
+    // the finishing pass may be scheduled as this grid drains (it waits for it to finish)
+    asm volatile("griddepcontrol.launch_dependents;");
     const BigChunk ch = chunks[blockIdx.x];
     const BigCell C = cells[ch.big];
     const uint32_t nb = 1u << C.nbits;
@@ -2446,19 +2448,14 @@ __device__ __forceinline__ bool finish_bucket(const StepArgs& a, const EffTab* _
             }
         }
         if (QUEUE) {
-            // (cell, slots, pair index m | BIG) to the step's queue, one reservation per warp
-            const uint32_t mine = (uint32_t)need[0] + (uint32_t)need[1];
-            uint32_t pre = mine;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o);
-                if (lane >= (uint32_t)o) pre += t;
-            }
-            const uint32_t tot = __shfl_sync(0xffffffffu, pre, 31);
+            // (cell, slots, pair index m | BIG) to the step's queue, one reservation per warp, lane by lane
+            const unsigned m0 = __ballot_sync(0xffffffffu, need[0]), m1 = __ballot_sync(0xffffffffu, need[1]);
+            const uint32_t tot = __popc(m0) + __popc(m1);
             if (tot) {
                 uint32_t qb = 0;
                 if (lane == 0) qb = atomicAdd(W.count, tot);
-                qb = __shfl_sync(0xffffffffu, qb, 0) + pre - mine;
+                const unsigned lt = (1u << lane) - 1u;
+                qb = __shfl_sync(0xffffffffu, qb, 0) + __popc(m0 & lt) + __popc(m1 & lt);
 #pragma unroll
                 for (uint32_t h = 0; h < 2; ++h)
                     if (need[h])
@@ -2508,6 +2505,10 @@ __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const
     if (!QUEUE) load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;
     __syncthreads();
+    // launched as a dependent of the scatter pass: its records and plan are complete from here;
+    // the pair kernel that follows may be scheduled as this grid drains
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     FinQueue& Q = *(FinQueue*)(ws + L.o_q);         // used only without QUEUE
     uint32_t qcnt = 0, qbig = 0;                   // warp-uniform
     CellCtx qcc{};

@@ -350,6 +350,19 @@ def test_sort_contract_sparse_buckets_bitexact():
     assert 50 < int(np.count_nonzero(xi)) < 300
 
 
+@pytest.mark.parametrize("target", [512, 1024])
+def test_sort_contract_wide_buckets_bitexact(target):
+    """2^16 SDs in buckets of 512 or 1024 on average: a bucket's sub-bucket counters number 512,
+    1024 or 2048 (each form of the warp's 16-bit scan), and the bins past the first 256 of a
+    sorted bucket are gathered one by one."""
+    s = inputs.removal_box(1 << 16, seed=8, xi_max=3, p_median=0.3)
+    o, ost, xi, at, gst = _run_both(s, 6, seed=5, shuffle="sort", schedule=dict(tile_slots=1024, bucket_target=target))
+    _assert_bitexact(o, xi, at)
+    for k in ("n_pairs", "n_collisions", "n_removed"):
+        assert ost[k] == gst[k], k
+    assert gst["n_collisions"] > 1000 and gst["n_removed"] > 0
+
+
 @pytest.mark.parametrize("shuffle", SHUFFLES)
 def test_grid_bimodal_sample_bitexact(shuffle):
     s = inputs.grid_bimodal(nx=32, ny=32)      # the 2D-grid workload on a 32 x 32 patch
