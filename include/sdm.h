@@ -298,9 +298,22 @@ sdm_status sdm_sync(sdm_state* st);
  * the current layout to cap (a multiple of 32, at least 32, at most the
  * current capacity; SDM_EINVAL otherwise), so that a test can make a bucket
  * overflow.  The next layout change (sdm_set_schedule, sdm_init_state*)
- * restores the computed capacity. */
+ * restores the computed capacity.
+ *
+ * sdm_debug_stage_shortfall: in the SORT contract's large-cell step, each
+ * finishing warp stages a bucket's records in shared memory by a bulk copy
+ * whose mbarrier expects the copy's bytes; with extra_bytes != 0 (at most
+ * 4096) every copy announces extra_bytes more than it delivers, so that the
+ * barrier's phase never completes and the warp's bounded wait runs out: the
+ * warp records SDM_ETIMEOUT, waits once more (bounded), and stops without
+ * queueing pairs; no copy is left in flight.  Each wait polls for
+ * 2^wait_log2 SM cycles (10 <= wait_log2 <= 31), or about one second with
+ * wait_log2 = 0.  Applies to the steps enqueued after the call (allocating
+ * entry points only) until it is called again with extra_bytes = 0 and
+ * wait_log2 = 0.  SDM_EINVAL for a NULL state or arguments out of range. */
 sdm_status sdm_debug_wait_timeout(sdm_state* st, uint32_t spin_limit, int withhold);
 sdm_status sdm_debug_bucket_capacity(sdm_state* st, uint32_t cap);
+sdm_status sdm_debug_stage_shortfall(sdm_state* st, uint32_t extra_bytes, uint32_t wait_log2);
 
 /* Release the state and the device memory the library allocated. NULL is a no-op. */
 void sdm_free(sdm_state* st);

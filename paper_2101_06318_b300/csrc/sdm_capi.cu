@@ -107,6 +107,7 @@ struct sdm_state {
     uint32_t n_chunks = 0;
     BucketDesc* d_bucket_desc = nullptr;      // [n_buckets] the cell of each SORT bucket
     uint32_t n_buckets = 0, bucket_cap = 0, max_nb = 0;
+    uint32_t dbg_stage_extra = 0, dbg_wait_log2 = 0;   // sdm_debug_stage_shortfall
     uint32_t* d_cursor = nullptr;            // [n_buckets] appends per bucket (zero between steps)
     uint4* d_plan = nullptr;                 // [n_buckets] each bucket's start, records and cell total this step
     uint32_t* d_ticket = nullptr;            // [n_big] scatter CTAs of each large cell that finished
@@ -959,6 +960,8 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
     a.stats = with_stats ? st->d_stats : nullptr;
     a.err = st->d_err;
     a.surr = st->d_surr;
+    a.stage_extra = st->dbg_stage_extra;
+    a.wait_log2 = st->dbg_wait_log2;
     const sdm_schedule& S = st->sched;
     const uint32_t scatter_smem = sizeof(uint32_t) * 2 * st->max_nb;
     for (uint32_t s = 0; s < n_steps; ++s) {
@@ -1647,6 +1650,14 @@ sdm_status sdm_debug_wait_timeout(sdm_state* st, uint32_t spin_limit, int withho
     cfg.numAttrs = 1;
     SDM_CUDA(cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, words, words + 1, st->d_err, spin_limit,
                                 (uint32_t)(withhold != 0)));
+    return SDM_OK;
+}
+
+sdm_status sdm_debug_stage_shortfall(sdm_state* st, uint32_t extra_bytes, uint32_t wait_log2)
+{
+    if (!st || extra_bytes > 4096 || (wait_log2 != 0 && (wait_log2 < 10 || wait_log2 > 31))) return SDM_EINVAL;
+    st->dbg_stage_extra = extra_bytes;
+    st->dbg_wait_log2 = wait_log2;
     return SDM_OK;
 }
 

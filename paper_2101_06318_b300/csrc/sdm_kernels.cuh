@@ -26,11 +26,13 @@
 //  big_scatter_kernel / big_finish_kernel
 //                     the same cells under the SORT contract: the first pass
 //                     scatters (key, position) records into fixed-capacity
-//                     buckets by the key's top bits, the second orders each
-//                     bucket, locates it in the cell's order from the bucket
-//                     offsets and takes its pairs through the early exit; the
-//                     surviving pairs go to the step's queue (the allocation-free
-//                     step's form evaluates them in the finishing warps).
+//                     buckets by the key's top bits and writes each bucket's
+//                     plan (its start in the cell's order); the second, one
+//                     warp per bucket with the records staged by bulk copies,
+//                     orders each bucket and takes its pairs through the early
+//                     exit; the surviving pairs go to the step's queue (the
+//                     allocation-free step's form evaluates them in the
+//                     finishing warps).
 //
 // Every path realises the same shuffled list of the random-number contract
 // (sort by (key, position), or the keyed bijection), so the tile size, bucket
@@ -80,6 +82,9 @@ struct StepArgs {
     unsigned long long* stats;  // [5] or nullptr
     uint32_t* err;
     const SurrogateDev* surr;   // device copy; used when precision == PREC_SURROGATE
+    uint32_t stage_extra;       // failure-path self-test: bytes a staged bucket's copy announces
+                                // beyond those it delivers (0: none; the wait then runs out)
+    uint32_t wait_log2;         // bounded waits of the staged copies: 2^wait_log2 SM cycles (0: default)
 };
 
 // a cell is shuffled by sorting keys when it is small or the SORT contract is selected
@@ -2134,11 +2139,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > ASYNC_WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -2222,12 +2227,16 @@ __device__ __forceinline__ void fin_drain(const StepArgs& a, const EffTab* __res
     qcnt -= take;
 }
 
-// The warp's record buffer and its mbarrier; 'pending' while a copy into it is in flight.
+// The warp's record buffer and its mbarrier; 'pending' while a copy into it is in flight.  extra:
+// bytes each copy announces beyond those it delivers (the failure-path self-test; 0 otherwise);
+// limit: the SM cycles a wait polls before it gives up.
 struct FinStage {
     uint64_t* rec;
     uint64_t* bar;
     uint32_t phase;
     bool pending;
+    uint32_t extra;
+    long long limit;
 };
 
 // Start the bulk copy of bucket g's records (plan P) into the record buffer (lane 0 issues it);
@@ -2241,7 +2250,7 @@ __device__ __forceinline__ void fin_stage(FinStage& F, const uint4& P, uint32_t 
     if (lane == 0) {
         const uint32_t bytes = 8u * ((P.y + 1u) & ~1u);
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(F.bar, bytes);
+        mbar_arrive_expect_tx(F.bar, bytes + F.extra);
         bulk_copy_g2s(F.rec, rec + (uint64_t)g * cap, bytes, F.bar);
     }
     F.pending = true;
@@ -2252,10 +2261,10 @@ __device__ __forceinline__ void fin_stage(FinStage& F, const uint4& P, uint32_t 
 __device__ __forceinline__ bool fin_wait(FinStage& F, uint32_t* err, uint32_t lane)
 {
     if (!F.pending) return true;
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(F.bar, F.phase));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(F.bar, F.phase, F.limit));
     if (!ok) {
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-        mbar_wait_bounded(F.bar, F.phase);
+        mbar_wait_bounded(F.bar, F.phase, F.limit);
     }
     F.pending = false;
     F.phase ^= 1u;
@@ -2500,7 +2509,8 @@ __global__ void __launch_bounds__(256, MINB) big_finish_kernel(StepArgs a, const
     unsigned char* ws = smem + align_up((uint32_t)sizeof(EffTab), 16) + warp * L.warp_bytes;
     const uint32_t step = step_index(a);
     LocalStats ls = {0, 0, 0, 0, 0ull};
-    FinStage F{(uint64_t*)(ws + L.o_rec), (uint64_t*)(ws + L.o_bar), 0u, false};
+    FinStage F{(uint64_t*)(ws + L.o_rec), (uint64_t*)(ws + L.o_bar), 0u, false, a.stage_extra,
+               a.wait_log2 ? (1ll << a.wait_log2) : ASYNC_WAIT_CYCLES};
     if (lane == 0) mbar_init(F.bar);
     if (!QUEUE) load_eff_tab(tab);
     if (tid < 5) red[tid] = 0;

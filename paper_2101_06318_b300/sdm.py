@@ -37,7 +37,7 @@ EXPORTS = ["sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_alloc", 
            "sdm_launches_per_step", "sdm_coalescence_step_noalloc", "sdm_surrogate_create", "sdm_surrogate_free",
            "sdm_surrogate_train", "sdm_surrogate_build_mask", "sdm_surrogate_params_io", "sdm_surrogate_info",
            "sdm_surrogate_loss_grad", "sdm_surrogate_eval", "sdm_attach_surrogate", "sdm_debug_wait_timeout",
-           "sdm_debug_bucket_capacity"]
+           "sdm_debug_bucket_capacity", "sdm_debug_stage_shortfall"]
 
 
 class SurrogateParams(C.Structure):
@@ -126,6 +126,7 @@ def lib(build_if_needed: bool = True):
         L.sdm_attach_surrogate.argtypes = [vp, vp]
         L.sdm_debug_wait_timeout.argtypes = [vp, u32, i32]
         L.sdm_debug_bucket_capacity.argtypes = [vp, u32]
+        L.sdm_debug_stage_shortfall.argtypes = [vp, u32, u32]
         for name in EXPORTS:
             if name not in ("sdm_version", "sdm_status_str", "sdm_workspace_bytes", "sdm_free", "sdm_surrogate_free"):
                 getattr(L, name).restype = i32
@@ -301,6 +302,10 @@ class State:
 
     def debug_bucket_capacity(self, cap):
         _check(self._L.sdm_debug_bucket_capacity(self._h, int(cap)), "sdm_debug_bucket_capacity")
+
+    def debug_stage_shortfall(self, extra_bytes, wait_log2=0):
+        _check(self._L.sdm_debug_stage_shortfall(self._h, int(extra_bytes), int(wait_log2)),
+               "sdm_debug_stage_shortfall")
 
     # -- schedule ------------------------------------------------------------------
     @property

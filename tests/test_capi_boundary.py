@@ -47,6 +47,7 @@ def test_host_only_calls():
     assert L.sdm_sync(None) == 1
     assert L.sdm_debug_wait_timeout(None, 100, 1) == 1
     assert L.sdm_debug_bucket_capacity(None, 64) == 1
+    assert L.sdm_debug_stage_shortfall(None, 16, 20) == 1
     L.sdm_free(None)
 
 

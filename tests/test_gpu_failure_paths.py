@@ -9,6 +9,10 @@
 * A SORT-contract bucket that overflows (its capacity lowered for the test):
   the step reports SDM_ECAPACITY and leaves the cell unchanged; with the
   capacity restored the same step matches the oracle.
+* The finishing warps' bulk copies announcing more bytes than they deliver
+  (a phase nothing completes): every bounded wait runs out, the step reports
+  SDM_ETIMEOUT and queues no pair of the cell, so the state is unchanged; with
+  the switch off the same step matches the oracle.
 """
 import time
 
@@ -85,5 +89,33 @@ def test_sort_bucket_overflow_reports_capacity_and_leaves_the_cell_unchanged():
     g.close()
     o = _oracle(s, "sort")
     st = o.run(s["dt"], 42, 0, 1)
+    assert st["n_collisions"] > 0
+    assert np.array_equal(o.xi, xi) and np.array_equal(o.attr.view(np.uint64), at.view(np.uint64))
+
+
+def test_staged_copy_wait_runs_out_and_the_state_stays_usable():
+    s = inputs.gravitational_box(n_sd=1 << 16)
+    g = _state(s)
+    with pytest.raises(sdm.SDMError):
+        g.debug_stage_shortfall(8192, 20)           # more than 4096 extra bytes: refused
+    with pytest.raises(sdm.SDMError):
+        g.debug_stage_shortfall(16, 5)              # a wait below 2^10 cycles: refused
+    g.debug_stage_shortfall(16, 20)                 # waits of 2^20 cycles (~0.5 ms)
+    t0 = time.perf_counter()
+    g.step(s["dt"], 42, 0, 1, golovin_b=s["golovin_b"], shuffle="sort")
+    with pytest.raises(sdm.SDMError) as e:
+        g.sync()
+    assert e.value.code == SDM_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    g.sync()                                        # reported once, then cleared
+    xi, at, _ = g.get_state()
+    assert np.array_equal(xi, s["xi"]) and np.array_equal(at[0], s["v"])
+    g.debug_stage_shortfall(0, 0)
+    g.step(s["dt"], 42, 0, 2, golovin_b=s["golovin_b"], shuffle="sort")
+    g.sync()
+    xi, at, _ = g.get_state()
+    g.close()
+    o = _oracle(s, "sort")
+    st = o.run(s["dt"], 42, 0, 2)
     assert st["n_collisions"] > 0
     assert np.array_equal(o.xi, xi) and np.array_equal(o.attr.view(np.uint64), at.view(np.uint64))
