@@ -1164,9 +1164,16 @@ __device__ void warp_cell_step(const StepArgs& a, const WcQueue& W, WarpCellSmem
             qb = __shfl_sync(0xffffffffu, qb, 0) + __popc(m0 & lt) + __popc(m1 & lt);
 #pragma unroll
             for (uint32_t h = 0; h < 2; ++h)
-                if (need[h])
-                    W.q[qb++] = make_uint4(cell, (uint32_t)s0 + (ii[h] & 0xffffu), (uint32_t)s0 + (ii[h] >> 16),
-                                           2 * M + h);
+                if (need[h]) {
+                    const uint64_t g1 = s0 + (ii[h] & 0xffffu), g2 = s0 + (ii[h] >> 16);
+                    W.q[qb++] = make_uint4(cell, (uint32_t)g1, (uint32_t)g2, 2 * M + h);
+                    // the pair kernel reads both SDs' multiplicities and volumes: this kernel
+                    // leaves DRAM nearly idle, so start bringing them to L2 now
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + g1));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + g2));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.attr + g1));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.attr + g2));
+                }
         }
     }
 }
