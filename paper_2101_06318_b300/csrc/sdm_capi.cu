@@ -115,6 +115,7 @@ struct sdm_state {
     uint32_t* d_big_removed = nullptr;       // [n_big] removal flags, then the 64-bit end-of-step ticket
     uint32_t n_quads = 0, prp_grid = 0;      // PRP contract: quads of all large cells, grid size
     uint32_t prp_threads = PRP_THREADS;      // and CTA size
+    bool prp_gq = false;                     // the PRP kernel's surviving pairs go to the step's queue
     uint32_t* d_cta_first = nullptr;         // [prp_grid] first large cell of each CTA (many large cells)
     unsigned long long* d_big_xmax = nullptr;   // [n_big] largest multiplicity of the cell
     // a PRP step may have left large cells flagged for Step 0 since the last compaction;
@@ -382,20 +383,28 @@ sdm_status ensure_device_tables()
 // CTA size of the PRP kernel for a layout with n_big large cells
 uint32_t prp_threads_for(uint32_t n_big) { return n_big >= PRP_MANY_CELLS ? PRP_THREADS_MANY : PRP_THREADS; }
 
+// whether a layout's PRP step queues its large cells' surviving pairs for the pair kernel (many
+// large cells: the finer CTAs) rather than deciding them in the PRP kernel
+bool prp_gq_for(uint32_t threads) { return threads == PRP_THREADS_MANY; }
+
 // Grid of the PRP kernel: one wave of resident CTAs, at most one CTA per warp's worth of quads.
-uint32_t prp_grid_size(uint32_t n_quads, int n_sm, uint32_t threads)
+uint32_t prp_grid_size(uint32_t n_quads, int n_sm, uint32_t threads, bool gq = false)
 {
     // one wave of resident blocks of either instantiation (the launch is cooperative)
     int per_sm = 0, per_sm_s = 0;
     const bool many = threads == PRP_THREADS_MANY;
-    const cudaError_t e1 = many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                      &per_sm, big_prp_kernel<false, PRP_THREADS_MANY>, (int)threads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>,
-                                                                               (int)threads, 0);
-    const cudaError_t e2 = many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                      &per_sm_s, big_prp_kernel<true, PRP_THREADS_MANY>, (int)threads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true>,
-                                                                               (int)threads, 0);
+    const cudaError_t e1 =
+        gq     ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &per_sm, big_prp_kernel<false, PRP_THREADS_MANY, false, true>, (int)threads, 0)
+        : many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false, PRP_THREADS_MANY>,
+                                                               (int)threads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, big_prp_kernel<false>, (int)threads, 0);
+    const cudaError_t e2 =
+        gq     ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &per_sm_s, big_prp_kernel<true, PRP_THREADS_MANY, false, true>, (int)threads, 0)
+        : many ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true, PRP_THREADS_MANY>,
+                                                               (int)threads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, big_prp_kernel<true>, (int)threads, 0);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
         per_sm = per_sm_s = 1;
@@ -660,7 +669,8 @@ sdm_status build_layout(sdm_state* st)
     st->n_quads = n_quads;
     if (n_quads) {
         st->prp_threads = prp_threads_for((uint32_t)bigs.size());
-        st->prp_grid = prp_grid_size(n_quads, st->n_sm, st->prp_threads);
+        st->prp_gq = prp_gq_for(st->prp_threads);
+        st->prp_grid = prp_grid_size(n_quads, st->n_sm, st->prp_threads, st->prp_gq);
         std::vector<uint32_t> first(st->prp_grid);
         for (uint32_t b = 0, c = 0; b < st->prp_grid; ++b) {
             const uint32_t qa = (uint32_t)(((uint64_t)b * n_quads) / st->prp_grid);
@@ -970,6 +980,8 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
         // that fill the queue, as programmatic dependents (their blocks may be scheduled while the
         // previous kernel drains; each waits for it with griddepcontrol.wait)
         const bool sort_big = st->n_big && p->shuffle == SDM_SHUFFLE_SORT;
+        const bool prp_gq = st->n_big && p->shuffle == SDM_SHUFFLE_PRP && st->prp_gq;
+        const bool queue_after_big = sort_big || prp_gq;
         auto launch_queue = [&]() -> sdm_status {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
@@ -997,7 +1009,7 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
                 else                                      // above 256 SDs the keyed bijection
                     warp_cells_kernel<WC_SORT_PRP><<<st->wc_grid, 32 * WC_WARPS, 0, st->stream>>>(
                         a, st->wq, st->d_wcells, st->n_wcells);
-                if (!sort_big) SDM_TRY(launch_queue());
+                if (!queue_after_big) SDM_TRY(launch_queue());
             }
             if (st->n_tiles) {
                 uint32_t grid = st->n_tiles;
@@ -1018,10 +1030,12 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             // cooperative: a step that finds cells flagged by the previous one compacts them first,
             // behind a grid barrier (every block resident)
             ProfScope ps(st, 3);
-            st->big_deferred = true;
-            cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-            SDM_CUDA(cudaStreamIsCapturing(st->stream, &cap_status));
-            if (cap_status != cudaStreamCaptureStatusNone) st->big_deferred_always = true;
+            if (!prp_gq) {      // cells that lose SDs stay flagged until the next launch's Step 0
+                st->big_deferred = true;
+                cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+                SDM_CUDA(cudaStreamIsCapturing(st->stream, &cap_status));
+                if (cap_status != cudaStreamCaptureStatusNone) st->big_deferred_always = true;
+            }
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(st->prp_grid);
             cfg.blockDim = dim3(st->prp_threads);
@@ -1033,13 +1047,19 @@ sdm_status launch_steps(sdm_state* st, const sdm_step_params* p, uint32_t n_step
             cfg.attrs = at;
             cfg.numAttrs = 1;
             const bool surr = p->precision == SDM_PREC_SURROGATE;
-            if (st->prp_threads == PRP_THREADS_MANY)
+            if (prp_gq) {
+                SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? big_prp_kernel<true, PRP_THREADS_MANY, false, true>
+                                                       : big_prp_kernel<false, PRP_THREADS_MANY, false, true>,
+                                            a, st->prp_launch, bb, st->wq));
+                SDM_TRY(launch_queue());                 // the large cells' (and small cells') queued pairs
+            } else if (st->prp_threads == PRP_THREADS_MANY) {
                 SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? big_prp_kernel<true, PRP_THREADS_MANY>
                                                        : big_prp_kernel<false, PRP_THREADS_MANY>,
-                                            a, st->prp_launch, bb));
-            else
+                                            a, st->prp_launch, bb, WcQueue{}));
+            } else {
                 SDM_CUDA(cudaLaunchKernelEx(&cfg, surr ? big_prp_kernel<true> : big_prp_kernel<false>, a,
-                                            st->prp_launch, bb));
+                                            st->prp_launch, bb, WcQueue{}));
+            }
         } else if (st->n_big) {
             SDM_TRY(flush_big_compaction(st));      // cells left flagged by a PRP step
             const BucketBook bk{st->d_cursor, st->d_plan, st->d_ticket, st->n_buckets, st->bucket_cap};
@@ -1696,7 +1716,7 @@ sdm_status sdm_launches_per_step(sdm_state* st, uint32_t shuffle, uint32_t* n)
     // cells the previous step left flagged) or scatter + finish (SORT contract)
     // small cells: one kernel per kind; large cells: one kernel (PRP contract) or scatter + finish
     // (SORT contract); the queue's pair and compaction kernels once when any kernel fills it
-    const bool queue = st->n_wcells || (st->n_big && shuffle == SDM_SHUFFLE_SORT);
+    const bool queue = st->n_wcells || (st->n_big && (shuffle == SDM_SHUFFLE_SORT || st->prp_gq));
     *n = (st->n_wcells ? 1u : 0u) + (st->n_tiles ? 1u : 0u) + (queue ? 2u : 0u) +
          (st->n_big ? (shuffle == SDM_SHUFFLE_PRP ? 1u : 2u) : 0u);
     return SDM_OK;
@@ -1856,7 +1876,7 @@ extern "C" sdm_status sdm_coalescence_step_noalloc(uint64_t* xi, double* attr, u
         BigLaunch L{1, n_quads, d_cell, d_xmax, nullptr, {}};
         L.pc[0] = C;
         big_prp_kernel<false, PRP_THREADS, false><<<prp_grid_size(n_quads, n_sm, PRP_THREADS), PRP_THREADS, 0, stream>>>(
-            a, L, bb);
+            a, L, bb, WcQueue{});
         SDM_TRY(launch_big_compact(a, d_cell, live + 3, 1, live + 6, n_sm, stream));
     } else {
         uint32_t* cursor = (uint32_t*)(base + NA_OFF_CURSOR);

@@ -1665,17 +1665,47 @@ __device__ __forceinline__ void exit_or_queue(const StepArgs& a, PairQueue& Q, u
     qcnt += __popc(m);
 }
 
+// The same for a layout whose large cells' surviving pairs go to the step's queue (evaluated by
+// wc_pairs_kernel, the cells that lost SDs compacted by wc_compact_kernel): (cell, slots, pair
+// index m | WQ_BIG) appended, one reservation per warp; the SDs' multiplicities and volumes
+// prefetched into L2 for the pair kernel.
+__device__ __forceinline__ void exit_or_gqueue(const StepArgs& a, const WcQueue& W, bool has, uint32_t cell,
+                                               uint32_t s1, uint32_t s2, uint32_t m, uint32_t k1, uint32_t k2,
+                                               uint32_t w_hi, const float* __restrict__ tb, float c_upx,
+                                               LocalStats& ls, uint32_t lane)
+{
+    bool need = false;
+    if (has) {
+        need = !(__fmul_ru(__ldg(tb + pb_index(k1, k2)), c_upx) <= phi_lo23(w_hi));
+        ls.pairs += need ? 0u : 1u;
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, need);
+    if (mk) {
+        uint32_t qb = 0;
+        if (lane == 0) qb = atomicAdd(W.count, (uint32_t)__popc(mk));
+        qb = __shfl_sync(0xffffffffu, qb, 0) + __popc(mk & ((1u << lane) - 1u));
+        if (need) {
+            W.q[qb] = make_uint4(cell, s1, s2, m | WQ_BIG);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + s1));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.xi + s2));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.attr + s1));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.attr + s2));
+        }
+    }
+}
+
 // The quads [sa, sb) of one large cell for one warp: per iteration PRP_QPT quads
 // per lane (quads g, g + 32, ...; a warp-uniform trip count), their bijection
 // images, the gathers of the volumes' high words, the early exit and the queue
 // of pairs that need the kernel.  FULL: n = A B is a power of two, so no image
-// walks and the rounds take their shift-and-mask form.
-template <bool SURR, bool FULL>
+// walks and the rounds take their shift-and-mask form.  GQ: the surviving pairs go to the step's
+// queue W instead of the warp's (whose memory then only holds the walk lists).
+template <bool SURR, bool FULL, bool GQ>
 __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* __restrict__ tab, const CellCtx& cc,
                                                const Prp& P, const BigCell& C, uint32_t sa, uint32_t sb,
                                                uint32_t step, const float* __restrict__ tb, float c_upx, PairQueue& Q,
                                                uint32_t& qcnt, LocalStats& ls, uint32_t* rflag, uint32_t warp,
-                                               uint32_t lane, uint32_t nt)
+                                               uint32_t lane, uint32_t nt, const WcQueue& W)
 {
     const uint32_t npairs = cc.n >> 1;
     // PRP_QPT quads per thread and iteration: g, g + 32, ... (warp-uniform trip count)
@@ -1726,28 +1756,38 @@ __device__ __forceinline__ void prp_cell_quads(const StepArgs& a, const EffTab* 
         for (int j = 0; j < (int)PRP_QPT; ++j) {
             U4 w = {0, 0, 0, 0};
             if (h0[j]) w = philox(qj[j], C.cell, step, 1u, a.pk);
-            exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
-                          c_upx, ls, lane);
-            exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
-                          w.w, tb, c_upx, ls, lane);
+            if (GQ) {
+                exit_or_gqueue(a, W, h0[j], C.cell, e[4 * j], e[4 * j + 1], 2 * qj[j], vh[4 * j], vh[4 * j + 1], w.x,
+                               tb, c_upx, ls, lane);
+                exit_or_gqueue(a, W, h1[j], C.cell, e[4 * j + 2], e[4 * j + 3], 2 * qj[j] + 1, vh[4 * j + 2],
+                               vh[4 * j + 3], w.z, tb, c_upx, ls, lane);
+            } else {
+                exit_or_queue(a, Q, qcnt, h0[j], e[4 * j], e[4 * j + 1], vh[4 * j], vh[4 * j + 1], w.x, w.y, tb,
+                              c_upx, ls, lane);
+                exit_or_queue(a, Q, qcnt, h1[j], e[4 * j + 2], e[4 * j + 3], vh[4 * j + 2], vh[4 * j + 3], w.z,
+                              w.w, tb, c_upx, ls, lane);
+            }
         }
-        if (FULL) {
+        if (GQ) {
+        } else if (FULL) {
             while (qcnt >= 32) drain_queue<SURR>(a, tab, cc, Q, qcnt, 32, ls, rflag, lane);
         } else {                      // empty the queue for the next walk list
             while (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, min(qcnt, 32u), ls, rflag, lane);
         }
     }
-    if (qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
+    if (!GQ && qcnt > 0) drain_queue<SURR>(a, tab, cc, Q, qcnt, qcnt, ls, rflag, lane);
 }
 
 // THREADS: CTA size (the same registers and warps per SM for both sizes)
 // STEP0: the launch may find cells flagged by the previous launch and compact them first (the
 // allocating path); false where a compaction kernel always follows the step (the
-// allocation-free call), so no launch ever starts with a flagged cell.
-template <bool SURR, uint32_t THREADS = PRP_THREADS, bool STEP0 = true>
-__global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / THREADS) big_prp_kernel(StepArgs a,
-                                                                                                     BigLaunch L,
-                                                                                                     BigBook bk)
+// allocation-free call, and GQ), so no launch ever starts with a flagged cell.
+// GQ: the surviving pairs go to the step's queue W (wc_pairs_kernel decides them and
+// wc_compact_kernel compacts the cells that lost SDs, in the same step): the kernel then holds
+// neither the pairs' decisions nor Step 0.
+template <bool SURR, uint32_t THREADS = PRP_THREADS, bool STEP0 = true, bool GQ = false>
+__global__ void __launch_bounds__(THREADS, (GQ ? 3 : 2) * SDM_PRP_MIN_BLOCKS * PRP_THREADS / THREADS / 2)
+    big_prp_kernel(StepArgs a, BigLaunch L, BigBook bk, WcQueue W)
 {
     const EffTab* __restrict__ tab = &g_eff_tab;   // read through L1: no staging on the critical path
     // a compaction kernel that follows (allocation-free step) may start launching
@@ -1853,13 +1893,13 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
             const CellCtx cc{C.cell, n, kid, s32, dv};
             const float c_upx = __fmul_ru(exit_scale(s32, kid, a.golovin_bf, a.precision), xup);
             if (P.pow2 && n == C.width) {
-                prp_cell_quads<SURR, true>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp, lane,
-                                           nt);
+                prp_cell_quads<SURR, true, GQ>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp,
+                                               lane, nt, W);
             } else {
                 if (!prp_same_network(P, n)) prp_set_domain(P, n);
                 P.n = n;
-                prp_cell_quads<SURR, false>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp, lane,
-                                            nt);
+                prp_cell_quads<SURR, false, GQ>(a, tab, cc, P, C, sa, sb, step, tb, c_upx, Q, qcnt, ls, rflag, warp,
+                                                lane, nt, W);
             }
         } else if (n >= 2 && C.quad_begin >= qa) {
             // few live SDs left in a large cell: sorted by key by the CTA holding the cell's
@@ -1875,11 +1915,24 @@ __global__ void __launch_bounds__(THREADS, SDM_PRP_MIN_BLOCKS * PRP_THREADS / TH
                 srt_s[r] = (uint16_t)t;
             }
             __syncthreads();
-            const CellCtx cc{C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
-            for (uint32_t mm = tid; mm < npairs; mm += nt) {
-                const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
-                process_pair<SURR>(a, tab, cc, phi_u53(a.pk, C.cell, step, mm), s1, s2, a.xi[s1],
-                             a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
+            if (GQ) {                                   // every pair to the step's queue
+                for (uint32_t m0 = warp * 32; m0 < npairs; m0 += nt) {   // warp-uniform
+                    const uint32_t mm = m0 + lane;
+                    const unsigned mk = __ballot_sync(0xffffffffu, mm < npairs);
+                    uint32_t qb = 0;
+                    if (lane == 0) qb = atomicAdd(W.count, (uint32_t)__popc(mk));
+                    qb = __shfl_sync(0xffffffffu, qb, 0) + lane;
+                    if (mm < npairs)
+                        W.q[qb] = make_uint4(C.cell, C.slot_begin + srt_s[2 * mm], C.slot_begin + srt_s[2 * mm + 1],
+                                             mm | WQ_BIG);
+                }
+            } else {
+                const CellCtx cc{C.cell, n, kid, pair_ratio_dtdv_f(n, a.dt_f, dv), dv};
+                for (uint32_t mm = tid; mm < npairs; mm += nt) {
+                    const uint64_t s1 = C.slot_begin + srt_s[2 * mm], s2 = C.slot_begin + srt_s[2 * mm + 1];
+                    process_pair<SURR>(a, tab, cc, phi_u53(a.pk, C.cell, step, mm), s1, s2, a.xi[s1],
+                                 a.xi[s2], a.attr[s1], a.attr[s2], ls, rflag);
+                }
             }
         }
     }

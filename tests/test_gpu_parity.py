@@ -377,6 +377,24 @@ def test_ensemble_sample_bitexact(shuffle):
     _assert_bitexact(o, xi, at)
 
 
+def test_many_large_cells_with_small_cells_bitexact():
+    """70 boxes of 1100 .. 3000 SDs of multiplicity 1 or 2 next to 300 small cells, all losing SDs
+    every step: the PRP step of a layout with this many large cells queues their surviving pairs
+    with the small cells' pairs (one pair kernel, one compaction for both), and boxes that fall
+    below 257 live SDs have all their pairs queued."""
+    rng = np.random.default_rng(17)
+    boxes = [inputs.removal_box(int(n), seed=100 + i, xi_max=2, p_median=0.25)
+             for i, n in enumerate(rng.integers(1100, 3000, 70))]
+    small = inputs.random_cells(n_cell=300, mean_per_cell=40, seed=4, dead_fraction=0.05, xi_max=3, dv=1e-12)
+    s = inputs.concat_states(boxes + [small])
+    o, ost, xi, at, gst = _run_both(s, 15, seed=9)
+    _assert_bitexact(o, xi, at)
+    for k in ("n_pairs", "n_collisions", "n_removed", "sum_gamma"):
+        assert ost[k] == gst[k], k
+    live = [int(np.count_nonzero(xi[a:b])) for a, b in zip(s["cell_start"][:70], s["cell_start"][1:71])]
+    assert gst["n_removed"] > 10000 and min(live) < 257
+
+
 def test_many_large_cells_bitexact():
     """80 boxes of 2^10 .. 2^13 SDs, each a large cell: the PRP step runs in its finer CTAs
     (64 threads) when a layout holds this many large cells."""
