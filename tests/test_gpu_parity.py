@@ -395,6 +395,29 @@ def test_many_large_cells_with_small_cells_bitexact():
     assert gst["n_removed"] > 10000 and min(live) < 257
 
 
+def test_many_large_cells_alternating_contracts_bitexact():
+    """70 large cells (the PRP step's queue form) losing SDs every step, stepped under the PRP and
+    SORT contracts in turn: neither contract's step leaves a cell uncompacted for the other."""
+    rng = np.random.default_rng(23)
+    boxes = [inputs.removal_box(int(n), seed=200 + i, xi_max=2, p_median=0.25)
+             for i, n in enumerate(rng.integers(1100, 3000, 70))]
+    s = inputs.concat_states(boxes)
+    o = _oracle_system(s)
+    g = _gpu_state(s)
+    removed = 0
+    for k, shuffle in enumerate(["prp", "prp", "sort", "prp", "sort", "sort", "prp", "prp"]):
+        o.shuffle = shuffle
+        o.run(s["dt"], 13, k, 1)
+        st = g.step(s["dt"], 13, k, 1, golovin_b=s["golovin_b"], stats=True, shuffle=shuffle)
+        removed += st["n_removed"]
+    g.sync()
+    xi, at, _ = g.get_state()
+    assert g.check() == (0, 0)
+    g.close()
+    _assert_bitexact(o, xi, at)
+    assert removed > 10000
+
+
 def test_many_large_cells_bitexact():
     """80 boxes of 2^10 .. 2^13 SDs, each a large cell: the PRP step runs in its finer CTAs
     (64 threads) when a layout holds this many large cells."""
