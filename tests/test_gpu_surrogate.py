@@ -180,3 +180,39 @@ def test_what_the_surrogate_gains(trained):
     assert l1["fp64"] == 0.0 and dn["fp64"] == 0.0
     assert l1["surrogate"] < 1e-3 and abs(dn["surrogate"]) < 1e-4
     assert ratio > 1.2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "surrogate"])
+def test_many_cell_queue_form_equals_one_cell_form(trained, prec):
+    """The PRP step of a layout of 64 or more large cells decides the pairs its early exit leaves
+    in the pair kernel (its queue form); a layout holding one large cell decides them in the PRP
+    kernel.  70 gravitational boxes stepped together, and some of them stepped alone in a state of
+    the same 70 cells with the others empty (so with the same cell indices and random streams):
+    each box's state after eight steps is the same bit for bit, in every precision."""
+    s, _, _, _ = trained
+    rng = np.random.default_rng(41)
+    boxes = [inputs.gravitational_box(n_sd=int(n), seed=300 + i) for i, n in enumerate(rng.integers(1100, 2600, 70))]
+    full = inputs.concat_states(boxes)
+    cs = full["cell_start"].astype(np.int64)
+
+    def run(state):
+        g = sdm.from_inputs(state)
+        if prec == "surrogate":
+            g.attach_surrogate(s)
+        st = g.step(state["dt"], 5, 0, 8, precision=prec, stats=True)
+        g.sync()
+        xi, at, _ = g.get_state()
+        g.close()
+        return xi, at[0], st
+
+    xi_all, v_all, st_all = run(full)
+    assert st_all["n_collisions"] > 1000
+    for i in (0, 17, 42, 69):
+        lo, hi = cs[i], cs[i + 1]
+        counts = np.zeros(70, np.int64)
+        counts[i] = hi - lo
+        one = inputs._state(full["xi"][lo:hi], full["v"][lo:hi], counts, full["dv"], full["kernel_id"], "one",
+                            dt=full["dt"], golovin_b=full["golovin_b"])
+        xi1, v1, _ = run(one)
+        assert np.array_equal(xi1, xi_all[lo:hi]), i
+        assert np.array_equal(v1.view(np.uint64), v_all[lo:hi].view(np.uint64)), i
