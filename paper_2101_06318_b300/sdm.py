@@ -314,8 +314,13 @@ class State:
         _check(self._L.sdm_get_schedule(self._h, C.byref(s)), "sdm_get_schedule")
         return s.as_dict()
 
-    def set_schedule(self, tile_slots=1024, tile_threads=256, bucket_target=1024, persistent=0):
-        s = Schedule(tile_slots, tile_threads, bucket_target, persistent)
+    def set_schedule(self, tile_slots=None, tile_threads=None, bucket_target=None, persistent=None):
+        """Set the launch schedule; a field left as None keeps its current value."""
+        cur = self.schedule
+        s = Schedule(cur["tile_slots"] if tile_slots is None else tile_slots,
+                     cur["tile_threads"] if tile_threads is None else tile_threads,
+                     cur["bucket_target"] if bucket_target is None else bucket_target,
+                     cur["persistent"] if persistent is None else persistent)
         _check(self._L.sdm_set_schedule(self._h, C.byref(s)), "sdm_set_schedule")
 
     def autotune(self, dt=1.0, seed=42, step=0, n_steps=3, precision="fp64", golovin_b=1500.0, shuffle="prp"):

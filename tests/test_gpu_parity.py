@@ -831,6 +831,19 @@ def test_device_pointer_init_and_workspace():
     assert e.value.code == 2
 
 
+def test_set_schedule_keeps_the_fields_not_given():
+    """The binding's set_schedule changes only the fields it is given (the library's defaults:
+    1024-slot tiles of 256 threads, 256-SD buckets, no persistent grid)."""
+    s = inputs.gravitational_box(n_sd=1 << 12)
+    g = _gpu_state(s)
+    before = g.schedule
+    assert before == {"tile_slots": 1024, "tile_threads": 256, "bucket_target": 256, "persistent": 0}
+    g.set_schedule(tile_slots=2048)
+    after = g.schedule
+    g.close()
+    assert after == dict(before, tile_slots=2048)
+
+
 def test_autotune_keeps_results():
     s = inputs.random_cells(n_cell=500, mean_per_cell=100, seed=3, xi_max=10 ** 4, dv=1e-2)
     a = _gpu_state(s)
